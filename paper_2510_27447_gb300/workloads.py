@@ -1,0 +1,298 @@
+"""Seeded synthetic inputs for the partitioned bidomain step.
+
+This module builds the *inputs* of a simulation and nothing else: node
+coordinates, element connectivity, per-element fibre directions, stimulus node
+sets, seeded perturbations of an initial state and the arrival stream of the
+serving workload.  It holds none of the method's arithmetic (no assembly, no
+ionic model, no time stepping), so that the FP64 oracle and the CUDA path can
+both be fed from it without sharing any computation.
+
+Workload shapes follow the paper's experiments (Sec. 4): structured P1 meshes
+of the unit square / square sheets (Sec. 4.1-4.2; the paper uses Q1 quads of
+the same node grid), a 3-D slab with transmural fibre rotation (Sec. 4.4) and
+S1-S2 stimulation protocols (Sec. 4.3).  All randomness uses numpy's PCG64 with
+an explicit seed.
+
+Units throughout: cm, ms, mV, mS/cm, uA/cm^2, uF/cm^2, 1/cm.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# meshes
+# ---------------------------------------------------------------------------
+
+
+def rect_grid(nx: int, ny: int, lx: float, ly: float) -> Tuple[np.ndarray, np.ndarray]:
+    """Structured P1 triangle mesh of [0,lx]x[0,ly] with nx x ny nodes.
+
+    Node (i, j) (i along x, j along y) has index j*nx + i.  Every grid cell is
+    split along its (i,j)->(i+1,j+1) diagonal into two counter-clockwise
+    triangles.  Returns (xyz[N,2] float64, tris[E,3] int32).
+    """
+    if nx < 2 or ny < 2:
+        raise ValueError("rect_grid needs at least 2 nodes per direction")
+    X, Y = np.meshgrid(np.linspace(0.0, lx, nx), np.linspace(0.0, ly, ny), indexing="xy")
+    xyz = np.stack([X.ravel(), Y.ravel()], axis=1).astype(np.float64)
+    i, j = np.meshgrid(np.arange(nx - 1), np.arange(ny - 1), indexing="xy")
+    i = i.ravel()
+    j = j.ravel()
+    a = j * nx + i
+    b = j * nx + i + 1
+    c = (j + 1) * nx + i + 1
+    d = (j + 1) * nx + i
+    tris = np.empty((2 * len(a), 3), dtype=np.int32)
+    tris[0::2] = np.stack([a, b, c], axis=1)
+    tris[1::2] = np.stack([a, c, d], axis=1)
+    return xyz, tris
+
+
+def square_grid(n: int, length: float = 1.0) -> Tuple[np.ndarray, np.ndarray]:
+    """n x n node P1 triangle mesh of [0,L]^2 (see rect_grid)."""
+    return rect_grid(n, n, length, length)
+
+
+def slab_grid(nx: int, ny: int, nz: int, lx: float, ly: float, lz: float
+              ) -> Tuple[np.ndarray, np.ndarray]:
+    """Structured P1 tetrahedral mesh of [0,lx]x[0,ly]x[0,lz].
+
+    Node (i,j,k) has index (k*ny + j)*nx + i.  Every hexahedron is split into
+    the six Kuhn tetrahedra that share its (0,0,0)->(1,1,1) diagonal, so the
+    mesh is conforming.  Returns (xyz[N,3] float64, tets[E,4] int32).
+    """
+    if min(nx, ny, nz) < 2:
+        raise ValueError("slab_grid needs at least 2 nodes per direction")
+    xs = np.linspace(0.0, lx, nx)
+    ys = np.linspace(0.0, ly, ny)
+    zs = np.linspace(0.0, lz, nz)
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    xyz = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1).astype(np.float64)
+    k, j, i = np.meshgrid(np.arange(nz - 1), np.arange(ny - 1), np.arange(nx - 1),
+                          indexing="ij")
+    i = i.ravel().astype(np.int64)
+    j = j.ravel().astype(np.int64)
+    k = k.ravel().astype(np.int64)
+
+    def node(di, dj, dk):
+        return ((k + dk) * ny + (j + dj)) * nx + (i + di)
+
+    v000 = node(0, 0, 0)
+    v111 = node(1, 1, 1)
+    # the six monotone lattice paths from (0,0,0) to (1,1,1)
+    paths = [((1, 0, 0), (1, 1, 0)), ((1, 0, 0), (1, 0, 1)),
+             ((0, 1, 0), (1, 1, 0)), ((0, 1, 0), (0, 1, 1)),
+             ((0, 0, 1), (1, 0, 1)), ((0, 0, 1), (0, 1, 1))]
+    tets = []
+    for p1, p2 in paths:
+        tets.append(np.stack([v000, node(*p1), node(*p2), v111], axis=1))
+    tets = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
+    return xyz, tets
+
+
+# ---------------------------------------------------------------------------
+# fibres, stimulus sets, initial perturbations
+# ---------------------------------------------------------------------------
+
+
+def fibers_along_x(n_elems: int, dim: int) -> np.ndarray:
+    """Unit fibre direction e_x for every element, shape [E, dim]."""
+    f = np.zeros((n_elems, dim), dtype=np.float64)
+    f[:, 0] = 1.0
+    return f
+
+
+def fibers_transmural(xyz: np.ndarray, elems: np.ndarray, z0: float, z1: float,
+                      theta0_deg: float, theta1_deg: float) -> np.ndarray:
+    """Fibre direction (cos t, sin t, 0) per tetrahedron, where the angle t
+    varies linearly from theta0 at z=z0 to theta1 at z=z1, evaluated at the
+    element centroid's z (slab workload of Sec. 4.4)."""
+    zc = xyz[elems, 2].mean(axis=1)
+    s = np.clip((zc - z0) / (z1 - z0), 0.0, 1.0)
+    t = np.deg2rad(theta0_deg + (theta1_deg - theta0_deg) * s)
+    f = np.zeros((len(elems), 3), dtype=np.float64)
+    f[:, 0] = np.cos(t)
+    f[:, 1] = np.sin(t)
+    return f
+
+
+def nodes_x_below(xyz: np.ndarray, x_max: float) -> np.ndarray:
+    """uint8 node mask of the planar strip x < x_max (strict)."""
+    return (xyz[:, 0] < x_max).astype(np.uint8)
+
+
+def nodes_in_box(xyz: np.ndarray, lo: Sequence[float], hi: Sequence[float]) -> np.ndarray:
+    """uint8 node mask of the closed box lo <= x <= hi (componentwise)."""
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    d = len(lo)
+    m = np.all((xyz[:, :d] >= lo) & (xyz[:, :d] <= hi), axis=1)
+    return m.astype(np.uint8)
+
+
+def perturb_rows(X: np.ndarray, rows: Sequence[int], frac: float, seed: int,
+                 clip01: bool = True) -> np.ndarray:
+    """Multiply the given state rows of a node-major SoA state X[ns, N] by
+    (1 + U(-frac, frac)), drawn with numpy PCG64(seed) in row-then-node
+    order, optionally clipping to [0, 1] (gating variables)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Y = np.array(X, dtype=np.float64, copy=True)
+    for r in rows:
+        Y[r] = Y[r] * (1.0 + rng.uniform(-frac, frac, size=Y.shape[1]))
+        if clip01:
+            np.clip(Y[r], 0.0, 1.0, out=Y[r])
+    return Y
+
+
+# ---------------------------------------------------------------------------
+# workload descriptions
+# ---------------------------------------------------------------------------
+
+LR91 = 0            # Luo-Rudy 1991, original parameters
+LR91_PAPER_MOD = 1  # LR91 with G_si=0.02, G_Na=4.0, G_K=0.423 (Sec. 4)
+TP06_EPI = 2        # ten Tusscher-Panfilov 2006, epicardial parameters
+
+N_STATES = {LR91: 8, LR91_PAPER_MOD: 8, TP06_EPI: 19}
+
+
+@dataclasses.dataclass
+class Stimulus:
+    mask: np.ndarray        # uint8 per node
+    t_on: float             # ms
+    duration: float         # ms
+    amplitude: float        # uA/cm^2 (membrane current density, depolarising)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    xyz: np.ndarray
+    elems: np.ndarray
+    fibers: np.ndarray
+    sigma: Tuple[float, float, float, float]   # (s_il, s_it, s_el, s_et) mS/cm
+    chi: float
+    cm: float
+    model: int
+    stimuli: List[Stimulus]
+    dt: float
+    n_steps: int
+    n_sdc_nodes: int = 3
+    n_sweeps: int = 2
+    pin_node: int = 0
+    cg_tol: float = 1e-10
+    initial: Optional[np.ndarray] = None     # X[ns, N] or None => model rest
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.xyz.shape[0])
+
+    @property
+    def dim(self) -> int:
+        return int(self.xyz.shape[1])
+
+
+CONFIG0_SIGMA = (3.0, 0.31, 2.0, 1.35)
+STIM_AMP = 80.0
+
+
+def sheet(n: int, length: float, model: int, dt: float, n_steps: int,
+          sigma=CONFIG0_SIGMA, strip: float = 0.1, s2: Optional[Tuple[float, float]] = None,
+          name: str = "sheet", **kw) -> Workload:
+    """2-D square sheet with fibres along x and a left-edge S1 strip at t=0
+    (1 ms, 80 uA/cm^2).  s2=(t_on, side) adds an S2 on the corner square
+    [0,side]^2."""
+    xyz, tris = square_grid(n, length)
+    stims = [Stimulus(nodes_x_below(xyz, strip), 0.0, 1.0, STIM_AMP)]
+    if s2 is not None:
+        stims.append(Stimulus(nodes_in_box(xyz, (0.0, 0.0), (s2[1], s2[1])), s2[0], 1.0, STIM_AMP))
+    return Workload(name=name, xyz=xyz, elems=tris, fibers=fibers_along_x(len(tris), 2),
+                    sigma=tuple(sigma), chi=2000.0, cm=1.0, model=model, stimuli=stims,
+                    dt=dt, n_steps=n_steps, **kw)
+
+
+def config0() -> Workload:
+    """LR91 on the unit square, 65x65 nodes, 10 ms at dt = 0.02 ms, FP64."""
+    return sheet(65, 1.0, LR91, 0.02, 500, name="lr91_sheet_65x65", cg_tol=1e-10)
+
+
+def config1() -> Workload:
+    """TP06-epi on a 2.5 cm sheet, 257x257 nodes, S1 left edge, S2 corner
+    quadrant at 310 ms; 600 ms at dt = 0.02 ms."""
+    return sheet(257, 2.5, TP06_EPI, 0.02, 30000, s2=(310.0, 1.25),
+                 name="tp06_sheet_257x257")
+
+
+def config2(nx: int = 201, ny: int = 201, nz: int = 51, seed: int = 2,
+            rest: Optional[np.ndarray] = None, gate_rows: Sequence[int] = ()) -> Workload:
+    """TP06 in a 2x2x0.5 cm slab with -60..+60 deg transmural fibre rotation,
+    seeded +-2% gate perturbation around rest, S1 plane x<0.1 at 0 ms and S2
+    on the half-slab y<1 at 150 ms; 200 ms at dt = 0.025 ms."""
+    xyz, tets = slab_grid(nx, ny, nz, 2.0, 2.0, 0.5)
+    fib = fibers_transmural(xyz, tets, 0.0, 0.5, -60.0, 60.0)
+    stims = [Stimulus(nodes_x_below(xyz, 0.1), 0.0, 1.0, STIM_AMP),
+             Stimulus((xyz[:, 1] < 1.0).astype(np.uint8), 150.0, 1.0, STIM_AMP)]
+    init = None
+    if rest is not None:
+        X = np.repeat(np.asarray(rest, dtype=np.float64)[:, None], len(xyz), axis=1)
+        init = perturb_rows(X, gate_rows, 0.02, seed)
+    return Workload(name=f"tp06_slab_{nx}x{ny}x{nz}", xyz=xyz, elems=tets, fibers=fib,
+                    sigma=CONFIG0_SIGMA, chi=2000.0, cm=1.0, model=TP06_EPI,
+                    stimuli=stims, dt=0.025, n_steps=8000, initial=init)
+
+
+# ---------------------------------------------------------------------------
+# serving workload: a seeded stream of independent sheet simulations
+# ---------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival_s: float
+    side: int
+    model: int
+    sigma: Tuple[float, float, float, float]
+    strip_x: float
+    s2_time: float
+    t_end: float = 400.0
+    dt: float = 0.02
+
+
+def request_stream(n_requests: int = 512, rate_per_s: float = 40.0, seed: int = 4,
+                   sides: Sequence[int] = (33, 65, 129, 257, 513),
+                   t_end: float = 400.0) -> List[Request]:
+    """Poisson arrivals of independent square-sheet requests: side uniform
+    over `sides`, LR91/TP06 50/50, each conductivity jittered by U(-20%, 20%),
+    S1 strip whose left edge x0/L is U(0, 0.5) (width 0.1 L), S2 time
+    U(250, 350) ms on the quadrant opposite the strip."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    out = []
+    for r in range(n_requests):
+        t += rng.exponential(1.0 / rate_per_s)
+        side = int(sides[rng.integers(0, len(sides))])
+        model = LR91 if rng.uniform() < 0.5 else TP06_EPI
+        sig = tuple(float(s * (1.0 + rng.uniform(-0.2, 0.2))) for s in CONFIG0_SIGMA)
+        strip = float(rng.uniform(0.0, 0.5))
+        s2 = float(rng.uniform(250.0, 350.0))
+        out.append(Request(r, t, side, model, sig, strip, s2, t_end=t_end))
+    return out
+
+
+def request_workload(req: Request, length: float = 1.0, n_steps: Optional[int] = None) -> Workload:
+    """Materialise one serving request as a Workload on [0,L]^2: S1 on the
+    strip [x0, x0 + 0.1 L) at t=0, S2 on the upper-right quadrant at s2_time."""
+    xyz, tris = square_grid(req.side, length)
+    x0 = req.strip_x * length
+    s1 = ((xyz[:, 0] >= x0) & (xyz[:, 0] < x0 + 0.1 * length)).astype(np.uint8)
+    s2 = nodes_in_box(xyz, (0.5 * length, 0.5 * length), (length, length))
+    steps = n_steps if n_steps is not None else int(round(req.t_end / req.dt))
+    return Workload(name=f"req{req.rid}", xyz=xyz, elems=tris,
+                    fibers=fibers_along_x(len(tris), 2), sigma=req.sigma, chi=2000.0,
+                    cm=1.0, model=req.model,
+                    stimuli=[Stimulus(s1, 0.0, 1.0, STIM_AMP),
+                             Stimulus(s2, req.s2_time, 1.0, STIM_AMP)],
+                    dt=req.dt, n_steps=steps)
