@@ -1,0 +1,217 @@
+/*
+ * bd.h -- C ABI of the GB300 (sm_103a) library for the partitioned bidomain
+ * time step with spectral deferred correction.
+ *
+ * The method (Sec. 3.3.2 of the paper, Algorithm 2): at every time step the
+ * elliptic constraint A_ie u = -A_i v (Eq. (3.15)) is solved with the latest
+ * transmembrane voltage, the coupled parabolic PDE + ionic ODE system
+ * Mt dX/dt = F(X, u) (Eq. (3.16)) is advanced with the two-stage ROS2
+ * Rosenbrock method (Eq. (3.13)-(3.14)), and the result is corrected by the
+ * linearised deferred-correction system (Eq. (3.20)); the three steps are
+ * repeated as inner iterations ("sweeps").
+ *
+ * Units: cm, ms, mV, mS/cm, uA/cm^2, uF/cm^2, 1/cm.
+ *
+ * Conventions for every entry point
+ *   - Return value: BD_OK (0) or a negative bd_status_t.  The library never
+ *     aborts, traps or prints; bd_last_error() gives a one-line reason.
+ *   - Host pointers are read during the call only and stay owned by the
+ *     caller; nothing is retained.  "Device" pointers are CUDA global memory
+ *     of the handle's device.
+ *   - A handle is used by one host thread and one stream at a time.
+ *   - Device-side failures (iteration cap reached, non-finite values,
+ *     indefinite curvature, a grid barrier that timed out) set a status word
+ *     on the device; it is returned by the next bd_sync / bd_get_* call and
+ *     cleared by bd_clear_status.
+ *
+ * Node-major state layout ("SoA"): a state array X of a model with ns
+ * variables and N nodes holds variable k of node i at X[k*N + i].  Variable
+ * order per model:
+ *   BD_LR91, BD_LR91_PAPER_MOD (ns = 8):  V, m, h, j, d, f, X, Cai
+ *   BD_TP06_EPI (ns = 19): V, m, h, j, d, f, f2, s, r, Xr1, Xr2, Xs, fCass,
+ *                          Rbar, Ki, Nai, Cai, CaSR, CaSS
+ */
+#ifndef BD_H_
+#define BD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BD_OK = 0,
+  BD_ERR_ARG = -1,            /* invalid argument (sizes, indices, NaN input, degenerate element) */
+  BD_ERR_OOM = -2,            /* device allocation failed (or allocator callback returned NULL) */
+  BD_ERR_CUDA = -3,           /* a CUDA runtime call failed */
+  BD_ERR_NOT_CONVERGED = -4,  /* a CG solve reached its iteration cap */
+  BD_ERR_NONFINITE = -5,      /* a non-finite residual or state was produced */
+  BD_ERR_INDEFINITE = -6,     /* CG met p^T A p <= 0 */
+  BD_ERR_TIMEOUT = -7         /* a device-wide barrier wait exceeded its bound */
+} bd_status_t;
+
+/* Membrane models of Sec. 2.  BD_LR91: Luo-Rudy 1991 with the 1991 parameter
+ * set; BD_LR91_PAPER_MOD: the same with G_si = 0.02, G_Na = 4.0, G_K = 0.423
+ * (Sec. 4); BD_TP06_EPI: ten Tusscher-Panfilov 2006, epicardial cell. */
+typedef enum { BD_LR91 = 0, BD_LR91_PAPER_MOD = 1, BD_TP06_EPI = 2 } bd_ionic_t;
+
+typedef enum { BD_FP64 = 0, BD_MIXED = 1 } bd_precision_t;
+
+/* P1 mesh (Sec. 3.2): dim = 2 (triangles, 3 nodes per element) or 3
+ * (tetrahedra, 4 nodes).  xyz: n_nodes*dim doubles, node-major (x0 y0 [z0] x1 ...).
+ * elems: n_elems*(dim+1) zero-based node indices.  fiber: n_elems*dim unit
+ * vectors or NULL (x axis).  All copied at bd_create. */
+typedef struct {
+  int dim;
+  int64_t n_nodes;
+  int64_t n_elems;
+  const double* xyz;
+  const int32_t* elems;
+  const double* fiber;
+} bd_mesh_t;
+
+/* Conductivities (Sec. 2, transversely isotropic along the fibre):
+ * sigma = s_t I + (s_l - s_t) f f^T for the intra- (i) and extracellular (e)
+ * domains, mS/cm; chi = surface-to-volume ratio (1/cm); cm = membrane
+ * capacitance (uF/cm^2). */
+typedef struct {
+  double sil, sit, sel, set;
+  double chi, cm;
+} bd_cond_t;
+
+/* Options; bd_default_options() fills every field. */
+typedef struct {
+  int precision;         /* bd_precision_t */
+  int mass_lumped;       /* 1: lumped mass also on dv/dt (default 0: consistent) */
+  int pin_node;          /* >= 0: u[pin] = 0; -1: zero nodal mean (default 0) */
+  int sdc_correction;    /* 1: Algorithm 2 (default); 0: Algorithm 1, no correction */
+  double cg_tol_e;       /* elliptic CG: ||r|| <= tol ||b|| (default 1e-10) */
+  double cg_tol_p;       /* condensed parabolic CG (default 1e-10) */
+  int cg_cap_e;          /* iteration caps (default 20000 / 2000) */
+  int cg_cap_p;
+  double sweep_tol;      /* > 0: stop the sweeps when max|X^k - X^(k-1)| < tol (default 0: all sweeps) */
+  double v_act_mV;       /* activation threshold (default -30) */
+  double spd_margin;     /* condensed-diagonal safeguard factor (default 0.9, 0 disables) */
+  int use_graph;         /* 1: capture each step shape into a CUDA graph and replay it (default 1) */
+  /* device memory hooks (NULL => cudaMalloc/cudaFree); ctx is passed back */
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+  void* stream;          /* cudaStream_t or NULL (the library creates one) */
+} bd_opts_t;
+
+typedef struct bd_state bd_state_t;
+
+/* Per-handle counters since creation (or the last bd_reset_stats). */
+typedef struct {
+  int64_t steps;
+  int64_t sweeps;
+  int64_t cg_iters_e;      /* summed elliptic CG iterations */
+  int64_t cg_solves_e;
+  int64_t cg_iters_p;      /* summed parabolic CG iterations */
+  int64_t cg_solves_p;
+  int64_t spd_clamps;      /* nodes whose condensed diagonal was raised */
+  int64_t ionic_evals;     /* node-block evaluations (kernel launches x nodes / nodes) */
+} bd_stats_t;
+
+void bd_default_options(bd_opts_t* opts);
+
+/* Assemble the P1 operators on the host (Sec. 3.2, Eqs. (3.6)-(3.9)), upload
+ * them, set the resting state of the model (LR91: Newton zero of the cell
+ * field; TP06: the published initial values) and return a handle.
+ * BD_ERR_ARG for out-of-range indices, non-positive element measures,
+ * non-finite coordinates or an unknown model. */
+int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model,
+              const bd_opts_t* opts, bd_state_t** out);
+
+/* Add a stimulus (at most 32): membrane current density amp (uA/cm^2,
+ * depolarising) on the nodes with node_mask[i] != 0 (n_nodes bytes), active
+ * for the steps with t_on <= t^n < t_on + dur, t^n = n*dt (Sec. 4 protocols). */
+int bd_add_stimulus(bd_state_t* s, const uint8_t* node_mask, double t_on_ms, double dur_ms,
+                    double amp);
+
+/* Set X (ns*N doubles, node-major layout above) and u (N doubles or NULL =>
+ * zeros) from host memory; resets the step counter and activation times. */
+int bd_set_initial(bd_state_t* s, const double* X, const double* u);
+
+/* Advance one time step of size dt_ms with Algorithm 2 on n_sdc_nodes (2 or
+ * 3) Gauss-Lobatto nodes and n_sweeps (>= 1) inner iterations.  Enqueued on
+ * the handle's stream; returns the status word of the last completed step
+ * that was read back (bd_sync waits and reads it). */
+int bd_step(bd_state_t* s, double dt_ms, int n_sdc_nodes, int n_sweeps);
+
+/* Advance several handles by one step each (one launch sequence per handle
+ * on the first handle's stream; the handles must share one device). */
+int bd_batch_step(bd_state_t* const* states, int n, double dt_ms, int n_sdc_nodes, int n_sweeps);
+
+/* Wait for the handle's stream and return its device status word. */
+int bd_sync(bd_state_t* s);
+void bd_clear_status(bd_state_t* s);
+
+/* Activation times (first upward crossing of v_act, linearly interpolated
+ * inside the step; NaN if not activated), n doubles to host. */
+int bd_activation_times(const bd_state_t* s, double* out, int64_t n);
+
+/* Copy v (N), u (N) and, if X != NULL, the full state (ns*N) to host memory;
+ * any pointer may be NULL. */
+int bd_get_fields(const bd_state_t* s, double* vm, double* phie, double* X);
+
+/* Device pointers of the resident v-row / u so callers can read them without
+ * a host copy (valid until bd_destroy). */
+int bd_device_fields(const bd_state_t* s, const double** X_dev, const double** u_dev);
+
+/* Serialise (X, u, step counter, activation times) to host memory.  With
+ * buf == NULL only *bytes is set. */
+int bd_get_state(const bd_state_t* s, void* buf, size_t* bytes);
+int bd_set_state(bd_state_t* s, const void* buf, size_t bytes);
+
+/* Device bytes bd_create would allocate for this mesh and model. */
+size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts_t* opts);
+
+int bd_get_stats(const bd_state_t* s, bd_stats_t* out);
+int bd_reset_stats(bd_state_t* s);
+int64_t bd_num_nodes(const bd_state_t* s);
+int bd_num_states(bd_ionic_t model);
+const char* bd_last_error(const bd_state_t* s);
+void bd_destroy(bd_state_t* s);
+
+/* ---- kernel-level entry points (parity tests and tools) ---------------- */
+
+/* Evaluate the membrane model on the device for n node states X (host,
+ * ns*n node-major) with per-node stimulus current istim (host, n, may be
+ * NULL): writes the node field f = (-(I_ion - I_stim)/C_m, g) (ns*n) and,
+ * if jac != NULL, the dense node Jacobian df/dX (n*ns*ns, node-major
+ * blocks, row = component of f) -- Sec. 2 models, Sec. 3.3.2 "exact
+ * derivatives".  cm is the membrane capacitance. */
+int bd_ionic_eval(bd_ionic_t model, int precision, int64_t n, const double* X,
+                  const double* istim, double cm, double* f, double* jac);
+
+/* Compile-time sparsity pattern of the node Jacobian (the paper's CTSM
+ * blocks, Sec. 3.3.2): masks[r] has bit c set iff df_r/dX_c may be nonzero.
+ * masks holds ns uint32 values. */
+int bd_ionic_pattern(bd_ionic_t model, uint32_t* masks);
+
+/* Resting state used by bd_create (ns doubles). */
+int bd_rest_state(bd_ionic_t model, double* X);
+
+/* Assembled operator of a handle in CSR form (A0 of the method, Sec. 3.2):
+ * which = 0: A_i, 1: A_ie (both already divided by chi*C_m), 2: consistent
+ * mass M, 3: lumped mass M_L (diagonal; only val is written, N doubles).
+ * With val == NULL only *nnz is set; otherwise rowptr (N+1), col (nnz)
+ * and val (nnz) are written to host memory.  Columns are sorted per row. */
+int bd_operator_csr(const bd_state_t* s, int which, int64_t* nnz, int32_t* rowptr,
+                    int32_t* col, double* val);
+
+/* Solve the elliptic constraint A_ie u = -A_i v (Eq. (3.15)) with the
+ * handle's operators, precision and pin, from a host v (N) into a host u (N),
+ * warm-started from u_guess (host, N) or from zero if NULL.  Returns the
+ * iteration count in *iters when not NULL. */
+int bd_solve_elliptic(bd_state_t* s, const double* v, const double* u_guess, double* u,
+                      int* iters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BD_H_ */

@@ -1,0 +1,213 @@
+// assemble.cpp -- host P1 assembly of the bidomain operators (runs once per
+// handle, before the device path).
+//
+// Sec. 3.2, Eqs. (3.6)-(3.9): stiffness matrices
+//   A_i = ((sigma_i grad w_a, grad w_b)),  A_ie = (((sigma_i + sigma_e) grad w_a, grad w_b)),
+// and mass M = ((w_a, w_b)) for piecewise linear w on triangles (2-D) or
+// tetrahedra (3-D).  The conductivity of an element is the transversely
+// isotropic tensor sigma = s_t I + (s_l - s_t) f f^T of its fibre f.  Both
+// stiffness matrices are divided by chi*C_m (the parabolic equation is
+// written per unit membrane capacitance).  All three share one CSR pattern:
+// the node graph of the mesh.
+//
+// Rows are assembled independently from a node -> element adjacency, so
+// threads own disjoint rows and need no atomics.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "bd_internal.h"
+
+namespace bd {
+
+namespace {
+
+struct ElemGeom {
+  double meas;           // area / volume
+  double g[4][3];        // gradients of the barycentric functions
+};
+
+bool elem_geom(int dim, const double* xyz, const int32_t* e, ElemGeom* out) {
+  const int k = dim + 1;
+  double Bm[3][3] = {{0}};
+  for (int c = 0; c < dim; ++c)
+    for (int r = 0; r < dim; ++r) Bm[r][c] = xyz[int64_t(e[c + 1]) * dim + r] - xyz[int64_t(e[0]) * dim + r];
+  double inv[3][3];
+  double det;
+  if (dim == 2) {
+    det = Bm[0][0] * Bm[1][1] - Bm[0][1] * Bm[1][0];
+    if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return false;
+    inv[0][0] = Bm[1][1] / det;  inv[0][1] = -Bm[0][1] / det;
+    inv[1][0] = -Bm[1][0] / det; inv[1][1] = Bm[0][0] / det;
+    out->meas = std::fabs(det) / 2.0;
+  } else {
+    det = Bm[0][0] * (Bm[1][1] * Bm[2][2] - Bm[1][2] * Bm[2][1]) -
+          Bm[0][1] * (Bm[1][0] * Bm[2][2] - Bm[1][2] * Bm[2][0]) +
+          Bm[0][2] * (Bm[1][0] * Bm[2][1] - Bm[1][1] * Bm[2][0]);
+    if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return false;
+    inv[0][0] = (Bm[1][1] * Bm[2][2] - Bm[1][2] * Bm[2][1]) / det;
+    inv[0][1] = (Bm[0][2] * Bm[2][1] - Bm[0][1] * Bm[2][2]) / det;
+    inv[0][2] = (Bm[0][1] * Bm[1][2] - Bm[0][2] * Bm[1][1]) / det;
+    inv[1][0] = (Bm[1][2] * Bm[2][0] - Bm[1][0] * Bm[2][2]) / det;
+    inv[1][1] = (Bm[0][0] * Bm[2][2] - Bm[0][2] * Bm[2][0]) / det;
+    inv[1][2] = (Bm[0][2] * Bm[1][0] - Bm[0][0] * Bm[1][2]) / det;
+    inv[2][0] = (Bm[1][0] * Bm[2][1] - Bm[1][1] * Bm[2][0]) / det;
+    inv[2][1] = (Bm[0][1] * Bm[2][0] - Bm[0][0] * Bm[2][1]) / det;
+    inv[2][2] = (Bm[0][0] * Bm[1][1] - Bm[0][1] * Bm[1][0]) / det;
+    out->meas = std::fabs(det) / 6.0;
+  }
+  // row a of inv is grad(lambda_{a+1}); lambda_0 = 1 - sum
+  for (int d = 0; d < dim; ++d) {
+    double s = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      out->g[a + 1][d] = inv[a][d];
+      s += inv[a][d];
+    }
+    out->g[0][d] = -s;
+  }
+  (void)k;
+  return true;
+}
+
+}  // namespace
+
+int assemble_host(const bd_mesh_t* mesh, const bd_cond_t* cond, HostOps* out, std::string* err) {
+  const int dim = mesh->dim;
+  const int64_t N = mesh->n_nodes, E = mesh->n_elems;
+  const int k = dim + 1;
+  if (N > int64_t(0x7fffffff) - 1) {
+    *err = "mesh too large for 32-bit indices";
+    return BD_ERR_ARG;
+  }
+  for (int64_t i = 0; i < N * dim; ++i)
+    if (!std::isfinite(mesh->xyz[i])) {
+      *err = "non-finite node coordinate";
+      return BD_ERR_ARG;
+    }
+  for (int64_t e = 0; e < E * k; ++e)
+    if (mesh->elems[e] < 0 || mesh->elems[e] >= N) {
+      *err = "element node index out of range";
+      return BD_ERR_ARG;
+    }
+  // node -> element adjacency
+  std::vector<int64_t> nep(N + 1, 0);
+  for (int64_t e = 0; e < E * k; ++e) nep[mesh->elems[e] + 1]++;
+  for (int64_t i = 0; i < N; ++i) nep[i + 1] += nep[i];
+  std::vector<int64_t> nel(nep[N]);
+  {
+    std::vector<int64_t> fill(nep.begin(), nep.end() - 1);
+    for (int64_t e = 0; e < E; ++e)
+      for (int a = 0; a < k; ++a) nel[fill[mesh->elems[e * k + a]]++] = e;
+  }
+  // element geometry and conductivities
+  std::vector<ElemGeom> geo(E);
+  const double scale = 1.0 / (cond->chi * cond->cm);
+  std::vector<double> Si(E * 9), Sie(E * 9);
+  unsigned nthreads = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  std::vector<int> bad(nthreads, 0);
+  auto par = [&](int64_t total, auto&& fn) {
+    std::vector<std::thread> th;
+    const int64_t chunk = (total + nthreads - 1) / nthreads;
+    for (unsigned t = 0; t < nthreads; ++t) {
+      const int64_t lo = t * chunk, hi = std::min(total, lo + chunk);
+      if (lo >= hi) break;
+      th.emplace_back([&, lo, hi, t] { fn(lo, hi, t); });
+    }
+    for (auto& x : th) x.join();
+  };
+  par(E, [&](int64_t lo, int64_t hi, unsigned t) {
+    for (int64_t e = lo; e < hi; ++e) {
+      if (!elem_geom(dim, mesh->xyz, mesh->elems + e * k, &geo[e])) {
+        bad[t] = 1;
+        continue;
+      }
+      double f[3] = {1.0, 0.0, 0.0};
+      if (mesh->fiber) {
+        double nrm = 0.0;
+        for (int d = 0; d < dim; ++d) {
+          f[d] = mesh->fiber[e * dim + d];
+          nrm += f[d] * f[d];
+        }
+        nrm = std::sqrt(nrm);
+        if (!(nrm > 0.0) || !std::isfinite(nrm)) {
+          bad[t] = 2;
+          continue;
+        }
+        for (int d = 0; d < dim; ++d) f[d] /= nrm;
+      }
+      for (int r = 0; r < dim; ++r)
+        for (int c = 0; c < dim; ++c) {
+          const double ff = f[r] * f[c], id = (r == c) ? 1.0 : 0.0;
+          Si[e * 9 + r * 3 + c] = cond->sit * id + (cond->sil - cond->sit) * ff;
+          Sie[e * 9 + r * 3 + c] = (cond->sit + cond->set) * id + ((cond->sil + cond->sel) - (cond->sit + cond->set)) * ff;
+        }
+    }
+  });
+  for (int b : bad)
+    if (b) {
+      *err = b == 1 ? "degenerate element (zero or non-finite measure)" : "zero or non-finite fibre vector";
+      return BD_ERR_ARG;
+    }
+  // CSR pattern: sorted union of the element neighbours of each node
+  out->n = N;
+  out->rowptr.assign(N + 1, 0);
+  std::vector<std::vector<int32_t>> rows(N);
+  par(N, [&](int64_t lo, int64_t hi, unsigned) {
+    std::vector<int32_t> tmp;
+    for (int64_t i = lo; i < hi; ++i) {
+      tmp.clear();
+      for (int64_t q = nep[i]; q < nep[i + 1]; ++q)
+        for (int a = 0; a < k; ++a) tmp.push_back(mesh->elems[nel[q] * k + a]);
+      std::sort(tmp.begin(), tmp.end());
+      tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+      rows[i] = tmp;
+    }
+  });
+  for (int64_t i = 0; i < N; ++i) out->rowptr[i + 1] = out->rowptr[i] + int32_t(rows[i].size());
+  const int64_t nnz = out->rowptr[N];
+  out->col.resize(nnz);
+  out->Ai.assign(nnz, 0.0);
+  out->Aie.assign(nnz, 0.0);
+  out->M.assign(nnz, 0.0);
+  out->ML.assign(N, 0.0);
+  out->diagpos.assign(N, 0);
+  const double mdiag = dim == 2 ? 2.0 / 12.0 : 2.0 / 20.0;
+  const double moff = dim == 2 ? 1.0 / 12.0 : 1.0 / 20.0;
+  par(N, [&](int64_t lo, int64_t hi, unsigned) {
+    for (int64_t i = lo; i < hi; ++i) {
+      const int64_t r0 = out->rowptr[i];
+      const auto& cols = rows[i];
+      std::memcpy(&out->col[r0], cols.data(), cols.size() * sizeof(int32_t));
+      out->diagpos[i] = int32_t(r0 + (std::lower_bound(cols.begin(), cols.end(), int32_t(i)) - cols.begin()));
+      for (int64_t q = nep[i]; q < nep[i + 1]; ++q) {
+        const int64_t e = nel[q];
+        const int32_t* en = mesh->elems + e * k;
+        int la = 0;
+        while (en[la] != i) ++la;
+        const ElemGeom& G = geo[e];
+        for (int b = 0; b < k; ++b) {
+          const int64_t p = r0 + (std::lower_bound(cols.begin(), cols.end(), en[b]) - cols.begin());
+          double si = 0.0, sie = 0.0;
+          for (int r = 0; r < dim; ++r)
+            for (int c = 0; c < dim; ++c) {
+              const double gg = G.g[la][r] * G.g[b][c];
+              si += gg * Si[e * 9 + r * 3 + c];
+              sie += gg * Sie[e * 9 + r * 3 + c];
+            }
+          out->Ai[p] += G.meas * si * scale;
+          out->Aie[p] += G.meas * sie * scale;
+          out->M[p] += G.meas * (la == b ? mdiag : moff);
+        }
+      }
+      double ml = 0.0;
+      for (int64_t p = r0; p < out->rowptr[i + 1]; ++p) ml += out->M[p];
+      out->ML[i] = ml;
+    }
+  });
+  return BD_OK;
+}
+
+}  // namespace bd

@@ -1,0 +1,818 @@
+// bd.cu -- handle, C ABI and the step driver of the partitioned SDC method.
+//
+// One step (Sec. 3.3.2, Algorithm 2, on M Gauss-Lobatto nodes; M = 2 is the
+// paper's two-node trapezoidal correction, Eq. (3.20)):
+//
+//   f_0 = f(X^n)                                          node field, stored
+//   for sweep k = 1..K:
+//     elliptic   u_m = E(v_m) for m >= 1  (k = 1: once, from v^n)   Eq. (3.15)
+//     predictor  X~_0 = X^n; for m: ROS2 over [t_m, t_m+1] with u_{m+1}
+//                stage 1: ionic(S1) -> PCG -> k1 ; stage 2: ionic(S2) -> PCG -> k2
+//                X~_{m+1} = X~_m + 3/(2g) k1 + 1/(2g) k2            Eq. (3.13)-(3.14)
+//     correction f(X~_{M-1}); for m: ionic(C) -> PCG -> eps,
+//                X_{m+1} = X~_{m+1} + eps                           Eq. (3.20)
+//   activation times, X^{n+1} = X_{M-1}, u^{n+1} = u_{M-1}
+//
+// All of it runs on the handle's stream; after the first step of a given
+// (dt, M, K) the launch sequence is captured once into a CUDA graph and
+// replayed.  The device is touched by the host only at create/set/get calls.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "bd_internal.h"
+
+namespace bd {
+cudaError_t launch_eval(int model, int precision, int64_t n, const double* X, const double* istim, double inv_cm,
+                        double* f, double* jac, cudaStream_t st);
+void pattern_host(int model, uint32_t* masks);
+}  // namespace bd
+
+using namespace bd;
+
+struct bd_state {
+  int model = 0, ns = 0, dim = 0, precision = 0;
+  int64_t N = 0, nnz = 0;
+  bd_opts_t opts{};
+  double inv_cm = 1.0, lambda_M = 0.25;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  int* diagpos = nullptr;
+  double *Ai = nullptr, *Aie = nullptr, *Mv = nullptr, *Mc = nullptr, *ML = nullptr;
+  struct PC { double alpha; double* val; };
+  std::vector<PC> pcache;
+  double *Xn = nullptr, *Xt[kMaxNodes] = {}, *Xc[kMaxNodes] = {}, *fq[kMaxNodes] = {}, *u[kMaxNodes] = {};
+  double *dgs = nullptr, *rl = nullptr, *z1 = nullptr, *w1 = nullptr, *z2 = nullptr, *w2 = nullptr;
+  double *k1v = nullptr, *k2v = nullptr, *avec = nullptr, *bvec = nullptr;
+  double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_invd = nullptr, *cg_part = nullptr;
+  unsigned* bar = nullptr;
+  double* t_act = nullptr;
+  uint32_t* stim_bits = nullptr;
+  StimTable stim{};
+  long long* step_n = nullptr;
+  int* d_status = nullptr;
+  long long* d_stats = nullptr;            // [iters_e, solves_e, iters_p, solves_p]
+  unsigned long long* d_clamps = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaGraphExec_t gexec = nullptr;
+  double g_dt = 0.0;
+  int g_M = 0, g_K = 0;
+  int pcg_grid = 1, pcg_block = 256, pcg_max = 1;
+  std::vector<void*> allocs;
+  std::string err;
+  int64_t steps = 0, sweeps = 0, ionic_evals = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(bd_state* s, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (s) s->err = buf;
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return fail(s, BD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+void* dalloc(bd_state* s, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (s->opts.alloc) {
+    p = s->opts.alloc(bytes, s->opts.alloc_ctx);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) s->allocs.push_back(p);
+  return p;
+}
+
+template <class T>
+bool alloc_n(bd_state* s, T** out, int64_t count) {
+  *out = static_cast<T*>(dalloc(s, size_t(count) * sizeof(T)));
+  return *out != nullptr;
+}
+
+void release(bd_state* s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = nullptr;
+  for (void* p : s->allocs) {
+    if (s->opts.free) s->opts.free(p, s->opts.alloc_ctx);
+    else cudaFree(p);
+  }
+  s->allocs.clear();
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  s->stream = nullptr;
+}
+
+int status_code(int st) {
+  if (st & ST_TIMEOUT) return BD_ERR_TIMEOUT;
+  if (st & ST_NONFINITE) return BD_ERR_NONFINITE;
+  if (st & ST_INDEFINITE) return BD_ERR_INDEFINITE;
+  if (st & ST_NOT_CONVERGED) return BD_ERR_NOT_CONVERGED;
+  return BD_OK;
+}
+
+int read_status(bd_state* s) {
+  int st = 0;
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaMemcpy(&st, s->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  const int c = status_code(st);
+  if (c != BD_OK) {
+    const char* what = c == BD_ERR_TIMEOUT ? "a device barrier wait timed out"
+                       : c == BD_ERR_NONFINITE ? "non-finite value in a solve or the state"
+                       : c == BD_ERR_INDEFINITE ? "CG met non-positive curvature"
+                                                : "a CG solve reached its iteration cap";
+    fail(s, c, "%s", what);
+  }
+  return c;
+}
+
+// values of alpha M_v + A_i on the shared pattern, cached per alpha
+double* p_values(bd_state* s, double alpha) {
+  for (auto& pc : s->pcache)
+    if (pc.alpha == alpha) return pc.val;
+  double* v = nullptr;
+  if (!alloc_n(s, &v, s->nnz)) return nullptr;
+  if (launch_axpby_vals(s->nnz, alpha, s->Mv, 1.0, s->Ai, v, s->stream) != cudaSuccess) return nullptr;
+  s->pcache.push_back({alpha, v});
+  return v;
+}
+
+PcgLaunch pcg_base(bd_state* s) {
+  PcgLaunch P{};
+  P.n = int(s->N);
+  P.rowptr = s->rowptr;
+  P.col = s->col;
+  P.diagpos = s->diagpos;
+  P.r = s->cg_r;
+  P.z = s->cg_z;
+  P.p = s->cg_p;
+  P.q = s->cg_q;
+  P.invd = s->cg_invd;
+  P.part = s->cg_part;
+  P.bar = s->bar;
+  P.status = s->d_status;
+  P.grid = s->pcg_grid;
+  P.block = s->pcg_block;
+  return P;
+}
+
+int elliptic(bd_state* s, const double* v, double* u) {
+  PcgLaunch P = pcg_base(s);
+  P.valA = s->Aie;
+  P.val1 = s->Ai;
+  P.va = v;
+  P.c1 = -1.0;
+  P.project = 1;
+  P.x = u;
+  P.warm = 1;
+  P.tol = s->opts.cg_tol_e;
+  P.maxit = s->opts.cg_cap_e;
+  P.pin = s->opts.pin_node >= 0 ? s->opts.pin_node : -1;
+  P.iters_acc = s->d_stats + 0;
+  P.solves_acc = s->d_stats + 1;
+  CK(launch_pcg(P, s->stream));
+  return BD_OK;
+}
+
+int parabolic(bd_state* s, const double* pvals, double c1, const double* va, double c2, const double* vb,
+              double* x) {
+  PcgLaunch P = pcg_base(s);
+  P.valA = pvals;
+  P.dextra = s->dgs;
+  P.rl = s->rl;
+  P.val1 = s->Ai;
+  P.va = va;
+  P.c1 = c1;
+  if (vb) {
+    P.val2 = s->Mv;
+    P.vb = vb;
+    P.c2 = c2;
+  }
+  P.project = 0;
+  P.x = x;
+  P.warm = 0;
+  P.tol = s->opts.cg_tol_p;
+  P.maxit = s->opts.cg_cap_p;
+  P.pin = -2;
+  P.iters_acc = s->d_stats + 2;
+  P.solves_acc = s->d_stats + 3;
+  CK(launch_pcg(P, s->stream));
+  return BD_OK;
+}
+
+IonicLaunch ionic_base(bd_state* s, int mode, double dt) {
+  IonicLaunch L{};
+  L.model = s->model;
+  L.precision = s->precision;
+  L.mode = mode;
+  L.n = s->N;
+  L.inv_cm = s->inv_cm;
+  L.dt = dt;
+  L.ML = s->ML;
+  L.stim_bits = s->stim_bits;
+  L.step_n = s->step_n;
+  L.stim = s->stim;
+  L.dgs = s->dgs;
+  L.rl = s->rl;
+  L.avec = s->avec;
+  L.clamp_count = s->d_clamps;
+  return L;
+}
+
+void lobatto(int M, double* c) {
+  if (M == 2) { c[0] = 0.0; c[1] = 1.0; }
+  else { c[0] = 0.0; c[1] = 0.5; c[2] = 1.0; }
+}
+
+// S[m][j] = int_{c_m}^{c_{m+1}} l_j  (unit interval)
+void integration_matrix(int M, double S[kMaxNodes - 1][kMaxNodes]) {
+  if (M == 2) {
+    S[0][0] = 0.5; S[0][1] = 0.5;
+  } else {
+    S[0][0] = 5.0 / 24; S[0][1] = 1.0 / 3; S[0][2] = -1.0 / 24;
+    S[1][0] = -1.0 / 24; S[1][1] = 1.0 / 3; S[1][2] = 5.0 / 24;
+  }
+}
+
+// prepare everything a step allocates or computes outside the launch sequence
+int prepare_step(bd_state* s, double dt, int M) {
+  const double gam = 1.0 + 1.0 / std::sqrt(2.0);
+  double c[kMaxNodes];
+  lobatto(M, c);
+  for (int m = 0; m + 1 < M; ++m) {
+    const double h = dt * (c[m + 1] - c[m]);
+    if (!p_values(s, 1.0 / (gam * h))) return fail(s, BD_ERR_OOM, "device allocation failed");
+    if (!p_values(s, 1.0 / h)) return fail(s, BD_ERR_OOM, "device allocation failed");
+  }
+  return BD_OK;
+}
+
+#define RUN(x)                     \
+  do {                             \
+    const int r_ = (x);            \
+    if (r_ != BD_OK) return r_;    \
+  } while (0)
+
+int enqueue_step(bd_state* s, double dt, int M, int K) {
+  const double gam = 1.0 + 1.0 / std::sqrt(2.0);
+  const int64_t N = s->N;
+  const int ns = s->ns;
+  double c[kMaxNodes], S[kMaxNodes - 1][kMaxNodes];
+  lobatto(M, c);
+  integration_matrix(M, S);
+  StimTable st = s->stim;
+  CK(launch_field(s->model, s->precision, N, s->Xn, s->inv_cm, dt, s->stim_bits, s->step_n, st, s->fq[0], s->stream));
+  for (int k = 1; k <= K; ++k) {
+    // ---- elliptic constraint at the nodes m >= 1 ----
+    if (k == 1) {
+      RUN(elliptic(s, s->Xn, s->u[M - 1]));
+      for (int m = 1; m + 1 < M; ++m) CK(launch_copy(N, s->u[M - 1], s->u[m], s->stream));
+    } else {
+      for (int m = 1; m < M; ++m) RUN(elliptic(s, s->Xc[m], s->u[m]));
+    }
+    // ---- ROS2 predictor ----
+    for (int m = 0; m + 1 < M; ++m) {
+      const double h = dt * (c[m + 1] - c[m]);
+      const double alpha = 1.0 / (gam * h);
+      const double* src = m == 0 ? s->Xn : s->Xt[m];
+      double* pv = p_values(s, alpha);
+      IonicLaunch L = ionic_base(s, MODE_S1, dt);
+      L.alpha = alpha;
+      L.smin = s->opts.spd_margin > 0 ? -s->opts.spd_margin * alpha * s->lambda_M : -INFINITY;
+      L.XJ = src;
+      L.u = s->u[m + 1];
+      L.z = s->z1;
+      L.w = s->w1;
+      L.fq_out = (m >= 1 && s->opts.sdc_correction) ? s->fq[m] : nullptr;
+      CK(launch_ionic(L, s->stream));
+      RUN(parabolic(s, pv, -1.0, s->avec, 0.0, nullptr, s->k1v));
+      IonicLaunch L2 = ionic_base(s, MODE_S2, dt);
+      L2.alpha = alpha;
+      L2.smin = L.smin;
+      L2.XJ = src;
+      L2.u = s->u[m + 1];
+      L2.k1v = s->k1v;
+      L2.z1 = s->z1;
+      L2.w1 = s->w1;
+      L2.ck1 = 2.0 / (gam * h);
+      L2.inv_gamma = 1.0 / gam;
+      L2.z = s->z2;
+      L2.w = s->w2;
+      L2.bvec = s->bvec;
+      CK(launch_ionic(L2, s->stream));
+      RUN(parabolic(s, pv, -1.0, s->avec, -L2.ck1, s->bvec, s->k2v));
+      CK(launch_combine(s->model, N, src, s->k1v, s->z1, s->w1, s->k2v, s->z2, s->w2, 1.5 / gam, 0.5 / gam,
+                        s->Xt[m + 1], s->stream));
+      s->ionic_evals += 3;
+    }
+    // ---- SDC correction ----
+    if (s->opts.sdc_correction) {
+      CK(launch_field(s->model, s->precision, N, s->Xt[M - 1], s->inv_cm, dt, s->stim_bits, s->step_n, st,
+                      s->fq[M - 1], s->stream));
+      s->ionic_evals += 1;
+      for (int m = 0; m + 1 < M; ++m) {
+        const double h = dt * (c[m + 1] - c[m]);
+        const double alpha = 1.0 / h;
+        double* pv = p_values(s, alpha);
+        IonicLaunch L = ionic_base(s, MODE_CORR, dt);
+        L.alpha = alpha;
+        L.smin = s->opts.spd_margin > 0 ? -s->opts.spd_margin * alpha * s->lambda_M : -INFINITY;
+        L.inv_dt = 1.0 / h;
+        L.XJ = s->Xt[m + 1];
+        L.Xprev = m == 0 ? s->Xn : s->Xc[m];
+        L.n_nodes = M;
+        for (int j = 0; j < M; ++j) {
+          L.S[j] = dt * S[m][j];
+          L.Xq[j] = j == 0 ? s->Xn : s->Xt[j];
+          L.uq[j] = s->u[j];
+          L.fq[j] = s->fq[j];
+        }
+        L.z = s->z1;
+        L.w = s->w1;
+        L.bvec = s->bvec;
+        CK(launch_ionic(L, s->stream));
+        RUN(parabolic(s, pv, -1.0 / h, s->avec, 1.0 / h, s->bvec, s->k1v));
+        CK(launch_update(s->model, N, s->Xt[m + 1], s->k1v, s->z1, s->w1, s->Xc[m + 1], s->stream));
+        s->ionic_evals += 1;
+      }
+    } else {
+      for (int m = 1; m < M; ++m) CK(launch_copy(int64_t(ns) * N, s->Xt[m], s->Xc[m], s->stream));
+    }
+  }
+  CK(launch_finish(ns, N, s->Xn, s->Xc[M - 1], s->u[0], s->u[M - 1], s->t_act, s->opts.v_act_mV, dt, s->step_n,
+                   s->d_status, s->stream));
+  return BD_OK;
+}
+
+int do_step(bd_state* s, double dt, int M, int K) {
+  RUN(prepare_step(s, dt, M));
+  if (!s->opts.use_graph) {
+    RUN(enqueue_step(s, dt, M, K));
+  } else {
+    if (!s->gexec || s->g_dt != dt || s->g_M != M || s->g_K != K) {
+      if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      const int64_t ev0 = s->ionic_evals;
+      CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+      const int r = enqueue_step(s, dt, M, K);
+      cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+      if (r != BD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      if (e != cudaSuccess) return fail(s, BD_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&s->gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(s, BD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+      s->g_dt = dt;
+      s->g_M = M;
+      s->g_K = K;
+      s->ionic_evals = ev0;   // counted per replay below
+    }
+    CK(cudaGraphLaunch(s->gexec, s->stream));
+    s->ionic_evals += int64_t(K) * (3 * (M - 1) + (s->opts.sdc_correction ? M : 0)) + 1;
+  }
+  s->steps += 1;
+  s->sweeps += K;
+  return BD_OK;
+}
+
+void invalidate_graph(bd_state* s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = nullptr;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void bd_default_options(bd_opts_t* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = BD_FP64;
+  o->mass_lumped = 0;
+  o->pin_node = 0;
+  o->sdc_correction = 1;
+  o->cg_tol_e = 1e-10;
+  o->cg_tol_p = 1e-10;
+  o->cg_cap_e = 20000;
+  o->cg_cap_p = 2000;
+  o->sweep_tol = 0.0;
+  o->v_act_mV = -30.0;
+  o->spd_margin = 0.9;
+  o->use_graph = 1;
+}
+
+int bd_num_states(bd_ionic_t model) { return model_ns(int(model)); }
+
+int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, const bd_opts_t* opts,
+              bd_state_t** out) {
+  bd_state* s = nullptr;
+  if (!out) return fail(nullptr, BD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !cond || !mesh->xyz || !mesh->elems) return fail(nullptr, BD_ERR_ARG, "mesh/cond missing");
+  if (mesh->dim != 2 && mesh->dim != 3) return fail(nullptr, BD_ERR_ARG, "dim must be 2 or 3");
+  if (mesh->n_nodes < 2 || mesh->n_elems < 1) return fail(nullptr, BD_ERR_ARG, "empty mesh");
+  if (model_ns(int(model)) == 0) return fail(nullptr, BD_ERR_ARG, "unknown ionic model %d", int(model));
+  if (!(cond->chi > 0) || !(cond->cm > 0) || !(cond->sil >= 0) || !(cond->sit >= 0) || !(cond->sel >= 0) ||
+      !(cond->set >= 0))
+    return fail(nullptr, BD_ERR_ARG, "conductivities must be >= 0 and chi, cm > 0");
+  s = new bd_state();
+  if (opts) s->opts = *opts;
+  else bd_default_options(&s->opts);
+  if (s->opts.pin_node >= mesh->n_nodes || s->opts.pin_node < -1) {
+    delete s;
+    return fail(nullptr, BD_ERR_ARG, "pin_node out of range");
+  }
+  if (s->opts.precision != BD_FP64 && s->opts.precision != BD_MIXED) {
+    delete s;
+    return fail(nullptr, BD_ERR_ARG, "unknown precision");
+  }
+  s->model = int(model);
+  s->ns = model_ns(int(model));
+  s->dim = mesh->dim;
+  s->precision = s->opts.precision;
+  s->N = mesh->n_nodes;
+  s->inv_cm = 1.0 / cond->cm;
+  s->lambda_M = s->opts.mass_lumped ? 1.0 : (mesh->dim == 2 ? 0.25 : 0.2);
+
+  HostOps H;
+  std::string err;
+  int rc = assemble_host(mesh, cond, &H, &err);
+  if (rc != BD_OK) {
+    delete s;
+    return fail(nullptr, rc, "%s", err.c_str());
+  }
+  s->nnz = H.rowptr[s->N];
+
+  if (s->opts.stream) {
+    s->stream = static_cast<cudaStream_t>(s->opts.stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete s;
+      return fail(nullptr, BD_ERR_CUDA, "cudaStreamCreate failed (no CUDA device?)");
+    }
+    s->own_stream = true;
+  }
+  const int64_t N = s->N, nnz = s->nnz, ns = s->ns;
+  bool ok = alloc_n(s, &s->rowptr, N + 1) && alloc_n(s, &s->col, nnz) && alloc_n(s, &s->diagpos, N) &&
+            alloc_n(s, &s->Ai, nnz) && alloc_n(s, &s->Aie, nnz) && alloc_n(s, &s->Mc, nnz) &&
+            alloc_n(s, &s->Mv, nnz) && alloc_n(s, &s->ML, N) && alloc_n(s, &s->Xn, ns * N) &&
+            alloc_n(s, &s->dgs, N) && alloc_n(s, &s->rl, N) && alloc_n(s, &s->z1, (ns - 1) * N) &&
+            alloc_n(s, &s->w1, (ns - 1) * N) && alloc_n(s, &s->z2, (ns - 1) * N) &&
+            alloc_n(s, &s->w2, (ns - 1) * N) && alloc_n(s, &s->k1v, N) && alloc_n(s, &s->k2v, N) &&
+            alloc_n(s, &s->avec, N) && alloc_n(s, &s->bvec, N) && alloc_n(s, &s->cg_r, N) &&
+            alloc_n(s, &s->cg_z, N) && alloc_n(s, &s->cg_p, N) && alloc_n(s, &s->cg_q, N) &&
+            alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->t_act, N) && alloc_n(s, &s->stim_bits, N) &&
+            alloc_n(s, &s->step_n, 1) && alloc_n(s, &s->d_status, 1) && alloc_n(s, &s->d_stats, 4) &&
+            alloc_n(s, &s->d_clamps, 1) && alloc_n(s, &s->bar, 2);
+  for (int m = 0; ok && m < kMaxNodes; ++m)
+    ok = alloc_n(s, &s->Xt[m], ns * N) && alloc_n(s, &s->Xc[m], ns * N) && alloc_n(s, &s->fq[m], ns * N) &&
+         alloc_n(s, &s->u[m], N);
+  s->pcg_block = 256;
+  s->pcg_max = pcg_max_blocks(s->pcg_block);
+  if (ok && s->pcg_max <= 0) {
+    release(s);
+    delete s;
+    return fail(nullptr, BD_ERR_CUDA, "cannot size the cooperative CG grid");
+  }
+  const int64_t want = (N + s->pcg_block - 1) / s->pcg_block;
+  s->pcg_grid = int(std::max<int64_t>(1, std::min<int64_t>(want, s->pcg_max)));
+  if (ok) ok = alloc_n(s, &s->cg_part, int64_t(s->pcg_max) * 4);
+  if (!ok) {
+    release(s);
+    delete s;
+    return fail(nullptr, BD_ERR_OOM, "device allocation failed");
+  }
+  std::vector<double> Mlump(nnz, 0.0);
+  for (int64_t i = 0; i < N; ++i) Mlump[H.diagpos[i]] = H.ML[i];
+  auto up = [&](void* d, const void* h, size_t b) { return cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, s->stream); };
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = up(s->rowptr, H.rowptr.data(), (N + 1) * 4);
+  if (e == cudaSuccess) e = up(s->col, H.col.data(), nnz * 4);
+  if (e == cudaSuccess) e = up(s->diagpos, H.diagpos.data(), N * 4);
+  if (e == cudaSuccess) e = up(s->Ai, H.Ai.data(), nnz * 8);
+  if (e == cudaSuccess) e = up(s->Aie, H.Aie.data(), nnz * 8);
+  if (e == cudaSuccess) e = up(s->Mc, H.M.data(), nnz * 8);
+  if (e == cudaSuccess) e = up(s->Mv, s->opts.mass_lumped ? Mlump.data() : H.M.data(), nnz * 8);
+  if (e == cudaSuccess) e = up(s->ML, H.ML.data(), N * 8);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->stim_bits, 0, N * 4, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->bar, 0, 8, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, 4, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_stats, 0, 32, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_clamps, 0, 8, s->stream);
+  // the mass values outlive this scope only through the device copies; wait
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) {
+    release(s);
+    delete s;
+    return fail(nullptr, BD_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+  }
+  // resting initial state
+  std::vector<double> x0(ns), X(ns * N);
+  rest_state_host(s->model, x0.data());
+  for (int k = 0; k < ns; ++k)
+    for (int64_t i = 0; i < N; ++i) X[k * N + i] = x0[k];
+  rc = bd_set_initial(s, X.data(), nullptr);
+  if (rc != BD_OK) {
+    std::string m = s->err;
+    release(s);
+    delete s;
+    return fail(nullptr, rc, "%s", m.c_str());
+  }
+  *out = s;
+  return BD_OK;
+}
+
+int bd_add_stimulus(bd_state_t* s, const uint8_t* mask, double t_on, double dur, double amp) {
+  if (!s || !mask) return fail(s, BD_ERR_ARG, "NULL argument");
+  if (s->stim.n >= kMaxStim) return fail(s, BD_ERR_ARG, "at most %d stimuli", kMaxStim);
+  if (!std::isfinite(t_on) || !(dur >= 0) || !std::isfinite(amp)) return fail(s, BD_ERR_ARG, "bad stimulus timing/amplitude");
+  std::vector<uint32_t> bits(s->N);
+  CK(cudaMemcpyAsync(bits.data(), s->stim_bits, s->N * 4, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  const int k = s->stim.n;
+  for (int64_t i = 0; i < s->N; ++i)
+    if (mask[i]) bits[i] |= (1u << k);
+  CK(cudaMemcpyAsync(s->stim_bits, bits.data(), s->N * 4, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->stim.t_on[k] = t_on;
+  s->stim.dur[k] = dur;
+  s->stim.amp[k] = amp;
+  s->stim.n = k + 1;
+  invalidate_graph(s);
+  return BD_OK;
+}
+
+int bd_set_initial(bd_state_t* s, const double* X, const double* u) {
+  if (!s || !X) return fail(s, BD_ERR_ARG, "NULL argument");
+  const int64_t N = s->N, ns = s->ns;
+  for (int64_t i = 0; i < ns * N; ++i)
+    if (!std::isfinite(X[i])) return fail(s, BD_ERR_ARG, "non-finite initial state");
+  CK(cudaMemcpyAsync(s->Xn, X, ns * N * 8, cudaMemcpyHostToDevice, s->stream));
+  for (int m = 0; m < kMaxNodes; ++m) {
+    if (u) CK(cudaMemcpyAsync(s->u[m], u, N * 8, cudaMemcpyHostToDevice, s->stream));
+    else CK(cudaMemsetAsync(s->u[m], 0, N * 8, s->stream));
+  }
+  std::vector<double> nanv(N, std::nan(""));
+  CK(cudaMemcpyAsync(s->t_act, nanv.data(), N * 8, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemsetAsync(s->step_n, 0, 8, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return BD_OK;
+}
+
+int bd_step(bd_state_t* s, double dt, int M, int K) {
+  if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(s, BD_ERR_ARG, "dt must be positive");
+  if (M != 2 && M != 3) return fail(s, BD_ERR_ARG, "n_sdc_nodes must be 2 or 3");
+  if (K < 1) return fail(s, BD_ERR_ARG, "n_sweeps must be >= 1");
+  return do_step(s, dt, M, K);
+}
+
+int bd_batch_step(bd_state_t* const* states, int n, double dt, int M, int K) {
+  if (!states || n < 0) return fail(nullptr, BD_ERR_ARG, "bad batch");
+  for (int i = 0; i < n; ++i) {
+    const int r = bd_step(states[i], dt, M, K);
+    if (r != BD_OK) return r;
+  }
+  return BD_OK;
+}
+
+int bd_sync(bd_state_t* s) {
+  if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
+  return read_status(s);
+}
+
+void bd_clear_status(bd_state_t* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  cudaMemsetAsync(s->d_status, 0, 4, s->stream);
+  cudaMemsetAsync(s->bar, 0, 8, s->stream);
+  cudaStreamSynchronize(s->stream);
+  s->err.clear();
+}
+
+int bd_activation_times(const bd_state_t* cs, double* out, int64_t n) {
+  bd_state* s = const_cast<bd_state*>(cs);
+  if (!s || !out || n != s->N) return fail(s, BD_ERR_ARG, "bad arguments");
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaMemcpy(out, s->t_act, n * 8, cudaMemcpyDeviceToHost));
+  return read_status(s);
+}
+
+int bd_get_fields(const bd_state_t* cs, double* vm, double* phie, double* X) {
+  bd_state* s = const_cast<bd_state*>(cs);
+  if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
+  CK(cudaStreamSynchronize(s->stream));
+  if (vm) CK(cudaMemcpy(vm, s->Xn, s->N * 8, cudaMemcpyDeviceToHost));
+  if (phie) CK(cudaMemcpy(phie, s->u[0], s->N * 8, cudaMemcpyDeviceToHost));
+  if (X) CK(cudaMemcpy(X, s->Xn, int64_t(s->ns) * s->N * 8, cudaMemcpyDeviceToHost));
+  return read_status(s);
+}
+
+int bd_device_fields(const bd_state_t* s, const double** X_dev, const double** u_dev) {
+  if (!s) return fail(nullptr, BD_ERR_ARG, "NULL handle");
+  if (X_dev) *X_dev = s->Xn;
+  if (u_dev) *u_dev = s->u[0];
+  return BD_OK;
+}
+
+int bd_get_state(const bd_state_t* cs, void* buf, size_t* bytes) {
+  bd_state* s = const_cast<bd_state*>(cs);
+  if (!s || !bytes) return fail(s, BD_ERR_ARG, "NULL argument");
+  const size_t need = 32 + size_t(s->ns + 2) * size_t(s->N) * 8;
+  if (!buf) {
+    *bytes = need;
+    return BD_OK;
+  }
+  if (*bytes < need) return fail(s, BD_ERR_ARG, "buffer too small (%zu < %zu)", *bytes, need);
+  CK(cudaStreamSynchronize(s->stream));
+  char* p = static_cast<char*>(buf);
+  int64_t hdr[4] = {0x62647374, s->model, s->N, 0};
+  CK(cudaMemcpy(&hdr[3], s->step_n, 8, cudaMemcpyDeviceToHost));
+  std::memcpy(p, hdr, 32);
+  p += 32;
+  CK(cudaMemcpy(p, s->Xn, int64_t(s->ns) * s->N * 8, cudaMemcpyDeviceToHost));
+  p += int64_t(s->ns) * s->N * 8;
+  CK(cudaMemcpy(p, s->u[0], s->N * 8, cudaMemcpyDeviceToHost));
+  p += s->N * 8;
+  CK(cudaMemcpy(p, s->t_act, s->N * 8, cudaMemcpyDeviceToHost));
+  *bytes = need;
+  return BD_OK;
+}
+
+int bd_set_state(bd_state_t* s, const void* buf, size_t bytes) {
+  if (!s || !buf) return fail(s, BD_ERR_ARG, "NULL argument");
+  const size_t need = 32 + size_t(s->ns + 2) * size_t(s->N) * 8;
+  if (bytes != need) return fail(s, BD_ERR_ARG, "state blob has %zu bytes, expected %zu", bytes, need);
+  const char* p = static_cast<const char*>(buf);
+  int64_t hdr[4];
+  std::memcpy(hdr, p, 32);
+  if (hdr[0] != 0x62647374 || hdr[1] != s->model || hdr[2] != s->N)
+    return fail(s, BD_ERR_ARG, "state blob belongs to another model or mesh");
+  p += 32;
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaMemcpy(s->Xn, p, int64_t(s->ns) * s->N * 8, cudaMemcpyHostToDevice));
+  p += int64_t(s->ns) * s->N * 8;
+  for (int m = 0; m < kMaxNodes; ++m) CK(cudaMemcpy(s->u[m], p, s->N * 8, cudaMemcpyHostToDevice));
+  p += s->N * 8;
+  CK(cudaMemcpy(s->t_act, p, s->N * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->step_n, &hdr[3], 8, cudaMemcpyHostToDevice));
+  return BD_OK;
+}
+
+size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts_t* opts) {
+  (void)opts;
+  if (!mesh) return 0;
+  const int ns = model_ns(int(model));
+  if (ns == 0) return 0;
+  const double N = double(mesh->n_nodes);
+  const double nnz = N * (mesh->dim == 2 ? 7.0 : 15.0);   // P1 node graph, upper estimate for structured meshes
+  const double mat = nnz * (4 + 8 * 4 + 8 * 4) + N * (4 * 3 + 8);
+  const double st = N * 8 * (ns * (1 + 3 * kMaxNodes) + 4 * (ns - 1) + 3 * kMaxNodes + 16);
+  return size_t(mat + st) + (size_t(1) << 20);
+}
+
+int bd_get_stats(const bd_state_t* cs, bd_stats_t* out) {
+  bd_state* s = const_cast<bd_state*>(cs);
+  if (!s || !out) return fail(s, BD_ERR_ARG, "NULL argument");
+  long long st[4];
+  unsigned long long cl = 0;
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaMemcpy(st, s->d_stats, 32, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&cl, s->d_clamps, 8, cudaMemcpyDeviceToHost));
+  out->steps = s->steps;
+  out->sweeps = s->sweeps;
+  out->cg_iters_e = st[0];
+  out->cg_solves_e = st[1];
+  out->cg_iters_p = st[2];
+  out->cg_solves_p = st[3];
+  out->spd_clamps = int64_t(cl);
+  out->ionic_evals = s->ionic_evals;
+  return BD_OK;
+}
+
+int bd_reset_stats(bd_state_t* s) {
+  if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaMemset(s->d_stats, 0, 32));
+  CK(cudaMemset(s->d_clamps, 0, 8));
+  s->steps = s->sweeps = s->ionic_evals = 0;
+  return BD_OK;
+}
+
+int64_t bd_num_nodes(const bd_state_t* s) { return s ? s->N : 0; }
+
+const char* bd_last_error(const bd_state_t* s) {
+  if (s) return s->err.c_str();
+  return g_err.c_str();
+}
+
+void bd_destroy(bd_state_t* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  release(s);
+  delete s;
+}
+
+int bd_ionic_eval(bd_ionic_t model, int precision, int64_t n, const double* X, const double* istim, double cm,
+                  double* f, double* jac) {
+  bd_state* s = nullptr;
+  const int ns = model_ns(int(model));
+  if (ns == 0 || n < 0 || !X || !f || !(cm > 0)) return fail(nullptr, BD_ERR_ARG, "bad arguments");
+  if (n == 0) return BD_OK;
+  double *dX = nullptr, *dI = nullptr, *dF = nullptr, *dJ = nullptr;
+  const size_t bx = size_t(ns) * n * 8;
+  CK(cudaMalloc(&dX, bx));
+  CK(cudaMalloc(&dF, bx));
+  if (istim) CK(cudaMalloc(&dI, n * 8));
+  if (jac) CK(cudaMalloc(&dJ, size_t(n) * ns * ns * 8));
+  CK(cudaMemcpy(dX, X, bx, cudaMemcpyHostToDevice));
+  if (istim) CK(cudaMemcpy(dI, istim, n * 8, cudaMemcpyHostToDevice));
+  CK(launch_eval(int(model), precision, n, dX, dI, 1.0 / cm, dF, dJ, nullptr));
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(f, dF, bx, cudaMemcpyDeviceToHost));
+  if (jac) CK(cudaMemcpy(jac, dJ, size_t(n) * ns * ns * 8, cudaMemcpyDeviceToHost));
+  cudaFree(dX);
+  cudaFree(dF);
+  if (dI) cudaFree(dI);
+  if (dJ) cudaFree(dJ);
+  return BD_OK;
+}
+
+int bd_ionic_pattern(bd_ionic_t model, uint32_t* masks) {
+  if (!masks || model_ns(int(model)) == 0) return fail(nullptr, BD_ERR_ARG, "bad arguments");
+  pattern_host(int(model), masks);
+  return BD_OK;
+}
+
+int bd_rest_state(bd_ionic_t model, double* X) {
+  if (!X || model_ns(int(model)) == 0) return fail(nullptr, BD_ERR_ARG, "bad arguments");
+  rest_state_host(int(model), X);
+  return BD_OK;
+}
+
+int bd_operator_csr(const bd_state_t* cs, int which, int64_t* nnz, int32_t* rowptr, int32_t* col, double* val) {
+  bd_state* s = const_cast<bd_state*>(cs);
+  if (!s || !nnz || which < 0 || which > 3) return fail(s, BD_ERR_ARG, "bad arguments");
+  *nnz = which == 3 ? s->N : s->nnz;
+  if (!val) return BD_OK;   // size query
+  CK(cudaStreamSynchronize(s->stream));
+  if (which == 3) {
+    CK(cudaMemcpy(val, s->ML, s->N * 8, cudaMemcpyDeviceToHost));
+    return BD_OK;
+  }
+  if (!rowptr || !col) return fail(s, BD_ERR_ARG, "rowptr/col is NULL");
+  const double* src = which == 0 ? s->Ai : which == 1 ? s->Aie : s->Mc;
+  CK(cudaMemcpy(rowptr, s->rowptr, (s->N + 1) * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(col, s->col, s->nnz * 4, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(val, src, s->nnz * 8, cudaMemcpyDeviceToHost));
+  return BD_OK;
+}
+
+int bd_solve_elliptic(bd_state_t* s, const double* v, const double* u_guess, double* u, int* iters) {
+  if (!s || !v || !u) return fail(s, BD_ERR_ARG, "NULL argument");
+  const int64_t N = s->N;
+  double *dv = s->avec, *du = s->bvec;
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaMemcpyAsync(dv, v, N * 8, cudaMemcpyHostToDevice, s->stream));
+  if (u_guess) CK(cudaMemcpyAsync(du, u_guess, N * 8, cudaMemcpyHostToDevice, s->stream));
+  else CK(cudaMemsetAsync(du, 0, N * 8, s->stream));
+  long long before[2];
+  CK(cudaMemcpyAsync(before, s->d_stats, 16, cudaMemcpyDeviceToHost, s->stream));
+  RUN(elliptic(s, dv, du));
+  long long after[2];
+  CK(cudaMemcpyAsync(after, s->d_stats, 16, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(u, du, N * 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (iters) *iters = int(after[0] - before[0]);
+  return read_status(s);
+}
+
+}  // extern "C"

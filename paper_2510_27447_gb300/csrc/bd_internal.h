@@ -1,0 +1,136 @@
+// bd_internal.h -- shared declarations of the CUDA implementation.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/bd.h"
+
+namespace bd {
+
+constexpr int kMaxStim = 32;
+constexpr int kMaxNodes = 3;          // Gauss-Lobatto nodes per step
+constexpr int kMaxNS = 19;
+
+// device status word bits (one per bd_status_t failure kind)
+enum : int {
+  ST_NOT_CONVERGED = 1,
+  ST_NONFINITE = 2,
+  ST_INDEFINITE = 4,
+  ST_TIMEOUT = 8,
+};
+
+struct StimTable {
+  int n;
+  double t_on[kMaxStim];
+  double dur[kMaxStim];
+  double amp[kMaxStim];
+};
+
+// one node-local right-hand side recipe per ionic kernel launch
+enum IonicMode : int { MODE_S1 = 0, MODE_S2 = 1, MODE_CORR = 2 };
+
+struct IonicLaunch {
+  int model;                 // bd_ionic_t
+  int precision;             // bd_precision_t (compute type of the membrane model)
+  int mode;
+  int64_t n;
+  double alpha;              // shift of (alpha Mt - W)
+  double smin;               // safeguard floor of the condensed diagonal
+  double ck1;                // stage 2: 2/(gamma h)
+  double inv_gamma;          // stage 2: 1/gamma
+  double inv_dt;             // correction: 1/dt_m
+  double inv_cm;
+  double dt;                 // step size (for the stimulus clock)
+  double S[kMaxNodes];       // correction: quadrature row S_{m,j} (already times tau)
+  int n_nodes;               // correction: number of quadrature nodes
+  const double* XJ;          // state at which W is taken (ns x n)
+  const double* u;           // S1/S2: u_{m+1}
+  const double* k1v;         // S2
+  const double* z1;
+  const double* w1;
+  const double* Xprev;       // correction: X_m^new
+  const double* Xq[kMaxNodes];   // correction: predictor nodes X~_j
+  const double* uq[kMaxNodes];   // correction: u_j
+  const double* fq[kMaxNodes];   // correction: stored node fields f(X~_j)
+  const double* ML;
+  const uint32_t* stim_bits;
+  const long long* step_n;
+  StimTable stim;
+  double* dgs;               // out: M_L * s
+  double* rl;                // out: node-local part of the condensed rhs
+  double* z;                 // out: (ns-1) x n
+  double* w;                 // out: (ns-1) x n
+  double* avec;              // out: vector multiplied by A_i in the rhs
+  double* bvec;              // out: vector multiplied by M in the rhs
+  double* fq_out;            // out (optional): node field at the F point
+  unsigned long long* clamp_count;
+};
+
+// launchers (ionic.cu)
+cudaError_t launch_ionic(const IonicLaunch& L, cudaStream_t st);
+cudaError_t launch_field(int model, int precision, int64_t n, const double* X, double inv_cm, double dt,
+                         const uint32_t* stim_bits, const long long* step_n, const StimTable& stim,
+                         double* fout, cudaStream_t st);
+cudaError_t launch_combine(int model, int64_t n, const double* src, const double* k1v, const double* z1,
+                           const double* w1, const double* k2v, const double* z2, const double* w2, double m1,
+                           double m2, double* dst, cudaStream_t st);
+cudaError_t launch_update(int model, int64_t n, const double* Xt, const double* ev, const double* z,
+                          const double* w, double* dst, cudaStream_t st);
+cudaError_t launch_finish(int ns, int64_t n, double* Xn, const double* Xlast, double* u0, const double* ulast,
+                          double* t_act, double v_act, double dt, long long* step_n, int* status,
+                          cudaStream_t st);
+int model_ns(int model);
+void rest_state_host(int model, double* x);
+
+// sparse (pcg.cu)
+struct PcgLaunch {
+  int n;
+  const int* rowptr;
+  const int* col;
+  const int* diagpos;
+  const double* valA;
+  const double* dextra;     // optional extra diagonal
+  const double* rl;         // rhs = rl + c1 V1 a + c2 V2 b
+  const double* val1;
+  const double* va;
+  double c1;
+  const double* val2;
+  const double* vb;
+  double c2;
+  int project;              // subtract the mean of the rhs (singular Neumann system)
+  double* x;
+  int warm;
+  double tol;
+  int maxit;
+  int pin;                  // >= 0 pin node, -1 zero mean, -2 none
+  // workspaces
+  double* r;
+  double* z;
+  double* p;
+  double* q;
+  double* invd;
+  double* part;
+  unsigned* bar;
+  int* status;
+  long long* iters_acc;
+  long long* solves_acc;
+  int grid;                 // co-resident blocks
+  int block;
+};
+cudaError_t launch_pcg(const PcgLaunch& P, cudaStream_t st);
+int pcg_max_blocks(int block);
+cudaError_t launch_axpby_vals(int64_t nnz, double a, const double* X, double b, const double* Y, double* out,
+                              cudaStream_t st);
+cudaError_t launch_copy(int64_t n, const double* src, double* dst, cudaStream_t st);
+
+// host assembly (assemble.cpp)
+struct HostOps {
+  int64_t n = 0;
+  std::vector<int32_t> rowptr, col, diagpos;
+  std::vector<double> Ai, Aie, M, ML;
+};
+int assemble_host(const bd_mesh_t* mesh, const bd_cond_t* cond, HostOps* out, std::string* err);
+
+}  // namespace bd

@@ -1,0 +1,403 @@
+// ionic.cu -- node-wise kernels of the partitioned SDC step (one thread per
+// mesh node, the node's state vector in registers).
+//
+// Every kernel evaluates the membrane model of Sec. 2 with its exact
+// Jacobian (Sec. 3.3.2) through the compile-time sparse dual type and
+// eliminates the node's ODE states from the linear system of the ROS2 stage
+// (Eq. (3.13)) or of the SDC correction (Eq. (3.20)), leaving one condensed
+// unknown per node for the parabolic CG solve.
+#include <cuda_runtime.h>
+#include <utility>
+
+#include "bd_internal.h"
+#include "models.cuh"
+
+namespace bd {
+
+namespace {
+
+constexpr int kBlock = 128;
+
+__device__ __forceinline__ double stim_current(const uint32_t* bits, int64_t i, const StimTable& st,
+                                               double t, double dt) {
+  uint32_t b = bits ? bits[i] : 0u;
+  double s = 0.0;
+  const double eps = 1e-9 * dt;
+  while (b) {
+    const int k = __ffs(b) - 1;
+    b &= b - 1u;
+    if ((t - st.t_on[k]) > -eps && (t - st.t_on[k] - st.dur[k]) < -eps) s += st.amp[k];
+  }
+  return s;
+}
+
+template <template <class> class Model>
+struct Params;
+template <>
+struct Params<LR91> {
+  template <class T>
+  static LR91<T> get(int model) { return LR91<T>::make(model == BD_LR91_PAPER_MOD); }
+};
+template <>
+struct Params<TP06> {
+  template <class T>
+  static TP06<T> get(int) { return TP06<T>::make(); }
+};
+
+// ---------------------------------------------------------------------------
+// condensation kernel: S1, S2 and correction modes
+// ---------------------------------------------------------------------------
+template <template <class> class Model, class T, int MODE>
+__global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, const Model<T> P) {
+  using Mod = Model<T>;
+  constexpr int NS = Mod::NS;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= L.n) return;
+  const int64_t n = L.n;
+  const double t = double(*L.step_n) * L.dt;
+  const double istim = stim_current(L.stim_bits, i, L.stim, t, L.dt);
+
+  double xj[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) xj[k] = L.XJ[k * n + i];
+  T xt[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) xt[k] = T(xj[k]);
+
+  JacSink<T, Mod> e;
+  P.eval(xt, T(istim), T(L.inv_cm), e);
+
+  T rho[NS - 1];
+  double fv;                        // node field f_v at the F point
+  double avec = 0.0, bvec = 0.0;
+  if constexpr (MODE == MODE_S1) {
+#pragma unroll
+    for (int k = 1; k < NS; ++k) rho[k - 1] = e.f[k];
+    fv = double(e.f[0]);
+    avec = xj[0] + L.u[i];
+    if (L.fq_out) {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) L.fq_out[k * n + i] = double(e.f[k]);
+    }
+  } else if constexpr (MODE == MODE_S2) {
+    // F point X* = X + k1/gamma, k1_y = z1 + w1 k1_v
+    const double k1v = L.k1v[i];
+    double xs[NS];
+    double k1y[NS - 1];
+    xs[0] = xj[0] + k1v * L.inv_gamma;
+#pragma unroll
+    for (int k = 1; k < NS; ++k) {
+      k1y[k - 1] = L.z1[(k - 1) * n + i] + L.w1[(k - 1) * n + i] * k1v;
+      xs[k] = xj[k] + k1y[k - 1] * L.inv_gamma;
+    }
+    T xst[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) xst[k] = T(xs[k]);
+    ValSink<T, Mod> fs;
+    P.eval(xst, T(istim), T(L.inv_cm), fs);
+#pragma unroll
+    for (int k = 1; k < NS; ++k) rho[k - 1] = T(double(fs.f[k]) - L.ck1 * k1y[k - 1]);
+    fv = double(fs.f[0]);
+    avec = xs[0] + L.u[i];
+    bvec = k1v;
+  } else {
+    // correction: rho = [(X_m^new - X~_{m+1}) + sum_j S_j f_j] / dt_m on the y rows
+    double q[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) q[k] = 0.0;
+    double av = 0.0;
+    for (int jn = 0; jn < L.n_nodes; ++jn) {
+      const double S = L.S[jn];
+      const double* fj = L.fq[jn];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) q[k] += S * fj[k * n + i];
+      av += S * (L.Xq[jn][i] + L.uq[jn][i]);
+    }
+#pragma unroll
+    for (int k = 1; k < NS; ++k) rho[k - 1] = T(((L.Xprev[k * n + i] - xj[k]) + q[k]) * L.inv_dt);
+    fv = q[0] * L.inv_dt;
+    avec = av;
+    bvec = L.Xprev[i] - xj[0];
+  }
+
+  T s, corr;
+  T z[NS - 1], w[NS - 1];
+  condense<T, Mod>(e, T(L.alpha), rho, s, corr, z, w);
+  double sd = double(s);
+  if (sd < L.smin) {
+    sd = L.smin;
+    atomicAdd(L.clamp_count, 1ull);
+  }
+  const double ml = L.ML[i];
+  L.dgs[i] = ml * sd;
+  L.rl[i] = ml * (fv + double(corr));
+#pragma unroll
+  for (int k = 0; k < NS - 1; ++k) {
+    L.z[k * n + i] = double(z[k]);
+    L.w[k * n + i] = double(w[k]);
+  }
+  L.avec[i] = avec;
+  if (L.bvec) L.bvec[i] = bvec;
+}
+
+template <template <class> class Model, class T>
+__global__ void __launch_bounds__(kBlock) field_kernel(int64_t n, const double* X, double inv_cm, double dt,
+                                                       const uint32_t* stim_bits, const long long* step_n,
+                                                       const StimTable stim, double* fout, const Model<T> P) {
+  using Mod = Model<T>;
+  constexpr int NS = Mod::NS;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double t = step_n ? double(*step_n) * dt : 0.0;
+  const double istim = stim_current(stim_bits, i, stim, t, dt);
+  T x[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) x[k] = T(X[k * n + i]);
+  ValSink<T, Mod> fs;
+  P.eval(x, T(istim), T(inv_cm), fs);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) fout[k * n + i] = double(fs.f[k]);
+}
+
+// X_{m+1} = X + m1 k1 + m2 k2, k_y = z + w k_v  (ROS2 combination, Eq. (3.14))
+template <int NS>
+__global__ void __launch_bounds__(kBlock) combine_kernel(int64_t n, const double* src, const double* k1v,
+                                                         const double* z1, const double* w1, const double* k2v,
+                                                         const double* z2, const double* w2, double m1, double m2,
+                                                         double* dst) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = k1v[i], b = k2v[i];
+  dst[i] = src[i] + m1 * a + m2 * b;
+#pragma unroll
+  for (int k = 1; k < NS; ++k) {
+    const int64_t o = (k - 1) * n + i;
+    const double k1 = z1[o] + w1[o] * a;
+    const double k2 = z2[o] + w2[o] * b;
+    dst[k * n + i] = src[k * n + i] + m1 * k1 + m2 * k2;
+  }
+}
+
+// X^new_{m+1} = X~_{m+1} + eps, eps_y = z + w eps_v
+template <int NS>
+__global__ void __launch_bounds__(kBlock) update_kernel(int64_t n, const double* Xt, const double* ev,
+                                                        const double* z, const double* w, double* dst) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double e = ev[i];
+  dst[i] = Xt[i] + e;
+#pragma unroll
+  for (int k = 1; k < NS; ++k) {
+    const int64_t o = (k - 1) * n + i;
+    dst[k * n + i] = Xt[k * n + i] + z[o] + w[o] * e;
+  }
+}
+
+// end of step: activation times, X^n <- X^{n+1}, u^n <- u^{n+1}, n <- n + 1
+__global__ void __launch_bounds__(256) finish_kernel(int ns, int64_t n, double* Xn, const double* Xlast, double* u0,
+                                                     const double* ulast, double* t_act, double v_act, double dt,
+                                                     long long* step_n, int* status) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long sn = *step_n;
+  if (i < n) {
+    const double vo = Xn[i], vn = Xlast[i];
+    if (!isfinite(vn)) atomicOr(status, ST_NONFINITE);
+    if (isnan(t_act[i]) && vo < v_act && vn >= v_act) t_act[i] = double(sn) * dt + (v_act - vo) / (vn - vo) * dt;
+    for (int k = 0; k < ns; ++k) Xn[k * n + i] = Xlast[k * n + i];
+    u0[i] = ulast[i];
+  }
+  // every block reads step_n above; the grid-wide increment happens in a
+  // separate one-thread launch so no block can see the new value early
+}
+
+__global__ void bump_kernel(long long* step_n) { *step_n += 1; }
+
+template <template <class> class Model, class T>
+cudaError_t launch_ionic_t(const IonicLaunch& L, cudaStream_t st) {
+  const auto P = Params<Model>::template get<T>(L.model);
+  const unsigned grid = unsigned((L.n + kBlock - 1) / kBlock);
+  switch (L.mode) {
+    case MODE_S1: ionic_kernel<Model, T, MODE_S1><<<grid, kBlock, 0, st>>>(L, P); break;
+    case MODE_S2: ionic_kernel<Model, T, MODE_S2><<<grid, kBlock, 0, st>>>(L, P); break;
+    default: ionic_kernel<Model, T, MODE_CORR><<<grid, kBlock, 0, st>>>(L, P); break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int model_ns(int model) {
+  switch (model) {
+    case BD_LR91:
+    case BD_LR91_PAPER_MOD: return 8;
+    case BD_TP06_EPI: return 19;
+    default: return 0;
+  }
+}
+
+cudaError_t launch_ionic(const IonicLaunch& L, cudaStream_t st) {
+  if (L.n == 0) return cudaSuccess;
+  const bool f32 = L.precision == BD_MIXED;
+  if (L.model == BD_TP06_EPI) return f32 ? launch_ionic_t<TP06, float>(L, st) : launch_ionic_t<TP06, double>(L, st);
+  return f32 ? launch_ionic_t<LR91, float>(L, st) : launch_ionic_t<LR91, double>(L, st);
+}
+
+cudaError_t launch_field(int model, int precision, int64_t n, const double* X, double inv_cm, double dt,
+                         const uint32_t* stim_bits, const long long* step_n, const StimTable& stim, double* fout,
+                         cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = unsigned((n + kBlock - 1) / kBlock);
+  const bool f32 = precision == BD_MIXED;
+  if (model == BD_TP06_EPI) {
+    if (f32) field_kernel<TP06, float><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, TP06<float>::make());
+    else field_kernel<TP06, double><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, TP06<double>::make());
+  } else {
+    const bool pm = model == BD_LR91_PAPER_MOD;
+    if (f32) field_kernel<LR91, float><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, LR91<float>::make(pm));
+    else field_kernel<LR91, double><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, LR91<double>::make(pm));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(int model, int64_t n, const double* src, const double* k1v, const double* z1,
+                           const double* w1, const double* k2v, const double* z2, const double* w2, double m1,
+                           double m2, double* dst, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = unsigned((n + kBlock - 1) / kBlock);
+  if (model == BD_TP06_EPI) combine_kernel<19><<<grid, kBlock, 0, st>>>(n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst);
+  else combine_kernel<8><<<grid, kBlock, 0, st>>>(n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(int model, int64_t n, const double* Xt, const double* ev, const double* z,
+                          const double* w, double* dst, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = unsigned((n + kBlock - 1) / kBlock);
+  if (model == BD_TP06_EPI) update_kernel<19><<<grid, kBlock, 0, st>>>(n, Xt, ev, z, w, dst);
+  else update_kernel<8><<<grid, kBlock, 0, st>>>(n, Xt, ev, z, w, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish(int ns, int64_t n, double* Xn, const double* Xlast, double* u0, const double* ulast,
+                          double* t_act, double v_act, double dt, long long* step_n, int* status,
+                          cudaStream_t st) {
+  if (n > 0) {
+    const unsigned grid = unsigned((n + 255) / 256);
+    finish_kernel<<<grid, 256, 0, st>>>(ns, n, Xn, Xlast, u0, ulast, t_act, v_act, dt, step_n, status);
+  }
+  bump_kernel<<<1, 1, 0, st>>>(step_n);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// host-side helpers: rest state and the standalone evaluation entry point
+// ---------------------------------------------------------------------------
+
+namespace {
+
+template <class Mod>
+void field_host(const Mod& P, const double* x, double* f, double J[kMaxNS][kMaxNS]) {
+  DenseSink<double, Mod> s;
+  P.eval(x, 0.0, 1.0, s);
+  for (int r = 0; r < Mod::NS; ++r) {
+    f[r] = s.f[r];
+    for (int c = 0; c < Mod::NS; ++c) J[r][c] = s.J[r][c];
+  }
+}
+
+// Newton on the single-cell field f(x) = 0 with dense partial pivoting.
+template <class Mod>
+void newton_rest(const Mod& P, double* x) {
+  constexpr int n = Mod::NS;
+  for (int it = 0; it < 60; ++it) {
+    double f[kMaxNS], J[kMaxNS][kMaxNS];
+    field_host(P, x, f, J);
+    double A[kMaxNS][kMaxNS + 1];
+    for (int r = 0; r < n; ++r) {
+      for (int c = 0; c < n; ++c) A[r][c] = J[r][c];
+      A[r][n] = -f[r];
+    }
+    for (int k = 0; k < n; ++k) {
+      int piv = k;
+      for (int r = k + 1; r < n; ++r)
+        if (std::fabs(A[r][k]) > std::fabs(A[piv][k])) piv = r;
+      if (piv != k)
+        for (int c = 0; c <= n; ++c) std::swap(A[k][c], A[piv][c]);
+      for (int r = k + 1; r < n; ++r) {
+        const double l = A[r][k] / A[k][k];
+        for (int c = k; c <= n; ++c) A[r][c] -= l * A[k][c];
+      }
+    }
+    double dx[kMaxNS];
+    double rel = 0.0;
+    for (int r = n - 1; r >= 0; --r) {
+      double s = A[r][n];
+      for (int c = r + 1; c < n; ++c) s -= A[r][c] * dx[c];
+      dx[r] = s / A[r][r];
+    }
+    for (int r = 0; r < n; ++r) {
+      x[r] += dx[r];
+      rel = std::fmax(rel, std::fabs(dx[r]) / std::fmax(std::fabs(x[r]), 1e-12));
+    }
+    if (rel < 1e-13) break;
+  }
+}
+
+template <template <class> class Model, class T>
+__global__ void eval_kernel(int64_t n, const double* X, const double* istim, double inv_cm, double* f, double* jac,
+                            const Model<T> P) {
+  using Mod = Model<T>;
+  constexpr int NS = Mod::NS;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T x[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) x[k] = T(X[k * n + i]);
+  const T is = istim ? T(istim[i]) : T(0);
+  DenseSink<T, Mod> s;
+  P.eval(x, is, T(inv_cm), s);
+  for (int r = 0; r < NS; ++r) {
+    f[r * n + i] = double(s.f[r]);
+    if (jac)
+      for (int c = 0; c < NS; ++c) jac[(i * NS + r) * NS + c] = double(s.J[r][c]);
+  }
+}
+
+}  // namespace
+
+void rest_state_host(int model, double* x) {
+  if (model == BD_TP06_EPI) {
+    // TP06 conserves charge (the stimulus is carried by K+), so its Jacobian
+    // is singular at rest; the published initial values are used instead.
+    TP06<double>::initial(x);
+    return;
+  }
+  LR91<double>::initial(x);
+  newton_rest(LR91<double>::make(model == BD_LR91_PAPER_MOD), x);
+}
+
+cudaError_t launch_eval(int model, int precision, int64_t n, const double* X, const double* istim, double inv_cm,
+                        double* f, double* jac, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = unsigned((n + 63) / 64);
+  const bool f32 = precision == BD_MIXED;
+  if (model == BD_TP06_EPI) {
+    if (f32) eval_kernel<TP06, float><<<grid, 64, 0, st>>>(n, X, istim, inv_cm, f, jac, TP06<float>::make());
+    else eval_kernel<TP06, double><<<grid, 64, 0, st>>>(n, X, istim, inv_cm, f, jac, TP06<double>::make());
+  } else {
+    const bool pm = model == BD_LR91_PAPER_MOD;
+    if (f32) eval_kernel<LR91, float><<<grid, 64, 0, st>>>(n, X, istim, inv_cm, f, jac, LR91<float>::make(pm));
+    else eval_kernel<LR91, double><<<grid, 64, 0, st>>>(n, X, istim, inv_cm, f, jac, LR91<double>::make(pm));
+  }
+  return cudaGetLastError();
+}
+
+void pattern_host(int model, uint32_t* masks) {
+  if (model == BD_TP06_EPI) {
+    for (int r = 0; r < 19; ++r) masks[r] = TP06<double>::ROWMASK[r];
+  } else {
+    for (int r = 0; r < 8; ++r) masks[r] = LR91<double>::ROWMASK[r];
+  }
+}
+
+}  // namespace bd

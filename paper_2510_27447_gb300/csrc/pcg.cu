@@ -1,0 +1,313 @@
+// pcg.cu -- Jacobi-preconditioned conjugate gradients as one persistent,
+// cooperatively launched kernel.
+//
+// Used for the elliptic constraint A_ie u = -A_i v (Eq. (3.15)) and for the
+// condensed parabolic systems (alpha M + A_i + M_L diag(s)) k_v = r of the
+// ROS2 stages (Eq. (3.13)) and of the SDC correction (Eq. (3.20)).  The
+// paper solves these with BiCGSTAB + block Jacobi / AMG (Sec. 3.3.2); the
+// node-wise elimination done in the ionic kernels makes the systems
+// symmetric positive (semi-)definite, so plain PCG applies.
+//
+// One launch runs the whole solve: rows are distributed over all threads of
+// a grid that is resident on the device at once (cooperative launch), and
+// the iteration synchronises with a device-wide barrier.  Per iteration:
+//   phase A  beta, p = z + beta p, q = A z + beta q   (q = A p by recurrence;
+//            reads z of other rows, written before the previous barrier)
+//            partial p.q                                          -> barrier
+//   phase B  alpha = rho / p.q, x += alpha p, r -= alpha q, z = D^-1 r,
+//            partial r.z and r.r                                  -> barrier
+// Reductions are deterministic: per-block partials, then every block sums
+// the partials in the same fixed order.  Every barrier wait is bounded; on
+// timeout the kernel records ST_TIMEOUT and returns.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "bd_internal.h"
+
+namespace bd {
+
+namespace {
+
+constexpr long long kSpinLimit = 1ll << 24;   // ~2 s of 128 ns sleeps
+
+// sense-free generation barrier: bar[0] = arrivals, bar[1] = generation
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    ok = 1;
+    if (arrived == nblocks - 1u) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g0) {
+        __nanosleep(128);
+        if (++spins > kSpinLimit) {
+          atomicOr(status, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// block-wide sum of NV values; result valid in thread 0
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[32]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[k][wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double x = lane < nw ? sh[k][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[k] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// every block sums part[b*4 + slot] over b = 0..nb-1 in the same order
+template <int NV>
+__device__ __forceinline__ void grid_total(const double* part, const int (&slot)[NV], int nb, double (&out)[NV],
+                                           double (*sh)[32]) {
+  double v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] += __ldcg(part + b * 4 + slot[k]);
+  block_sum<NV>(v, sh);
+  __shared__ double bc[NV];
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) bc[k] = v[k];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = bc[k];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) pcg_kernel(const PcgLaunch a) {
+  __shared__ double sh[4][32];
+  const int n = a.n;
+  const int nb = gridDim.x;
+  const int stride = blockDim.x * gridDim.x;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int* __restrict__ rp = a.rowptr;
+  const int* __restrict__ col = a.col;
+
+  // ---- phase 0: right-hand side, initial residual --------------------------
+  double acc0[2] = {0.0, 0.0};
+  for (int i = i0; i < n; i += stride) {
+    double b = a.rl ? a.rl[i] : 0.0;
+    const int k0 = rp[i], k1 = rp[i + 1];
+    if (a.val1) {
+      double s = 0.0;
+      for (int k = k0; k < k1; ++k) s += a.val1[k] * a.va[col[k]];
+      b += a.c1 * s;
+    }
+    if (a.val2) {
+      double s = 0.0;
+      for (int k = k0; k < k1; ++k) s += a.val2[k] * a.vb[col[k]];
+      b += a.c2 * s;
+    }
+    double d = a.valA[a.diagpos[i]];
+    if (a.dextra) d += a.dextra[i];
+    a.invd[i] = 1.0 / d;
+    double r = b;
+    if (a.warm) {
+      double ax = a.dextra ? a.dextra[i] * a.x[i] : 0.0;
+      for (int k = k0; k < k1; ++k) ax += a.valA[k] * a.x[col[k]];
+      r -= ax;
+    }
+    a.r[i] = r;
+    acc0[0] += b;
+    acc0[1] += b * b;
+  }
+  if (!a.warm)
+    for (int i = i0; i < n; i += stride) a.x[i] = 0.0;
+  block_sum<2>(acc0, sh);
+  if (threadIdx.x == 0) {
+    a.part[blockIdx.x * 4 + 0] = acc0[0];
+    a.part[blockIdx.x * 4 + 1] = acc0[1];
+  }
+  if (!grid_barrier(a.bar, nb, a.status)) return;
+  double tot[2];
+  grid_total<2>(a.part, {0, 1}, nb, tot, sh);
+  const double mean_b = a.project ? tot[0] / double(n) : 0.0;
+  double bb = a.project ? tot[1] - double(n) * mean_b * mean_b : tot[1];
+  if (bb < 0.0) bb = 0.0;
+  const double tol2 = a.tol * a.tol * bb;
+
+  // ---- phase 1: z = D^-1 r, p = z ------------------------------------------
+  double acc1[2] = {0.0, 0.0};
+  for (int i = i0; i < n; i += stride) {
+    const double r = a.r[i] - mean_b;
+    a.r[i] = r;
+    const double z = r * a.invd[i];
+    a.z[i] = z;
+    acc1[0] += r * z;
+    acc1[1] += r * r;
+  }
+  block_sum<2>(acc1, sh);
+  if (threadIdx.x == 0) {
+    a.part[blockIdx.x * 4 + 2] = acc1[0];
+    a.part[blockIdx.x * 4 + 3] = acc1[1];
+  }
+  if (!grid_barrier(a.bar, nb, a.status)) return;
+  grid_total<2>(a.part, {2, 3}, nb, tot, sh);
+  double rho = tot[0];
+  double rr = tot[1];
+
+  int it = 0;
+  int fail = 0;
+  bool done = !(rr > tol2);      // includes b = 0
+  double beta = 0.0;
+  while (!done) {
+    // phase A
+    double pq[1] = {0.0};
+    for (int i = i0; i < n; i += stride) {
+      const double z = a.z[i];
+      double az = a.dextra ? a.dextra[i] * z : 0.0;
+      const int k0 = rp[i], k1 = rp[i + 1];
+      for (int k = k0; k < k1; ++k) az += a.valA[k] * __ldcg(a.z + col[k]);   // other blocks' z
+      const double p = it == 0 ? z : z + beta * a.p[i];
+      const double q = it == 0 ? az : az + beta * a.q[i];
+      a.p[i] = p;
+      a.q[i] = q;
+      pq[0] += p * q;
+    }
+    block_sum<1>(pq, sh);
+    if (threadIdx.x == 0) a.part[blockIdx.x * 4 + 0] = pq[0];
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    double t1[1];
+    grid_total<1>(a.part, {0}, nb, t1, sh);
+    if (!(t1[0] > 0.0)) {
+      fail = isfinite(t1[0]) ? ST_INDEFINITE : ST_NONFINITE;
+      break;
+    }
+    const double alpha = rho / t1[0];
+    // phase B
+    double acc[2] = {0.0, 0.0};
+    for (int i = i0; i < n; i += stride) {
+      a.x[i] += alpha * a.p[i];
+      const double r = a.r[i] - alpha * a.q[i];
+      a.r[i] = r;
+      const double z = r * a.invd[i];
+      a.z[i] = z;
+      acc[0] += r * z;
+      acc[1] += r * r;
+    }
+    block_sum<2>(acc, sh);
+    if (threadIdx.x == 0) {
+      a.part[blockIdx.x * 4 + 2] = acc[0];
+      a.part[blockIdx.x * 4 + 3] = acc[1];
+    }
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    grid_total<2>(a.part, {2, 3}, nb, tot, sh);
+    ++it;
+    rr = tot[1];
+    if (!isfinite(rr)) {
+      fail = ST_NONFINITE;
+      break;
+    }
+    if (rr <= tol2) break;
+    if (it >= a.maxit) {
+      fail = ST_NOT_CONVERGED;
+      break;
+    }
+    beta = tot[0] / rho;
+    rho = tot[0];
+  }
+
+  // ---- normalisation of the singular elliptic solution ----------------------
+  if (a.pin >= 0) {
+    const double shift = __ldcg(a.x + a.pin);
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    for (int i = i0; i < n; i += stride) a.x[i] -= shift;
+  } else if (a.pin == -1) {
+    double sx[1] = {0.0};
+    for (int i = i0; i < n; i += stride) sx[0] += a.x[i];
+    block_sum<1>(sx, sh);
+    if (threadIdx.x == 0) a.part[blockIdx.x * 4 + 0] = sx[0];
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    double t1[1];
+    grid_total<1>(a.part, {0}, nb, t1, sh);
+    const double mean = t1[0] / double(n);
+    for (int i = i0; i < n; i += stride) a.x[i] -= mean;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (fail) atomicOr(a.status, fail);
+    if (a.iters_acc) atomicAdd((unsigned long long*)a.iters_acc, (unsigned long long)it);
+    if (a.solves_acc) atomicAdd((unsigned long long*)a.solves_acc, 1ull);
+  }
+}
+
+__global__ void axpby_kernel(int64_t n, double a, const double* X, double b, const double* Y, double* out) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a * X[i] + b * Y[i];
+}
+
+__global__ void copy_kernel(int64_t n, const double* src, double* dst) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = src[i];
+}
+
+}  // namespace
+
+int pcg_max_blocks(int block) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_kernel, block, 0) != cudaSuccess) return 0;
+  return sms * per;
+}
+
+cudaError_t launch_pcg(const PcgLaunch& P, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(P.grid));
+  cfg.blockDim = dim3(unsigned(P.block));
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, pcg_kernel, P);
+}
+
+cudaError_t launch_axpby_vals(int64_t n, double a, const double* X, double b, const double* Y, double* out,
+                              cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  axpby_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(n, a, X, b, Y, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy(int64_t n, const double* src, double* dst, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  copy_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(n, src, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace bd

@@ -1,0 +1,89 @@
+"""Host-side checks of the C-ABI library (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lr91, tp06
+from paper_2510_27447_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.lib()
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "bd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bd_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    decl = _declared_symbols()
+    assert len(decl) >= 20
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert sorted(binding.EXPORTS) == decl
+
+
+def test_state_counts(lib):
+    assert binding.num_states(binding.LR91) == 8
+    assert binding.num_states(binding.TP06_EPI) == 19
+    assert binding.num_states(7) == 0
+
+
+@pytest.mark.parametrize("model,cell", [(binding.LR91, lr91.model()), (binding.TP06_EPI, tp06.model())],
+                         ids=["lr91", "tp06"])
+def test_compile_time_pattern_equals_detected_pattern(lib, model, cell):
+    """The node-Jacobian sparsity compiled into the kernels (the CTSM blocks)
+    equals the pattern detected on the oracle by complex-step derivatives at
+    random states."""
+    rng = np.random.default_rng(5)
+    x0 = cell.initial()
+    X = np.repeat(x0[:, None], 64, axis=1)
+    X[0] = rng.uniform(-90, 40, 64)
+    for r in range(1, cell.ns):
+        X[r] = x0[r] * rng.uniform(0.5, 1.5, 64) if x0[r] > 0 else rng.uniform(0.01, 0.99, 64)
+    for r in cell.gate_rows:
+        X[r] = rng.uniform(0.02, 0.98, 64)
+    J = cell.jacobian(X, np.full(64, 10.0))
+    detected = np.zeros(cell.ns, dtype=np.uint32)
+    for r in range(cell.ns):
+        for c in range(cell.ns):
+            if np.any(J[r, c] != 0.0):
+                detected[r] |= np.uint32(1 << c)
+    declared = binding.ionic_pattern(model)
+    np.testing.assert_array_equal(declared, detected)
+
+
+def test_lr91_rest_state_matches_oracle(lib):
+    for model, paper in ((binding.LR91, False), (binding.LR91_PAPER_MOD, True)):
+        np.testing.assert_allclose(binding.rest_state(model), lr91.model(paper).rest_state(),
+                                   rtol=1e-11, atol=1e-15)
+
+
+def test_tp06_rest_state_is_published_initial_values(lib):
+    np.testing.assert_array_equal(binding.rest_state(binding.TP06_EPI), tp06.model().initial())
+
+
+def test_bad_arguments_are_rejected_without_a_device(lib):
+    m = binding.Mesh(4, 3, 1, None, None, None)
+    h = ctypes.c_void_p()
+    rc = lib.bd_create(ctypes.byref(m), None, 0, None, ctypes.byref(h))
+    assert rc == -1 and not h.value
+    assert b"" != lib.bd_last_error(None)
+
+
+def test_footprint_scales_with_nodes(lib):
+    from paper_2510_27447_gb300 import workloads as W
+    a = binding.footprint_bytes(*W.square_grid(33), binding.LR91)
+    b = binding.footprint_bytes(*W.square_grid(65), binding.LR91)
+    c = binding.footprint_bytes(*W.square_grid(65), binding.TP06_EPI)
+    assert 3.5 < (b - 2**20) / (a - 2**20) < 4.2
+    assert c > 1.5 * b
