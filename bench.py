@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Throughput of the partitioned-SDC bidomain step on GB300.
+
+Metric: node-steps/s of one partitioned-SDC time step (Algorithm 2: elliptic
+solve, ROS2 predictor, SDC correction; 3 Gauss-Lobatto nodes, 2 sweeps) on
+the TP06 epicardial sheet of 257 x 257 P1 nodes (66,049 nodes, 2.5 cm square,
+fibres along x, dt = 0.02 ms, S1 strip x < 0.1 cm at t = 0), inputs resident
+in HBM.  `value` is the mixed-precision path, `fp64` the pure FP64 path.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs one independent replica per GPU (the method has no data-path
+exchange here) under torchrun; rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "node-steps/s, partitioned SDC step, mixed vs FP64 on 1 GB300"
+WORKLOAD = "tp06_sheet_257x257"
+SIDE, LENGTH, DT, M_NODES, K_SWEEPS = 257, 2.5, 0.02, 3, 2
+SAMPLE_SIDE = 33          # oracle sample: 33 x 33 nodes at the same spacing
+
+
+# ---------------------------------------------------------------------------
+# oracle legs (CPU): cpu_baseline and --impl reference
+# ---------------------------------------------------------------------------
+
+def oracle_sample_problem():
+    from oracle import bidomain as OB
+    from oracle import tp06 as OT
+    from paper_2510_27447_gb300 import workloads as W
+    h = LENGTH / (SIDE - 1)
+    w = W.sheet(SAMPLE_SIDE, h * (SAMPLE_SIDE - 1), W.TP06_EPI, DT, 1)
+    cell = OT.model()
+    P = OB.Bidomain(w.xyz, w.elems, w.fibers, w.sigma, w.chi, w.cm, cell, w.stimuli, pin_node=0)
+    import numpy as np
+    X = np.repeat(cell.initial()[:, None], w.n_nodes, axis=1)
+    return P, X, w.n_nodes
+
+
+def oracle_rate(warmup: int, steps: int, seconds: float) -> dict:
+    import numpy as np
+    P, X, n = oracle_sample_problem()
+    u = np.zeros(n)
+    for k in range(warmup):
+        X, u, _ = P.step(X, u, k * DT, DT, M_NODES, K_SWEEPS)
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps or (seconds > 0 and time.perf_counter() - t0 < seconds):
+        X, u, _ = P.step(X, u, (warmup + done) * DT, DT, M_NODES, K_SWEEPS)
+        done += 1
+        if seconds > 0 and done >= steps and time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n * done / el, "steps": done, "seconds": el, "nodes": n}
+
+
+def run_oracle_subprocess(warmup: int, steps: int, seconds: float) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--warmup", str(warmup),
+           "--steps", str(steps), "--seconds", str(seconds)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def sample_text(res: dict) -> str:
+    return (f"FP64 oracle (numpy/scipy, sparse direct solves), TP06 sheet of {SAMPLE_SIDE}x{SAMPLE_SIDE} "
+            f"nodes at the 257x257 grid spacing, dt={DT} ms, M={M_NODES}, K={K_SWEEPS}, "
+            f"{res['steps']} steps from t=0 in {res['seconds']:.1f} s, 1 thread")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+
+def pcg_bytes(iters: int, solves: int, n: int, nnz: int, parabolic: bool) -> float:
+    """Algorithmic HBM bytes of the CSR PCG kernel (FP64 values, int32 indices).
+
+    Per iteration: SpMV q = A z reads values + columns (12 B/nnz), row
+    pointers (4 B/row) and z once (8 B/row); the vector updates of the two
+    phases move p, q, x, r (read+write), z (read+write), 1/D (read) and, for the
+    condensed parabolic operator, its extra diagonal: 104 (+8) B/row.
+    Per solve: the right-hand side SpMV(s) and the initial residual
+    (2 x (12 nnz + 8 n) + 48 n).
+    """
+    per_iter = 12.0 * nnz + 4.0 * n + (112.0 if parabolic else 104.0) * n
+    per_solve = 2.0 * (12.0 * nnz + 8.0 * n) + 48.0 * n
+    return iters * per_iter + solves * per_solve
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pcg.cu", "bd_internal.h"):
+        with open(os.path.join(ROOT, "paper_2510_27447_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kind: str):
+    """DRAM traffic per launch from the committed ncu summary, if the kernel
+    source is unchanged since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d.get(kind)
+        if e and e.get("source_hash") == kernel_source_hash():
+            return e.get("bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+
+def make_sim(precision: int, stream_handle: int):
+    from paper_2510_27447_gb300 import binding, workloads as W
+    w = W.sheet(SIDE, LENGTH, W.TP06_EPI, DT, 1, name=WORKLOAD)
+    opts = binding.default_options(precision=precision, stream=stream_handle, cg_tol_e=1e-10, cg_tol_p=1e-10)
+    return binding.simulation_from_workload(w, opts), w
+
+
+def time_steps(sim, torch, stream, flush, steps: int) -> list:
+    ms = []
+    for _ in range(steps):
+        flush.add_(1.0)                       # evict L2 between timed steps
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(DT, M_NODES, K_SWEEPS)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def e2e_rate(sim, torch, steps: int) -> dict:
+    """Same metric through the C ABI with host buffers: every step uploads the
+    state blob from pinned host memory, steps, and reads v and u back."""
+    import ctypes as C
+    from paper_2510_27447_gb300 import binding
+    L = binding.lib()
+    blob = sim.get_state()
+    nb = len(blob)
+    host = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+    host.numpy()[:] = memoryview(blob)
+    vout = torch.empty(sim.N, dtype=torch.float64, pin_memory=True)
+    uout = torch.empty(sim.N, dtype=torch.float64, pin_memory=True)
+    dp = C.POINTER(C.c_double)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        rc = L.bd_set_state(sim.h, C.c_void_p(host.data_ptr()), nb)
+        if rc:
+            raise binding.BdError(rc, "set_state")
+        sim.step(DT, M_NODES, K_SWEEPS)
+        rc = L.bd_get_fields(sim.h, C.cast(C.c_void_p(vout.data_ptr()), dp),
+                             C.cast(C.c_void_p(uout.data_ptr()), dp), None)
+        if rc:
+            raise binding.BdError(rc, "get_fields")
+    el = time.perf_counter() - t0
+    return {"value": sim.N * steps / el, "unit": "node-steps/s", "h2d_bytes_per_step": nb,
+            "d2h_bytes_per_step": 2 * 8 * sim.N}
+
+
+def run_ours(args) -> None:
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        import __graft_entry__ as g
+        g.build()
+    if dist:
+        dist.barrier()
+    from paper_2510_27447_gb300 import binding
+    stream = torch.cuda.Stream()
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    results = {}
+    profiles = {}
+    for name, prec in (("mixed", binding.MIXED), ("fp64", binding.FP64)):
+        with torch.cuda.stream(stream):
+            sim, w = make_sim(prec, stream.cuda_stream)
+            for _ in range(args.warmup):
+                sim.step(DT, M_NODES, K_SWEEPS)
+            sim.sync()
+            st0 = sim.stats()
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            with ClockSampler(local) as clk:
+                ms = time_steps(sim, torch, stream, flush, args.steps)
+            torch.cuda.synchronize()
+            sim.sync()
+            st1 = sim.stats()
+            total = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
+            if dist:
+                dist.all_reduce(total, op=dist.ReduceOp.MAX)
+            total_ms = float(total.item())
+            results[name] = {"ms_per_step": total_ms / args.steps,
+                             "value": world * sim.N * args.steps / (total_ms / 1e3),
+                             "clocks": clk.summary(),
+                             "launches": st1["kernel_launches"] - st0["kernel_launches"],
+                             "cg_iters_e": (st1["cg_iters_e"] - st0["cg_iters_e"]) / max(1, st1["cg_solves_e"] - st0["cg_solves_e"]),
+                             "cg_iters_p": (st1["cg_iters_p"] - st0["cg_iters_p"]) / max(1, st1["cg_solves_p"] - st0["cg_solves_p"])}
+            profiles[name] = sim.profile_steps(DT, M_NODES, K_SWEEPS, args.steps)
+            if name == "mixed":
+                results[name]["e2e"] = e2e_rate(sim, torch, max(3, args.steps // 2))
+            sim.close()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    prof = profiles["mixed"]
+    dom = max(prof["ms"], key=lambda k: prof["ms"][k])
+    peaks = measured_peaks()
+    n, nnz = results and 0, prof["nnz"]
+    n = SIDE * SIDE
+    roof = None
+    if dom in ("pcg_elliptic", "pcg_parabolic"):
+        idx = 0 if dom == "pcg_elliptic" else 1
+        launches = prof["launches"][dom]
+        byt = pcg_bytes(prof["cg_iters"][idx], prof["cg_solves"][idx], n, nnz, idx == 1) / launches
+        avg_s = prof["ms"][dom] / launches / 1e3
+        achieved = byt / avg_s / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": load_traffic(dom),
+                "algorithmic_bytes_per_launch": round(byt), "avg_launch_ms": round(avg_s * 1e3, 4),
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+    share = {k: round(v / sum(prof["ms"].values()), 4) for k, v in prof["ms"].items()}
+
+    base = None
+    if world == 1 and not args.no_baseline:
+        try:
+            res = run_oracle_subprocess(0, 1, 15.0)
+            base = {"value": round(res["value"], 2), "unit": "node-steps/s", "cores": 1, "kind": "oracle",
+                    "sample": sample_text(res)}
+        except Exception as e:  # noqa: BLE001
+            base = {"value": None, "unit": "node-steps/s", "cores": 1, "kind": "oracle",
+                    "sample": f"failed: {e}"[:200]}
+
+    mixed = results["mixed"]
+    line = {
+        "metric": "node-steps/s",
+        "value": round(mixed["value"], 1),
+        "unit": "node-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(mixed["ms_per_step"], 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "mixed: f32 membrane model, f64 solves and state",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": n, "model": "TP06 epicardial", "dt_ms": DT,
+                   "sdc_nodes": M_NODES, "sweeps": K_SWEEPS, "start": "rest + S1 at t=0",
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
+        "fp64": {"value": round(results["fp64"]["value"], 1),
+                 "ms_per_step": round(results["fp64"]["ms_per_step"], 4), "dtype": "f64"},
+        "e2e": {k: (round(v, 1) if isinstance(v, float) else v) for k, v in mixed["e2e"].items()},
+        "gpu_launches": int(mixed["launches"]),
+        "clocks": mixed["clocks"],
+        "roofline": roof,
+        "kernel_share": share,
+        "cg_iters_per_solve": {"elliptic": round(mixed["cg_iters_e"], 1), "parabolic": round(mixed["cg_iters_p"], 1)},
+        "cpu_baseline": base,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = run_oracle_subprocess(args.warmup, args.steps, 0.0)
+    val = round(res["value"], 3)
+    line = {"impl": "reference", "metric": "node-steps/s", "value": val, "unit": "node-steps/s",
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": res["steps"], "warmup": args.warmup,
+            "ms_per_step": round(1e3 * res["seconds"] / res["steps"], 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_nodes": res["nodes"], "model": "TP06 epicardial",
+                       "dt_ms": DT, "sdc_nodes": M_NODES, "sweeps": K_SWEEPS},
+            "cpu_baseline": {"value": val, "unit": "node-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample_text(res)},
+            "e2e": {"value": val, "unit": "node-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--seconds", type=float, default=0.0, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.oracle_sample:
+        import numpy as np
+        np.seterr(all="ignore")
+        print(json.dumps(oracle_rate(args.warmup, args.steps, args.seconds)))
+        return
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

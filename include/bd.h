@@ -114,7 +114,26 @@ typedef struct {
   int64_t cg_solves_p;
   int64_t spd_clamps;      /* nodes whose condensed diagonal was raised */
   int64_t ionic_evals;     /* node-block evaluations (kernel launches x nodes / nodes) */
+  int64_t kernel_launches; /* device kernels launched by the steps */
 } bd_stats_t;
+
+/* Per-kind device time of profiled steps (bd_profile_steps). */
+enum {
+  BD_K_PCG_ELLIPTIC = 0,   /* persistent PCG, elliptic constraint (A2) */
+  BD_K_PCG_PARABOLIC = 1,  /* persistent PCG, condensed parabolic systems (A5, A9) */
+  BD_K_IONIC = 2,          /* node-wise model + Jacobian + condensation (A4, A6, A8) */
+  BD_K_FIELD = 3,          /* node field only (quadrature values, A8) */
+  BD_K_COMBINE = 4,        /* ROS2 combination / correction update / copies (A7, A9) */
+  BD_K_FINISH = 5,         /* activation times and state rotation (A10) */
+  BD_K_COUNT = 6
+};
+typedef struct {
+  double ms[BD_K_COUNT];        /* summed kernel durations (CUDA events on the handle's stream) */
+  int64_t launches[BD_K_COUNT];
+  int64_t cg_iters[2];          /* elliptic, parabolic CG iterations in the profiled steps */
+  int64_t cg_solves[2];
+  int64_t nnz;                  /* nonzeros of the shared operator pattern */
+} bd_profile_t;
 
 void bd_default_options(bd_opts_t* opts);
 
@@ -171,6 +190,12 @@ int bd_set_state(bd_state_t* s, const void* buf, size_t bytes);
 size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts_t* opts);
 
 int bd_get_stats(const bd_state_t* s, bd_stats_t* out);
+
+/* Run n_steps steps without graph replay, with a CUDA event pair recorded on
+ * the handle's stream around every kernel launch, and return the per-kind
+ * device times.  The steps advance the simulation like bd_step. */
+int bd_profile_steps(bd_state_t* s, double dt_ms, int n_sdc_nodes, int n_sweeps, int n_steps,
+                     bd_profile_t* out);
 int bd_reset_stats(bd_state_t* s);
 int64_t bd_num_nodes(const bd_state_t* s);
 int bd_num_states(bd_ionic_t model);

@@ -25,7 +25,7 @@ EXPORTS = ["bd_default_options", "bd_create", "bd_add_stimulus", "bd_set_initial
            "bd_device_fields", "bd_get_state", "bd_set_state", "bd_footprint_bytes", "bd_get_stats",
            "bd_reset_stats", "bd_num_nodes", "bd_num_states", "bd_last_error", "bd_destroy",
            "bd_ionic_eval", "bd_ionic_pattern", "bd_rest_state", "bd_operator_csr",
-           "bd_solve_elliptic"]
+           "bd_solve_elliptic", "bd_profile_steps"]
 
 
 class LibraryMissing(RuntimeError):
@@ -64,7 +64,16 @@ class Opts(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("steps", "sweeps", "cg_iters_e", "cg_solves_e",
-                                          "cg_iters_p", "cg_solves_p", "spd_clamps", "ionic_evals")]
+                                          "cg_iters_p", "cg_solves_p", "spd_clamps", "ionic_evals",
+                                          "kernel_launches")]
+
+
+KERNEL_KINDS = ("pcg_elliptic", "pcg_parabolic", "ionic", "field", "combine", "finish")
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 6), ("launches", C.c_int64 * 6), ("cg_iters", C.c_int64 * 2),
+                ("cg_solves", C.c_int64 * 2), ("nnz", C.c_int64)]
 
 
 _lib = None
@@ -106,6 +115,7 @@ def lib():
         "bd_rest_state": (C.c_int, [C.c_int, dp]),
         "bd_operator_csr": (C.c_int, [C.c_void_p, C.c_int, P(C.c_int64), ip, ip, dp]),
         "bd_solve_elliptic": (C.c_int, [C.c_void_p, dp, dp, dp, P(C.c_int)]),
+        "bd_profile_steps": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_int, P(Profile)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -258,6 +268,15 @@ class Simulation:
         s = Stats()
         _check(lib().bd_get_stats(self.h, C.byref(s)), self.h)
         return {k: int(getattr(s, k)) for k, _ in Stats._fields_}
+
+    def profile_steps(self, dt: float, n_sdc_nodes: int, n_sweeps: int, n_steps: int) -> dict:
+        p = Profile()
+        _check(lib().bd_profile_steps(self.h, float(dt), int(n_sdc_nodes), int(n_sweeps),
+                                      int(n_steps), C.byref(p)), self.h)
+        return {"ms": dict(zip(KERNEL_KINDS, list(p.ms))),
+                "launches": dict(zip(KERNEL_KINDS, [int(x) for x in p.launches])),
+                "cg_iters": [int(p.cg_iters[0]), int(p.cg_iters[1])],
+                "cg_solves": [int(p.cg_solves[0]), int(p.cg_solves[1])], "nnz": int(p.nnz)}
 
     def reset_stats(self):
         _check(lib().bd_reset_stats(self.h), self.h)

@@ -66,7 +66,14 @@ struct bd_state {
   int pcg_grid = 1, pcg_block = 256, pcg_max = 1;
   std::vector<void*> allocs;
   std::string err;
-  int64_t steps = 0, sweeps = 0, ionic_evals = 0;
+  int64_t steps = 0, sweeps = 0, ionic_evals = 0, launches = 0;
+  int64_t launches_per_step = 0;
+  // profiling: an event pair per launch while prof is set
+  struct Ev { int kind; cudaEvent_t a, b; };
+  bool prof = false;
+  std::vector<Ev> evpool;
+  size_t evused = 0;
+  int64_t enq_launches = 0;
 };
 
 namespace {
@@ -111,6 +118,11 @@ bool alloc_n(bd_state* s, T** out, int64_t count) {
 }
 
 void release(bd_state* s) {
+  for (auto& e : s->evpool) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  s->evpool.clear();
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   s->gexec = nullptr;
   for (void* p : s->allocs) {
@@ -121,6 +133,30 @@ void release(bd_state* s) {
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   s->stream = nullptr;
 }
+
+// brackets one launch with an event pair while profiling; counts launches
+struct Timed {
+  bd_state* s;
+  int kind;
+  int nlaunch;
+  size_t slot;
+  Timed(bd_state* st, int k, int nl = 1) : s(st), kind(k), nlaunch(nl), slot(0) {
+    s->enq_launches += nl;
+    if (!s->prof) return;
+    if (s->evused == s->evpool.size()) {
+      bd_state::Ev e{k, nullptr, nullptr};
+      cudaEventCreate(&e.a);
+      cudaEventCreate(&e.b);
+      s->evpool.push_back(e);
+    }
+    slot = s->evused++;
+    s->evpool[slot].kind = k;
+    cudaEventRecord(s->evpool[slot].a, s->stream);
+  }
+  ~Timed() {
+    if (s->prof) cudaEventRecord(s->evpool[slot].b, s->stream);
+  }
+};
 
 int status_code(int st) {
   if (st & ST_TIMEOUT) return BD_ERR_TIMEOUT;
@@ -189,6 +225,7 @@ int elliptic(bd_state* s, const double* v, double* u) {
   P.pin = s->opts.pin_node >= 0 ? s->opts.pin_node : -1;
   P.iters_acc = s->d_stats + 0;
   P.solves_acc = s->d_stats + 1;
+  Timed t(s, BD_K_PCG_ELLIPTIC);
   CK(launch_pcg(P, s->stream));
   return BD_OK;
 }
@@ -215,6 +252,7 @@ int parabolic(bd_state* s, const double* pvals, double c1, const double* va, dou
   P.pin = -2;
   P.iters_acc = s->d_stats + 2;
   P.solves_acc = s->d_stats + 3;
+  Timed t(s, BD_K_PCG_PARABOLIC);
   CK(launch_pcg(P, s->stream));
   return BD_OK;
 }
@@ -280,12 +318,18 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
   lobatto(M, c);
   integration_matrix(M, S);
   StimTable st = s->stim;
-  CK(launch_field(s->model, s->precision, N, s->Xn, s->inv_cm, dt, s->stim_bits, s->step_n, st, s->fq[0], s->stream));
+  {
+    Timed t(s, BD_K_FIELD);
+    CK(launch_field(s->model, s->precision, N, s->Xn, s->inv_cm, dt, s->stim_bits, s->step_n, st, s->fq[0], s->stream));
+  }
   for (int k = 1; k <= K; ++k) {
     // ---- elliptic constraint at the nodes m >= 1 ----
     if (k == 1) {
       RUN(elliptic(s, s->Xn, s->u[M - 1]));
-      for (int m = 1; m + 1 < M; ++m) CK(launch_copy(N, s->u[M - 1], s->u[m], s->stream));
+      for (int m = 1; m + 1 < M; ++m) {
+        Timed t(s, BD_K_COMBINE);
+        CK(launch_copy(N, s->u[M - 1], s->u[m], s->stream));
+      }
     } else {
       for (int m = 1; m < M; ++m) RUN(elliptic(s, s->Xc[m], s->u[m]));
     }
@@ -303,7 +347,10 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       L.z = s->z1;
       L.w = s->w1;
       L.fq_out = (m >= 1 && s->opts.sdc_correction) ? s->fq[m] : nullptr;
-      CK(launch_ionic(L, s->stream));
+      {
+        Timed t(s, BD_K_IONIC);
+        CK(launch_ionic(L, s->stream));
+      }
       RUN(parabolic(s, pv, -1.0, s->avec, 0.0, nullptr, s->k1v));
       IonicLaunch L2 = ionic_base(s, MODE_S2, dt);
       L2.alpha = alpha;
@@ -318,16 +365,25 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       L2.z = s->z2;
       L2.w = s->w2;
       L2.bvec = s->bvec;
-      CK(launch_ionic(L2, s->stream));
+      {
+        Timed t(s, BD_K_IONIC);
+        CK(launch_ionic(L2, s->stream));
+      }
       RUN(parabolic(s, pv, -1.0, s->avec, -L2.ck1, s->bvec, s->k2v));
-      CK(launch_combine(s->model, N, src, s->k1v, s->z1, s->w1, s->k2v, s->z2, s->w2, 1.5 / gam, 0.5 / gam,
-                        s->Xt[m + 1], s->stream));
+      {
+        Timed t(s, BD_K_COMBINE);
+        CK(launch_combine(s->model, N, src, s->k1v, s->z1, s->w1, s->k2v, s->z2, s->w2, 1.5 / gam, 0.5 / gam,
+                          s->Xt[m + 1], s->stream));
+      }
       s->ionic_evals += 3;
     }
     // ---- SDC correction ----
     if (s->opts.sdc_correction) {
-      CK(launch_field(s->model, s->precision, N, s->Xt[M - 1], s->inv_cm, dt, s->stim_bits, s->step_n, st,
-                      s->fq[M - 1], s->stream));
+      {
+        Timed t(s, BD_K_FIELD);
+        CK(launch_field(s->model, s->precision, N, s->Xt[M - 1], s->inv_cm, dt, s->stim_bits, s->step_n, st,
+                        s->fq[M - 1], s->stream));
+      }
       s->ionic_evals += 1;
       for (int m = 0; m + 1 < M; ++m) {
         const double h = dt * (c[m + 1] - c[m]);
@@ -349,24 +405,38 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
         L.z = s->z1;
         L.w = s->w1;
         L.bvec = s->bvec;
-        CK(launch_ionic(L, s->stream));
+        {
+          Timed t(s, BD_K_IONIC);
+          CK(launch_ionic(L, s->stream));
+        }
         RUN(parabolic(s, pv, -1.0 / h, s->avec, 1.0 / h, s->bvec, s->k1v));
-        CK(launch_update(s->model, N, s->Xt[m + 1], s->k1v, s->z1, s->w1, s->Xc[m + 1], s->stream));
+        {
+          Timed t(s, BD_K_COMBINE);
+          CK(launch_update(s->model, N, s->Xt[m + 1], s->k1v, s->z1, s->w1, s->Xc[m + 1], s->stream));
+        }
         s->ionic_evals += 1;
       }
     } else {
-      for (int m = 1; m < M; ++m) CK(launch_copy(int64_t(ns) * N, s->Xt[m], s->Xc[m], s->stream));
+      for (int m = 1; m < M; ++m) {
+        Timed t(s, BD_K_COMBINE);
+        CK(launch_copy(int64_t(ns) * N, s->Xt[m], s->Xc[m], s->stream));
+      }
     }
   }
-  CK(launch_finish(ns, N, s->Xn, s->Xc[M - 1], s->u[0], s->u[M - 1], s->t_act, s->opts.v_act_mV, dt, s->step_n,
-                   s->d_status, s->stream));
+  {
+    Timed t(s, BD_K_FINISH, 2);
+    CK(launch_finish(ns, N, s->Xn, s->Xc[M - 1], s->u[0], s->u[M - 1], s->t_act, s->opts.v_act_mV, dt,
+                     s->step_n, s->d_status, s->stream));
+  }
   return BD_OK;
 }
 
 int do_step(bd_state* s, double dt, int M, int K) {
   RUN(prepare_step(s, dt, M));
-  if (!s->opts.use_graph) {
+  if (!s->opts.use_graph || s->prof) {
+    s->enq_launches = 0;
     RUN(enqueue_step(s, dt, M, K));
+    s->launches += s->enq_launches;
   } else {
     if (!s->gexec || s->g_dt != dt || s->g_M != M || s->g_K != K) {
       if (s->gexec) {
@@ -375,8 +445,10 @@ int do_step(bd_state* s, double dt, int M, int K) {
       }
       cudaGraph_t g = nullptr;
       const int64_t ev0 = s->ionic_evals;
+      s->enq_launches = 0;
       CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
       const int r = enqueue_step(s, dt, M, K);
+      s->launches_per_step = s->enq_launches;
       cudaError_t e = cudaStreamEndCapture(s->stream, &g);
       if (r != BD_OK) {
         if (g) cudaGraphDestroy(g);
@@ -392,6 +464,7 @@ int do_step(bd_state* s, double dt, int M, int K) {
       s->ionic_evals = ev0;   // counted per replay below
     }
     CK(cudaGraphLaunch(s->gexec, s->stream));
+    s->launches += s->launches_per_step;
     s->ionic_evals += int64_t(K) * (3 * (M - 1) + (s->opts.sdc_correction ? M : 0)) + 1;
   }
   s->steps += 1;
@@ -715,7 +788,44 @@ int bd_get_stats(const bd_state_t* cs, bd_stats_t* out) {
   out->cg_solves_p = st[3];
   out->spd_clamps = int64_t(cl);
   out->ionic_evals = s->ionic_evals;
+  out->kernel_launches = s->launches;
   return BD_OK;
+}
+
+int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_profile_t* out) {
+  if (!s || !out || n_steps < 0) return fail(s, BD_ERR_ARG, "bad arguments");
+  if (!(dt > 0) || (M != 2 && M != 3) || K < 1) return fail(s, BD_ERR_ARG, "bad step shape");
+  std::memset(out, 0, sizeof(*out));
+  out->nnz = s->nnz;
+  long long st0[4], st1[4];
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaMemcpy(st0, s->d_stats, 32, cudaMemcpyDeviceToHost));
+  s->prof = true;
+  int rc = BD_OK;
+  for (int n = 0; n < n_steps && rc == BD_OK; ++n) {
+    s->evused = 0;
+    rc = do_step(s, dt, M, K);
+    if (rc != BD_OK) break;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
+      rc = fail(s, BD_ERR_CUDA, "profiled step failed");
+      break;
+    }
+    for (size_t e = 0; e < s->evused; ++e) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, s->evpool[e].a, s->evpool[e].b);
+      out->ms[s->evpool[e].kind] += ms;
+      out->launches[s->evpool[e].kind] += 1;
+    }
+    out->launches[BD_K_FINISH] += 1;   // the step-counter launch shares the finish bracket
+  }
+  s->prof = false;
+  if (rc != BD_OK) return rc;
+  CK(cudaMemcpy(st1, s->d_stats, 32, cudaMemcpyDeviceToHost));
+  out->cg_iters[0] = st1[0] - st0[0];
+  out->cg_solves[0] = st1[1] - st0[1];
+  out->cg_iters[1] = st1[2] - st0[2];
+  out->cg_solves[1] = st1[3] - st0[3];
+  return read_status(s);
 }
 
 int bd_reset_stats(bd_state_t* s) {
@@ -723,7 +833,7 @@ int bd_reset_stats(bd_state_t* s) {
   CK(cudaStreamSynchronize(s->stream));
   CK(cudaMemset(s->d_stats, 0, 32));
   CK(cudaMemset(s->d_clamps, 0, 8));
-  s->steps = s->sweeps = s->ionic_evals = 0;
+  s->steps = s->sweeps = s->ionic_evals = s->launches = 0;
   return BD_OK;
 }
 
