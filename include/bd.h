@@ -95,6 +95,8 @@ typedef struct {
   double v_act_mV;       /* activation threshold (default -30) */
   double spd_margin;     /* condensed-diagonal safeguard factor (default 0.9, 0 disables) */
   int use_graph;         /* 1: capture each step shape into a CUDA graph and replay it (default 1) */
+  int cg_block;          /* CG threads per block (0 = auto: 256) */
+  int cg_grid;           /* CG blocks (0 = auto: one per 256 rows, at most the co-resident maximum) */
   /* device memory hooks (NULL => cudaMalloc/cudaFree); ctx is passed back */
   void* (*alloc)(size_t bytes, void* ctx);
   void (*free)(void* ptr, void* ctx);

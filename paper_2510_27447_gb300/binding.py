@@ -58,6 +58,7 @@ class Opts(C.Structure):
                 ("sdc_correction", C.c_int), ("cg_tol_e", C.c_double), ("cg_tol_p", C.c_double),
                 ("cg_cap_e", C.c_int), ("cg_cap_p", C.c_int), ("sweep_tol", C.c_double),
                 ("v_act_mV", C.c_double), ("spd_margin", C.c_double), ("use_graph", C.c_int),
+                ("cg_block", C.c_int), ("cg_grid", C.c_int),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("stream", C.c_void_p)]
 

@@ -568,14 +568,19 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   for (int m = 0; ok && m < kMaxNodes; ++m)
     ok = alloc_n(s, &s->Xt[m], ns * N) && alloc_n(s, &s->Xc[m], ns * N) && alloc_n(s, &s->fq[m], ns * N) &&
          alloc_n(s, &s->u[m], N);
-  s->pcg_block = 256;
+  s->pcg_block = s->opts.cg_block > 0 ? s->opts.cg_block : 256;
+  if (s->pcg_block % 32 != 0 || s->pcg_block > 1024) {
+    release(s);
+    delete s;
+    return fail(nullptr, BD_ERR_ARG, "cg_block must be a multiple of 32 up to 1024");
+  }
   s->pcg_max = pcg_max_blocks(s->pcg_block);
   if (ok && s->pcg_max <= 0) {
     release(s);
     delete s;
     return fail(nullptr, BD_ERR_CUDA, "cannot size the cooperative CG grid");
   }
-  const int64_t want = (N + s->pcg_block - 1) / s->pcg_block;
+  const int64_t want = s->opts.cg_grid > 0 ? s->opts.cg_grid : (N + s->pcg_block - 1) / s->pcg_block;
   s->pcg_grid = int(std::max<int64_t>(1, std::min<int64_t>(want, s->pcg_max)));
   if (ok) ok = alloc_n(s, &s->cg_part, int64_t(s->pcg_max) * 4);
   if (!ok) {

@@ -28,7 +28,10 @@ namespace bd {
 
 namespace {
 
-constexpr long long kSpinLimit = 1ll << 24;   // ~2 s of 128 ns sleeps
+#ifndef BD_PCG_SLEEP_NS
+#define BD_PCG_SLEEP_NS 0
+#endif
+constexpr long long kSpinLimit = 1ll << 26;   // bounded wait: about a second of polling
 
 // sense-free generation barrier: bar[0] = arrivals, bar[1] = generation
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
@@ -47,7 +50,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
     } else {
       long long spins = 0;
       while (*gen == g0) {
-        __nanosleep(128);
+        if (BD_PCG_SLEEP_NS > 0) __nanosleep(BD_PCG_SLEEP_NS);
         if (++spins > kSpinLimit) {
           atomicOr(status, ST_TIMEOUT);
           ok = 0;
@@ -107,7 +110,7 @@ __device__ __forceinline__ void grid_total(const double* part, const int (&slot)
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) pcg_kernel(const PcgLaunch a) {
+__global__ void __launch_bounds__(1024) pcg_kernel(const PcgLaunch a) {
   __shared__ double sh[4][32];
   const int n = a.n;
   const int nb = gridDim.x;
