@@ -18,6 +18,7 @@
 // replayed.  The device is touched by the host only at create/set/get calls.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -40,9 +41,13 @@ struct bd_state {
   int64_t N = 0, nnz = 0;
   bd_opts_t opts{};
   double inv_cm = 1.0, lambda_M = 0.25;
-  int* rowptr = nullptr;
+  int64_t* sptr = nullptr;      // SELL-32 layout of the shared operator pattern
+  int* swidth = nullptr;
   int* col = nullptr;
   int* diagpos = nullptr;
+  int64_t ell_n = 0;
+  int wmax = 0;
+  HostOps host;                   // CSR copies (bd_operator_csr)
   double *Ai = nullptr, *Aie = nullptr, *Mv = nullptr, *Mc = nullptr, *ML = nullptr;
   struct PC { double alpha; double* val; };
   std::vector<PC> pcache;
@@ -186,8 +191,8 @@ double* p_values(bd_state* s, double alpha) {
   for (auto& pc : s->pcache)
     if (pc.alpha == alpha) return pc.val;
   double* v = nullptr;
-  if (!alloc_n(s, &v, s->nnz)) return nullptr;
-  if (launch_axpby_vals(s->nnz, alpha, s->Mv, 1.0, s->Ai, v, s->stream) != cudaSuccess) return nullptr;
+  if (!alloc_n(s, &v, s->ell_n)) return nullptr;
+  if (launch_axpby_vals(s->ell_n, alpha, s->Mv, 1.0, s->Ai, v, s->stream) != cudaSuccess) return nullptr;
   s->pcache.push_back({alpha, v});
   return v;
 }
@@ -195,7 +200,8 @@ double* p_values(bd_state* s, double alpha) {
 PcgLaunch pcg_base(bd_state* s) {
   PcgLaunch P{};
   P.n = int(s->N);
-  P.rowptr = s->rowptr;
+  P.sptr = s->sptr;
+  P.swidth = s->swidth;
   P.col = s->col;
   P.diagpos = s->diagpos;
   P.r = s->cg_r;
@@ -226,7 +232,7 @@ int elliptic(bd_state* s, const double* v, double* u) {
   P.iters_acc = s->d_stats + 0;
   P.solves_acc = s->d_stats + 1;
   Timed t(s, BD_K_PCG_ELLIPTIC);
-  CK(launch_pcg(P, s->stream));
+  CK(launch_pcg(P, s->wmax, s->stream));
   return BD_OK;
 }
 
@@ -253,7 +259,7 @@ int parabolic(bd_state* s, const double* pvals, double c1, const double* va, dou
   P.iters_acc = s->d_stats + 2;
   P.solves_acc = s->d_stats + 3;
   Timed t(s, BD_K_PCG_PARABOLIC);
-  CK(launch_pcg(P, s->stream));
+  CK(launch_pcg(P, s->wmax, s->stream));
   return BD_OK;
 }
 
@@ -542,6 +548,44 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     return fail(nullptr, rc, "%s", err.c_str());
   }
   s->nnz = H.rowptr[s->N];
+  // SELL-32 layout of the shared pattern
+  const int64_t nsl = (s->N + 31) / 32;
+  std::vector<int64_t> h_sptr(nsl);
+  std::vector<int> h_sw(nsl);
+  int maxw = 0;
+  {
+    int64_t off = 0;
+    for (int64_t sl = 0; sl < nsl; ++sl) {
+      int w = 0;
+      for (int64_t i = sl * 32; i < std::min<int64_t>(s->N, sl * 32 + 32); ++i)
+        w = std::max(w, H.rowptr[i + 1] - H.rowptr[i]);
+      h_sw[sl] = w;
+      h_sptr[sl] = off;
+      off += 32 * int64_t(w);
+      maxw = std::max(maxw, w);
+    }
+    s->ell_n = off;
+  }
+  s->wmax = maxw <= 8 ? 8 : maxw <= 16 ? 16 : maxw <= 32 ? 32 : 0;
+  std::vector<int> e_col(s->ell_n, 0), e_diag(s->N);
+  auto to_ell = [&](const std::vector<double>& v) {
+    std::vector<double> e(s->ell_n, 0.0);
+    for (int64_t i = 0; i < s->N; ++i) {
+      const int64_t base = h_sptr[i / 32] + (i % 32);
+      for (int k = 0; k < H.rowptr[i + 1] - H.rowptr[i]; ++k) e[base + 32 * k] = v[H.rowptr[i] + k];
+    }
+    return e;
+  };
+  for (int64_t i = 0; i < s->N; ++i) {
+    const int64_t base = h_sptr[i / 32] + (i % 32);
+    const int len = H.rowptr[i + 1] - H.rowptr[i];
+    for (int k = 0; k < h_sw[i / 32]; ++k) e_col[base + 32 * k] = k < len ? H.col[H.rowptr[i] + k] : int(i);
+    e_diag[i] = int(base + 32 * int64_t(H.diagpos[i] - H.rowptr[i]));
+  }
+  if (s->ell_n > int64_t(0x7fffffff)) {
+    delete s;
+    return fail(nullptr, BD_ERR_ARG, "operator too large for 32-bit SELL offsets");
+  }
 
   if (s->opts.stream) {
     s->stream = static_cast<cudaStream_t>(s->opts.stream);
@@ -554,9 +598,10 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     s->own_stream = true;
   }
   const int64_t N = s->N, nnz = s->nnz, ns = s->ns;
-  bool ok = alloc_n(s, &s->rowptr, N + 1) && alloc_n(s, &s->col, nnz) && alloc_n(s, &s->diagpos, N) &&
-            alloc_n(s, &s->Ai, nnz) && alloc_n(s, &s->Aie, nnz) && alloc_n(s, &s->Mc, nnz) &&
-            alloc_n(s, &s->Mv, nnz) && alloc_n(s, &s->ML, N) && alloc_n(s, &s->Xn, ns * N) &&
+  const int64_t en = s->ell_n;
+  bool ok = alloc_n(s, &s->sptr, nsl) && alloc_n(s, &s->swidth, nsl) && alloc_n(s, &s->col, en) &&
+            alloc_n(s, &s->diagpos, N) && alloc_n(s, &s->Ai, en) && alloc_n(s, &s->Aie, en) &&
+            alloc_n(s, &s->Mc, en) && alloc_n(s, &s->Mv, en) && alloc_n(s, &s->ML, N) && alloc_n(s, &s->Xn, ns * N) &&
             alloc_n(s, &s->dgs, N) && alloc_n(s, &s->rl, N) && alloc_n(s, &s->z1, (ns - 1) * N) &&
             alloc_n(s, &s->w1, (ns - 1) * N) && alloc_n(s, &s->z2, (ns - 1) * N) &&
             alloc_n(s, &s->w2, (ns - 1) * N) && alloc_n(s, &s->k1v, N) && alloc_n(s, &s->k2v, N) &&
@@ -574,7 +619,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     delete s;
     return fail(nullptr, BD_ERR_ARG, "cg_block must be a multiple of 32 up to 1024");
   }
-  s->pcg_max = pcg_max_blocks(s->pcg_block);
+  s->pcg_max = pcg_max_blocks(s->pcg_block, s->wmax);
   if (ok && s->pcg_max <= 0) {
     release(s);
     delete s;
@@ -590,15 +635,18 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   }
   std::vector<double> Mlump(nnz, 0.0);
   for (int64_t i = 0; i < N; ++i) Mlump[H.diagpos[i]] = H.ML[i];
+  const std::vector<double> eAi = to_ell(H.Ai), eAie = to_ell(H.Aie), eM = to_ell(H.M),
+                            eMv = s->opts.mass_lumped ? to_ell(Mlump) : eM;
   auto up = [&](void* d, const void* h, size_t b) { return cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, s->stream); };
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = up(s->rowptr, H.rowptr.data(), (N + 1) * 4);
-  if (e == cudaSuccess) e = up(s->col, H.col.data(), nnz * 4);
-  if (e == cudaSuccess) e = up(s->diagpos, H.diagpos.data(), N * 4);
-  if (e == cudaSuccess) e = up(s->Ai, H.Ai.data(), nnz * 8);
-  if (e == cudaSuccess) e = up(s->Aie, H.Aie.data(), nnz * 8);
-  if (e == cudaSuccess) e = up(s->Mc, H.M.data(), nnz * 8);
-  if (e == cudaSuccess) e = up(s->Mv, s->opts.mass_lumped ? Mlump.data() : H.M.data(), nnz * 8);
+  if (e == cudaSuccess) e = up(s->sptr, h_sptr.data(), nsl * 8);
+  if (e == cudaSuccess) e = up(s->swidth, h_sw.data(), nsl * 4);
+  if (e == cudaSuccess) e = up(s->col, e_col.data(), en * 4);
+  if (e == cudaSuccess) e = up(s->diagpos, e_diag.data(), N * 4);
+  if (e == cudaSuccess) e = up(s->Ai, eAi.data(), en * 8);
+  if (e == cudaSuccess) e = up(s->Aie, eAie.data(), en * 8);
+  if (e == cudaSuccess) e = up(s->Mc, eM.data(), en * 8);
+  if (e == cudaSuccess) e = up(s->Mv, eMv.data(), en * 8);
   if (e == cudaSuccess) e = up(s->ML, H.ML.data(), N * 8);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->stim_bits, 0, N * 4, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->bar, 0, 8, s->stream);
@@ -612,6 +660,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     delete s;
     return fail(nullptr, BD_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
   }
+  s->host = std::move(H);
   // resting initial state
   std::vector<double> x0(ns), X(ns * N);
   rest_state_host(s->model, x0.data());
@@ -898,16 +947,16 @@ int bd_operator_csr(const bd_state_t* cs, int which, int64_t* nnz, int32_t* rowp
   if (!s || !nnz || which < 0 || which > 3) return fail(s, BD_ERR_ARG, "bad arguments");
   *nnz = which == 3 ? s->N : s->nnz;
   if (!val) return BD_OK;   // size query
-  CK(cudaStreamSynchronize(s->stream));
+  const HostOps& H = s->host;
   if (which == 3) {
-    CK(cudaMemcpy(val, s->ML, s->N * 8, cudaMemcpyDeviceToHost));
+    std::memcpy(val, H.ML.data(), s->N * 8);
     return BD_OK;
   }
   if (!rowptr || !col) return fail(s, BD_ERR_ARG, "rowptr/col is NULL");
-  const double* src = which == 0 ? s->Ai : which == 1 ? s->Aie : s->Mc;
-  CK(cudaMemcpy(rowptr, s->rowptr, (s->N + 1) * 4, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(col, s->col, s->nnz * 4, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(val, src, s->nnz * 8, cudaMemcpyDeviceToHost));
+  const std::vector<double>& src = which == 0 ? H.Ai : which == 1 ? H.Aie : H.M;
+  std::memcpy(rowptr, H.rowptr.data(), (s->N + 1) * 4);
+  std::memcpy(col, H.col.data(), s->nnz * 4);
+  std::memcpy(val, src.data(), s->nnz * 8);
   return BD_OK;
 }
 

@@ -85,11 +85,18 @@ int model_ns(int model);
 void rest_state_host(int model, double* x);
 
 // sparse (pcg.cu)
+//
+// Operators are stored in sliced ELL ("SELL-32"): rows are grouped in slices
+// of 32 consecutive rows; slice s has width w_s = its longest row, and entry k
+// of row i = 32 s + l sits at sptr[s] + 32 k + l (column-major inside the
+// slice), so one warp reads 32 consecutive values per load.  Padding entries
+// carry value 0 and point at their own row.  All operators share one layout.
 struct PcgLaunch {
   int n;
-  const int* rowptr;
-  const int* col;
-  const int* diagpos;
+  const int64_t* sptr;      // slice offsets (n_slices)
+  const int* swidth;        // slice widths (n_slices)
+  const int* col;           // SELL column indices
+  const int* diagpos;       // SELL position of each row's diagonal
   const double* valA;
   const double* dextra;     // optional extra diagonal
   const double* rl;         // rhs = rl + c1 V1 a + c2 V2 b
@@ -119,8 +126,8 @@ struct PcgLaunch {
   int grid;                 // co-resident blocks
   int block;
 };
-cudaError_t launch_pcg(const PcgLaunch& P, cudaStream_t st);
-int pcg_max_blocks(int block);
+cudaError_t launch_pcg(const PcgLaunch& P, int wmax, cudaStream_t st);
+int pcg_max_blocks(int block, int wmax);
 cudaError_t launch_axpby_vals(int64_t nnz, double a, const double* X, double b, const double* Y, double* out,
                               cudaStream_t st);
 cudaError_t launch_copy(int64_t n, const double* src, double* dst, cudaStream_t st);

@@ -110,37 +110,57 @@ __device__ __forceinline__ void grid_total(const double* part, const int (&slot)
   __syncthreads();
 }
 
+// sum_k val[k] x[col[k]] over row i of a SELL-32 operator.  For WMAX > 0 the
+// loads are fully unrolled and predicated so a thread issues all its column
+// and value loads back to back (memory-level parallelism); WMAX = 0 loops.
+template <int WMAX, bool CROSS>
+__device__ __forceinline__ double sell_row(const PcgLaunch& a, const double* __restrict__ val,
+                                           const double* x, int i) {
+  const int s = i >> 5;
+  const int64_t base = a.sptr[s] + (i & 31);
+  const int w = a.swidth[s];
+  double acc = 0.0;
+  if constexpr (WMAX > 0) {
+    int c[WMAX];
+    double v[WMAX];
+#pragma unroll
+    for (int k = 0; k < WMAX; ++k)
+      if (k < w) {
+        c[k] = a.col[base + 32 * k];
+        v[k] = val[base + 32 * k];
+      }
+#pragma unroll
+    for (int k = 0; k < WMAX; ++k)
+      if (k < w) acc += v[k] * (CROSS ? __ldcg(x + c[k]) : x[c[k]]);
+  } else {
+    for (int k = 0; k < w; ++k) {
+      const int c = a.col[base + 32 * k];
+      acc += val[base + 32 * k] * (CROSS ? __ldcg(x + c) : x[c]);
+    }
+  }
+  return acc;
+}
+
+template <int WMAX>
 __global__ void __launch_bounds__(1024) pcg_kernel(const PcgLaunch a) {
   __shared__ double sh[4][32];
   const int n = a.n;
   const int nb = gridDim.x;
   const int stride = blockDim.x * gridDim.x;
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int* __restrict__ rp = a.rowptr;
-  const int* __restrict__ col = a.col;
 
   // ---- phase 0: right-hand side, initial residual --------------------------
   double acc0[2] = {0.0, 0.0};
   for (int i = i0; i < n; i += stride) {
     double b = a.rl ? a.rl[i] : 0.0;
-    const int k0 = rp[i], k1 = rp[i + 1];
-    if (a.val1) {
-      double s = 0.0;
-      for (int k = k0; k < k1; ++k) s += a.val1[k] * a.va[col[k]];
-      b += a.c1 * s;
-    }
-    if (a.val2) {
-      double s = 0.0;
-      for (int k = k0; k < k1; ++k) s += a.val2[k] * a.vb[col[k]];
-      b += a.c2 * s;
-    }
+    if (a.val1) b += a.c1 * sell_row<WMAX, false>(a, a.val1, a.va, i);
+    if (a.val2) b += a.c2 * sell_row<WMAX, false>(a, a.val2, a.vb, i);
     double d = a.valA[a.diagpos[i]];
     if (a.dextra) d += a.dextra[i];
     a.invd[i] = 1.0 / d;
     double r = b;
     if (a.warm) {
-      double ax = a.dextra ? a.dextra[i] * a.x[i] : 0.0;
-      for (int k = k0; k < k1; ++k) ax += a.valA[k] * a.x[col[k]];
+      const double ax = (a.dextra ? a.dextra[i] * a.x[i] : 0.0) + sell_row<WMAX, false>(a, a.valA, a.x, i);
       r -= ax;
     }
     a.r[i] = r;
@@ -192,8 +212,7 @@ __global__ void __launch_bounds__(1024) pcg_kernel(const PcgLaunch a) {
     for (int i = i0; i < n; i += stride) {
       const double z = a.z[i];
       double az = a.dextra ? a.dextra[i] * z : 0.0;
-      const int k0 = rp[i], k1 = rp[i + 1];
-      for (int k = k0; k < k1; ++k) az += a.valA[k] * __ldcg(a.z + col[k]);   // other blocks' z
+      az += sell_row<WMAX, true>(a, a.valA, a.z, i);   // reads other blocks' z through L2
       const double p = it == 0 ? z : z + beta * a.p[i];
       const double q = it == 0 ? az : az + beta * a.q[i];
       a.p[i] = p;
@@ -278,15 +297,27 @@ __global__ void copy_kernel(int64_t n, const double* src, double* dst) {
 
 }  // namespace
 
-int pcg_max_blocks(int block) {
+namespace {
+template <int W>
+int max_blocks_t(int block) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_kernel, block, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_kernel<W>, block, 0) != cudaSuccess) return 0;
   return sms * per;
 }
+}  // namespace
 
-cudaError_t launch_pcg(const PcgLaunch& P, cudaStream_t st) {
+int pcg_max_blocks(int block, int wmax) {
+  switch (wmax) {
+    case 8: return max_blocks_t<8>(block);
+    case 16: return max_blocks_t<16>(block);
+    case 32: return max_blocks_t<32>(block);
+    default: return max_blocks_t<0>(block);
+  }
+}
+
+cudaError_t launch_pcg(const PcgLaunch& P, int wmax, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(P.grid));
   cfg.blockDim = dim3(unsigned(P.block));
@@ -297,7 +328,12 @@ cudaError_t launch_pcg(const PcgLaunch& P, cudaStream_t st) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, pcg_kernel, P);
+  switch (wmax) {
+    case 8: return cudaLaunchKernelEx(&cfg, pcg_kernel<8>, P);
+    case 16: return cudaLaunchKernelEx(&cfg, pcg_kernel<16>, P);
+    case 32: return cudaLaunchKernelEx(&cfg, pcg_kernel<32>, P);
+    default: return cudaLaunchKernelEx(&cfg, pcg_kernel<0>, P);
+  }
 }
 
 cudaError_t launch_axpby_vals(int64_t n, double a, const double* X, double b, const double* Y, double* out,
