@@ -193,6 +193,32 @@ size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts
 
 int bd_get_stats(const bd_state_t* s, bd_stats_t* out);
 
+/* Allocation-free variant of bd_solve_elliptic for callers that must not
+ * allocate GPU memory during the call -- for example code running under an
+ * external memory budget or allocator, or a latency-critical loop that cannot
+ * afford cudaMalloc/cudaFree, which may synchronise the whole device.  The
+ * paper has no counterpart; this is a service of the library.
+ *
+ * Solves A_ie u = -A_i v with the handle's resident operators, precision and
+ * pin: v_dev (N doubles, device) is read, u_dev (N doubles, device) is
+ * written, u_guess_dev (device, N) warm-starts the iteration or is NULL for a
+ * zero start.  The call allocates nothing: the CG work vectors, partial sums,
+ * barrier words and status live in one file-scope __device__ array of the
+ * library sized for at most BD_NOALLOC_MAX_NODES nodes (about 5.4 MB, held
+ * by every GPU that loads the library until the process exits).  Larger
+ * meshes return BD_ERR_ARG.
+ *
+ * The first call on a device looks up that array's device address (with the
+ * handle's device current) and caches it, so the first call should come
+ * before any stream capture.  Every call shares the array: the words that must
+ * start at zero are cleared at the start of each call, and calls that overlap
+ * on the GPU (on different streams or handles) race with each other.  The call
+ * runs on the handle's stream and waits for it; *iters (if not NULL) receives
+ * the iteration count. */
+#define BD_NOALLOC_MAX_NODES 131072
+int bd_solve_elliptic_noalloc(bd_state_t* s, const double* v_dev, const double* u_guess_dev, double* u_dev,
+                              int* iters);
+
 /* Run n_steps steps without graph replay, with a CUDA event pair recorded on
  * the handle's stream around every kernel launch, and return the per-kind
  * device times.  The steps advance the simulation like bd_step. */

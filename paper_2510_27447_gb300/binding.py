@@ -25,7 +25,7 @@ EXPORTS = ["bd_default_options", "bd_create", "bd_add_stimulus", "bd_set_initial
            "bd_device_fields", "bd_get_state", "bd_set_state", "bd_footprint_bytes", "bd_get_stats",
            "bd_reset_stats", "bd_num_nodes", "bd_num_states", "bd_last_error", "bd_destroy",
            "bd_ionic_eval", "bd_ionic_pattern", "bd_rest_state", "bd_operator_csr",
-           "bd_solve_elliptic", "bd_profile_steps"]
+           "bd_solve_elliptic", "bd_profile_steps", "bd_solve_elliptic_noalloc"]
 
 
 class LibraryMissing(RuntimeError):
@@ -117,6 +117,7 @@ def lib():
         "bd_operator_csr": (C.c_int, [C.c_void_p, C.c_int, P(C.c_int64), ip, ip, dp]),
         "bd_solve_elliptic": (C.c_int, [C.c_void_p, dp, dp, dp, P(C.c_int)]),
         "bd_profile_steps": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_int, P(Profile)]),
+        "bd_solve_elliptic_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, P(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

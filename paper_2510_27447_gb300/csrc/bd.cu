@@ -23,6 +23,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -35,6 +36,19 @@ void pattern_host(int model, uint32_t* masks);
 }  // namespace bd
 
 using namespace bd;
+
+// ---------------------------------------------------------------------------
+// fixed scratch of bd_solve_elliptic_noalloc (see include/bd.h)
+// layout in doubles: r, z, p, q, 1/D (5 x max nodes), partial sums (4 x max
+// blocks), then 4 control words: barrier (2 x uint32), status (int32),
+// iteration counter (int64)
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int64_t kNoAllocRows = BD_NOALLOC_MAX_NODES;
+constexpr int64_t kNoAllocBlocks = 4096;
+constexpr int64_t kNoAllocWords = 5 * kNoAllocRows + 4 * kNoAllocBlocks + 4;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocWords];
+}  // namespace
 
 struct bd_state {
   int model = 0, ns = 0, dim = 0, precision = 0;
@@ -843,6 +857,68 @@ int bd_get_stats(const bd_state_t* cs, bd_stats_t* out) {
   out->spd_clamps = int64_t(cl);
   out->ionic_evals = s->ionic_evals;
   out->kernel_launches = s->launches;
+  return BD_OK;
+}
+
+int bd_solve_elliptic_noalloc(bd_state_t* s, const double* v_dev, const double* u_guess_dev, double* u_dev,
+                              int* iters) {
+  static std::mutex mu;
+  static double* addr[64] = {};
+  if (!s || !v_dev || !u_dev) return fail(s, BD_ERR_ARG, "NULL argument");
+  if (s->N > kNoAllocRows)
+    return fail(s, BD_ERR_ARG, "bd_solve_elliptic_noalloc supports at most %lld nodes (mesh has %lld)",
+                (long long)kNoAllocRows, (long long)s->N);
+  if (s->pcg_grid > kNoAllocBlocks) return fail(s, BD_ERR_ARG, "CG grid larger than the fixed scratch allows");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(s, BD_ERR_ARG, "device ordinal out of range");
+  double* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+      void* p = nullptr;
+      CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+      addr[dev] = static_cast<double*>(p);
+    }
+    base = addr[dev];
+  }
+  double* part = base + 5 * kNoAllocRows;
+  double* ctl = part + 4 * kNoAllocBlocks;
+  unsigned* bar = reinterpret_cast<unsigned*>(ctl);
+  int* status = reinterpret_cast<int*>(ctl + 1);
+  long long* it = reinterpret_cast<long long*>(ctl + 2);
+  CK(cudaMemsetAsync(ctl, 0, 4 * sizeof(double), s->stream));
+  if (u_guess_dev && u_guess_dev != u_dev)
+    CK(cudaMemcpyAsync(u_dev, u_guess_dev, s->N * 8, cudaMemcpyDeviceToDevice, s->stream));
+  PcgLaunch P = pcg_base(s);
+  P.r = base;
+  P.z = base + kNoAllocRows;
+  P.p = base + 2 * kNoAllocRows;
+  P.q = base + 3 * kNoAllocRows;
+  P.invd = base + 4 * kNoAllocRows;
+  P.part = part;
+  P.bar = bar;
+  P.status = status;
+  P.iters_acc = it;
+  P.solves_acc = nullptr;
+  P.valA = s->Aie;
+  P.val1 = s->Ai;
+  P.va = v_dev;
+  P.c1 = -1.0;
+  P.project = 1;
+  P.x = u_dev;
+  P.warm = u_guess_dev ? 1 : 0;
+  P.tol = s->opts.cg_tol_e;
+  P.maxit = s->opts.cg_cap_e;
+  P.pin = s->opts.pin_node >= 0 ? s->opts.pin_node : -1;
+  CK(launch_pcg(P, s->wmax, s->stream));
+  long long h_ctl[2] = {0, 0};
+  CK(cudaMemcpyAsync(h_ctl, ctl + 1, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  const int st = int(h_ctl[0] & 0xffffffffll);
+  if (iters) *iters = int(h_ctl[1]);
+  const int c = status_code(st);
+  if (c != BD_OK) return fail(s, c, "elliptic CG failed (device status %d)", st);
   return BD_OK;
 }
 
