@@ -149,24 +149,9 @@ class ClockSampler:
 # roofline bookkeeping
 # ---------------------------------------------------------------------------
 
-def pcg_bytes(iters: int, solves: int, n: int, nnz: int, parabolic: bool) -> float:
-    """Algorithmic HBM bytes of the CSR PCG kernel (FP64 values, int32 indices).
-
-    Per iteration: SpMV q = A z reads values + columns (12 B/nnz), row
-    pointers (4 B/row) and z once (8 B/row); the vector updates of the two
-    phases move p, q, x, r (read+write), z (read+write), 1/D (read) and, for the
-    condensed parabolic operator, its extra diagonal: 104 (+8) B/row.
-    Per solve: the right-hand side SpMV(s) and the initial residual
-    (2 x (12 nnz + 8 n) + 48 n).
-    """
-    per_iter = 12.0 * nnz + 4.0 * n + (112.0 if parabolic else 104.0) * n
-    per_solve = 2.0 * (12.0 * nnz + 8.0 * n) + 48.0 * n
-    return iters * per_iter + solves * per_solve
-
-
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("pcg.cu", "bd_internal.h"):
+    for f in ("pcg.cu", "amg.cu", "mixed.cu", "sparse.cuh", "vcycle.cuh", "bd_internal.h"):
         with open(os.path.join(ROOT, "paper_2510_27447_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -305,19 +290,19 @@ def run_ours(args) -> None:
     prof = profiles["mixed"]
     dom = max(prof["ms"], key=lambda k: prof["ms"][k])
     peaks = measured_peaks()
-    n, nnz = results and 0, prof["nnz"]
     n = SIDE * SIDE
     roof = None
     if dom in ("pcg_elliptic", "pcg_parabolic"):
         idx = 0 if dom == "pcg_elliptic" else 1
         launches = prof["launches"][dom]
-        byt = pcg_bytes(prof["cg_iters"][idx], prof["cg_solves"][idx], n, nnz, idx == 1) / launches
+        byt = prof["alg_bytes"][idx] / launches
         avg_s = prof["ms"][dom] / launches / 1e3
         achieved = byt / avg_s / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": load_traffic(dom),
                 "algorithmic_bytes_per_launch": round(byt), "avg_launch_ms": round(avg_s * 1e3, 4),
+                "cg_iters_per_launch": round(prof["cg_iters"][idx] / launches, 1),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     share = {k: round(v / sum(prof["ms"].values()), 4) for k, v in prof["ms"].items()}
 
@@ -343,7 +328,7 @@ def run_ours(args) -> None:
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "mixed: f32 membrane model, f64 solves and state",
+        "dtype": "mixed: f32 membrane model and Krylov iterations, f64 refinement and state",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "nodes": n, "model": "TP06 epicardial", "dt_ms": DT,
                    "sdc_nodes": M_NODES, "sweeps": K_SWEEPS, "start": "rest + S1 at t=0",

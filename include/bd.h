@@ -95,6 +95,8 @@ typedef struct {
   double v_act_mV;       /* activation threshold (default -30) */
   double spd_margin;     /* condensed-diagonal safeguard factor (default 0.9, 0 disables) */
   int use_graph;         /* 1: capture each step shape into a CUDA graph and replay it (default 1) */
+  int elliptic_precond;  /* 1: aggregation AMG V(1,1) cycle (default; meshes of at most
+                            400 nodes use Jacobi), 0: Jacobi */
   int cg_block;          /* CG threads per block (0 = auto: 256) */
   int cg_grid;           /* CG blocks (0 = auto: one per 256 rows, at most the co-resident maximum) */
   /* device memory hooks (NULL => cudaMalloc/cudaFree); ctx is passed back */
@@ -134,7 +136,12 @@ typedef struct {
   int64_t launches[BD_K_COUNT];
   int64_t cg_iters[2];          /* elliptic, parabolic CG iterations in the profiled steps */
   int64_t cg_solves[2];
+  int64_t outer_iters[2];       /* FP64 residual passes (mixed path: refinement steps) */
   int64_t nnz;                  /* nonzeros of the shared operator pattern */
+  double alg_bytes[2];          /* algorithmic DRAM bytes of all elliptic / parabolic solves:
+                                   every operator value, index and vector element the
+                                   algorithm must move once per use (SpMV: values + indices
+                                   + one gather of x; vectors: each stream read or written) */
 } bd_profile_t;
 
 void bd_default_options(bd_opts_t* opts);
@@ -199,8 +206,9 @@ int bd_get_stats(const bd_state_t* s, bd_stats_t* out);
  * afford cudaMalloc/cudaFree, which may synchronise the whole device.  The
  * paper has no counterpart; this is a service of the library.
  *
- * Solves A_ie u = -A_i v with the handle's resident operators, precision and
- * pin: v_dev (N doubles, device) is read, u_dev (N doubles, device) is
+ * Solves A_ie u = -A_i v by Jacobi-preconditioned CG (whatever the handle's
+ * elliptic_precond) with the handle's resident operators, tolerance and pin:
+ * v_dev (N doubles, device) is read, u_dev (N doubles, device) is
  * written, u_guess_dev (device, N) warm-starts the iteration or is NULL for a
  * zero start.  The call allocates nothing: the CG work vectors, partial sums,
  * barrier words and status live in one file-scope __device__ array of the

@@ -58,7 +58,7 @@ class Opts(C.Structure):
                 ("sdc_correction", C.c_int), ("cg_tol_e", C.c_double), ("cg_tol_p", C.c_double),
                 ("cg_cap_e", C.c_int), ("cg_cap_p", C.c_int), ("sweep_tol", C.c_double),
                 ("v_act_mV", C.c_double), ("spd_margin", C.c_double), ("use_graph", C.c_int),
-                ("cg_block", C.c_int), ("cg_grid", C.c_int),
+                ("elliptic_precond", C.c_int), ("cg_block", C.c_int), ("cg_grid", C.c_int),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("stream", C.c_void_p)]
 
@@ -74,7 +74,8 @@ KERNEL_KINDS = ("pcg_elliptic", "pcg_parabolic", "ionic", "field", "combine", "f
 
 class Profile(C.Structure):
     _fields_ = [("ms", C.c_double * 6), ("launches", C.c_int64 * 6), ("cg_iters", C.c_int64 * 2),
-                ("cg_solves", C.c_int64 * 2), ("nnz", C.c_int64)]
+                ("cg_solves", C.c_int64 * 2), ("outer_iters", C.c_int64 * 2), ("nnz", C.c_int64),
+                ("alg_bytes", C.c_double * 2)]
 
 
 _lib = None
@@ -278,7 +279,9 @@ class Simulation:
         return {"ms": dict(zip(KERNEL_KINDS, list(p.ms))),
                 "launches": dict(zip(KERNEL_KINDS, [int(x) for x in p.launches])),
                 "cg_iters": [int(p.cg_iters[0]), int(p.cg_iters[1])],
-                "cg_solves": [int(p.cg_solves[0]), int(p.cg_solves[1])], "nnz": int(p.nnz)}
+                "cg_solves": [int(p.cg_solves[0]), int(p.cg_solves[1])],
+                "outer_iters": [int(p.outer_iters[0]), int(p.outer_iters[1])], "nnz": int(p.nnz),
+                "alg_bytes": [float(p.alg_bytes[0]), float(p.alg_bytes[1])]}
 
     def reset_stats(self):
         _check(lib().bd_reset_stats(self.h), self.h)

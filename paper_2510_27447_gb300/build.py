@@ -19,8 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libbd.so")
 
-SOURCES = ["bd.cu", "ionic.cu", "pcg.cu", "assemble.cpp"]
-HEADERS = ["bd_internal.h", "models.cuh", "sd.cuh"]
+SOURCES = ["bd.cu", "ionic.cu", "pcg.cu", "amg.cu", "mixed.cu", "assemble.cpp", "amg.cpp"]
+HEADERS = ["bd_internal.h", "models.cuh", "sd.cuh", "sparse.cuh", "vcycle.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-std=c++20", ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O3",
               "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
@@ -34,7 +34,7 @@ def nvcc() -> str:
 
 
 def _obj(src: str) -> str:
-    return os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+    return os.path.join(BUILD, src.replace(".", "_") + ".o")
 
 
 def _stale(src: str) -> bool:

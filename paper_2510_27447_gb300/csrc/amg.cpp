@@ -1,0 +1,360 @@
+// amg.cpp -- host setup of an aggregation algebraic multigrid hierarchy for the
+// elliptic operator A_ie.
+//
+// The paper preconditions the elliptic solve with an algebraic multigrid
+// method built by a greedy aggregation heuristic on the strength of
+// connection (Sec. 3.3.2, "AMG preconditioner ... greedy heuristic algorithm
+// based on the strength of connection").  This is the smoothed-aggregation
+// variant (Vanek, Mandel & Brezina, Computing 56, 1996):
+//   strength   j is a strong neighbour of i if |a_ij| >= theta sqrt(a_ii a_jj)
+//   aggregates greedy: (1) a node whose strong neighbours are all free starts
+//              an aggregate with them; (2) remaining nodes join the aggregate
+//              of their strongest aggregated neighbour; (3) leftovers start
+//              aggregates with their free strong neighbours
+//   prolongator P = (I - omega D^-1 A) T, T the aggregate indicator,
+//              omega = 4 / (3 rho(D^-1 A)) (rho by power iteration)
+//   coarse op  A_c = P^T A P
+// until the operator has at most `coarse_max` rows; that last operator is
+// singular (A 1 = 0 is preserved: T 1 = 1 and A 1 = 0), so its solve uses the
+// dense inverse of A_c + c 1 1^T, which returns the zero-mean solution for any
+// right-hand side orthogonal to 1.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "bd_internal.h"
+
+namespace bd {
+
+namespace {
+
+template <class F>
+void par_rows(int64_t n, F&& fn) {
+  const unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  if (n < 4096 || nt == 1) {
+    fn(int64_t(0), n);
+    return;
+  }
+  std::vector<std::thread> th;
+  const int64_t chunk = (n + nt - 1) / nt;
+  for (unsigned t = 0; t < nt; ++t) {
+    const int64_t lo = t * chunk, hi = std::min(n, lo + chunk);
+    if (lo >= hi) break;
+    th.emplace_back([&, lo, hi] { fn(lo, hi); });
+  }
+  for (auto& x : th) x.join();
+}
+
+// C = A * B (row-wise, dense marker accumulator per thread)
+HCsr spgemm(const HCsr& A, const HCsr& B) {
+  HCsr C;
+  C.n = A.n;
+  C.m = B.m;
+  std::vector<std::vector<int32_t>> rc(A.n);
+  std::vector<std::vector<double>> rv(A.n);
+  par_rows(A.n, [&](int64_t lo, int64_t hi) {
+    std::vector<int64_t> mark(B.m, -1);
+    std::vector<double> acc(B.m, 0.0);
+    std::vector<int32_t> cols;
+    for (int64_t i = lo; i < hi; ++i) {
+      cols.clear();
+      for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
+        const int32_t k = A.ci[p];
+        const double a = A.v[p];
+        for (int64_t q = B.rp[k]; q < B.rp[k + 1]; ++q) {
+          const int32_t j = B.ci[q];
+          if (mark[j] != i) {
+            mark[j] = i;
+            acc[j] = 0.0;
+            cols.push_back(j);
+          }
+          acc[j] += a * B.v[q];
+        }
+      }
+      std::sort(cols.begin(), cols.end());
+      rc[i] = cols;
+      rv[i].resize(cols.size());
+      for (size_t t = 0; t < cols.size(); ++t) rv[i][t] = acc[cols[t]];
+    }
+  });
+  C.rp.assign(A.n + 1, 0);
+  for (int64_t i = 0; i < A.n; ++i) C.rp[i + 1] = C.rp[i] + int64_t(rc[i].size());
+  C.ci.resize(C.rp[A.n]);
+  C.v.resize(C.rp[A.n]);
+  for (int64_t i = 0; i < A.n; ++i) {
+    std::copy(rc[i].begin(), rc[i].end(), C.ci.begin() + C.rp[i]);
+    std::copy(rv[i].begin(), rv[i].end(), C.v.begin() + C.rp[i]);
+  }
+  return C;
+}
+
+HCsr transpose(const HCsr& A) {
+  HCsr T;
+  T.n = A.m;
+  T.m = A.n;
+  T.rp.assign(T.n + 1, 0);
+  for (int32_t j : A.ci) T.rp[j + 1]++;
+  for (int64_t i = 0; i < T.n; ++i) T.rp[i + 1] += T.rp[i];
+  T.ci.resize(A.ci.size());
+  T.v.resize(A.v.size());
+  std::vector<int64_t> fill(T.rp.begin(), T.rp.end() - 1);
+  for (int64_t i = 0; i < A.n; ++i)
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
+      const int64_t q = fill[A.ci[p]]++;
+      T.ci[q] = int32_t(i);
+      T.v[q] = A.v[p];
+    }
+  return T;
+}
+
+std::vector<double> diagonal(const HCsr& A) {
+  std::vector<double> d(A.n, 0.0);
+  for (int64_t i = 0; i < A.n; ++i)
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p)
+      if (A.ci[p] == i) d[i] = A.v[p];
+  return d;
+}
+
+// spectral radius of D^-1 A by power iteration (deterministic start vector)
+double rho_dinv_a(const HCsr& A, const std::vector<double>& d, int iters) {
+  std::vector<double> x(A.n), y(A.n);
+  for (int64_t i = 0; i < A.n; ++i) x[i] = 1.0 + 0.37 * std::sin(1.3 * double(i) + 0.2) + ((i & 1) ? 0.5 : -0.5);
+  double lam = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    double nrm = 0.0;
+    for (int64_t i = 0; i < A.n; ++i) nrm += x[i] * x[i];
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 0)) break;
+    for (auto& v : x) v /= nrm;
+    for (int64_t i = 0; i < A.n; ++i) {
+      double s = 0.0;
+      for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) s += A.v[p] * x[A.ci[p]];
+      y[i] = s / d[i];
+    }
+    double num = 0.0;
+    for (int64_t i = 0; i < A.n; ++i) num += x[i] * y[i];
+    lam = num;
+    x.swap(y);
+  }
+  // Rayleigh quotients approach rho from below; a small margin keeps the
+  // smoother and the prolongator damping on the safe side
+  return 1.05 * lam;
+}
+
+std::vector<int32_t> aggregate(const HCsr& A, const std::vector<double>& d, double theta, int64_t* n_agg) {
+  const int64_t n = A.n;
+  std::vector<uint8_t> strong(A.ci.size(), 0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
+      const int64_t j = A.ci[p];
+      if (j != i && std::fabs(A.v[p]) >= theta * std::sqrt(std::fabs(d[i] * d[j]))) strong[p] = 1;
+    }
+  std::vector<int32_t> agg(n, -1);
+  int32_t na = 0;
+  // pass 1: nodes whose strong neighbourhood is entirely free
+  for (int64_t i = 0; i < n; ++i) {
+    if (agg[i] >= 0) continue;
+    bool free_nb = true, any = false;
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p)
+      if (strong[p]) {
+        any = true;
+        if (agg[A.ci[p]] >= 0) {
+          free_nb = false;
+          break;
+        }
+      }
+    if (!free_nb || !any) continue;
+    agg[i] = na;
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p)
+      if (strong[p]) agg[A.ci[p]] = na;
+    ++na;
+  }
+  // pass 2: join the strongest aggregated neighbour (decided from pass-1 state)
+  std::vector<int32_t> agg1 = agg;
+  for (int64_t i = 0; i < n; ++i) {
+    if (agg1[i] >= 0) continue;
+    double best = -1.0;
+    int32_t b = -1;
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p)
+      if (strong[p] && agg1[A.ci[p]] >= 0 && std::fabs(A.v[p]) > best) {
+        best = std::fabs(A.v[p]);
+        b = agg1[A.ci[p]];
+      }
+    if (b >= 0) agg[i] = b;
+  }
+  // pass 3: leftovers form aggregates with their free strong neighbours
+  for (int64_t i = 0; i < n; ++i) {
+    if (agg[i] >= 0) continue;
+    agg[i] = na;
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p)
+      if (strong[p] && agg[A.ci[p]] < 0) agg[A.ci[p]] = na;
+    ++na;
+  }
+  *n_agg = na;
+  return agg;
+}
+
+// dense Cholesky of an SPD matrix and its explicit inverse (row-major n x n)
+bool dense_spd_inverse(std::vector<double>& a, int64_t n, std::vector<double>* inv) {
+  for (int64_t j = 0; j < n; ++j) {
+    double s = a[j * n + j];
+    for (int64_t k = 0; k < j; ++k) s -= a[j * n + k] * a[j * n + k];
+    if (!(s > 0)) return false;
+    const double l = std::sqrt(s);
+    a[j * n + j] = l;
+    for (int64_t i = j + 1; i < n; ++i) {
+      double t = a[i * n + j];
+      for (int64_t k = 0; k < j; ++k) t -= a[i * n + k] * a[j * n + k];
+      a[i * n + j] = t / l;
+    }
+  }
+  inv->assign(n * n, 0.0);
+  std::vector<double> y(n);
+  for (int64_t c = 0; c < n; ++c) {
+    for (int64_t i = 0; i < n; ++i) {
+      double t = (i == c) ? 1.0 : 0.0;
+      for (int64_t k = 0; k < i; ++k) t -= a[i * n + k] * y[k];
+      y[i] = t / a[i * n + i];
+    }
+    for (int64_t i = n - 1; i >= 0; --i) {
+      double t = y[i];
+      for (int64_t k = i + 1; k < n; ++k) t -= a[k * n + i] * (*inv)[k * n + c];
+      (*inv)[i * n + c] = t / a[i * n + i];
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+int amg_build(const HCsr& A0, const AmgParams& prm, AmgHost* out, std::string* err) {
+  out->lev.clear();
+  HCsr A = A0;
+  while (A.n > prm.coarse_max && int(out->lev.size()) < prm.max_levels) {
+    AmgHostLevel L;
+    const std::vector<double> d = diagonal(A);
+    for (int64_t i = 0; i < A.n; ++i)
+      if (!(d[i] > 0)) {
+        *err = "AMG: non-positive diagonal";
+        return BD_ERR_ARG;
+      }
+    const double rho = rho_dinv_a(A, d, 30);
+    int64_t nc = 0;
+    const std::vector<int32_t> agg = aggregate(A, d, prm.theta, &nc);
+    if (nc >= A.n) break;   // no coarsening possible
+    // P = (I - w D^-1 A) T
+    const double w = 4.0 / (3.0 * rho);
+    HCsr P;
+    P.n = A.n;
+    P.m = nc;
+    P.rp.assign(A.n + 1, 0);
+    {
+      std::vector<std::vector<int32_t>> rc(A.n);
+      std::vector<std::vector<double>> rv(A.n);
+      par_rows(A.n, [&](int64_t lo, int64_t hi) {
+        std::vector<int32_t> cols;
+        std::vector<double> vals;
+        for (int64_t i = lo; i < hi; ++i) {
+          cols.clear();
+          vals.clear();
+          auto add = [&](int32_t c, double v) {
+            for (size_t t = 0; t < cols.size(); ++t)
+              if (cols[t] == c) {
+                vals[t] += v;
+                return;
+              }
+            cols.push_back(c);
+            vals.push_back(v);
+          };
+          add(agg[i], 1.0);
+          for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) add(agg[A.ci[p]], -w * A.v[p] / d[i]);
+          std::vector<size_t> ord(cols.size());
+          std::iota(ord.begin(), ord.end(), 0);
+          std::sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return cols[x] < cols[y]; });
+          for (size_t t : ord) {
+            rc[i].push_back(cols[t]);
+            rv[i].push_back(vals[t]);
+          }
+        }
+      });
+      for (int64_t i = 0; i < A.n; ++i) P.rp[i + 1] = P.rp[i] + int64_t(rc[i].size());
+      P.ci.resize(P.rp[A.n]);
+      P.v.resize(P.rp[A.n]);
+      for (int64_t i = 0; i < A.n; ++i) {
+        std::copy(rc[i].begin(), rc[i].end(), P.ci.begin() + P.rp[i]);
+        std::copy(rv[i].begin(), rv[i].end(), P.v.begin() + P.rp[i]);
+      }
+    }
+    HCsr R = transpose(P);
+    HCsr Ac = spgemm(R, spgemm(A, P));
+    L.invdiag.resize(A.n);
+    for (int64_t i = 0; i < A.n; ++i) L.invdiag[i] = 1.0 / d[i];
+    L.omega = 4.0 / (3.0 * rho);
+    L.A = std::move(A);
+    L.P = std::move(P);
+    L.R = std::move(R);
+    out->lev.push_back(std::move(L));
+    A = std::move(Ac);
+  }
+  // coarsest operator: dense inverse of A_c + c 1 1^T
+  const int64_t n = A.n;
+  if (n > 4096) {
+    *err = "AMG: coarsest level too large for a dense solve";
+    return BD_ERR_ARG;
+  }
+  std::vector<double> dense(n * n, 0.0);
+  double dmean = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
+      dense[i * n + A.ci[p]] += A.v[p];
+      if (A.ci[p] == i) dmean += A.v[p];
+    }
+  dmean /= double(std::max<int64_t>(n, 1));
+  const double c = dmean / double(std::max<int64_t>(n, 1));
+  for (auto& x : dense) x += c;
+  if (!dense_spd_inverse(dense, n, &out->cinv)) {
+    *err = "AMG: coarsest operator is not positive definite";
+    return BD_ERR_ARG;
+  }
+  out->nc = n;
+  return BD_OK;
+}
+
+}  // namespace bd
+
+namespace bd {
+
+SellHost sell_from_csr(const HCsr& A) {
+  SellHost S;
+  S.n = A.n;
+  const int64_t nsl = (A.n + 31) / 32;
+  S.sptr.resize(nsl);
+  S.sw.resize(nsl);
+  int64_t off = 0;
+  int maxw = 0;
+  for (int64_t sl = 0; sl < nsl; ++sl) {
+    int w = 0;
+    for (int64_t i = sl * 32; i < std::min<int64_t>(A.n, sl * 32 + 32); ++i)
+      w = std::max<int>(w, int(A.rp[i + 1] - A.rp[i]));
+    S.sw[sl] = w;
+    S.sptr[sl] = off;
+    off += 32 * int64_t(w);
+    maxw = std::max(maxw, w);
+  }
+  S.col.assign(off, 0);
+  S.val.assign(off, 0.0);
+  for (int64_t i = 0; i < A.n; ++i) {
+    const int64_t base = S.sptr[i / 32] + (i % 32);
+    for (int64_t k = 0; k < A.rp[i + 1] - A.rp[i]; ++k) {
+      S.col[base + 32 * k] = A.ci[A.rp[i] + k];
+      S.val[base + 32 * k] = A.v[A.rp[i] + k];
+    }
+  }
+  S.wmax = maxw <= 8 ? 8 : maxw <= 16 ? 16 : maxw <= 32 ? 32 : maxw <= 64 ? 64 : 0;
+  return S;
+}
+
+}  // namespace bd

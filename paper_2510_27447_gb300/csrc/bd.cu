@@ -62,6 +62,20 @@ struct bd_state {
   int64_t ell_n = 0;
   int wmax = 0;
   HostOps host;                   // CSR copies (bd_operator_csr)
+  bool use_amg = false;
+  AmgDev amg{};
+  AmgDevF amgf{};                 // FP32 copy of the hierarchy (mixed path)
+  // mixed path: FP32 operator values and CG workspaces
+  float* fAie = nullptr;
+  struct PCF { double alpha; float* val; };
+  std::vector<PCF> fpcache;
+  float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *invd32 = nullptr, *d32 = nullptr;
+  float* partf = nullptr;
+  double *b64 = nullptr, *r64 = nullptr;
+  int mixed_grid = 1;
+  int amg_grid = 1;
+  int amg_levels = 0;
+  double amg_cycle_bytes[2] = {0.0, 0.0};   // algorithmic bytes of one V-cycle (FP64, FP32 values)
   double *Ai = nullptr, *Aie = nullptr, *Mv = nullptr, *Mc = nullptr, *ML = nullptr;
   struct PC { double alpha; double* val; };
   std::vector<PC> pcache;
@@ -75,7 +89,7 @@ struct bd_state {
   StimTable stim{};
   long long* step_n = nullptr;
   int* d_status = nullptr;
-  long long* d_stats = nullptr;            // [iters_e, solves_e, iters_p, solves_p]
+  long long* d_stats = nullptr;            // [iters_e, solves_e, iters_p, solves_p, outer_e, outer_p]
   unsigned long long* d_clamps = nullptr;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -211,6 +225,31 @@ double* p_values(bd_state* s, double alpha) {
   return v;
 }
 
+// FP32 copy of alpha M_v + A_i (mixed path), cached per alpha
+float* p_values_f(bd_state* s, double alpha) {
+  for (auto& pc : s->fpcache)
+    if (pc.alpha == alpha) return pc.val;
+  double* dv = p_values(s, alpha);
+  float* v = nullptr;
+  if (!dv || !alloc_n(s, &v, s->ell_n)) return nullptr;
+  if (launch_to_float(s->ell_n, dv, v, s->stream) != cudaSuccess) return nullptr;
+  s->fpcache.push_back({alpha, v});
+  return v;
+}
+
+MixedLaunch mixed_base(bd_state* s) {
+  MixedLaunch X{};
+  X.r32 = s->r32;
+  X.z32 = s->z32;
+  X.p32 = s->p32;
+  X.q32 = s->q32;
+  X.invd32 = s->invd32;
+  X.d32 = s->d32;
+  X.b64 = s->b64;
+  X.r64 = s->r64;
+  return X;
+}
+
 PcgLaunch pcg_base(bd_state* s) {
   PcgLaunch P{};
   P.n = int(s->N);
@@ -245,15 +284,29 @@ int elliptic(bd_state* s, const double* v, double* u) {
   P.pin = s->opts.pin_node >= 0 ? s->opts.pin_node : -1;
   P.iters_acc = s->d_stats + 0;
   P.solves_acc = s->d_stats + 1;
+  P.outer_acc = s->d_stats + 4;
   Timed t(s, BD_K_PCG_ELLIPTIC);
-  CK(launch_pcg(P, s->wmax, s->stream));
+  if (s->precision == BD_MIXED) {
+    MixedLaunch X = mixed_base(s);
+    X.valA32 = s->fAie;
+    X.tol_inner = 1e-4f;
+    X.max_outer = 12;
+    X.inner_cap = s->opts.cg_cap_e;
+    X.use_amg = s->use_amg ? 1 : 0;
+    P.grid = s->mixed_grid;
+    CK(launch_pcg_mixed(P, X, s->amgf, s->wmax, s->stream, s->partf));
+  } else if (s->use_amg) {
+    P.grid = s->amg_grid;
+    CK(launch_pcg_amg(P, s->amg, s->wmax, s->stream));
+  } else {
+    CK(launch_pcg(P, s->wmax, s->stream));
+  }
   return BD_OK;
 }
 
-int parabolic(bd_state* s, const double* pvals, double c1, const double* va, double c2, const double* vb,
-              double* x) {
+int parabolic(bd_state* s, double alpha, double c1, const double* va, double c2, const double* vb, double* x) {
   PcgLaunch P = pcg_base(s);
-  P.valA = pvals;
+  P.valA = p_values(s, alpha);
   P.dextra = s->dgs;
   P.rl = s->rl;
   P.val1 = s->Ai;
@@ -272,8 +325,20 @@ int parabolic(bd_state* s, const double* pvals, double c1, const double* va, dou
   P.pin = -2;
   P.iters_acc = s->d_stats + 2;
   P.solves_acc = s->d_stats + 3;
+  P.outer_acc = s->d_stats + 5;
   Timed t(s, BD_K_PCG_PARABOLIC);
-  CK(launch_pcg(P, s->wmax, s->stream));
+  if (s->precision == BD_MIXED) {
+    MixedLaunch X = mixed_base(s);
+    X.valA32 = p_values_f(s, alpha);
+    X.tol_inner = float(std::max(s->opts.cg_tol_p, 1e-6));
+    X.max_outer = 1;
+    X.inner_cap = s->opts.cg_cap_p;
+    X.use_amg = 0;
+    P.grid = s->mixed_grid;
+    CK(launch_pcg_mixed(P, X, s->amgf, s->wmax, s->stream, s->partf));
+  } else {
+    CK(launch_pcg(P, s->wmax, s->stream));
+  }
   return BD_OK;
 }
 
@@ -318,9 +383,126 @@ int prepare_step(bd_state* s, double dt, int M) {
   lobatto(M, c);
   for (int m = 0; m + 1 < M; ++m) {
     const double h = dt * (c[m + 1] - c[m]);
-    if (!p_values(s, 1.0 / (gam * h))) return fail(s, BD_ERR_OOM, "device allocation failed");
-    if (!p_values(s, 1.0 / h)) return fail(s, BD_ERR_OOM, "device allocation failed");
+    for (double alpha : {1.0 / (gam * h), 1.0 / h}) {
+      if (!p_values(s, alpha)) return fail(s, BD_ERR_OOM, "device allocation failed");
+      if (s->precision == BD_MIXED && !p_values_f(s, alpha)) return fail(s, BD_ERR_OOM, "device allocation failed");
+    }
   }
+  return BD_OK;
+}
+
+// build the AMG hierarchy of A_ie on the host and upload it (SELL-32 operators)
+int setup_amg(bd_state* s, const HostOps& H) {
+  HCsr A;
+  A.n = A.m = s->N;
+  A.rp.assign(H.rowptr.begin(), H.rowptr.end());
+  A.ci = H.col;
+  A.v = H.Aie;
+  AmgHost AH;
+  std::string err;
+  const int rc = amg_build(A, AmgParams{}, &AH, &err);
+  if (rc != BD_OK) return fail(s, rc, "%s", err.c_str());
+  if (AH.lev.empty()) return BD_OK;   // small operator: Jacobi-PCG is used
+  if (int(AH.lev.size()) > kMaxAmgLevels)
+    return fail(s, BD_ERR_ARG, "AMG hierarchy has %d levels", int(AH.lev.size()));
+  auto upload = [&](const void* h, size_t bytes) -> void* {
+    void* d = dalloc(s, bytes);
+    if (d && cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) return nullptr;
+    return d;
+  };
+  auto sell_dev = [&](const HCsr& M, SellDev* out) {
+    const SellHost S = sell_from_csr(M);
+    out->n = int(S.n);
+    out->wmax = S.wmax;
+    out->sptr = static_cast<const int64_t*>(upload(S.sptr.data(), S.sptr.size() * 8));
+    out->sw = static_cast<const int*>(upload(S.sw.data(), S.sw.size() * 4));
+    out->col = static_cast<const int*>(upload(S.col.data(), S.col.size() * 4));
+    out->val = static_cast<const double*>(upload(S.val.data(), S.val.size() * 8));
+    // the host vectors die with S: wait for the copies
+    return out->sptr && out->sw && out->col && out->val && cudaStreamSynchronize(s->stream) == cudaSuccess;
+  };
+  AmgDev& M = s->amg;
+  M.nlev = int(AH.lev.size());
+  for (int l = 0; l < M.nlev; ++l) {
+    const AmgHostLevel& Lh = AH.lev[l];
+    AmgLevelDev& Ld = M.L[l];
+    bool ok = true;
+    if (l == 0) {
+      Ld.A = SellDev{int(s->N), s->wmax, s->sptr, s->swidth, s->col, s->Aie};
+    } else {
+      ok = sell_dev(Lh.A, &Ld.A);
+    }
+    ok = ok && sell_dev(Lh.P, &Ld.P) && sell_dev(Lh.R, &Ld.R);
+    Ld.invd = static_cast<const double*>(upload(Lh.invdiag.data(), Lh.invdiag.size() * 8));
+    Ld.omega = Lh.omega;
+    const int64_t n = Lh.A.n;
+    ok = ok && Ld.invd && alloc_n(s, &Ld.x, n) && alloc_n(s, &Ld.r, n);
+    if (l > 0) ok = ok && alloc_n(s, &Ld.b, n) && alloc_n(s, &Ld.y, n);
+    if (!ok || cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, BD_ERR_OOM, "AMG upload failed");
+  }
+  M.nc = int(AH.nc);
+  M.cinv = static_cast<const double*>(upload(AH.cinv.data(), AH.cinv.size() * 8));
+  if (!M.cinv || !alloc_n(s, &M.bc, AH.nc) || !alloc_n(s, &M.xc, AH.nc) ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return fail(s, BD_ERR_OOM, "AMG upload failed");
+  if (s->precision == BD_MIXED) {
+    auto sell_devf = [&](const HCsr& Mh, SellDevT<float>* out) {
+      const SellHost S = sell_from_csr(Mh);
+      std::vector<float> fv(S.val.begin(), S.val.end());
+      out->n = int(S.n);
+      out->wmax = S.wmax;
+      out->sptr = static_cast<const int64_t*>(upload(S.sptr.data(), S.sptr.size() * 8));
+      out->sw = static_cast<const int*>(upload(S.sw.data(), S.sw.size() * 4));
+      out->col = static_cast<const int*>(upload(S.col.data(), S.col.size() * 4));
+      out->val = static_cast<const float*>(upload(fv.data(), fv.size() * 4));
+      return out->sptr && out->sw && out->col && out->val && cudaStreamSynchronize(s->stream) == cudaSuccess;
+    };
+    AmgDevF& F = s->amgf;
+    F.nlev = M.nlev;
+    for (int l = 0; l < F.nlev; ++l) {
+      const AmgHostLevel& Lh = AH.lev[l];
+      AmgLevelDevT<float>& Ld = F.L[l];
+      bool ok = true;
+      if (l == 0) Ld.A = SellDevT<float>{int(s->N), s->wmax, s->sptr, s->swidth, s->col, s->fAie};
+      else ok = sell_devf(Lh.A, &Ld.A);
+      ok = ok && sell_devf(Lh.P, &Ld.P) && sell_devf(Lh.R, &Ld.R);
+      std::vector<float> fid(Lh.invdiag.begin(), Lh.invdiag.end());
+      Ld.invd = static_cast<const float*>(upload(fid.data(), fid.size() * 4));
+      Ld.omega = float(Lh.omega);
+      const int64_t n = Lh.A.n;
+      ok = ok && Ld.invd && alloc_n(s, &Ld.x, n) && alloc_n(s, &Ld.r, n);
+      if (l > 0) ok = ok && alloc_n(s, &Ld.b, n) && alloc_n(s, &Ld.y, n);
+      if (!ok || cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, BD_ERR_OOM, "AMG upload failed");
+    }
+    std::vector<float> fci(AH.cinv.begin(), AH.cinv.end());
+    F.nc = int(AH.nc);
+    F.cinv = static_cast<const float*>(upload(fci.data(), fci.size() * 4));
+    if (!F.cinv || !alloc_n(s, &F.bc, AH.nc) || !alloc_n(s, &F.xc, AH.nc) ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+      return fail(s, BD_ERR_OOM, "AMG upload failed");
+  }
+  const int mx = pcg_amg_max_blocks(s->pcg_block);
+  if (mx <= 0) return fail(s, BD_ERR_CUDA, "cannot size the cooperative AMG-CG grid");
+  s->amg_grid = std::min(s->pcg_grid, mx);
+  for (int v = 0; v < 2; ++v) {
+    const double vb = v == 0 ? 8.0 : 4.0;
+    double b = 0.0;
+    for (size_t l = 0; l < AH.lev.size(); ++l) {
+      const AmgHostLevel& Lh = AH.lev[l];
+      const double n = double(Lh.A.n), nn = double(Lh.P.m);
+      const double spA = double(Lh.A.ci.size()) * (vb + 4) + n * vb;
+      const double spR = double(Lh.R.ci.size()) * (vb + 4) + n * vb;
+      const double spP = double(Lh.P.ci.size()) * (vb + 4) + nn * vb;
+      // 2 A products (residual, post-smoothing), R, P; vector streams of the
+      // pre-smoothing, residual, restriction, prolongation and post-smoothing
+      b += 2 * spA + spR + spP + vb * (3 * n + 2 * n + 3 * nn + 2 * n + 4 * n);
+    }
+    const double nc = double(AH.nc);
+    b += vb * (nc * nc + 2 * nc);
+    s->amg_cycle_bytes[v] = b;
+  }
+  s->amg_levels = M.nlev;
+  s->use_amg = true;
   return BD_OK;
 }
 
@@ -358,7 +540,6 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       const double h = dt * (c[m + 1] - c[m]);
       const double alpha = 1.0 / (gam * h);
       const double* src = m == 0 ? s->Xn : s->Xt[m];
-      double* pv = p_values(s, alpha);
       IonicLaunch L = ionic_base(s, MODE_S1, dt);
       L.alpha = alpha;
       L.smin = s->opts.spd_margin > 0 ? -s->opts.spd_margin * alpha * s->lambda_M : -INFINITY;
@@ -371,7 +552,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
         Timed t(s, BD_K_IONIC);
         CK(launch_ionic(L, s->stream));
       }
-      RUN(parabolic(s, pv, -1.0, s->avec, 0.0, nullptr, s->k1v));
+      RUN(parabolic(s, alpha, -1.0, s->avec, 0.0, nullptr, s->k1v));
       IonicLaunch L2 = ionic_base(s, MODE_S2, dt);
       L2.alpha = alpha;
       L2.smin = L.smin;
@@ -389,7 +570,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
         Timed t(s, BD_K_IONIC);
         CK(launch_ionic(L2, s->stream));
       }
-      RUN(parabolic(s, pv, -1.0, s->avec, -L2.ck1, s->bvec, s->k2v));
+      RUN(parabolic(s, alpha, -1.0, s->avec, -L2.ck1, s->bvec, s->k2v));
       {
         Timed t(s, BD_K_COMBINE);
         CK(launch_combine(s->model, N, src, s->k1v, s->z1, s->w1, s->k2v, s->z2, s->w2, 1.5 / gam, 0.5 / gam,
@@ -408,7 +589,6 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       for (int m = 0; m + 1 < M; ++m) {
         const double h = dt * (c[m + 1] - c[m]);
         const double alpha = 1.0 / h;
-        double* pv = p_values(s, alpha);
         IonicLaunch L = ionic_base(s, MODE_CORR, dt);
         L.alpha = alpha;
         L.smin = s->opts.spd_margin > 0 ? -s->opts.spd_margin * alpha * s->lambda_M : -INFINITY;
@@ -429,7 +609,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
           Timed t(s, BD_K_IONIC);
           CK(launch_ionic(L, s->stream));
         }
-        RUN(parabolic(s, pv, -1.0 / h, s->avec, 1.0 / h, s->bvec, s->k1v));
+        RUN(parabolic(s, alpha, -1.0 / h, s->avec, 1.0 / h, s->bvec, s->k1v));
         {
           Timed t(s, BD_K_COMBINE);
           CK(launch_update(s->model, N, s->Xt[m + 1], s->k1v, s->z1, s->w1, s->Xc[m + 1], s->stream));
@@ -519,6 +699,7 @@ void bd_default_options(bd_opts_t* o) {
   o->v_act_mV = -30.0;
   o->spd_margin = 0.9;
   o->use_graph = 1;
+  o->elliptic_precond = 1;
 }
 
 int bd_num_states(bd_ionic_t model) { return model_ns(int(model)); }
@@ -622,7 +803,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
             alloc_n(s, &s->avec, N) && alloc_n(s, &s->bvec, N) && alloc_n(s, &s->cg_r, N) &&
             alloc_n(s, &s->cg_z, N) && alloc_n(s, &s->cg_p, N) && alloc_n(s, &s->cg_q, N) &&
             alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->t_act, N) && alloc_n(s, &s->stim_bits, N) &&
-            alloc_n(s, &s->step_n, 1) && alloc_n(s, &s->d_status, 1) && alloc_n(s, &s->d_stats, 4) &&
+            alloc_n(s, &s->step_n, 1) && alloc_n(s, &s->d_status, 1) && alloc_n(s, &s->d_stats, 8) &&
             alloc_n(s, &s->d_clamps, 1) && alloc_n(s, &s->bar, 2);
   for (int m = 0; ok && m < kMaxNodes; ++m)
     ok = alloc_n(s, &s->Xt[m], ns * N) && alloc_n(s, &s->Xc[m], ns * N) && alloc_n(s, &s->fq[m], ns * N) &&
@@ -642,6 +823,15 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   const int64_t want = s->opts.cg_grid > 0 ? s->opts.cg_grid : (N + s->pcg_block - 1) / s->pcg_block;
   s->pcg_grid = int(std::max<int64_t>(1, std::min<int64_t>(want, s->pcg_max)));
   if (ok) ok = alloc_n(s, &s->cg_part, int64_t(s->pcg_max) * 4);
+  if (ok && s->precision == BD_MIXED) {
+    ok = alloc_n(s, &s->fAie, s->ell_n) && alloc_n(s, &s->r32, N) && alloc_n(s, &s->z32, N) &&
+         alloc_n(s, &s->p32, N) && alloc_n(s, &s->q32, N) && alloc_n(s, &s->invd32, N) &&
+         alloc_n(s, &s->d32, N) && alloc_n(s, &s->b64, N) && alloc_n(s, &s->r64, N) &&
+         alloc_n(s, &s->partf, int64_t(s->pcg_max) * 4);
+    const int mx = pcg_mixed_max_blocks(s->pcg_block);
+    if (ok && mx <= 0) ok = false;
+    s->mixed_grid = std::min(s->pcg_grid, std::max(mx, 1));
+  }
   if (!ok) {
     release(s);
     delete s;
@@ -665,7 +855,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   if (e == cudaSuccess) e = cudaMemsetAsync(s->stim_bits, 0, N * 4, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->bar, 0, 8, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, 4, s->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_stats, 0, 32, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_stats, 0, 64, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_clamps, 0, 8, s->stream);
   // the mass values outlive this scope only through the device copies; wait
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -673,6 +863,22 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     release(s);
     delete s;
     return fail(nullptr, BD_ERR_CUDA, "upload: %s", cudaGetErrorString(e));
+  }
+  if (s->precision == BD_MIXED &&
+      (launch_to_float(s->ell_n, s->Aie, s->fAie, s->stream) != cudaSuccess ||
+       cudaStreamSynchronize(s->stream) != cudaSuccess)) {
+    release(s);
+    delete s;
+    return fail(nullptr, BD_ERR_CUDA, "FP32 operator copy failed");
+  }
+  if (s->opts.elliptic_precond == 1) {
+    rc = setup_amg(s, H);
+    if (rc != BD_OK) {
+      std::string m = s->err;
+      release(s);
+      delete s;
+      return fail(nullptr, rc, "%s", m.c_str());
+    }
   }
   s->host = std::move(H);
   // resting initial state
@@ -927,9 +1133,9 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
   if (!(dt > 0) || (M != 2 && M != 3) || K < 1) return fail(s, BD_ERR_ARG, "bad step shape");
   std::memset(out, 0, sizeof(*out));
   out->nnz = s->nnz;
-  long long st0[4], st1[4];
+  long long st0[6], st1[6];
   CK(cudaStreamSynchronize(s->stream));
-  CK(cudaMemcpy(st0, s->d_stats, 32, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(st0, s->d_stats, 48, cudaMemcpyDeviceToHost));
   s->prof = true;
   int rc = BD_OK;
   for (int n = 0; n < n_steps && rc == BD_OK; ++n) {
@@ -950,18 +1156,39 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
   }
   s->prof = false;
   if (rc != BD_OK) return rc;
-  CK(cudaMemcpy(st1, s->d_stats, 32, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(st1, s->d_stats, 48, cudaMemcpyDeviceToHost));
   out->cg_iters[0] = st1[0] - st0[0];
   out->cg_solves[0] = st1[1] - st0[1];
   out->cg_iters[1] = st1[2] - st0[2];
   out->cg_solves[1] = st1[3] - st0[3];
+  out->outer_iters[0] = st1[4] - st0[4];
+  out->outer_iters[1] = st1[5] - st0[5];
+  // algorithmic bytes (see bd_profile_t); vb = bytes per value of the Krylov iteration
+  const double n = double(s->N), nnz = double(s->nnz);
+  const bool mixed = s->precision == BD_MIXED;
+  const double vb = mixed ? 4.0 : 8.0;
+  auto spmv = [&](double v) { return nnz * (v + 4) + n * v; };
+  for (int k = 0; k < 2; ++k) {
+    const bool ell = k == 0;
+    const double iters = double(out->cg_iters[k]), solves = double(out->cg_solves[k]);
+    const double extra = ell ? 0.0 : 8.0 * n;                       // condensed diagonal
+    double per_iter = spmv(vb) + 13.0 * vb * n + extra;
+    if (ell && s->use_amg) per_iter += s->amg_cycle_bytes[mixed ? 1 : 0] - 2.0 * vb * n;  // cycle replaces 1/D r
+    const double per_solve = (ell ? 1.0 : 2.0) * spmv(8.0) + 5.0 * 8.0 * n + extra;
+    double b = solves * per_solve + iters * per_iter;
+    if (mixed) {
+      const double outer = double(out->outer_iters[k]);
+      b += outer * (ell ? spmv(8.0) + 3.0 * 8.0 * n : 2.0 * 8.0 * n) + outer * 12.0 * n;  // FP64 residual + conversion
+    }
+    out->alg_bytes[k] = b;
+  }
   return read_status(s);
 }
 
 int bd_reset_stats(bd_state_t* s) {
   if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
   CK(cudaStreamSynchronize(s->stream));
-  CK(cudaMemset(s->d_stats, 0, 32));
+  CK(cudaMemset(s->d_stats, 0, 64));
   CK(cudaMemset(s->d_clamps, 0, 8));
   s->steps = s->sweeps = s->ionic_evals = s->launches = 0;
   return BD_OK;

@@ -123,6 +123,7 @@ struct PcgLaunch {
   int* status;
   long long* iters_acc;
   long long* solves_acc;
+  long long* outer_acc;     // FP64 residual passes (mixed kernel)
   int grid;                 // co-resident blocks
   int block;
 };
@@ -131,6 +132,98 @@ int pcg_max_blocks(int block, int wmax);
 cudaError_t launch_axpby_vals(int64_t nnz, double a, const double* X, double b, const double* Y, double* out,
                               cudaStream_t st);
 cudaError_t launch_copy(int64_t n, const double* src, double* dst, cudaStream_t st);
+
+// ---- algebraic multigrid (amg.cpp host setup, amg.cu device V-cycle) -------
+struct HCsr {                      // host CSR, n x m
+  int64_t n = 0, m = 0;
+  std::vector<int64_t> rp;
+  std::vector<int32_t> ci;
+  std::vector<double> v;
+};
+struct AmgParams {
+  double theta = 0.08;             // strength-of-connection threshold
+  int64_t coarse_max = 400;        // rows of the dense coarsest solve
+  int max_levels = 9;
+};
+struct AmgHostLevel {
+  HCsr A, P, R;                    // A: n x n, P: n x n_next, R = P^T
+  std::vector<double> invdiag;
+  double omega = 0.0;              // damped-Jacobi weight 4 / (3 rho(D^-1 A))
+};
+struct AmgHost {
+  std::vector<AmgHostLevel> lev;   // smoothed levels (fine to coarse)
+  int64_t nc = 0;                  // rows of the coarsest operator
+  std::vector<double> cinv;        // dense inverse of A_c + c 1 1^T (nc x nc, row-major)
+};
+int amg_build(const HCsr& A, const AmgParams& prm, AmgHost* out, std::string* err);
+
+struct SellHost {
+  int64_t n = 0;
+  std::vector<int64_t> sptr;
+  std::vector<int> sw;
+  std::vector<int> col;
+  std::vector<double> val;
+  int wmax = 0;                    // 8, 16, 32, 64 or 0 (looped rows)
+};
+SellHost sell_from_csr(const HCsr& A);
+
+constexpr int kMaxAmgLevels = 10;
+template <class T>
+struct SellDevT {
+  int n;
+  int wmax;
+  const int64_t* sptr;
+  const int* sw;
+  const int* col;
+  const T* val;
+};
+template <class T>
+struct AmgLevelDevT {
+  SellDevT<T> A, P, R;
+  const T* invd;
+  T omega;
+  T* x;                            // pre-smoothed / prolongation-corrected iterate
+  T* b;                            // right-hand side (level >= 1)
+  T* r;                            // residual
+  T* y;                            // post-smoothed result (level >= 1)
+};
+template <class T>
+struct AmgDevT {
+  int nlev;                        // smoothed levels
+  AmgLevelDevT<T> L[kMaxAmgLevels];
+  int nc;
+  const T* cinv;
+  T* bc;
+  T* xc;
+};
+using SellDev = SellDevT<double>;
+using AmgLevelDev = AmgLevelDevT<double>;
+using AmgDev = AmgDevT<double>;
+using AmgDevF = AmgDevT<float>;
+cudaError_t launch_pcg_amg(const PcgLaunch& P, const AmgDev& M, int wmax, cudaStream_t st);
+int pcg_amg_max_blocks(int block);
+
+// mixed precision (mixed.cu): FP64 right-hand side and outer residual, FP32
+// inner CG (Jacobi or the FP32 copy of the AMG hierarchy), x += d in FP64
+struct MixedLaunch {
+  const float* valA32;      // FP32 copy of the operator values (SELL)
+  float* r32;
+  float* z32;
+  float* p32;
+  float* q32;
+  float* invd32;
+  float* d32;               // inner solution
+  double* b64;              // right-hand side
+  double* r64;              // outer residual
+  float tol_inner;          // relative residual reduction of each inner solve
+  int max_outer;            // 1: single FP32 solve (x = d); > 1: iterative refinement
+  int inner_cap;
+  int use_amg;
+};
+cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const AmgDevF& M, int wmax, cudaStream_t st,
+                             float* partf);
+int pcg_mixed_max_blocks(int block);
+cudaError_t launch_to_float(int64_t n, const double* src, float* dst, cudaStream_t st);
 
 // host assembly (assemble.cpp)
 struct HostOps {

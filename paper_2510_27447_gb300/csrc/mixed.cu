@@ -1,0 +1,292 @@
+// mixed.cu -- mixed-precision conjugate gradients for the mixed path.
+//
+// One persistent cooperative kernel:
+//   FP64   b (right-hand side; mean-projected for the singular elliptic
+//          operator) and, per outer step, the residual r = b - A x of the
+//          FP64 solution x
+//   FP32   an inner CG on A d = r from d = 0 with FP32 operator values,
+//          vectors and accumulation, preconditioned by Jacobi or by one
+//          FP32 AMG V(1,1) cycle, until |r_inner| <= tol_inner |r|
+//   FP64   x += d
+// With max_outer > 1 the outer step repeats until |b - A x| <= tol |b| in
+// FP64 (iterative refinement: the elliptic solve keeps FP64 accuracy while
+// every Krylov iteration runs in FP32); with max_outer = 1 the single FP32
+// solve is the answer (the well-conditioned condensed parabolic systems).
+// FP64 partial sums use their own slots (part), FP32 ones another buffer
+// (partf); each slot is rewritten only after a barrier that follows its
+// last read, as in pcg.cu.
+#include <cuda_runtime.h>
+
+#include "bd_internal.h"
+#include "sparse.cuh"
+#include "vcycle.cuh"
+
+namespace bd {
+
+namespace {
+
+template <int WMAX, bool AMG>
+__global__ void __launch_bounds__(1024) pcg_mixed_kernel(const PcgLaunch a, const MixedLaunch m, const AmgDevF M,
+                                                          float* partf) {
+  __shared__ double shd[4][32];
+  __shared__ float shf[4][32];
+  const int n = a.n;
+  const int nb = gridDim.x;
+  const int stride = blockDim.x * gridDim.x;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+
+  // ---- FP64 right-hand side, FP32 Jacobi scaling ---------------------------
+  double acc0[2] = {0.0, 0.0};
+  for (int i = i0; i < n; i += stride) {
+    double b = a.rl ? a.rl[i] : 0.0;
+    if (a.val1) b += a.c1 * sell_row<WMAX, false>(a, a.val1, a.va, i);
+    if (a.val2) b += a.c2 * sell_row<WMAX, false>(a, a.val2, a.vb, i);
+    m.b64[i] = b;
+    double d = a.valA[a.diagpos[i]];
+    if (a.dextra) d += a.dextra[i];
+    m.invd32[i] = float(1.0 / d);
+    acc0[0] += b;
+    acc0[1] += b * b;
+  }
+  if (!a.warm)
+    for (int i = i0; i < n; i += stride) a.x[i] = 0.0;
+  block_sum<2, double>(acc0, shd);
+  if (threadIdx.x == 0) {
+    a.part[blockIdx.x * 4 + 0] = acc0[0];
+    a.part[blockIdx.x * 4 + 1] = acc0[1];
+  }
+  if (!grid_barrier(a.bar, nb, a.status)) return;
+  double tot[2];
+  grid_total<2, double>(a.part, {0, 1}, nb, tot, shd);
+  const double mean_b = a.project ? tot[0] / double(n) : 0.0;
+  double bb = a.project ? tot[1] - double(n) * mean_b * mean_b : tot[1];
+  if (bb < 0.0) bb = 0.0;
+  const double tol2 = a.tol * a.tol * bb;
+  if (a.project)
+    for (int i = i0; i < n; i += stride) m.b64[i] -= mean_b;
+
+  int fail = 0;
+  long long inner_total = 0;
+  long long outer_total = 0;
+  for (int outer = 0;; ++outer) {
+    ++outer_total;
+    // ---- FP64 outer residual ---------------------------------------------
+    double accr[1] = {0.0};
+    if (outer == 0 && !a.warm) {
+      for (int i = i0; i < n; i += stride) {
+        const double r = m.b64[i];
+        m.r64[i] = r;
+        accr[0] += r * r;
+      }
+    } else {
+      for (int i = i0; i < n; i += stride) {
+        const double ax = (a.dextra ? a.dextra[i] * a.x[i] : 0.0) + sell_row<WMAX, true>(a, a.valA, a.x, i);
+        const double r = m.b64[i] - ax;
+        m.r64[i] = r;
+        accr[0] += r * r;
+      }
+    }
+    block_sum<1, double>(accr, shd);
+    if (threadIdx.x == 0) a.part[blockIdx.x * 4 + 2] = accr[0];
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    double t1[1];
+    grid_total<1, double>(a.part, {2}, nb, t1, shd);
+    const double rr64 = t1[0];
+    if (!isfinite(rr64)) {
+      fail = ST_NONFINITE;
+      break;
+    }
+    if (m.max_outer > 1 && rr64 <= tol2) break;
+    if (outer >= m.max_outer) {
+      if (m.max_outer > 1) fail = ST_NOT_CONVERGED;
+      break;
+    }
+    if (!(rr64 > 0.0)) break;   // b = 0 with x = 0
+    // the inner system is scaled to a unit residual (FP32 range is then never
+    // an issue, whatever the magnitude of b) and solved until its residual is
+    // tol_inner, or just what the outer tolerance still needs
+    const double scale = sqrt(rr64);
+    const double inv_scale = 1.0 / scale;
+    double tgt = double(m.tol_inner) * double(m.tol_inner);
+    if (m.max_outer > 1) tgt = fmax(tgt, 0.25 * tol2 / rr64);
+    const float target2 = float(tgt);
+
+    // ---- FP32 inner CG on A d = r / |r| ----------------------------------
+    for (int i = i0; i < n; i += stride) {
+      m.r32[i] = float(m.r64[i] * inv_scale);
+      m.d32[i] = 0.0f;
+    }
+    if constexpr (AMG) {
+      if (!vcycle<float>(M, m.r32, m.z32, a.bar, nb, a.status)) return;
+    } else {
+      for (int i = i0; i < n; i += stride) m.z32[i] = m.invd32[i] * m.r32[i];
+    }
+    float accf[2] = {0.0f, 0.0f};
+    for (int i = i0; i < n; i += stride) {
+      accf[0] += m.r32[i] * m.z32[i];
+      accf[1] += m.r32[i] * m.r32[i];
+    }
+    block_sum<2, float>(accf, shf);
+    if (threadIdx.x == 0) {
+      partf[blockIdx.x * 4 + 2] = accf[0];
+      partf[blockIdx.x * 4 + 3] = accf[1];
+    }
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    float tf[2];
+    grid_total<2, float>(partf, {2, 3}, nb, tf, shf);
+    float rho = tf[0];
+    float rr = tf[1];
+    int it = 0;
+    float beta = 0.0f;
+    bool done = !(rr > target2);
+    while (!done) {
+      float pq[1] = {0.0f};
+      for (int i = i0; i < n; i += stride) {
+        const float z = m.z32[i];
+        float az = a.dextra ? float(a.dextra[i]) * z : 0.0f;
+        az += sell_row<WMAX, true, float>(a.sptr, a.swidth, a.col, m.valA32, m.z32, i);
+        const float p = it == 0 ? z : z + beta * m.p32[i];
+        const float q = it == 0 ? az : az + beta * m.q32[i];
+        m.p32[i] = p;
+        m.q32[i] = q;
+        pq[0] += p * q;
+      }
+      block_sum<1, float>(pq, shf);
+      if (threadIdx.x == 0) partf[blockIdx.x * 4 + 0] = pq[0];
+      if (!grid_barrier(a.bar, nb, a.status)) return;
+      float tq[1];
+      grid_total<1, float>(partf, {0}, nb, tq, shf);
+      if (!(tq[0] > 0.0f)) {
+        if (!isfinite(tq[0])) fail = ST_NONFINITE;
+        break;     // FP32 breakdown: keep d, the outer step decides
+      }
+      const float alpha = rho / tq[0];
+      float rrl = 0.0f;
+      for (int i = i0; i < n; i += stride) {
+        m.d32[i] += alpha * m.p32[i];
+        const float r = m.r32[i] - alpha * m.q32[i];
+        m.r32[i] = r;
+        rrl += r * r;
+      }
+      if constexpr (AMG) {
+        if (!vcycle<float>(M, m.r32, m.z32, a.bar, nb, a.status)) return;
+      } else {
+        for (int i = i0; i < n; i += stride) m.z32[i] = m.invd32[i] * m.r32[i];
+      }
+      float acc[2] = {0.0f, rrl};
+      for (int i = i0; i < n; i += stride) acc[0] += m.r32[i] * m.z32[i];
+      block_sum<2, float>(acc, shf);
+      if (threadIdx.x == 0) {
+        partf[blockIdx.x * 4 + 2] = acc[0];
+        partf[blockIdx.x * 4 + 3] = acc[1];
+      }
+      if (!grid_barrier(a.bar, nb, a.status)) return;
+      grid_total<2, float>(partf, {2, 3}, nb, tf, shf);
+      ++it;
+      rr = tf[1];
+      if (!isfinite(rr) || !isfinite(tf[0])) {
+        fail = ST_NONFINITE;
+        break;
+      }
+      if (rr <= target2) break;
+      if (it >= m.inner_cap) {
+        if (m.max_outer == 1) fail = ST_NOT_CONVERGED;
+        break;
+      }
+      beta = tf[0] / rho;
+      rho = tf[0];
+    }
+    inner_total += it;
+    if (fail) break;
+    for (int i = i0; i < n; i += stride) a.x[i] += scale * double(m.d32[i]);
+    if (m.max_outer == 1) break;
+    if (!grid_barrier(a.bar, nb, a.status)) return;   // x complete before the next residual
+  }
+
+  if (a.pin >= 0) {
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    const double shift = __ldcg(a.x + a.pin);
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    for (int i = i0; i < n; i += stride) a.x[i] -= shift;
+  } else if (a.pin == -1) {
+    double sx[1] = {0.0};
+    for (int i = i0; i < n; i += stride) sx[0] += a.x[i];
+    block_sum<1, double>(sx, shd);
+    if (threadIdx.x == 0) a.part[blockIdx.x * 4 + 0] = sx[0];
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    double tm[1];
+    grid_total<1, double>(a.part, {0}, nb, tm, shd);
+    const double mean = tm[0] / double(n);
+    for (int i = i0; i < n; i += stride) a.x[i] -= mean;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (fail) atomicOr(a.status, fail);
+    if (a.iters_acc) atomicAdd((unsigned long long*)a.iters_acc, (unsigned long long)inner_total);
+    if (a.outer_acc) atomicAdd((unsigned long long*)a.outer_acc, (unsigned long long)outer_total);
+    if (a.solves_acc) atomicAdd((unsigned long long*)a.solves_acc, 1ull);
+  }
+}
+
+template <int W, bool AMG>
+int max_blocks_t(int block) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_mixed_kernel<W, AMG>, block, 0) != cudaSuccess)
+    return 0;
+  return sms * per;
+}
+
+__global__ void to_float_kernel(int64_t n, const double* src, float* dst) {
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = float(src[i]);
+}
+
+}  // namespace
+
+int pcg_mixed_max_blocks(int block) {
+  int m = max_blocks_t<8, false>(block);
+  m = std::min(m, max_blocks_t<16, false>(block));
+  m = std::min(m, max_blocks_t<32, false>(block));
+  m = std::min(m, max_blocks_t<0, false>(block));
+  m = std::min(m, max_blocks_t<8, true>(block));
+  m = std::min(m, max_blocks_t<16, true>(block));
+  m = std::min(m, max_blocks_t<32, true>(block));
+  m = std::min(m, max_blocks_t<0, true>(block));
+  return m;
+}
+
+cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const AmgDevF& M, int wmax, cudaStream_t st,
+                             float* partf) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(P.grid));
+  cfg.blockDim = dim3(unsigned(P.block));
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (X.use_amg) {
+    switch (wmax) {
+      case 8: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<8, true>, P, X, M, partf);
+      case 16: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<16, true>, P, X, M, partf);
+      case 32: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<32, true>, P, X, M, partf);
+      default: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<0, true>, P, X, M, partf);
+    }
+  }
+  switch (wmax) {
+    case 8: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<8, false>, P, X, M, partf);
+    case 16: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<16, false>, P, X, M, partf);
+    case 32: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<32, false>, P, X, M, partf);
+    default: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<0, false>, P, X, M, partf);
+  }
+}
+
+cudaError_t launch_to_float(int64_t n, const double* src, float* dst, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  to_float_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(n, src, dst);
+  return cudaGetLastError();
+}
+
+}  // namespace bd

@@ -23,123 +23,11 @@
 #include <cuda_runtime.h>
 
 #include "bd_internal.h"
+#include "sparse.cuh"
 
 namespace bd {
 
 namespace {
-
-#ifndef BD_PCG_SLEEP_NS
-#define BD_PCG_SLEEP_NS 0
-#endif
-constexpr long long kSpinLimit = 1ll << 26;   // bounded wait: about a second of polling
-
-// sense-free generation barrier: bar[0] = arrivals, bar[1] = generation
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g0 = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
-    ok = 1;
-    if (arrived == nblocks - 1u) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long spins = 0;
-      while (*gen == g0) {
-        if (BD_PCG_SLEEP_NS > 0) __nanosleep(BD_PCG_SLEEP_NS);
-        if (++spins > kSpinLimit) {
-          atomicOr(status, ST_TIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-// block-wide sum of NV values; result valid in thread 0
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sh)[32]) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double x = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) sh[k][wid] = x;
-  }
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double x = lane < nw ? sh[k][lane] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-      v[k] = x;
-    }
-  }
-  __syncthreads();
-}
-
-// every block sums part[b*4 + slot] over b = 0..nb-1 in the same order
-template <int NV>
-__device__ __forceinline__ void grid_total(const double* part, const int (&slot)[NV], int nb, double (&out)[NV],
-                                           double (*sh)[32]) {
-  double v[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] += __ldcg(part + b * 4 + slot[k]);
-  block_sum<NV>(v, sh);
-  __shared__ double bc[NV];
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) bc[k] = v[k];
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) out[k] = bc[k];
-  __syncthreads();
-}
-
-// sum_k val[k] x[col[k]] over row i of a SELL-32 operator.  For WMAX > 0 the
-// loads are fully unrolled and predicated so a thread issues all its column
-// and value loads back to back (memory-level parallelism); WMAX = 0 loops.
-template <int WMAX, bool CROSS>
-__device__ __forceinline__ double sell_row(const PcgLaunch& a, const double* __restrict__ val,
-                                           const double* x, int i) {
-  const int s = i >> 5;
-  const int64_t base = a.sptr[s] + (i & 31);
-  const int w = a.swidth[s];
-  double acc = 0.0;
-  if constexpr (WMAX > 0) {
-    int c[WMAX];
-    double v[WMAX];
-#pragma unroll
-    for (int k = 0; k < WMAX; ++k)
-      if (k < w) {
-        c[k] = a.col[base + 32 * k];
-        v[k] = val[base + 32 * k];
-      }
-#pragma unroll
-    for (int k = 0; k < WMAX; ++k)
-      if (k < w) acc += v[k] * (CROSS ? __ldcg(x + c[k]) : x[c[k]]);
-  } else {
-    for (int k = 0; k < w; ++k) {
-      const int c = a.col[base + 32 * k];
-      acc += val[base + 32 * k] * (CROSS ? __ldcg(x + c) : x[c]);
-    }
-  }
-  return acc;
-}
 
 template <int WMAX>
 __global__ void __launch_bounds__(1024) pcg_kernel(const PcgLaunch a) {

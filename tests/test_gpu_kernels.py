@@ -102,3 +102,22 @@ def test_equal_anisotropy_closed_form_on_gpu():
     want -= want[5]
     np.testing.assert_allclose(u, want, atol=1e-9)
     sim.close()
+
+
+@pytest.mark.parametrize("side", [65, 129])
+def test_amg_preconditioned_elliptic_solve(side):
+    """The AMG-preconditioned CG (the paper's elliptic preconditioner class)
+    reaches the same solution as the direct solve and as Jacobi-PCG, with an
+    iteration count that does not grow with the mesh."""
+    w = W.sheet(side, 1.0, W.LR91, 0.02, 1)
+    xyz = w.xyz
+    v = -80 + 100 * np.exp(-30 * ((xyz[:, 0] - 0.3) ** 2 + (xyz[:, 1] - 0.6) ** 2))
+    u_ref = oracle_problem(w).elliptic(v)
+    sim_a = gpu_sim(w, cg_tol_e=1e-13, elliptic_precond=1)
+    sim_j = gpu_sim(w, cg_tol_e=1e-13, elliptic_precond=0)
+    ua, ita = sim_a.solve_elliptic(v)
+    uj, itj = sim_j.solve_elliptic(v)
+    assert rel(ua, u_ref) < 1e-10 and rel(uj, u_ref) < 1e-10
+    assert ita < 45 and ita * 8 < itj
+    sim_a.close()
+    sim_j.close()

@@ -39,7 +39,7 @@ def _rel(a, b):
 def test_noalloc_solve_matches_allocating_solve_on_two_calls():
     w = W.sheet(65, 1.0, W.LR91, 0.02, 1)
     sim = binding.Simulation(w.xyz, w.elems, w.fibers, w.sigma, w.chi, w.cm, w.model,
-                             binding.default_options(cg_tol_e=1e-13))
+                             binding.default_options(cg_tol_e=1e-13, elliptic_precond=0))
     xyz = w.xyz
     v = -80.0 + 100.0 * np.exp(-30.0 * ((xyz[:, 0] - 0.3) ** 2 + (xyz[:, 1] - 0.6) ** 2))
     u_ref, it_ref = sim.solve_elliptic(v)
