@@ -233,6 +233,31 @@ def e2e_rate(sim, torch, steps: int) -> dict:
             "d2h_bytes_per_step": 2 * 8 * sim.N}
 
 
+def serve_leg(args) -> dict:
+    """Scaled serving workload (the 512-request, 400 ms stream is hours of GPU
+    time): args.serve_requests Poisson(40/s) arrivals, sides 33/65/129,
+    LR91/TP06 50/50, jittered conductivities, each simulated for
+    args.serve_ms ms.  Continuous batching on the mixed path vs the same
+    requests one at a time through the plain FP64 path."""
+    from paper_2510_27447_gb300 import binding, serving as S, workloads as W
+    reqs = W.request_stream(args.serve_requests, 40.0, seed=4, sides=(33, 65, 129), t_end=args.serve_ms)
+
+    def jobs():
+        return [S.Job(r.rid, r.arrival_s, r.side ** 2, int(round(args.serve_ms / r.dt)), W.request_workload(r))
+                for r in reqs]
+    out = {"requests": len(reqs), "rate_per_s": 40.0, "sides": [33, 65, 129], "t_end_ms": args.serve_ms,
+           "slots": 8, "chunk_steps": 25}
+    for name, prec, slots in (("batched_mixed", binding.MIXED, 8), ("one_at_a_time_fp64", binding.FP64, 1)):
+        ex = S.GpuExecutor(lambda p=prec: binding.default_options(precision=p), dt=0.02)
+        t0 = time.perf_counter()
+        done = S.Server(ex, max_slots=slots, hbm_budget=32 << 30, chunk_steps=25).run(jobs())
+        wall = time.perf_counter() - t0
+        sm = S.summarize(done)
+        out[name] = {"p50_ms": round(sm["p50_ms"], 2), "p99_ms": round(sm["p99_ms"], 2),
+                     "node_steps_per_s": round(sm["node_steps_per_s"], 1), "wall_s": round(wall, 2)}
+    return out
+
+
 def run_ours(args) -> None:
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -306,6 +331,13 @@ def run_ours(args) -> None:
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     share = {k: round(v / sum(prof["ms"].values()), 4) for k, v in prof["ms"].items()}
 
+    serve = None
+    if args.serve_requests > 0:
+        try:
+            serve = serve_leg(args)
+        except Exception as e:  # noqa: BLE001
+            serve = {"error": str(e)[:200]}
+
     base = None
     if world == 1 and not args.no_baseline:
         try:
@@ -342,6 +374,7 @@ def run_ours(args) -> None:
         "kernel_share": share,
         "cg_iters_per_solve": {"elliptic": round(mixed["cg_iters_e"], 1), "parabolic": round(mixed["cg_iters_p"], 1)},
         "cpu_baseline": base,
+        "serve": serve,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -373,6 +406,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-ms", type=float, default=10.0)
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--seconds", type=float, default=0.0, help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -91,12 +91,16 @@ typedef struct {
   double cg_tol_p;       /* condensed parabolic CG (default 1e-10) */
   int cg_cap_e;          /* iteration caps (default 20000 / 2000) */
   int cg_cap_p;
-  double sweep_tol;      /* > 0: stop the sweeps when max|X^k - X^(k-1)| < tol (default 0: all sweeps) */
+  double sweep_tol;      /* > 0: Algorithm 2's test -- after sweep k < n_sweeps, stop when
+                            max over all nodes and states |X^k - X^(k-1)| (X^0 = X^n, last
+                            Lobatto node) < sweep_tol; decided on the device, so graph
+                            replay is kept (default 0: always n_sweeps sweeps) */
   double v_act_mV;       /* activation threshold (default -30) */
   double spd_margin;     /* condensed-diagonal safeguard factor (default 0.9, 0 disables) */
   int use_graph;         /* 1: capture each step shape into a CUDA graph and replay it (default 1) */
-  int elliptic_precond;  /* 1: aggregation AMG V(1,1) cycle (default; meshes of at most
-                            400 nodes use Jacobi), 0: Jacobi */
+  int elliptic_precond;  /* 1: aggregation AMG V(1,1) cycle (default; meshes small enough
+                            for the dense coarse level use Jacobi), 0: Jacobi */
+  int amg_coarse_max;    /* rows of the dense coarsest AMG level (0 = default 1500) */
   int cg_block;          /* CG threads per block (0 = auto: 256) */
   int cg_grid;           /* CG blocks (0 = auto: one per 256 rows, at most the co-resident maximum) */
   /* device memory hooks (NULL => cudaMalloc/cudaFree); ctx is passed back */
@@ -176,6 +180,11 @@ int bd_batch_step(bd_state_t* const* states, int n, double dt_ms, int n_sdc_node
 
 /* Wait for the handle's stream and return its device status word. */
 int bd_sync(bd_state_t* s);
+
+/* Non-blocking: 1 if every step enqueued on the handle has completed, 0 if
+ * work is still in flight, negative on a CUDA error.  Lets one host thread
+ * keep many handles (each on its own stream) busy at once. */
+int bd_query(bd_state_t* s);
 void bd_clear_status(bd_state_t* s);
 
 /* Activation times (first upward crossing of v_act, linearly interpolated

@@ -25,7 +25,7 @@ EXPORTS = ["bd_default_options", "bd_create", "bd_add_stimulus", "bd_set_initial
            "bd_device_fields", "bd_get_state", "bd_set_state", "bd_footprint_bytes", "bd_get_stats",
            "bd_reset_stats", "bd_num_nodes", "bd_num_states", "bd_last_error", "bd_destroy",
            "bd_ionic_eval", "bd_ionic_pattern", "bd_rest_state", "bd_operator_csr",
-           "bd_solve_elliptic", "bd_profile_steps", "bd_solve_elliptic_noalloc"]
+           "bd_solve_elliptic", "bd_profile_steps", "bd_solve_elliptic_noalloc", "bd_query"]
 
 
 class LibraryMissing(RuntimeError):
@@ -58,7 +58,8 @@ class Opts(C.Structure):
                 ("sdc_correction", C.c_int), ("cg_tol_e", C.c_double), ("cg_tol_p", C.c_double),
                 ("cg_cap_e", C.c_int), ("cg_cap_p", C.c_int), ("sweep_tol", C.c_double),
                 ("v_act_mV", C.c_double), ("spd_margin", C.c_double), ("use_graph", C.c_int),
-                ("elliptic_precond", C.c_int), ("cg_block", C.c_int), ("cg_grid", C.c_int),
+                ("elliptic_precond", C.c_int), ("amg_coarse_max", C.c_int), ("cg_block", C.c_int),
+                ("cg_grid", C.c_int),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("stream", C.c_void_p)]
 
@@ -99,6 +100,7 @@ def lib():
         "bd_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int]),
         "bd_batch_step": (C.c_int, [P(C.c_void_p), C.c_int, C.c_double, C.c_int, C.c_int]),
         "bd_sync": (C.c_int, [C.c_void_p]),
+        "bd_query": (C.c_int, [C.c_void_p]),
         "bd_clear_status": (None, [C.c_void_p]),
         "bd_activation_times": (C.c_int, [C.c_void_p, dp, C.c_int64]),
         "bd_get_fields": (C.c_int, [C.c_void_p, dp, dp, dp]),
@@ -240,6 +242,13 @@ class Simulation:
 
     def sync(self):
         _check(lib().bd_sync(self.h), self.h)
+
+    def ready(self) -> bool:
+        """True when all enqueued steps have completed (never blocks)."""
+        r = lib().bd_query(self.h)
+        if r < 0:
+            _check(r, self.h)
+        return r == 1
 
     def clear_status(self):
         lib().bd_clear_status(self.h)

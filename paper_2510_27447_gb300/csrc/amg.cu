@@ -26,6 +26,7 @@ namespace {
 template <int WMAX>
 __global__ void __launch_bounds__(1024) pcg_amg_kernel(const PcgLaunch a, const AmgDev M) {
   __shared__ double sh[4][32];
+  if (a.gate && *a.gate == 0) return;
   const int n = a.n;
   const int nb = gridDim.x;
   const int stride = blockDim.x * gridDim.x;

@@ -89,7 +89,10 @@ struct bd_state {
   StimTable stim{};
   long long* step_n = nullptr;
   int* d_status = nullptr;
-  long long* d_stats = nullptr;            // [iters_e, solves_e, iters_p, solves_p, outer_e, outer_p]
+  long long* d_stats = nullptr;            // [iters_e, solves_e, iters_p, solves_p, outer_e, outer_p, extra sweeps]
+  int* gate = nullptr;                     // sweep test of Algorithm 2 (sweep_tol > 0)
+  unsigned long long* dmax = nullptr;
+  double* Xsave = nullptr;
   unsigned long long* d_clamps = nullptr;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -267,6 +270,7 @@ PcgLaunch pcg_base(bd_state* s) {
   P.status = s->d_status;
   P.grid = s->pcg_grid;
   P.block = s->pcg_block;
+  P.gate = s->opts.sweep_tol > 0 ? s->gate : nullptr;
   return P;
 }
 
@@ -358,6 +362,7 @@ IonicLaunch ionic_base(bd_state* s, int mode, double dt) {
   L.rl = s->rl;
   L.avec = s->avec;
   L.clamp_count = s->d_clamps;
+  L.gate = s->opts.sweep_tol > 0 ? s->gate : nullptr;
   return L;
 }
 
@@ -400,7 +405,9 @@ int setup_amg(bd_state* s, const HostOps& H) {
   A.v = H.Aie;
   AmgHost AH;
   std::string err;
-  const int rc = amg_build(A, AmgParams{}, &AH, &err);
+  AmgParams prm;
+  if (s->opts.amg_coarse_max > 0) prm.coarse_max = s->opts.amg_coarse_max;
+  const int rc = amg_build(A, prm, &AH, &err);
   if (rc != BD_OK) return fail(s, rc, "%s", err.c_str());
   if (AH.lev.empty()) return BD_OK;   // small operator: Jacobi-PCG is used
   if (int(AH.lev.size()) > kMaxAmgLevels)
@@ -520,6 +527,11 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
   lobatto(M, c);
   integration_matrix(M, S);
   StimTable st = s->stim;
+  const int* gate = s->opts.sweep_tol > 0 ? s->gate : nullptr;
+  if (gate) {
+    Timed t(s, BD_K_COMBINE);
+    CK(launch_set_int(s->gate, 1, s->dmax, s->stream));
+  }
   {
     Timed t(s, BD_K_FIELD);
     CK(launch_field(s->model, s->precision, N, s->Xn, s->inv_cm, dt, s->stim_bits, s->step_n, st, s->fq[0], s->stream));
@@ -530,7 +542,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       RUN(elliptic(s, s->Xn, s->u[M - 1]));
       for (int m = 1; m + 1 < M; ++m) {
         Timed t(s, BD_K_COMBINE);
-        CK(launch_copy(N, s->u[M - 1], s->u[m], s->stream));
+        CK(launch_copy(N, s->u[M - 1], s->u[m], s->stream, gate));
       }
     } else {
       for (int m = 1; m < M; ++m) RUN(elliptic(s, s->Xc[m], s->u[m]));
@@ -574,7 +586,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       {
         Timed t(s, BD_K_COMBINE);
         CK(launch_combine(s->model, N, src, s->k1v, s->z1, s->w1, s->k2v, s->z2, s->w2, 1.5 / gam, 0.5 / gam,
-                          s->Xt[m + 1], s->stream));
+                          s->Xt[m + 1], s->stream, gate));
       }
       s->ionic_evals += 3;
     }
@@ -583,7 +595,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       {
         Timed t(s, BD_K_FIELD);
         CK(launch_field(s->model, s->precision, N, s->Xt[M - 1], s->inv_cm, dt, s->stim_bits, s->step_n, st,
-                        s->fq[M - 1], s->stream));
+                        s->fq[M - 1], s->stream, gate));
       }
       s->ionic_evals += 1;
       for (int m = 0; m + 1 < M; ++m) {
@@ -612,15 +624,23 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
         RUN(parabolic(s, alpha, -1.0 / h, s->avec, 1.0 / h, s->bvec, s->k1v));
         {
           Timed t(s, BD_K_COMBINE);
-          CK(launch_update(s->model, N, s->Xt[m + 1], s->k1v, s->z1, s->w1, s->Xc[m + 1], s->stream));
+          CK(launch_update(s->model, N, s->Xt[m + 1], s->k1v, s->z1, s->w1, s->Xc[m + 1], s->stream, gate));
         }
         s->ionic_evals += 1;
       }
     } else {
       for (int m = 1; m < M; ++m) {
         Timed t(s, BD_K_COMBINE);
-        CK(launch_copy(int64_t(ns) * N, s->Xt[m], s->Xc[m], s->stream));
+        CK(launch_copy(int64_t(ns) * N, s->Xt[m], s->Xc[m], s->stream, gate));
       }
+    }
+    // Algorithm 2's test: stop the sweeps once max |X^k - X^(k-1)| < sweep_tol
+    if (gate && k < K) {
+      Timed t(s, BD_K_COMBINE, 4);
+      CK(cudaMemsetAsync(s->dmax, 0, 8, s->stream));
+      CK(launch_sweep_delta(int64_t(ns) * N, s->Xc[M - 1], k == 1 ? s->Xn : s->Xsave, s->dmax, gate, s->stream));
+      CK(launch_sweep_gate(s->dmax, s->opts.sweep_tol, s->gate, s->d_stats + 6, s->stream));
+      CK(launch_copy(int64_t(ns) * N, s->Xc[M - 1], s->Xsave, s->stream, gate));
     }
   }
   {
@@ -723,6 +743,10 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     delete s;
     return fail(nullptr, BD_ERR_ARG, "pin_node out of range");
   }
+  if (!(s->opts.sweep_tol >= 0.0)) {
+    delete s;
+    return fail(nullptr, BD_ERR_ARG, "sweep_tol must be >= 0");
+  }
   if (s->opts.precision != BD_FP64 && s->opts.precision != BD_MIXED) {
     delete s;
     return fail(nullptr, BD_ERR_ARG, "unknown precision");
@@ -823,6 +847,8 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   const int64_t want = s->opts.cg_grid > 0 ? s->opts.cg_grid : (N + s->pcg_block - 1) / s->pcg_block;
   s->pcg_grid = int(std::max<int64_t>(1, std::min<int64_t>(want, s->pcg_max)));
   if (ok) ok = alloc_n(s, &s->cg_part, int64_t(s->pcg_max) * 4);
+  if (ok && s->opts.sweep_tol > 0)
+    ok = alloc_n(s, &s->gate, 1) && alloc_n(s, &s->dmax, 1) && alloc_n(s, &s->Xsave, ns * N);
   if (ok && s->precision == BD_MIXED) {
     ok = alloc_n(s, &s->fAie, s->ell_n) && alloc_n(s, &s->r32, N) && alloc_n(s, &s->z32, N) &&
          alloc_n(s, &s->p32, N) && alloc_n(s, &s->q32, N) && alloc_n(s, &s->invd32, N) &&
@@ -956,6 +982,14 @@ int bd_sync(bd_state_t* s) {
   return read_status(s);
 }
 
+int bd_query(bd_state_t* s) {
+  if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
+  const cudaError_t e = cudaStreamQuery(s->stream);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) return 0;
+  return fail(s, BD_ERR_CUDA, "cudaStreamQuery: %s", cudaGetErrorString(e));
+}
+
 void bd_clear_status(bd_state_t* s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
@@ -1049,13 +1083,13 @@ size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts
 int bd_get_stats(const bd_state_t* cs, bd_stats_t* out) {
   bd_state* s = const_cast<bd_state*>(cs);
   if (!s || !out) return fail(s, BD_ERR_ARG, "NULL argument");
-  long long st[4];
+  long long st[7];
   unsigned long long cl = 0;
   CK(cudaStreamSynchronize(s->stream));
-  CK(cudaMemcpy(st, s->d_stats, 32, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(st, s->d_stats, 56, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&cl, s->d_clamps, 8, cudaMemcpyDeviceToHost));
   out->steps = s->steps;
-  out->sweeps = s->sweeps;
+  out->sweeps = s->opts.sweep_tol > 0 ? s->steps + st[6] : s->sweeps;
   out->cg_iters_e = st[0];
   out->cg_solves_e = st[1];
   out->cg_iters_p = st[2];

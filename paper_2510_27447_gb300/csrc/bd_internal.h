@@ -66,18 +66,26 @@ struct IonicLaunch {
   double* bvec;              // out: vector multiplied by M in the rhs
   double* fq_out;            // out (optional): node field at the F point
   unsigned long long* clamp_count;
+  const int* gate;           // optional: kernel does nothing when *gate == 0 (sweep test)
 };
 
 // launchers (ionic.cu)
 cudaError_t launch_ionic(const IonicLaunch& L, cudaStream_t st);
 cudaError_t launch_field(int model, int precision, int64_t n, const double* X, double inv_cm, double dt,
                          const uint32_t* stim_bits, const long long* step_n, const StimTable& stim,
-                         double* fout, cudaStream_t st);
+                         double* fout, cudaStream_t st, const int* gate = nullptr);
 cudaError_t launch_combine(int model, int64_t n, const double* src, const double* k1v, const double* z1,
                            const double* w1, const double* k2v, const double* z2, const double* w2, double m1,
-                           double m2, double* dst, cudaStream_t st);
+                           double m2, double* dst, cudaStream_t st, const int* gate = nullptr);
 cudaError_t launch_update(int model, int64_t n, const double* Xt, const double* ev, const double* z,
-                          const double* w, double* dst, cudaStream_t st);
+                          const double* w, double* dst, cudaStream_t st, const int* gate = nullptr);
+// sweep test of Algorithm 2: dmax = max |a - b| (dmax reset by the caller),
+// then gate = (dmax >= tol) and, while open, sweeps += 1
+cudaError_t launch_sweep_delta(int64_t n, const double* a, const double* b, unsigned long long* dmax,
+                               const int* gate, cudaStream_t st);
+cudaError_t launch_sweep_gate(const unsigned long long* dmax, double tol, int* gate, long long* sweeps,
+                              cudaStream_t st);
+cudaError_t launch_set_int(int* p, int v, unsigned long long* clear, cudaStream_t st);
 cudaError_t launch_finish(int ns, int64_t n, double* Xn, const double* Xlast, double* u0, const double* ulast,
                           double* t_act, double v_act, double dt, long long* step_n, int* status,
                           cudaStream_t st);
@@ -124,6 +132,7 @@ struct PcgLaunch {
   long long* iters_acc;
   long long* solves_acc;
   long long* outer_acc;     // FP64 residual passes (mixed kernel)
+  const int* gate;          // optional: the solve is skipped when *gate == 0
   int grid;                 // co-resident blocks
   int block;
 };
@@ -131,7 +140,7 @@ cudaError_t launch_pcg(const PcgLaunch& P, int wmax, cudaStream_t st);
 int pcg_max_blocks(int block, int wmax);
 cudaError_t launch_axpby_vals(int64_t nnz, double a, const double* X, double b, const double* Y, double* out,
                               cudaStream_t st);
-cudaError_t launch_copy(int64_t n, const double* src, double* dst, cudaStream_t st);
+cudaError_t launch_copy(int64_t n, const double* src, double* dst, cudaStream_t st, const int* gate = nullptr);
 
 // ---- algebraic multigrid (amg.cpp host setup, amg.cu device V-cycle) -------
 struct HCsr {                      // host CSR, n x m
@@ -142,7 +151,7 @@ struct HCsr {                      // host CSR, n x m
 };
 struct AmgParams {
   double theta = 0.08;             // strength-of-connection threshold
-  int64_t coarse_max = 400;        // rows of the dense coarsest solve
+  int64_t coarse_max = 1500;       // rows of the dense coarsest solve
   int max_levels = 9;
 };
 struct AmgHostLevel {

@@ -7,6 +7,7 @@
 // (Eq. (3.13)) or of the SDC correction (Eq. (3.20)), leaving one condensed
 // unknown per node for the parabolic CG solve.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <utility>
 
 #include "bd_internal.h"
@@ -53,6 +54,7 @@ __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, cons
   constexpr int NS = Mod::NS;
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= L.n) return;
+  if (L.gate && *L.gate == 0) return;
   const int64_t n = L.n;
   const double t = double(*L.step_n) * L.dt;
   const double istim = stim_current(L.stim_bits, i, L.stim, t, L.dt);
@@ -143,11 +145,13 @@ __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, cons
 template <template <class> class Model, class T>
 __global__ void __launch_bounds__(kBlock) field_kernel(int64_t n, const double* X, double inv_cm, double dt,
                                                        const uint32_t* stim_bits, const long long* step_n,
-                                                       const StimTable stim, double* fout, const Model<T> P) {
+                                                       const StimTable stim, double* fout, const Model<T> P,
+                                                       const int* gate) {
   using Mod = Model<T>;
   constexpr int NS = Mod::NS;
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (gate && *gate == 0) return;
   const double t = step_n ? double(*step_n) * dt : 0.0;
   const double istim = stim_current(stim_bits, i, stim, t, dt);
   T x[NS];
@@ -164,9 +168,10 @@ template <int NS>
 __global__ void __launch_bounds__(kBlock) combine_kernel(int64_t n, const double* src, const double* k1v,
                                                          const double* z1, const double* w1, const double* k2v,
                                                          const double* z2, const double* w2, double m1, double m2,
-                                                         double* dst) {
+                                                         double* dst, const int* gate) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (gate && *gate == 0) return;
   const double a = k1v[i], b = k2v[i];
   dst[i] = src[i] + m1 * a + m2 * b;
 #pragma unroll
@@ -181,9 +186,11 @@ __global__ void __launch_bounds__(kBlock) combine_kernel(int64_t n, const double
 // X^new_{m+1} = X~_{m+1} + eps, eps_y = z + w eps_v
 template <int NS>
 __global__ void __launch_bounds__(kBlock) update_kernel(int64_t n, const double* Xt, const double* ev,
-                                                        const double* z, const double* w, double* dst) {
+                                                        const double* z, const double* w, double* dst,
+                                                        const int* gate) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (gate && *gate == 0) return;
   const double e = ev[i];
   dst[i] = Xt[i] + e;
 #pragma unroll
@@ -211,6 +218,31 @@ __global__ void __launch_bounds__(256) finish_kernel(int ns, int64_t n, double* 
 }
 
 __global__ void bump_kernel(long long* step_n) { *step_n += 1; }
+
+__global__ void sweep_delta_kernel(int64_t n, const double* a, const double* b, unsigned long long* dmax,
+                                   const int* gate) {
+  if (gate && *gate == 0) return;
+  double m = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    m = fmax(m, fabs(a[i] - b[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  // non-negative doubles order like their bit patterns: the maximum is exact
+  // and independent of the order of the updates
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(dmax, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void sweep_gate_kernel(const unsigned long long* dmax, double tol, int* gate, long long* sweeps) {
+  if (*gate == 0) return;
+  const double d = __longlong_as_double((long long)*dmax);
+  if (d < tol) *gate = 0;
+  else *sweeps += 1;
+}
+
+__global__ void set_int_kernel(int* p, int v, unsigned long long* clear) {
+  *p = v;
+  if (clear) *clear = 0ull;
+}
 
 template <template <class> class Model, class T>
 cudaError_t launch_ionic_t(const IonicLaunch& L, cudaStream_t st) {
@@ -244,37 +276,37 @@ cudaError_t launch_ionic(const IonicLaunch& L, cudaStream_t st) {
 
 cudaError_t launch_field(int model, int precision, int64_t n, const double* X, double inv_cm, double dt,
                          const uint32_t* stim_bits, const long long* step_n, const StimTable& stim, double* fout,
-                         cudaStream_t st) {
+                         cudaStream_t st, const int* gate) {
   if (n == 0) return cudaSuccess;
   const unsigned grid = unsigned((n + kBlock - 1) / kBlock);
   const bool f32 = precision == BD_MIXED;
   if (model == BD_TP06_EPI) {
-    if (f32) field_kernel<TP06, float><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, TP06<float>::make());
-    else field_kernel<TP06, double><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, TP06<double>::make());
+    if (f32) field_kernel<TP06, float><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, TP06<float>::make(), gate);
+    else field_kernel<TP06, double><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, TP06<double>::make(), gate);
   } else {
     const bool pm = model == BD_LR91_PAPER_MOD;
-    if (f32) field_kernel<LR91, float><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, LR91<float>::make(pm));
-    else field_kernel<LR91, double><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, LR91<double>::make(pm));
+    if (f32) field_kernel<LR91, float><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, LR91<float>::make(pm), gate);
+    else field_kernel<LR91, double><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, LR91<double>::make(pm), gate);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_combine(int model, int64_t n, const double* src, const double* k1v, const double* z1,
                            const double* w1, const double* k2v, const double* z2, const double* w2, double m1,
-                           double m2, double* dst, cudaStream_t st) {
+                           double m2, double* dst, cudaStream_t st, const int* gate) {
   if (n == 0) return cudaSuccess;
   const unsigned grid = unsigned((n + kBlock - 1) / kBlock);
-  if (model == BD_TP06_EPI) combine_kernel<19><<<grid, kBlock, 0, st>>>(n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst);
-  else combine_kernel<8><<<grid, kBlock, 0, st>>>(n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst);
+  if (model == BD_TP06_EPI) combine_kernel<19><<<grid, kBlock, 0, st>>>(n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst, gate);
+  else combine_kernel<8><<<grid, kBlock, 0, st>>>(n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst, gate);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update(int model, int64_t n, const double* Xt, const double* ev, const double* z,
-                          const double* w, double* dst, cudaStream_t st) {
+                          const double* w, double* dst, cudaStream_t st, const int* gate) {
   if (n == 0) return cudaSuccess;
   const unsigned grid = unsigned((n + kBlock - 1) / kBlock);
-  if (model == BD_TP06_EPI) update_kernel<19><<<grid, kBlock, 0, st>>>(n, Xt, ev, z, w, dst);
-  else update_kernel<8><<<grid, kBlock, 0, st>>>(n, Xt, ev, z, w, dst);
+  if (model == BD_TP06_EPI) update_kernel<19><<<grid, kBlock, 0, st>>>(n, Xt, ev, z, w, dst, gate);
+  else update_kernel<8><<<grid, kBlock, 0, st>>>(n, Xt, ev, z, w, dst, gate);
   return cudaGetLastError();
 }
 
@@ -286,6 +318,25 @@ cudaError_t launch_finish(int ns, int64_t n, double* Xn, const double* Xlast, do
     finish_kernel<<<grid, 256, 0, st>>>(ns, n, Xn, Xlast, u0, ulast, t_act, v_act, dt, step_n, status);
   }
   bump_kernel<<<1, 1, 0, st>>>(step_n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_delta(int64_t n, const double* a, const double* b, unsigned long long* dmax,
+                               const int* gate, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = unsigned(std::min<int64_t>((n + 255) / 256, 4096));
+  sweep_delta_kernel<<<grid, 256, 0, st>>>(n, a, b, dmax, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_gate(const unsigned long long* dmax, double tol, int* gate, long long* sweeps,
+                              cudaStream_t st) {
+  sweep_gate_kernel<<<1, 1, 0, st>>>(dmax, tol, gate, sweeps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_int(int* p, int v, unsigned long long* clear, cudaStream_t st) {
+  set_int_kernel<<<1, 1, 0, st>>>(p, v, clear);
   return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(1024) pcg_mixed_kernel(const PcgLaunch a, cons
                                                           float* partf) {
   __shared__ double shd[4][32];
   __shared__ float shf[4][32];
+  if (a.gate && *a.gate == 0) return;
   const int n = a.n;
   const int nb = gridDim.x;
   const int stride = blockDim.x * gridDim.x;

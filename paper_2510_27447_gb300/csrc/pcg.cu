@@ -32,6 +32,7 @@ namespace {
 template <int WMAX>
 __global__ void __launch_bounds__(1024) pcg_kernel(const PcgLaunch a) {
   __shared__ double sh[4][32];
+  if (a.gate && *a.gate == 0) return;   // same value for every block: all skip together
   const int n = a.n;
   const int nb = gridDim.x;
   const int stride = blockDim.x * gridDim.x;
@@ -178,8 +179,9 @@ __global__ void axpby_kernel(int64_t n, double a, const double* X, double b, con
   if (i < n) out[i] = a * X[i] + b * Y[i];
 }
 
-__global__ void copy_kernel(int64_t n, const double* src, double* dst) {
+__global__ void copy_kernel(int64_t n, const double* src, double* dst, const int* gate) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (gate && *gate == 0) return;
   if (i < n) dst[i] = src[i];
 }
 
@@ -231,9 +233,9 @@ cudaError_t launch_axpby_vals(int64_t n, double a, const double* X, double b, co
   return cudaGetLastError();
 }
 
-cudaError_t launch_copy(int64_t n, const double* src, double* dst, cudaStream_t st) {
+cudaError_t launch_copy(int64_t n, const double* src, double* dst, cudaStream_t st, const int* gate) {
   if (n == 0) return cudaSuccess;
-  copy_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(n, src, dst);
+  copy_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(n, src, dst, gate);
   return cudaGetLastError();
 }
 

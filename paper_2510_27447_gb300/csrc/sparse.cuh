@@ -13,32 +13,39 @@ namespace bd {
 #endif
 constexpr long long kSpinLimit = 1ll << 26;   // bounded wait: about a second of polling
 
-// sense-free generation barrier: bar[0] = arrivals, bar[1] = generation
+// Device-wide barrier on one arrival word: block 0 adds 2^31 - (nblocks - 1),
+// every other block adds 1, so the word's top bit flips exactly when the last
+// block of a round arrives and the low bits return to their old value (no
+// reset step).  Arrival is a release RMW (publishes the block's writes), the
+// wait an acquire load (sees every arriving block's writes).  The wait is
+// bounded: on timeout the kernel records ST_TIMEOUT and the caller returns.
+__device__ __forceinline__ unsigned bar_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned bar_add_acq_rel(unsigned* p, unsigned x) {
+  unsigned v;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "r"(x) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g0 = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u);
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (nblocks - 1u) : 1u;
+    const unsigned old = bar_add_acq_rel(bar, add);
     ok = 1;
-    if (arrived == nblocks - 1u) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long spins = 0;
-      while (*gen == g0) {
-        if (BD_PCG_SLEEP_NS > 0) __nanosleep(BD_PCG_SLEEP_NS);
-        if (++spins > kSpinLimit) {
-          atomicOr(status, ST_TIMEOUT);
-          ok = 0;
-          break;
-        }
+    long long spins = 0;
+    while (((old ^ bar_ld_acquire(bar)) & 0x80000000u) == 0u) {
+      if (BD_PCG_SLEEP_NS > 0) __nanosleep(BD_PCG_SLEEP_NS);
+      if (++spins > kSpinLimit) {
+        atomicOr(status, ST_TIMEOUT);
+        ok = 0;
+        break;
       }
     }
-    __threadfence();
   }
   __syncthreads();
   return ok != 0;

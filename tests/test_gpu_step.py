@@ -140,3 +140,27 @@ def test_invalid_inputs_and_iteration_cap_are_reported():
     sim.clear_status()
     sim.sync()
     sim.close()
+
+
+def test_sweep_tolerance_matches_oracle():
+    """Algorithm 2's stopping test ||X^k - X^(k-1)|| < tol (max norm, last
+    Lobatto node), decided on the device: same sweep counts and states as the
+    oracle with the same tolerance."""
+    w = W.sheet(15, 0.3, W.LR91_PAPER_MOD, 0.05, 12, strip=0.05)
+    X0 = rest_X(w)
+    P = oracle_problem(w)
+    X, u = X0.copy(), np.zeros(w.n_nodes)
+    sweeps = 0
+    for n in range(12):
+        X, u, k = P.step(X, u, n * w.dt, w.dt, 3, 6, True, sweep_tol=1e-3)
+        sweeps += k
+    sim = gpu_sim(w, sweep_tol=1e-3, **TIGHT)
+    sim.set_initial(X0)
+    for _ in range(12):
+        sim.step(w.dt, 3, 6)
+    v, ug, Xg = sim.fields(full=True)
+    st = sim.stats()
+    sim.close()
+    assert 12 < sweeps < 72                 # the test stopped some, not all, steps early
+    assert st["sweeps"] == sweeps
+    assert rel(Xg, X) < 1e-10 and rel(ug, u) < 1e-8

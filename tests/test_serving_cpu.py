@@ -1,0 +1,73 @@
+"""Scheduler logic of the continuous-batching server (no GPU): admission by
+free slot and HBM footprint, FIFO order, overlap of admitted requests,
+completion accounting and latency statistics."""
+import numpy as np
+import pytest
+
+from paper_2510_27447_gb300 import serving as S
+from paper_2510_27447_gb300 import workloads as W
+
+
+def _jobs(n, rate, seed, sizes=(1089, 4225, 16641)):
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for r in range(n):
+        t += rng.exponential(1.0 / rate)
+        out.append(S.Job(r, t, int(sizes[rng.integers(0, len(sizes))]), 200))
+    return out
+
+
+def test_every_request_completes_once_with_positive_latency():
+    ex = S.VirtualExecutor(rate=2e8)
+    done = S.Server(ex, max_slots=4, hbm_budget=10**9, chunk_steps=25).run(_jobs(40, 50.0, 1))
+    assert sorted(c.rid for c in done) == list(range(40))
+    for c in done:
+        assert c.finished >= c.admitted >= c.arrival
+    s = S.summarize(done)
+    assert s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_slots_and_memory_bound_the_resident_set():
+    ex = S.VirtualExecutor(rate=1e8, bytes_per_node=1000)
+    jobs = [S.Job(r, 0.0, 16641, 100) for r in range(10)]
+    # budget fits two 16641-node requests at a time although 6 slots are free
+    done = S.Server(ex, max_slots=6, hbm_budget=2 * 16641 * 1000, chunk_steps=20).run(jobs)
+    assert len(done) == 10
+    assert ex.max_live == 2
+
+
+def test_fifo_admission_and_overlap():
+    ex = S.VirtualExecutor(rate=1e8)
+    jobs = [S.Job(r, 0.001 * r, 4225, 100) for r in range(8)]
+    done = S.Server(ex, max_slots=3, hbm_budget=10**12, chunk_steps=10).run(jobs)
+    assert ex.started == list(range(8))          # admitted in arrival order
+    assert ex.max_live == 3                      # requests overlap up to the slot count
+    # with processor sharing, three resident requests finish later than one alone
+    first = min(done, key=lambda c: c.rid)
+    assert first.latency > 4225 * 100 / 1e8
+
+
+def test_request_larger_than_budget_is_refused():
+    ex = S.VirtualExecutor(bytes_per_node=1000)
+    with pytest.raises(ValueError):
+        S.Server(ex, max_slots=2, hbm_budget=1000).run([S.Job(0, 0.0, 5000, 10)])
+
+
+def test_idle_gaps_advance_the_clock_to_the_next_arrival():
+    ex = S.VirtualExecutor(rate=1e9)
+    jobs = [S.Job(0, 0.0, 1089, 10), S.Job(1, 5.0, 1089, 10)]
+    done = S.Server(ex, max_slots=2, hbm_budget=10**9).run(jobs)
+    late = [c for c in done if c.rid == 1][0]
+    assert late.admitted >= 5.0 and late.latency < 0.1
+
+
+def test_request_stream_workloads_are_well_formed():
+    reqs = W.request_stream(16, 40.0, seed=4, t_end=2.0)
+    assert all(r.side in (33, 65, 129, 257, 513) for r in reqs)
+    assert all(250 <= r.s2_time <= 350 for r in reqs)
+    times = [r.arrival_s for r in reqs]
+    assert times == sorted(times)
+    w = W.request_workload(reqs[0])
+    assert w.n_nodes == reqs[0].side ** 2 and w.n_steps == 100
+    assert w.stimuli[0].mask.sum() > 0
