@@ -293,12 +293,10 @@ def run_ours(args) -> None:
             torch.cuda.synchronize()
             sim.sync()
             st1 = sim.stats()
-            total = torch.tensor([sum(ms)], dtype=torch.float64, device="cuda")
-            if dist:
-                dist.all_reduce(total, op=dist.ReduceOp.MAX)
-            total_ms = float(total.item())
-            results[name] = {"ms_per_step": total_ms / args.steps,
-                             "value": world * sim.N * args.steps / (total_ms / 1e3),
+            from paper_2510_27447_gb300.replicas import whole_job_rate
+            rate, secs = whole_job_rate(sim.N * args.steps, sum(ms) / 1e3, device="cuda")
+            results[name] = {"ms_per_step": secs * 1e3 / args.steps,
+                             "value": rate,
                              "clocks": clk.summary(),
                              "launches": st1["kernel_launches"] - st0["kernel_launches"],
                              "cg_iters_e": (st1["cg_iters_e"] - st0["cg_iters_e"]) / max(1, st1["cg_solves_e"] - st0["cg_solves_e"]),
