@@ -330,11 +330,20 @@ namespace bd {
 SellHost sell_from_csr(const HCsr& A) {
   SellHost S;
   S.n = A.n;
+  int64_t maxw = 0;
+  for (int64_t i = 0; i < A.n; ++i) maxw = std::max(maxw, A.rp[i + 1] - A.rp[i]);
+  if (maxw > 32) {
+    // long rows (coarse operators, restrictions in 3-D): CSR, one warp per row
+    S.rp = A.rp;
+    S.col.assign(A.ci.begin(), A.ci.end());
+    S.val = A.v;
+    S.wmax = -1;
+    return S;
+  }
   const int64_t nsl = (A.n + 31) / 32;
   S.sptr.resize(nsl);
   S.sw.resize(nsl);
   int64_t off = 0;
-  int maxw = 0;
   for (int64_t sl = 0; sl < nsl; ++sl) {
     int w = 0;
     for (int64_t i = sl * 32; i < std::min<int64_t>(A.n, sl * 32 + 32); ++i)
@@ -342,7 +351,6 @@ SellHost sell_from_csr(const HCsr& A) {
     S.sw[sl] = w;
     S.sptr[sl] = off;
     off += 32 * int64_t(w);
-    maxw = std::max(maxw, w);
   }
   S.col.assign(off, 0);
   S.val.assign(off, 0.0);
@@ -353,7 +361,7 @@ SellHost sell_from_csr(const HCsr& A) {
       S.val[base + 32 * k] = A.v[A.rp[i] + k];
     }
   }
-  S.wmax = maxw <= 8 ? 8 : maxw <= 16 ? 16 : maxw <= 32 ? 32 : maxw <= 64 ? 64 : 0;
+  S.wmax = maxw <= 8 ? 8 : maxw <= 16 ? 16 : 32;
   return S;
 }
 

@@ -421,12 +421,15 @@ int setup_amg(bd_state* s, const HostOps& H) {
     const SellHost S = sell_from_csr(M);
     out->n = int(S.n);
     out->wmax = S.wmax;
-    out->sptr = static_cast<const int64_t*>(upload(S.sptr.data(), S.sptr.size() * 8));
-    out->sw = static_cast<const int*>(upload(S.sw.data(), S.sw.size() * 4));
+    const bool csr = !S.rp.empty();
+    out->rp = csr ? static_cast<const int64_t*>(upload(S.rp.data(), S.rp.size() * 8)) : nullptr;
+    out->sptr = csr ? nullptr : static_cast<const int64_t*>(upload(S.sptr.data(), S.sptr.size() * 8));
+    out->sw = csr ? nullptr : static_cast<const int*>(upload(S.sw.data(), S.sw.size() * 4));
     out->col = static_cast<const int*>(upload(S.col.data(), S.col.size() * 4));
     out->val = static_cast<const double*>(upload(S.val.data(), S.val.size() * 8));
     // the host vectors die with S: wait for the copies
-    return out->sptr && out->sw && out->col && out->val && cudaStreamSynchronize(s->stream) == cudaSuccess;
+    return (csr ? out->rp != nullptr : (out->sptr && out->sw)) && out->col && out->val &&
+           cudaStreamSynchronize(s->stream) == cudaSuccess;
   };
   AmgDev& M = s->amg;
   M.nlev = int(AH.lev.size());
@@ -435,7 +438,7 @@ int setup_amg(bd_state* s, const HostOps& H) {
     AmgLevelDev& Ld = M.L[l];
     bool ok = true;
     if (l == 0) {
-      Ld.A = SellDev{int(s->N), s->wmax, s->sptr, s->swidth, s->col, s->Aie};
+      Ld.A = SellDev{int(s->N), s->wmax, s->sptr, s->swidth, s->col, s->Aie, nullptr};
     } else {
       ok = sell_dev(Lh.A, &Ld.A);
     }
@@ -458,11 +461,14 @@ int setup_amg(bd_state* s, const HostOps& H) {
       std::vector<float> fv(S.val.begin(), S.val.end());
       out->n = int(S.n);
       out->wmax = S.wmax;
-      out->sptr = static_cast<const int64_t*>(upload(S.sptr.data(), S.sptr.size() * 8));
-      out->sw = static_cast<const int*>(upload(S.sw.data(), S.sw.size() * 4));
+      const bool csr = !S.rp.empty();
+      out->rp = csr ? static_cast<const int64_t*>(upload(S.rp.data(), S.rp.size() * 8)) : nullptr;
+      out->sptr = csr ? nullptr : static_cast<const int64_t*>(upload(S.sptr.data(), S.sptr.size() * 8));
+      out->sw = csr ? nullptr : static_cast<const int*>(upload(S.sw.data(), S.sw.size() * 4));
       out->col = static_cast<const int*>(upload(S.col.data(), S.col.size() * 4));
       out->val = static_cast<const float*>(upload(fv.data(), fv.size() * 4));
-      return out->sptr && out->sw && out->col && out->val && cudaStreamSynchronize(s->stream) == cudaSuccess;
+      return (csr ? out->rp != nullptr : (out->sptr && out->sw)) && out->col && out->val &&
+             cudaStreamSynchronize(s->stream) == cudaSuccess;
     };
     AmgDevF& F = s->amgf;
     F.nlev = M.nlev;
@@ -470,7 +476,7 @@ int setup_amg(bd_state* s, const HostOps& H) {
       const AmgHostLevel& Lh = AH.lev[l];
       AmgLevelDevT<float>& Ld = F.L[l];
       bool ok = true;
-      if (l == 0) Ld.A = SellDevT<float>{int(s->N), s->wmax, s->sptr, s->swidth, s->col, s->fAie};
+      if (l == 0) Ld.A = SellDevT<float>{int(s->N), s->wmax, s->sptr, s->swidth, s->col, s->fAie, nullptr};
       else ok = sell_devf(Lh.A, &Ld.A);
       ok = ok && sell_devf(Lh.P, &Ld.P) && sell_devf(Lh.R, &Ld.R);
       std::vector<float> fid(Lh.invdiag.begin(), Lh.invdiag.end());

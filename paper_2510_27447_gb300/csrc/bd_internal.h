@@ -172,7 +172,8 @@ struct SellHost {
   std::vector<int> sw;
   std::vector<int> col;
   std::vector<double> val;
-  int wmax = 0;                    // 8, 16, 32, 64 or 0 (looped rows)
+  int wmax = 0;                    // 8, 16 or 32 (SELL, thread per row)
+  std::vector<int64_t> rp;         // non-empty: CSR layout, one warp per row (rows longer than 32)
 };
 SellHost sell_from_csr(const HCsr& A);
 
@@ -185,6 +186,7 @@ struct SellDevT {
   const int* sw;
   const int* col;
   const T* val;
+  const int64_t* rp;               // non-null: CSR (col/val row-major), one warp per row
 };
 template <class T>
 struct AmgLevelDevT {
