@@ -174,6 +174,22 @@ int bd_set_initial(bd_state_t* s, const double* X, const double* u);
  * that was read back (bd_sync waits and reads it). */
 int bd_step(bd_state_t* s, double dt_ms, int n_sdc_nodes, int n_sweeps);
 
+/* Adaptive step (the paper's production mode, Sec. 3.3.2 and Sec. 4.3: the
+ * embedded ROS2 solution X_hat = X + k1/gamma of Eq. (3.14) determines the
+ * future step, at most dt_max).  Error estimate: the maximum, over the last
+ * sweep's ROS2 sub-steps, nodes and state variables, of
+ * |X_new - X_hat| / (tol (1 + |X_new|)).  err <= 1 accepts the step (also at
+ * the smallest step dt_max 2^-7); otherwise X^n is restored and the step is
+ * repeated with a smaller step.  The next step is dt * min(2, max(0.5,
+ * 0.9 err^-1/2)) rounded down to the ladder dt_max 2^-k, k = 0..7 (one CUDA
+ * graph per rung).  Synchronises once per attempt.  Outputs (each may be
+ * NULL): the step taken, its error estimate, the number of rejections. */
+int bd_step_adaptive(bd_state_t* s, double dt_max, double tol, int n_sdc_nodes, int n_sweeps,
+                     double* dt_taken, double* err, int* rejected);
+
+/* Simulated time t^n (ms) and number of completed steps (each may be NULL). */
+int bd_get_time(const bd_state_t* s, double* t_ms, int64_t* steps);
+
 /* Advance several handles by one step each (one launch sequence per handle
  * on the first handle's stream; the handles must share one device). */
 int bd_batch_step(bd_state_t* const* states, int n, double dt_ms, int n_sdc_nodes, int n_sweeps);
@@ -199,8 +215,8 @@ int bd_get_fields(const bd_state_t* s, double* vm, double* phie, double* X);
  * a host copy (valid until bd_destroy). */
 int bd_device_fields(const bd_state_t* s, const double** X_dev, const double** u_dev);
 
-/* Serialise (X, u, step counter, activation times) to host memory.  With
- * buf == NULL only *bytes is set. */
+/* Serialise (X, u, step counter, simulated time, adaptive step, activation
+ * times) to host memory.  With buf == NULL only *bytes is set. */
 int bd_get_state(const bd_state_t* s, void* buf, size_t* bytes);
 int bd_set_state(bd_state_t* s, const void* buf, size_t bytes);
 

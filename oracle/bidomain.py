@@ -150,6 +150,8 @@ class Bidomain:
         self.keep = keep
         self.ell_lu = spla.splu(self.ops.A_ie[keep][:, keep].tocsc())
         self.clamp_count = 0
+        self.adaptive_tol = 0.0    # > 0: step() records the embedded error estimate
+        self.last_err = 0.0
 
     # -- data ----------------------------------------------------------------
     def i_stim(self, t: float, dt: float) -> np.ndarray:
@@ -229,7 +231,11 @@ class Bidomain:
         k1 = self.shifted_solve(alpha, j, self.F(X, u, istim))
         r2 = self.F(X + k1 / GAMMA, u, istim) - (2.0 / (GAMMA * h)) * self.Mt(k1)
         k2 = self.shifted_solve(alpha, j, r2)
-        return X + (1.5 / GAMMA) * k1 + (0.5 / GAMMA) * k2
+        X_new = X + (1.5 / GAMMA) * k1 + (0.5 / GAMMA) * k2
+        # embedded first-order solution X_hat = X + m_hat . k, m_hat = (1/gamma, 0)
+        # (Eq. (3.14)); its distance from X_new is the local error estimate
+        self.last_embedded = X + k1 / GAMMA
+        return X_new
 
     # -- one time step (Algorithm 2) -----------------------------------------
     def step(self, X: np.ndarray, u_n: np.ndarray, t: float, dt: float,
@@ -248,8 +254,13 @@ class Bidomain:
             for m in range(1, M):
                 u[m] = self.elliptic(Xk[m][0])
             Xt = [X]
+            err = 0.0
             for m in range(M - 1):
                 Xt.append(self.ros2(Xt[m], dts[m], u[m + 1], istim))
+                if self.adaptive_tol > 0.0:
+                    E = np.abs(Xt[m + 1] - self.last_embedded)
+                    err = max(err, float(np.max(E / (self.adaptive_tol * (1.0 + np.abs(Xt[m + 1]))))))
+            self.last_err = err
             if correction:
                 Fq = [self.F(Xt[jn], u[jn], istim) for jn in range(M)]
                 new = [X]
@@ -297,6 +308,65 @@ def run(problem: Bidomain, X0: np.ndarray, n_steps: int, dt: float, n_sdc_nodes:
         if callback is not None:
             callback(n + 1, X, u)
     return X, u, t_act
+
+
+# ---------------------------------------------------------------------------
+# adaptive time step from the embedded ROS2 solution (Sec. 3.3.2, Eq. (3.14))
+# ---------------------------------------------------------------------------
+#
+# Reading (the paper states only that the second solution "determines the
+# future time step", with a maximum step of 0.05 ms in its reentry runs):
+#   error   err = max over the last sweep's ROS2 sub-steps, nodes and state
+#           variables of |X_new - X_hat| / (tol (1 + |X_new|))
+#   accept  err <= 1 (or the smallest step of the ladder is reached)
+#   next    dt * min(2, max(0.5, 0.9 err^(-1/2))) (the embedded solution is of
+#           order 1), rounded down to the ladder dt_max 2^-k, k = 0..ladder-1
+#   reject  err > 1: the step is repeated from X^n with the step so chosen
+#           (at least one rung smaller)
+
+def ladder_step(dt_max: float, dt_want: float, ladder: int) -> float:
+    """Largest dt_max 2^-k (k < ladder) not above dt_want (the smallest rung
+    if none is)."""
+    for k in range(ladder):
+        d = dt_max * 0.5 ** k
+        if d <= dt_want * (1.0 + 1e-12):
+            return d
+    return dt_max * 0.5 ** (ladder - 1)
+
+
+def controller_factor(err: float) -> float:
+    if err <= 0.0:
+        return 2.0
+    return min(2.0, max(0.5, 0.9 * err ** -0.5))
+
+
+def run_adaptive(problem: Bidomain, X0: np.ndarray, n_steps: int, dt_max: float, tol: float,
+                 n_sdc_nodes: int = 3, n_sweeps: int = 2, ladder: int = 8, v_act: float = -30.0):
+    """n_steps accepted adaptive steps from X0 (u0 = 0); returns
+    (X, u, t, activation_times, accepted dts, rejections)."""
+    X = np.array(X0, dtype=np.float64, copy=True)
+    u = np.zeros(problem.N)
+    t = 0.0
+    t_act = np.full(problem.N, np.nan)
+    dt = dt_max
+    dts, rejected = [], 0
+    problem.adaptive_tol = tol
+    for _ in range(n_steps):
+        while True:
+            Xn, un, _ = problem.step(X, u, t, dt, n_sdc_nodes, n_sweeps, True)
+            err = problem.last_err
+            smallest = dt <= dt_max * 0.5 ** (ladder - 1) * (1.0 + 1e-12)
+            if err <= 1.0 or smallest:
+                break
+            rejected += 1
+            dt = min(ladder_step(dt_max, dt * controller_factor(err), ladder), dt * 0.5)
+        activation_update(t_act, X[0], Xn[0], t, dt, v_act)
+        X, u = Xn, un
+        t = t + dt
+        dts.append(dt)
+        dt = ladder_step(dt_max, min(dt_max, dt * controller_factor(err)), ladder)
+    problem.adaptive_tol = 0.0
+    return X, u, t, t_act, dts, rejected
 
 
 def conduction_velocity(xyz: np.ndarray, t_act: np.ndarray, y_line: float,

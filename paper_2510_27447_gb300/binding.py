@@ -25,7 +25,8 @@ EXPORTS = ["bd_default_options", "bd_create", "bd_add_stimulus", "bd_set_initial
            "bd_device_fields", "bd_get_state", "bd_set_state", "bd_footprint_bytes", "bd_get_stats",
            "bd_reset_stats", "bd_num_nodes", "bd_num_states", "bd_last_error", "bd_destroy",
            "bd_ionic_eval", "bd_ionic_pattern", "bd_rest_state", "bd_operator_csr",
-           "bd_solve_elliptic", "bd_profile_steps", "bd_solve_elliptic_noalloc", "bd_query"]
+           "bd_solve_elliptic", "bd_profile_steps", "bd_solve_elliptic_noalloc", "bd_query",
+           "bd_step_adaptive", "bd_get_time"]
 
 
 class LibraryMissing(RuntimeError):
@@ -101,6 +102,9 @@ def lib():
         "bd_batch_step": (C.c_int, [P(C.c_void_p), C.c_int, C.c_double, C.c_int, C.c_int]),
         "bd_sync": (C.c_int, [C.c_void_p]),
         "bd_query": (C.c_int, [C.c_void_p]),
+        "bd_step_adaptive": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int, dp, dp,
+                                       P(C.c_int)]),
+        "bd_get_time": (C.c_int, [C.c_void_p, dp, P(C.c_int64)]),
         "bd_clear_status": (None, [C.c_void_p]),
         "bd_activation_times": (C.c_int, [C.c_void_p, dp, C.c_int64]),
         "bd_get_fields": (C.c_int, [C.c_void_p, dp, dp, dp]),
@@ -242,6 +246,22 @@ class Simulation:
 
     def sync(self):
         _check(lib().bd_sync(self.h), self.h)
+
+    def step_adaptive(self, dt_max: float, tol: float, n_sdc_nodes: int = 3, n_sweeps: int = 2):
+        """One accepted adaptive step; returns (dt taken, error estimate, rejections)."""
+        dt = C.c_double(0.0)
+        err = C.c_double(0.0)
+        rej = C.c_int(0)
+        _check(lib().bd_step_adaptive(self.h, float(dt_max), float(tol), int(n_sdc_nodes), int(n_sweeps),
+                                      C.byref(dt), C.byref(err), C.byref(rej)), self.h)
+        return dt.value, err.value, rej.value
+
+    def time(self):
+        """(simulated time in ms, completed steps)."""
+        t = C.c_double(0.0)
+        n = C.c_int64(0)
+        _check(lib().bd_get_time(self.h, C.byref(t), C.byref(n)), self.h)
+        return t.value, n.value
 
     def ready(self) -> bool:
         """True when all enqueued steps have completed (never blocks)."""

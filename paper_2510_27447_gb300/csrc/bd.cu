@@ -96,9 +96,16 @@ struct bd_state {
   unsigned long long* d_clamps = nullptr;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  cudaGraphExec_t gexec = nullptr;
-  double g_dt = 0.0;
-  int g_M = 0, g_K = 0;
+  // one captured graph per step shape (dt, M, K, embedded-error estimate on/off)
+  struct GraphEntry { double dt; int M, K, adapt; cudaGraphExec_t exec; int64_t launches; };
+  std::vector<GraphEntry> graphs;
+  double* t_now = nullptr;                 // simulated time t^n
+  // adaptive stepping (bd_step_adaptive)
+  bool adapt_on = false;                   // the step being enqueued estimates its error
+  double adapt_tol = 1.0;
+  double dt_adapt = 0.0;                   // next step size (0: start at dt_max)
+  unsigned long long* d_err = nullptr;
+  double *Xbak = nullptr, *ubak = nullptr, *tbak = nullptr;
   int pcg_grid = 1, pcg_block = 256, pcg_max = 1;
   std::vector<void*> allocs;
   std::string err;
@@ -159,8 +166,8 @@ void release(bd_state* s) {
     cudaEventDestroy(e.b);
   }
   s->evpool.clear();
-  if (s->gexec) cudaGraphExecDestroy(s->gexec);
-  s->gexec = nullptr;
+  for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
+  s->graphs.clear();
   for (void* p : s->allocs) {
     if (s->opts.free) s->opts.free(p, s->opts.alloc_ctx);
     else cudaFree(p);
@@ -356,7 +363,7 @@ IonicLaunch ionic_base(bd_state* s, int mode, double dt) {
   L.dt = dt;
   L.ML = s->ML;
   L.stim_bits = s->stim_bits;
-  L.step_n = s->step_n;
+  L.t_now = s->t_now;
   L.stim = s->stim;
   L.dgs = s->dgs;
   L.rl = s->rl;
@@ -525,6 +532,21 @@ int setup_amg(bd_state* s, const HostOps& H) {
     if (r_ != BD_OK) return r_;    \
   } while (0)
 
+// adaptive stepping: ladder dt_max 2^-k, k = 0..kAdaptLadder-1, controller
+// factor 0.9 err^(-1/2) clamped to [0.5, 2] (embedded solution of order 1)
+constexpr int kAdaptLadder = 8;
+double ladder_step(double dt_max, double want) {
+  for (int k = 0; k < kAdaptLadder; ++k) {
+    const double d = dt_max * std::ldexp(1.0, -k);
+    if (d <= want * (1.0 + 1e-12)) return d;
+  }
+  return dt_max * std::ldexp(1.0, -(kAdaptLadder - 1));
+}
+double controller_factor(double err) {
+  if (!(err > 0.0)) return 2.0;
+  return std::min(2.0, std::max(0.5, 0.9 / std::sqrt(err)));
+}
+
 int enqueue_step(bd_state* s, double dt, int M, int K) {
   const double gam = 1.0 + 1.0 / std::sqrt(2.0);
   const int64_t N = s->N;
@@ -540,7 +562,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
   }
   {
     Timed t(s, BD_K_FIELD);
-    CK(launch_field(s->model, s->precision, N, s->Xn, s->inv_cm, dt, s->stim_bits, s->step_n, st, s->fq[0], s->stream));
+    CK(launch_field(s->model, s->precision, N, s->Xn, s->inv_cm, dt, s->stim_bits, s->t_now, st, s->fq[0], s->stream));
   }
   for (int k = 1; k <= K; ++k) {
     // ---- elliptic constraint at the nodes m >= 1 ----
@@ -554,6 +576,10 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       for (int m = 1; m < M; ++m) RUN(elliptic(s, s->Xc[m], s->u[m]));
     }
     // ---- ROS2 predictor ----
+    if (s->adapt_on) {   // the estimate is the one of the last sweep that ran
+      Timed t(s, BD_K_COMBINE);
+      CK(launch_clear_gated(s->d_err, gate, s->stream));
+    }
     for (int m = 0; m + 1 < M; ++m) {
       const double h = dt * (c[m + 1] - c[m]);
       const double alpha = 1.0 / (gam * h);
@@ -592,7 +618,8 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       {
         Timed t(s, BD_K_COMBINE);
         CK(launch_combine(s->model, N, src, s->k1v, s->z1, s->w1, s->k2v, s->z2, s->w2, 1.5 / gam, 0.5 / gam,
-                          s->Xt[m + 1], s->stream, gate));
+                          s->Xt[m + 1], s->stream, gate, 1.0 / gam, s->adapt_tol,
+                          s->adapt_on ? s->d_err : nullptr));
       }
       s->ionic_evals += 3;
     }
@@ -600,7 +627,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
     if (s->opts.sdc_correction) {
       {
         Timed t(s, BD_K_FIELD);
-        CK(launch_field(s->model, s->precision, N, s->Xt[M - 1], s->inv_cm, dt, s->stim_bits, s->step_n, st,
+        CK(launch_field(s->model, s->precision, N, s->Xt[M - 1], s->inv_cm, dt, s->stim_bits, s->t_now, st,
                         s->fq[M - 1], s->stream, gate));
       }
       s->ionic_evals += 1;
@@ -652,7 +679,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
   {
     Timed t(s, BD_K_FINISH, 2);
     CK(launch_finish(ns, N, s->Xn, s->Xc[M - 1], s->u[0], s->u[M - 1], s->t_act, s->opts.v_act_mV, dt,
-                     s->step_n, s->d_status, s->stream));
+                     s->step_n, s->t_now, s->d_status, s->stream));
   }
   return BD_OK;
 }
@@ -664,32 +691,37 @@ int do_step(bd_state* s, double dt, int M, int K) {
     RUN(enqueue_step(s, dt, M, K));
     s->launches += s->enq_launches;
   } else {
-    if (!s->gexec || s->g_dt != dt || s->g_M != M || s->g_K != K) {
-      if (s->gexec) {
-        cudaGraphExecDestroy(s->gexec);
-        s->gexec = nullptr;
+    const int adapt = s->adapt_on ? 1 : 0;
+    bd_state::GraphEntry* ge = nullptr;
+    for (auto& g : s->graphs)
+      if (g.dt == dt && g.M == M && g.K == K && g.adapt == adapt) ge = &g;
+    if (!ge) {
+      if (s->graphs.size() >= 16) {   // keep the cache bounded
+        cudaGraphExecDestroy(s->graphs.front().exec);
+        s->graphs.erase(s->graphs.begin());
       }
       cudaGraph_t g = nullptr;
       const int64_t ev0 = s->ionic_evals;
       s->enq_launches = 0;
       CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
       const int r = enqueue_step(s, dt, M, K);
-      s->launches_per_step = s->enq_launches;
+      const int64_t nl = s->enq_launches;
       cudaError_t e = cudaStreamEndCapture(s->stream, &g);
       if (r != BD_OK) {
         if (g) cudaGraphDestroy(g);
         return r;
       }
       if (e != cudaSuccess) return fail(s, BD_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&s->gexec, g, 0);
+      cudaGraphExec_t ex = nullptr;
+      e = cudaGraphInstantiate(&ex, g, 0);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return fail(s, BD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-      s->g_dt = dt;
-      s->g_M = M;
-      s->g_K = K;
+      s->graphs.push_back({dt, M, K, adapt, ex, nl});
+      ge = &s->graphs.back();
       s->ionic_evals = ev0;   // counted per replay below
     }
-    CK(cudaGraphLaunch(s->gexec, s->stream));
+    s->launches_per_step = ge->launches;
+    CK(cudaGraphLaunch(ge->exec, s->stream));
     s->launches += s->launches_per_step;
     s->ionic_evals += int64_t(K) * (3 * (M - 1) + (s->opts.sdc_correction ? M : 0)) + 1;
   }
@@ -699,8 +731,8 @@ int do_step(bd_state* s, double dt, int M, int K) {
 }
 
 void invalidate_graph(bd_state* s) {
-  if (s->gexec) cudaGraphExecDestroy(s->gexec);
-  s->gexec = nullptr;
+  for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
+  s->graphs.clear();
 }
 
 }  // namespace
@@ -833,7 +865,8 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
             alloc_n(s, &s->avec, N) && alloc_n(s, &s->bvec, N) && alloc_n(s, &s->cg_r, N) &&
             alloc_n(s, &s->cg_z, N) && alloc_n(s, &s->cg_p, N) && alloc_n(s, &s->cg_q, N) &&
             alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->t_act, N) && alloc_n(s, &s->stim_bits, N) &&
-            alloc_n(s, &s->step_n, 1) && alloc_n(s, &s->d_status, 1) && alloc_n(s, &s->d_stats, 8) &&
+            alloc_n(s, &s->step_n, 1) && alloc_n(s, &s->t_now, 1) && alloc_n(s, &s->d_err, 1) &&
+            alloc_n(s, &s->d_status, 1) && alloc_n(s, &s->d_stats, 8) &&
             alloc_n(s, &s->d_clamps, 1) && alloc_n(s, &s->bar, 2);
   for (int m = 0; ok && m < kMaxNodes; ++m)
     ok = alloc_n(s, &s->Xt[m], ns * N) && alloc_n(s, &s->Xc[m], ns * N) && alloc_n(s, &s->fq[m], ns * N) &&
@@ -962,6 +995,8 @@ int bd_set_initial(bd_state_t* s, const double* X, const double* u) {
   std::vector<double> nanv(N, std::nan(""));
   CK(cudaMemcpyAsync(s->t_act, nanv.data(), N * 8, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemsetAsync(s->step_n, 0, 8, s->stream));
+  CK(cudaMemsetAsync(s->t_now, 0, 8, s->stream));
+  s->dt_adapt = 0.0;
   CK(cudaStreamSynchronize(s->stream));
   return BD_OK;
 }
@@ -1033,7 +1068,7 @@ int bd_device_fields(const bd_state_t* s, const double** X_dev, const double** u
 int bd_get_state(const bd_state_t* cs, void* buf, size_t* bytes) {
   bd_state* s = const_cast<bd_state*>(cs);
   if (!s || !bytes) return fail(s, BD_ERR_ARG, "NULL argument");
-  const size_t need = 32 + size_t(s->ns + 2) * size_t(s->N) * 8;
+  const size_t need = 48 + size_t(s->ns + 2) * size_t(s->N) * 8;
   if (!buf) {
     *bytes = need;
     return BD_OK;
@@ -1041,10 +1076,12 @@ int bd_get_state(const bd_state_t* cs, void* buf, size_t* bytes) {
   if (*bytes < need) return fail(s, BD_ERR_ARG, "buffer too small (%zu < %zu)", *bytes, need);
   CK(cudaStreamSynchronize(s->stream));
   char* p = static_cast<char*>(buf);
-  int64_t hdr[4] = {0x62647374, s->model, s->N, 0};
+  int64_t hdr[6] = {0x62647375, s->model, s->N, 0, 0, 0};
   CK(cudaMemcpy(&hdr[3], s->step_n, 8, cudaMemcpyDeviceToHost));
-  std::memcpy(p, hdr, 32);
-  p += 32;
+  CK(cudaMemcpy(&hdr[4], s->t_now, 8, cudaMemcpyDeviceToHost));
+  std::memcpy(&hdr[5], &s->dt_adapt, 8);
+  std::memcpy(p, hdr, 48);
+  p += 48;
   CK(cudaMemcpy(p, s->Xn, int64_t(s->ns) * s->N * 8, cudaMemcpyDeviceToHost));
   p += int64_t(s->ns) * s->N * 8;
   CK(cudaMemcpy(p, s->u[0], s->N * 8, cudaMemcpyDeviceToHost));
@@ -1056,14 +1093,14 @@ int bd_get_state(const bd_state_t* cs, void* buf, size_t* bytes) {
 
 int bd_set_state(bd_state_t* s, const void* buf, size_t bytes) {
   if (!s || !buf) return fail(s, BD_ERR_ARG, "NULL argument");
-  const size_t need = 32 + size_t(s->ns + 2) * size_t(s->N) * 8;
+  const size_t need = 48 + size_t(s->ns + 2) * size_t(s->N) * 8;
   if (bytes != need) return fail(s, BD_ERR_ARG, "state blob has %zu bytes, expected %zu", bytes, need);
   const char* p = static_cast<const char*>(buf);
-  int64_t hdr[4];
-  std::memcpy(hdr, p, 32);
-  if (hdr[0] != 0x62647374 || hdr[1] != s->model || hdr[2] != s->N)
+  int64_t hdr[6];
+  std::memcpy(hdr, p, 48);
+  if (hdr[0] != 0x62647375 || hdr[1] != s->model || hdr[2] != s->N)
     return fail(s, BD_ERR_ARG, "state blob belongs to another model or mesh");
-  p += 32;
+  p += 48;
   CK(cudaStreamSynchronize(s->stream));
   CK(cudaMemcpy(s->Xn, p, int64_t(s->ns) * s->N * 8, cudaMemcpyHostToDevice));
   p += int64_t(s->ns) * s->N * 8;
@@ -1071,6 +1108,71 @@ int bd_set_state(bd_state_t* s, const void* buf, size_t bytes) {
   p += s->N * 8;
   CK(cudaMemcpy(s->t_act, p, s->N * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->step_n, &hdr[3], 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->t_now, &hdr[4], 8, cudaMemcpyHostToDevice));
+  std::memcpy(&s->dt_adapt, &hdr[5], 8);
+  return BD_OK;
+}
+
+int bd_get_time(const bd_state_t* cs, double* t, int64_t* steps) {
+  bd_state* s = const_cast<bd_state*>(cs);
+  if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
+  CK(cudaStreamSynchronize(s->stream));
+  if (t) CK(cudaMemcpy(t, s->t_now, 8, cudaMemcpyDeviceToHost));
+  if (steps) CK(cudaMemcpy(steps, s->step_n, 8, cudaMemcpyDeviceToHost));
+  return BD_OK;
+}
+
+int bd_step_adaptive(bd_state_t* s, double dt_max, double tol, int M, int K, double* dt_taken, double* err_out,
+                     int* rejected) {
+  if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
+  if (!(dt_max > 0) || !std::isfinite(dt_max) || !(tol > 0)) return fail(s, BD_ERR_ARG, "dt_max and tol must be positive");
+  if (M != 2 && M != 3) return fail(s, BD_ERR_ARG, "n_sdc_nodes must be 2 or 3");
+  if (K < 1) return fail(s, BD_ERR_ARG, "n_sweeps must be >= 1");
+  const int64_t N = s->N, ns = s->ns;
+  if (!s->Xbak) {
+    if (!alloc_n(s, &s->Xbak, ns * N) || !alloc_n(s, &s->ubak, N) || !alloc_n(s, &s->tbak, N + 4))
+      return fail(s, BD_ERR_OOM, "device allocation failed");
+  }
+  const double dt_min = dt_max * std::ldexp(1.0, -(kAdaptLadder - 1));
+  double dt = s->dt_adapt > 0 ? std::min(s->dt_adapt, dt_max) : dt_max;
+  dt = ladder_step(dt_max, dt);
+  int rej = 0;
+  double err = 0.0;
+  for (;;) {
+    // keep X^n, u^n, activation times and the clock for a possible rejection
+    CK(cudaMemcpyAsync(s->Xbak, s->Xn, ns * N * 8, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->ubak, s->u[0], N * 8, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->tbak, s->t_act, N * 8, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->tbak + N, s->t_now, 8, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->tbak + N + 1, s->step_n, 8, cudaMemcpyDeviceToDevice, s->stream));
+    s->adapt_on = true;
+    s->adapt_tol = tol;
+    const int r = do_step(s, dt, M, K);
+    s->adapt_on = false;
+    if (r != BD_OK) return r;
+    unsigned long long bits = 0;
+    CK(cudaMemcpyAsync(&bits, s->d_err, 8, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    std::memcpy(&err, &bits, 8);
+    const int st = read_status(s);
+    if (st != BD_OK) return st;
+    if (err <= 1.0 || dt <= dt_min * (1.0 + 1e-12)) break;
+    // reject: restore X^n and retry with a smaller step
+    ++rej;
+    CK(cudaMemcpyAsync(s->Xn, s->Xbak, ns * N * 8, cudaMemcpyDeviceToDevice, s->stream));
+    for (int m = 0; m < kMaxNodes; ++m)
+      CK(cudaMemcpyAsync(s->u[m], s->ubak, N * 8, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->t_act, s->tbak, N * 8, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->t_now, s->tbak + N, 8, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->step_n, s->tbak + N + 1, 8, cudaMemcpyDeviceToDevice, s->stream));
+    s->steps -= 1;
+    s->sweeps -= K;
+    dt = std::min(ladder_step(dt_max, dt * controller_factor(err)), 0.5 * dt);
+  }
+  if (dt_taken) *dt_taken = dt;
+  if (err_out) *err_out = err;
+  if (rejected) *rejected = rej;
+  s->dt_adapt = ladder_step(dt_max, std::min(dt_max, dt * controller_factor(err)));
   return BD_OK;
 }
 

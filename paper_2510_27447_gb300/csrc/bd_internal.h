@@ -56,7 +56,7 @@ struct IonicLaunch {
   const double* fq[kMaxNodes];   // correction: stored node fields f(X~_j)
   const double* ML;
   const uint32_t* stim_bits;
-  const long long* step_n;
+  const double* t_now;       // simulated time t^n of the step
   StimTable stim;
   double* dgs;               // out: M_L * s
   double* rl;                // out: node-local part of the condensed rhs
@@ -72,11 +72,12 @@ struct IonicLaunch {
 // launchers (ionic.cu)
 cudaError_t launch_ionic(const IonicLaunch& L, cudaStream_t st);
 cudaError_t launch_field(int model, int precision, int64_t n, const double* X, double inv_cm, double dt,
-                         const uint32_t* stim_bits, const long long* step_n, const StimTable& stim,
+                         const uint32_t* stim_bits, const double* t_now, const StimTable& stim,
                          double* fout, cudaStream_t st, const int* gate = nullptr);
 cudaError_t launch_combine(int model, int64_t n, const double* src, const double* k1v, const double* z1,
                            const double* w1, const double* k2v, const double* z2, const double* w2, double m1,
-                           double m2, double* dst, cudaStream_t st, const int* gate = nullptr);
+                           double m2, double* dst, cudaStream_t st, const int* gate = nullptr, double mhat1 = 0.0,
+                           double etol = 1.0, unsigned long long* err = nullptr);
 cudaError_t launch_update(int model, int64_t n, const double* Xt, const double* ev, const double* z,
                           const double* w, double* dst, cudaStream_t st, const int* gate = nullptr);
 // sweep test of Algorithm 2: dmax = max |a - b| (dmax reset by the caller),
@@ -86,8 +87,10 @@ cudaError_t launch_sweep_delta(int64_t n, const double* a, const double* b, unsi
 cudaError_t launch_sweep_gate(const unsigned long long* dmax, double tol, int* gate, long long* sweeps,
                               cudaStream_t st);
 cudaError_t launch_set_int(int* p, int v, unsigned long long* clear, cudaStream_t st);
+// *p = 0 unless *gate == 0 (gate may be NULL)
+cudaError_t launch_clear_gated(unsigned long long* p, const int* gate, cudaStream_t st);
 cudaError_t launch_finish(int ns, int64_t n, double* Xn, const double* Xlast, double* u0, const double* ulast,
-                          double* t_act, double v_act, double dt, long long* step_n, int* status,
+                          double* t_act, double v_act, double dt, long long* step_n, double* t_now, int* status,
                           cudaStream_t st);
 int model_ns(int model);
 void rest_state_host(int model, double* x);

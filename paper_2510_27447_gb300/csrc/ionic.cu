@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, cons
   if (i >= L.n) return;
   if (L.gate && *L.gate == 0) return;
   const int64_t n = L.n;
-  const double t = double(*L.step_n) * L.dt;
+  const double t = *L.t_now;
   const double istim = stim_current(L.stim_bits, i, L.stim, t, L.dt);
 
   double xj[NS];
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, cons
 
 template <template <class> class Model, class T>
 __global__ void __launch_bounds__(kBlock) field_kernel(int64_t n, const double* X, double inv_cm, double dt,
-                                                       const uint32_t* stim_bits, const long long* step_n,
+                                                       const uint32_t* stim_bits, const double* t_now,
                                                        const StimTable stim, double* fout, const Model<T> P,
                                                        const int* gate) {
   using Mod = Model<T>;
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kBlock) field_kernel(int64_t n, const double* 
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (gate && *gate == 0) return;
-  const double t = step_n ? double(*step_n) * dt : 0.0;
+  const double t = t_now ? *t_now : 0.0;
   const double istim = stim_current(stim_bits, i, stim, t, dt);
   T x[NS];
 #pragma unroll
@@ -163,23 +163,38 @@ __global__ void __launch_bounds__(kBlock) field_kernel(int64_t n, const double* 
   for (int k = 0; k < NS; ++k) fout[k * n + i] = double(fs.f[k]);
 }
 
-// X_{m+1} = X + m1 k1 + m2 k2, k_y = z + w k_v  (ROS2 combination, Eq. (3.14))
+// X_{m+1} = X + m1 k1 + m2 k2, k_y = z + w k_v  (ROS2 combination, Eq. (3.14)).
+// With err != nullptr also the embedded error estimate: X_hat = X + k1/gamma,
+// |X_{m+1} - X_hat| / (etol (1 + |X_{m+1}|)), maximum over the launch
+// accumulated with an order-independent atomicMax on the bit pattern.
 template <int NS>
 __global__ void __launch_bounds__(kBlock) combine_kernel(int64_t n, const double* src, const double* k1v,
                                                          const double* z1, const double* w1, const double* k2v,
                                                          const double* z2, const double* w2, double m1, double m2,
-                                                         double* dst, const int* gate) {
+                                                         double* dst, const int* gate, double mhat1, double etol,
+                                                         unsigned long long* err) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (gate && *gate == 0) return;
-  const double a = k1v[i], b = k2v[i];
-  dst[i] = src[i] + m1 * a + m2 * b;
+  double e = 0.0;
+  if (i < n && !(gate && *gate == 0)) {
+    const double a = k1v[i], b = k2v[i];
+    const double x0 = src[i] + m1 * a + m2 * b;
+    dst[i] = x0;
+    if (err) e = fabs(x0 - (src[i] + mhat1 * a)) / (etol * (1.0 + fabs(x0)));
 #pragma unroll
-  for (int k = 1; k < NS; ++k) {
-    const int64_t o = (k - 1) * n + i;
-    const double k1 = z1[o] + w1[o] * a;
-    const double k2 = z2[o] + w2[o] * b;
-    dst[k * n + i] = src[k * n + i] + m1 * k1 + m2 * k2;
+    for (int k = 1; k < NS; ++k) {
+      const int64_t o = (k - 1) * n + i;
+      const double k1 = z1[o] + w1[o] * a;
+      const double k2 = z2[o] + w2[o] * b;
+      const double xs = src[k * n + i];
+      const double xk = xs + m1 * k1 + m2 * k2;
+      dst[k * n + i] = xk;
+      if (err) e = fmax(e, fabs(xk - (xs + mhat1 * k1)) / (etol * (1.0 + fabs(xk))));
+    }
+  }
+  if (err) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = fmax(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0 && e > 0.0) atomicMax(err, (unsigned long long)__double_as_longlong(e));
   }
 }
 
@@ -200,24 +215,28 @@ __global__ void __launch_bounds__(kBlock) update_kernel(int64_t n, const double*
   }
 }
 
-// end of step: activation times, X^n <- X^{n+1}, u^n <- u^{n+1}, n <- n + 1
+// end of step: activation times, X^n <- X^{n+1}, u^n <- u^{n+1}
 __global__ void __launch_bounds__(256) finish_kernel(int ns, int64_t n, double* Xn, const double* Xlast, double* u0,
                                                      const double* ulast, double* t_act, double v_act, double dt,
-                                                     long long* step_n, int* status) {
+                                                     const double* t_now, int* status) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const long long sn = *step_n;
+  const double t = *t_now;
   if (i < n) {
     const double vo = Xn[i], vn = Xlast[i];
     if (!isfinite(vn)) atomicOr(status, ST_NONFINITE);
-    if (isnan(t_act[i]) && vo < v_act && vn >= v_act) t_act[i] = double(sn) * dt + (v_act - vo) / (vn - vo) * dt;
+    if (isnan(t_act[i]) && vo < v_act && vn >= v_act) t_act[i] = t + (v_act - vo) / (vn - vo) * dt;
     for (int k = 0; k < ns; ++k) Xn[k * n + i] = Xlast[k * n + i];
     u0[i] = ulast[i];
   }
-  // every block reads step_n above; the grid-wide increment happens in a
-  // separate one-thread launch so no block can see the new value early
+  // every block reads the clock above; it advances in a separate one-thread
+  // launch so no block can see the new value early
 }
 
-__global__ void bump_kernel(long long* step_n) { *step_n += 1; }
+// simulated time t^{n+1} = t^n + dt and the step counter
+__global__ void bump_kernel(long long* step_n, double* t_now, double dt) {
+  *step_n += 1;
+  *t_now += dt;
+}
 
 __global__ void sweep_delta_kernel(int64_t n, const double* a, const double* b, unsigned long long* dmax,
                                    const int* gate) {
@@ -242,6 +261,11 @@ __global__ void sweep_gate_kernel(const unsigned long long* dmax, double tol, in
 __global__ void set_int_kernel(int* p, int v, unsigned long long* clear) {
   *p = v;
   if (clear) *clear = 0ull;
+}
+
+__global__ void clear_gated_kernel(unsigned long long* p, const int* gate) {
+  if (gate && *gate == 0) return;
+  *p = 0ull;
 }
 
 template <template <class> class Model, class T>
@@ -275,7 +299,7 @@ cudaError_t launch_ionic(const IonicLaunch& L, cudaStream_t st) {
 }
 
 cudaError_t launch_field(int model, int precision, int64_t n, const double* X, double inv_cm, double dt,
-                         const uint32_t* stim_bits, const long long* step_n, const StimTable& stim, double* fout,
+                         const uint32_t* stim_bits, const double* step_n, const StimTable& stim, double* fout,
                          cudaStream_t st, const int* gate) {
   if (n == 0) return cudaSuccess;
   const unsigned grid = unsigned((n + kBlock - 1) / kBlock);
@@ -293,11 +317,14 @@ cudaError_t launch_field(int model, int precision, int64_t n, const double* X, d
 
 cudaError_t launch_combine(int model, int64_t n, const double* src, const double* k1v, const double* z1,
                            const double* w1, const double* k2v, const double* z2, const double* w2, double m1,
-                           double m2, double* dst, cudaStream_t st, const int* gate) {
+                           double m2, double* dst, cudaStream_t st, const int* gate, double mhat1, double etol,
+                           unsigned long long* err) {
   if (n == 0) return cudaSuccess;
   const unsigned grid = unsigned((n + kBlock - 1) / kBlock);
-  if (model == BD_TP06_EPI) combine_kernel<19><<<grid, kBlock, 0, st>>>(n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst, gate);
-  else combine_kernel<8><<<grid, kBlock, 0, st>>>(n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst, gate);
+  if (model == BD_TP06_EPI)
+    combine_kernel<19><<<grid, kBlock, 0, st>>>(n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst, gate, mhat1, etol, err);
+  else
+    combine_kernel<8><<<grid, kBlock, 0, st>>>(n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst, gate, mhat1, etol, err);
   return cudaGetLastError();
 }
 
@@ -311,13 +338,13 @@ cudaError_t launch_update(int model, int64_t n, const double* Xt, const double* 
 }
 
 cudaError_t launch_finish(int ns, int64_t n, double* Xn, const double* Xlast, double* u0, const double* ulast,
-                          double* t_act, double v_act, double dt, long long* step_n, int* status,
+                          double* t_act, double v_act, double dt, long long* step_n, double* t_now, int* status,
                           cudaStream_t st) {
   if (n > 0) {
     const unsigned grid = unsigned((n + 255) / 256);
-    finish_kernel<<<grid, 256, 0, st>>>(ns, n, Xn, Xlast, u0, ulast, t_act, v_act, dt, step_n, status);
+    finish_kernel<<<grid, 256, 0, st>>>(ns, n, Xn, Xlast, u0, ulast, t_act, v_act, dt, t_now, status);
   }
-  bump_kernel<<<1, 1, 0, st>>>(step_n);
+  bump_kernel<<<1, 1, 0, st>>>(step_n, t_now, dt);
   return cudaGetLastError();
 }
 
@@ -337,6 +364,11 @@ cudaError_t launch_sweep_gate(const unsigned long long* dmax, double tol, int* g
 
 cudaError_t launch_set_int(int* p, int v, unsigned long long* clear, cudaStream_t st) {
   set_int_kernel<<<1, 1, 0, st>>>(p, v, clear);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clear_gated(unsigned long long* p, const int* gate, cudaStream_t st) {
+  clear_gated_kernel<<<1, 1, 0, st>>>(p, gate);
   return cudaGetLastError();
 }
 

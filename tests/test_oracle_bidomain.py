@@ -208,3 +208,90 @@ def test_stimulus_window():
     dt = 0.02
     on = [bool(P.i_stim(n * dt, dt)[0]) for n in range(200)]
     assert on.index(True) == 50 and sum(on) == 50
+
+
+# ---------------------------------------------------------------------------
+# adaptive stepping: embedded ROS2 estimate and step controller
+# ---------------------------------------------------------------------------
+
+def _embedded_amplification(z):
+    """X_hat = X + k1/gamma on y' = lambda y: k1 = gamma z X/(1 - gamma z),
+    so X_hat/X = (1 + (1 - gamma) z)/(1 - gamma z), a first-order method."""
+    g = B.GAMMA
+    return (1.0 + (1.0 - g) * z) / (1.0 - g * z)
+
+
+def test_embedded_estimate_closed_form():
+    lam = np.array([-3.0, -50.0, -0.2])
+    P = _problem(LinearCell(lam))
+    x = np.array([1.3, -0.7, 2.0])
+    X = np.repeat(x[:, None], P.N, axis=1)
+    tol = 1e-3
+    P.adaptive_tol = tol
+    for h in (0.01, 0.1, 1.0):
+        # M = 2: the last sweep's predictor is one ROS2 step of length h
+        P.step(X, np.zeros(P.N), 0.0, h, n_sdc_nodes=2, n_sweeps=2)
+        z = lam * h
+        R, Rh = B.ros2_amplification(z), _embedded_amplification(z)
+        want = np.max(np.abs((R - Rh) * x) / (tol * (1.0 + np.abs(R * x))))
+        assert P.last_err == pytest.approx(want, rel=1e-10)
+        # M = 3: two sub-steps of h/2, the second from the first's result
+        P.step(X, np.zeros(P.N), 0.0, h, n_sdc_nodes=3, n_sweeps=1)
+        z2 = z / 2
+        R2, Rh2 = B.ros2_amplification(z2), _embedded_amplification(z2)
+        x1 = R2 * x
+        e1 = np.abs((R2 - Rh2) * x) / (tol * (1.0 + np.abs(x1)))
+        e2 = np.abs((R2 - Rh2) * x1) / (tol * (1.0 + np.abs(R2 * x1)))
+        assert P.last_err == pytest.approx(max(e1.max(), e2.max()), rel=1e-10)
+    # the embedded method is of order one: local error O(z^2)
+    r = abs(_embedded_amplification(1e-3) - np.exp(1e-3)) / abs(_embedded_amplification(5e-4) - np.exp(5e-4))
+    assert 3.9 < r < 4.1
+
+
+def test_embedded_estimate_scales_with_h_squared_on_lr91():
+    """A smooth sub-threshold phase: halving the step divides the estimate by
+    about four (difference of a second- and a first-order solution).  The
+    steps are long enough for v to dominate the maximum; below about 0.005 ms
+    the stiff m gate (time constant of microseconds) takes over, whose
+    estimate is not yet in its asymptotic range."""
+    cellm = lr91.model(True)
+    P = _problem(cellm, n=4, stim=[B.Stim(np.ones(16, np.uint8), 0.0, 5.0, 15.0)])
+    P.adaptive_tol = 1.0
+    X = np.repeat(cellm.rest_state()[:, None], P.N, axis=1)
+    errs = []
+    for h in (0.04, 0.02, 0.01):
+        P.step(X, np.zeros(P.N), 0.0, h, n_sdc_nodes=2, n_sweeps=1)
+        errs.append(P.last_err)
+    r = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all((r > 3.5) & (r < 4.5)), (errs, r)
+
+
+def test_controller_ladder_and_factor():
+    assert B.ladder_step(0.05, 0.05, 8) == 0.05
+    assert B.ladder_step(0.05, 0.049, 8) == 0.025
+    assert B.ladder_step(0.05, 0.0125, 8) == 0.0125
+    assert B.ladder_step(0.05, 1e-9, 8) == 0.05 / 128
+    assert B.ladder_step(0.05, 1.0, 8) == 0.05
+    assert B.controller_factor(0.0) == 2.0
+    assert B.controller_factor(0.01) == 2.0
+    assert B.controller_factor(1.0) == pytest.approx(0.9)
+    assert B.controller_factor(4.0) == pytest.approx(0.5)
+    assert B.controller_factor(100.0) == 0.5
+
+
+def test_adaptive_limits_reduce_to_fixed_steps():
+    """tol -> infinity: every step dt_max, identical to the fixed-step march;
+    tol -> 0: the first step is rejected down the whole ladder (7 times),
+    then every step stays on the smallest rung."""
+    cellm = lr91.model(True)
+    stim = [B.Stim(np.ones(16, np.uint8), 0.0, 1.0, 30.0)]
+    P = _problem(cellm, n=4, stim=stim)
+    X0 = np.repeat(cellm.rest_state()[:, None], P.N, axis=1)
+    X, u, t, ta, dts, rej = B.run_adaptive(P, X0, 5, 0.05, 1e30)
+    Xf, uf, _ = B.run(_problem(cellm, n=4, stim=stim), X0, 5, 0.05)
+    assert dts == [0.05] * 5 and rej == 0 and t == pytest.approx(0.25)
+    np.testing.assert_array_equal(X, Xf)
+    X, u, t, ta, dts, rej = B.run_adaptive(P, X0, 3, 0.05, 1e-30)
+    assert dts == [0.05 / 128] * 3 and rej == 7
+    Xf, uf, _ = B.run(_problem(cellm, n=4, stim=stim), X0, 3, 0.05 / 128)
+    np.testing.assert_array_equal(X, Xf)
