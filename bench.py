@@ -215,7 +215,7 @@ def e2e_rate(sim, torch, steps: int) -> dict:
     nb = len(blob)
     host = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
     host.numpy()[:] = memoryview(blob)
-    vout = torch.empty(sim.N, dtype=torch.float64, pin_memory=True)
+    vout = torch.empty(sim.NT, dtype=torch.float64, pin_memory=True)
     uout = torch.empty(sim.N, dtype=torch.float64, pin_memory=True)
     dp = C.POINTER(C.c_double)
     t0 = time.perf_counter()
@@ -230,7 +230,50 @@ def e2e_rate(sim, torch, steps: int) -> dict:
             raise binding.BdError(rc, "get_fields")
     el = time.perf_counter() - t0
     return {"value": sim.N * steps / el, "unit": "node-steps/s", "h2d_bytes_per_step": nb,
-            "d2h_bytes_per_step": 2 * 8 * sim.N}
+            "d2h_bytes_per_step": 8 * (sim.NT + sim.N)}
+
+
+def bath_leg(args, torch, stream, flush) -> dict:
+    """The bidomain-bath run of Sec. 4 (801^2 nodes over [-1, 7]^2, tissue
+    [0, 6]^2 with 601^2 nodes, LR91, 3 Lobatto nodes, 2 sweeps) at its maximum
+    step dt = 0.05 ms, from rest + S1: node-steps/s over all nodes (the unit
+    the paper's 34 h for 600 ms on 2 x 28 cores converts to: 641,601 x 12,000
+    steps / 122,400 s = 6.29e4 node-steps/s, if every step is the maximum)."""
+    from paper_2510_27447_gb300 import binding, workloads as W
+    w = W.bath_paper_2d()
+    out = {"workload": w.name, "nodes": w.n_nodes, "tissue_nodes": w.n_tissue, "dt_ms": w.dt,
+           "sigma_bath": w.sbath, "paper_rate_node_steps_per_s": 6.29e4}
+    for name, prec in (("mixed", binding.MIXED), ("fp64", binding.FP64)):
+        with torch.cuda.stream(stream):
+            opts = binding.default_options(precision=prec, stream=stream.cuda_stream, pin_node=w.pin_node,
+                                           cg_tol_e=1e-10, cg_tol_p=1e-10)
+            sim = binding.simulation_from_workload(w, opts)
+            for _ in range(max(3, args.warmup)):
+                sim.step(w.dt, 3, 2)
+            sim.sync()
+            st0 = sim.stats()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.bath_steps):
+                flush.add_(1.0)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sim.step(w.dt, 3, 2)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            sim.sync()
+            st1 = sim.stats()
+            sim.close()
+        t = sum(ms) / len(ms)
+        out[name] = {"ms_per_step": round(t, 3), "value": round(w.n_nodes / (t / 1e3), 1),
+                     "cg_iters_e": round((st1["cg_iters_e"] - st0["cg_iters_e"]) /
+                                         max(1, st1["cg_solves_e"] - st0["cg_solves_e"]), 1),
+                     "cg_iters_p": round((st1["cg_iters_p"] - st0["cg_iters_p"]) /
+                                         max(1, st1["cg_solves_p"] - st0["cg_solves_p"]), 1)}
+    out["steps"] = args.bath_steps
+    return out
 
 
 def serve_leg(args) -> dict:
@@ -329,6 +372,13 @@ def run_ours(args) -> None:
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     share = {k: round(v / sum(prof["ms"].values()), 4) for k, v in prof["ms"].items()}
 
+    bath = None
+    if args.bath_steps > 0:
+        try:
+            bath = bath_leg(args, torch, stream, flush)
+        except Exception as e:  # noqa: BLE001
+            bath = {"error": str(e)[:200]}
+
     serve = None
     if args.serve_requests > 0:
         try:
@@ -373,6 +423,7 @@ def run_ours(args) -> None:
         "cg_iters_per_solve": {"elliptic": round(mixed["cg_iters_e"], 1), "parabolic": round(mixed["cg_iters_p"], 1)},
         "cpu_baseline": base,
         "serve": serve,
+        "bath": bath,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -406,6 +457,8 @@ def main():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-ms", type=float, default=10.0)
+    ap.add_argument("--bath-steps", type=int, default=10,
+                    help="timed steps of the 801^2 bidomain-bath leg (0: skip)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--seconds", type=float, default=0.0, help=argparse.SUPPRESS)
     args = ap.parse_args()

@@ -62,7 +62,15 @@ typedef enum { BD_FP64 = 0, BD_MIXED = 1 } bd_precision_t;
 /* P1 mesh (Sec. 3.2): dim = 2 (triangles, 3 nodes per element) or 3
  * (tetrahedra, 4 nodes).  xyz: n_nodes*dim doubles, node-major (x0 y0 [z0] x1 ...).
  * elems: n_elems*(dim+1) zero-based node indices.  fiber: n_elems*dim unit
- * vectors or NULL (x axis).  All copied at bd_create. */
+ * vectors or NULL (x axis).  All copied at bd_create.
+ *
+ * Bidomain-bath coupling (Sec. 4, "Results for Bidomain-Bath"): elem_bath
+ * (n_elems bytes, or NULL = all tissue) marks the elements of a conductive
+ * bath.  The tissue nodes are the nodes of the tissue elements; they must be
+ * numbered first, 0 .. n_tissue-1 (BD_ERR_ARG otherwise).  Only the tissue
+ * nodes carry v and the membrane state; u lives on every node and is the
+ * extracellular potential in the tissue and the bath potential in the bath
+ * (continuous across the interface, no intracellular current through it). */
 typedef struct {
   int dim;
   int64_t n_nodes;
@@ -70,15 +78,18 @@ typedef struct {
   const double* xyz;
   const int32_t* elems;
   const double* fiber;
+  const uint8_t* elem_bath;
 } bd_mesh_t;
 
 /* Conductivities (Sec. 2, transversely isotropic along the fibre):
  * sigma = s_t I + (s_l - s_t) f f^T for the intra- (i) and extracellular (e)
  * domains, mS/cm; chi = surface-to-volume ratio (1/cm); cm = membrane
- * capacitance (uF/cm^2). */
+ * capacitance (uF/cm^2); sbath = isotropic bath conductivity (mS/cm, > 0 when
+ * the mesh has bath elements, else ignored). */
 typedef struct {
   double sil, sit, sel, set;
   double chi, cm;
+  double sbath;
 } bd_cond_t;
 
 /* Options; bd_default_options() fills every field. */
@@ -159,13 +170,14 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model,
               const bd_opts_t* opts, bd_state_t** out);
 
 /* Add a stimulus (at most 32): membrane current density amp (uA/cm^2,
- * depolarising) on the nodes with node_mask[i] != 0 (n_nodes bytes), active
+ * depolarising) on the tissue nodes with node_mask[i] != 0 (n_tissue bytes), active
  * for the steps with t_on <= t^n < t_on + dur, t^n = n*dt (Sec. 4 protocols). */
 int bd_add_stimulus(bd_state_t* s, const uint8_t* node_mask, double t_on_ms, double dur_ms,
                     double amp);
 
-/* Set X (ns*N doubles, node-major layout above) and u (N doubles or NULL =>
- * zeros) from host memory; resets the step counter and activation times. */
+/* Set X (ns*n_tissue doubles, state-major: X[k*n_tissue + i]) and u
+ * (n_nodes doubles or NULL => zeros) from host memory; resets the step
+ * counter, the clock and the activation times. */
 int bd_set_initial(bd_state_t* s, const double* X, const double* u);
 
 /* Advance one time step of size dt_ms with Algorithm 2 on n_sdc_nodes (2 or
@@ -203,12 +215,13 @@ int bd_sync(bd_state_t* s);
 int bd_query(bd_state_t* s);
 void bd_clear_status(bd_state_t* s);
 
-/* Activation times (first upward crossing of v_act, linearly interpolated
- * inside the step; NaN if not activated), n doubles to host. */
+/* Activation times of the tissue nodes (first upward crossing of v_act,
+ * linearly interpolated inside the step; NaN if not activated),
+ * n = n_tissue doubles to host. */
 int bd_activation_times(const bd_state_t* s, double* out, int64_t n);
 
-/* Copy v (N), u (N) and, if X != NULL, the full state (ns*N) to host memory;
- * any pointer may be NULL. */
+/* Copy v (n_tissue), u (n_nodes) and, if X != NULL, the full state
+ * (ns*n_tissue) to host memory; any pointer may be NULL. */
 int bd_get_fields(const bd_state_t* s, double* vm, double* phie, double* X);
 
 /* Device pointers of the resident v-row / u so callers can read them without
@@ -233,9 +246,10 @@ int bd_get_stats(const bd_state_t* s, bd_stats_t* out);
  *
  * Solves A_ie u = -A_i v by Jacobi-preconditioned CG (whatever the handle's
  * elliptic_precond) with the handle's resident operators, tolerance and pin:
- * v_dev (N doubles, device) is read, u_dev (N doubles, device) is
- * written, u_guess_dev (device, N) warm-starts the iteration or is NULL for a
- * zero start.  The call allocates nothing: the CG work vectors, partial sums,
+ * v_dev (n_nodes doubles, device; with a bath the entries of bath nodes are
+ * multiplied by zero and must be finite) is read, u_dev (n_nodes doubles,
+ * device) is written, u_guess_dev (device, n_nodes) warm-starts the iteration
+ * or is NULL for a zero start.  The call allocates nothing: the CG work vectors, partial sums,
  * barrier words and status live in one file-scope __device__ array of the
  * library sized for at most BD_NOALLOC_MAX_NODES nodes (about 5.4 MB, held
  * by every GPU that loads the library until the process exits).  Larger
@@ -259,6 +273,8 @@ int bd_profile_steps(bd_state_t* s, double dt_ms, int n_sdc_nodes, int n_sweeps,
                      bd_profile_t* out);
 int bd_reset_stats(bd_state_t* s);
 int64_t bd_num_nodes(const bd_state_t* s);
+/* Nodes that carry v and the membrane state (= bd_num_nodes without a bath). */
+int64_t bd_num_tissue_nodes(const bd_state_t* s);
 int bd_num_states(bd_ionic_t model);
 const char* bd_last_error(const bd_state_t* s);
 void bd_destroy(bd_state_t* s);
@@ -291,9 +307,9 @@ int bd_operator_csr(const bd_state_t* s, int which, int64_t* nnz, int32_t* rowpt
                     int32_t* col, double* val);
 
 /* Solve the elliptic constraint A_ie u = -A_i v (Eq. (3.15)) with the
- * handle's operators, precision and pin, from a host v (N) into a host u (N),
- * warm-started from u_guess (host, N) or from zero if NULL.  Returns the
- * iteration count in *iters when not NULL. */
+ * handle's operators, precision and pin, from a host v (n_tissue) into a host
+ * u (n_nodes), warm-started from u_guess (host, n_nodes) or from zero if NULL.
+ * Returns the iteration count in *iters when not NULL. */
 int bd_solve_elliptic(bd_state_t* s, const double* v, const double* u_guess, double* u,
                       int* iters);
 

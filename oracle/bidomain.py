@@ -54,6 +54,15 @@ Elliptic constraint (Eq. (3.15), Sec. 2 Dirichlet part left unstated): u is
 the solution of A_ie u = -A_i v with u[pin] = 0 (pin >= 0), or with zero
 nodal mean (pin < 0); solved by eliminating the pinned row and column.
 
+Bidomain-bath (Sec. 4, "Results for Bidomain-Bath"; the paper states no
+equations for it): the tissue nodes, numbered first, carry X; u lives on all
+nodes and solves A_ie u = -A_i v, where A_ie includes the bath stiffness and
+A_i vanishes outside the tissue (see ``fem.py``).  The parabolic and ODE rows
+are those above, restricted to the tissue nodes, with u taken there.
+
+Adaptive step (Sec. 3.3.2: the embedded X_hat "determines the future step";
+Sec. 4 runs use a maximum step of 0.05 ms): ``run_adaptive`` below.
+
 Stimulus: I_stim,i = sum over stimuli of amplitude * mask_i when
 t_on <= t^n < t_on + duration (t^n = n tau, 1e-9 tau tolerance), constant
 over the step.
@@ -130,12 +139,26 @@ class Bidomain:
     """Discrete bidomain problem on a P1 mesh (oracle)."""
 
     def __init__(self, xyz, elems, fibers, sigma, chi, cm, cell, stimuli: Sequence = (),
-                 pin_node: int = 0, mass_lumped: bool = False):
-        self.ops = fem.assemble(np.asarray(xyz, np.float64), np.asarray(elems),
-                                np.asarray(fibers, np.float64), sigma, chi, cm)
+                 pin_node: int = 0, mass_lumped: bool = False, elem_bath=None,
+                 sigma_b: float = 0.0):
+        ops = fem.assemble(np.asarray(xyz, np.float64), np.asarray(elems),
+                           np.asarray(fibers, np.float64), sigma, chi, cm, elem_bath, sigma_b)
+        # tissue nodes (those of tissue elements) are numbered first: v and the
+        # membrane state live on them, u on all nodes (bidomain-bath, Sec. 4)
+        self.N_all = xyz.shape[0]
+        NT = self.N_all
+        if elem_bath is not None:
+            tis = np.zeros(self.N_all, dtype=bool)
+            tis[np.asarray(elems)[np.asarray(elem_bath) == 0].ravel()] = True
+            NT = int(tis.sum())
+            if not np.all(tis[:NT]):
+                raise ValueError("tissue nodes must be numbered before bath nodes")
+        self.A_i_rect = ops.A_i[:, :NT].tocsr()         # -A_i v on every node (elliptic rhs)
+        self.ops = fem.Operators(A_i=ops.A_i[:NT, :NT].tocsr(), A_ie=ops.A_ie,
+                                 M=ops.M[:NT, :NT].tocsr(), M_L=ops.M_L[:NT].copy())
         self.cell = cell
         self.cm = float(cm)
-        self.N = xyz.shape[0]
+        self.N = NT
         self.ns = cell.ns
         self.dim = xyz.shape[1]
         self.mass_lumped = mass_lumped
@@ -144,7 +167,7 @@ class Bidomain:
         self.stimuli = [Stim(np.asarray(s.mask), float(s.t_on), float(s.duration),
                              float(s.amplitude)) for s in stimuli]
         self.pin = pin_node
-        keep = np.ones(self.N, dtype=bool)
+        keep = np.ones(self.N_all, dtype=bool)
         self.pin_row = pin_node if pin_node >= 0 else 0
         keep[self.pin_row] = False
         self.keep = keep
@@ -159,7 +182,7 @@ class Bidomain:
         eps = 1e-9 * dt
         for s in self.stimuli:
             if (t - s.t_on) > -eps and (t - s.t_on - s.duration) < -eps:
-                out += s.amplitude * s.mask
+                out += s.amplitude * s.mask[:self.N]
         return out
 
     def Mt(self, X: np.ndarray) -> np.ndarray:
@@ -172,15 +195,16 @@ class Bidomain:
         """F(X, u) of Eq. (3.11)."""
         f = self.cell.field(X, istim, self.cm).real
         out = np.empty_like(X)
-        out[0] = -(self.ops.A_i @ (X[0] + u)) + self.ops.M_L * f[0]
+        out[0] = -(self.ops.A_i @ (X[0] + u[:self.N])) + self.ops.M_L * f[0]
         out[1:] = self.ops.M_L[None, :] * f[1:]
         return out
 
     # -- elliptic constraint ---------------------------------------------------
     def elliptic(self, v: np.ndarray) -> np.ndarray:
-        """u with A_ie u = -A_i v and u[pin] = 0 (or zero mean if pin < 0)."""
-        b = -(self.ops.A_i @ v)
-        u = np.zeros(self.N)
+        """u with A_ie u = -A_i v and u[pin] = 0 (or zero mean if pin < 0);
+        u on every node (tissue and bath), v on the tissue nodes."""
+        b = -(self.A_i_rect @ v)
+        u = np.zeros(self.N_all)
         u[self.keep] = self.ell_lu.solve(b[self.keep])
         if self.pin < 0:
             u -= u.mean()
@@ -298,7 +322,7 @@ def run(problem: Bidomain, X0: np.ndarray, n_steps: int, dt: float, n_sdc_nodes:
     """March n_steps steps from X0 (u0 = 0 if not given); returns
     (X, u, activation_times)."""
     X = np.array(X0, dtype=np.float64, copy=True)
-    u = np.zeros(problem.N) if u0 is None else np.array(u0, dtype=np.float64)
+    u = np.zeros(problem.N_all) if u0 is None else np.array(u0, dtype=np.float64)
     t_act = np.full(problem.N, np.nan)
     for n in range(n_steps):
         t = n * dt
@@ -345,7 +369,7 @@ def run_adaptive(problem: Bidomain, X0: np.ndarray, n_steps: int, dt_max: float,
     """n_steps accepted adaptive steps from X0 (u0 = 0); returns
     (X, u, t, activation_times, accepted dts, rejections)."""
     X = np.array(X0, dtype=np.float64, copy=True)
-    u = np.zeros(problem.N)
+    u = np.zeros(problem.N_all)
     t = 0.0
     t_act = np.full(problem.N, np.nan)
     dt = dt_max

@@ -19,6 +19,14 @@ barycentric basis, exact integral of the product of two linear functions) and
 scattered with scipy's COO->CSR summation.  The lumped mass M_L is the row sum
 of M.
 
+Bidomain-bath coupling (Sec. 4, "Results for Bidomain-Bath"): a bath element
+has no intracellular space and no membrane; it adds sigma_b I (isotropic) to
+the extracellular conductivity only.  Hence A_i, M and M_L collect tissue
+elements only, and A_ie collects K(sigma_i + sigma_e) over the tissue plus
+K(sigma_b I) over the bath -- the weak form of div((sigma_i + sigma_e) grad u
++ sigma_i grad v) = 0 in the tissue, div(sigma_b grad u) = 0 in the bath,
+with u continuous and the normal currents balanced on the interface.
+
 Pins (tests/test_oracle_fem.py): manufactured solution with observed O(h^2),
 exact null space (A 1 = 0), total mass = area/volume, closed-form element
 matrices of the reference triangle, and the equal-anisotropy identity
@@ -87,13 +95,22 @@ class Operators:
     M_L: np.ndarray         # lumped mass (row sums of M)
 
 
-def assemble(xyz, elems, fibers, sigma, chi, cm) -> Operators:
+def assemble(xyz, elems, fibers, sigma, chi, cm, elem_bath=None, sigma_b: float = 0.0) -> Operators:
     """Operators of Eqs. (3.6)-(3.7) for conductivities
-    sigma = (s_il, s_it, s_el, s_et) in mS/cm."""
+    sigma = (s_il, s_it, s_el, s_et) in mS/cm; elements with elem_bath != 0
+    are bath elements of isotropic conductivity sigma_b."""
     s_il, s_it, s_el, s_et = sigma
     scale = 1.0 / (chi * cm)
-    A_i = stiffness(xyz, elems, fibers, s_il, s_it) * scale
-    A_ie = stiffness(xyz, elems, fibers, s_il + s_el, s_it + s_et) * scale
-    M = mass(xyz, elems)
+    if elem_bath is None:
+        tis = np.ones(len(elems), dtype=bool)
+    else:
+        tis = np.asarray(elem_bath) == 0
+    et, ft = elems[tis], fibers[tis]
+    A_i = stiffness(xyz, et, ft, s_il, s_it) * scale
+    A_ie = stiffness(xyz, et, ft, s_il + s_el, s_it + s_et) * scale
+    M = mass(xyz, et)
+    if not np.all(tis):
+        eb, fb = elems[~tis], fibers[~tis]
+        A_ie = A_ie + stiffness(xyz, eb, fb, sigma_b, sigma_b) * scale
     M_L = np.asarray(M.sum(axis=1)).ravel()
     return Operators(A_i=A_i.tocsr(), A_ie=A_ie.tocsr(), M=M.tocsr(), M_L=M_L)

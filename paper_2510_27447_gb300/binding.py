@@ -26,7 +26,7 @@ EXPORTS = ["bd_default_options", "bd_create", "bd_add_stimulus", "bd_set_initial
            "bd_reset_stats", "bd_num_nodes", "bd_num_states", "bd_last_error", "bd_destroy",
            "bd_ionic_eval", "bd_ionic_pattern", "bd_rest_state", "bd_operator_csr",
            "bd_solve_elliptic", "bd_profile_steps", "bd_solve_elliptic_noalloc", "bd_query",
-           "bd_step_adaptive", "bd_get_time"]
+           "bd_step_adaptive", "bd_get_time", "bd_num_tissue_nodes"]
 
 
 class LibraryMissing(RuntimeError):
@@ -42,12 +42,12 @@ class BdError(RuntimeError):
 class Mesh(C.Structure):
     _fields_ = [("dim", C.c_int), ("n_nodes", C.c_int64), ("n_elems", C.c_int64),
                 ("xyz", C.POINTER(C.c_double)), ("elems", C.POINTER(C.c_int32)),
-                ("fiber", C.POINTER(C.c_double))]
+                ("fiber", C.POINTER(C.c_double)), ("elem_bath", C.POINTER(C.c_uint8))]
 
 
 class Cond(C.Structure):
     _fields_ = [("sil", C.c_double), ("sit", C.c_double), ("sel", C.c_double),
-                ("set", C.c_double), ("chi", C.c_double), ("cm", C.c_double)]
+                ("set", C.c_double), ("chi", C.c_double), ("cm", C.c_double), ("sbath", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -115,6 +115,7 @@ def lib():
         "bd_get_stats": (C.c_int, [C.c_void_p, P(Stats)]),
         "bd_reset_stats": (C.c_int, [C.c_void_p]),
         "bd_num_nodes": (C.c_int64, [C.c_void_p]),
+        "bd_num_tissue_nodes": (C.c_int64, [C.c_void_p]),
         "bd_num_states": (C.c_int, [C.c_int]),
         "bd_last_error": (C.c_char_p, [C.c_void_p]),
         "bd_destroy": (None, [C.c_void_p]),
@@ -184,17 +185,22 @@ def ionic_eval(model: int, X: np.ndarray, istim: Optional[np.ndarray] = None, cm
     return (f, J) if jacobian else f
 
 
-def mesh_struct(xyz: np.ndarray, elems: np.ndarray, fibers: Optional[np.ndarray]):
+def mesh_struct(xyz: np.ndarray, elems: np.ndarray, fibers: Optional[np.ndarray],
+                elem_bath: Optional[np.ndarray] = None):
     xyz = np.ascontiguousarray(xyz, dtype=np.float64)
     elems = np.ascontiguousarray(elems, dtype=np.int32)
     fib = None if fibers is None else np.ascontiguousarray(fibers, dtype=np.float64)
+    bath = None if elem_bath is None else np.ascontiguousarray(elem_bath, dtype=np.uint8)
+    if bath is not None and bath.shape != (elems.shape[0],):
+        raise ValueError("elem_bath must have one byte per element")
     m = Mesh(xyz.shape[1], xyz.shape[0], elems.shape[0], _dp(xyz),
-             elems.ctypes.data_as(C.POINTER(C.c_int32)), _dp(fib))
-    return m, (xyz, elems, fib)
+             elems.ctypes.data_as(C.POINTER(C.c_int32)), _dp(fib),
+             None if bath is None else bath.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return m, (xyz, elems, fib, bath)
 
 
-def footprint_bytes(xyz, elems, model: int, opts: Optional[Opts] = None) -> int:
-    m, keep = mesh_struct(xyz, elems, None)
+def footprint_bytes(xyz, elems, model: int, opts: Optional[Opts] = None, elem_bath=None) -> int:
+    m, keep = mesh_struct(xyz, elems, None, elem_bath)
     return int(lib().bd_footprint_bytes(C.byref(m), model, C.byref(opts) if opts else None))
 
 
@@ -202,16 +208,18 @@ class Simulation:
     """One bidomain handle (bd_state_t)."""
 
     def __init__(self, xyz, elems, fibers, sigma: Sequence[float], chi: float, cm: float,
-                 model: int, opts: Optional[Opts] = None, stimuli=()):
+                 model: int, opts: Optional[Opts] = None, stimuli=(), elem_bath=None,
+                 sbath: float = 0.0):
         L = lib()
-        m, self._keep = mesh_struct(xyz, elems, fibers)
-        cond = Cond(*[float(x) for x in sigma], float(chi), float(cm))
+        m, self._keep = mesh_struct(xyz, elems, fibers, elem_bath)
+        cond = Cond(*[float(x) for x in sigma], float(chi), float(cm), float(sbath))
         self.opts = opts if opts is not None else default_options()
         h = C.c_void_p()
         _check(L.bd_create(C.byref(m), C.byref(cond), model, C.byref(self.opts), C.byref(h)))
         self.h = h
         self.model = model
-        self.N = int(L.bd_num_nodes(h))
+        self.N = int(L.bd_num_nodes(h))             # all nodes (u)
+        self.NT = int(L.bd_num_tissue_nodes(h))     # tissue nodes (v, membrane state)
         self.ns = num_states(model)
         for s in stimuli:
             self.add_stimulus(s.mask, s.t_on, s.duration, s.amplitude)
@@ -229,15 +237,19 @@ class Simulation:
 
     def add_stimulus(self, mask, t_on, duration, amplitude):
         mk = np.ascontiguousarray(mask, dtype=np.uint8)
-        if mk.shape != (self.N,):
-            raise ValueError("mask must have one byte per node")
+        if mk.shape == (self.N,) and self.NT < self.N:
+            if np.any(mk[self.NT:]):
+                raise ValueError("a stimulus mask may only cover tissue nodes")
+            mk = np.ascontiguousarray(mk[:self.NT])
+        if mk.shape != (self.NT,):
+            raise ValueError("mask must have one byte per (tissue) node")
         _check(lib().bd_add_stimulus(self.h, mk.ctypes.data_as(C.POINTER(C.c_uint8)),
                                      float(t_on), float(duration), float(amplitude)), self.h)
 
     def set_initial(self, X: np.ndarray, u: Optional[np.ndarray] = None):
         X = np.ascontiguousarray(X, dtype=np.float64)
-        if X.shape != (self.ns, self.N):
-            raise ValueError(f"X must be ({self.ns}, {self.N})")
+        if X.shape != (self.ns, self.NT):
+            raise ValueError(f"X must be ({self.ns}, {self.NT})")
         uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
         _check(lib().bd_set_initial(self.h, _dp(X), _dp(uu)), self.h)
 
@@ -274,15 +286,15 @@ class Simulation:
         lib().bd_clear_status(self.h)
 
     def fields(self, full: bool = False):
-        v = np.empty(self.N)
+        v = np.empty(self.NT)
         u = np.empty(self.N)
-        X = np.empty((self.ns, self.N)) if full else None
+        X = np.empty((self.ns, self.NT)) if full else None
         _check(lib().bd_get_fields(self.h, _dp(v), _dp(u), _dp(X)), self.h)
         return (v, u, X) if full else (v, u)
 
     def activation_times(self) -> np.ndarray:
-        out = np.empty(self.N)
-        _check(lib().bd_activation_times(self.h, _dp(out), self.N), self.h)
+        out = np.empty(self.NT)
+        _check(lib().bd_activation_times(self.h, _dp(out), self.NT), self.h)
         return out
 
     def get_state(self) -> bytes:
@@ -349,7 +361,8 @@ def batch_step(sims: Sequence[Simulation], dt: float, n_sdc_nodes: int = 3, n_sw
 def simulation_from_workload(w, opts: Optional[Opts] = None) -> Simulation:
     """Handle for a paper_2510_27447_gb300.workloads.Workload."""
     o = opts if opts is not None else default_options(cg_tol_e=w.cg_tol, pin_node=w.pin_node)
-    sim = Simulation(w.xyz, w.elems, w.fibers, w.sigma, w.chi, w.cm, w.model, o, w.stimuli)
+    sim = Simulation(w.xyz, w.elems, w.fibers, w.sigma, w.chi, w.cm, w.model, o, w.stimuli,
+                     elem_bath=getattr(w, "elem_bath", None), sbath=getattr(w, "sbath", 0.0))
     if w.initial is not None:
         sim.set_initial(w.initial)
     return sim

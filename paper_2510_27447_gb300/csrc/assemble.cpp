@@ -10,6 +10,11 @@
 // written per unit membrane capacitance).  All three share one CSR pattern:
 // the node graph of the mesh.
 //
+// Bidomain-bath coupling: a bath element contributes sigma_b I to A_ie only
+// (no intracellular space, no membrane), so A_i, M and M_L vanish on the bath
+// nodes and u is continuous across the interface with the normal currents in
+// balance (the natural interface conditions of the weak form).
+//
 // Rows are assembled independently from a node -> element adjacency, so
 // threads own disjoint rows and need no atomics.
 #include <algorithm>
@@ -106,6 +111,31 @@ int assemble_host(const bd_mesh_t* mesh, const bd_cond_t* cond, HostOps* out, st
   std::vector<ElemGeom> geo(E);
   const double scale = 1.0 / (cond->chi * cond->cm);
   std::vector<double> Si(E * 9), Sie(E * 9);
+  const uint8_t* bath = mesh->elem_bath;
+  // tissue nodes: the nodes of the tissue elements, numbered first
+  out->n_tissue = N;
+  if (bath) {
+    if (!(cond->sbath > 0.0) || !std::isfinite(cond->sbath)) {
+      *err = "a mesh with bath elements needs sbath > 0";
+      return BD_ERR_ARG;
+    }
+    std::vector<uint8_t> tis(N, 0);
+    for (int64_t e = 0; e < E; ++e)
+      if (!bath[e])
+        for (int a = 0; a < k; ++a) tis[mesh->elems[e * k + a]] = 1;
+    int64_t nt = 0;
+    while (nt < N && tis[nt]) ++nt;
+    for (int64_t i = nt; i < N; ++i)
+      if (tis[i]) {
+        *err = "tissue nodes must be numbered before bath nodes";
+        return BD_ERR_ARG;
+      }
+    if (nt < 1) {
+      *err = "the mesh has no tissue element";
+      return BD_ERR_ARG;
+    }
+    out->n_tissue = nt;
+  }
   unsigned nthreads = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
   std::vector<int> bad(nthreads, 0);
   auto par = [&](int64_t total, auto&& fn) {
@@ -138,11 +168,13 @@ int assemble_host(const bd_mesh_t* mesh, const bd_cond_t* cond, HostOps* out, st
         }
         for (int d = 0; d < dim; ++d) f[d] /= nrm;
       }
+      const bool b = bath && bath[e];
       for (int r = 0; r < dim; ++r)
         for (int c = 0; c < dim; ++c) {
           const double ff = f[r] * f[c], id = (r == c) ? 1.0 : 0.0;
-          Si[e * 9 + r * 3 + c] = cond->sit * id + (cond->sil - cond->sit) * ff;
-          Sie[e * 9 + r * 3 + c] = (cond->sit + cond->set) * id + ((cond->sil + cond->sel) - (cond->sit + cond->set)) * ff;
+          Si[e * 9 + r * 3 + c] = b ? 0.0 : cond->sit * id + (cond->sil - cond->sit) * ff;
+          Sie[e * 9 + r * 3 + c] = b ? cond->sbath * id
+                                     : (cond->sit + cond->set) * id + ((cond->sil + cond->sel) - (cond->sit + cond->set)) * ff;
         }
     }
   });
@@ -199,7 +231,7 @@ int assemble_host(const bd_mesh_t* mesh, const bd_cond_t* cond, HostOps* out, st
             }
           out->Ai[p] += G.meas * si * scale;
           out->Aie[p] += G.meas * sie * scale;
-          out->M[p] += G.meas * (la == b ? mdiag : moff);
+          if (!(bath && bath[e])) out->M[p] += G.meas * (la == b ? mdiag : moff);
         }
       }
       double ml = 0.0;

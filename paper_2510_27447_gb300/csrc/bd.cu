@@ -53,6 +53,9 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocWords];
 struct bd_state {
   int model = 0, ns = 0, dim = 0, precision = 0;
   int64_t N = 0, nnz = 0;
+  int64_t NT = 0;                 // tissue nodes (v, membrane state); N - NT bath nodes follow them
+  int64_t nnz_t = 0;              // nonzeros of the tissue block (rows and columns < NT)
+  double* vfull = nullptr;        // bath: v on all N nodes, zero on the bath nodes
   bd_opts_t opts{};
   double inv_cm = 1.0, lambda_M = 0.25;
   int64_t* sptr = nullptr;      // SELL-32 layout of the shared operator pattern
@@ -283,6 +286,11 @@ PcgLaunch pcg_base(bd_state* s) {
 
 int elliptic(bd_state* s, const double* v, double* u) {
   PcgLaunch P = pcg_base(s);
+  if (s->NT < s->N) {   // the right-hand side -A_i v gathers v over all columns
+    Timed t(s, BD_K_COMBINE);
+    CK(launch_copy(s->NT, v, s->vfull, s->stream, P.gate));
+    v = s->vfull;
+  }
   P.valA = s->Aie;
   P.val1 = s->Ai;
   P.va = v;
@@ -317,6 +325,7 @@ int elliptic(bd_state* s, const double* v, double* u) {
 
 int parabolic(bd_state* s, double alpha, double c1, const double* va, double c2, const double* vb, double* x) {
   PcgLaunch P = pcg_base(s);
+  P.n = int(s->NT);   // tissue rows; their bath columns hold zeros
   P.valA = p_values(s, alpha);
   P.dextra = s->dgs;
   P.rl = s->rl;
@@ -358,7 +367,7 @@ IonicLaunch ionic_base(bd_state* s, int mode, double dt) {
   L.model = s->model;
   L.precision = s->precision;
   L.mode = mode;
-  L.n = s->N;
+  L.n = s->NT;
   L.inv_cm = s->inv_cm;
   L.dt = dt;
   L.ML = s->ML;
@@ -549,7 +558,7 @@ double controller_factor(double err) {
 
 int enqueue_step(bd_state* s, double dt, int M, int K) {
   const double gam = 1.0 + 1.0 / std::sqrt(2.0);
-  const int64_t N = s->N;
+  const int64_t N = s->NT, Nu = s->N;
   const int ns = s->ns;
   double c[kMaxNodes], S[kMaxNodes - 1][kMaxNodes];
   lobatto(M, c);
@@ -570,7 +579,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       RUN(elliptic(s, s->Xn, s->u[M - 1]));
       for (int m = 1; m + 1 < M; ++m) {
         Timed t(s, BD_K_COMBINE);
-        CK(launch_copy(N, s->u[M - 1], s->u[m], s->stream, gate));
+        CK(launch_copy(Nu, s->u[M - 1], s->u[m], s->stream, gate));
       }
     } else {
       for (int m = 1; m < M; ++m) RUN(elliptic(s, s->Xc[m], s->u[m]));
@@ -678,7 +687,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
   }
   {
     Timed t(s, BD_K_FINISH, 2);
-    CK(launch_finish(ns, N, s->Xn, s->Xc[M - 1], s->u[0], s->u[M - 1], s->t_act, s->opts.v_act_mV, dt,
+    CK(launch_finish(ns, N, Nu, s->Xn, s->Xc[M - 1], s->u[0], s->u[M - 1], s->t_act, s->opts.v_act_mV, dt,
                      s->step_n, s->t_now, s->d_status, s->stream));
   }
   return BD_OK;
@@ -805,6 +814,13 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     return fail(nullptr, rc, "%s", err.c_str());
   }
   s->nnz = H.rowptr[s->N];
+  s->NT = H.n_tissue;
+  for (int64_t i = 0; i < s->NT; ++i)
+    for (int64_t p = H.rowptr[i]; p < H.rowptr[i + 1]; ++p) s->nnz_t += H.col[p] < s->NT ? 1 : 0;
+  if (s->opts.pin_node >= s->N) {
+    delete s;
+    return fail(nullptr, BD_ERR_ARG, "pin_node out of range");
+  }
   // SELL-32 layout of the shared pattern
   const int64_t nsl = (s->N + 31) / 32;
   std::vector<int64_t> h_sptr(nsl);
@@ -854,22 +870,24 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     }
     s->own_stream = true;
   }
-  const int64_t N = s->N, nnz = s->nnz, ns = s->ns;
+  // N: all nodes (u, elliptic); NT: tissue nodes (v, membrane state, parabolic)
+  const int64_t N = s->N, NT = s->NT, nnz = s->nnz, ns = s->ns;
   const int64_t en = s->ell_n;
   bool ok = alloc_n(s, &s->sptr, nsl) && alloc_n(s, &s->swidth, nsl) && alloc_n(s, &s->col, en) &&
             alloc_n(s, &s->diagpos, N) && alloc_n(s, &s->Ai, en) && alloc_n(s, &s->Aie, en) &&
-            alloc_n(s, &s->Mc, en) && alloc_n(s, &s->Mv, en) && alloc_n(s, &s->ML, N) && alloc_n(s, &s->Xn, ns * N) &&
-            alloc_n(s, &s->dgs, N) && alloc_n(s, &s->rl, N) && alloc_n(s, &s->z1, (ns - 1) * N) &&
-            alloc_n(s, &s->w1, (ns - 1) * N) && alloc_n(s, &s->z2, (ns - 1) * N) &&
-            alloc_n(s, &s->w2, (ns - 1) * N) && alloc_n(s, &s->k1v, N) && alloc_n(s, &s->k2v, N) &&
+            alloc_n(s, &s->Mc, en) && alloc_n(s, &s->Mv, en) && alloc_n(s, &s->ML, NT) && alloc_n(s, &s->Xn, ns * NT) &&
+            alloc_n(s, &s->dgs, NT) && alloc_n(s, &s->rl, NT) && alloc_n(s, &s->z1, (ns - 1) * NT) &&
+            alloc_n(s, &s->w1, (ns - 1) * NT) && alloc_n(s, &s->z2, (ns - 1) * NT) &&
+            alloc_n(s, &s->w2, (ns - 1) * NT) && alloc_n(s, &s->k1v, N) && alloc_n(s, &s->k2v, N) &&
             alloc_n(s, &s->avec, N) && alloc_n(s, &s->bvec, N) && alloc_n(s, &s->cg_r, N) &&
             alloc_n(s, &s->cg_z, N) && alloc_n(s, &s->cg_p, N) && alloc_n(s, &s->cg_q, N) &&
-            alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->t_act, N) && alloc_n(s, &s->stim_bits, N) &&
+            alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->t_act, NT) && alloc_n(s, &s->stim_bits, NT) &&
+            (NT == N || alloc_n(s, &s->vfull, N)) &&
             alloc_n(s, &s->step_n, 1) && alloc_n(s, &s->t_now, 1) && alloc_n(s, &s->d_err, 1) &&
             alloc_n(s, &s->d_status, 1) && alloc_n(s, &s->d_stats, 8) &&
             alloc_n(s, &s->d_clamps, 1) && alloc_n(s, &s->bar, 2);
   for (int m = 0; ok && m < kMaxNodes; ++m)
-    ok = alloc_n(s, &s->Xt[m], ns * N) && alloc_n(s, &s->Xc[m], ns * N) && alloc_n(s, &s->fq[m], ns * N) &&
+    ok = alloc_n(s, &s->Xt[m], ns * NT) && alloc_n(s, &s->Xc[m], ns * NT) && alloc_n(s, &s->fq[m], ns * NT) &&
          alloc_n(s, &s->u[m], N);
   s->pcg_block = s->opts.cg_block > 0 ? s->opts.cg_block : 256;
   if (s->pcg_block % 32 != 0 || s->pcg_block > 1024) {
@@ -887,7 +905,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   s->pcg_grid = int(std::max<int64_t>(1, std::min<int64_t>(want, s->pcg_max)));
   if (ok) ok = alloc_n(s, &s->cg_part, int64_t(s->pcg_max) * 4);
   if (ok && s->opts.sweep_tol > 0)
-    ok = alloc_n(s, &s->gate, 1) && alloc_n(s, &s->dmax, 1) && alloc_n(s, &s->Xsave, ns * N);
+    ok = alloc_n(s, &s->gate, 1) && alloc_n(s, &s->dmax, 1) && alloc_n(s, &s->Xsave, ns * NT);
   if (ok && s->precision == BD_MIXED) {
     ok = alloc_n(s, &s->fAie, s->ell_n) && alloc_n(s, &s->r32, N) && alloc_n(s, &s->z32, N) &&
          alloc_n(s, &s->p32, N) && alloc_n(s, &s->q32, N) && alloc_n(s, &s->invd32, N) &&
@@ -916,8 +934,18 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   if (e == cudaSuccess) e = up(s->Aie, eAie.data(), en * 8);
   if (e == cudaSuccess) e = up(s->Mc, eM.data(), en * 8);
   if (e == cudaSuccess) e = up(s->Mv, eMv.data(), en * 8);
-  if (e == cudaSuccess) e = up(s->ML, H.ML.data(), N * 8);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->stim_bits, 0, N * 4, s->stream);
+  if (e == cudaSuccess) e = up(s->ML, H.ML.data(), NT * 8);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->stim_bits, 0, NT * 4, s->stream);
+  // The parabolic solves run over the tissue rows only, and their bath
+  // columns hold zero operator values; the vectors those rows gather from
+  // must still hold finite numbers there (0 * NaN would poison a row), so
+  // every node-length vector starts at zero.  Afterwards only the elliptic
+  // solves write the bath entries, with finite values.
+  for (double* v : {s->k1v, s->k2v, s->avec, s->bvec, s->cg_r, s->cg_z, s->cg_p, s->cg_q, s->cg_invd, s->vfull,
+                    s->b64, s->r64})
+    if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, N * 8, s->stream);
+  for (float* v : {s->r32, s->z32, s->p32, s->q32, s->invd32, s->d32})
+    if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, N * 4, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->bar, 0, 8, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, 4, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_stats, 0, 64, s->stream);
@@ -947,10 +975,10 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   }
   s->host = std::move(H);
   // resting initial state
-  std::vector<double> x0(ns), X(ns * N);
+  std::vector<double> x0(ns), X(ns * NT);
   rest_state_host(s->model, x0.data());
   for (int k = 0; k < ns; ++k)
-    for (int64_t i = 0; i < N; ++i) X[k * N + i] = x0[k];
+    for (int64_t i = 0; i < NT; ++i) X[k * NT + i] = x0[k];
   rc = bd_set_initial(s, X.data(), nullptr);
   if (rc != BD_OK) {
     std::string m = s->err;
@@ -966,13 +994,13 @@ int bd_add_stimulus(bd_state_t* s, const uint8_t* mask, double t_on, double dur,
   if (!s || !mask) return fail(s, BD_ERR_ARG, "NULL argument");
   if (s->stim.n >= kMaxStim) return fail(s, BD_ERR_ARG, "at most %d stimuli", kMaxStim);
   if (!std::isfinite(t_on) || !(dur >= 0) || !std::isfinite(amp)) return fail(s, BD_ERR_ARG, "bad stimulus timing/amplitude");
-  std::vector<uint32_t> bits(s->N);
-  CK(cudaMemcpyAsync(bits.data(), s->stim_bits, s->N * 4, cudaMemcpyDeviceToHost, s->stream));
+  std::vector<uint32_t> bits(s->NT);
+  CK(cudaMemcpyAsync(bits.data(), s->stim_bits, s->NT * 4, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   const int k = s->stim.n;
-  for (int64_t i = 0; i < s->N; ++i)
+  for (int64_t i = 0; i < s->NT; ++i)
     if (mask[i]) bits[i] |= (1u << k);
-  CK(cudaMemcpyAsync(s->stim_bits, bits.data(), s->N * 4, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->stim_bits, bits.data(), s->NT * 4, cudaMemcpyHostToDevice, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   s->stim.t_on[k] = t_on;
   s->stim.dur[k] = dur;
@@ -984,13 +1012,13 @@ int bd_add_stimulus(bd_state_t* s, const uint8_t* mask, double t_on, double dur,
 
 int bd_set_initial(bd_state_t* s, const double* X, const double* u) {
   if (!s || !X) return fail(s, BD_ERR_ARG, "NULL argument");
-  const int64_t N = s->N, ns = s->ns;
+  const int64_t N = s->NT, Nu = s->N, ns = s->ns;
   for (int64_t i = 0; i < ns * N; ++i)
     if (!std::isfinite(X[i])) return fail(s, BD_ERR_ARG, "non-finite initial state");
   CK(cudaMemcpyAsync(s->Xn, X, ns * N * 8, cudaMemcpyHostToDevice, s->stream));
   for (int m = 0; m < kMaxNodes; ++m) {
-    if (u) CK(cudaMemcpyAsync(s->u[m], u, N * 8, cudaMemcpyHostToDevice, s->stream));
-    else CK(cudaMemsetAsync(s->u[m], 0, N * 8, s->stream));
+    if (u) CK(cudaMemcpyAsync(s->u[m], u, Nu * 8, cudaMemcpyHostToDevice, s->stream));
+    else CK(cudaMemsetAsync(s->u[m], 0, Nu * 8, s->stream));
   }
   std::vector<double> nanv(N, std::nan(""));
   CK(cudaMemcpyAsync(s->t_act, nanv.data(), N * 8, cudaMemcpyHostToDevice, s->stream));
@@ -1042,7 +1070,7 @@ void bd_clear_status(bd_state_t* s) {
 
 int bd_activation_times(const bd_state_t* cs, double* out, int64_t n) {
   bd_state* s = const_cast<bd_state*>(cs);
-  if (!s || !out || n != s->N) return fail(s, BD_ERR_ARG, "bad arguments");
+  if (!s || !out || n != s->NT) return fail(s, BD_ERR_ARG, "bad arguments");
   CK(cudaStreamSynchronize(s->stream));
   CK(cudaMemcpy(out, s->t_act, n * 8, cudaMemcpyDeviceToHost));
   return read_status(s);
@@ -1052,9 +1080,9 @@ int bd_get_fields(const bd_state_t* cs, double* vm, double* phie, double* X) {
   bd_state* s = const_cast<bd_state*>(cs);
   if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
   CK(cudaStreamSynchronize(s->stream));
-  if (vm) CK(cudaMemcpy(vm, s->Xn, s->N * 8, cudaMemcpyDeviceToHost));
+  if (vm) CK(cudaMemcpy(vm, s->Xn, s->NT * 8, cudaMemcpyDeviceToHost));
   if (phie) CK(cudaMemcpy(phie, s->u[0], s->N * 8, cudaMemcpyDeviceToHost));
-  if (X) CK(cudaMemcpy(X, s->Xn, int64_t(s->ns) * s->N * 8, cudaMemcpyDeviceToHost));
+  if (X) CK(cudaMemcpy(X, s->Xn, int64_t(s->ns) * s->NT * 8, cudaMemcpyDeviceToHost));
   return read_status(s);
 }
 
@@ -1068,7 +1096,7 @@ int bd_device_fields(const bd_state_t* s, const double** X_dev, const double** u
 int bd_get_state(const bd_state_t* cs, void* buf, size_t* bytes) {
   bd_state* s = const_cast<bd_state*>(cs);
   if (!s || !bytes) return fail(s, BD_ERR_ARG, "NULL argument");
-  const size_t need = 48 + size_t(s->ns + 2) * size_t(s->N) * 8;
+  const size_t need = 48 + (size_t(s->ns + 1) * size_t(s->NT) + size_t(s->N)) * 8;
   if (!buf) {
     *bytes = need;
     return BD_OK;
@@ -1082,18 +1110,18 @@ int bd_get_state(const bd_state_t* cs, void* buf, size_t* bytes) {
   std::memcpy(&hdr[5], &s->dt_adapt, 8);
   std::memcpy(p, hdr, 48);
   p += 48;
-  CK(cudaMemcpy(p, s->Xn, int64_t(s->ns) * s->N * 8, cudaMemcpyDeviceToHost));
-  p += int64_t(s->ns) * s->N * 8;
+  CK(cudaMemcpy(p, s->Xn, int64_t(s->ns) * s->NT * 8, cudaMemcpyDeviceToHost));
+  p += int64_t(s->ns) * s->NT * 8;
   CK(cudaMemcpy(p, s->u[0], s->N * 8, cudaMemcpyDeviceToHost));
   p += s->N * 8;
-  CK(cudaMemcpy(p, s->t_act, s->N * 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(p, s->t_act, s->NT * 8, cudaMemcpyDeviceToHost));
   *bytes = need;
   return BD_OK;
 }
 
 int bd_set_state(bd_state_t* s, const void* buf, size_t bytes) {
   if (!s || !buf) return fail(s, BD_ERR_ARG, "NULL argument");
-  const size_t need = 48 + size_t(s->ns + 2) * size_t(s->N) * 8;
+  const size_t need = 48 + (size_t(s->ns + 1) * size_t(s->NT) + size_t(s->N)) * 8;
   if (bytes != need) return fail(s, BD_ERR_ARG, "state blob has %zu bytes, expected %zu", bytes, need);
   const char* p = static_cast<const char*>(buf);
   int64_t hdr[6];
@@ -1102,11 +1130,11 @@ int bd_set_state(bd_state_t* s, const void* buf, size_t bytes) {
     return fail(s, BD_ERR_ARG, "state blob belongs to another model or mesh");
   p += 48;
   CK(cudaStreamSynchronize(s->stream));
-  CK(cudaMemcpy(s->Xn, p, int64_t(s->ns) * s->N * 8, cudaMemcpyHostToDevice));
-  p += int64_t(s->ns) * s->N * 8;
+  CK(cudaMemcpy(s->Xn, p, int64_t(s->ns) * s->NT * 8, cudaMemcpyHostToDevice));
+  p += int64_t(s->ns) * s->NT * 8;
   for (int m = 0; m < kMaxNodes; ++m) CK(cudaMemcpy(s->u[m], p, s->N * 8, cudaMemcpyHostToDevice));
   p += s->N * 8;
-  CK(cudaMemcpy(s->t_act, p, s->N * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->t_act, p, s->NT * 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->step_n, &hdr[3], 8, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(s->t_now, &hdr[4], 8, cudaMemcpyHostToDevice));
   std::memcpy(&s->dt_adapt, &hdr[5], 8);
@@ -1128,9 +1156,9 @@ int bd_step_adaptive(bd_state_t* s, double dt_max, double tol, int M, int K, dou
   if (!(dt_max > 0) || !std::isfinite(dt_max) || !(tol > 0)) return fail(s, BD_ERR_ARG, "dt_max and tol must be positive");
   if (M != 2 && M != 3) return fail(s, BD_ERR_ARG, "n_sdc_nodes must be 2 or 3");
   if (K < 1) return fail(s, BD_ERR_ARG, "n_sweeps must be >= 1");
-  const int64_t N = s->N, ns = s->ns;
+  const int64_t N = s->NT, Nu = s->N, ns = s->ns;
   if (!s->Xbak) {
-    if (!alloc_n(s, &s->Xbak, ns * N) || !alloc_n(s, &s->ubak, N) || !alloc_n(s, &s->tbak, N + 4))
+    if (!alloc_n(s, &s->Xbak, ns * N) || !alloc_n(s, &s->ubak, Nu) || !alloc_n(s, &s->tbak, N + 4))
       return fail(s, BD_ERR_OOM, "device allocation failed");
   }
   const double dt_min = dt_max * std::ldexp(1.0, -(kAdaptLadder - 1));
@@ -1141,7 +1169,7 @@ int bd_step_adaptive(bd_state_t* s, double dt_max, double tol, int M, int K, dou
   for (;;) {
     // keep X^n, u^n, activation times and the clock for a possible rejection
     CK(cudaMemcpyAsync(s->Xbak, s->Xn, ns * N * 8, cudaMemcpyDeviceToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->ubak, s->u[0], N * 8, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->ubak, s->u[0], Nu * 8, cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(s->tbak, s->t_act, N * 8, cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(s->tbak + N, s->t_now, 8, cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(s->tbak + N + 1, s->step_n, 8, cudaMemcpyDeviceToDevice, s->stream));
@@ -1161,7 +1189,7 @@ int bd_step_adaptive(bd_state_t* s, double dt_max, double tol, int M, int K, dou
     ++rej;
     CK(cudaMemcpyAsync(s->Xn, s->Xbak, ns * N * 8, cudaMemcpyDeviceToDevice, s->stream));
     for (int m = 0; m < kMaxNodes; ++m)
-      CK(cudaMemcpyAsync(s->u[m], s->ubak, N * 8, cudaMemcpyDeviceToDevice, s->stream));
+      CK(cudaMemcpyAsync(s->u[m], s->ubak, Nu * 8, cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(s->t_act, s->tbak, N * 8, cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(s->t_now, s->tbak + N, 8, cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(s->step_n, s->tbak + N + 1, 8, cudaMemcpyDeviceToDevice, s->stream));
@@ -1182,9 +1210,22 @@ size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts
   const int ns = model_ns(int(model));
   if (ns == 0) return 0;
   const double N = double(mesh->n_nodes);
+  double NT = N;
+  if (mesh->elem_bath && mesh->elems) {
+    const int k = mesh->dim + 1;
+    std::vector<uint8_t> tis(mesh->n_nodes, 0);
+    for (int64_t e = 0; e < mesh->n_elems; ++e)
+      if (!mesh->elem_bath[e])
+        for (int a = 0; a < k; ++a) {
+          const int32_t q = mesh->elems[e * k + a];
+          if (q >= 0 && q < mesh->n_nodes) tis[q] = 1;
+        }
+    NT = 0.0;
+    for (uint8_t t : tis) NT += t;
+  }
   const double nnz = N * (mesh->dim == 2 ? 7.0 : 15.0);   // P1 node graph, upper estimate for structured meshes
   const double mat = nnz * (4 + 8 * 4 + 8 * 4) + N * (4 * 3 + 8);
-  const double st = N * 8 * (ns * (1 + 3 * kMaxNodes) + 4 * (ns - 1) + 3 * kMaxNodes + 16);
+  const double st = NT * 8 * (ns * (1 + 3 * kMaxNodes) + 4 * (ns - 1) + 4) + N * 8 * (3 * kMaxNodes + 12);
   return size_t(mat + st) + (size_t(1) << 20);
 }
 
@@ -1306,12 +1347,13 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
   out->outer_iters[0] = st1[4] - st0[4];
   out->outer_iters[1] = st1[5] - st0[5];
   // algorithmic bytes (see bd_profile_t); vb = bytes per value of the Krylov iteration
-  const double n = double(s->N), nnz = double(s->nnz);
   const bool mixed = s->precision == BD_MIXED;
   const double vb = mixed ? 4.0 : 8.0;
-  auto spmv = [&](double v) { return nnz * (v + 4) + n * v; };
   for (int k = 0; k < 2; ++k) {
     const bool ell = k == 0;
+    // elliptic: all nodes and the whole pattern; parabolic: the tissue block
+    const double n = double(ell ? s->N : s->NT), nnz = double(ell ? s->nnz : s->nnz_t);
+    auto spmv = [&](double v) { return nnz * (v + 4) + n * v; };
     const double iters = double(out->cg_iters[k]), solves = double(out->cg_solves[k]);
     const double extra = ell ? 0.0 : 8.0 * n;                       // condensed diagonal
     double per_iter = spmv(vb) + 13.0 * vb * n + extra;
@@ -1337,6 +1379,8 @@ int bd_reset_stats(bd_state_t* s) {
 }
 
 int64_t bd_num_nodes(const bd_state_t* s) { return s ? s->N : 0; }
+
+int64_t bd_num_tissue_nodes(const bd_state_t* s) { return s ? s->NT : 0; }
 
 const char* bd_last_error(const bd_state_t* s) {
   if (s) return s->err.c_str();
@@ -1410,15 +1454,18 @@ int bd_solve_elliptic(bd_state_t* s, const double* v, const double* u_guess, dou
   const int64_t N = s->N;
   double *dv = s->avec, *du = s->bvec;
   CK(cudaStreamSynchronize(s->stream));
-  CK(cudaMemcpyAsync(dv, v, N * 8, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(dv, v, s->NT * 8, cudaMemcpyHostToDevice, s->stream));
   if (u_guess) CK(cudaMemcpyAsync(du, u_guess, N * 8, cudaMemcpyHostToDevice, s->stream));
   else CK(cudaMemsetAsync(du, 0, N * 8, s->stream));
   long long before[2];
   CK(cudaMemcpyAsync(before, s->d_stats, 16, cudaMemcpyDeviceToHost, s->stream));
+  if (s->gate) CK(launch_set_int(s->gate, 1, nullptr, s->stream));   // a step's sweep test may have closed it
   RUN(elliptic(s, dv, du));
   long long after[2];
   CK(cudaMemcpyAsync(after, s->d_stats, 16, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaMemcpyAsync(u, du, N * 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemsetAsync(du, 0, N * 8, s->stream));
+  CK(cudaMemsetAsync(dv, 0, N * 8, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   if (iters) *iters = int(after[0] - before[0]);
   return read_status(s);

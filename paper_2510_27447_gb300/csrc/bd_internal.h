@@ -89,9 +89,11 @@ cudaError_t launch_sweep_gate(const unsigned long long* dmax, double tol, int* g
 cudaError_t launch_set_int(int* p, int v, unsigned long long* clear, cudaStream_t st);
 // *p = 0 unless *gate == 0 (gate may be NULL)
 cudaError_t launch_clear_gated(unsigned long long* p, const int* gate, cudaStream_t st);
-cudaError_t launch_finish(int ns, int64_t n, double* Xn, const double* Xlast, double* u0, const double* ulast,
-                          double* t_act, double v_act, double dt, long long* step_n, double* t_now, int* status,
-                          cudaStream_t st);
+// X^n <- X_last and activation times on the n tissue nodes, u^n <- u_last on
+// all nu nodes, then t^n += dt, n += 1
+cudaError_t launch_finish(int ns, int64_t n, int64_t nu, double* Xn, const double* Xlast, double* u0,
+                          const double* ulast, double* t_act, double v_act, double dt, long long* step_n,
+                          double* t_now, int* status, cudaStream_t st);
 int model_ns(int model);
 void rest_state_host(int model, double* x);
 
@@ -242,6 +244,7 @@ cudaError_t launch_to_float(int64_t n, const double* src, float* dst, cudaStream
 // host assembly (assemble.cpp)
 struct HostOps {
   int64_t n = 0;
+  int64_t n_tissue = 0;            // nodes [0, n_tissue) carry v and the membrane state
   std::vector<int32_t> rowptr, col, diagpos;
   std::vector<double> Ai, Aie, M, ML;
 };

@@ -216,9 +216,9 @@ __global__ void __launch_bounds__(kBlock) update_kernel(int64_t n, const double*
 }
 
 // end of step: activation times, X^n <- X^{n+1}, u^n <- u^{n+1}
-__global__ void __launch_bounds__(256) finish_kernel(int ns, int64_t n, double* Xn, const double* Xlast, double* u0,
-                                                     const double* ulast, double* t_act, double v_act, double dt,
-                                                     const double* t_now, int* status) {
+__global__ void __launch_bounds__(256) finish_kernel(int ns, int64_t n, int64_t nu, double* Xn, const double* Xlast,
+                                                     double* u0, const double* ulast, double* t_act, double v_act,
+                                                     double dt, const double* t_now, int* status) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const double t = *t_now;
   if (i < n) {
@@ -226,8 +226,8 @@ __global__ void __launch_bounds__(256) finish_kernel(int ns, int64_t n, double* 
     if (!isfinite(vn)) atomicOr(status, ST_NONFINITE);
     if (isnan(t_act[i]) && vo < v_act && vn >= v_act) t_act[i] = t + (v_act - vo) / (vn - vo) * dt;
     for (int k = 0; k < ns; ++k) Xn[k * n + i] = Xlast[k * n + i];
-    u0[i] = ulast[i];
   }
+  if (i < nu) u0[i] = ulast[i];
   // every block reads the clock above; it advances in a separate one-thread
   // launch so no block can see the new value early
 }
@@ -337,12 +337,13 @@ cudaError_t launch_update(int model, int64_t n, const double* Xt, const double* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish(int ns, int64_t n, double* Xn, const double* Xlast, double* u0, const double* ulast,
-                          double* t_act, double v_act, double dt, long long* step_n, double* t_now, int* status,
-                          cudaStream_t st) {
-  if (n > 0) {
-    const unsigned grid = unsigned((n + 255) / 256);
-    finish_kernel<<<grid, 256, 0, st>>>(ns, n, Xn, Xlast, u0, ulast, t_act, v_act, dt, t_now, status);
+cudaError_t launch_finish(int ns, int64_t n, int64_t nu, double* Xn, const double* Xlast, double* u0,
+                          const double* ulast, double* t_act, double v_act, double dt, long long* step_n,
+                          double* t_now, int* status, cudaStream_t st) {
+  const int64_t m = std::max(n, nu);
+  if (m > 0) {
+    const unsigned grid = unsigned((m + 255) / 256);
+    finish_kernel<<<grid, 256, 0, st>>>(ns, n, nu, Xn, Xlast, u0, ulast, t_act, v_act, dt, t_now, status);
   }
   bump_kernel<<<1, 1, 0, st>>>(step_n, t_now, dt);
   return cudaGetLastError();

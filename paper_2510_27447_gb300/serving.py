@@ -159,7 +159,7 @@ class GpuExecutor(Executor):
 
     def footprint(self, job: Job) -> int:
         w = job.payload
-        return self.b.footprint_bytes(w.xyz, w.elems, w.model, self.options())
+        return self.b.footprint_bytes(w.xyz, w.elems, w.model, self.options(), w.elem_bath)
 
     def start(self, job: Job):
         return self.b.simulation_from_workload(job.payload, self.options())

@@ -166,6 +166,17 @@ class Stimulus:
     amplitude: float        # uA/cm^2 (membrane current density, depolarising)
 
 
+def tissue_first(xyz: np.ndarray, elems: np.ndarray, elem_bath: np.ndarray):
+    """Renumber the nodes so that the nodes of tissue elements come first
+    (each group in its original order).  Returns (xyz, elems, new_of_old)."""
+    tis = np.zeros(len(xyz), dtype=bool)
+    tis[elems[np.asarray(elem_bath) == 0].ravel()] = True
+    order = np.concatenate([np.nonzero(tis)[0], np.nonzero(~tis)[0]])
+    new_of_old = np.empty(len(xyz), dtype=np.int64)
+    new_of_old[order] = np.arange(len(xyz))
+    return xyz[order].copy(), new_of_old[elems].astype(np.int32), new_of_old
+
+
 @dataclasses.dataclass
 class Workload:
     name: str
@@ -184,6 +195,16 @@ class Workload:
     pin_node: int = 0
     cg_tol: float = 1e-10
     initial: Optional[np.ndarray] = None     # X[ns, N] or None => model rest
+    elem_bath: Optional[np.ndarray] = None   # per element, 1 = bath (tissue nodes numbered first)
+    sbath: float = 0.0                       # bath conductivity, mS/cm
+
+    @property
+    def n_tissue(self) -> int:
+        if self.elem_bath is None:
+            return self.n_nodes
+        tis = np.zeros(self.n_nodes, dtype=bool)
+        tis[self.elems[self.elem_bath == 0].ravel()] = True
+        return int(tis.sum())
 
     @property
     def n_nodes(self) -> int:
@@ -211,6 +232,55 @@ def sheet(n: int, length: float, model: int, dt: float, n_steps: int,
     return Workload(name=name, xyz=xyz, elems=tris, fibers=fibers_along_x(len(tris), 2),
                     sigma=tuple(sigma), chi=2000.0, cm=1.0, model=model, stimuli=stims,
                     dt=dt, n_steps=n_steps, **kw)
+
+
+BATH_SIGMA = 20.0      # mS/cm, bath conductivity of the bidomain-bath runs
+
+
+def bath_sheet(n_cells: int, lo: float, hi: float, t_lo: float, t_hi: float, model: int,
+               dt: float, n_steps: int, sigma=CONFIG0_SIGMA, sbath: float = BATH_SIGMA,
+               strip: float = 0.1, s1_amp: float = 100.0, s1_dur: float = 2.0,
+               s2: Optional[Tuple[float, float, float]] = None, name: str = "bath_sheet",
+               **kw) -> Workload:
+    """Bidomain-bath square (Sec. 4): the domain [lo, hi]^2 split into
+    n_cells^2 squares (two triangles each); the elements whose centroid lies
+    in the tissue square [t_lo, t_hi]^2 are tissue, the rest bath.  Tissue
+    nodes are numbered first, fibres run along x.  Stimuli follow the reentry
+    protocol of Sec. 4: S1 (s1_amp uA/cm^2, s1_dur ms, t = 0) on the tissue
+    strip t_lo <= y < t_lo + strip along the bottom edge; s2 = (t_on, x_len,
+    y_len) adds an S2 on [t_lo, t_lo + x_len] x [t_lo, t_lo + y_len].  u is
+    pinned at the domain corner (lo, lo), a bath node."""
+    L = hi - lo
+    xyz, tris = square_grid(n_cells + 1, L)
+    xyz = xyz + lo
+    cen = xyz[tris].mean(axis=1)
+    inside = np.all((cen > t_lo) & (cen < t_hi), axis=1)
+    bath = (~inside).astype(np.uint8)
+    corner = int(np.argmin(np.abs(xyz[:, 0] - lo) + np.abs(xyz[:, 1] - lo)))
+    xyz, tris, new_of_old = tissue_first(xyz, tris, bath)
+    nt = int(np.count_nonzero(np.bincount(tris[bath == 0].ravel(), minlength=len(xyz))))
+    eps = 1e-9 * L
+    tissue = np.zeros(len(xyz), dtype=bool)
+    tissue[:nt] = True
+    x, y = xyz[:, 0], xyz[:, 1]
+    m1 = tissue & (y < t_lo + strip - eps)
+    stims = [Stimulus(m1.astype(np.uint8), 0.0, s1_dur, s1_amp)]
+    if s2 is not None:
+        m2 = tissue & (x <= t_lo + s2[1] + eps) & (y <= t_lo + s2[2] + eps)
+        stims.append(Stimulus(m2.astype(np.uint8), s2[0], s1_dur, s1_amp))
+    return Workload(name=name, xyz=xyz, elems=tris, fibers=fibers_along_x(len(tris), 2),
+                    sigma=tuple(sigma), chi=2000.0, cm=1.0, model=model, stimuli=stims,
+                    dt=dt, n_steps=n_steps, pin_node=int(new_of_old[corner]), elem_bath=bath,
+                    sbath=sbath, **kw)
+
+
+def bath_paper_2d(n_steps: int = 12000, dt: float = 0.05) -> Workload:
+    """The bidomain-bath run of Sec. 4: domain [-1, 7]^2 on 800 x 800 cells
+    (801^2 = 641,601 nodes), tissue [0, 6]^2 (601^2 = 361,201 nodes), LR91,
+    reentry protocol (S1 bottom edge at 0 ms, S2 on [0, 1] x [0, 3] at
+    120 ms), 600 ms."""
+    return bath_sheet(800, -1.0, 7.0, 0.0, 6.0, LR91, dt, n_steps, s2=(120.0, 1.0, 3.0),
+                      name="lr91_bath_801x801")
 
 
 def config0() -> Workload:

@@ -17,19 +17,20 @@ def oracle_cell(model):
 def oracle_problem(w, mass_lumped=False, pin=None):
     return OB.Bidomain(w.xyz, w.elems, w.fibers, w.sigma, w.chi, w.cm, oracle_cell(w.model),
                        w.stimuli, pin_node=w.pin_node if pin is None else pin,
-                       mass_lumped=mass_lumped)
+                       mass_lumped=mass_lumped, elem_bath=w.elem_bath, sigma_b=w.sbath)
 
 
 def rest_X(w):
     cell = oracle_cell(w.model)
     x = cell.initial() if w.model == W.TP06_EPI else cell.rest_state()
-    return np.repeat(x[:, None], w.n_nodes, axis=1)
+    return np.repeat(x[:, None], w.n_tissue, axis=1)
 
 
 def gpu_sim(w, **opt):
     opt.setdefault("pin_node", w.pin_node)
     o = binding.default_options(**opt)
-    return binding.Simulation(w.xyz, w.elems, w.fibers, w.sigma, w.chi, w.cm, w.model, o, w.stimuli)
+    return binding.Simulation(w.xyz, w.elems, w.fibers, w.sigma, w.chi, w.cm, w.model, o, w.stimuli,
+                              elem_bath=w.elem_bath, sbath=w.sbath)
 
 
 def rel(a, b):

@@ -87,3 +87,34 @@ def test_footprint_scales_with_nodes(lib):
     c = binding.footprint_bytes(*W.square_grid(65), binding.TP06_EPI)
     assert 3.5 < (b - 2**20) / (a - 2**20) < 4.2
     assert c > 1.5 * b
+
+
+def test_bath_mesh_errors_are_host_side(lib):
+    """Bath meshes are validated during host assembly, before any device
+    call: tissue nodes must come first and the bath needs sbath > 0."""
+    from paper_2510_27447_gb300 import workloads as W
+    w = W.bath_sheet(8, -0.25, 1.25, 0.0, 1.0, W.LR91, 0.05, 1)
+    cond = binding.Cond(*w.sigma, w.chi, w.cm, 0.0)
+    h = ctypes.c_void_p()
+    m, keep = binding.mesh_struct(w.xyz, w.elems, w.fibers, w.elem_bath)
+    assert lib.bd_create(ctypes.byref(m), ctypes.byref(cond), 0, None, ctypes.byref(h)) == -1
+    assert b"sbath" in lib.bd_last_error(None)
+    # swap a tissue node with a bath node: the numbering rule is broken
+    perm = np.arange(w.n_nodes)
+    perm[[0, w.n_nodes - 1]] = perm[[w.n_nodes - 1, 0]]
+    xyz = w.xyz[perm]
+    inv = np.argsort(perm)
+    elems = inv[w.elems].astype(np.int32)
+    cond = binding.Cond(*w.sigma, w.chi, w.cm, 20.0)
+    m, keep = binding.mesh_struct(xyz, elems, w.fibers, w.elem_bath)
+    assert lib.bd_create(ctypes.byref(m), ctypes.byref(cond), 0, None, ctypes.byref(h)) == -1
+    assert b"numbered before" in lib.bd_last_error(None)
+    assert not h.value
+
+
+def test_bath_footprint_counts_tissue_state_only(lib):
+    from paper_2510_27447_gb300 import workloads as W
+    w = W.bath_sheet(64, -0.25, 1.25, 0.0, 1.0, W.TP06_EPI, 0.05, 1)
+    with_bath = binding.footprint_bytes(w.xyz, w.elems, binding.TP06_EPI, None, w.elem_bath)
+    all_tissue = binding.footprint_bytes(w.xyz, w.elems, binding.TP06_EPI)
+    assert with_bath < 0.7 * all_tissue
