@@ -186,6 +186,17 @@ int bd_set_initial(bd_state_t* s, const double* X, const double* u);
  * that was read back (bd_sync waits and reads it). */
 int bd_step(bd_state_t* s, double dt_ms, int n_sdc_nodes, int n_sweeps);
 
+/* One step of the decoupled CN-RK2 scheme, the paper's reference decoupled
+ * strategy (Sec. 3.3.3): Strang splitting of the node reaction (explicit
+ * midpoint rule over two half steps dt/2, the step's stimulus included) and
+ * the diffusion (one Crank-Nicolson step of M dv/dt = -A_i (v + u^n),
+ * solved by CG for the increment), then the elliptic constraint
+ * A_ie u^{n+1} = -A_i v^{n+1}.  Explicit in the membrane model, so dt must
+ * resolve its fastest gate (the paper uses dt = 0.001 ms).  Shares the
+ * handle, its operators, precision, statistics, activation times and clock
+ * with bd_step; one CUDA graph per dt. */
+int bd_step_decoupled(bd_state_t* s, double dt_ms);
+
 /* Adaptive step (the paper's production mode, Sec. 3.3.2 and Sec. 4.3: the
  * embedded ROS2 solution X_hat = X + k1/gamma of Eq. (3.14) determines the
  * future step, at most dt_max).  Error estimate: the maximum, over the last

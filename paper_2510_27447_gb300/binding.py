@@ -26,7 +26,7 @@ EXPORTS = ["bd_default_options", "bd_create", "bd_add_stimulus", "bd_set_initial
            "bd_reset_stats", "bd_num_nodes", "bd_num_states", "bd_last_error", "bd_destroy",
            "bd_ionic_eval", "bd_ionic_pattern", "bd_rest_state", "bd_operator_csr",
            "bd_solve_elliptic", "bd_profile_steps", "bd_solve_elliptic_noalloc", "bd_query",
-           "bd_step_adaptive", "bd_get_time", "bd_num_tissue_nodes"]
+           "bd_step_adaptive", "bd_get_time", "bd_num_tissue_nodes", "bd_step_decoupled"]
 
 
 class LibraryMissing(RuntimeError):
@@ -99,6 +99,7 @@ def lib():
         "bd_add_stimulus": (C.c_int, [C.c_void_p, u8p, C.c_double, C.c_double, C.c_double]),
         "bd_set_initial": (C.c_int, [C.c_void_p, dp, dp]),
         "bd_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int]),
+        "bd_step_decoupled": (C.c_int, [C.c_void_p, C.c_double]),
         "bd_batch_step": (C.c_int, [P(C.c_void_p), C.c_int, C.c_double, C.c_int, C.c_int]),
         "bd_sync": (C.c_int, [C.c_void_p]),
         "bd_query": (C.c_int, [C.c_void_p]),
@@ -258,6 +259,10 @@ class Simulation:
 
     def sync(self):
         _check(lib().bd_sync(self.h), self.h)
+
+    def step_decoupled(self, dt: float):
+        """One CN-RK2 step (decoupled strategy, Strang splitting)."""
+        _check(lib().bd_step_decoupled(self.h, float(dt)), self.h)
 
     def step_adaptive(self, dt_max: float, tol: float, n_sdc_nodes: int = 3, n_sweeps: int = 2):
         """One accepted adaptive step; returns (dt taken, error estimate, rejections)."""

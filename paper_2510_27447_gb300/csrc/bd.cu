@@ -323,12 +323,15 @@ int elliptic(bd_state* s, const double* v, double* u) {
   return BD_OK;
 }
 
-int parabolic(bd_state* s, double alpha, double c1, const double* va, double c2, const double* vb, double* x) {
+// (alpha M_v + A_i + diag(dgs)) x = rl + c1 A_i va + c2 M_v vb; node_terms =
+// false drops diag(dgs) and rl (the plain Crank-Nicolson operator)
+int parabolic(bd_state* s, double alpha, double c1, const double* va, double c2, const double* vb, double* x,
+              bool node_terms = true) {
   PcgLaunch P = pcg_base(s);
   P.n = int(s->NT);   // tissue rows; their bath columns hold zeros
   P.valA = p_values(s, alpha);
-  P.dextra = s->dgs;
-  P.rl = s->rl;
+  P.dextra = node_terms ? s->dgs : nullptr;
+  P.rl = node_terms ? s->rl : nullptr;
   P.val1 = s->Ai;
   P.va = va;
   P.c1 = c1;
@@ -398,7 +401,13 @@ void integration_matrix(int M, double S[kMaxNodes - 1][kMaxNodes]) {
 }
 
 // prepare everything a step allocates or computes outside the launch sequence
+// (M = 0: the CN-RK2 step)
 int prepare_step(bd_state* s, double dt, int M) {
+  if (M == 0) {
+    if (!p_values(s, 2.0 / dt) || (s->precision == BD_MIXED && !p_values_f(s, 2.0 / dt)))
+      return fail(s, BD_ERR_OOM, "device allocation failed");
+    return BD_OK;
+  }
   const double gam = 1.0 + 1.0 / std::sqrt(2.0);
   double c[kMaxNodes];
   lobatto(M, c);
@@ -693,11 +702,49 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
   return BD_OK;
 }
 
+// One step of the decoupled CN-RK2 scheme (Sec. 3.3.3, the paper's reference
+// decoupled strategy): Strang splitting of the node reaction and the
+// diffusion, the elliptic constraint solved last.
+//   X*      = reaction half step (dt/2) from X^n               rk2 kernel
+//   (2/dt M_v + A_i) dv = -2 A_i (v* + u^n)                   CG, Crank-Nicolson
+//   X^{n+1} = reaction half step from (v* + dv, y*)            rk2 kernel
+//   A_ie u^{n+1} = -A_i v^{n+1}                                 CG (Eq. (3.15) form)
+int enqueue_cnrk2(bd_state* s, double dt) {
+  const int64_t N = s->NT, Nu = s->N;
+  if (s->gate) {   // an earlier SDC step's sweep test may have closed the gate
+    Timed t(s, BD_K_COMBINE);
+    CK(launch_set_int(s->gate, 1, nullptr, s->stream));
+  }
+  {
+    Timed t(s, BD_K_IONIC);
+    CK(launch_rk2(s->model, s->precision, N, s->Xn, nullptr, s->Xt[1], 0.5 * dt, s->inv_cm, dt, s->stim_bits,
+                  s->t_now, s->stim, s->u[0], s->avec, s->stream));
+  }
+  RUN(parabolic(s, 2.0 / dt, -2.0, s->avec, 0.0, nullptr, s->k1v, false));
+  {
+    Timed t(s, BD_K_IONIC);
+    CK(launch_rk2(s->model, s->precision, N, s->Xt[1], s->k1v, s->Xc[1], 0.5 * dt, s->inv_cm, dt, s->stim_bits,
+                  s->t_now, s->stim, nullptr, nullptr, s->stream));
+  }
+  RUN(elliptic(s, s->Xc[1], s->u[1]));
+  {
+    Timed t(s, BD_K_FINISH, 2);
+    CK(launch_finish(s->ns, N, Nu, s->Xn, s->Xc[1], s->u[0], s->u[1], s->t_act, s->opts.v_act_mV, dt,
+                     s->step_n, s->t_now, s->d_status, s->stream));
+  }
+  s->ionic_evals += 4;
+  return BD_OK;
+}
+
+int enqueue_any(bd_state* s, double dt, int M, int K) {
+  return M == 0 ? enqueue_cnrk2(s, dt) : enqueue_step(s, dt, M, K);
+}
+
 int do_step(bd_state* s, double dt, int M, int K) {
   RUN(prepare_step(s, dt, M));
   if (!s->opts.use_graph || s->prof) {
     s->enq_launches = 0;
-    RUN(enqueue_step(s, dt, M, K));
+    RUN(enqueue_any(s, dt, M, K));
     s->launches += s->enq_launches;
   } else {
     const int adapt = s->adapt_on ? 1 : 0;
@@ -713,7 +760,7 @@ int do_step(bd_state* s, double dt, int M, int K) {
       const int64_t ev0 = s->ionic_evals;
       s->enq_launches = 0;
       CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-      const int r = enqueue_step(s, dt, M, K);
+      const int r = enqueue_any(s, dt, M, K);
       const int64_t nl = s->enq_launches;
       cudaError_t e = cudaStreamEndCapture(s->stream, &g);
       if (r != BD_OK) {
@@ -732,7 +779,7 @@ int do_step(bd_state* s, double dt, int M, int K) {
     s->launches_per_step = ge->launches;
     CK(cudaGraphLaunch(ge->exec, s->stream));
     s->launches += s->launches_per_step;
-    s->ionic_evals += int64_t(K) * (3 * (M - 1) + (s->opts.sdc_correction ? M : 0)) + 1;
+    s->ionic_evals += M == 0 ? 4 : int64_t(K) * (3 * (M - 1) + (s->opts.sdc_correction ? M : 0)) + 1;
   }
   s->steps += 1;
   s->sweeps += K;
@@ -1035,6 +1082,12 @@ int bd_step(bd_state_t* s, double dt, int M, int K) {
   if (M != 2 && M != 3) return fail(s, BD_ERR_ARG, "n_sdc_nodes must be 2 or 3");
   if (K < 1) return fail(s, BD_ERR_ARG, "n_sweeps must be >= 1");
   return do_step(s, dt, M, K);
+}
+
+int bd_step_decoupled(bd_state_t* s, double dt) {
+  if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(s, BD_ERR_ARG, "dt must be positive");
+  return do_step(s, dt, 0, 0);
 }
 
 int bd_batch_step(bd_state_t* const* states, int n, double dt, int M, int K) {

@@ -78,6 +78,11 @@ cudaError_t launch_combine(int model, int64_t n, const double* src, const double
                            const double* w1, const double* k2v, const double* z2, const double* w2, double m1,
                            double m2, double* dst, cudaStream_t st, const int* gate = nullptr, double mhat1 = 0.0,
                            double etol = 1.0, unsigned long long* err = nullptr);
+// CN-RK2 reaction half step: Xout = X' + h f(X' + (h/2) f(X')), X' = X with
+// v += dv (dv may be NULL); avec = v_out + u when avec != NULL
+cudaError_t launch_rk2(int model, int precision, int64_t n, const double* X, const double* dv, double* Xout,
+                       double h, double inv_cm, double dt, const uint32_t* stim_bits, const double* t_now,
+                       const StimTable& stim, const double* u, double* avec, cudaStream_t st);
 cudaError_t launch_update(int model, int64_t n, const double* Xt, const double* ev, const double* z,
                           const double* w, double* dst, cudaStream_t st, const int* gate = nullptr);
 // sweep test of Algorithm 2: dmax = max |a - b| (dmax reset by the caller),

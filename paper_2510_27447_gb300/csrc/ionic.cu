@@ -198,6 +198,40 @@ __global__ void __launch_bounds__(kBlock) combine_kernel(int64_t n, const double
   }
 }
 
+// Reaction half step of the CN-RK2 splitting (Sec. 3.3.3): the explicit
+// midpoint rule over h = dt/2 on the node ODE system with the step's stimulus,
+//   X_mid = X + (h/2) f(X),   X_out = X + h f(X_mid),
+// starting from X with dv added to v (the Crank-Nicolson increment, or none).
+// With avec != nullptr also writes avec = v_out + u, the operand of the
+// diffusion step's right-hand side.
+template <template <class> class Model, class T>
+__global__ void __launch_bounds__(kBlock) rk2_kernel(int64_t n, const double* X, const double* dv, double* Xout,
+                                                     double h, double inv_cm, double dt, const uint32_t* stim_bits,
+                                                     const double* t_now, const StimTable stim, const double* u,
+                                                     double* avec, const Model<T> P) {
+  using Mod = Model<T>;
+  constexpr int NS = Mod::NS;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double istim = stim_current(stim_bits, i, stim, *t_now, dt);
+  double x[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) x[k] = X[k * n + i];
+  if (dv) x[0] += dv[i];
+  T xt[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) xt[k] = T(x[k]);
+  ValSink<T, Mod> f1;
+  P.eval(xt, T(istim), T(inv_cm), f1);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) xt[k] = T(x[k] + 0.5 * h * double(f1.f[k]));
+  ValSink<T, Mod> f2;
+  P.eval(xt, T(istim), T(inv_cm), f2);
+#pragma unroll
+  for (int k = 0; k < NS; ++k) Xout[k * n + i] = x[k] + h * double(f2.f[k]);
+  if (avec) avec[i] = x[0] + h * double(f2.f[0]) + u[i];
+}
+
 // X^new_{m+1} = X~_{m+1} + eps, eps_y = z + w eps_v
 template <int NS>
 __global__ void __launch_bounds__(kBlock) update_kernel(int64_t n, const double* Xt, const double* ev,
@@ -311,6 +345,23 @@ cudaError_t launch_field(int model, int precision, int64_t n, const double* X, d
     const bool pm = model == BD_LR91_PAPER_MOD;
     if (f32) field_kernel<LR91, float><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, LR91<float>::make(pm), gate);
     else field_kernel<LR91, double><<<grid, kBlock, 0, st>>>(n, X, inv_cm, dt, stim_bits, step_n, stim, fout, LR91<double>::make(pm), gate);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rk2(int model, int precision, int64_t n, const double* X, const double* dv, double* Xout,
+                       double h, double inv_cm, double dt, const uint32_t* stim_bits, const double* t_now,
+                       const StimTable& stim, const double* u, double* avec, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = unsigned((n + kBlock - 1) / kBlock);
+  const bool f32 = precision == BD_MIXED;
+  if (model == BD_TP06_EPI) {
+    if (f32) rk2_kernel<TP06, float><<<grid, kBlock, 0, st>>>(n, X, dv, Xout, h, inv_cm, dt, stim_bits, t_now, stim, u, avec, TP06<float>::make());
+    else rk2_kernel<TP06, double><<<grid, kBlock, 0, st>>>(n, X, dv, Xout, h, inv_cm, dt, stim_bits, t_now, stim, u, avec, TP06<double>::make());
+  } else {
+    const bool pm = model == BD_LR91_PAPER_MOD;
+    if (f32) rk2_kernel<LR91, float><<<grid, kBlock, 0, st>>>(n, X, dv, Xout, h, inv_cm, dt, stim_bits, t_now, stim, u, avec, LR91<float>::make(pm));
+    else rk2_kernel<LR91, double><<<grid, kBlock, 0, st>>>(n, X, dv, Xout, h, inv_cm, dt, stim_bits, t_now, stim, u, avec, LR91<double>::make(pm));
   }
   return cudaGetLastError();
 }

@@ -45,10 +45,10 @@ def test_bath_elliptic_solve_matches_direct_solve(precond, n_cells):
     w = _small(n_cells=n_cells)
     v = _v(w)
     u_ref = oracle_problem(w).elliptic(v)
-    sim = gpu_sim(w, cg_tol_e=1e-13, elliptic_precond=precond)
+    sim = gpu_sim(w, cg_tol_e=1e-11, elliptic_precond=precond)
     u, it = sim.solve_elliptic(v)
     assert u.shape == (w.n_nodes,) and u[w.pin_node] == 0.0
-    assert rel(u, u_ref) < 1e-10
+    assert rel(u, u_ref) < 1e-9
     assert np.ptp(u[w.n_tissue:]) > 1e-3 * np.ptp(u)      # the bath carries a field
     sim.close()
 
