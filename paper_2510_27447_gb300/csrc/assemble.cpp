@@ -107,10 +107,11 @@ int assemble_host(const bd_mesh_t* mesh, const bd_cond_t* cond, HostOps* out, st
     for (int64_t e = 0; e < E; ++e)
       for (int a = 0; a < k; ++a) nel[fill[mesh->elems[e * k + a]]++] = e;
   }
-  // element geometry and conductivities
-  std::vector<ElemGeom> geo(E);
+  // element geometry and conductivity tensors are recomputed wherever an
+  // element is used (once per node of it) instead of being stored: for meshes
+  // of tens of millions of elements the stored form would need ~250 bytes per
+  // element of host memory.  A first pass only validates.
   const double scale = 1.0 / (cond->chi * cond->cm);
-  std::vector<double> Si(E * 9), Sie(E * 9);
   const uint8_t* bath = mesh->elem_bath;
   // tissue nodes: the nodes of the tissue elements, numbered first
   out->n_tissue = N;
@@ -148,35 +149,35 @@ int assemble_host(const bd_mesh_t* mesh, const bd_cond_t* cond, HostOps* out, st
     }
     for (auto& x : th) x.join();
   };
-  par(E, [&](int64_t lo, int64_t hi, unsigned t) {
-    for (int64_t e = lo; e < hi; ++e) {
-      if (!elem_geom(dim, mesh->xyz, mesh->elems + e * k, &geo[e])) {
-        bad[t] = 1;
-        continue;
+  // geometry and the intra- / total conductivity tensors of element e;
+  // returns 0, 1 (degenerate element) or 2 (bad fibre)
+  auto element = [&](int64_t e, ElemGeom* G, double* Si, double* Sie) -> int {
+    if (!elem_geom(dim, mesh->xyz, mesh->elems + e * k, G)) return 1;
+    double f[3] = {1.0, 0.0, 0.0};
+    if (mesh->fiber) {
+      double nrm = 0.0;
+      for (int d = 0; d < dim; ++d) {
+        f[d] = mesh->fiber[e * dim + d];
+        nrm += f[d] * f[d];
       }
-      double f[3] = {1.0, 0.0, 0.0};
-      if (mesh->fiber) {
-        double nrm = 0.0;
-        for (int d = 0; d < dim; ++d) {
-          f[d] = mesh->fiber[e * dim + d];
-          nrm += f[d] * f[d];
-        }
-        nrm = std::sqrt(nrm);
-        if (!(nrm > 0.0) || !std::isfinite(nrm)) {
-          bad[t] = 2;
-          continue;
-        }
-        for (int d = 0; d < dim; ++d) f[d] /= nrm;
-      }
-      const bool b = bath && bath[e];
-      for (int r = 0; r < dim; ++r)
-        for (int c = 0; c < dim; ++c) {
-          const double ff = f[r] * f[c], id = (r == c) ? 1.0 : 0.0;
-          Si[e * 9 + r * 3 + c] = b ? 0.0 : cond->sit * id + (cond->sil - cond->sit) * ff;
-          Sie[e * 9 + r * 3 + c] = b ? cond->sbath * id
-                                     : (cond->sit + cond->set) * id + ((cond->sil + cond->sel) - (cond->sit + cond->set)) * ff;
-        }
+      nrm = std::sqrt(nrm);
+      if (!(nrm > 0.0) || !std::isfinite(nrm)) return 2;
+      for (int d = 0; d < dim; ++d) f[d] /= nrm;
     }
+    const bool b = bath && bath[e];
+    for (int r = 0; r < dim; ++r)
+      for (int c = 0; c < dim; ++c) {
+        const double ff = f[r] * f[c], id = (r == c) ? 1.0 : 0.0;
+        Si[r * 3 + c] = b ? 0.0 : cond->sit * id + (cond->sil - cond->sit) * ff;
+        Sie[r * 3 + c] = b ? cond->sbath * id
+                           : (cond->sit + cond->set) * id + ((cond->sil + cond->sel) - (cond->sit + cond->set)) * ff;
+      }
+    return 0;
+  };
+  par(E, [&](int64_t lo, int64_t hi, unsigned t) {
+    ElemGeom G;
+    double Si[9], Sie[9];
+    for (int64_t e = lo; e < hi && !bad[t]; ++e) bad[t] = element(e, &G, Si, Sie);
   });
   for (int b : bad)
     if (b) {
@@ -214,20 +215,22 @@ int assemble_host(const bd_mesh_t* mesh, const bd_cond_t* cond, HostOps* out, st
       const auto& cols = rows[i];
       std::memcpy(&out->col[r0], cols.data(), cols.size() * sizeof(int32_t));
       out->diagpos[i] = int32_t(r0 + (std::lower_bound(cols.begin(), cols.end(), int32_t(i)) - cols.begin()));
+      ElemGeom G;
+      double Si[9], Sie[9];
       for (int64_t q = nep[i]; q < nep[i + 1]; ++q) {
         const int64_t e = nel[q];
         const int32_t* en = mesh->elems + e * k;
         int la = 0;
         while (en[la] != i) ++la;
-        const ElemGeom& G = geo[e];
+        element(e, &G, Si, Sie);
         for (int b = 0; b < k; ++b) {
           const int64_t p = r0 + (std::lower_bound(cols.begin(), cols.end(), en[b]) - cols.begin());
           double si = 0.0, sie = 0.0;
           for (int r = 0; r < dim; ++r)
             for (int c = 0; c < dim; ++c) {
               const double gg = G.g[la][r] * G.g[b][c];
-              si += gg * Si[e * 9 + r * 3 + c];
-              sie += gg * Sie[e * 9 + r * 3 + c];
+              si += gg * Si[r * 3 + c];
+              sie += gg * Sie[r * 3 + c];
             }
           out->Ai[p] += G.meas * si * scale;
           out->Aie[p] += G.meas * sie * scale;

@@ -56,19 +56,14 @@ def square_grid(n: int, length: float = 1.0) -> Tuple[np.ndarray, np.ndarray]:
     return rect_grid(n, n, length, length)
 
 
-def slab_grid(nx: int, ny: int, nz: int, lx: float, ly: float, lz: float
-              ) -> Tuple[np.ndarray, np.ndarray]:
-    """Structured P1 tetrahedral mesh of [0,lx]x[0,ly]x[0,lz].
-
-    Node (i,j,k) has index (k*ny + j)*nx + i.  Every hexahedron is split into
-    the six Kuhn tetrahedra that share its (0,0,0)->(1,1,1) diagonal, so the
-    mesh is conforming.  Returns (xyz[N,3] float64, tets[E,4] int32).
-    """
+def lattice_tets(xs: np.ndarray, ys: np.ndarray, zs: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
+    """Tensor-product lattice of the coordinate vectors xs, ys, zs split into
+    P1 tetrahedra.  Node (i,j,k) has index (k*ny + j)*nx + i.  Every
+    hexahedron is split into the six Kuhn tetrahedra that share its
+    (0,0,0)->(1,1,1) diagonal, so the mesh is conforming."""
+    nx, ny, nz = len(xs), len(ys), len(zs)
     if min(nx, ny, nz) < 2:
-        raise ValueError("slab_grid needs at least 2 nodes per direction")
-    xs = np.linspace(0.0, lx, nx)
-    ys = np.linspace(0.0, ly, ny)
-    zs = np.linspace(0.0, lz, nz)
+        raise ValueError("a lattice needs at least 2 nodes per direction")
     Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
     xyz = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1).astype(np.float64)
     k, j, i = np.meshgrid(np.arange(nz - 1), np.arange(ny - 1), np.arange(nx - 1),
@@ -91,6 +86,31 @@ def slab_grid(nx: int, ny: int, nz: int, lx: float, ly: float, lz: float
         tets.append(np.stack([v000, node(*p1), node(*p2), v111], axis=1))
     tets = np.stack(tets, axis=1).reshape(-1, 4).astype(np.int32)
     return xyz, tets
+
+
+def slab_grid(nx: int, ny: int, nz: int, lx: float, ly: float, lz: float
+              ) -> Tuple[np.ndarray, np.ndarray]:
+    """Structured P1 tetrahedral mesh of [0,lx]x[0,ly]x[0,lz] with
+    nx x ny x nz nodes (see lattice_tets).  Returns (xyz[N,3], tets[E,4])."""
+    return lattice_tets(np.linspace(0.0, lx, nx), np.linspace(0.0, ly, ny), np.linspace(0.0, lz, nz))
+
+
+def graded_axis(lo: float, hi: float, h: float, margin: float, grade: float) -> np.ndarray:
+    """Coordinates of [lo - margin, hi + margin]: spacing h on [lo, hi'] (hi'
+    = lo + h*ceil((hi-lo)/h)), cells growing by the factor `grade` across each
+    margin (rescaled to fill it exactly)."""
+    n = int(np.ceil((hi - lo) / h - 1e-9))
+    core = lo + h * np.arange(n + 1)
+    cells = []
+    d, tot = h, 0.0
+    while tot < margin - 1e-12:
+        d *= grade
+        cells.append(d)
+        tot += d
+    cells = np.array(cells) * (margin / tot) if cells else np.zeros(0)
+    left = core[0] - np.cumsum(cells)[::-1]
+    right = core[-1] + np.cumsum(cells)
+    return np.concatenate([left, core, right])
 
 
 # ---------------------------------------------------------------------------
@@ -281,6 +301,98 @@ def bath_paper_2d(n_steps: int = 12000, dt: float = 0.05) -> Workload:
     120 ms), 600 ms."""
     return bath_sheet(800, -1.0, 7.0, 0.0, 6.0, LR91, dt, n_steps, s2=(120.0, 1.0, 3.0),
                       name="lr91_bath_801x801")
+
+
+# truncated prolate LV shell in a bath box (bidomain-bath, 3-D)
+LV_ENDO = (2.5, 2.5, 5.0)     # endocardial semi-axes, cm
+LV_WALL = 1.0                 # wall thickness, cm
+LV_ZCUT = 2.5                 # base plane z = +2.5 cm
+
+
+def _lv_radii(xyz: np.ndarray):
+    a, b, c = LV_ENDO
+    ri = np.sqrt((xyz[:, 0] / a) ** 2 + (xyz[:, 1] / b) ** 2 + (xyz[:, 2] / c) ** 2)
+    t = LV_WALL
+    ro = np.sqrt((xyz[:, 0] / (a + t)) ** 2 + (xyz[:, 1] / (b + t)) ** 2 + (xyz[:, 2] / (c + t)) ** 2)
+    return ri, ro
+
+
+def lv_shell_fibers(cen: np.ndarray, theta0: float = -60.0, theta1: float = 60.0) -> np.ndarray:
+    """Helical fibres: in the tangent plane of the ellipsoidal level set
+    through the centroid, f = cos(t) e_circ + sin(t) e_long with t rising
+    linearly from theta0 (endocardium) to theta1 (epicardium) in the
+    transmural coordinate e = (r_i - 1)/(r_i - r_o), r_i, r_o the scaled
+    radii of the endo- and epicardial ellipsoids."""
+    a, b, c = LV_ENDO
+    ri, ro = _lv_radii(cen)
+    e = np.clip((ri - 1.0) / np.maximum(ri - ro, 1e-12), 0.0, 1.0)
+    t = np.deg2rad(theta0 + (theta1 - theta0) * e)
+    n = np.stack([cen[:, 0] / a ** 2, cen[:, 1] / b ** 2, cen[:, 2] / c ** 2], axis=1)
+    n /= np.maximum(np.linalg.norm(n, axis=1, keepdims=True), 1e-300)
+    circ = np.stack([-cen[:, 1], cen[:, 0], np.zeros(len(cen))], axis=1)
+    cn = np.linalg.norm(circ, axis=1, keepdims=True)
+    circ = np.where(cn > 1e-9, circ / np.maximum(cn, 1e-300), np.array([[1.0, 0.0, 0.0]]))
+    lon = np.cross(n, circ)
+    lon /= np.maximum(np.linalg.norm(lon, axis=1, keepdims=True), 1e-300)
+    f = np.cos(t)[:, None] * circ + np.sin(t)[:, None] * lon
+    return f / np.linalg.norm(f, axis=1, keepdims=True)
+
+
+def lv_shell_bath(h: float = 0.04, margin: float = 1.0, grade: float = 1.3, jitter: float = 0.125,
+                  seed: int = 3, model: int = TP06_EPI, dt: float = 0.025, n_steps: int = 4000,
+                  sbath: float = BATH_SIGMA, s2_ms: float = 60.0, name: Optional[str] = None) -> Workload:
+    """Bidomain-bath LV model: a truncated prolate-ellipsoid shell
+    (endocardial semi-axes 2.5/2.5/5.0 cm, wall 1.0 cm, cut at z = +2.5 cm)
+    with helical -60..+60 deg fibres, embedded in a box bath extending
+    `margin` beyond it on every side.
+
+    Mesh: a tensor lattice of spacing h over the shell's bounding box and
+    geometrically growing cells across the margins (a coarser bath), every
+    interior node moved by a seeded uniform jitter of at most jitter*h_local
+    per axis (numpy PCG64(seed)), hexahedra split into Kuhn tetrahedra;
+    elements whose centroid lies in the wall (r_i >= 1, r_o <= 1, z <= cut)
+    are tissue, the rest bath (the cavity included).  Tissue nodes are
+    numbered first.  Stimuli: apical pacing on the tissue nodes within
+    0.3 cm of (0, 0, -(c + wall/2)) at t = 0 (2 ms, 100 uA/cm^2); an S2 on
+    the quadrant x > 0, y > 0, z > -2 of the wall at s2_ms."""
+    a, b, c = LV_ENDO
+    t = LV_WALL
+    xs = graded_axis(-(a + t), a + t, h, margin, grade)
+    ys = graded_axis(-(b + t), b + t, h, margin, grade)
+    zs = graded_axis(-(c + t), LV_ZCUT, h, margin, grade)
+    xyz, tets = lattice_tets(xs, ys, zs)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    for d, ax in enumerate((xs, ys, zs)):
+        sp = np.minimum(np.diff(ax)[:-1], np.diff(ax)[1:]) if len(ax) > 2 else np.zeros(0)
+        loc = np.concatenate([[0.0], sp, [0.0]])          # boundary nodes stay on the box faces
+        shape = [1, 1, 1]
+        shape[2 - d] = len(ax)
+        amp = np.broadcast_to(loc.reshape(shape), (len(zs), len(ys), len(xs))).ravel()
+        xyz[:, d] += jitter * amp * rng.uniform(-1.0, 1.0, size=len(xyz))
+    cen = np.zeros((len(tets), 3))
+    for q in range(4):                                   # centroids without a [E, 4, 3] temporary
+        cen += xyz[tets[:, q]]
+    cen *= 0.25
+    ri, ro = _lv_radii(cen)
+    tissue = (ri >= 1.0) & (ro <= 1.0) & (cen[:, 2] <= LV_ZCUT)
+    bath = (~tissue).astype(np.uint8)
+    fib = np.zeros((len(tets), 3))
+    fib[:, 0] = 1.0                                      # bath elements: unused
+    fib[tissue] = lv_shell_fibers(cen[tissue])
+    del cen, ri, ro
+    corner = 0                                           # (x_min, y_min, z_min), a bath node
+    xyz, tets, new_of_old = tissue_first(xyz, tets, bath)
+    nt = int(np.count_nonzero(np.bincount(tets[bath == 0].ravel(), minlength=len(xyz))))
+    tis = np.zeros(len(xyz), dtype=bool)
+    tis[:nt] = True
+    apex = np.array([0.0, 0.0, -(c + 0.5 * t)])
+    s1 = tis & (np.linalg.norm(xyz - apex, axis=1) <= 0.3)
+    s2 = tis & (xyz[:, 0] > 0) & (xyz[:, 1] > 0) & (xyz[:, 2] > -2.0)
+    stims = [Stimulus(s1.astype(np.uint8), 0.0, 2.0, 100.0),
+             Stimulus(s2.astype(np.uint8), s2_ms, 2.0, 100.0)]
+    return Workload(name=name or f"tp06_lv_shell_bath_h{h:g}", xyz=xyz, elems=tets, fibers=fib,
+                    sigma=tuple(CONFIG0_SIGMA), chi=2000.0, cm=1.0, model=model, stimuli=stims, dt=dt,
+                    n_steps=n_steps, pin_node=int(new_of_old[corner]), elem_bath=bath, sbath=sbath)
 
 
 def config0() -> Workload:

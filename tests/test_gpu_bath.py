@@ -104,3 +104,21 @@ def test_bath_checkpoint_and_adaptive_step():
     assert got == ref
     for p, q in zip(Xa, Xb):
         np.testing.assert_array_equal(p, q)
+
+
+def test_lv_shell_in_bath_matches_oracle():
+    """The 3-D bidomain-bath geometry (truncated prolate LV shell, helical
+    fibres, box bath) on a coarse jittered lattice: TP06 steps against the
+    oracle, FP64 and mixed."""
+    w = W.lv_shell_bath(h=0.35, n_steps=3)
+    assert w.n_tissue < w.n_nodes and w.stimuli[0].mask.sum() > 0
+    X0 = rest_X(w)
+    Xo, uo, _ = OB.run(oracle_problem(w), X0, 3, w.dt, 3, 2)
+    for prec, tx, tu in ((binding.FP64, 1e-10, 1e-8), (binding.MIXED, 1e-4, 1e-3)):
+        sim = gpu_sim(w, precision=prec, **(TIGHT if prec == binding.FP64 else {}))
+        sim.set_initial(X0)
+        for _ in range(3):
+            sim.step(w.dt)
+        v, u, X = sim.fields(full=True)
+        sim.close()
+        assert rel(X, Xo) < tx and rel(u, uo) < tu, prec
