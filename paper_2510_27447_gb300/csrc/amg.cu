@@ -176,21 +176,21 @@ int pcg_amg_max_blocks(int block) {
 }
 
 cudaError_t launch_pcg_amg(const PcgLaunch& P, const AmgDev& M, int wmax, cudaStream_t st) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(P.grid));
-  cfg.blockDim = dim3(unsigned(P.block));
-  cfg.stream = st;
+  cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  PcgLaunch K;
+  solver_launch_config(P, st, &cfg, attr, &K);
   switch (wmax) {
-    case 8: return cudaLaunchKernelEx(&cfg, pcg_amg_kernel<8>, P, M);
-    case 16: return cudaLaunchKernelEx(&cfg, pcg_amg_kernel<16>, P, M);
-    case 32: return cudaLaunchKernelEx(&cfg, pcg_amg_kernel<32>, P, M);
-    default: return cudaLaunchKernelEx(&cfg, pcg_amg_kernel<0>, P, M);
+    case 8: return cudaLaunchKernelEx(&cfg, pcg_amg_kernel<8>, K, M);
+    case 16: return cudaLaunchKernelEx(&cfg, pcg_amg_kernel<16>, K, M);
+    case 32: return cudaLaunchKernelEx(&cfg, pcg_amg_kernel<32>, K, M);
+    default: return cudaLaunchKernelEx(&cfg, pcg_amg_kernel<0>, K, M);
   }
+}
+
+bool amg_cluster_ok(int block, int size) {
+  return solver_cluster_ok(pcg_amg_kernel<8>, block, size) && solver_cluster_ok(pcg_amg_kernel<16>, block, size) &&
+         solver_cluster_ok(pcg_amg_kernel<32>, block, size) && solver_cluster_ok(pcg_amg_kernel<0>, block, size);
 }
 
 }  // namespace bd

@@ -110,6 +110,7 @@ struct bd_state {
   unsigned long long* d_err = nullptr;
   double *Xbak = nullptr, *ubak = nullptr, *tbak = nullptr;
   int pcg_grid = 1, pcg_block = 256, pcg_max = 1;
+  int cluster = 0;                         // > 0: solvers run as one cluster of this many 1024-thread blocks
   std::vector<void*> allocs;
   std::string err;
   int64_t steps = 0, sweeps = 0, ionic_evals = 0, launches = 0;
@@ -280,6 +281,8 @@ PcgLaunch pcg_base(bd_state* s) {
   P.status = s->d_status;
   P.grid = s->pcg_grid;
   P.block = s->pcg_block;
+  P.cluster = s->cluster;
+  if (s->cluster > 0) P.block = 1024;
   P.gate = s->opts.sweep_tol > 0 ? s->gate : nullptr;
   return P;
 }
@@ -550,6 +553,20 @@ int setup_amg(bd_state* s, const HostOps& H) {
     if (r_ != BD_OK) return r_;    \
   } while (0)
 
+}  // namespace
+
+namespace bd {
+int solver_cluster_size(int block, int want) {
+  for (int size : {16, 8}) {
+    if (size > want) continue;
+    if (pcg_cluster_ok(block, size) && amg_cluster_ok(block, size) && mixed_cluster_ok(block, size)) return size;
+  }
+  return 0;
+}
+}  // namespace bd
+
+namespace {
+
 // adaptive stepping: ladder dt_max 2^-k, k = 0..kAdaptLadder-1, controller
 // factor 0.9 err^(-1/2) clamped to [0.5, 2] (embedded solution of order 1)
 constexpr int kAdaptLadder = 8;
@@ -814,6 +831,7 @@ void bd_default_options(bd_opts_t* o) {
   o->spd_margin = 0.9;
   o->use_graph = 1;
   o->elliptic_precond = 1;
+  o->cg_cluster = -1;
 }
 
 int bd_num_states(bd_ionic_t model) { return model_ns(int(model)); }
@@ -950,6 +968,15 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   }
   const int64_t want = s->opts.cg_grid > 0 ? s->opts.cg_grid : (N + s->pcg_block - 1) / s->pcg_block;
   s->pcg_grid = int(std::max<int64_t>(1, std::min<int64_t>(want, s->pcg_max)));
+  {
+    const int cc = s->opts.cg_cluster;
+    if (cc != -1 && cc != 0 && cc != 8 && cc != 16) {
+      release(s);
+      delete s;
+      return fail(nullptr, BD_ERR_ARG, "cg_cluster must be -1, 0, 8 or 16");
+    }
+    if (cc > 0 || (cc == -1 && N <= BD_CLUSTER_AUTO_NODES)) s->cluster = solver_cluster_size(1024, cc > 0 ? cc : 16);
+  }
   if (ok) ok = alloc_n(s, &s->cg_part, int64_t(s->pcg_max) * 4);
   if (ok && s->opts.sweep_tol > 0)
     ok = alloc_n(s, &s->gate, 1) && alloc_n(s, &s->dmax, 1) && alloc_n(s, &s->Xsave, ns * NT);

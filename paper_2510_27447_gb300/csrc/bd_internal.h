@@ -145,7 +145,19 @@ struct PcgLaunch {
   const int* gate;          // optional: the solve is skipped when *gate == 0
   int grid;                 // co-resident blocks
   int block;
+  int cluster;              // > 0: one thread-block cluster of this many blocks (grid = cluster),
+                            // hardware cluster barriers; 0: cooperative grid, device-wide barriers
 };
+// launch configuration of a persistent solver kernel: cooperative grid, or a
+// single cluster (then the kernel gets bar = nullptr)
+void solver_launch_config(const PcgLaunch& P, cudaStream_t st, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr,
+                          PcgLaunch* Pk);
+// largest usable single-cluster size (16, 8 or 0) for the solver kernels at
+// this block size; enables non-portable cluster sizes where needed
+int solver_cluster_size(int block, int want);
+bool pcg_cluster_ok(int block, int size);     // pcg.cu
+bool amg_cluster_ok(int block, int size);     // amg.cu
+bool mixed_cluster_ok(int block, int size);   // mixed.cu
 cudaError_t launch_pcg(const PcgLaunch& P, int wmax, cudaStream_t st);
 int pcg_max_blocks(int block, int wmax);
 cudaError_t launch_axpby_vals(int64_t nnz, double a, const double* X, double b, const double* Y, double* out,

@@ -259,29 +259,35 @@ int pcg_mixed_max_blocks(int block) {
 
 cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const AmgDevF& M, int wmax, cudaStream_t st,
                              float* partf) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(P.grid));
-  cfg.blockDim = dim3(unsigned(P.block));
-  cfg.stream = st;
+  cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  PcgLaunch K;
+  solver_launch_config(P, st, &cfg, attr, &K);
   if (X.use_amg) {
     switch (wmax) {
-      case 8: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<8, true>, P, X, M, partf);
-      case 16: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<16, true>, P, X, M, partf);
-      case 32: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<32, true>, P, X, M, partf);
-      default: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<0, true>, P, X, M, partf);
+      case 8: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<8, true>, K, X, M, partf);
+      case 16: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<16, true>, K, X, M, partf);
+      case 32: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<32, true>, K, X, M, partf);
+      default: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<0, true>, K, X, M, partf);
     }
   }
   switch (wmax) {
-    case 8: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<8, false>, P, X, M, partf);
-    case 16: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<16, false>, P, X, M, partf);
-    case 32: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<32, false>, P, X, M, partf);
-    default: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<0, false>, P, X, M, partf);
+    case 8: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<8, false>, K, X, M, partf);
+    case 16: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<16, false>, K, X, M, partf);
+    case 32: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<32, false>, K, X, M, partf);
+    default: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<0, false>, K, X, M, partf);
   }
+}
+
+bool mixed_cluster_ok(int block, int size) {
+  return solver_cluster_ok(pcg_mixed_kernel<8, true>, block, size) &&
+         solver_cluster_ok(pcg_mixed_kernel<16, true>, block, size) &&
+         solver_cluster_ok(pcg_mixed_kernel<32, true>, block, size) &&
+         solver_cluster_ok(pcg_mixed_kernel<0, true>, block, size) &&
+         solver_cluster_ok(pcg_mixed_kernel<8, false>, block, size) &&
+         solver_cluster_ok(pcg_mixed_kernel<16, false>, block, size) &&
+         solver_cluster_ok(pcg_mixed_kernel<32, false>, block, size) &&
+         solver_cluster_ok(pcg_mixed_kernel<0, false>, block, size);
 }
 
 cudaError_t launch_to_float(int64_t n, const double* src, float* dst, cudaStream_t st) {

@@ -198,6 +198,11 @@ int max_blocks_t(int block) {
 }
 }  // namespace
 
+bool pcg_cluster_ok(int block, int size) {
+  return solver_cluster_ok(pcg_kernel<8>, block, size) && solver_cluster_ok(pcg_kernel<16>, block, size) &&
+         solver_cluster_ok(pcg_kernel<32>, block, size) && solver_cluster_ok(pcg_kernel<0>, block, size);
+}
+
 int pcg_max_blocks(int block, int wmax) {
   switch (wmax) {
     case 8: return max_blocks_t<8>(block);
@@ -207,22 +212,40 @@ int pcg_max_blocks(int block, int wmax) {
   }
 }
 
+void solver_launch_config(const PcgLaunch& P, cudaStream_t st, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr,
+                          PcgLaunch* Pk) {
+  *cfg = cudaLaunchConfig_t{};
+  *Pk = P;
+  cfg->blockDim = dim3(unsigned(P.block));
+  cfg->dynamicSmemBytes = 0;
+  cfg->stream = st;
+  cfg->attrs = attr;
+  cfg->numAttrs = 1;
+  if (P.cluster > 0) {
+    cfg->gridDim = dim3(unsigned(P.cluster));
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = unsigned(P.cluster);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    Pk->bar = nullptr;
+    Pk->grid = P.cluster;
+  } else {
+    cfg->gridDim = dim3(unsigned(P.grid));
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+  }
+}
+
 cudaError_t launch_pcg(const PcgLaunch& P, int wmax, cudaStream_t st) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(P.grid));
-  cfg.blockDim = dim3(unsigned(P.block));
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = st;
+  cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  PcgLaunch K;
+  solver_launch_config(P, st, &cfg, attr, &K);
   switch (wmax) {
-    case 8: return cudaLaunchKernelEx(&cfg, pcg_kernel<8>, P);
-    case 16: return cudaLaunchKernelEx(&cfg, pcg_kernel<16>, P);
-    case 32: return cudaLaunchKernelEx(&cfg, pcg_kernel<32>, P);
-    default: return cudaLaunchKernelEx(&cfg, pcg_kernel<0>, P);
+    case 8: return cudaLaunchKernelEx(&cfg, pcg_kernel<8>, K);
+    case 16: return cudaLaunchKernelEx(&cfg, pcg_kernel<16>, K);
+    case 32: return cudaLaunchKernelEx(&cfg, pcg_kernel<32>, K);
+    default: return cudaLaunchKernelEx(&cfg, pcg_kernel<0>, K);
   }
 }
 

@@ -30,7 +30,19 @@ __device__ __forceinline__ unsigned bar_add_acq_rel(unsigned* p, unsigned x) {
   return v;
 }
 
+// Single-cluster launches (bar == nullptr): the whole grid is one thread-block
+// cluster, and the barrier is the cluster's hardware barrier (every thread
+// arrives with release and waits with acquire semantics at cluster scope).
+// Every solver kernel reaches its barriers in grid-uniform control flow.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
+  if (bar == nullptr) {
+    cluster_barrier();
+    return true;
+  }
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -49,6 +61,32 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
   }
   __syncthreads();
   return ok != 0;
+}
+
+// can `kernel` run as one cluster of `size` blocks of `block` threads?
+// (non-portable sizes above 8 are enabled on the kernel first)
+template <class K>
+inline bool solver_cluster_ok(K kernel, int block, int size) {
+  if (size > 8 && cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(size));
+  cfg.blockDim = dim3(unsigned(block));
+  cudaLaunchAttribute a;
+  a.id = cudaLaunchAttributeClusterDimension;
+  a.val.clusterDim.x = unsigned(size);
+  a.val.clusterDim.y = 1;
+  a.val.clusterDim.z = 1;
+  cfg.attrs = &a;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n >= 1;
 }
 
 // block-wide sum of NV values; result valid in thread 0

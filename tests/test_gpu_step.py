@@ -164,3 +164,19 @@ def test_sweep_tolerance_matches_oracle():
     assert 12 < sweeps < 72                 # the test stopped some, not all, steps early
     assert st["sweeps"] == sweeps
     assert rel(Xg, X) < 1e-10 and rel(ug, u) < 1e-8
+
+
+@pytest.mark.parametrize("cluster", [0, 8, 16])
+def test_solver_launch_modes_match_oracle(cluster):
+    """The persistent CG kernels as a cooperative grid (device-wide barriers)
+    or as one thread-block cluster (hardware cluster barriers): same
+    solutions within the solver tolerance."""
+    w = W.sheet(17, 0.4, W.LR91, 0.02, 10, strip=0.06)
+    (X, u, ta, st), (Xo, uo, to) = _run_both(w, 10, 3, 2, True, cg_cluster=cluster)
+    assert rel(X, Xo) < 1e-10 and rel(u, uo) < 1e-8
+    for prec in (binding.FP64, binding.MIXED):
+        sim = gpu_sim(w, precision=prec, cg_cluster=cluster, cg_tol_e=1e-12)
+        v = -80 + 100 * np.exp(-30 * ((w.xyz[:, 0] - 0.1) ** 2 + (w.xyz[:, 1] - 0.3) ** 2))
+        u1, _ = sim.solve_elliptic(v)
+        sim.close()
+        assert rel(u1, oracle_problem(w).elliptic(v)) < 1e-9
