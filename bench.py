@@ -276,6 +276,59 @@ def bath_leg(args, torch, stream, flush) -> dict:
     return out
 
 
+def lv_leg(args, torch, stream, flush) -> dict:
+    """The 3-D bidomain-bath configuration: TP06 in a truncated prolate LV
+    shell inside a box bath (jittered Kuhn lattice, h = args.lv_h cm in the
+    shell's bounding box, coarser bath margins), dt = 0.025 ms, 3 Lobatto
+    nodes, 2 sweeps, mixed and FP64, from rest + apical pacing: node-steps/s
+    over all nodes."""
+    from paper_2510_27447_gb300 import binding, workloads as W
+    t0 = time.perf_counter()
+    w = W.lv_shell_bath(h=args.lv_h)
+    gen_s = time.perf_counter() - t0
+    out = {"workload": w.name, "nodes": w.n_nodes, "tissue_nodes": w.n_tissue, "elements": int(len(w.elems)),
+           "dt_ms": w.dt, "sigma_bath": w.sbath, "mesh_s": round(gen_s, 1)}
+    for name, prec in (("mixed", binding.MIXED), ("fp64", binding.FP64)):
+        with torch.cuda.stream(stream):
+            t0 = time.perf_counter()
+            opts = binding.default_options(precision=prec, stream=stream.cuda_stream, pin_node=w.pin_node,
+                                           cg_tol_e=1e-10, cg_tol_p=1e-10)
+            sim = binding.simulation_from_workload(w, opts)
+            setup = time.perf_counter() - t0
+            for _ in range(max(3, args.warmup)):
+                sim.step(w.dt, 3, 2)
+            sim.sync()
+            st0 = sim.stats()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.lv_steps):
+                flush.add_(1.0)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                sim.step(w.dt, 3, 2)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            sim.sync()
+            st1 = sim.stats()
+            prof = sim.profile_steps(w.dt, 3, 2, 2)
+            sim.close()
+        t = sum(ms) / len(ms)
+        tot = sum(prof["ms"].values())
+        out[name] = {"ms_per_step": round(t, 3), "value": round(w.n_nodes / (t / 1e3), 1),
+                     "setup_s": round(setup, 1),
+                     "cg_iters_e": round((st1["cg_iters_e"] - st0["cg_iters_e"]) /
+                                         max(1, st1["cg_solves_e"] - st0["cg_solves_e"]), 1),
+                     "cg_iters_p": round((st1["cg_iters_p"] - st0["cg_iters_p"]) /
+                                         max(1, st1["cg_solves_p"] - st0["cg_solves_p"]), 1),
+                     "share": {k: round(v / tot, 3) for k, v in prof["ms"].items()},
+                     "elliptic_alg_gbs": round(prof["alg_bytes"][0] / (prof["ms"]["pcg_elliptic"] / 1e3) / 1e9, 1),
+                     "parabolic_alg_gbs": round(prof["alg_bytes"][1] / (prof["ms"]["pcg_parabolic"] / 1e3) / 1e9, 1)}
+    out["steps"] = args.lv_steps
+    return out
+
+
 def serve_leg(args) -> dict:
     """Scaled serving workload (the 512-request, 400 ms stream is hours of GPU
     time): args.serve_requests Poisson(40/s) arrivals, sides 33/65/129,
@@ -372,6 +425,13 @@ def run_ours(args) -> None:
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
     share = {k: round(v / sum(prof["ms"].values()), 4) for k, v in prof["ms"].items()}
 
+    lv = None
+    if args.lv_steps > 0:
+        try:
+            lv = lv_leg(args, torch, stream, flush)
+        except Exception as e:  # noqa: BLE001
+            lv = {"error": str(e)[:200]}
+
     bath = None
     if args.bath_steps > 0:
         try:
@@ -424,6 +484,7 @@ def run_ours(args) -> None:
         "cpu_baseline": base,
         "serve": serve,
         "bath": bath,
+        "lv_shell_bath": lv,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -457,6 +518,9 @@ def main():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-ms", type=float, default=10.0)
+    ap.add_argument("--lv-steps", type=int, default=0,
+                    help="timed steps of the 3-D LV-shell-in-bath leg (0: skip; setup takes minutes)")
+    ap.add_argument("--lv-h", type=float, default=0.04, help="lattice spacing of the LV leg (cm)")
     ap.add_argument("--bath-steps", type=int, default=10,
                     help="timed steps of the 801^2 bidomain-bath leg (0: skip)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)

@@ -119,15 +119,13 @@ typedef struct {
   void (*free)(void* ptr, void* ctx);
   void* alloc_ctx;
   void* stream;          /* cudaStream_t or NULL (the library creates one) */
-  int cg_cluster;        /* persistent CG kernels as ONE thread-block cluster of this many
-                            1024-thread blocks with hardware cluster barriers instead of a
-                            cooperative grid with device-wide barriers (latency-bound small
-                            meshes): -1 = auto (default: 16, else 8, when the mesh has at most
-                            BD_CLUSTER_AUTO_NODES nodes and the device supports it), 0 = off,
-                            8 or 16 = on when supported */
+  int cg_cluster;        /* 0 (default): persistent CG kernels on a cooperative grid with
+                            device-wide barriers; 8 or 16: as ONE thread-block cluster of that
+                            many 1024-thread blocks with hardware cluster barriers (BD_ERR_ARG
+                            for other values; falls back to the grid when the device cannot
+                            schedule the cluster).  Measured slower on GB300 for 4k-263k-node
+                            meshes (16 SMs stream less than the grid); kept for experiments. */
 } bd_opts_t;
-
-#define BD_CLUSTER_AUTO_NODES 200000
 
 typedef struct bd_state bd_state_t;
 

@@ -37,6 +37,12 @@ void pattern_host(int model, uint32_t* masks);
 
 using namespace bd;
 
+// relative residual reduction of each FP32 inner solve of the mixed elliptic
+// refinement
+#ifndef BD_MIXED_TOL_INNER
+#define BD_MIXED_TOL_INNER 1e-4f
+#endif
+
 // ---------------------------------------------------------------------------
 // fixed scratch of bd_solve_elliptic_noalloc (see include/bd.h)
 // layout in doubles: r, z, p, q, 1/D (5 x max nodes), partial sums (4 x max
@@ -311,7 +317,7 @@ int elliptic(bd_state* s, const double* v, double* u) {
   if (s->precision == BD_MIXED) {
     MixedLaunch X = mixed_base(s);
     X.valA32 = s->fAie;
-    X.tol_inner = 1e-4f;
+    X.tol_inner = BD_MIXED_TOL_INNER;
     X.max_outer = 12;
     X.inner_cap = s->opts.cg_cap_e;
     X.use_amg = s->use_amg ? 1 : 0;
@@ -831,7 +837,7 @@ void bd_default_options(bd_opts_t* o) {
   o->spd_margin = 0.9;
   o->use_graph = 1;
   o->elliptic_precond = 1;
-  o->cg_cluster = -1;
+  o->cg_cluster = 0;
 }
 
 int bd_num_states(bd_ionic_t model) { return model_ns(int(model)); }
@@ -970,12 +976,12 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   s->pcg_grid = int(std::max<int64_t>(1, std::min<int64_t>(want, s->pcg_max)));
   {
     const int cc = s->opts.cg_cluster;
-    if (cc != -1 && cc != 0 && cc != 8 && cc != 16) {
+    if (cc != 0 && cc != 8 && cc != 16) {
       release(s);
       delete s;
-      return fail(nullptr, BD_ERR_ARG, "cg_cluster must be -1, 0, 8 or 16");
+      return fail(nullptr, BD_ERR_ARG, "cg_cluster must be 0, 8 or 16");
     }
-    if (cc > 0 || (cc == -1 && N <= BD_CLUSTER_AUTO_NODES)) s->cluster = solver_cluster_size(1024, cc > 0 ? cc : 16);
+    if (cc > 0) s->cluster = solver_cluster_size(1024, cc);
   }
   if (ok) ok = alloc_n(s, &s->cg_part, int64_t(s->pcg_max) * 4);
   if (ok && s->opts.sweep_tol > 0)
