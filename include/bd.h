@@ -125,7 +125,13 @@ typedef struct {
                             for other values; falls back to the grid when the device cannot
                             schedule the cluster).  Measured slower on GB300 for 4k-263k-node
                             meshes (16 SMs stream less than the grid); kept for experiments. */
+  int amg_cycle;         /* AMG V(1,1) cycle form: 0 = auto (default: fused up to
+                            BD_AMG_FUSED_AUTO_ROWS rows), 1 = classic (four device barriers
+                            per level), 2 = fused (two per level: precomputed R (I - w A D^-1)
+                            and A P; more operator bytes, fewer latency-bound phases) */
 } bd_opts_t;
+
+#define BD_AMG_FUSED_AUTO_ROWS 1000000
 
 typedef struct bd_state bd_state_t;
 

@@ -1,7 +1,7 @@
 """Summarise an `ncu --metrics gpu__time_duration.sum --csv` launch list:
 per kernel (demangled short name) its launches, total time and share.
 
-usage: python profiles/summarize_launches.py <launches.csv>
+usage: python -m paper_2510_27447_gb300.launch_summary <launches.csv>
 """
 import csv
 import re
