@@ -112,8 +112,8 @@ typedef struct {
   int elliptic_precond;  /* 1: aggregation AMG V(1,1) cycle (default; meshes small enough
                             for the dense coarse level use Jacobi), 0: Jacobi */
   int amg_coarse_max;    /* rows of the dense coarsest AMG level (0 = default 1500) */
-  int cg_block;          /* CG threads per block (0 = auto: 256) */
-  int cg_grid;           /* CG blocks (0 = auto: one per 256 rows, at most the co-resident maximum) */
+  int cg_block;          /* CG threads per block (0 = auto: 512) */
+  int cg_grid;           /* CG blocks (0 = auto: one per cg_block rows, at most the co-resident maximum) */
   /* device memory hooks (NULL => cudaMalloc/cudaFree); ctx is passed back */
   void* (*alloc)(size_t bytes, void* ctx);
   void (*free)(void* ptr, void* ctx);
@@ -125,13 +125,13 @@ typedef struct {
                             for other values; falls back to the grid when the device cannot
                             schedule the cluster).  Measured slower on GB300 for 4k-263k-node
                             meshes (16 SMs stream less than the grid); kept for experiments. */
-  int amg_cycle;         /* AMG V(1,1) cycle form: 0 = auto (default: fused up to
-                            BD_AMG_FUSED_AUTO_ROWS rows), 1 = classic (four device barriers
-                            per level), 2 = fused (two per level: precomputed R (I - w A D^-1)
-                            and A P; more operator bytes, fewer latency-bound phases) */
+  int amg_cycle;         /* AMG V(1,1) cycle form: 0 (default) = classic, four device barriers
+                            per level; 1 = fused, two per level (precomputed R (I - w A D^-1)
+                            and A P, each thread recomputing the smoothed values of the
+                            neighbours it reads).  The same preconditioner in exact
+                            arithmetic; measured 5-40 % slower on GB300 (heavier phases
+                            outweigh the saved barriers), kept for experiments. */
 } bd_opts_t;
-
-#define BD_AMG_FUSED_AUTO_ROWS 1000000
 
 typedef struct bd_state bd_state_t;
 

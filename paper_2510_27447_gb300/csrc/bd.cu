@@ -117,7 +117,7 @@ struct bd_state {
   double dt_adapt = 0.0;                   // next step size (0: start at dt_max)
   unsigned long long* d_err = nullptr;
   double *Xbak = nullptr, *ubak = nullptr, *tbak = nullptr;
-  int pcg_grid = 1, pcg_block = 256, pcg_max = 1;
+  int pcg_grid = 1, pcg_block = 512, pcg_max = 1;
   int cluster = 0;                         // > 0: solvers run as one cluster of this many 1024-thread blocks
   std::vector<void*> allocs;
   std::string err;
@@ -445,7 +445,7 @@ int setup_amg(bd_state* s, const HostOps& H) {
   std::string err;
   AmgParams prm;
   if (s->opts.amg_coarse_max > 0) prm.coarse_max = s->opts.amg_coarse_max;
-  prm.fused = s->opts.amg_cycle == 2 || (s->opts.amg_cycle == 0 && s->N <= BD_AMG_FUSED_AUTO_ROWS);
+  prm.fused = s->opts.amg_cycle == 1;
   const int rc = amg_build(A, prm, &AH, &err);
   if (rc != BD_OK) return fail(s, rc, "%s", err.c_str());
   if (AH.lev.empty()) return BD_OK;   // small operator: Jacobi-PCG is used
@@ -855,6 +855,7 @@ void bd_default_options(bd_opts_t* o) {
   o->use_graph = 1;
   o->elliptic_precond = 1;
   o->cg_cluster = 0;
+  o->amg_cycle = 0;
 }
 
 int bd_num_states(bd_ionic_t model) { return model_ns(int(model)); }
@@ -978,7 +979,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   for (int m = 0; ok && m < kMaxNodes; ++m)
     ok = alloc_n(s, &s->Xt[m], ns * NT) && alloc_n(s, &s->Xc[m], ns * NT) && alloc_n(s, &s->fq[m], ns * NT) &&
          alloc_n(s, &s->u[m], N);
-  s->pcg_block = s->opts.cg_block > 0 ? s->opts.cg_block : 256;
+  s->pcg_block = s->opts.cg_block > 0 ? s->opts.cg_block : 512;
   if (s->pcg_block % 32 != 0 || s->pcg_block > 1024) {
     release(s);
     delete s;
@@ -1000,10 +1001,10 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
       return fail(nullptr, BD_ERR_ARG, "cg_cluster must be 0, 8 or 16");
     }
     if (cc > 0) s->cluster = solver_cluster_size(1024, cc);
-    if (s->opts.amg_cycle < 0 || s->opts.amg_cycle > 2) {
+    if (s->opts.amg_cycle != 0 && s->opts.amg_cycle != 1) {
       release(s);
       delete s;
-      return fail(nullptr, BD_ERR_ARG, "amg_cycle must be 0, 1 or 2");
+      return fail(nullptr, BD_ERR_ARG, "amg_cycle must be 0 or 1");
     }
   }
   if (ok) ok = alloc_n(s, &s->cg_part, int64_t(s->pcg_max) * 4);
