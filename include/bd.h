@@ -125,12 +125,6 @@ typedef struct {
                             for other values; falls back to the grid when the device cannot
                             schedule the cluster).  Measured slower on GB300 for 4k-263k-node
                             meshes (16 SMs stream less than the grid); kept for experiments. */
-  int amg_cycle;         /* AMG V(1,1) cycle form: 0 (default) = classic, four device barriers
-                            per level; 1 = fused, two per level (precomputed R (I - w A D^-1)
-                            and A P, each thread recomputing the smoothed values of the
-                            neighbours it reads).  The same preconditioner in exact
-                            arithmetic; measured 5-40 % slower on GB300 (heavier phases
-                            outweigh the saved barriers), kept for experiments. */
 } bd_opts_t;
 
 typedef struct bd_state bd_state_t;

@@ -62,7 +62,7 @@ class Opts(C.Structure):
                 ("elliptic_precond", C.c_int), ("amg_coarse_max", C.c_int), ("cg_block", C.c_int),
                 ("cg_grid", C.c_int),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("stream", C.c_void_p), ("cg_cluster", C.c_int), ("amg_cycle", C.c_int)]
+                ("stream", C.c_void_p), ("cg_cluster", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -14,9 +14,7 @@
 //   prolongator P = (I - omega D^-1 A) T, T the aggregate indicator,
 //              omega = 4 / (3 rho(D^-1 A)) (rho by power iteration)
 //   coarse op  A_c = P^T A P
-// until the operator has at most `coarse_max` rows (with `fused`, also
-//   Q = R (I - omega A D^-1) and A P for the cycle of vcycle.cuh that needs
-//   only two device barriers per level); that last operator is
+// until the operator has at most `coarse_max` rows; that last operator is
 // singular (A 1 = 0 is preserved: T 1 = 1 and A 1 = 0), so its solve uses the
 // dense inverse of A_c + c 1 1^T, which returns the zero-mean solution for any
 // right-hand side orthogonal to 1.
@@ -291,38 +289,7 @@ int amg_build(const HCsr& A0, const AmgParams& prm, AmgHost* out, std::string* e
       }
     }
     HCsr R = transpose(P);
-    HCsr AP = spgemm(A, P);
-    HCsr Ac = spgemm(R, AP);
-    if (prm.fused) {
-      // Q = R (I - w D^-1 ... ) with the smoother weight: B = I - w A D^-1
-      HCsr B = A;
-      for (int64_t i = 0; i < A.n; ++i)
-        for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) {
-          const int64_t j = A.ci[p];
-          B.v[p] = (j == i ? 1.0 : 0.0) - w * A.v[p] / d[j];
-        }
-      L.Q = spgemm(R, B);
-      // P's values on A P's pattern (P's columns of a row are among A P's)
-      HCsr UP = AP;
-      for (int64_t i = 0; i < A.n; ++i) {
-        int64_t q = P.rp[i], matched = 0;
-        for (int64_t p = AP.rp[i]; p < AP.rp[i + 1]; ++p) {
-          double v = 0.0;
-          while (q < P.rp[i + 1] && P.ci[q] < AP.ci[p]) ++q;
-          if (q < P.rp[i + 1] && P.ci[q] == AP.ci[p]) {
-            v = P.v[q];
-            ++matched;
-          }
-          UP.v[p] = v;
-        }
-        if (matched != P.rp[i + 1] - P.rp[i]) {
-          *err = "AMG: a column of P is missing from the pattern of A P";
-          return BD_ERR_ARG;
-        }
-      }
-      L.U = std::move(AP);
-      L.UP = std::move(UP);
-    }
+    HCsr Ac = spgemm(R, spgemm(A, P));
     L.invdiag.resize(A.n);
     for (int64_t i = 0; i < A.n; ++i) L.invdiag[i] = 1.0 / d[i];
     L.omega = 4.0 / (3.0 * rho);

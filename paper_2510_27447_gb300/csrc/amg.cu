@@ -24,7 +24,11 @@ namespace bd {
 namespace {
 
 template <int WMAX>
-__global__ void __launch_bounds__(1024) pcg_amg_kernel(const PcgLaunch a, const AmgDev M) {
+__global__ void __launch_bounds__(1024, 1) pcg_amg_kernel(const __grid_constant__ PcgLaunch a,
+                                                           const AmgDev* __restrict__ Mp) {
+  // the descriptor lives in global memory: level loops index it at run time,
+  // which a by-value kernel parameter would turn into a local-memory copy
+  const AmgDev& M = *Mp;
   __shared__ double sh[4][32];
   if (a.gate && *a.gate == 0) return;
   const int n = a.n;
@@ -58,27 +62,15 @@ __global__ void __launch_bounds__(1024) pcg_amg_kernel(const PcgLaunch a, const 
   double bb = a.project ? tot[1] - double(n) * mean_b * mean_b : tot[1];
   if (bb < 0.0) bb = 0.0;
   const double tol2 = a.tol * a.tol * bb;
-  // the fused cycle folds the CG residual update into its first phase, so the
-  // residual ping-pongs between r and r2 (neighbours recompute r - alpha q)
-  double* rc = a.r;
-  double* rn = a.r2;
   double rr_loc = 0.0;
   for (int i = i0; i < n; i += stride) {
-    const double r = rc[i] - mean_b;
-    rc[i] = r;
+    const double r = a.r[i] - mean_b;
+    a.r[i] = r;
     rr_loc += r * r;
   }
-  double rz_loc = 0.0;
-  if (M.fused) {
-    if (!grid_barrier(a.bar, nb, a.status)) return;
-    auto b0 = [&](int j) { return __ldcg(rc + j); };
-    auto zh = [&](int i, double z) { rz_loc += __ldcg(rc + i) * z; };
-    if (!vcycle_fused<double>(M, b0, a.z, zh, a.bar, nb, a.status)) return;
-  } else {
-    if (!vcycle<double>(M, rc, a.z, a.bar, nb, a.status)) return;
-    for (int i = i0; i < n; i += stride) rz_loc += rc[i] * a.z[i];
-  }
-  double acc1[2] = {rz_loc, rr_loc};
+  if (!vcycle<double>(M, a.r, a.z, a.bar, nb, a.status)) return;
+  double acc1[2] = {0.0, rr_loc};
+  for (int i = i0; i < n; i += stride) acc1[0] += a.r[i] * a.z[i];
   block_sum<2>(acc1, sh);
   if (threadIdx.x == 0) {
     a.part[blockIdx.x * 4 + 2] = acc1[0];
@@ -113,32 +105,16 @@ __global__ void __launch_bounds__(1024) pcg_amg_kernel(const PcgLaunch a, const 
       break;
     }
     const double alpha = rho / t1[0];
-    double rrl = 0.0, rz = 0.0;
-    if (M.fused) {
-      for (int i = i0; i < n; i += stride) {
-        a.x[i] += alpha * a.p[i];
-        const double r = fma(-alpha, a.q[i], rc[i]);
-        rn[i] = r;
-        rrl += r * r;
-      }
-      const double* q = a.q;
-      auto b0 = [&](int j) { return fma(-alpha, __ldcg(q + j), __ldcg(rc + j)); };
-      auto zh = [&](int i, double z) { rz += __ldcg(rn + i) * z; };
-      if (!vcycle_fused<double>(M, b0, a.z, zh, a.bar, nb, a.status)) return;
-      double* t = rc;
-      rc = rn;
-      rn = t;
-    } else {
-      for (int i = i0; i < n; i += stride) {
-        a.x[i] += alpha * a.p[i];
-        const double r = rc[i] - alpha * a.q[i];
-        rc[i] = r;
-        rrl += r * r;
-      }
-      if (!vcycle<double>(M, rc, a.z, a.bar, nb, a.status)) return;
-      for (int i = i0; i < n; i += stride) rz += rc[i] * a.z[i];
+    double rrl = 0.0;
+    for (int i = i0; i < n; i += stride) {
+      a.x[i] += alpha * a.p[i];
+      const double r = a.r[i] - alpha * a.q[i];
+      a.r[i] = r;
+      rrl += r * r;
     }
-    double acc[2] = {rz, rrl};
+    if (!vcycle<double>(M, a.r, a.z, a.bar, nb, a.status)) return;
+    double acc[2] = {0.0, rrl};
+    for (int i = i0; i < n; i += stride) acc[0] += a.r[i] * a.z[i];
     block_sum<2>(acc, sh);
     if (threadIdx.x == 0) {
       a.part[blockIdx.x * 4 + 2] = acc[0];
@@ -203,7 +179,7 @@ int pcg_amg_max_blocks(int block) {
   return m;
 }
 
-cudaError_t launch_pcg_amg(const PcgLaunch& P, const AmgDev& M, int wmax, cudaStream_t st) {
+cudaError_t launch_pcg_amg(const PcgLaunch& P, const AmgDev* M, int wmax, cudaStream_t st) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];
   PcgLaunch K;

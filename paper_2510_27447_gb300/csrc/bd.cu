@@ -74,6 +74,8 @@ struct bd_state {
   bool use_amg = false;
   AmgDev amg{};
   AmgDevF amgf{};                 // FP32 copy of the hierarchy (mixed path)
+  AmgDev* d_amg = nullptr;        // device copies of the two descriptors (kernel arguments)
+  AmgDevF* d_amgf = nullptr;
   // mixed path: FP32 operator values and CG workspaces
   float* fAie = nullptr;
   struct PCF { double alpha; float* val; };
@@ -91,8 +93,6 @@ struct bd_state {
   double *Xn = nullptr, *Xt[kMaxNodes] = {}, *Xc[kMaxNodes] = {}, *fq[kMaxNodes] = {}, *u[kMaxNodes] = {};
   double *dgs = nullptr, *rl = nullptr, *z1 = nullptr, *w1 = nullptr, *z2 = nullptr, *w2 = nullptr;
   double *k1v = nullptr, *k2v = nullptr, *avec = nullptr, *bvec = nullptr;
-  double* cg_r2 = nullptr;
-  float* r32b = nullptr;
   double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_invd = nullptr, *cg_part = nullptr;
   unsigned* bar = nullptr;
   double* t_act = nullptr;
@@ -267,7 +267,6 @@ MixedLaunch mixed_base(bd_state* s) {
   X.q32 = s->q32;
   X.invd32 = s->invd32;
   X.d32 = s->d32;
-  X.r32b = s->r32b;
   X.b64 = s->b64;
   X.r64 = s->r64;
   return X;
@@ -281,7 +280,6 @@ PcgLaunch pcg_base(bd_state* s) {
   P.col = s->col;
   P.diagpos = s->diagpos;
   P.r = s->cg_r;
-  P.r2 = s->cg_r2;
   P.z = s->cg_z;
   P.p = s->cg_p;
   P.q = s->cg_q;
@@ -326,10 +324,10 @@ int elliptic(bd_state* s, const double* v, double* u) {
     X.inner_cap = s->opts.cg_cap_e;
     X.use_amg = s->use_amg ? 1 : 0;
     P.grid = s->mixed_grid;
-    CK(launch_pcg_mixed(P, X, s->amgf, s->wmax, s->stream, s->partf));
+    CK(launch_pcg_mixed(P, X, s->d_amgf, s->wmax, s->stream, s->partf));
   } else if (s->use_amg) {
     P.grid = s->amg_grid;
-    CK(launch_pcg_amg(P, s->amg, s->wmax, s->stream));
+    CK(launch_pcg_amg(P, s->d_amg, s->wmax, s->stream));
   } else {
     CK(launch_pcg(P, s->wmax, s->stream));
   }
@@ -371,7 +369,7 @@ int parabolic(bd_state* s, double alpha, double c1, const double* va, double c2,
     X.inner_cap = s->opts.cg_cap_p;
     X.use_amg = 0;
     P.grid = s->mixed_grid;
-    CK(launch_pcg_mixed(P, X, s->amgf, s->wmax, s->stream, s->partf));
+    CK(launch_pcg_mixed(P, X, s->d_amgf, s->wmax, s->stream, s->partf));
   } else {
     CK(launch_pcg(P, s->wmax, s->stream));
   }
@@ -445,7 +443,6 @@ int setup_amg(bd_state* s, const HostOps& H) {
   std::string err;
   AmgParams prm;
   if (s->opts.amg_coarse_max > 0) prm.coarse_max = s->opts.amg_coarse_max;
-  prm.fused = s->opts.amg_cycle == 1;
   const int rc = amg_build(A, prm, &AH, &err);
   if (rc != BD_OK) return fail(s, rc, "%s", err.c_str());
   if (AH.lev.empty()) return BD_OK;   // small operator: Jacobi-PCG is used
@@ -482,11 +479,6 @@ int setup_amg(bd_state* s, const HostOps& H) {
       ok = sell_dev(Lh.A, &Ld.A);
     }
     ok = ok && sell_dev(Lh.P, &Ld.P) && sell_dev(Lh.R, &Ld.R);
-    if (prm.fused) {
-      SellDev up{};
-      ok = ok && sell_dev(Lh.Q, &Ld.Q) && sell_dev(Lh.U, &Ld.U) && sell_dev(Lh.UP, &up);
-      Ld.uP = up.val;   // same pattern as U, so the same layout
-    }
     Ld.invd = static_cast<const double*>(upload(Lh.invdiag.data(), Lh.invdiag.size() * 8));
     Ld.omega = Lh.omega;
     const int64_t n = Lh.A.n;
@@ -494,7 +486,6 @@ int setup_amg(bd_state* s, const HostOps& H) {
     if (l > 0) ok = ok && alloc_n(s, &Ld.b, n) && alloc_n(s, &Ld.y, n);
     if (!ok || cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, BD_ERR_OOM, "AMG upload failed");
   }
-  M.fused = prm.fused ? 1 : 0;
   M.nc = int(AH.nc);
   M.cinv = static_cast<const double*>(upload(AH.cinv.data(), AH.cinv.size() * 8));
   if (!M.cinv || !alloc_n(s, &M.bc, AH.nc) || !alloc_n(s, &M.xc, AH.nc) ||
@@ -517,7 +508,6 @@ int setup_amg(bd_state* s, const HostOps& H) {
     };
     AmgDevF& F = s->amgf;
     F.nlev = M.nlev;
-    F.fused = M.fused;
     for (int l = 0; l < F.nlev; ++l) {
       const AmgHostLevel& Lh = AH.lev[l];
       AmgLevelDevT<float>& Ld = F.L[l];
@@ -525,11 +515,6 @@ int setup_amg(bd_state* s, const HostOps& H) {
       if (l == 0) Ld.A = SellDevT<float>{int(s->N), s->wmax, s->sptr, s->swidth, s->col, s->fAie, nullptr};
       else ok = sell_devf(Lh.A, &Ld.A);
       ok = ok && sell_devf(Lh.P, &Ld.P) && sell_devf(Lh.R, &Ld.R);
-      if (prm.fused) {
-        SellDevT<float> up{};
-        ok = ok && sell_devf(Lh.Q, &Ld.Q) && sell_devf(Lh.U, &Ld.U) && sell_devf(Lh.UP, &up);
-        Ld.uP = up.val;
-      }
       std::vector<float> fid(Lh.invdiag.begin(), Lh.invdiag.end());
       Ld.invd = static_cast<const float*>(upload(fid.data(), fid.size() * 4));
       Ld.omega = float(Lh.omega);
@@ -566,6 +551,11 @@ int setup_amg(bd_state* s, const HostOps& H) {
     s->amg_cycle_bytes[v] = b;
   }
   s->amg_levels = M.nlev;
+  // the kernels read the descriptors from device memory
+  if (cudaMemcpyAsync(s->d_amg, &s->amg, sizeof(AmgDev), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+      cudaMemcpyAsync(s->d_amgf, &s->amgf, sizeof(AmgDevF), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return fail(s, BD_ERR_CUDA, "AMG descriptor upload failed");
   s->use_amg = true;
   return BD_OK;
 }
@@ -855,7 +845,6 @@ void bd_default_options(bd_opts_t* o) {
   o->use_graph = 1;
   o->elliptic_precond = 1;
   o->cg_cluster = 0;
-  o->amg_cycle = 0;
 }
 
 int bd_num_states(bd_ionic_t model) { return model_ns(int(model)); }
@@ -970,12 +959,14 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
             alloc_n(s, &s->w2, (ns - 1) * NT) && alloc_n(s, &s->k1v, N) && alloc_n(s, &s->k2v, N) &&
             alloc_n(s, &s->avec, N) && alloc_n(s, &s->bvec, N) && alloc_n(s, &s->cg_r, N) &&
             alloc_n(s, &s->cg_z, N) && alloc_n(s, &s->cg_p, N) && alloc_n(s, &s->cg_q, N) &&
-            alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->cg_r2, N) && alloc_n(s, &s->t_act, NT) &&
+            alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->t_act, NT) &&
             alloc_n(s, &s->stim_bits, NT) &&
             (NT == N || alloc_n(s, &s->vfull, N)) &&
             alloc_n(s, &s->step_n, 1) && alloc_n(s, &s->t_now, 1) && alloc_n(s, &s->d_err, 1) &&
             alloc_n(s, &s->d_status, 1) && alloc_n(s, &s->d_stats, 8) &&
-            alloc_n(s, &s->d_clamps, 1) && alloc_n(s, &s->bar, 2);
+            alloc_n(s, &s->d_clamps, 1) && alloc_n(s, &s->bar, 2) &&
+            alloc_n(s, reinterpret_cast<char**>(&s->d_amg), int64_t(sizeof(AmgDev))) &&
+            alloc_n(s, reinterpret_cast<char**>(&s->d_amgf), int64_t(sizeof(AmgDevF)));
   for (int m = 0; ok && m < kMaxNodes; ++m)
     ok = alloc_n(s, &s->Xt[m], ns * NT) && alloc_n(s, &s->Xc[m], ns * NT) && alloc_n(s, &s->fq[m], ns * NT) &&
          alloc_n(s, &s->u[m], N);
@@ -1001,11 +992,6 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
       return fail(nullptr, BD_ERR_ARG, "cg_cluster must be 0, 8 or 16");
     }
     if (cc > 0) s->cluster = solver_cluster_size(1024, cc);
-    if (s->opts.amg_cycle != 0 && s->opts.amg_cycle != 1) {
-      release(s);
-      delete s;
-      return fail(nullptr, BD_ERR_ARG, "amg_cycle must be 0 or 1");
-    }
   }
   if (ok) ok = alloc_n(s, &s->cg_part, int64_t(s->pcg_max) * 4);
   if (ok && s->opts.sweep_tol > 0)
@@ -1013,7 +999,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   if (ok && s->precision == BD_MIXED) {
     ok = alloc_n(s, &s->fAie, s->ell_n) && alloc_n(s, &s->r32, N) && alloc_n(s, &s->z32, N) &&
          alloc_n(s, &s->p32, N) && alloc_n(s, &s->q32, N) && alloc_n(s, &s->invd32, N) &&
-         alloc_n(s, &s->d32, N) && alloc_n(s, &s->r32b, N) && alloc_n(s, &s->b64, N) && alloc_n(s, &s->r64, N) &&
+         alloc_n(s, &s->d32, N) && alloc_n(s, &s->b64, N) && alloc_n(s, &s->r64, N) &&
          alloc_n(s, &s->partf, int64_t(s->pcg_max) * 4);
     const int mx = pcg_mixed_max_blocks(s->pcg_block);
     if (ok && mx <= 0) ok = false;
@@ -1045,15 +1031,17 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   // must still hold finite numbers there (0 * NaN would poison a row), so
   // every node-length vector starts at zero.  Afterwards only the elliptic
   // solves write the bath entries, with finite values.
-  for (double* v : {s->k1v, s->k2v, s->avec, s->bvec, s->cg_r, s->cg_r2, s->cg_z, s->cg_p, s->cg_q, s->cg_invd,
+  for (double* v : {s->k1v, s->k2v, s->avec, s->bvec, s->cg_r, s->cg_z, s->cg_p, s->cg_q, s->cg_invd,
                     s->vfull, s->b64, s->r64})
     if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, N * 8, s->stream);
-  for (float* v : {s->r32, s->r32b, s->z32, s->p32, s->q32, s->invd32, s->d32})
+  for (float* v : {s->r32, s->z32, s->p32, s->q32, s->invd32, s->d32})
     if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, N * 4, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->bar, 0, 8, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, 4, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_stats, 0, 64, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_clamps, 0, 8, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_amg, 0, sizeof(AmgDev), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_amgf, 0, sizeof(AmgDevF), s->stream);
   // the mass values outlive this scope only through the device copies; wait
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) {

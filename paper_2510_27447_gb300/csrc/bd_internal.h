@@ -132,7 +132,6 @@ struct PcgLaunch {
   int pin;                  // >= 0 pin node, -1 zero mean, -2 none
   // workspaces
   double* r;
-  double* r2;               // second residual buffer (fused AMG cycle)
   double* z;
   double* p;
   double* q;
@@ -173,14 +172,12 @@ struct HCsr {                      // host CSR, n x m
   std::vector<double> v;
 };
 struct AmgParams {
-  bool fused = false;              // also build the operators of the fused cycle
   double theta = 0.08;             // strength-of-connection threshold
   int64_t coarse_max = 1500;       // rows of the dense coarsest solve
   int max_levels = 9;
 };
 struct AmgHostLevel {
   HCsr A, P, R;                    // A: n x n, P: n x n_next, R = P^T
-  HCsr Q, U, UP;                   // fused cycle: R (I - omega A D^-1), A P, P on A P's pattern
   std::vector<double> invdiag;
   double omega = 0.0;              // damped-Jacobi weight 4 / (3 rho(D^-1 A))
 };
@@ -216,10 +213,6 @@ struct SellDevT {
 template <class T>
 struct AmgLevelDevT {
   SellDevT<T> A, P, R;
-  // fused cycle: Q = R (I - omega A D^-1) maps the level's right-hand side to
-  // the next level's; U = A P (values) with uP = P on U's pattern
-  SellDevT<T> Q, U;
-  const T* uP;
   const T* invd;
   T omega;
   T* x;                            // pre-smoothed / prolongation-corrected iterate
@@ -230,7 +223,6 @@ struct AmgLevelDevT {
 template <class T>
 struct AmgDevT {
   int nlev;                        // smoothed levels
-  int fused;                       // 1: two device barriers per level (Q, U operators present)
   AmgLevelDevT<T> L[kMaxAmgLevels];
   int nc;
   const T* cinv;
@@ -241,7 +233,8 @@ using SellDev = SellDevT<double>;
 using AmgLevelDev = AmgLevelDevT<double>;
 using AmgDev = AmgDevT<double>;
 using AmgDevF = AmgDevT<float>;
-cudaError_t launch_pcg_amg(const PcgLaunch& P, const AmgDev& M, int wmax, cudaStream_t st);
+// M: device copy of the hierarchy descriptor (read through L1 by the level loops)
+cudaError_t launch_pcg_amg(const PcgLaunch& P, const AmgDev* M, int wmax, cudaStream_t st);
 int pcg_amg_max_blocks(int block);
 
 // mixed precision (mixed.cu): FP64 right-hand side and outer residual, FP32
@@ -254,7 +247,6 @@ struct MixedLaunch {
   float* q32;
   float* invd32;
   float* d32;               // inner solution
-  float* r32b;              // second residual buffer (fused AMG cycle)
   double* b64;              // right-hand side
   double* r64;              // outer residual
   float tol_inner;          // relative residual reduction of each inner solve
@@ -262,7 +254,7 @@ struct MixedLaunch {
   int inner_cap;
   int use_amg;
 };
-cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const AmgDevF& M, int wmax, cudaStream_t st,
+cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const AmgDevF* M, int wmax, cudaStream_t st,
                              float* partf);
 int pcg_mixed_max_blocks(int block);
 cudaError_t launch_to_float(int64_t n, const double* src, float* dst, cudaStream_t st);

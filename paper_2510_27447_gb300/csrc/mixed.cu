@@ -26,8 +26,10 @@ namespace bd {
 namespace {
 
 template <int WMAX, bool AMG>
-__global__ void __launch_bounds__(1024) pcg_mixed_kernel(const PcgLaunch a, const MixedLaunch m, const AmgDevF M,
-                                                          float* partf) {
+__global__ void __launch_bounds__(1024, 1) pcg_mixed_kernel(const __grid_constant__ PcgLaunch a,
+                                                             const __grid_constant__ MixedLaunch m,
+                                                             const AmgDevF* __restrict__ Mp, float* partf) {
+  const AmgDevF& M = *Mp;   // descriptor in global memory (see pcg_amg_kernel)
   __shared__ double shd[4][32];
   __shared__ float shf[4][32];
   if (a.gate && *a.gate == 0) return;
@@ -113,110 +115,6 @@ __global__ void __launch_bounds__(1024) pcg_mixed_kernel(const PcgLaunch a, cons
     const float target2 = float(tgt);
 
     // ---- FP32 inner CG on A d = r / |r| ----------------------------------
-    if constexpr (AMG) {
-      if (M.fused) {
-        // two device barriers per CG iteration plus two per level: the CG
-        // residual update is folded into the cycle's first phase (r ping-pongs
-        // between r32 and r32b so neighbours can recompute r - alpha q)
-        float* rc = m.r32;
-        float* rn = m.r32b;
-        float rrl0 = 0.0f;
-        for (int i = i0; i < n; i += stride) {
-          const float r = float(m.r64[i] * inv_scale);
-          rc[i] = r;
-          m.d32[i] = 0.0f;
-          rrl0 += r * r;
-        }
-        if (!grid_barrier(a.bar, nb, a.status)) return;
-        float rz0 = 0.0f;
-        {
-          auto b0 = [&](int j) { return __ldcg(rc + j); };
-          auto zh = [&](int i, float z) { rz0 += __ldcg(rc + i) * z; };
-          if (!vcycle_fused<float>(M, b0, m.z32, zh, a.bar, nb, a.status)) return;
-        }
-        float accf[2] = {rz0, rrl0};
-        block_sum<2, float>(accf, shf);
-        if (threadIdx.x == 0) {
-          partf[blockIdx.x * 4 + 2] = accf[0];
-          partf[blockIdx.x * 4 + 3] = accf[1];
-        }
-        if (!grid_barrier(a.bar, nb, a.status)) return;
-        float tf[2];
-        grid_total<2, float>(partf, {2, 3}, nb, tf, shf);
-        float rho = tf[0];
-        float rr = tf[1];
-        int it = 0;
-        float beta = 0.0f;
-        bool done = !(rr > target2);
-        while (!done) {
-          float pq[1] = {0.0f};
-          for (int i = i0; i < n; i += stride) {
-            const float z = m.z32[i];
-            float az = a.dextra ? float(a.dextra[i]) * z : 0.0f;
-            az += sell_row<WMAX, true, float>(a.sptr, a.swidth, a.col, m.valA32, m.z32, i);
-            const float p = it == 0 ? z : z + beta * m.p32[i];
-            const float q = it == 0 ? az : az + beta * m.q32[i];
-            m.p32[i] = p;
-            m.q32[i] = q;
-            pq[0] += p * q;
-          }
-          block_sum<1, float>(pq, shf);
-          if (threadIdx.x == 0) partf[blockIdx.x * 4 + 0] = pq[0];
-          if (!grid_barrier(a.bar, nb, a.status)) return;
-          float tq[1];
-          grid_total<1, float>(partf, {0}, nb, tq, shf);
-          if (!(tq[0] > 0.0f)) {
-            if (!isfinite(tq[0])) fail = ST_NONFINITE;
-            break;     // FP32 breakdown: keep d, the outer step decides
-          }
-          const float alpha = rho / tq[0];
-          float rrl = 0.0f;
-          for (int i = i0; i < n; i += stride) {
-            m.d32[i] += alpha * m.p32[i];
-            const float r = fmaf(-alpha, m.q32[i], rc[i]);
-            rn[i] = r;
-            rrl += r * r;
-          }
-          float rz = 0.0f;
-          {
-            const float* q32 = m.q32;
-            auto b0 = [&](int j) { return fmaf(-alpha, __ldcg(q32 + j), __ldcg(rc + j)); };
-            auto zh = [&](int i, float z) { rz += __ldcg(rn + i) * z; };
-            if (!vcycle_fused<float>(M, b0, m.z32, zh, a.bar, nb, a.status)) return;
-          }
-          float acc[2] = {rz, rrl};
-          block_sum<2, float>(acc, shf);
-          if (threadIdx.x == 0) {
-            partf[blockIdx.x * 4 + 2] = acc[0];
-            partf[blockIdx.x * 4 + 3] = acc[1];
-          }
-          if (!grid_barrier(a.bar, nb, a.status)) return;
-          grid_total<2, float>(partf, {2, 3}, nb, tf, shf);
-          ++it;
-          rr = tf[1];
-          float* t = rc;
-          rc = rn;
-          rn = t;
-          if (!isfinite(rr) || !isfinite(tf[0])) {
-            fail = ST_NONFINITE;
-            break;
-          }
-          if (rr <= target2) break;
-          if (it >= m.inner_cap) {
-            if (m.max_outer == 1) fail = ST_NOT_CONVERGED;
-            break;
-          }
-          beta = tf[0] / rho;
-          rho = tf[0];
-        }
-        inner_total += it;
-        if (fail) break;
-        for (int i = i0; i < n; i += stride) a.x[i] += scale * double(m.d32[i]);
-        if (m.max_outer == 1) break;
-        if (!grid_barrier(a.bar, nb, a.status)) return;   // x complete before the next residual
-        continue;
-      }
-    }
     for (int i = i0; i < n; i += stride) {
       m.r32[i] = float(m.r64[i] * inv_scale);
       m.d32[i] = 0.0f;
@@ -361,7 +259,7 @@ int pcg_mixed_max_blocks(int block) {
   return m;
 }
 
-cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const AmgDevF& M, int wmax, cudaStream_t st,
+cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const AmgDevF* M, int wmax, cudaStream_t st,
                              float* partf) {
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[1];

@@ -11,6 +11,9 @@ namespace bd {
 #ifndef BD_PCG_SLEEP_NS
 #define BD_PCG_SLEEP_NS 0
 #endif
+#ifndef BD_SELL_CHUNK
+#define BD_SELL_CHUNK 8
+#endif
 constexpr long long kSpinLimit = 1ll << 26;   // bounded wait: about a second of polling
 
 // Device-wide barrier on one arrival word: block 0 adds 2^31 - (nblocks - 1),
@@ -146,17 +149,25 @@ __device__ __forceinline__ T sell_row(const int64_t* __restrict__ sptr, const in
   const int w = swidth[s];
   T acc = T(0);
   if constexpr (WMAX > 0) {
-    int c[WMAX];
-    T v[WMAX];
+    // chunks of BD_SELL_CHUNK entries: all loads of a chunk in flight at
+    // once, without holding a whole 32-wide row in registers
+    constexpr int CH = BD_SELL_CHUNK;
+    for (int k0 = 0; k0 < w; k0 += CH) {
+      int c[CH];
+      T v[CH], g[CH];
 #pragma unroll
-    for (int k = 0; k < WMAX; ++k)
-      if (k < w) {
-        c[k] = colv[base + 32 * k];
-        v[k] = val[base + 32 * k];
-      }
+      for (int k = 0; k < CH; ++k)
+        if (k0 + k < w) {
+          c[k] = colv[base + 32 * (k0 + k)];
+          v[k] = val[base + 32 * (k0 + k)];
+        }
 #pragma unroll
-    for (int k = 0; k < WMAX; ++k)
-      if (k < w) acc += v[k] * (CROSS ? __ldcg(x + c[k]) : x[c[k]]);
+      for (int k = 0; k < CH; ++k)
+        if (k0 + k < w) g[k] = CROSS ? __ldcg(x + c[k]) : x[c[k]];
+#pragma unroll
+      for (int k = 0; k < CH; ++k)
+        if (k0 + k < w) acc += v[k] * g[k];
+    }
   } else {
     for (int k = 0; k < w; ++k) {
       const int c = colv[base + 32 * k];

@@ -7,14 +7,11 @@
 
 namespace bd {
 
+// row i of a SELL operator against x read through L2 (sell_row processes any
+// width in chunks of eight, so one instantiation serves every level)
 template <class T>
 __device__ __forceinline__ T sdot(const SellDevT<T>& M, const T* x, int i) {
-  switch (M.wmax) {
-    case 8: return sell_row<8, true, T>(M.sptr, M.sw, M.col, M.val, x, i);
-    case 16: return sell_row<16, true, T>(M.sptr, M.sw, M.col, M.val, x, i);
-    case 32: return sell_row<32, true, T>(M.sptr, M.sw, M.col, M.val, x, i);
-    default: return sell_row<0, true, T>(M.sptr, M.sw, M.col, M.val, x, i);
-  }
+  return sell_row<8, true, T>(M.sptr, M.sw, M.col, M.val, x, i);
 }
 
 // For every row i of M: epi(i, (M x)_i).  SELL operators use one thread per
@@ -40,67 +37,21 @@ __device__ __forceinline__ void apply_rows(const SellDevT<T>& M, const T* x, int
   }
 }
 
-// sum_k val[k] g(col[k]) over row i of a SELL operator, entries in the same
-// order as sell_row; loads issued eight at a time for memory-level parallelism
-template <class T, class G>
-__device__ __forceinline__ T sell_row_f(const SellDevT<T>& M, int i, G& g) {
-  const int s = i >> 5;
-  const int64_t base = M.sptr[s] + (i & 31);
-  const int w = M.sw[s];
-  T acc = T(0);
-  for (int k0 = 0; k0 < w; k0 += 8) {
-    int c[8];
-    T v[8], gv[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (k0 + k < w) {
-        c[k] = M.col[base + 32 * (k0 + k)];
-        v[k] = M.val[base + 32 * (k0 + k)];
-      }
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (k0 + k < w) gv[k] = g(c[k]);
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (k0 + k < w) acc += v[k] * gv[k];
-  }
-  return acc;
-}
-
-// For every row i of M: epi(i, sum_k val[k] g(col[k])) -- apply_rows with the
-// gathered value given by a functor (values other threads wrote in earlier
-// phases must be read through L2 inside g)
-template <class T, class G, class F>
-__device__ __forceinline__ void apply_rows_f(const SellDevT<T>& M, int i0, int stride, G&& g, F&& epi) {
-  if (M.rp) {
-    const int lane = threadIdx.x & 31;
-    for (int i = i0 >> 5; i < M.n; i += stride >> 5) {
-      T s = T(0);
-      const int64_t e = M.rp[i + 1];
-      for (int64_t p = M.rp[i] + lane; p < e; p += 32) s += M.val[p] * g(M.col[p]);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) epi(i, s);
-    }
-  } else {
-    for (int i = i0; i < M.n; i += stride) epi(i, sell_row_f<T>(M, i, g));
-  }
-}
-
-// For every row i of U: epi(i, sum_k v2[k] x[col[k]], sum_k val[k] x[col[k]])
-// (two operators on one pattern, one gather of x per entry)
+// For every row i of M: epi(i, (M x0)_i, (M x1)_i) -- two vectors through one
+// pass over the operator (values and indices loaded once)
 template <class T, class F>
-__device__ __forceinline__ void apply_rows2(const SellDevT<T>& M, const T* v2, const T* x, int i0, int stride,
-                                            F&& epi) {
+__device__ __forceinline__ void apply_rows_2v(const SellDevT<T>& M, const T* x0, const T* x1, int i0, int stride,
+                                              F&& epi) {
   if (M.rp) {
     const int lane = threadIdx.x & 31;
     for (int i = i0 >> 5; i < M.n; i += stride >> 5) {
       T a = T(0), b = T(0);
       const int64_t e = M.rp[i + 1];
       for (int64_t p = M.rp[i] + lane; p < e; p += 32) {
-        const T xv = __ldcg(x + M.col[p]);
-        a += v2[p] * xv;
-        b += M.val[p] * xv;
+        const int c = M.col[p];
+        const T v = M.val[p];
+        a += v * __ldcg(x0 + c);
+        b += v * __ldcg(x1 + c);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -115,21 +66,26 @@ __device__ __forceinline__ void apply_rows2(const SellDevT<T>& M, const T* v2, c
       const int64_t base = M.sptr[s] + (i & 31);
       const int w = M.sw[s];
       T a = T(0), b = T(0);
-      for (int k0 = 0; k0 < w; k0 += 8) {
-        T xv[8], p2[8], pv[8];
+      for (int k0 = 0; k0 < w; k0 += 4) {
+        int c[4];
+        T v[4], g0[4], g1[4];
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < 4; ++k)
           if (k0 + k < w) {
-            const int64_t q = base + 32 * (k0 + k);
-            xv[k] = __ldcg(x + M.col[q]);
-            p2[k] = v2[q];
-            pv[k] = M.val[q];
+            c[k] = M.col[base + 32 * (k0 + k)];
+            v[k] = M.val[base + 32 * (k0 + k)];
           }
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < 4; ++k)
           if (k0 + k < w) {
-            a += p2[k] * xv[k];
-            b += pv[k] * xv[k];
+            g0[k] = __ldcg(x0 + c[k]);
+            g1[k] = __ldcg(x1 + c[k]);
+          }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (k0 + k < w) {
+            a += v[k] * g0[k];
+            b += v[k] * g1[k];
           }
       }
       epi(i, a, b);
@@ -137,73 +93,93 @@ __device__ __forceinline__ void apply_rows2(const SellDevT<T>& M, const T* v2, c
   }
 }
 
-// Fused V(1,1) cycle, the same operator as vcycle() below in exact arithmetic
-// but with two device barriers per level instead of four.  With zero initial
-// guesses the pre-smoothed iterate is x = w D^-1 b, so on the way down one
-// phase per level computes, from b alone,
-//   x = w D^-1 b,   r = b - A (w D^-1 b),   b_next = Q b,  Q = R (I - w A D^-1)
-// (each thread recomputing the x_j of the neighbours it needs), and on the way
-// up one phase per level computes prolongation and post-smoothing together,
-//   y = x + P x_c + w D^-1 (r - (A P) x_c).
-// b0(j) gives the level-0 right-hand side at any row j (the caller's CG
-// update r - alpha q is folded in this way, saving its barrier); zhook(i, z_i)
-// is called for every level-0 row of the result.  The caller must place a
-// device barrier between the last writes of b0's inputs and the call.
-template <class T, class B0, class Z0>
-__device__ bool vcycle_fused(const AmgDevT<T>& M, B0& b0, T* zout, Z0& zhook, unsigned* bar, int nb, int* status) {
+// Two V(1,1) cycles at once (z_k = V(r_k), k = 0, 1) sharing every device
+// barrier and every pass over the operators.  H0 carries the operators and the
+// level vectors of the first right-hand side, H1 the level vectors of the
+// second (its operators are not read).  Each z_k is the cycle vcycle() below
+// computes for r_k, with the same order of every sum.
+template <class T>
+__device__ bool vcycle2(const AmgDevT<T>& H0, const AmgDevT<T>& H1, const T* r0, const T* r1, T* z0, T* z1,
+                        unsigned* bar, int nb, int* status) {
   const int stride = blockDim.x * gridDim.x;
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int L = M.nlev;
-  for (int l = 0; l < L; ++l) {
-    const AmgLevelDevT<T>& Lv = M.L[l];
-    if (l > 0 && !grid_barrier(bar, nb, status)) return false;
-    const bool last = l + 1 == L;
-    T* nrhs = last ? M.bc : M.L[l + 1].b;
-    auto down = [&](auto& bf) {
-      auto g = [&](int j) { return Lv.omega * Lv.invd[j] * bf(j); };
-      apply_rows_f(Lv.A, i0, stride, g, [&](int i, T s) {
-        const T bi = bf(i);
-        Lv.x[i] = Lv.omega * Lv.invd[i] * bi;
-        Lv.r[i] = bi - s;
-      });
-      apply_rows_f(Lv.Q, i0, stride, bf, [&](int k, T s) { nrhs[k] = s; });
-    };
-    if (l == 0) {
-      down(b0);
-    } else {
-      auto bl = [&](int j) { return __ldcg(Lv.b + j); };
-      down(bl);
+  const int L = H0.nlev;
+  {
+    const AmgLevelDevT<T>& l0 = H0.L[0];
+    T* xa = l0.x;
+    T* xb = H1.L[0].x;
+    for (int i = i0; i < l0.A.n; i += stride) {
+      xa[i] = l0.omega * l0.invd[i] * r0[i];
+      xb[i] = l0.omega * l0.invd[i] * r1[i];
     }
+  }
+  for (int l = 0; l < L; ++l) {
+    const AmgLevelDevT<T>& Lv = H0.L[l];
+    const AmgLevelDevT<T>& Lw = H1.L[l];
+    const T* ba = l == 0 ? r0 : Lv.b;
+    const T* bb = l == 0 ? r1 : Lw.b;
+    if (!grid_barrier(bar, nb, status)) return false;
+    apply_rows_2v(Lv.A, Lv.x, Lw.x, i0, stride, [&](int i, T da, T db) {
+      Lv.r[i] = __ldcg(ba + i) - da;
+      Lw.r[i] = __ldcg(bb + i) - db;
+    });
+    if (!grid_barrier(bar, nb, status)) return false;
+    const bool last = l + 1 == L;
+    T* na = last ? H0.bc : H0.L[l + 1].b;
+    T* nbv = last ? H1.bc : H1.L[l + 1].b;
+    apply_rows_2v(Lv.R, Lv.r, Lw.r, i0, stride, [&](int i, T va, T vb) {
+      na[i] = va;
+      nbv[i] = vb;
+      if (!last) {
+        const AmgLevelDevT<T>& Nx = H0.L[l + 1];
+        Nx.x[i] = Nx.omega * Nx.invd[i] * va;
+        H1.L[l + 1].x[i] = Nx.omega * Nx.invd[i] * vb;
+      }
+    });
   }
   if (!grid_barrier(bar, nb, status)) return false;
   {
     const int lane = threadIdx.x & 31;
     const int warp = i0 >> 5;
     const int nwarps = stride >> 5;
-    for (int i = warp; i < M.nc; i += nwarps) {
-      const T* row = M.cinv + int64_t(i) * M.nc;
-      T s = T(0);
-      for (int j = lane; j < M.nc; j += 32) s += row[j] * __ldcg(M.bc + j);
+    for (int i = warp; i < H0.nc; i += nwarps) {
+      const T* row = H0.cinv + int64_t(i) * H0.nc;
+      T a = T(0), b = T(0);
+      for (int j = lane; j < H0.nc; j += 32) {
+        const T c = row[j];
+        a += c * __ldcg(H0.bc + j);
+        b += c * __ldcg(H1.bc + j);
+      }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) M.xc[i] = s;
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+      }
+      if (lane == 0) {
+        H0.xc[i] = a;
+        H1.xc[i] = b;
+      }
     }
   }
   for (int l = L - 1; l >= 0; --l) {
-    const AmgLevelDevT<T>& Lv = M.L[l];
-    const T* xc = l + 1 == L ? M.xc : M.L[l + 1].y;
+    const AmgLevelDevT<T>& Lv = H0.L[l];
+    const AmgLevelDevT<T>& Lw = H1.L[l];
+    const T* ca = l + 1 == L ? H0.xc : H0.L[l + 1].y;
+    const T* cb = l + 1 == L ? H1.xc : H1.L[l + 1].y;
     if (!grid_barrier(bar, nb, status)) return false;
-    if (l == 0) {
-      apply_rows2(Lv.U, Lv.uP, xc, i0, stride, [&](int i, T sp, T sap) {
-        const T z = __ldcg(Lv.x + i) + sp + Lv.omega * Lv.invd[i] * (__ldcg(Lv.r + i) - sap);
-        zout[i] = z;
-        zhook(i, z);
-      });
-    } else {
-      apply_rows2(Lv.U, Lv.uP, xc, i0, stride, [&](int i, T sp, T sap) {
-        Lv.y[i] = __ldcg(Lv.x + i) + sp + Lv.omega * Lv.invd[i] * (__ldcg(Lv.r + i) - sap);
-      });
-    }
+    apply_rows_2v(Lv.P, ca, cb, i0, stride, [&](int i, T da, T db) {
+      Lv.x[i] = __ldcg(Lv.x + i) + da;
+      Lw.x[i] = __ldcg(Lw.x + i) + db;
+    });
+    if (!grid_barrier(bar, nb, status)) return false;
+    const T* ba = l == 0 ? r0 : Lv.b;
+    const T* bb = l == 0 ? r1 : Lw.b;
+    T* ya = l == 0 ? z0 : Lv.y;
+    T* yb = l == 0 ? z1 : Lw.y;
+    apply_rows_2v(Lv.A, Lv.x, Lw.x, i0, stride, [&](int i, T da, T db) {
+      ya[i] = __ldcg(Lv.x + i) + Lv.omega * Lv.invd[i] * (__ldcg(ba + i) - da);
+      yb[i] = __ldcg(Lw.x + i) + Lv.omega * Lv.invd[i] * (__ldcg(bb + i) - db);
+    });
   }
   return true;
 }

@@ -121,30 +121,3 @@ def test_amg_preconditioned_elliptic_solve(side):
     assert ita < 45 and ita * 8 < itj
     sim_a.close()
     sim_j.close()
-
-
-@pytest.mark.parametrize("cycle", [0, 1])
-@pytest.mark.parametrize("dim", [2, 3])
-def test_amg_cycle_forms_reach_the_direct_solution(cycle, dim):
-    """Classic V(1,1) cycle (four device barriers per level) and the fused
-    form (two per level, precomputed R (I - w A D^-1) and A P): the same
-    preconditioner in exact arithmetic, so both reach the direct solution with
-    about the same iteration count, in FP64 and in the mixed path."""
-    if dim == 2:
-        w = W.sheet(129, 1.0, W.LR91, 0.02, 1)
-    else:
-        xyz, tets = W.slab_grid(31, 27, 9, 1.0, 0.85, 0.25)
-        fib = W.fibers_transmural(xyz, tets, 0.0, 0.25, -60, 60)
-        w = W.Workload("slab", xyz, tets, fib, W.CONFIG0_SIGMA, 2000.0, 1.0, W.TP06_EPI, [], 0.025, 1)
-    xyz = w.xyz
-    v = -80 + 100 * np.exp(-30 * ((xyz[:, 0] - 0.3) ** 2 + (xyz[:, 1] - 0.6) ** 2))
-    u_ref = oracle_problem(w).elliptic(v)
-    its = []
-    for prec in (binding.FP64, binding.MIXED):
-        sim = gpu_sim(w, cg_tol_e=1e-12, elliptic_precond=1, amg_cycle=cycle, precision=prec,
-                      amg_coarse_max=300)
-        u, it = sim.solve_elliptic(v)
-        sim.close()
-        assert rel(u, u_ref) < 1e-9, (prec, rel(u, u_ref))
-        its.append(it)
-    assert its[0] < 60
