@@ -26,9 +26,11 @@ namespace {
 template <int WMAX>
 __global__ void __launch_bounds__(1024, 1) pcg_amg_kernel(const __grid_constant__ PcgLaunch a,
                                                            const AmgDev* __restrict__ Mp) {
-  // the descriptor lives in global memory: level loops index it at run time,
-  // which a by-value kernel parameter would turn into a local-memory copy
-  const AmgDev& M = *Mp;
+  // level loops index the descriptor at run time: a by-value kernel parameter
+  // would be copied to local memory, so it is staged in shared memory
+  __shared__ AmgDev sM;
+  load_descriptor(sM, Mp);
+  const AmgDev& M = sM;
   __shared__ double sh[4][32];
   if (a.gate && *a.gate == 0) return;
   const int n = a.n;

@@ -29,7 +29,9 @@ template <int WMAX, bool AMG>
 __global__ void __launch_bounds__(1024, 1) pcg_mixed_kernel(const __grid_constant__ PcgLaunch a,
                                                              const __grid_constant__ MixedLaunch m,
                                                              const AmgDevF* __restrict__ Mp, float* partf) {
-  const AmgDevF& M = *Mp;   // descriptor in global memory (see pcg_amg_kernel)
+  __shared__ AmgDevF sM;    // descriptor staged in shared memory (see pcg_amg_kernel)
+  if constexpr (AMG) load_descriptor(sM, Mp);
+  const AmgDevF& M = sM;
   __shared__ double shd[4][32];
   __shared__ float shf[4][32];
   if (a.gate && *a.gate == 0) return;

@@ -12,7 +12,7 @@ namespace bd {
 #define BD_PCG_SLEEP_NS 0
 #endif
 #ifndef BD_SELL_CHUNK
-#define BD_SELL_CHUNK 8
+#define BD_SELL_CHUNK 4
 #endif
 constexpr long long kSpinLimit = 1ll << 26;   // bounded wait: about a second of polling
 
@@ -92,6 +92,18 @@ inline bool solver_cluster_ok(K kernel, int block, int size) {
   return n >= 1;
 }
 
+// copy a trivially copyable descriptor (e.g. the AMG hierarchy) from global
+// into the block's shared memory; level loops then index it at run time with
+// shared-memory latency
+template <class D>
+__device__ __forceinline__ void load_descriptor(D& dst, const D* src) {
+  static_assert(sizeof(D) % 4 == 0, "descriptor size");
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(&dst);
+  for (int i = threadIdx.x; i < int(sizeof(D) / 4); i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+}
+
 // block-wide sum of NV values; result valid in thread 0
 template <int NV, class T = double>
 __device__ __forceinline__ void block_sum(T (&v)[NV], T (*sh)[32]) {
@@ -117,8 +129,8 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T (*sh)[32]) {
   __syncthreads();
 }
 
-// every block sums part[b*4 + slot] over b = 0..nb-1 in the same order
-template <int NV, class T = double>
+// every block sums part[b*STRIDE + slot] over b = 0..nb-1 in the same order
+template <int NV, class T = double, int STRIDE = 4>
 __device__ __forceinline__ void grid_total(const T* part, const int (&slot)[NV], int nb, T (&out)[NV],
                                            T (*sh)[32]) {
   T v[NV];
@@ -126,7 +138,7 @@ __device__ __forceinline__ void grid_total(const T* part, const int (&slot)[NV],
   for (int k = 0; k < NV; ++k) v[k] = T(0);
   for (int b = threadIdx.x; b < nb; b += blockDim.x)
 #pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] += __ldcg(part + b * 4 + slot[k]);
+    for (int k = 0; k < NV; ++k) v[k] += __ldcg(part + b * STRIDE + slot[k]);
   block_sum<NV, T>(v, sh);
   __shared__ T bc[NV];
   if (threadIdx.x == 0)
@@ -150,7 +162,8 @@ __device__ __forceinline__ T sell_row(const int64_t* __restrict__ sptr, const in
   T acc = T(0);
   if constexpr (WMAX > 0) {
     // chunks of BD_SELL_CHUNK entries: all loads of a chunk in flight at
-    // once, without holding a whole 32-wide row in registers
+    // once, without holding a whole 32-wide row in registers (4 measured
+    // best on GB300 against 8 and against whole-row unrolling)
     constexpr int CH = BD_SELL_CHUNK;
     for (int k0 = 0; k0 < w; k0 += CH) {
       int c[CH];
