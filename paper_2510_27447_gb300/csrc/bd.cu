@@ -74,6 +74,12 @@ struct bd_state {
   bool use_amg = false;
   AmgDev amg{};
   AmgDevF amgf{};                 // FP32 copy of the hierarchy (mixed path)
+  AmgDevF amgf2{};                // its operators with a second set of level vectors (two-RHS solves)
+  AmgDevF* d_amgf2 = nullptr;
+  bool two_rhs = false;           // sweeps >= 2 solve their elliptic pair in one launch (mixed AMG path)
+  float* partf8 = nullptr;
+  double* partd8 = nullptr;
+  double* vfull2 = nullptr;
   AmgDev* d_amg = nullptr;        // device copies of the two descriptors (kernel arguments)
   AmgDevF* d_amgf = nullptr;
   // mixed path: FP32 operator values and CG workspaces
@@ -87,6 +93,7 @@ struct bd_state {
   int amg_grid = 1;
   int amg_levels = 0;
   double amg_cycle_bytes[2] = {0.0, 0.0};   // algorithmic bytes of one V-cycle (FP64, FP32 values)
+  double amg_cycle_opbytes[2] = {0.0, 0.0}; // ... of which operator values and indices
   double *Ai = nullptr, *Aie = nullptr, *Mv = nullptr, *Mc = nullptr, *ML = nullptr;
   struct PC { double alpha; double* val; };
   std::vector<PC> pcache;
@@ -100,7 +107,8 @@ struct bd_state {
   StimTable stim{};
   long long* step_n = nullptr;
   int* d_status = nullptr;
-  long long* d_stats = nullptr;            // [iters_e, solves_e, iters_p, solves_p, outer_e, outer_p, extra sweeps]
+  long long* d_stats = nullptr;            // [iters_e, solves_e, iters_p, solves_p, outer_e, outer_p, extra sweeps,
+                                           //  paired elliptic iterations]
   int* gate = nullptr;                     // sweep test of Algorithm 2 (sweep_tol > 0)
   unsigned long long* dmax = nullptr;
   double* Xsave = nullptr;
@@ -334,6 +342,48 @@ int elliptic(bd_state* s, const double* v, double* u) {
   return BD_OK;
 }
 
+// u1 = E(v1) and u2 = E(v2): one two-RHS launch on the mixed AMG path, else
+// two solves
+int elliptic2(bd_state* s, const double* v1, double* u1, const double* v2, double* u2) {
+  if (!s->two_rhs || s->precision != BD_MIXED || !s->use_amg) {
+    const int r = elliptic(s, v1, u1);
+    if (r != BD_OK) return r;
+    return elliptic(s, v2, u2);
+  }
+  PcgLaunch P = pcg_base(s);
+  if (s->NT < s->N) {
+    Timed t(s, BD_K_COMBINE, 2);
+    CK(launch_copy(s->NT, v1, s->vfull, s->stream, P.gate));
+    CK(launch_copy(s->NT, v2, s->vfull2, s->stream, P.gate));
+    v1 = s->vfull;
+    v2 = s->vfull2;
+  }
+  P.valA = s->Aie;
+  P.val1 = s->Ai;
+  P.va = v1;
+  P.c1 = -1.0;
+  P.project = 1;
+  P.x = u1;
+  P.warm = 1;
+  P.tol = s->opts.cg_tol_e;
+  P.maxit = s->opts.cg_cap_e;
+  P.pin = s->opts.pin_node >= 0 ? s->opts.pin_node : -1;
+  P.iters_acc = s->d_stats + 0;
+  P.solves_acc = s->d_stats + 1;
+  P.outer_acc = s->d_stats + 4;
+  P.pair_acc = s->d_stats + 7;
+  P.grid = s->mixed_grid;
+  MixedLaunch X = mixed_base(s);
+  X.valA32 = s->fAie;
+  X.tol_inner = BD_MIXED_TOL_INNER;
+  X.max_outer = 12;
+  X.inner_cap = s->opts.cg_cap_e;
+  X.use_amg = 1;
+  Timed t(s, BD_K_PCG_ELLIPTIC);
+  CK(launch_pcg_mixed2(P, v2, u2, X, s->d_amgf, s->d_amgf2, s->wmax, s->stream, s->partf8, s->partd8));
+  return BD_OK;
+}
+
 // (alpha M_v + A_i + diag(dgs)) x = rl + c1 A_i va + c2 M_v vb; node_terms =
 // false drops diag(dgs) and rl (the plain Crank-Nicolson operator)
 int parabolic(bd_state* s, double alpha, double c1, const double* va, double c2, const double* vb, double* x,
@@ -529,16 +579,29 @@ int setup_amg(bd_state* s, const HostOps& H) {
     if (!F.cinv || !alloc_n(s, &F.bc, AH.nc) || !alloc_n(s, &F.xc, AH.nc) ||
         cudaStreamSynchronize(s->stream) != cudaSuccess)
       return fail(s, BD_ERR_OOM, "AMG upload failed");
+    // the same hierarchy with its own level vectors: the second system of the
+    // two-RHS solves (sweeps >= 2 solve the elliptic constraint at two nodes)
+    AmgDevF& G = s->amgf2;
+    G = F;
+    bool ok2 = alloc_n(s, &G.bc, AH.nc) && alloc_n(s, &G.xc, AH.nc);
+    for (int l = 0; ok2 && l < G.nlev; ++l) {
+      const int64_t n = AH.lev[l].A.n;
+      ok2 = alloc_n(s, &G.L[l].x, n) && alloc_n(s, &G.L[l].r, n);
+      if (ok2 && l > 0) ok2 = alloc_n(s, &G.L[l].b, n) && alloc_n(s, &G.L[l].y, n);
+    }
+    if (!ok2) return fail(s, BD_ERR_OOM, "AMG upload failed");
+    s->two_rhs = true;
   }
   const int mx = pcg_amg_max_blocks(s->pcg_block);
   if (mx <= 0) return fail(s, BD_ERR_CUDA, "cannot size the cooperative AMG-CG grid");
   s->amg_grid = std::min(s->pcg_grid, mx);
   for (int v = 0; v < 2; ++v) {
     const double vb = v == 0 ? 8.0 : 4.0;
-    double b = 0.0;
+    double b = 0.0, ob = 0.0;
     for (size_t l = 0; l < AH.lev.size(); ++l) {
       const AmgHostLevel& Lh = AH.lev[l];
       const double n = double(Lh.A.n), nn = double(Lh.P.m);
+      ob += double(2 * Lh.A.ci.size() + Lh.R.ci.size() + Lh.P.ci.size()) * (vb + 4);
       const double spA = double(Lh.A.ci.size()) * (vb + 4) + n * vb;
       const double spR = double(Lh.R.ci.size()) * (vb + 4) + n * vb;
       const double spP = double(Lh.P.ci.size()) * (vb + 4) + nn * vb;
@@ -549,11 +612,14 @@ int setup_amg(bd_state* s, const HostOps& H) {
     const double nc = double(AH.nc);
     b += vb * (nc * nc + 2 * nc);
     s->amg_cycle_bytes[v] = b;
+    s->amg_cycle_opbytes[v] = ob + vb * nc * nc;
   }
   s->amg_levels = M.nlev;
   // the kernels read the descriptors from device memory
   if (cudaMemcpyAsync(s->d_amg, &s->amg, sizeof(AmgDev), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
       cudaMemcpyAsync(s->d_amgf, &s->amgf, sizeof(AmgDevF), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+      (s->d_amgf2 &&
+       cudaMemcpyAsync(s->d_amgf2, &s->amgf2, sizeof(AmgDevF), cudaMemcpyHostToDevice, s->stream) != cudaSuccess) ||
       cudaStreamSynchronize(s->stream) != cudaSuccess)
     return fail(s, BD_ERR_CUDA, "AMG descriptor upload failed");
   s->use_amg = true;
@@ -621,7 +687,11 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
         CK(launch_copy(Nu, s->u[M - 1], s->u[m], s->stream, gate));
       }
     } else {
-      for (int m = 1; m < M; ++m) RUN(elliptic(s, s->Xc[m], s->u[m]));
+      if (M == 3) {
+        RUN(elliptic2(s, s->Xc[1], s->u[1], s->Xc[2], s->u[2]));
+      } else {
+        for (int m = 1; m < M; ++m) RUN(elliptic(s, s->Xc[m], s->u[m]));
+      }
     }
     // ---- ROS2 predictor ----
     if (s->adapt_on) {   // the estimate is the one of the last sweep that ran
@@ -997,9 +1067,13 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   if (ok && s->opts.sweep_tol > 0)
     ok = alloc_n(s, &s->gate, 1) && alloc_n(s, &s->dmax, 1) && alloc_n(s, &s->Xsave, ns * NT);
   if (ok && s->precision == BD_MIXED) {
-    ok = alloc_n(s, &s->fAie, s->ell_n) && alloc_n(s, &s->r32, N) && alloc_n(s, &s->z32, N) &&
-         alloc_n(s, &s->p32, N) && alloc_n(s, &s->q32, N) && alloc_n(s, &s->invd32, N) &&
-         alloc_n(s, &s->d32, N) && alloc_n(s, &s->b64, N) && alloc_n(s, &s->r64, N) &&
+    // r, z, p, q, d, b, r64 hold two systems (two-RHS elliptic solves)
+    ok = alloc_n(s, &s->fAie, s->ell_n) && alloc_n(s, &s->r32, 2 * N) && alloc_n(s, &s->z32, 2 * N) &&
+         alloc_n(s, &s->p32, 2 * N) && alloc_n(s, &s->q32, 2 * N) && alloc_n(s, &s->invd32, N) &&
+         alloc_n(s, &s->d32, 2 * N) && alloc_n(s, &s->b64, 2 * N) && alloc_n(s, &s->r64, 2 * N) &&
+         alloc_n(s, &s->partf8, int64_t(s->pcg_max) * 8) && alloc_n(s, &s->partd8, int64_t(s->pcg_max) * 8) &&
+         (NT == N || alloc_n(s, &s->vfull2, N)) &&
+         alloc_n(s, reinterpret_cast<char**>(&s->d_amgf2), int64_t(sizeof(AmgDevF))) &&
          alloc_n(s, &s->partf, int64_t(s->pcg_max) * 4);
     const int mx = pcg_mixed_max_blocks(s->pcg_block);
     if (ok && mx <= 0) ok = false;
@@ -1032,10 +1106,13 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   // every node-length vector starts at zero.  Afterwards only the elliptic
   // solves write the bath entries, with finite values.
   for (double* v : {s->k1v, s->k2v, s->avec, s->bvec, s->cg_r, s->cg_z, s->cg_p, s->cg_q, s->cg_invd,
-                    s->vfull, s->b64, s->r64})
+                    s->vfull, s->vfull2})
     if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, N * 8, s->stream);
-  for (float* v : {s->r32, s->z32, s->p32, s->q32, s->invd32, s->d32})
-    if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, N * 4, s->stream);
+  for (double* v : {s->b64, s->r64})
+    if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, 2 * N * 8, s->stream);
+  for (float* v : {s->r32, s->z32, s->p32, s->q32, s->d32})
+    if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, 2 * N * 4, s->stream);
+  if (e == cudaSuccess && s->invd32) e = cudaMemsetAsync(s->invd32, 0, N * 4, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->bar, 0, 8, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, 4, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_stats, 0, 64, s->stream);
@@ -1414,9 +1491,9 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
   if (!(dt > 0) || (M != 2 && M != 3) || K < 1) return fail(s, BD_ERR_ARG, "bad step shape");
   std::memset(out, 0, sizeof(*out));
   out->nnz = s->nnz;
-  long long st0[6], st1[6];
+  long long st0[8], st1[8];
   CK(cudaStreamSynchronize(s->stream));
-  CK(cudaMemcpy(st0, s->d_stats, 48, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(st0, s->d_stats, 64, cudaMemcpyDeviceToHost));
   s->prof = true;
   int rc = BD_OK;
   for (int n = 0; n < n_steps && rc == BD_OK; ++n) {
@@ -1437,7 +1514,7 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
   }
   s->prof = false;
   if (rc != BD_OK) return rc;
-  CK(cudaMemcpy(st1, s->d_stats, 48, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(st1, s->d_stats, 64, cudaMemcpyDeviceToHost));
   out->cg_iters[0] = st1[0] - st0[0];
   out->cg_solves[0] = st1[1] - st0[1];
   out->cg_iters[1] = st1[2] - st0[2];
@@ -1461,6 +1538,12 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
     if (mixed) {
       const double outer = double(out->outer_iters[k]);
       b += outer * (ell ? spmv(8.0) + 3.0 * 8.0 * n : 2.0 * 8.0 * n) + outer * 12.0 * n;  // FP64 residual + conversion
+    }
+    if (ell && mixed && s->use_amg) {
+      // paired solves read the operators once for both systems in the
+      // iterations where both advance
+      const double pairs = double(st1[7] - st0[7]);
+      b -= pairs * (nnz * (vb + 4) + s->amg_cycle_opbytes[1]);
     }
     out->alg_bytes[k] = b;
   }

@@ -142,6 +142,7 @@ struct PcgLaunch {
   long long* iters_acc;
   long long* solves_acc;
   long long* outer_acc;     // FP64 residual passes (mixed kernel)
+  long long* pair_acc;      // two-RHS kernel: inner iterations in which both systems advanced
   const int* gate;          // optional: the solve is skipped when *gate == 0
   int grid;                 // co-resident blocks
   int block;
@@ -257,6 +258,12 @@ struct MixedLaunch {
 cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const AmgDevF* M, int wmax, cudaStream_t st,
                              float* partf);
 int pcg_mixed_max_blocks(int block);
+// two elliptic solves (right-hand sides c1 A_i va and c1 A_i va1) in one launch;
+// the MixedLaunch workspaces hold 2 n entries, H1 the second system's AMG
+// level vectors, partf8 / partd8 8 values per block
+cudaError_t launch_pcg_mixed2(const PcgLaunch& P, const double* va1, double* x1, const MixedLaunch& X,
+                              const AmgDevF* H0, const AmgDevF* H1, int wmax, cudaStream_t st, float* partf8,
+                              double* partd8);
 cudaError_t launch_to_float(int64_t n, const double* src, float* dst, cudaStream_t st);
 
 // host assembly (assemble.cpp)

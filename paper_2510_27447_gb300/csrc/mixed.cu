@@ -232,6 +232,282 @@ __global__ void __launch_bounds__(1024, 1) pcg_mixed_kernel(const __grid_constan
   }
 }
 
+// Two elliptic solves A_ie u_k = c1 A_i v_k (k = 0, 1; the rhs mean-projected)
+// in one launch: the mixed-precision AMG-CG above, run for both right-hand
+// sides in lock-step so that they share every device barrier and every pass
+// over the operators.  Each right-hand side keeps its own Krylov scalars,
+// refinement passes and convergence test; a converged one stops changing.
+// Workspace vectors of the second system sit n entries after the first's;
+// partd / partf hold 8 values per block.
+template <int WMAX>
+__global__ void __launch_bounds__(1024, 1) pcg_mixed2_kernel(const __grid_constant__ PcgLaunch a,
+                                                              const double* va1, double* x1,
+                                                              const __grid_constant__ MixedLaunch m,
+                                                              const AmgDevF* __restrict__ H0p,
+                                                              const AmgDevF* __restrict__ H1p, float* partf,
+                                                              double* partd) {
+  __shared__ AmgDevF sH0, sH1;   // descriptors staged in shared memory
+  load_descriptor(sH0, H0p);
+  load_descriptor(sH1, H1p);
+  const AmgDevF& H0 = sH0;
+  const AmgDevF& H1 = sH1;
+  __shared__ double shd[4][32];
+  __shared__ float shf[4][32];
+  if (a.gate && *a.gate == 0) return;
+  const int n = a.n;
+  const int nb = gridDim.x;
+  const int stride = blockDim.x * gridDim.x;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  double* X[2] = {a.x, x1};
+  const double* V[2] = {a.va, va1};
+  double* b64[2] = {m.b64, m.b64 + n};
+  double* r64[2] = {m.r64, m.r64 + n};
+  float* r32[2] = {m.r32, m.r32 + n};
+  float* z32[2] = {m.z32, m.z32 + n};
+  float* p32[2] = {m.p32, m.p32 + n};
+  float* q32[2] = {m.q32, m.q32 + n};
+  float* d32[2] = {m.d32, m.d32 + n};
+
+  // ---- FP64 right-hand sides ----------------------------------------------
+  double acc0[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i = i0; i < n; i += stride) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const double b = a.c1 * sell_row<WMAX, false>(a, a.val1, V[k], i);
+      b64[k][i] = b;
+      acc0[2 * k] += b;
+      acc0[2 * k + 1] += b * b;
+    }
+  }
+  if (!a.warm)
+    for (int i = i0; i < n; i += stride) {
+      X[0][i] = 0.0;
+      X[1][i] = 0.0;
+    }
+  block_sum<4, double>(acc0, shd);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) partd[blockIdx.x * 8 + k] = acc0[k];
+  if (!grid_barrier(a.bar, nb, a.status)) return;
+  {
+    double t[4];
+    grid_total<4, double, 8>(partd, {0, 1, 2, 3}, nb, t, shd);
+    for (int k = 0; k < 4; ++k) acc0[k] = t[k];
+  }
+  double tol2[2];
+  for (int k = 0; k < 2; ++k) {
+    const double mean_b = a.project ? acc0[2 * k] / double(n) : 0.0;
+    double bb = a.project ? acc0[2 * k + 1] - double(n) * mean_b * mean_b : acc0[2 * k + 1];
+    if (bb < 0.0) bb = 0.0;
+    tol2[k] = a.tol * a.tol * bb;
+    if (a.project)
+      for (int i = i0; i < n; i += stride) b64[k][i] -= mean_b;
+  }
+
+  int fail = 0;
+  long long inner_total[2] = {0, 0};
+  long long outer_total = 0, shared = 0;
+  for (int outer = 0;; ++outer) {
+    ++outer_total;
+    // ---- FP64 outer residuals -----------------------------------------------
+    double accr[2] = {0.0, 0.0};
+    for (int i = i0; i < n; i += stride) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const double r = (outer == 0 && !a.warm) ? b64[k][i]
+                                                 : b64[k][i] - sell_row<WMAX, true>(a, a.valA, X[k], i);
+        r64[k][i] = r;
+        accr[k] += r * r;
+      }
+    }
+    block_sum<2, double>(accr, shd);
+    if (threadIdx.x == 0) {
+      partd[blockIdx.x * 8 + 4] = accr[0];
+      partd[blockIdx.x * 8 + 5] = accr[1];
+    }
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    double rr64[2];
+    grid_total<2, double, 8>(partd, {4, 5}, nb, rr64, shd);
+    if (!isfinite(rr64[0]) || !isfinite(rr64[1])) {
+      fail = ST_NONFINITE;
+      break;
+    }
+    bool active[2];
+    for (int k = 0; k < 2; ++k) active[k] = rr64[k] > tol2[k] && rr64[k] > 0.0;
+    if (!active[0] && !active[1]) break;
+    if (outer >= m.max_outer) {
+      fail = ST_NOT_CONVERGED;
+      break;
+    }
+    double scale[2] = {1.0, 1.0};
+    float target2[2] = {0.0f, 0.0f};
+    for (int k = 0; k < 2; ++k)
+      if (active[k]) {
+        scale[k] = sqrt(rr64[k]);
+        double tgt = double(m.tol_inner) * double(m.tol_inner);
+        tgt = fmax(tgt, 0.25 * tol2[k] / rr64[k]);
+        target2[k] = float(tgt);
+      }
+
+    // ---- FP32 inner CG on both unit-scaled systems ---------------------------
+    for (int i = i0; i < n; i += stride) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        r32[k][i] = active[k] ? float(r64[k][i] / scale[k]) : 0.0f;
+        d32[k][i] = 0.0f;
+      }
+    }
+    if (!vcycle2<float>(H0, H1, r32[0], r32[1], z32[0], z32[1], a.bar, nb, a.status)) return;
+    float accf[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int i = i0; i < n; i += stride) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        accf[2 * k] += r32[k][i] * z32[k][i];
+        accf[2 * k + 1] += r32[k][i] * r32[k][i];
+      }
+    }
+    block_sum<4, float>(accf, shf);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 4; ++k) partf[blockIdx.x * 8 + 2 + k] = accf[k];
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    float tf[4];
+    grid_total<4, float, 8>(partf, {2, 3, 4, 5}, nb, tf, shf);
+    float rho[2] = {tf[0], tf[2]};
+    bool done[2];
+    for (int k = 0; k < 2; ++k) done[k] = !active[k] || !(tf[2 * k + 1] > target2[k]);
+    int it[2] = {0, 0};
+    float beta[2] = {0.0f, 0.0f};
+    while (!(done[0] && done[1])) {
+      float pq[2] = {0.0f, 0.0f};
+      for (int i = i0; i < n; i += stride) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (done[k]) continue;
+          const float z = z32[k][i];
+          const float az = sell_row<WMAX, true, float>(a.sptr, a.swidth, a.col, m.valA32, z32[k], i);
+          const float p = it[k] == 0 ? z : z + beta[k] * p32[k][i];
+          const float q = it[k] == 0 ? az : az + beta[k] * q32[k][i];
+          p32[k][i] = p;
+          q32[k][i] = q;
+          pq[k] += p * q;
+        }
+      }
+      block_sum<2, float>(pq, shf);
+      if (threadIdx.x == 0) {
+        partf[blockIdx.x * 8 + 0] = pq[0];
+        partf[blockIdx.x * 8 + 1] = pq[1];
+      }
+      if (!grid_barrier(a.bar, nb, a.status)) return;
+      float tq[2];
+      grid_total<2, float, 8>(partf, {0, 1}, nb, tq, shf);
+      float alpha[2] = {0.0f, 0.0f};
+      bool upd[2] = {false, false};
+      for (int k = 0; k < 2; ++k) {
+        if (done[k]) continue;
+        if (!(tq[k] > 0.0f)) {
+          if (!isfinite(tq[k])) fail = ST_NONFINITE;
+          done[k] = true;          // FP32 breakdown: keep d, the outer step decides
+          continue;
+        }
+        alpha[k] = rho[k] / tq[k];
+        upd[k] = true;
+      }
+      if (upd[0] && upd[1]) ++shared;
+      float rrl[2] = {0.0f, 0.0f};
+      for (int i = i0; i < n; i += stride) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (!upd[k]) continue;
+          d32[k][i] += alpha[k] * p32[k][i];
+          const float r = r32[k][i] - alpha[k] * q32[k][i];
+          r32[k][i] = r;
+          rrl[k] += r * r;
+        }
+      }
+      if (!vcycle2<float>(H0, H1, r32[0], r32[1], z32[0], z32[1], a.bar, nb, a.status)) return;
+      float acc[4] = {0.0f, rrl[0], 0.0f, rrl[1]};
+      for (int i = i0; i < n; i += stride) {
+        acc[0] += r32[0][i] * z32[0][i];
+        acc[2] += r32[1][i] * z32[1][i];
+      }
+      block_sum<4, float>(acc, shf);
+      if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) partf[blockIdx.x * 8 + 2 + k] = acc[k];
+      if (!grid_barrier(a.bar, nb, a.status)) return;
+      grid_total<4, float, 8>(partf, {2, 3, 4, 5}, nb, tf, shf);
+      for (int k = 0; k < 2; ++k) {
+        if (!upd[k]) continue;
+        ++it[k];
+        const float rzk = tf[2 * k], rrk = tf[2 * k + 1];
+        if (!isfinite(rrk) || !isfinite(rzk)) {
+          fail = ST_NONFINITE;
+          done[k] = true;
+          continue;
+        }
+        if (rrk <= target2[k] || it[k] >= m.inner_cap) {
+          done[k] = true;
+          continue;
+        }
+        beta[k] = rzk / rho[k];
+        rho[k] = rzk;
+      }
+      if (fail) break;
+    }
+    inner_total[0] += it[0];
+    inner_total[1] += it[1];
+    if (fail) break;
+    for (int i = i0; i < n; i += stride) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        if (active[k]) X[k][i] += scale[k] * double(d32[k][i]);
+    }
+    if (!grid_barrier(a.bar, nb, a.status)) return;   // x complete before the next residual
+  }
+
+  // ---- normalisation of both singular solutions --------------------------------
+  if (a.pin >= 0) {
+    const double s0 = __ldcg(X[0] + a.pin), s1 = __ldcg(X[1] + a.pin);
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    for (int i = i0; i < n; i += stride) {
+      X[0][i] -= s0;
+      X[1][i] -= s1;
+    }
+  } else if (a.pin == -1) {
+    double sx[2] = {0.0, 0.0};
+    for (int i = i0; i < n; i += stride) {
+      sx[0] += X[0][i];
+      sx[1] += X[1][i];
+    }
+    block_sum<2, double>(sx, shd);
+    if (threadIdx.x == 0) {
+      partd[blockIdx.x * 8 + 0] = sx[0];
+      partd[blockIdx.x * 8 + 1] = sx[1];
+    }
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    double tm[2];
+    grid_total<2, double, 8>(partd, {0, 1}, nb, tm, shd);
+    for (int i = i0; i < n; i += stride) {
+      X[0][i] -= tm[0] / double(n);
+      X[1][i] -= tm[1] / double(n);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (fail) atomicOr(a.status, fail);
+    if (a.iters_acc) atomicAdd((unsigned long long*)a.iters_acc, (unsigned long long)(inner_total[0] + inner_total[1]));
+    if (a.outer_acc) atomicAdd((unsigned long long*)a.outer_acc, (unsigned long long)(2 * outer_total));
+    if (a.solves_acc) atomicAdd((unsigned long long*)a.solves_acc, 2ull);
+    if (a.pair_acc) atomicAdd((unsigned long long*)a.pair_acc, (unsigned long long)shared);
+  }
+}
+
+template <int W>
+int max_blocks2_t(int block) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_mixed2_kernel<W>, block, 0) != cudaSuccess) return 0;
+  return sms * per;
+}
+
 template <int W, bool AMG>
 int max_blocks_t(int block) {
   int dev = 0, sms = 0, per = 0;
@@ -258,6 +534,10 @@ int pcg_mixed_max_blocks(int block) {
   m = std::min(m, max_blocks_t<16, true>(block));
   m = std::min(m, max_blocks_t<32, true>(block));
   m = std::min(m, max_blocks_t<0, true>(block));
+  m = std::min(m, max_blocks2_t<8>(block));
+  m = std::min(m, max_blocks2_t<16>(block));
+  m = std::min(m, max_blocks2_t<32>(block));
+  m = std::min(m, max_blocks2_t<0>(block));
   return m;
 }
 
@@ -283,6 +563,21 @@ cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const Amg
   }
 }
 
+cudaError_t launch_pcg_mixed2(const PcgLaunch& P, const double* va1, double* x1, const MixedLaunch& X,
+                              const AmgDevF* H0, const AmgDevF* H1, int wmax, cudaStream_t st, float* partf8,
+                              double* partd8) {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  PcgLaunch K;
+  solver_launch_config(P, st, &cfg, attr, &K);
+  switch (wmax) {
+    case 8: return cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<8>, K, va1, x1, X, H0, H1, partf8, partd8);
+    case 16: return cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<16>, K, va1, x1, X, H0, H1, partf8, partd8);
+    case 32: return cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<32>, K, va1, x1, X, H0, H1, partf8, partd8);
+    default: return cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<0>, K, va1, x1, X, H0, H1, partf8, partd8);
+  }
+}
+
 bool mixed_cluster_ok(int block, int size) {
   return solver_cluster_ok(pcg_mixed_kernel<8, true>, block, size) &&
          solver_cluster_ok(pcg_mixed_kernel<16, true>, block, size) &&
@@ -291,7 +586,9 @@ bool mixed_cluster_ok(int block, int size) {
          solver_cluster_ok(pcg_mixed_kernel<8, false>, block, size) &&
          solver_cluster_ok(pcg_mixed_kernel<16, false>, block, size) &&
          solver_cluster_ok(pcg_mixed_kernel<32, false>, block, size) &&
-         solver_cluster_ok(pcg_mixed_kernel<0, false>, block, size);
+         solver_cluster_ok(pcg_mixed_kernel<0, false>, block, size) &&
+         solver_cluster_ok(pcg_mixed2_kernel<8>, block, size) && solver_cluster_ok(pcg_mixed2_kernel<16>, block, size) &&
+         solver_cluster_ok(pcg_mixed2_kernel<32>, block, size) && solver_cluster_ok(pcg_mixed2_kernel<0>, block, size);
 }
 
 cudaError_t launch_to_float(int64_t n, const double* src, float* dst, cudaStream_t st) {
