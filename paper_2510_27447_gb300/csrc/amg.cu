@@ -24,7 +24,7 @@ namespace bd {
 namespace {
 
 template <int WMAX>
-__global__ void __launch_bounds__(1024, 1) pcg_amg_kernel(const __grid_constant__ PcgLaunch a,
+__global__ void __launch_bounds__(1024, BD_SOLVER_MIN_BLOCKS) pcg_amg_kernel(const __grid_constant__ PcgLaunch a,
                                                            const AmgDev* __restrict__ Mp) {
   // level loops index the descriptor at run time: a by-value kernel parameter
   // would be copied to local memory, so it is staged in shared memory

@@ -26,7 +26,7 @@ namespace bd {
 namespace {
 
 template <int WMAX, bool AMG>
-__global__ void __launch_bounds__(1024, 1) pcg_mixed_kernel(const __grid_constant__ PcgLaunch a,
+__global__ void __launch_bounds__(1024, BD_SOLVER_MIN_BLOCKS) pcg_mixed_kernel(const __grid_constant__ PcgLaunch a,
                                                              const __grid_constant__ MixedLaunch m,
                                                              const AmgDevF* __restrict__ Mp, float* partf) {
   __shared__ AmgDevF sM;    // descriptor staged in shared memory (see pcg_amg_kernel)
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(1024, 1) pcg_mixed_kernel(const __grid_constan
 // Workspace vectors of the second system sit n entries after the first's;
 // partd / partf hold 8 values per block.
 template <int WMAX>
-__global__ void __launch_bounds__(1024, 1) pcg_mixed2_kernel(const __grid_constant__ PcgLaunch a,
+__global__ void __launch_bounds__(1024, BD_SOLVER_MIN_BLOCKS) pcg_mixed2_kernel(const __grid_constant__ PcgLaunch a,
                                                               const double* va1, double* x1,
                                                               const __grid_constant__ MixedLaunch m,
                                                               const AmgDevF* __restrict__ H0p,

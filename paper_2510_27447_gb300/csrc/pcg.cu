@@ -30,7 +30,7 @@ namespace bd {
 namespace {
 
 template <int WMAX>
-__global__ void __launch_bounds__(1024, 1) pcg_kernel(const __grid_constant__ PcgLaunch a) {
+__global__ void __launch_bounds__(1024, BD_SOLVER_MIN_BLOCKS) pcg_kernel(const __grid_constant__ PcgLaunch a) {
   __shared__ double sh[4][32];
   if (a.gate && *a.gate == 0) return;   // same value for every block: all skip together
   const int n = a.n;

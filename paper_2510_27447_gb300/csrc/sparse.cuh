@@ -11,6 +11,11 @@ namespace bd {
 #ifndef BD_PCG_SLEEP_NS
 #define BD_PCG_SLEEP_NS 0
 #endif
+// minimum resident 1024-thread blocks per SM the persistent solver kernels are
+// compiled for (1: up to 64 registers per thread)
+#ifndef BD_SOLVER_MIN_BLOCKS
+#define BD_SOLVER_MIN_BLOCKS 1
+#endif
 #ifndef BD_SELL_CHUNK
 #define BD_SELL_CHUNK 4
 #endif
