@@ -6,7 +6,8 @@
 // connection (Sec. 3.3.2, "AMG preconditioner ... greedy heuristic algorithm
 // based on the strength of connection").  This is the smoothed-aggregation
 // variant (Vanek, Mandel & Brezina, Computing 56, 1996):
-//   strength   j is a strong neighbour of i if |a_ij| >= theta sqrt(a_ii a_jj)
+//   strength   j is a strong neighbour of i if |a_ij| >= theta_l sqrt(a_ii a_jj),
+//              theta_l = theta 2^-l on level l
 //   aggregates greedy: (1) a node whose strong neighbours are all free starts
 //              an aggregate with them; (2) remaining nodes join the aggregate
 //              of their strongest aggregated neighbour; (3) leftovers start
@@ -243,7 +244,12 @@ int amg_build(const HCsr& A0, const AmgParams& prm, AmgHost* out, std::string* e
       }
     const double rho = rho_dinv_a(A, d, 30);
     int64_t nc = 0;
-    const std::vector<int32_t> agg = aggregate(A, d, prm.theta, &nc);
+    // the strength threshold halves per level (Vanek, Mandel & Brezina): the
+    // smoothed coarse operators spread their weight over many small entries,
+    // and a fixed threshold leaves ~2 strong neighbours per row there --
+    // aggregates of two and an exploding operator complexity
+    const double theta = prm.theta * std::ldexp(1.0, -int(out->lev.size()));
+    const std::vector<int32_t> agg = aggregate(A, d, theta, &nc);
     if (nc >= A.n) break;   // no coarsening possible
     // P = (I - w D^-1 A) T
     const double w = 4.0 / (3.0 * rho);
