@@ -118,13 +118,14 @@ struct bd_state {
   // one captured graph per step shape (dt, M, K, embedded-error estimate on/off)
   struct GraphEntry { double dt; int M, K, adapt; cudaGraphExec_t exec; int64_t launches; };
   std::vector<GraphEntry> graphs;
-  double* t_now = nullptr;                 // simulated time t^n
+  double* t_now = nullptr;                 // clock: t^n, t^{n-1}, previous-step data valid (0/1)
+  double* uprev = nullptr;                 // sweep-1 elliptic solution of the previous step
   // adaptive stepping (bd_step_adaptive)
   bool adapt_on = false;                   // the step being enqueued estimates its error
   double adapt_tol = 1.0;
   double dt_adapt = 0.0;                   // next step size (0: start at dt_max)
   unsigned long long* d_err = nullptr;
-  double *Xbak = nullptr, *ubak = nullptr, *tbak = nullptr;
+  double *Xbak = nullptr, *ubak = nullptr, *tbak = nullptr, *upbak = nullptr;
   int pcg_grid = 1, pcg_block = 512, pcg_max = 1;
   int cluster = 0;                         // > 0: solvers run as one cluster of this many 1024-thread blocks
   std::vector<void*> allocs;
@@ -687,6 +688,13 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
         CK(launch_copy(Nu, s->u[M - 1], s->u[m], s->stream, gate));
       }
     } else {
+      if (k == 2) {
+        // warm starts extrapolated in time from this and the previous step's
+        // sweep-1 solutions (u_m still holds E(v^n) at every node)
+        Timed t(s, BD_K_COMBINE, 2);
+        CK(launch_extrap(Nu, M == 3 ? s->u[1] : nullptr, s->u[M - 1], s->uprev, 0.5, dt, s->t_now, gate,
+                         s->stream));
+      }
       if (M == 3) {
         RUN(elliptic2(s, s->Xc[1], s->u[1], s->Xc[2], s->u[2]));
       } else {
@@ -1029,10 +1037,10 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
             alloc_n(s, &s->w2, (ns - 1) * NT) && alloc_n(s, &s->k1v, N) && alloc_n(s, &s->k2v, N) &&
             alloc_n(s, &s->avec, N) && alloc_n(s, &s->bvec, N) && alloc_n(s, &s->cg_r, N) &&
             alloc_n(s, &s->cg_z, N) && alloc_n(s, &s->cg_p, N) && alloc_n(s, &s->cg_q, N) &&
-            alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->t_act, NT) &&
+            alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->uprev, N) && alloc_n(s, &s->t_act, NT) &&
             alloc_n(s, &s->stim_bits, NT) &&
             (NT == N || alloc_n(s, &s->vfull, N)) &&
-            alloc_n(s, &s->step_n, 1) && alloc_n(s, &s->t_now, 1) && alloc_n(s, &s->d_err, 1) &&
+            alloc_n(s, &s->step_n, 1) && alloc_n(s, &s->t_now, 3) && alloc_n(s, &s->d_err, 1) &&
             alloc_n(s, &s->d_status, 1) && alloc_n(s, &s->d_stats, 8) &&
             alloc_n(s, &s->d_clamps, 1) && alloc_n(s, &s->bar, 2) &&
             alloc_n(s, reinterpret_cast<char**>(&s->d_amg), int64_t(sizeof(AmgDev))) &&
@@ -1106,7 +1114,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   // every node-length vector starts at zero.  Afterwards only the elliptic
   // solves write the bath entries, with finite values.
   for (double* v : {s->k1v, s->k2v, s->avec, s->bvec, s->cg_r, s->cg_z, s->cg_p, s->cg_q, s->cg_invd,
-                    s->vfull, s->vfull2})
+                    s->vfull, s->vfull2, s->uprev})
     if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, N * 8, s->stream);
   for (double* v : {s->b64, s->r64})
     if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, 2 * N * 8, s->stream);
@@ -1192,7 +1200,8 @@ int bd_set_initial(bd_state_t* s, const double* X, const double* u) {
   std::vector<double> nanv(N, std::nan(""));
   CK(cudaMemcpyAsync(s->t_act, nanv.data(), N * 8, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemsetAsync(s->step_n, 0, 8, s->stream));
-  CK(cudaMemsetAsync(s->t_now, 0, 8, s->stream));
+  CK(cudaMemsetAsync(s->t_now, 0, 24, s->stream));
+  CK(cudaMemsetAsync(s->uprev, 0, Nu * 8, s->stream));
   s->dt_adapt = 0.0;
   CK(cudaStreamSynchronize(s->stream));
   return BD_OK;
@@ -1268,10 +1277,17 @@ int bd_device_fields(const bd_state_t* s, const double** X_dev, const double** u
   return BD_OK;
 }
 
+// state blob: 64-byte header (magic, model, N, step counter, t^n, next adaptive
+// step, t^{n-1}, previous-step-data flag), then X (ns*NT), u (N), activation
+// times (NT) and the previous step's sweep-1 elliptic solution (N)
+static size_t state_bytes(const bd_state* s) {
+  return 64 + (size_t(s->ns + 1) * size_t(s->NT) + 2 * size_t(s->N)) * 8;
+}
+
 int bd_get_state(const bd_state_t* cs, void* buf, size_t* bytes) {
   bd_state* s = const_cast<bd_state*>(cs);
   if (!s || !bytes) return fail(s, BD_ERR_ARG, "NULL argument");
-  const size_t need = 48 + (size_t(s->ns + 1) * size_t(s->NT) + size_t(s->N)) * 8;
+  const size_t need = state_bytes(s);
   if (!buf) {
     *bytes = need;
     return BD_OK;
@@ -1279,39 +1295,51 @@ int bd_get_state(const bd_state_t* cs, void* buf, size_t* bytes) {
   if (*bytes < need) return fail(s, BD_ERR_ARG, "buffer too small (%zu < %zu)", *bytes, need);
   CK(cudaStreamSynchronize(s->stream));
   char* p = static_cast<char*>(buf);
-  int64_t hdr[6] = {0x62647375, s->model, s->N, 0, 0, 0};
+  int64_t hdr[8] = {0x62647376, s->model, s->N, 0, 0, 0, 0, 0};
+  double clk[3];
   CK(cudaMemcpy(&hdr[3], s->step_n, 8, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(&hdr[4], s->t_now, 8, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(clk, s->t_now, 24, cudaMemcpyDeviceToHost));
+  std::memcpy(&hdr[4], &clk[0], 8);
   std::memcpy(&hdr[5], &s->dt_adapt, 8);
-  std::memcpy(p, hdr, 48);
-  p += 48;
+  std::memcpy(&hdr[6], &clk[1], 8);
+  std::memcpy(&hdr[7], &clk[2], 8);
+  std::memcpy(p, hdr, 64);
+  p += 64;
   CK(cudaMemcpy(p, s->Xn, int64_t(s->ns) * s->NT * 8, cudaMemcpyDeviceToHost));
   p += int64_t(s->ns) * s->NT * 8;
   CK(cudaMemcpy(p, s->u[0], s->N * 8, cudaMemcpyDeviceToHost));
   p += s->N * 8;
   CK(cudaMemcpy(p, s->t_act, s->NT * 8, cudaMemcpyDeviceToHost));
+  p += s->NT * 8;
+  CK(cudaMemcpy(p, s->uprev, s->N * 8, cudaMemcpyDeviceToHost));
   *bytes = need;
   return BD_OK;
 }
 
 int bd_set_state(bd_state_t* s, const void* buf, size_t bytes) {
   if (!s || !buf) return fail(s, BD_ERR_ARG, "NULL argument");
-  const size_t need = 48 + (size_t(s->ns + 1) * size_t(s->NT) + size_t(s->N)) * 8;
+  const size_t need = state_bytes(s);
   if (bytes != need) return fail(s, BD_ERR_ARG, "state blob has %zu bytes, expected %zu", bytes, need);
   const char* p = static_cast<const char*>(buf);
-  int64_t hdr[6];
-  std::memcpy(hdr, p, 48);
-  if (hdr[0] != 0x62647375 || hdr[1] != s->model || hdr[2] != s->N)
+  int64_t hdr[8];
+  std::memcpy(hdr, p, 64);
+  if (hdr[0] != 0x62647376 || hdr[1] != s->model || hdr[2] != s->N)
     return fail(s, BD_ERR_ARG, "state blob belongs to another model or mesh");
-  p += 48;
+  p += 64;
   CK(cudaStreamSynchronize(s->stream));
   CK(cudaMemcpy(s->Xn, p, int64_t(s->ns) * s->NT * 8, cudaMemcpyHostToDevice));
   p += int64_t(s->ns) * s->NT * 8;
   for (int m = 0; m < kMaxNodes; ++m) CK(cudaMemcpy(s->u[m], p, s->N * 8, cudaMemcpyHostToDevice));
   p += s->N * 8;
   CK(cudaMemcpy(s->t_act, p, s->NT * 8, cudaMemcpyHostToDevice));
+  p += s->NT * 8;
+  CK(cudaMemcpy(s->uprev, p, s->N * 8, cudaMemcpyHostToDevice));
+  double clk[3];
+  std::memcpy(&clk[0], &hdr[4], 8);
+  std::memcpy(&clk[1], &hdr[6], 8);
+  std::memcpy(&clk[2], &hdr[7], 8);
   CK(cudaMemcpy(s->step_n, &hdr[3], 8, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(s->t_now, &hdr[4], 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(s->t_now, clk, 24, cudaMemcpyHostToDevice));
   std::memcpy(&s->dt_adapt, &hdr[5], 8);
   return BD_OK;
 }
@@ -1333,7 +1361,8 @@ int bd_step_adaptive(bd_state_t* s, double dt_max, double tol, int M, int K, dou
   if (K < 1) return fail(s, BD_ERR_ARG, "n_sweeps must be >= 1");
   const int64_t N = s->NT, Nu = s->N, ns = s->ns;
   if (!s->Xbak) {
-    if (!alloc_n(s, &s->Xbak, ns * N) || !alloc_n(s, &s->ubak, Nu) || !alloc_n(s, &s->tbak, N + 4))
+    if (!alloc_n(s, &s->Xbak, ns * N) || !alloc_n(s, &s->ubak, Nu) || !alloc_n(s, &s->tbak, N + 4) ||
+        !alloc_n(s, &s->upbak, Nu))
       return fail(s, BD_ERR_OOM, "device allocation failed");
   }
   const double dt_min = dt_max * std::ldexp(1.0, -(kAdaptLadder - 1));
@@ -1346,8 +1375,9 @@ int bd_step_adaptive(bd_state_t* s, double dt_max, double tol, int M, int K, dou
     CK(cudaMemcpyAsync(s->Xbak, s->Xn, ns * N * 8, cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(s->ubak, s->u[0], Nu * 8, cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(s->tbak, s->t_act, N * 8, cudaMemcpyDeviceToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->tbak + N, s->t_now, 8, cudaMemcpyDeviceToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->tbak + N + 1, s->step_n, 8, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->tbak + N, s->t_now, 24, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->tbak + N + 3, s->step_n, 8, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->upbak, s->uprev, Nu * 8, cudaMemcpyDeviceToDevice, s->stream));
     s->adapt_on = true;
     s->adapt_tol = tol;
     const int r = do_step(s, dt, M, K);
@@ -1366,8 +1396,9 @@ int bd_step_adaptive(bd_state_t* s, double dt_max, double tol, int M, int K, dou
     for (int m = 0; m < kMaxNodes; ++m)
       CK(cudaMemcpyAsync(s->u[m], s->ubak, Nu * 8, cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(s->t_act, s->tbak, N * 8, cudaMemcpyDeviceToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->t_now, s->tbak + N, 8, cudaMemcpyDeviceToDevice, s->stream));
-    CK(cudaMemcpyAsync(s->step_n, s->tbak + N + 1, 8, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->t_now, s->tbak + N, 24, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->step_n, s->tbak + N + 3, 8, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->uprev, s->upbak, Nu * 8, cudaMemcpyDeviceToDevice, s->stream));
     s->steps -= 1;
     s->sweeps -= K;
     dt = std::min(ladder_step(dt_max, dt * controller_factor(err)), 0.5 * dt);

@@ -92,6 +92,10 @@ cudaError_t launch_sweep_delta(int64_t n, const double* a, const double* b, unsi
 cudaError_t launch_sweep_gate(const unsigned long long* dmax, double tol, int* gate, long long* sweeps,
                               cudaStream_t st);
 cudaError_t launch_set_int(int* p, int v, unsigned long long* clear, cudaStream_t st);
+// sweep-2 elliptic initial guesses extrapolated in time (u1 may be NULL); clk =
+// (t^n, t^{n-1}, valid) is the handle's clock, marked valid afterwards
+cudaError_t launch_extrap(int64_t n, double* u1, double* u2, double* ep, double c1, double dt, double* clk,
+                          const int* gate, cudaStream_t st);
 // *p = 0 unless *gate == 0 (gate may be NULL)
 cudaError_t launch_clear_gated(unsigned long long* p, const int* gate, cudaStream_t st);
 // X^n <- X_last and activation times on the n tissue nodes, u^n <- u_last on

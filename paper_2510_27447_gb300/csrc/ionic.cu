@@ -266,10 +266,36 @@ __global__ void __launch_bounds__(256) finish_kernel(int ns, int64_t n, int64_t 
   // launch so no block can see the new value early
 }
 
-// simulated time t^{n+1} = t^n + dt and the step counter
+// simulated time t^{n+1} = t^n + dt (t_now[1] keeps t^n) and the step counter
 __global__ void bump_kernel(long long* step_n, double* t_now, double dt) {
   *step_n += 1;
-  *t_now += dt;
+  t_now[1] = t_now[0];
+  t_now[0] += dt;
+}
+
+// Initial guesses of the elliptic solves of sweep 2 (a warm start only: the
+// solves converge to their tolerance from any guess).  e = u2 holds the
+// sweep-1 solution E(v^n) at every node; with ep = the same quantity of the
+// previous step, u at t^n + c dt is extrapolated linearly in time:
+// u1 = e + c1 r (e - ep), u2 = e + r (e - ep), r = dt / (t^n - t^{n-1}).
+// clk = (t^n, t^{n-1}, valid); ep becomes e.
+__global__ void extrap_kernel(int64_t n, double* u1, double* u2, double* ep, double c1, double dt,
+                              const double* clk, const int* gate) {
+  if (gate && *gate == 0) return;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double h = clk[0] - clk[1];
+  const double r = (clk[2] != 0.0 && h > 0.0) ? fmin(dt / h, 4.0) : 0.0;
+  const double e = u2[i];
+  const double d = e - ep[i];
+  if (u1) u1[i] = e + c1 * r * d;
+  u2[i] = e + r * d;
+  ep[i] = e;
+}
+
+__global__ void set_valid_kernel(double* clk, const int* gate) {
+  if (gate && *gate == 0) return;
+  clk[2] = 1.0;
 }
 
 __global__ void sweep_delta_kernel(int64_t n, const double* a, const double* b, unsigned long long* dmax,
@@ -385,6 +411,13 @@ cudaError_t launch_update(int model, int64_t n, const double* Xt, const double* 
   const unsigned grid = unsigned((n + kBlock - 1) / kBlock);
   if (model == BD_TP06_EPI) update_kernel<19><<<grid, kBlock, 0, st>>>(n, Xt, ev, z, w, dst, gate);
   else update_kernel<8><<<grid, kBlock, 0, st>>>(n, Xt, ev, z, w, dst, gate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extrap(int64_t n, double* u1, double* u2, double* ep, double c1, double dt, double* clk,
+                          const int* gate, cudaStream_t st) {
+  if (n > 0) extrap_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(n, u1, u2, ep, c1, dt, clk, gate);
+  set_valid_kernel<<<1, 1, 0, st>>>(clk, gate);
   return cudaGetLastError();
 }
 
