@@ -100,6 +100,9 @@ struct bd_state {
   double *Xn = nullptr, *Xt[kMaxNodes] = {}, *Xc[kMaxNodes] = {}, *fq[kMaxNodes] = {}, *u[kMaxNodes] = {};
   double *dgs = nullptr, *rl = nullptr, *z1 = nullptr, *w1 = nullptr, *z2 = nullptr, *w2 = nullptr;
   double *k1v = nullptr, *k2v = nullptr, *avec = nullptr, *bvec = nullptr;
+  // increments of each (sub-interval, ROS2 stage 1 / 2, correction): sweeps
+  // >= 2 warm-start their solves from the previous sweep's
+  double* kinc[kMaxNodes - 1][3] = {};
   double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_invd = nullptr, *cg_part = nullptr;
   unsigned* bar = nullptr;
   double* t_act = nullptr;
@@ -388,7 +391,7 @@ int elliptic2(bd_state* s, const double* v1, double* u1, const double* v2, doubl
 // (alpha M_v + A_i + diag(dgs)) x = rl + c1 A_i va + c2 M_v vb; node_terms =
 // false drops diag(dgs) and rl (the plain Crank-Nicolson operator)
 int parabolic(bd_state* s, double alpha, double c1, const double* va, double c2, const double* vb, double* x,
-              bool node_terms = true) {
+              bool node_terms = true, bool warm = false) {
   PcgLaunch P = pcg_base(s);
   P.n = int(s->NT);   // tissue rows; their bath columns hold zeros
   P.valA = p_values(s, alpha);
@@ -404,7 +407,7 @@ int parabolic(bd_state* s, double alpha, double c1, const double* va, double c2,
   }
   P.project = 0;
   P.x = x;
-  P.warm = 0;
+  P.warm = warm ? 1 : 0;
   P.tol = s->opts.cg_tol_p;
   P.maxit = s->opts.cg_cap_p;
   P.pin = -2;
@@ -722,13 +725,15 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
         Timed t(s, BD_K_IONIC);
         CK(launch_ionic(L, s->stream));
       }
-      RUN(parabolic(s, alpha, -1.0, s->avec, 0.0, nullptr, s->k1v));
+      double* k1 = s->kinc[m][0];
+      double* k2 = s->kinc[m][1];
+      RUN(parabolic(s, alpha, -1.0, s->avec, 0.0, nullptr, k1, true, k > 1));
       IonicLaunch L2 = ionic_base(s, MODE_S2, dt);
       L2.alpha = alpha;
       L2.smin = L.smin;
       L2.XJ = src;
       L2.u = s->u[m + 1];
-      L2.k1v = s->k1v;
+      L2.k1v = k1;
       L2.z1 = s->z1;
       L2.w1 = s->w1;
       L2.ck1 = 2.0 / (gam * h);
@@ -740,10 +745,10 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
         Timed t(s, BD_K_IONIC);
         CK(launch_ionic(L2, s->stream));
       }
-      RUN(parabolic(s, alpha, -1.0, s->avec, -L2.ck1, s->bvec, s->k2v));
+      RUN(parabolic(s, alpha, -1.0, s->avec, -L2.ck1, s->bvec, k2, true, k > 1));
       {
         Timed t(s, BD_K_COMBINE);
-        CK(launch_combine(s->model, N, src, s->k1v, s->z1, s->w1, s->k2v, s->z2, s->w2, 1.5 / gam, 0.5 / gam,
+        CK(launch_combine(s->model, N, src, k1, s->z1, s->w1, k2, s->z2, s->w2, 1.5 / gam, 0.5 / gam,
                           s->Xt[m + 1], s->stream, gate, 1.0 / gam, s->adapt_tol,
                           s->adapt_on ? s->d_err : nullptr));
       }
@@ -780,10 +785,11 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
           Timed t(s, BD_K_IONIC);
           CK(launch_ionic(L, s->stream));
         }
-        RUN(parabolic(s, alpha, -1.0 / h, s->avec, 1.0 / h, s->bvec, s->k1v));
+        double* ek = s->kinc[m][2];
+        RUN(parabolic(s, alpha, -1.0 / h, s->avec, 1.0 / h, s->bvec, ek, true, k > 1));
         {
           Timed t(s, BD_K_COMBINE);
-          CK(launch_update(s->model, N, s->Xt[m + 1], s->k1v, s->z1, s->w1, s->Xc[m + 1], s->stream, gate));
+          CK(launch_update(s->model, N, s->Xt[m + 1], ek, s->z1, s->w1, s->Xc[m + 1], s->stream, gate));
         }
         s->ionic_evals += 1;
       }
@@ -1037,7 +1043,9 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
             alloc_n(s, &s->w2, (ns - 1) * NT) && alloc_n(s, &s->k1v, N) && alloc_n(s, &s->k2v, N) &&
             alloc_n(s, &s->avec, N) && alloc_n(s, &s->bvec, N) && alloc_n(s, &s->cg_r, N) &&
             alloc_n(s, &s->cg_z, N) && alloc_n(s, &s->cg_p, N) && alloc_n(s, &s->cg_q, N) &&
-            alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->uprev, N) && alloc_n(s, &s->t_act, NT) &&
+            alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->uprev, N) && alloc_n(s, &s->kinc[0][0], N) &&
+            alloc_n(s, &s->kinc[0][1], N) && alloc_n(s, &s->kinc[0][2], N) && alloc_n(s, &s->kinc[1][0], N) &&
+            alloc_n(s, &s->kinc[1][1], N) && alloc_n(s, &s->kinc[1][2], N) && alloc_n(s, &s->t_act, NT) &&
             alloc_n(s, &s->stim_bits, NT) &&
             (NT == N || alloc_n(s, &s->vfull, N)) &&
             alloc_n(s, &s->step_n, 1) && alloc_n(s, &s->t_now, 3) && alloc_n(s, &s->d_err, 1) &&
@@ -1114,7 +1122,8 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   // every node-length vector starts at zero.  Afterwards only the elliptic
   // solves write the bath entries, with finite values.
   for (double* v : {s->k1v, s->k2v, s->avec, s->bvec, s->cg_r, s->cg_z, s->cg_p, s->cg_q, s->cg_invd,
-                    s->vfull, s->vfull2, s->uprev})
+                    s->vfull, s->vfull2, s->uprev, s->kinc[0][0], s->kinc[0][1], s->kinc[0][2],
+                    s->kinc[1][0], s->kinc[1][1], s->kinc[1][2]})
     if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, N * 8, s->stream);
   for (double* v : {s->b64, s->r64})
     if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, 2 * N * 8, s->stream);

@@ -114,6 +114,9 @@ __global__ void __launch_bounds__(1024, BD_SOLVER_MIN_BLOCKS) pcg_mixed_kernel(c
     const double inv_scale = 1.0 / scale;
     double tgt = double(m.tol_inner) * double(m.tol_inner);
     if (m.max_outer > 1) tgt = fmax(tgt, 0.25 * tol2 / rr64);
+    // single solve: the target is tol_inner |b|, so a warm start that already
+    // reduced the residual needs fewer iterations (cold: rr64 = |b|^2)
+    else if (a.warm) tgt = fmax(tgt, tgt * bb / rr64);
     const float target2 = float(tgt);
 
     // ---- FP32 inner CG on A d = r / |r| ----------------------------------
