@@ -216,6 +216,14 @@ int bd_step_decoupled(bd_state_t* s, double dt_ms);
 int bd_step_adaptive(bd_state_t* s, double dt_max, double tol, int n_sdc_nodes, int n_sweeps,
                      double* dt_taken, double* err, int* rejected);
 
+/* Failure-path check (the paper has no counterpart): one block waits at a
+ * device-wide barrier sized for two blocks, so the wait runs out after its
+ * bound of about two seconds of device time, as a solver's wait would if a
+ * block never arrived.  Returns BD_ERR_TIMEOUT when the bound works (any
+ * other value is a fault of the build); the handle's status word and barrier
+ * are reset afterwards, so the handle stays usable. */
+int bd_selftest_wait_timeout(bd_state_t* s);
+
 /* Simulated time t^n (ms) and number of completed steps (each may be NULL). */
 int bd_get_time(const bd_state_t* s, double* t_ms, int64_t* steps);
 

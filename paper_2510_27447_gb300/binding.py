@@ -26,7 +26,8 @@ EXPORTS = ["bd_default_options", "bd_create", "bd_add_stimulus", "bd_set_initial
            "bd_reset_stats", "bd_num_nodes", "bd_num_states", "bd_last_error", "bd_destroy",
            "bd_ionic_eval", "bd_ionic_pattern", "bd_rest_state", "bd_operator_csr",
            "bd_solve_elliptic", "bd_profile_steps", "bd_solve_elliptic_noalloc", "bd_query",
-           "bd_step_adaptive", "bd_get_time", "bd_num_tissue_nodes", "bd_step_decoupled"]
+           "bd_step_adaptive", "bd_get_time", "bd_num_tissue_nodes", "bd_step_decoupled",
+           "bd_selftest_wait_timeout"]
 
 
 class LibraryMissing(RuntimeError):
@@ -100,6 +101,7 @@ def lib():
         "bd_set_initial": (C.c_int, [C.c_void_p, dp, dp]),
         "bd_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int]),
         "bd_step_decoupled": (C.c_int, [C.c_void_p, C.c_double]),
+        "bd_selftest_wait_timeout": (C.c_int, [C.c_void_p]),
         "bd_batch_step": (C.c_int, [P(C.c_void_p), C.c_int, C.c_double, C.c_int, C.c_int]),
         "bd_sync": (C.c_int, [C.c_void_p]),
         "bd_query": (C.c_int, [C.c_void_p]),

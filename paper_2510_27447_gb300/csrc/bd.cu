@@ -1224,6 +1224,18 @@ int bd_step(bd_state_t* s, double dt, int M, int K) {
   return do_step(s, dt, M, K);
 }
 
+int bd_selftest_wait_timeout(bd_state_t* s) {
+  if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaMemsetAsync(s->bar, 0, 8, s->stream));
+  CK(launch_wait_selftest(s->bar, s->d_status, s->stream));
+  const int rc = read_status(s);   // synchronises; BD_ERR_TIMEOUT expected
+  std::string msg = s->err;
+  bd_clear_status(s);              // status word and barrier back to zero
+  if (rc != BD_OK) fail(s, rc, "%s", msg.c_str());
+  return rc;
+}
+
 int bd_step_decoupled(bd_state_t* s, double dt) {
   if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
   if (!(dt > 0) || !std::isfinite(dt)) return fail(s, BD_ERR_ARG, "dt must be positive");

@@ -164,6 +164,8 @@ bool pcg_cluster_ok(int block, int size);     // pcg.cu
 bool amg_cluster_ok(int block, int size);     // amg.cu
 bool mixed_cluster_ok(int block, int size);   // mixed.cu
 cudaError_t launch_pcg(const PcgLaunch& P, int wmax, cudaStream_t st);
+// a device-barrier wait that must run out (bd_selftest_wait_timeout)
+cudaError_t launch_wait_selftest(unsigned* bar, int* status, cudaStream_t st);
 int pcg_max_blocks(int block, int wmax);
 cudaError_t launch_axpby_vals(int64_t nnz, double a, const double* X, double b, const double* Y, double* out,
                               cudaStream_t st);

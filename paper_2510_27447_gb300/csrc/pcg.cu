@@ -198,6 +198,15 @@ int max_blocks_t(int block) {
 }
 }  // namespace
 
+// one block waits at a device-wide barrier sized for two blocks: the second
+// never exists, so the wait runs out and records ST_TIMEOUT
+__global__ void wait_selftest_kernel(unsigned* bar, int* status) { grid_barrier(bar, 2u, status); }
+
+cudaError_t launch_wait_selftest(unsigned* bar, int* status, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(bar, status);
+  return cudaGetLastError();
+}
+
 bool pcg_cluster_ok(int block, int size) {
   return solver_cluster_ok(pcg_kernel<8>, block, size) && solver_cluster_ok(pcg_kernel<16>, block, size) &&
          solver_cluster_ok(pcg_kernel<32>, block, size) && solver_cluster_ok(pcg_kernel<0>, block, size);

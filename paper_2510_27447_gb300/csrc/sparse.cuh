@@ -19,14 +19,24 @@ namespace bd {
 #ifndef BD_SELL_CHUNK
 #define BD_SELL_CHUNK 4
 #endif
-constexpr long long kSpinLimit = 1ll << 26;   // bounded wait: about a second of polling
+// bounded waits: a device-barrier wait gives up after kWaitLimitNs of device
+// time (%globaltimer), with an iteration cap as a backstop
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+constexpr long long kSpinLimit = 1ll << 28;
+
+__device__ __forceinline__ unsigned long long device_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // Device-wide barrier on one arrival word: block 0 adds 2^31 - (nblocks - 1),
 // every other block adds 1, so the word's top bit flips exactly when the last
 // block of a round arrives and the low bits return to their old value (no
 // reset step).  Arrival is a release RMW (publishes the block's writes), the
 // wait an acquire load (sees every arriving block's writes).  The wait is
-// bounded: on timeout the kernel records ST_TIMEOUT and the caller returns.
+// bounded (two seconds): on timeout the kernel records ST_TIMEOUT and every
+// block returns, leaving the context usable.
 __device__ __forceinline__ unsigned bar_ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -58,9 +68,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
     const unsigned old = bar_add_acq_rel(bar, add);
     ok = 1;
     long long spins = 0;
+    const unsigned long long t0 = device_ns();
     while (((old ^ bar_ld_acquire(bar)) & 0x80000000u) == 0u) {
       if (BD_PCG_SLEEP_NS > 0) __nanosleep(BD_PCG_SLEEP_NS);
-      if (++spins > kSpinLimit) {
+      ++spins;
+      if (((spins & 255) == 0 && device_ns() - t0 > kWaitLimitNs) || spins > kSpinLimit) {
         atomicOr(status, ST_TIMEOUT);
         ok = 0;
         break;

@@ -180,3 +180,21 @@ def test_solver_launch_modes_match_oracle(cluster):
         u1, _ = sim.solve_elliptic(v)
         sim.close()
         assert rel(u1, oracle_problem(w).elliptic(v)) < 1e-9
+
+
+def test_device_barrier_wait_is_bounded():
+    """A device-wide barrier whose partner block never arrives gives up after
+    its bound (about two seconds of device time), reports BD_ERR_TIMEOUT, and
+    leaves the handle usable."""
+    import time
+    w = W.sheet(9, 0.2, W.LR91, 0.02, 3, strip=0.05)
+    sim = gpu_sim(w)
+    t0 = time.perf_counter()
+    rc = binding.lib().bd_selftest_wait_timeout(sim.h)
+    el = time.perf_counter() - t0
+    assert rc == -7 and 1.0 < el < 30.0, (rc, el)
+    for _ in range(3):
+        sim.step(w.dt)
+    v, u = sim.fields()
+    sim.close()
+    assert np.all(np.isfinite(v)) and np.all(np.isfinite(u))
