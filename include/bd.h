@@ -254,9 +254,10 @@ int bd_get_fields(const bd_state_t* s, double* vm, double* phie, double* X);
 int bd_device_fields(const bd_state_t* s, const double** X_dev, const double** u_dev);
 
 /* Serialise (X, u, step counter, simulated time and the previous step's,
- * adaptive step, activation times, the previous step's sweep-1 elliptic
- * solution used to extrapolate warm starts) to host memory, so a restored
- * handle continues bit for bit.  With buf == NULL only *bytes is set. */
+ * adaptive step, activation times, and the solver warm starts: the previous
+ * step's sweep-1 elliptic solution and the last parabolic increments) to
+ * host memory, so a restored handle continues bit for bit.  With
+ * buf == NULL only *bytes is set. */
 int bd_get_state(const bd_state_t* s, void* buf, size_t* bytes);
 int bd_set_state(bd_state_t* s, const void* buf, size_t bytes);
 

@@ -100,8 +100,8 @@ struct bd_state {
   double *Xn = nullptr, *Xt[kMaxNodes] = {}, *Xc[kMaxNodes] = {}, *fq[kMaxNodes] = {}, *u[kMaxNodes] = {};
   double *dgs = nullptr, *rl = nullptr, *z1 = nullptr, *w1 = nullptr, *z2 = nullptr, *w2 = nullptr;
   double *k1v = nullptr, *k2v = nullptr, *avec = nullptr, *bvec = nullptr;
-  // increments of each (sub-interval, ROS2 stage 1 / 2, correction): sweeps
-  // >= 2 warm-start their solves from the previous sweep's
+  // increments of each (sub-interval, ROS2 stage 1 / 2, correction): every
+  // solve warm-starts from the previous sweep's (sweep 1: the previous step's)
   double* kinc[kMaxNodes - 1][3] = {};
   double *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_q = nullptr, *cg_invd = nullptr, *cg_part = nullptr;
   unsigned* bar = nullptr;
@@ -727,7 +727,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       }
       double* k1 = s->kinc[m][0];
       double* k2 = s->kinc[m][1];
-      RUN(parabolic(s, alpha, -1.0, s->avec, 0.0, nullptr, k1, true, k > 1));
+      RUN(parabolic(s, alpha, -1.0, s->avec, 0.0, nullptr, k1, true, true));
       IonicLaunch L2 = ionic_base(s, MODE_S2, dt);
       L2.alpha = alpha;
       L2.smin = L.smin;
@@ -745,7 +745,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
         Timed t(s, BD_K_IONIC);
         CK(launch_ionic(L2, s->stream));
       }
-      RUN(parabolic(s, alpha, -1.0, s->avec, -L2.ck1, s->bvec, k2, true, k > 1));
+      RUN(parabolic(s, alpha, -1.0, s->avec, -L2.ck1, s->bvec, k2, true, true));
       {
         Timed t(s, BD_K_COMBINE);
         CK(launch_combine(s->model, N, src, k1, s->z1, s->w1, k2, s->z2, s->w2, 1.5 / gam, 0.5 / gam,
@@ -786,7 +786,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
           CK(launch_ionic(L, s->stream));
         }
         double* ek = s->kinc[m][2];
-        RUN(parabolic(s, alpha, -1.0 / h, s->avec, 1.0 / h, s->bvec, ek, true, k > 1));
+        RUN(parabolic(s, alpha, -1.0 / h, s->avec, 1.0 / h, s->bvec, ek, true, true));
         {
           Timed t(s, BD_K_COMBINE);
           CK(launch_update(s->model, N, s->Xt[m + 1], ek, s->z1, s->w1, s->Xc[m + 1], s->stream, gate));
@@ -1211,6 +1211,8 @@ int bd_set_initial(bd_state_t* s, const double* X, const double* u) {
   CK(cudaMemsetAsync(s->step_n, 0, 8, s->stream));
   CK(cudaMemsetAsync(s->t_now, 0, 24, s->stream));
   CK(cudaMemsetAsync(s->uprev, 0, Nu * 8, s->stream));
+  for (int m = 0; m < kMaxNodes - 1; ++m)
+    for (int g = 0; g < 3; ++g) CK(cudaMemsetAsync(s->kinc[m][g], 0, Nu * 8, s->stream));
   s->dt_adapt = 0.0;
   CK(cudaStreamSynchronize(s->stream));
   return BD_OK;
@@ -1300,9 +1302,10 @@ int bd_device_fields(const bd_state_t* s, const double** X_dev, const double** u
 
 // state blob: 64-byte header (magic, model, N, step counter, t^n, next adaptive
 // step, t^{n-1}, previous-step-data flag), then X (ns*NT), u (N), activation
-// times (NT) and the previous step's sweep-1 elliptic solution (N)
+// times (NT), the previous step's sweep-1 elliptic solution (N) and the last
+// parabolic increments (6 x NT; warm starts)
 static size_t state_bytes(const bd_state* s) {
-  return 64 + (size_t(s->ns + 1) * size_t(s->NT) + 2 * size_t(s->N)) * 8;
+  return 64 + (size_t(s->ns + 1 + 3 * (kMaxNodes - 1)) * size_t(s->NT) + 2 * size_t(s->N)) * 8;
 }
 
 int bd_get_state(const bd_state_t* cs, void* buf, size_t* bytes) {
@@ -1333,6 +1336,12 @@ int bd_get_state(const bd_state_t* cs, void* buf, size_t* bytes) {
   CK(cudaMemcpy(p, s->t_act, s->NT * 8, cudaMemcpyDeviceToHost));
   p += s->NT * 8;
   CK(cudaMemcpy(p, s->uprev, s->N * 8, cudaMemcpyDeviceToHost));
+  p += s->N * 8;
+  for (int m = 0; m < kMaxNodes - 1; ++m)
+    for (int g = 0; g < 3; ++g) {
+      CK(cudaMemcpy(p, s->kinc[m][g], s->NT * 8, cudaMemcpyDeviceToHost));
+      p += s->NT * 8;
+    }
   *bytes = need;
   return BD_OK;
 }
@@ -1355,6 +1364,12 @@ int bd_set_state(bd_state_t* s, const void* buf, size_t bytes) {
   CK(cudaMemcpy(s->t_act, p, s->NT * 8, cudaMemcpyHostToDevice));
   p += s->NT * 8;
   CK(cudaMemcpy(s->uprev, p, s->N * 8, cudaMemcpyHostToDevice));
+  p += s->N * 8;
+  for (int m = 0; m < kMaxNodes - 1; ++m)
+    for (int g = 0; g < 3; ++g) {
+      CK(cudaMemcpy(s->kinc[m][g], p, s->NT * 8, cudaMemcpyHostToDevice));
+      p += s->NT * 8;
+    }
   double clk[3];
   std::memcpy(&clk[0], &hdr[4], 8);
   std::memcpy(&clk[1], &hdr[6], 8);
