@@ -48,7 +48,7 @@ struct Params<TP06> {
 // ---------------------------------------------------------------------------
 // condensation kernel: S1, S2 and correction modes
 // ---------------------------------------------------------------------------
-template <template <class> class Model, class T, int MODE>
+template <template <class> class Model, class T, int MODE, int NQ = 0>
 __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, const Model<T> P) {
   using Mod = Model<T>;
   constexpr int NS = Mod::NS;
@@ -108,7 +108,10 @@ __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, cons
 #pragma unroll
     for (int k = 0; k < NS; ++k) q[k] = 0.0;
     double av = 0.0;
-    for (int jn = 0; jn < L.n_nodes; ++jn) {
+    // NQ quadrature nodes, known at compile time: the node loop unrolls and
+    // every pointer of L is read at a constant offset
+#pragma unroll
+    for (int jn = 0; jn < NQ; ++jn) {
       const double S = L.S[jn];
       const double* fj = L.fq[jn];
 #pragma unroll
@@ -335,7 +338,10 @@ cudaError_t launch_ionic_t(const IonicLaunch& L, cudaStream_t st) {
   switch (L.mode) {
     case MODE_S1: ionic_kernel<Model, T, MODE_S1><<<grid, kBlock, 0, st>>>(L, P); break;
     case MODE_S2: ionic_kernel<Model, T, MODE_S2><<<grid, kBlock, 0, st>>>(L, P); break;
-    default: ionic_kernel<Model, T, MODE_CORR><<<grid, kBlock, 0, st>>>(L, P); break;
+    default:
+      if (L.n_nodes == 3) ionic_kernel<Model, T, MODE_CORR, 3><<<grid, kBlock, 0, st>>>(L, P);
+      else ionic_kernel<Model, T, MODE_CORR, 2><<<grid, kBlock, 0, st>>>(L, P);
+      break;
   }
   return cudaGetLastError();
 }
