@@ -123,6 +123,7 @@ struct bd_state {
   std::vector<GraphEntry> graphs;
   double* t_now = nullptr;                 // clock: t^n, t^{n-1}, previous-step data valid (0/1)
   double* uprev = nullptr;                 // sweep-1 elliptic solution of the previous step
+  void* pack = nullptr;                    // stage-1 condensation of the current ROS2 step (stage 2 reuses it)
   // adaptive stepping (bd_step_adaptive)
   bool adapt_on = false;                   // the step being enqueued estimates its error
   double adapt_tol = 1.0;
@@ -721,6 +722,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       L.z = s->z1;
       L.w = s->w1;
       L.fq_out = (m >= 1 && s->opts.sdc_correction) ? s->fq[m] : nullptr;
+      L.pack = s->pack;
       {
         Timed t(s, BD_K_IONIC);
         CK(launch_ionic(L, s->stream));
@@ -728,7 +730,8 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       double* k1 = s->kinc[m][0];
       double* k2 = s->kinc[m][1];
       RUN(parabolic(s, alpha, -1.0, s->avec, 0.0, nullptr, k1, true, true));
-      IonicLaunch L2 = ionic_base(s, MODE_S2, dt);
+      IonicLaunch L2 = ionic_base(s, MODE_S2P, dt);   // reuses stage 1's condensation
+      L2.pack = s->pack;
       L2.alpha = alpha;
       L2.smin = L.smin;
       L2.XJ = src;
@@ -739,7 +742,6 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       L2.ck1 = 2.0 / (gam * h);
       L2.inv_gamma = 1.0 / gam;
       L2.z = s->z2;
-      L2.w = s->w2;
       L2.bvec = s->bvec;
       {
         Timed t(s, BD_K_IONIC);
@@ -748,7 +750,7 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       RUN(parabolic(s, alpha, -1.0, s->avec, -L2.ck1, s->bvec, k2, true, true));
       {
         Timed t(s, BD_K_COMBINE);
-        CK(launch_combine(s->model, N, src, k1, s->z1, s->w1, k2, s->z2, s->w2, 1.5 / gam, 0.5 / gam,
+        CK(launch_combine(s->model, N, src, k1, s->z1, s->w1, k2, s->z2, s->w1, 1.5 / gam, 0.5 / gam,
                           s->Xt[m + 1], s->stream, gate, 1.0 / gam, s->adapt_tol,
                           s->adapt_on ? s->d_err : nullptr));
       }
@@ -1043,7 +1045,8 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
             alloc_n(s, &s->w2, (ns - 1) * NT) && alloc_n(s, &s->k1v, N) && alloc_n(s, &s->k2v, N) &&
             alloc_n(s, &s->avec, N) && alloc_n(s, &s->bvec, N) && alloc_n(s, &s->cg_r, N) &&
             alloc_n(s, &s->cg_z, N) && alloc_n(s, &s->cg_p, N) && alloc_n(s, &s->cg_q, N) &&
-            alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->uprev, N) && alloc_n(s, &s->kinc[0][0], N) &&
+            alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->uprev, N) &&
+            alloc_n(s, reinterpret_cast<double**>(&s->pack), int64_t(cond_pack_values(s->model)) * NT) && alloc_n(s, &s->kinc[0][0], N) &&
             alloc_n(s, &s->kinc[0][1], N) && alloc_n(s, &s->kinc[0][2], N) && alloc_n(s, &s->kinc[1][0], N) &&
             alloc_n(s, &s->kinc[1][1], N) && alloc_n(s, &s->kinc[1][2], N) && alloc_n(s, &s->t_act, NT) &&
             alloc_n(s, &s->stim_bits, NT) &&

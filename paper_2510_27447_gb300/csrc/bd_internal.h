@@ -29,7 +29,8 @@ struct StimTable {
 };
 
 // one node-local right-hand side recipe per ionic kernel launch
-enum IonicMode : int { MODE_S1 = 0, MODE_S2 = 1, MODE_CORR = 2 };
+// MODE_S2P: stage 2 from the condensation stage 1 stored in `pack`
+enum IonicMode : int { MODE_S1 = 0, MODE_S2 = 1, MODE_CORR = 2, MODE_S2P = 3 };
 
 struct IonicLaunch {
   int model;                 // bd_ionic_t
@@ -67,7 +68,10 @@ struct IonicLaunch {
   double* fq_out;            // out (optional): node field at the F point
   unsigned long long* clamp_count;
   const int* gate;           // optional: kernel does nothing when *gate == 0 (sweep test)
+  void* pack;                // S1: store the condensation here (optional); S2P: read it
 };
+// values per node of the stage-1 condensation pack (model, compute type)
+int cond_pack_values(int model);
 
 // launchers (ionic.cu)
 cudaError_t launch_ionic(const IonicLaunch& L, cudaStream_t st);

@@ -62,6 +62,38 @@ __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, cons
   double xj[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) xj[k] = L.XJ[k * n + i];
+
+  if constexpr (MODE == MODE_S2P) {
+    // stage 2 without a second Jacobian: field at X* = X + k1/gamma, then
+    // z = A^-1 rho with stage 1's stored condensation; the condensed diagonal
+    // and w are stage 1's (unchanged)
+    const double k1v = L.k1v[i];
+    double xs[NS];
+    double k1y[NS - 1];
+    xs[0] = xj[0] + k1v * L.inv_gamma;
+#pragma unroll
+    for (int k = 1; k < NS; ++k) {
+      k1y[k - 1] = L.z1[(k - 1) * n + i] + L.w1[(k - 1) * n + i] * k1v;
+      xs[k] = xj[k] + k1y[k - 1] * L.inv_gamma;
+    }
+    T xst[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) xst[k] = T(xs[k]);
+    ValSink<T, Mod> fs;
+    P.eval(xst, T(istim), T(L.inv_cm), fs);
+    T rho[NS - 1];
+#pragma unroll
+    for (int k = 1; k < NS; ++k) rho[k - 1] = T(double(fs.f[k]) - L.ck1 * k1y[k - 1]);
+    T corr, z[NS - 1];
+    cond_solve<T, Mod>(static_cast<const T*>(L.pack) + i, n, rho, corr, z);
+    L.rl[i] = L.ML[i] * (double(fs.f[0]) + double(corr));
+#pragma unroll
+    for (int k = 0; k < NS - 1; ++k) L.z[k * n + i] = double(z[k]);
+    L.avec[i] = xs[0] + L.u[i];
+    if (L.bvec) L.bvec[i] = k1v;
+    return;
+  }
+
   T xt[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) xt[k] = T(xj[k]);
@@ -77,6 +109,7 @@ __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, cons
     for (int k = 1; k < NS; ++k) rho[k - 1] = e.f[k];
     fv = double(e.f[0]);
     avec = xj[0] + L.u[i];
+    if (L.pack) cond_store<T, Mod>(e, T(L.alpha), static_cast<T*>(L.pack) + i, n);
     if (L.fq_out) {
 #pragma unroll
       for (int k = 0; k < NS; ++k) L.fq_out[k * n + i] = double(e.f[k]);
@@ -338,6 +371,7 @@ cudaError_t launch_ionic_t(const IonicLaunch& L, cudaStream_t st) {
   switch (L.mode) {
     case MODE_S1: ionic_kernel<Model, T, MODE_S1><<<grid, kBlock, 0, st>>>(L, P); break;
     case MODE_S2: ionic_kernel<Model, T, MODE_S2><<<grid, kBlock, 0, st>>>(L, P); break;
+    case MODE_S2P: ionic_kernel<Model, T, MODE_S2P><<<grid, kBlock, 0, st>>>(L, P); break;
     default:
       if (L.n_nodes == 3) ionic_kernel<Model, T, MODE_CORR, 3><<<grid, kBlock, 0, st>>>(L, P);
       else ionic_kernel<Model, T, MODE_CORR, 2><<<grid, kBlock, 0, st>>>(L, P);
@@ -347,6 +381,10 @@ cudaError_t launch_ionic_t(const IonicLaunch& L, cudaStream_t st) {
 }
 
 }  // namespace
+
+int cond_pack_values(int model) {
+  return model == BD_TP06_EPI ? cond_pack_size<TP06<double>>() : cond_pack_size<LR91<double>>();
+}
 
 int model_ns(int model) {
   switch (model) {

@@ -555,4 +555,94 @@ BD_HD void condense(const JacSink<T, Model>& e, T alpha, const T* rho, T& s, T& 
   });
 }
 
+// What stage 2 of a ROS2 step needs of stage 1's condensation (same node
+// Jacobian, same shift alpha): stage 1 stores it, stage 2 then solves
+// A z = rho for its new rho without evaluating the Jacobian again.  Layout per
+// node, PACK values (strided by the node count):
+//   [0, NG)             1 / (alpha - d g_k / d x_k), gates k = 1..NG
+//   [NG, NG + NB NG)    d f_{NG+1+r} / d x_k, block row r, gate k (pattern entries)
+//   next NB NB          the block matrix alpha I - J_yy restricted to the block
+//   next NS             d f_0 / d X_c (pattern entries)
+template <class Model>
+constexpr int cond_pack_size() {
+  return Model::NG + Model::NB * Model::NG + Model::NB * Model::NB + Model::NS;
+}
+
+template <class T, class Model>
+BD_HD void cond_store(const JacSink<T, Model>& e, T alpha, T* pk, int64_t stride) {
+  constexpr int NG = Model::NG, NB = Model::NB;
+  constexpr uint32_t GATES = ((1u << (NG + 1)) - 1u) & ~1u;
+#pragma unroll
+  for (int g = 1; g <= NG; ++g) pk[(g - 1) * stride] = T(1) / (alpha - e.jgd[g]);
+  auto row = [&](auto rr) {
+    constexpr int r = decltype(rr)::value;
+    constexpr uint32_t RM = Model::ROWMASK[NG + 1 + r];
+    for_bits<RM & GATES>([&](auto b) {
+      constexpr int c = decltype(b)::value;
+      pk[(NG + r * NG + (c - 1)) * stride] = e.jb[r][c];
+    });
+#pragma unroll
+    for (int c = 0; c < NB; ++c) pk[(NG + NB * NG + r * NB + c) * stride] = (r == c) ? alpha : T(0);
+    for_bits<(RM >> (NG + 1))>([&](auto b) {
+      constexpr int c = decltype(b)::value;
+      pk[(NG + NB * NG + r * NB + c) * stride] = ((r == c) ? alpha : T(0)) - e.jb[r][NG + 1 + c];
+    });
+  };
+  [&]<int... R>(std::integer_sequence<int, R...>) { (row(std::integral_constant<int, R>{}), ...); }
+  (std::make_integer_sequence<int, NB>{});
+  for_bits<Model::ROWMASK[0] & ~1u>([&](auto b) {
+    constexpr int c = decltype(b)::value;
+    pk[(NG + NB * NG + NB * NB + c) * stride] = e.jv[c];
+  });
+}
+
+// z = A^-1 rho and corr = sum_c j_vc z_c from a stored pack: the arithmetic of
+// condense() for z and corr, operation for operation
+template <class T, class Model>
+BD_HD void cond_solve(const T* pk, int64_t stride, const T* rho, T& corr, T* z) {
+  constexpr int NG = Model::NG, NB = Model::NB;
+  constexpr uint32_t GATES = ((1u << (NG + 1)) - 1u) & ~1u;
+#pragma unroll
+  for (int g = 1; g <= NG; ++g) z[g - 1] = rho[g - 1] * pk[(g - 1) * stride];
+  T Bm[NB][NB];
+  T rz[NB];
+  auto fill = [&](auto rr) {
+    constexpr int r = decltype(rr)::value;
+    constexpr uint32_t RM = Model::ROWMASK[NG + 1 + r];
+    rz[r] = rho[NG + r];
+    for_bits<RM & GATES>([&](auto b) {
+      constexpr int c = decltype(b)::value;
+      rz[r] += pk[(NG + r * NG + (c - 1)) * stride] * z[c - 1];
+    });
+#pragma unroll
+    for (int c = 0; c < NB; ++c) Bm[r][c] = pk[(NG + NB * NG + r * NB + c) * stride];
+  };
+  [&]<int... R>(std::integer_sequence<int, R...>) { (fill(std::integral_constant<int, R>{}), ...); }
+  (std::make_integer_sequence<int, NB>{});
+#pragma unroll
+  for (int k = 0; k < NB; ++k) {
+    const T piv = T(1) / Bm[k][k];
+#pragma unroll
+    for (int i = k + 1; i < NB; ++i) {
+      const T l = Bm[i][k] * piv;
+#pragma unroll
+      for (int c = k + 1; c < NB; ++c) Bm[i][c] -= l * Bm[k][c];
+      rz[i] -= l * rz[k];
+    }
+  }
+#pragma unroll
+  for (int i = NB - 1; i >= 0; --i) {
+#pragma unroll
+    for (int c = i + 1; c < NB; ++c) rz[i] -= Bm[i][c] * rz[c];
+    const T inv = T(1) / Bm[i][i];
+    rz[i] *= inv;
+    z[NG + i] = rz[i];
+  }
+  corr = T(0);
+  for_bits<Model::ROWMASK[0] & ~1u>([&](auto b) {
+    constexpr int c = decltype(b)::value;
+    corr += pk[(NG + NB * NG + NB * NB + c) * stride] * z[c - 1];
+  });
+}
+
 }  // namespace bd
