@@ -23,8 +23,8 @@ namespace bd {
 
 namespace {
 
-template <int WMAX>
-__global__ void __launch_bounds__(1024, BD_SOLVER_MIN_BLOCKS) pcg_amg_kernel(const __grid_constant__ PcgLaunch a,
+template <int WMAX, int TPB>
+__global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_amg_kernel(const __grid_constant__ PcgLaunch a,
                                                            const AmgDev* __restrict__ Mp) {
   // level loops index the descriptor at run time: a by-value kernel parameter
   // would be copied to local memory, so it is staged in shared memory
@@ -161,24 +161,21 @@ __global__ void __launch_bounds__(1024, BD_SOLVER_MIN_BLOCKS) pcg_amg_kernel(con
   }
 }
 
-template <int W>
+template <int W, int TPB>
 int max_blocks_t(int block) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_amg_kernel<W>, block, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_amg_kernel<W, TPB>, block, 0) != cudaSuccess) return 0;
   return sms * per;
 }
 
 }  // namespace
 
-int pcg_amg_max_blocks(int block) {
-  // the smallest co-resident count over the instantiations keeps every launch legal
-  int m = max_blocks_t<8>(block);
-  m = std::min(m, max_blocks_t<16>(block));
-  m = std::min(m, max_blocks_t<32>(block));
-  m = std::min(m, max_blocks_t<0>(block));
-  return m;
+int pcg_amg_max_blocks(int block, int tier) {
+  // the smallest co-resident count over the tier's instantiations keeps every launch legal
+  if (tier) return std::min(max_blocks_t<8, 512>(block), max_blocks_t<0, 512>(block));
+  return std::min(max_blocks_t<8, 1024>(block), max_blocks_t<0, 1024>(block));
 }
 
 cudaError_t launch_pcg_amg(const PcgLaunch& P, const AmgDev* M, int wmax, cudaStream_t st) {
@@ -186,17 +183,16 @@ cudaError_t launch_pcg_amg(const PcgLaunch& P, const AmgDev* M, int wmax, cudaSt
   cudaLaunchAttribute attr[1];
   PcgLaunch K;
   solver_launch_config(P, st, &cfg, attr, &K);
-  switch (wmax) {
-    case 8: return cudaLaunchKernelEx(&cfg, pcg_amg_kernel<8>, K, M);
-    case 16: return cudaLaunchKernelEx(&cfg, pcg_amg_kernel<16>, K, M);
-    case 32: return cudaLaunchKernelEx(&cfg, pcg_amg_kernel<32>, K, M);
-    default: return cudaLaunchKernelEx(&cfg, pcg_amg_kernel<0>, K, M);
-  }
+  if (K.tier)
+    return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_amg_kernel<8, 512>, K, M)
+                    : cudaLaunchKernelEx(&cfg, pcg_amg_kernel<0, 512>, K, M);
+  return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_amg_kernel<8, 1024>, K, M)
+                  : cudaLaunchKernelEx(&cfg, pcg_amg_kernel<0, 1024>, K, M);
 }
 
 bool amg_cluster_ok(int block, int size) {
-  return solver_cluster_ok(pcg_amg_kernel<8>, block, size) && solver_cluster_ok(pcg_amg_kernel<16>, block, size) &&
-         solver_cluster_ok(pcg_amg_kernel<32>, block, size) && solver_cluster_ok(pcg_amg_kernel<0>, block, size);
+  return solver_cluster_ok(pcg_amg_kernel<8, 1024>, block, size) &&
+         solver_cluster_ok(pcg_amg_kernel<0, 1024>, block, size);
 }
 
 }  // namespace bd

@@ -131,6 +131,7 @@ struct bd_state {
   unsigned long long* d_err = nullptr;
   double *Xbak = nullptr, *ubak = nullptr, *tbak = nullptr, *upbak = nullptr;
   int pcg_grid = 1, pcg_block = 512, pcg_max = 1;
+  int tier = 0;                            // solver register tier (kSolverTierBlock)
   int cluster = 0;                         // > 0: solvers run as one cluster of this many 1024-thread blocks
   std::vector<void*> allocs;
   std::string err;
@@ -303,7 +304,8 @@ PcgLaunch pcg_base(bd_state* s) {
   P.grid = s->pcg_grid;
   P.block = s->pcg_block;
   P.cluster = s->cluster;
-  if (s->cluster > 0) P.block = 1024;
+  P.tier = s->tier;
+  if (s->cluster > 0) P.block = kSolverTierBlock[0];
   P.gate = s->opts.sweep_tol > 0 ? s->gate : nullptr;
   return P;
 }
@@ -597,7 +599,7 @@ int setup_amg(bd_state* s, const HostOps& H) {
     if (!ok2) return fail(s, BD_ERR_OOM, "AMG upload failed");
     s->two_rhs = true;
   }
-  const int mx = pcg_amg_max_blocks(s->pcg_block);
+  const int mx = pcg_amg_max_blocks(s->pcg_block, s->tier);
   if (mx <= 0) return fail(s, BD_ERR_CUDA, "cannot size the cooperative AMG-CG grid");
   s->amg_grid = std::min(s->pcg_grid, mx);
   for (int v = 0; v < 2; ++v) {
@@ -1060,18 +1062,26 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     ok = alloc_n(s, &s->Xt[m], ns * NT) && alloc_n(s, &s->Xc[m], ns * NT) && alloc_n(s, &s->fq[m], ns * NT) &&
          alloc_n(s, &s->u[m], N);
   s->pcg_block = s->opts.cg_block > 0 ? s->opts.cg_block : 512;
-  if (s->pcg_block % 32 != 0 || s->pcg_block > 1024) {
+  if (s->pcg_block % 32 != 0 || s->pcg_block > kSolverTierBlock[0]) {
     release(s);
     delete s;
     return fail(nullptr, BD_ERR_ARG, "cg_block must be a multiple of 32 up to 1024");
   }
-  s->pcg_max = pcg_max_blocks(s->pcg_block, s->wmax);
+  const int64_t want = s->opts.cg_grid > 0 ? s->opts.cg_grid : (N + s->pcg_block - 1) / s->pcg_block;
+  // register tier: the 128-register solver build when every solver kernel of
+  // that build holds the whole grid co-resident (no cluster launches)
+  s->tier = 0;
+  if (s->opts.cg_cluster == 0 && s->pcg_block <= kSolverTierBlock[1]) {
+    int m1 = std::min(pcg_max_blocks(s->pcg_block, s->wmax, 1), pcg_amg_max_blocks(s->pcg_block, 1));
+    if (s->precision == BD_MIXED) m1 = std::min(m1, pcg_mixed_max_blocks(s->pcg_block, 1));
+    if (m1 >= want) s->tier = 1;
+  }
+  s->pcg_max = pcg_max_blocks(s->pcg_block, s->wmax, s->tier);
   if (ok && s->pcg_max <= 0) {
     release(s);
     delete s;
     return fail(nullptr, BD_ERR_CUDA, "cannot size the cooperative CG grid");
   }
-  const int64_t want = s->opts.cg_grid > 0 ? s->opts.cg_grid : (N + s->pcg_block - 1) / s->pcg_block;
   s->pcg_grid = int(std::max<int64_t>(1, std::min<int64_t>(want, s->pcg_max)));
   {
     const int cc = s->opts.cg_cluster;
@@ -1080,7 +1090,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
       delete s;
       return fail(nullptr, BD_ERR_ARG, "cg_cluster must be 0, 8 or 16");
     }
-    if (cc > 0) s->cluster = solver_cluster_size(1024, cc);
+    if (cc > 0) s->cluster = solver_cluster_size(kSolverTierBlock[0], cc);
   }
   if (ok) ok = alloc_n(s, &s->cg_part, int64_t(s->pcg_max) * 4);
   if (ok && s->opts.sweep_tol > 0)
@@ -1094,7 +1104,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
          (NT == N || alloc_n(s, &s->vfull2, N)) &&
          alloc_n(s, reinterpret_cast<char**>(&s->d_amgf2), int64_t(sizeof(AmgDevF))) &&
          alloc_n(s, &s->partf, int64_t(s->pcg_max) * 4);
-    const int mx = pcg_mixed_max_blocks(s->pcg_block);
+    const int mx = pcg_mixed_max_blocks(s->pcg_block, s->tier);
     if (ok && mx <= 0) ok = false;
     s->mixed_grid = std::min(s->pcg_grid, std::max(mx, 1));
   }

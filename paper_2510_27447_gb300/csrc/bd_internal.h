@@ -12,6 +12,11 @@ namespace bd {
 constexpr int kMaxStim = 32;
 constexpr int kMaxNodes = 3;          // Gauss-Lobatto nodes per step
 constexpr int kMaxNS = 19;
+// The persistent solver kernels are built twice, for two __launch_bounds__:
+// tier 0 allows 1024-thread blocks (64 registers a thread; two 512-thread
+// blocks share an SM), tier 1 allows 512-thread blocks (128 registers; one
+// block an SM).  Tier 1 serves problems whose rows fit one block per SM.
+constexpr int kSolverTierBlock[2] = {1024, 512};
 
 // device status word bits (one per bd_status_t failure kind)
 enum : int {
@@ -156,6 +161,7 @@ struct PcgLaunch {
   int block;
   int cluster;              // > 0: one thread-block cluster of this many blocks (grid = cluster),
                             // hardware cluster barriers; 0: cooperative grid, device-wide barriers
+  int tier;                 // register tier of the solver build launched (kSolverTierBlock)
 };
 // launch configuration of a persistent solver kernel: cooperative grid, or a
 // single cluster (then the kernel gets bar = nullptr)
@@ -170,7 +176,7 @@ bool mixed_cluster_ok(int block, int size);   // mixed.cu
 cudaError_t launch_pcg(const PcgLaunch& P, int wmax, cudaStream_t st);
 // a device-barrier wait that must run out (bd_selftest_wait_timeout)
 cudaError_t launch_wait_selftest(unsigned* bar, int* status, cudaStream_t st);
-int pcg_max_blocks(int block, int wmax);
+int pcg_max_blocks(int block, int wmax, int tier);
 cudaError_t launch_axpby_vals(int64_t nnz, double a, const double* X, double b, const double* Y, double* out,
                               cudaStream_t st);
 cudaError_t launch_copy(int64_t n, const double* src, double* dst, cudaStream_t st, const int* gate = nullptr);
@@ -246,7 +252,7 @@ using AmgDev = AmgDevT<double>;
 using AmgDevF = AmgDevT<float>;
 // M: device copy of the hierarchy descriptor (read through L1 by the level loops)
 cudaError_t launch_pcg_amg(const PcgLaunch& P, const AmgDev* M, int wmax, cudaStream_t st);
-int pcg_amg_max_blocks(int block);
+int pcg_amg_max_blocks(int block, int tier);
 
 // mixed precision (mixed.cu): FP64 right-hand side and outer residual, FP32
 // inner CG (Jacobi or the FP32 copy of the AMG hierarchy), x += d in FP64
@@ -267,7 +273,7 @@ struct MixedLaunch {
 };
 cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const AmgDevF* M, int wmax, cudaStream_t st,
                              float* partf);
-int pcg_mixed_max_blocks(int block);
+int pcg_mixed_max_blocks(int block, int tier);
 // two elliptic solves (right-hand sides c1 A_i va and c1 A_i va1) in one launch;
 // the MixedLaunch workspaces hold 2 n entries, H1 the second system's AMG
 // level vectors, partf8 / partd8 8 values per block

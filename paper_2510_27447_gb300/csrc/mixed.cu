@@ -25,8 +25,8 @@ namespace bd {
 
 namespace {
 
-template <int WMAX, bool AMG>
-__global__ void __launch_bounds__(1024, BD_SOLVER_MIN_BLOCKS) pcg_mixed_kernel(const __grid_constant__ PcgLaunch a,
+template <int WMAX, bool AMG, int TPB>
+__global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_mixed_kernel(const __grid_constant__ PcgLaunch a,
                                                              const __grid_constant__ MixedLaunch m,
                                                              const AmgDevF* __restrict__ Mp, float* partf) {
   __shared__ AmgDevF sM;    // descriptor staged in shared memory (see pcg_amg_kernel)
@@ -242,8 +242,8 @@ __global__ void __launch_bounds__(1024, BD_SOLVER_MIN_BLOCKS) pcg_mixed_kernel(c
 // refinement passes and convergence test; a converged one stops changing.
 // Workspace vectors of the second system sit n entries after the first's;
 // partd / partf hold 8 values per block.
-template <int WMAX>
-__global__ void __launch_bounds__(1024, BD_SOLVER_MIN_BLOCKS) pcg_mixed2_kernel(const __grid_constant__ PcgLaunch a,
+template <int WMAX, int TPB>
+__global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_mixed2_kernel(const __grid_constant__ PcgLaunch a,
                                                               const double* va1, double* x1,
                                                               const __grid_constant__ MixedLaunch m,
                                                               const AmgDevF* __restrict__ H0p,
@@ -502,23 +502,53 @@ __global__ void __launch_bounds__(1024, BD_SOLVER_MIN_BLOCKS) pcg_mixed2_kernel(
   }
 }
 
-template <int W>
+template <int W, int TPB>
 int max_blocks2_t(int block) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_mixed2_kernel<W>, block, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_mixed2_kernel<W, TPB>, block, 0) != cudaSuccess)
+    return 0;
   return sms * per;
 }
 
-template <int W, bool AMG>
+template <int W, bool AMG, int TPB>
 int max_blocks_t(int block) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_mixed_kernel<W, AMG>, block, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_mixed_kernel<W, AMG, TPB>, block, 0) != cudaSuccess)
     return 0;
   return sms * per;
+}
+
+template <int TPB>
+int tier_max_blocks(int block) {
+  int m = max_blocks_t<8, false, TPB>(block);
+  m = std::min(m, max_blocks_t<0, false, TPB>(block));
+  m = std::min(m, max_blocks_t<8, true, TPB>(block));
+  m = std::min(m, max_blocks_t<0, true, TPB>(block));
+  m = std::min(m, max_blocks2_t<8, TPB>(block));
+  m = std::min(m, max_blocks2_t<0, TPB>(block));
+  return m;
+}
+
+template <int TPB>
+cudaError_t launch_mixed_tier(const cudaLaunchConfig_t& cfg, const PcgLaunch& K, const MixedLaunch& X,
+                              const AmgDevF* M, int wmax, float* partf) {
+  if (X.use_amg)
+    return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<8, true, TPB>, K, X, M, partf)
+                    : cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<0, true, TPB>, K, X, M, partf);
+  return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<8, false, TPB>, K, X, M, partf)
+                  : cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<0, false, TPB>, K, X, M, partf);
+}
+
+template <int TPB>
+cudaError_t launch_mixed2_tier(const cudaLaunchConfig_t& cfg, const PcgLaunch& K, const double* va1, double* x1,
+                               const MixedLaunch& X, const AmgDevF* H0, const AmgDevF* H1, int wmax,
+                               float* partf8, double* partd8) {
+  return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<8, TPB>, K, va1, x1, X, H0, H1, partf8, partd8)
+                  : cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<0, TPB>, K, va1, x1, X, H0, H1, partf8, partd8);
 }
 
 __global__ void to_float_kernel(int64_t n, const double* src, float* dst) {
@@ -528,20 +558,10 @@ __global__ void to_float_kernel(int64_t n, const double* src, float* dst) {
 
 }  // namespace
 
-int pcg_mixed_max_blocks(int block) {
-  int m = max_blocks_t<8, false>(block);
-  m = std::min(m, max_blocks_t<16, false>(block));
-  m = std::min(m, max_blocks_t<32, false>(block));
-  m = std::min(m, max_blocks_t<0, false>(block));
-  m = std::min(m, max_blocks_t<8, true>(block));
-  m = std::min(m, max_blocks_t<16, true>(block));
-  m = std::min(m, max_blocks_t<32, true>(block));
-  m = std::min(m, max_blocks_t<0, true>(block));
-  m = std::min(m, max_blocks2_t<8>(block));
-  m = std::min(m, max_blocks2_t<16>(block));
-  m = std::min(m, max_blocks2_t<32>(block));
-  m = std::min(m, max_blocks2_t<0>(block));
-  return m;
+// sell_row's chunked loop serves every width bound (8, 16, 32) with the same
+// code, so one instantiation covers them; 0 (rows wider than 32) loops
+int pcg_mixed_max_blocks(int block, int tier) {
+  return tier ? tier_max_blocks<512>(block) : tier_max_blocks<1024>(block);
 }
 
 cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const AmgDevF* M, int wmax, cudaStream_t st,
@@ -550,20 +570,8 @@ cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const Amg
   cudaLaunchAttribute attr[1];
   PcgLaunch K;
   solver_launch_config(P, st, &cfg, attr, &K);
-  if (X.use_amg) {
-    switch (wmax) {
-      case 8: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<8, true>, K, X, M, partf);
-      case 16: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<16, true>, K, X, M, partf);
-      case 32: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<32, true>, K, X, M, partf);
-      default: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<0, true>, K, X, M, partf);
-    }
-  }
-  switch (wmax) {
-    case 8: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<8, false>, K, X, M, partf);
-    case 16: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<16, false>, K, X, M, partf);
-    case 32: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<32, false>, K, X, M, partf);
-    default: return cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<0, false>, K, X, M, partf);
-  }
+  return K.tier ? launch_mixed_tier<512>(cfg, K, X, M, wmax, partf)
+                : launch_mixed_tier<1024>(cfg, K, X, M, wmax, partf);
 }
 
 cudaError_t launch_pcg_mixed2(const PcgLaunch& P, const double* va1, double* x1, const MixedLaunch& X,
@@ -573,25 +581,18 @@ cudaError_t launch_pcg_mixed2(const PcgLaunch& P, const double* va1, double* x1,
   cudaLaunchAttribute attr[1];
   PcgLaunch K;
   solver_launch_config(P, st, &cfg, attr, &K);
-  switch (wmax) {
-    case 8: return cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<8>, K, va1, x1, X, H0, H1, partf8, partd8);
-    case 16: return cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<16>, K, va1, x1, X, H0, H1, partf8, partd8);
-    case 32: return cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<32>, K, va1, x1, X, H0, H1, partf8, partd8);
-    default: return cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<0>, K, va1, x1, X, H0, H1, partf8, partd8);
-  }
+  return K.tier ? launch_mixed2_tier<512>(cfg, K, va1, x1, X, H0, H1, wmax, partf8, partd8)
+                : launch_mixed2_tier<1024>(cfg, K, va1, x1, X, H0, H1, wmax, partf8, partd8);
 }
 
+// cluster launches use tier 0 (full-size blocks)
 bool mixed_cluster_ok(int block, int size) {
-  return solver_cluster_ok(pcg_mixed_kernel<8, true>, block, size) &&
-         solver_cluster_ok(pcg_mixed_kernel<16, true>, block, size) &&
-         solver_cluster_ok(pcg_mixed_kernel<32, true>, block, size) &&
-         solver_cluster_ok(pcg_mixed_kernel<0, true>, block, size) &&
-         solver_cluster_ok(pcg_mixed_kernel<8, false>, block, size) &&
-         solver_cluster_ok(pcg_mixed_kernel<16, false>, block, size) &&
-         solver_cluster_ok(pcg_mixed_kernel<32, false>, block, size) &&
-         solver_cluster_ok(pcg_mixed_kernel<0, false>, block, size) &&
-         solver_cluster_ok(pcg_mixed2_kernel<8>, block, size) && solver_cluster_ok(pcg_mixed2_kernel<16>, block, size) &&
-         solver_cluster_ok(pcg_mixed2_kernel<32>, block, size) && solver_cluster_ok(pcg_mixed2_kernel<0>, block, size);
+  return solver_cluster_ok(pcg_mixed_kernel<8, true, 1024>, block, size) &&
+         solver_cluster_ok(pcg_mixed_kernel<0, true, 1024>, block, size) &&
+         solver_cluster_ok(pcg_mixed_kernel<8, false, 1024>, block, size) &&
+         solver_cluster_ok(pcg_mixed_kernel<0, false, 1024>, block, size) &&
+         solver_cluster_ok(pcg_mixed2_kernel<8, 1024>, block, size) &&
+         solver_cluster_ok(pcg_mixed2_kernel<0, 1024>, block, size);
 }
 
 cudaError_t launch_to_float(int64_t n, const double* src, float* dst, cudaStream_t st) {

@@ -29,8 +29,8 @@ namespace bd {
 
 namespace {
 
-template <int WMAX>
-__global__ void __launch_bounds__(1024, BD_SOLVER_MIN_BLOCKS) pcg_kernel(const __grid_constant__ PcgLaunch a) {
+template <int WMAX, int TPB>
+__global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_kernel(const __grid_constant__ PcgLaunch a) {
   __shared__ double sh[4][32];
   if (a.gate && *a.gate == 0) return;   // same value for every block: all skip together
   const int n = a.n;
@@ -188,12 +188,12 @@ __global__ void copy_kernel(int64_t n, const double* src, double* dst, const int
 }  // namespace
 
 namespace {
-template <int W>
+template <int W, int TPB>
 int max_blocks_t(int block) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_kernel<W>, block, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_kernel<W, TPB>, block, 0) != cudaSuccess) return 0;
   return sms * per;
 }
 }  // namespace
@@ -207,18 +207,16 @@ cudaError_t launch_wait_selftest(unsigned* bar, int* status, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// cluster launches use tier 0 (full-size blocks)
 bool pcg_cluster_ok(int block, int size) {
-  return solver_cluster_ok(pcg_kernel<8>, block, size) && solver_cluster_ok(pcg_kernel<16>, block, size) &&
-         solver_cluster_ok(pcg_kernel<32>, block, size) && solver_cluster_ok(pcg_kernel<0>, block, size);
+  return solver_cluster_ok(pcg_kernel<8, 1024>, block, size) && solver_cluster_ok(pcg_kernel<0, 1024>, block, size);
 }
 
-int pcg_max_blocks(int block, int wmax) {
-  switch (wmax) {
-    case 8: return max_blocks_t<8>(block);
-    case 16: return max_blocks_t<16>(block);
-    case 32: return max_blocks_t<32>(block);
-    default: return max_blocks_t<0>(block);
-  }
+// sell_row's chunked loop serves every width bound (8, 16, 32) with the same
+// code, so one instantiation covers them; 0 (rows wider than 32) loops
+int pcg_max_blocks(int block, int wmax, int tier) {
+  if (tier) return wmax > 0 ? max_blocks_t<8, 512>(block) : max_blocks_t<0, 512>(block);
+  return wmax > 0 ? max_blocks_t<8, 1024>(block) : max_blocks_t<0, 1024>(block);
 }
 
 void solver_launch_config(const PcgLaunch& P, cudaStream_t st, cudaLaunchConfig_t* cfg, cudaLaunchAttribute* attr,
@@ -238,6 +236,7 @@ void solver_launch_config(const PcgLaunch& P, cudaStream_t st, cudaLaunchConfig_
     attr[0].val.clusterDim.z = 1;
     Pk->bar = nullptr;
     Pk->grid = P.cluster;
+    Pk->tier = 0;
   } else {
     cfg->gridDim = dim3(unsigned(P.grid));
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -250,12 +249,10 @@ cudaError_t launch_pcg(const PcgLaunch& P, int wmax, cudaStream_t st) {
   cudaLaunchAttribute attr[1];
   PcgLaunch K;
   solver_launch_config(P, st, &cfg, attr, &K);
-  switch (wmax) {
-    case 8: return cudaLaunchKernelEx(&cfg, pcg_kernel<8>, K);
-    case 16: return cudaLaunchKernelEx(&cfg, pcg_kernel<16>, K);
-    case 32: return cudaLaunchKernelEx(&cfg, pcg_kernel<32>, K);
-    default: return cudaLaunchKernelEx(&cfg, pcg_kernel<0>, K);
-  }
+  if (K.tier)
+    return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_kernel<8, 512>, K) : cudaLaunchKernelEx(&cfg, pcg_kernel<0, 512>, K);
+  return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_kernel<8, 1024>, K)
+                  : cudaLaunchKernelEx(&cfg, pcg_kernel<0, 1024>, K);
 }
 
 cudaError_t launch_axpby_vals(int64_t n, double a, const double* X, double b, const double* Y, double* out,
