@@ -114,7 +114,9 @@ typedef struct {
   int amg_coarse_max;    /* rows of the dense coarsest AMG level (0 = default 1500) */
   int cg_block;          /* CG threads per block (0 = auto: 512) */
   int cg_grid;           /* CG blocks (0 = auto: one per cg_block rows, at most the co-resident maximum) */
-  /* device memory hooks (NULL => cudaMalloc/cudaFree); ctx is passed back */
+  /* device memory hooks (NULL => cudaMalloc/cudaFree); ctx is passed back.  Blocks
+     must be 16-byte aligned (kernels use vector loads); a misaligned block is
+     handed back to free() and counts as a failed allocation (BD_ERR_OOM). */
   void* (*alloc)(size_t bytes, void* ctx);
   void (*free)(void* ptr, void* ctx);
   void* alloc_ctx;

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_amg_kernel(cons
     a.r[i] = r;
     rr_loc += r * r;
   }
-  if (!vcycle<double>(M, a.r, a.z, a.bar, nb, a.status)) return;
+  if (!vcycle<double, TPB == 512>(M, a.r, a.z, a.bar, nb, a.status)) return;
   double acc1[2] = {0.0, rr_loc};
   for (int i = i0; i < n; i += stride) acc1[0] += a.r[i] * a.z[i];
   block_sum<2>(acc1, sh);
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_amg_kernel(cons
       a.r[i] = r;
       rrl += r * r;
     }
-    if (!vcycle<double>(M, a.r, a.z, a.bar, nb, a.status)) return;
+    if (!vcycle<double, TPB == 512>(M, a.r, a.z, a.bar, nb, a.status)) return;
     double acc[2] = {0.0, rrl};
     for (int i = i0; i < n; i += stride) acc[0] += a.r[i] * a.z[i];
     block_sum<2>(acc, sh);

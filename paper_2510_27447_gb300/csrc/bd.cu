@@ -172,6 +172,10 @@ void* dalloc(bd_state* s, size_t bytes) {
   bytes = (bytes + 255) & ~size_t(255);
   if (s->opts.alloc) {
     p = s->opts.alloc(bytes, s->opts.alloc_ctx);
+    if (p && (reinterpret_cast<uintptr_t>(p) & 15u) != 0) {   // vector loads need 16-byte alignment
+      if (s->opts.free) s->opts.free(p, s->opts.alloc_ctx);
+      p = nullptr;
+    }
   } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();
     p = nullptr;
@@ -543,8 +547,15 @@ int setup_amg(bd_state* s, const HostOps& H) {
     if (l > 0) ok = ok && alloc_n(s, &Ld.b, n) && alloc_n(s, &Ld.y, n);
     if (!ok || cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, BD_ERR_OOM, "AMG upload failed");
   }
-  M.nc = int(AH.nc);
-  M.cinv = static_cast<const double*>(upload(AH.cinv.data(), AH.cinv.size() * 8));
+  // the dense coarse inverse with rows padded to a multiple of 4 entries, so
+  // that every row starts on a 16-byte boundary (vector loads)
+  const int64_t ncr = AH.nc, ldc = (ncr + 3) & ~int64_t(3);
+  std::vector<double> cpad(size_t(ncr * ldc), 0.0);
+  for (int64_t i = 0; i < ncr; ++i)
+    std::copy(AH.cinv.begin() + i * ncr, AH.cinv.begin() + (i + 1) * ncr, cpad.begin() + i * ldc);
+  M.nc = int(ncr);
+  M.ldc = int(ldc);
+  M.cinv = static_cast<const double*>(upload(cpad.data(), cpad.size() * 8));
   if (!M.cinv || !alloc_n(s, &M.bc, AH.nc) || !alloc_n(s, &M.xc, AH.nc) ||
       cudaStreamSynchronize(s->stream) != cudaSuccess)
     return fail(s, BD_ERR_OOM, "AMG upload failed");
@@ -580,8 +591,9 @@ int setup_amg(bd_state* s, const HostOps& H) {
       if (l > 0) ok = ok && alloc_n(s, &Ld.b, n) && alloc_n(s, &Ld.y, n);
       if (!ok || cudaStreamSynchronize(s->stream) != cudaSuccess) return fail(s, BD_ERR_OOM, "AMG upload failed");
     }
-    std::vector<float> fci(AH.cinv.begin(), AH.cinv.end());
-    F.nc = int(AH.nc);
+    std::vector<float> fci(cpad.begin(), cpad.end());
+    F.nc = int(ncr);
+    F.ldc = int(ldc);
     F.cinv = static_cast<const float*>(upload(fci.data(), fci.size() * 4));
     if (!F.cinv || !alloc_n(s, &F.bc, AH.nc) || !alloc_n(s, &F.xc, AH.nc) ||
         cudaStreamSynchronize(s->stream) != cudaSuccess)

@@ -242,6 +242,7 @@ struct AmgDevT {
   int nlev;                        // smoothed levels
   AmgLevelDevT<T> L[kMaxAmgLevels];
   int nc;
+  int ldc;                         // row stride of cinv: nc rounded up to 4 (zero padded)
   const T* cinv;
   T* bc;
   T* xc;

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_mixed_kernel(co
       m.d32[i] = 0.0f;
     }
     if constexpr (AMG) {
-      if (!vcycle<float>(M, m.r32, m.z32, a.bar, nb, a.status)) return;
+      if (!vcycle<float, TPB == 512>(M, m.r32, m.z32, a.bar, nb, a.status)) return;
     } else {
       for (int i = i0; i < n; i += stride) m.z32[i] = m.invd32[i] * m.r32[i];
     }
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_mixed_kernel(co
         rrl += r * r;
       }
       if constexpr (AMG) {
-        if (!vcycle<float>(M, m.r32, m.z32, a.bar, nb, a.status)) return;
+        if (!vcycle<float, TPB == 512>(M, m.r32, m.z32, a.bar, nb, a.status)) return;
       } else {
         for (int i = i0; i < n; i += stride) m.z32[i] = m.invd32[i] * m.r32[i];
       }
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_mixed2_kernel(c
         d32[k][i] = 0.0f;
       }
     }
-    if (!vcycle2<float>(H0, H1, r32[0], r32[1], z32[0], z32[1], a.bar, nb, a.status)) return;
+    if (!vcycle2<float, TPB == 512>(H0, H1, r32[0], r32[1], z32[0], z32[1], a.bar, nb, a.status)) return;
     float accf[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     for (int i = i0; i < n; i += stride) {
 #pragma unroll
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_mixed2_kernel(c
           rrl[k] += r * r;
         }
       }
-      if (!vcycle2<float>(H0, H1, r32[0], r32[1], z32[0], z32[1], a.bar, nb, a.status)) return;
+      if (!vcycle2<float, TPB == 512>(H0, H1, r32[0], r32[1], z32[0], z32[1], a.bar, nb, a.status)) return;
       float acc[4] = {0.0f, rrl[0], 0.0f, rrl[1]};
       for (int i = i0; i < n; i += stride) {
         acc[0] += r32[0][i] * z32[0][i];

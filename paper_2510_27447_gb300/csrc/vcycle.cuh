@@ -2,13 +2,15 @@
 // generic in the value type (FP64 for the FP64 path, FP32 for the inner
 // solves of the mixed path).  See amg.cu for the cycle's definition.
 #pragma once
+#include <type_traits>
+
 #include "bd_internal.h"
 #include "sparse.cuh"
 
 namespace bd {
 
 // row i of a SELL operator against x read through L2 (sell_row processes any
-// width in chunks of eight, so one instantiation serves every level)
+// width in chunks, so one instantiation serves every level)
 template <class T>
 __device__ __forceinline__ T sdot(const SellDevT<T>& M, const T* x, int i) {
   return sell_row<8, true, T>(M.sptr, M.sw, M.col, M.val, x, i);
@@ -95,14 +97,92 @@ __device__ __forceinline__ void apply_rows_2v(const SellDevT<T>& M, const T* x0,
   }
 }
 
+// capacity (elements) of the shared-memory copy of the coarse right-hand sides
+constexpr int kCoarseStage = 1536;
+
+__device__ __forceinline__ float dot_vec(const float4& c, const float* b) {
+  return c.x * b[0] + c.y * b[1] + c.z * b[2] + c.w * b[3];
+}
+__device__ __forceinline__ double dot_vec(const double2& c, const double* b) { return c.x * b[0] + c.y * b[1]; }
+
+// Dense coarsest solve xc_k = Cinv bc_k (k < NV), one warp per row, the lanes
+// splitting the dot product and a butterfly sum giving the row's value.  When
+// a padded row fits kCoarseStage, every block that owns rows first copies the
+// right-hand sides into shared memory (one round trip for all of them) and the
+// warps read their rows as 16-byte vectors, up to B vectors a lane in flight
+// at once; the rows are zero padded to ldc (a multiple of 4 entries, so every
+// row starts 16-byte aligned).  Wider coarse operators take a lane-strided
+// loop over global memory.  bc is read through L2 (written by other blocks).
+template <class T, int NV>
+__device__ __forceinline__ void coarse_solve(const T* cinv, int nc, int ldc, const T* const (&bc)[NV],
+                                             T* const (&xc)[NV]) {
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int E = 16 / int(sizeof(T));           // entries per vector
+  constexpr int B = sizeof(T) == 4 ? 4 : 2;        // vectors per lane per batch (4 measured best)
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int warp = blockIdx.x * wpb + (threadIdx.x >> 5);
+  const int nwarps = gridDim.x * wpb;
+  __shared__ __align__(16) T sbc[NV][kCoarseStage];
+  if (ldc <= kCoarseStage) {
+    if (blockIdx.x * wpb >= nc) return;             // block-uniform: no rows here
+    for (int j = threadIdx.x; j < ldc; j += blockDim.x)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sbc[k][j] = j < nc ? __ldcg(bc[k] + j) : T(0);
+    __syncthreads();
+    const int nvec = ldc / E;
+    for (int i = warp; i < nc; i += nwarps) {
+      const V* row = reinterpret_cast<const V*>(cinv + int64_t(i) * ldc);
+      T s[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s[k] = T(0);
+      for (int q0 = lane; q0 < nvec; q0 += 32 * B) {
+        V c[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+          if (q0 + 32 * u < nvec) c[u] = __ldg(row + q0 + 32 * u);
+#pragma unroll
+        for (int u = 0; u < B; ++u)
+          if (q0 + 32 * u < nvec)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) s[k] += dot_vec(c[u], &sbc[k][(q0 + 32 * u) * E]);
+      }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+        if (lane == 0) xc[k][i] = s[k];
+      }
+    }
+  } else {
+    for (int i = warp; i < nc; i += nwarps) {
+      const T* row = cinv + int64_t(i) * ldc;
+      T s[NV];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s[k] = T(0);
+      for (int j = lane; j < nc; j += 32) {
+        const T c = row[j];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) s[k] += c * __ldcg(bc[k] + j);
+      }
+#pragma unroll
+      for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+        if (lane == 0) xc[k][i] = s[k];
+      }
+    }
+  }
+}
+
 // Two V(1,1) cycles at once (z_k = V(r_k), k = 0, 1) sharing every device
 // barrier and every pass over the operators.  H0 carries the operators and the
 // level vectors of the first right-hand side, H1 the level vectors of the
-// second (its operators are not read).  Each z_k is the cycle vcycle() below
+// second (its operators are not read).  Each z_k is the cycle vcycle_body() below
 // computes for r_k, with the same order of every sum.
 template <class T>
-__device__ bool vcycle2(const AmgDevT<T>& H0, const AmgDevT<T>& H1, const T* r0, const T* r1, T* z0, T* z1,
-                        unsigned* bar, int nb, int* status) {
+__device__ __forceinline__ bool vcycle2_body(const AmgDevT<T>& H0, const AmgDevT<T>& H1, const T* r0, const T* r1,
+                                             T* z0, T* z1, unsigned* bar, int nb, int* status) {
   const int stride = blockDim.x * gridDim.x;
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
   const int L = H0.nlev;
@@ -141,27 +221,9 @@ __device__ bool vcycle2(const AmgDevT<T>& H0, const AmgDevT<T>& H1, const T* r0,
   }
   if (!grid_barrier(bar, nb, status)) return false;
   {
-    const int lane = threadIdx.x & 31;
-    const int warp = i0 >> 5;
-    const int nwarps = stride >> 5;
-    for (int i = warp; i < H0.nc; i += nwarps) {
-      const T* row = H0.cinv + int64_t(i) * H0.nc;
-      T a = T(0), b = T(0);
-      for (int j = lane; j < H0.nc; j += 32) {
-        const T c = row[j];
-        a += c * __ldcg(H0.bc + j);
-        b += c * __ldcg(H1.bc + j);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-      }
-      if (lane == 0) {
-        H0.xc[i] = a;
-        H1.xc[i] = b;
-      }
-    }
+    const T* bcs[2] = {H0.bc, H1.bc};
+    T* xcs[2] = {H0.xc, H1.xc};
+    coarse_solve<T, 2>(H0.cinv, H0.nc, H0.ldc, bcs, xcs);
   }
   for (int l = L - 1; l >= 0; --l) {
     const AmgLevelDevT<T>& Lv = H0.L[l];
@@ -188,7 +250,8 @@ __device__ bool vcycle2(const AmgDevT<T>& H0, const AmgDevT<T>& H1, const T* r0,
 
 // z = V(rin); returns false if a barrier gave up
 template <class T>
-__device__ bool vcycle(const AmgDevT<T>& M, const T* rin, T* zout, unsigned* bar, int nb, int* status) {
+__device__ __forceinline__ bool vcycle_body(const AmgDevT<T>& M, const T* rin, T* zout, unsigned* bar, int nb,
+                                            int* status) {
   const int stride = blockDim.x * gridDim.x;
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
   const int L = M.nlev;
@@ -211,18 +274,9 @@ __device__ bool vcycle(const AmgDevT<T>& M, const T* rin, T* zout, unsigned* bar
   }
   if (!grid_barrier(bar, nb, status)) return false;
   {
-    // dense coarse solve, one warp per row (lanes split the dot product)
-    const int lane = threadIdx.x & 31;
-    const int warp = i0 >> 5;
-    const int nwarps = stride >> 5;
-    for (int i = warp; i < M.nc; i += nwarps) {
-      const T* row = M.cinv + int64_t(i) * M.nc;
-      T s = T(0);
-      for (int j = lane; j < M.nc; j += 32) s += row[j] * __ldcg(M.bc + j);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) M.xc[i] = s;
-    }
+    const T* bcs[1] = {M.bc};
+    T* xcs[1] = {M.xc};
+    coarse_solve<T, 1>(M.cinv, M.nc, M.ldc, bcs, xcs);
   }
   for (int l = L - 1; l >= 0; --l) {
     const AmgLevelDevT<T>& Lv = M.L[l];
@@ -237,6 +291,34 @@ __device__ bool vcycle(const AmgDevT<T>& M, const T* rin, T* zout, unsigned* bar
     });
   }
   return true;
+}
+
+// The cycles as calls: a called cycle gets the whole register budget of the
+// thread for itself, where an inlined one shares it with the Krylov loop
+// around it.  Measured on GB300, the call pays in the 128-register solver
+// build (mixed TP06 257^2 sheet: elliptic 1.99 -> 1.88 ms per step) and
+// costs a little in the 64-register build, so kernels choose with CALL.
+template <class T>
+__device__ __noinline__ bool vcycle_call(const AmgDevT<T>& M, const T* rin, T* zout, unsigned* bar, int nb,
+                                         int* status) {
+  return vcycle_body<T>(M, rin, zout, bar, nb, status);
+}
+template <class T>
+__device__ __noinline__ bool vcycle2_call(const AmgDevT<T>& H0, const AmgDevT<T>& H1, const T* r0, const T* r1,
+                                          T* z0, T* z1, unsigned* bar, int nb, int* status) {
+  return vcycle2_body<T>(H0, H1, r0, r1, z0, z1, bar, nb, status);
+}
+template <class T, bool CALL>
+__device__ __forceinline__ bool vcycle(const AmgDevT<T>& M, const T* rin, T* zout, unsigned* bar, int nb,
+                                       int* status) {
+  if constexpr (CALL) return vcycle_call<T>(M, rin, zout, bar, nb, status);
+  else return vcycle_body<T>(M, rin, zout, bar, nb, status);
+}
+template <class T, bool CALL>
+__device__ __forceinline__ bool vcycle2(const AmgDevT<T>& H0, const AmgDevT<T>& H1, const T* r0, const T* r1, T* z0,
+                                        T* z1, unsigned* bar, int nb, int* status) {
+  if constexpr (CALL) return vcycle2_call<T>(H0, H1, r0, r1, z0, z1, bar, nb, status);
+  else return vcycle2_body<T>(H0, H1, r0, r1, z0, z1, bar, nb, status);
 }
 
 }  // namespace bd
