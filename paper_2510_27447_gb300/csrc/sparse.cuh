@@ -17,7 +17,7 @@ namespace bd {
 #define BD_SOLVER_MIN_BLOCKS 1
 #endif
 #ifndef BD_SELL_CHUNK
-#define BD_SELL_CHUNK 4
+#define BD_SELL_CHUNK 2
 #endif
 // bounded waits: a device-barrier wait gives up after kWaitLimitNs of device
 // time (%globaltimer), with an iteration cap as a backstop
@@ -179,8 +179,9 @@ __device__ __forceinline__ T sell_row(const int64_t* __restrict__ sptr, const in
   T acc = T(0);
   if constexpr (WMAX > 0) {
     // chunks of BD_SELL_CHUNK entries: all loads of a chunk in flight at
-    // once, without holding a whole 32-wide row in registers (4 measured
-    // best on GB300 against 8 and against whole-row unrolling)
+    // once, without holding a whole 32-wide row in registers.  Measured on
+    // GB300 (TP06 257^2 sheet, 101x101x26 slab, LV shell), 2 beats 3, 4, 6
+    // and 8: the solver kernels are register-bound, and longer chunks spill.
     constexpr int CH = BD_SELL_CHUNK;
     for (int k0 = 0; k0 < w; k0 += CH) {
       int c[CH];

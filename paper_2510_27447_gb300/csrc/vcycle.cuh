@@ -16,14 +16,86 @@ __device__ __forceinline__ T sdot(const SellDevT<T>& M, const T* x, int i) {
   return sell_row<8, true, T>(M.sptr, M.sw, M.col, M.val, x, i);
 }
 
+// Lanes that share one row of a SELL operator: operators with few rows
+// (coarse levels) spread each row over g lanes (a power of two, at most half
+// the row-width bound) while the grid has threads for g lanes a row, so that
+// fewer dependent load rounds sit in each lane's part of the row.
+template <class T>
+__device__ __forceinline__ int lanes_per_row(const SellDevT<T>& M, int stride) {
+  int g = 1;
+  while (g < 32 && int64_t(M.n) * (2 * g) <= int64_t(stride) && 2 * g <= M.wmax) g *= 2;
+  return g;
+}
+
+// lane sub's part of row i (entries k = sub, sub + g, ...; in k order)
+template <class T, int NV>
+__device__ __forceinline__ void sell_row_part(const SellDevT<T>& M, const T* const (&x)[NV], int i, int sub, int g,
+                                              T (&acc)[NV]) {
+  const int s = i >> 5;
+  const int64_t base = M.sptr[s] + (i & 31);
+  const int w = M.sw[s];
+  constexpr int CH = BD_SELL_CHUNK;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = T(0);
+  for (int k0 = sub; k0 < w; k0 += g * CH) {
+    int c[CH];
+    T v[CH], gx[NV][CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k)
+      if (k0 + g * k < w) {
+        c[k] = M.col[base + 32 * (k0 + g * k)];
+        v[k] = M.val[base + 32 * (k0 + g * k)];
+      }
+#pragma unroll
+    for (int k = 0; k < CH; ++k)
+      if (k0 + g * k < w)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) gx[q][k] = __ldcg(x[q] + c[k]);
+#pragma unroll
+    for (int k = 0; k < CH; ++k)
+      if (k0 + g * k < w)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] += v[k] * gx[q][k];
+  }
+}
+
+// Rows of a SELL operator with g > 1 lanes a row: warp w takes rows
+// [w 32/g, (w+1) 32/g) of every round (the loop is warp-uniform, so every
+// lane reaches the shuffles), a butterfly over the row's lanes gives the sum
+// and the row's first lane runs epi(i, sums).
+template <class T, int NV, class F>
+__device__ __forceinline__ void apply_rows_spread(const SellDevT<T>& M, const T* const (&x)[NV], int g, int i0,
+                                                  int stride, F&& epi) {
+  const int lane = threadIdx.x & 31;
+  const int rpw = 32 / g;
+  const int sub = lane & (g - 1);
+  for (int r0 = (i0 >> 5) * rpw; r0 < M.n; r0 += (stride >> 5) * rpw) {
+    const int i = r0 + lane / g;
+    T acc[NV];
+    if (i < M.n) {
+      sell_row_part<T, NV>(M, x, i, sub, g, acc);
+    } else {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) acc[q] = T(0);
+    }
+    for (int o = g >> 1; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (sub == 0 && i < M.n) epi(i, acc);
+  }
+}
+
 // For every row i of M: epi(i, (M x)_i).  SELL operators use one thread per
-// row; CSR operators (long rows) one warp per row, the lanes reading the
-// row's contiguous entries and a butterfly reduction giving every lane the
-// same sum (deterministic); lane 0 runs the epilogue.  x and every vector an
-// epilogue reads may have been written by other threads in earlier phases,
-// so they are read through L2.
+// row, or g lanes per row (lanes_per_row) where `spread` allows it; CSR
+// operators (long rows) one warp per row, the lanes reading the row's
+// contiguous entries and a butterfly reduction giving every lane the same sum
+// (deterministic); lane 0 runs the epilogue.  x and every vector an epilogue
+// reads may have been written by other threads in earlier phases, so they are
+// read through L2.  `spread` is false for operators whose output the Krylov
+// loop reads back row by row without a barrier (the finest level's A).
 template <class T, class F>
-__device__ __forceinline__ void apply_rows(const SellDevT<T>& M, const T* x, int i0, int stride, F&& epi) {
+__device__ __forceinline__ void apply_rows(const SellDevT<T>& M, const T* x, int i0, int stride, F&& epi,
+                                           bool spread = true) {
   if (M.rp) {
     const int lane = threadIdx.x & 31;
     for (int i = i0 >> 5; i < M.n; i += stride >> 5) {
@@ -35,7 +107,13 @@ __device__ __forceinline__ void apply_rows(const SellDevT<T>& M, const T* x, int
       if (lane == 0) epi(i, s);
     }
   } else {
-    for (int i = i0; i < M.n; i += stride) epi(i, sdot<T>(M, x, i));
+    const int g = spread ? lanes_per_row(M, stride) : 1;
+    if (g == 1) {
+      for (int i = i0; i < M.n; i += stride) epi(i, sdot<T>(M, x, i));
+    } else {
+      const T* xs[1] = {x};
+      apply_rows_spread<T, 1>(M, xs, g, i0, stride, [&](int i, const T (&a)[1]) { epi(i, a[0]); });
+    }
   }
 }
 
@@ -44,7 +122,7 @@ __device__ __forceinline__ void apply_rows(const SellDevT<T>& M, const T* x, int
 // same order as sell_row's
 template <class T, class F>
 __device__ __forceinline__ void apply_rows_2v(const SellDevT<T>& M, const T* x0, const T* x1, int i0, int stride,
-                                              F&& epi) {
+                                              F&& epi, bool spread = true) {
   if (M.rp) {
     const int lane = threadIdx.x & 31;
     for (int i = i0 >> 5; i < M.n; i += stride >> 5) {
@@ -63,6 +141,9 @@ __device__ __forceinline__ void apply_rows_2v(const SellDevT<T>& M, const T* x0,
       }
       if (lane == 0) epi(i, a, b);
     }
+  } else if (const int g = spread ? lanes_per_row(M, stride) : 1; g > 1) {
+    const T* xs[2] = {x0, x1};
+    apply_rows_spread<T, 2>(M, xs, g, i0, stride, [&](int i, const T (&a)[2]) { epi(i, a[0], a[1]); });
   } else {
     constexpr int CH = BD_SELL_CHUNK;
     for (int i = i0; i < M.n; i += stride) {
@@ -204,7 +285,7 @@ __device__ __forceinline__ bool vcycle2_body(const AmgDevT<T>& H0, const AmgDevT
     apply_rows_2v(Lv.A, Lv.x, Lw.x, i0, stride, [&](int i, T da, T db) {
       Lv.r[i] = __ldcg(ba + i) - da;
       Lw.r[i] = __ldcg(bb + i) - db;
-    });
+    }, l > 0);
     if (!grid_barrier(bar, nb, status)) return false;
     const bool last = l + 1 == L;
     T* na = last ? H0.bc : H0.L[l + 1].b;
@@ -243,7 +324,7 @@ __device__ __forceinline__ bool vcycle2_body(const AmgDevT<T>& H0, const AmgDevT
     apply_rows_2v(Lv.A, Lv.x, Lw.x, i0, stride, [&](int i, T da, T db) {
       ya[i] = __ldcg(Lv.x + i) + Lv.omega * Lv.invd[i] * (__ldcg(ba + i) - da);
       yb[i] = __ldcg(Lw.x + i) + Lv.omega * Lv.invd[i] * (__ldcg(bb + i) - db);
-    });
+    }, l > 0);
   }
   return true;
 }
@@ -263,7 +344,7 @@ __device__ __forceinline__ bool vcycle_body(const AmgDevT<T>& M, const T* rin, T
     const AmgLevelDevT<T>& Lv = M.L[l];
     const T* b = l == 0 ? rin : Lv.b;
     if (!grid_barrier(bar, nb, status)) return false;
-    apply_rows(Lv.A, Lv.x, i0, stride, [&](int i, T d) { Lv.r[i] = __ldcg(b + i) - d; });
+    apply_rows(Lv.A, Lv.x, i0, stride, [&](int i, T d) { Lv.r[i] = __ldcg(b + i) - d; }, l > 0);
     if (!grid_barrier(bar, nb, status)) return false;
     const bool last = l + 1 == L;
     T* nb_rhs = last ? M.bc : M.L[l + 1].b;
@@ -288,7 +369,7 @@ __device__ __forceinline__ bool vcycle_body(const AmgDevT<T>& M, const T* rin, T
     T* y = l == 0 ? zout : Lv.y;
     apply_rows(Lv.A, Lv.x, i0, stride, [&](int i, T d) {
       y[i] = __ldcg(Lv.x + i) + Lv.omega * Lv.invd[i] * (__ldcg(b + i) - d);
-    });
+    }, l > 0);
   }
   return true;
 }
