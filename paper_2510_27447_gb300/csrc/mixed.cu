@@ -41,7 +41,10 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_mixed_kernel(co
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
 
   // ---- FP64 right-hand side, FP32 Jacobi scaling ---------------------------
-  double acc0[2] = {0.0, 0.0};
+  // Without mean projection the first outer residual is final here and is
+  // formed in the same pass (one device barrier fewer).
+  const bool fused = !a.project;
+  double acc0[3] = {0.0, 0.0, 0.0};
   for (int i = i0; i < n; i += stride) {
     double b = a.rl ? a.rl[i] : 0.0;
     if (a.val1) b += a.c1 * sell_row<WMAX, false>(a, a.val1, a.va, i);
@@ -52,17 +55,31 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_mixed_kernel(co
     m.invd32[i] = float(1.0 / d);
     acc0[0] += b;
     acc0[1] += b * b;
+    if (fused) {
+      double r = b;
+      if (a.warm) r = b - ((a.dextra ? a.dextra[i] * a.x[i] : 0.0) + sell_row<WMAX, true>(a, a.valA, a.x, i));
+      m.r64[i] = r;
+      acc0[2] += r * r;
+    }
   }
   if (!a.warm)
     for (int i = i0; i < n; i += stride) a.x[i] = 0.0;
-  block_sum<2, double>(acc0, shd);
+  block_sum<3, double>(acc0, shd);
   if (threadIdx.x == 0) {
     a.part[blockIdx.x * 4 + 0] = acc0[0];
     a.part[blockIdx.x * 4 + 1] = acc0[1];
+    a.part[blockIdx.x * 4 + 2] = acc0[2];
   }
   if (!grid_barrier(a.bar, nb, a.status)) return;
-  double tot[2];
-  grid_total<2, double>(a.part, {0, 1}, nb, tot, shd);
+  double tot[3] = {0.0, 0.0, 0.0};
+  if (fused) {
+    grid_total<3, double>(a.part, {0, 1, 2}, nb, tot, shd);
+  } else {
+    double t01[2];
+    grid_total<2, double>(a.part, {0, 1}, nb, t01, shd);
+    tot[0] = t01[0];
+    tot[1] = t01[1];
+  }
   const double mean_b = a.project ? tot[0] / double(n) : 0.0;
   double bb = a.project ? tot[1] - double(n) * mean_b * mean_b : tot[1];
   if (bb < 0.0) bb = 0.0;
@@ -76,27 +93,30 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_mixed_kernel(co
   for (int outer = 0;; ++outer) {
     ++outer_total;
     // ---- FP64 outer residual ---------------------------------------------
-    double accr[1] = {0.0};
-    if (outer == 0 && !a.warm) {
-      for (int i = i0; i < n; i += stride) {
-        const double r = m.b64[i];
-        m.r64[i] = r;
-        accr[0] += r * r;
+    double rr64 = tot[2];   // the first pass of a fused start has it already
+    if (!(outer == 0 && fused)) {
+      double accr[1] = {0.0};
+      if (outer == 0 && !a.warm) {
+        for (int i = i0; i < n; i += stride) {
+          const double r = m.b64[i];
+          m.r64[i] = r;
+          accr[0] += r * r;
+        }
+      } else {
+        for (int i = i0; i < n; i += stride) {
+          const double ax = (a.dextra ? a.dextra[i] * a.x[i] : 0.0) + sell_row<WMAX, true>(a, a.valA, a.x, i);
+          const double r = m.b64[i] - ax;
+          m.r64[i] = r;
+          accr[0] += r * r;
+        }
       }
-    } else {
-      for (int i = i0; i < n; i += stride) {
-        const double ax = (a.dextra ? a.dextra[i] * a.x[i] : 0.0) + sell_row<WMAX, true>(a, a.valA, a.x, i);
-        const double r = m.b64[i] - ax;
-        m.r64[i] = r;
-        accr[0] += r * r;
-      }
+      block_sum<1, double>(accr, shd);
+      if (threadIdx.x == 0) a.part[blockIdx.x * 4 + 2] = accr[0];
+      if (!grid_barrier(a.bar, nb, a.status)) return;
+      double t1[1];
+      grid_total<1, double>(a.part, {2}, nb, t1, shd);
+      rr64 = t1[0];
     }
-    block_sum<1, double>(accr, shd);
-    if (threadIdx.x == 0) a.part[blockIdx.x * 4 + 2] = accr[0];
-    if (!grid_barrier(a.bar, nb, a.status)) return;
-    double t1[1];
-    grid_total<1, double>(a.part, {2}, nb, t1, shd);
-    const double rr64 = t1[0];
     if (!isfinite(rr64)) {
       fail = ST_NONFINITE;
       break;

@@ -39,7 +39,10 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_kernel(const __
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
 
   // ---- phase 0: right-hand side, initial residual --------------------------
-  double acc0[2] = {0.0, 0.0};
+  // Without mean projection the residual is final here, so phase 1 (z = D^-1 r
+  // and its dot products) runs in the same pass: one device barrier fewer.
+  const bool fused = !a.project;
+  double acc0[4] = {0.0, 0.0, 0.0, 0.0};
   for (int i = i0; i < n; i += stride) {
     double b = a.rl ? a.rl[i] : 0.0;
     if (a.val1) b += a.c1 * sell_row<WMAX, false>(a, a.val1, a.va, i);
@@ -55,41 +58,58 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_kernel(const __
     a.r[i] = r;
     acc0[0] += b;
     acc0[1] += b * b;
+    if (fused) {
+      const double z = r * a.invd[i];
+      a.z[i] = z;
+      acc0[2] += r * z;
+      acc0[3] += r * r;
+    }
   }
   if (!a.warm)
     for (int i = i0; i < n; i += stride) a.x[i] = 0.0;
-  block_sum<2>(acc0, sh);
-  if (threadIdx.x == 0) {
-    a.part[blockIdx.x * 4 + 0] = acc0[0];
-    a.part[blockIdx.x * 4 + 1] = acc0[1];
-  }
+  block_sum<4>(acc0, sh);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a.part[blockIdx.x * 4 + k] = acc0[k];
   if (!grid_barrier(a.bar, nb, a.status)) return;
-  double tot[2];
-  grid_total<2>(a.part, {0, 1}, nb, tot, sh);
+  double tot[4] = {0.0, 0.0, 0.0, 0.0};
+  if (fused) {
+    grid_total<4>(a.part, {0, 1, 2, 3}, nb, tot, sh);
+  } else {
+    double t01[2];
+    grid_total<2>(a.part, {0, 1}, nb, t01, sh);
+    tot[0] = t01[0];
+    tot[1] = t01[1];
+  }
   const double mean_b = a.project ? tot[0] / double(n) : 0.0;
   double bb = a.project ? tot[1] - double(n) * mean_b * mean_b : tot[1];
   if (bb < 0.0) bb = 0.0;
   const double tol2 = a.tol * a.tol * bb;
 
-  // ---- phase 1: z = D^-1 r, p = z ------------------------------------------
-  double acc1[2] = {0.0, 0.0};
-  for (int i = i0; i < n; i += stride) {
-    const double r = a.r[i] - mean_b;
-    a.r[i] = r;
-    const double z = r * a.invd[i];
-    a.z[i] = z;
-    acc1[0] += r * z;
-    acc1[1] += r * r;
+  // ---- phase 1: z = D^-1 r, p = z (projected systems) ---------------------
+  if (!fused) {
+    double acc1[2] = {0.0, 0.0};
+    for (int i = i0; i < n; i += stride) {
+      const double r = a.r[i] - mean_b;
+      a.r[i] = r;
+      const double z = r * a.invd[i];
+      a.z[i] = z;
+      acc1[0] += r * z;
+      acc1[1] += r * r;
+    }
+    block_sum<2>(acc1, sh);
+    if (threadIdx.x == 0) {
+      a.part[blockIdx.x * 4 + 2] = acc1[0];
+      a.part[blockIdx.x * 4 + 3] = acc1[1];
+    }
+    if (!grid_barrier(a.bar, nb, a.status)) return;
+    double t23[2];
+    grid_total<2>(a.part, {2, 3}, nb, t23, sh);
+    tot[2] = t23[0];
+    tot[3] = t23[1];
   }
-  block_sum<2>(acc1, sh);
-  if (threadIdx.x == 0) {
-    a.part[blockIdx.x * 4 + 2] = acc1[0];
-    a.part[blockIdx.x * 4 + 3] = acc1[1];
-  }
-  if (!grid_barrier(a.bar, nb, a.status)) return;
-  grid_total<2>(a.part, {2, 3}, nb, tot, sh);
-  double rho = tot[0];
-  double rr = tot[1];
+  double rho = tot[2];
+  double rr = tot[3];
 
   int it = 0;
   int fail = 0;
@@ -135,9 +155,10 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_kernel(const __
       a.part[blockIdx.x * 4 + 3] = acc[1];
     }
     if (!grid_barrier(a.bar, nb, a.status)) return;
-    grid_total<2>(a.part, {2, 3}, nb, tot, sh);
+    double tk[2];
+    grid_total<2>(a.part, {2, 3}, nb, tk, sh);
     ++it;
-    rr = tot[1];
+    rr = tk[1];
     if (!isfinite(rr)) {
       fail = ST_NONFINITE;
       break;
@@ -147,8 +168,8 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_kernel(const __
       fail = ST_NOT_CONVERGED;
       break;
     }
-    beta = tot[0] / rho;
-    rho = tot[0];
+    beta = tk[0] / rho;
+    rho = tk[0];
   }
 
   // ---- normalisation of the singular elliptic solution ----------------------
