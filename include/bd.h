@@ -142,6 +142,10 @@ typedef struct {
   int64_t spd_clamps;      /* nodes whose condensed diagonal was raised */
   int64_t ionic_evals;     /* node-block evaluations (kernel launches x nodes / nodes) */
   int64_t kernel_launches; /* device kernels launched by the steps */
+  int64_t solver_block_bound; /* launch bound of the solver build in use: 512 (128 registers a
+                                 thread, chosen when the rows fit one block per SM) or 1024 */
+  int64_t amg_levels;      /* smoothed AMG levels of the elliptic preconditioner (0: Jacobi) */
+  int64_t amg_coarse_rows; /* rows of the dense coarsest AMG level (0: Jacobi) */
 } bd_stats_t;
 
 /* Per-kind device time of profiled steps (bd_profile_steps). */

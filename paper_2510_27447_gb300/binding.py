@@ -69,7 +69,8 @@ class Opts(C.Structure):
 class Stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("steps", "sweeps", "cg_iters_e", "cg_solves_e",
                                           "cg_iters_p", "cg_solves_p", "spd_clamps", "ionic_evals",
-                                          "kernel_launches")]
+                                          "kernel_launches", "solver_block_bound", "amg_levels",
+                                          "amg_coarse_rows")]
 
 
 KERNEL_KINDS = ("pcg_elliptic", "pcg_parabolic", "ionic", "field", "combine", "finish")

@@ -212,20 +212,34 @@ bool dense_spd_inverse(std::vector<double>& a, int64_t n, std::vector<double>* i
       a[i * n + j] = t / l;
     }
   }
-  inv->assign(n * n, 0.0);
-  std::vector<double> y(n);
-  for (int64_t c = 0; c < n; ++c) {
-    for (int64_t i = 0; i < n; ++i) {
-      double t = (i == c) ? 1.0 : 0.0;
-      for (int64_t k = 0; k < i; ++k) t -= a[i * n + k] * y[k];
-      y[i] = t / a[i * n + i];
+  // column c of the inverse: L y = e_c (y_i = 0 for i < c), then L^T x = y.
+  // L^T is stored row-major so that the backward substitution reads rows;
+  // columns are independent and split over threads.
+  std::vector<double> lt(size_t(n * n), 0.0);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = 0; k <= i; ++k) lt[k * n + i] = a[i * n + k];
+  inv->assign(size_t(n * n), 0.0);
+  auto columns = [&](int64_t t0, int64_t step) {
+    std::vector<double> y(n, 0.0), x(n);
+    for (int64_t c = t0; c < n; c += step) {
+      for (int64_t i = c; i < n; ++i) {
+        double t = (i == c) ? 1.0 : 0.0;
+        for (int64_t k = c; k < i; ++k) t -= a[i * n + k] * y[k];
+        y[i] = t / a[i * n + i];
+      }
+      for (int64_t i = n - 1; i >= 0; --i) {
+        double t = i >= c ? y[i] : 0.0;
+        for (int64_t k = i + 1; k < n; ++k) t -= lt[i * n + k] * x[k];
+        x[i] = t / a[i * n + i];
+      }
+      for (int64_t i = 0; i < n; ++i) (*inv)[i * n + c] = x[i];
     }
-    for (int64_t i = n - 1; i >= 0; --i) {
-      double t = y[i];
-      for (int64_t k = i + 1; k < n; ++k) t -= a[k * n + i] * (*inv)[k * n + c];
-      (*inv)[i * n + c] = t / a[i * n + i];
-    }
-  }
+  };
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>({32, int64_t(std::thread::hardware_concurrency()), n / 64}));
+  std::vector<std::thread> th;
+  // columns dealt round-robin (the forward pass of column c costs (n - c)^2 / 2)
+  for (int64_t t = 0; t < nt; ++t) th.emplace_back(columns, t, nt);
+  for (auto& x : th) x.join();
   return true;
 }
 

@@ -1513,6 +1513,9 @@ int bd_get_stats(const bd_state_t* cs, bd_stats_t* out) {
   out->spd_clamps = int64_t(cl);
   out->ionic_evals = s->ionic_evals;
   out->kernel_launches = s->launches;
+  out->solver_block_bound = s->cluster > 0 ? kSolverTierBlock[0] : kSolverTierBlock[s->tier];
+  out->amg_levels = s->use_amg ? s->amg.nlev : 0;
+  out->amg_coarse_rows = s->use_amg ? s->amg.nc : 0;
   return BD_OK;
 }
 
