@@ -127,6 +127,10 @@ typedef struct {
                             for other values; falls back to the grid when the device cannot
                             schedule the cluster).  Measured slower on GB300 for 4k-263k-node
                             meshes (16 SMs stream less than the grid); kept for experiments. */
+  int solver_tier;       /* 0 (default): choose the register tier of the solver kernels
+                            (bd_stats_t.solver_tier); 1, 2, 3: force tier 0, 1 or 2 (2 needs
+                            cg_block <= 512; 3 affects only the mixed AMG kernels);
+                            BD_ERR_ARG otherwise; ignored with cg_cluster */
 } bd_opts_t;
 
 typedef struct bd_state bd_state_t;
@@ -144,6 +148,9 @@ typedef struct {
   int64_t kernel_launches; /* device kernels launched by the steps */
   int64_t solver_block_bound; /* launch bound of the solver build in use: 512 (128 registers a
                                  thread, chosen when the rows fit one block per SM) or 1024 */
+  int64_t solver_tier;     /* 0: 1024-thread build (64 registers); 1: 512-thread build (128
+                              registers); 2: as 0, with the mixed AMG kernels built for two
+                              1024-thread blocks per SM (32 registers; meshes >= 1M rows) */
   int64_t amg_levels;      /* smoothed AMG levels of the elliptic preconditioner (0: Jacobi) */
   int64_t amg_coarse_rows; /* rows of the dense coarsest AMG level (0: Jacobi) */
 } bd_stats_t;

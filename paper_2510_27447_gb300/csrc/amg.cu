@@ -174,7 +174,7 @@ int max_blocks_t(int block) {
 
 int pcg_amg_max_blocks(int block, int tier) {
   // the smallest co-resident count over the tier's instantiations keeps every launch legal
-  if (tier) return std::min(max_blocks_t<8, 512>(block), max_blocks_t<0, 512>(block));
+  if (tier == 1) return std::min(max_blocks_t<8, 512>(block), max_blocks_t<0, 512>(block));
   return std::min(max_blocks_t<8, 1024>(block), max_blocks_t<0, 1024>(block));
 }
 
@@ -183,7 +183,7 @@ cudaError_t launch_pcg_amg(const PcgLaunch& P, const AmgDev* M, int wmax, cudaSt
   cudaLaunchAttribute attr[1];
   PcgLaunch K;
   solver_launch_config(P, st, &cfg, attr, &K);
-  if (K.tier)
+  if (K.tier == 1)
     return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_amg_kernel<8, 512>, K, M)
                     : cudaLaunchKernelEx(&cfg, pcg_amg_kernel<0, 512>, K, M);
   return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_amg_kernel<8, 1024>, K, M)

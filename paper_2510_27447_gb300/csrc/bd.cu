@@ -90,6 +90,7 @@ struct bd_state {
   float* partf = nullptr;
   double *b64 = nullptr, *r64 = nullptr;
   int mixed_grid = 1;
+  int mixed_amg_grid = 1;                  // grid of the mixed AMG kernels (differs in tier 2)
   int amg_grid = 1;
   int amg_levels = 0;
   double amg_cycle_bytes[2] = {0.0, 0.0};   // algorithmic bytes of one V-cycle (FP64, FP32 values)
@@ -342,7 +343,7 @@ int elliptic(bd_state* s, const double* v, double* u) {
     X.max_outer = 12;
     X.inner_cap = s->opts.cg_cap_e;
     X.use_amg = s->use_amg ? 1 : 0;
-    P.grid = s->mixed_grid;
+    P.grid = s->use_amg ? s->mixed_amg_grid : s->mixed_grid;
     CK(launch_pcg_mixed(P, X, s->d_amgf, s->wmax, s->stream, s->partf));
   } else if (s->use_amg) {
     P.grid = s->amg_grid;
@@ -383,7 +384,7 @@ int elliptic2(bd_state* s, const double* v1, double* u1, const double* v2, doubl
   P.solves_acc = s->d_stats + 1;
   P.outer_acc = s->d_stats + 4;
   P.pair_acc = s->d_stats + 7;
-  P.grid = s->mixed_grid;
+  P.grid = s->mixed_amg_grid;
   MixedLaunch X = mixed_base(s);
   X.valA32 = s->fAie;
   X.tol_inner = BD_MIXED_TOL_INNER;
@@ -1080,13 +1081,24 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     return fail(nullptr, BD_ERR_ARG, "cg_block must be a multiple of 32 up to 1024");
   }
   const int64_t want = s->opts.cg_grid > 0 ? s->opts.cg_grid : (N + s->pcg_block - 1) / s->pcg_block;
-  // register tier: the 128-register solver build when every solver kernel of
-  // that build holds the whole grid co-resident (no cluster launches)
+  // register tier (no cluster launches): the 128-register build when every
+  // solver kernel of it holds the whole grid co-resident, else the 64-register
+  // build, with the mixed AMG kernels at full occupancy on large meshes;
+  // solver_tier = 1..3 forces tier 0..2
+  const int force = s->opts.solver_tier;
+  if (force < 0 || force > 3 || (force == 2 && s->pcg_block > kSolverTierBlock[1])) {
+    release(s);
+    delete s;
+    return fail(nullptr, BD_ERR_ARG, "solver_tier must be 0..3 (2 needs cg_block <= 512)");
+  }
   s->tier = 0;
-  if (s->opts.cg_cluster == 0 && s->pcg_block <= kSolverTierBlock[1]) {
-    int m1 = std::min(pcg_max_blocks(s->pcg_block, s->wmax, 1), pcg_amg_max_blocks(s->pcg_block, 1));
-    if (s->precision == BD_MIXED) m1 = std::min(m1, pcg_mixed_max_blocks(s->pcg_block, 1));
-    if (m1 >= want) s->tier = 1;
+  if (s->opts.cg_cluster == 0) {
+    if (force == 2 || (force == 0 && s->pcg_block <= kSolverTierBlock[1])) {
+      int m1 = std::min(pcg_max_blocks(s->pcg_block, s->wmax, 1), pcg_amg_max_blocks(s->pcg_block, 1));
+      if (s->precision == BD_MIXED) m1 = std::min(m1, pcg_mixed_max_blocks(s->pcg_block, 1));
+      if (force == 2 || m1 >= want) s->tier = 1;
+    }
+    if (s->tier == 0 && s->precision == BD_MIXED && (force == 3 || (force == 0 && N >= kTier2Rows))) s->tier = 2;
   }
   s->pcg_max = pcg_max_blocks(s->pcg_block, s->wmax, s->tier);
   if (ok && s->pcg_max <= 0) {
@@ -1104,7 +1116,17 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     }
     if (cc > 0) s->cluster = solver_cluster_size(kSolverTierBlock[0], cc);
   }
-  if (ok) ok = alloc_n(s, &s->cg_part, int64_t(s->pcg_max) * 4);
+  // per-block partial sums: room for the largest grid of any solver launch
+  int part_blocks = s->pcg_max;
+  if (s->precision == BD_MIXED) {
+    const int mx = pcg_mixed_max_blocks(s->pcg_block, s->tier);
+    const int ma = pcg_mixed_amg_max_blocks(s->pcg_block, s->tier);
+    if (mx <= 0 || ma <= 0) ok = false;
+    s->mixed_grid = std::min(s->pcg_grid, std::max(mx, 1));
+    s->mixed_amg_grid = s->tier == 2 ? int(std::max<int64_t>(1, std::min<int64_t>(want, ma))) : s->mixed_grid;
+    part_blocks = std::max(part_blocks, s->mixed_amg_grid);
+  }
+  if (ok) ok = alloc_n(s, &s->cg_part, int64_t(part_blocks) * 4);
   if (ok && s->opts.sweep_tol > 0)
     ok = alloc_n(s, &s->gate, 1) && alloc_n(s, &s->dmax, 1) && alloc_n(s, &s->Xsave, ns * NT);
   if (ok && s->precision == BD_MIXED) {
@@ -1112,13 +1134,10 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     ok = alloc_n(s, &s->fAie, s->ell_n) && alloc_n(s, &s->r32, 2 * N) && alloc_n(s, &s->z32, 2 * N) &&
          alloc_n(s, &s->p32, 2 * N) && alloc_n(s, &s->q32, 2 * N) && alloc_n(s, &s->invd32, N) &&
          alloc_n(s, &s->d32, 2 * N) && alloc_n(s, &s->b64, 2 * N) && alloc_n(s, &s->r64, 2 * N) &&
-         alloc_n(s, &s->partf8, int64_t(s->pcg_max) * 8) && alloc_n(s, &s->partd8, int64_t(s->pcg_max) * 8) &&
+         alloc_n(s, &s->partf8, int64_t(part_blocks) * 8) && alloc_n(s, &s->partd8, int64_t(part_blocks) * 8) &&
          (NT == N || alloc_n(s, &s->vfull2, N)) &&
          alloc_n(s, reinterpret_cast<char**>(&s->d_amgf2), int64_t(sizeof(AmgDevF))) &&
-         alloc_n(s, &s->partf, int64_t(s->pcg_max) * 4);
-    const int mx = pcg_mixed_max_blocks(s->pcg_block, s->tier);
-    if (ok && mx <= 0) ok = false;
-    s->mixed_grid = std::min(s->pcg_grid, std::max(mx, 1));
+         alloc_n(s, &s->partf, int64_t(part_blocks) * 4);
   }
   if (!ok) {
     release(s);
@@ -1514,6 +1533,7 @@ int bd_get_stats(const bd_state_t* cs, bd_stats_t* out) {
   out->ionic_evals = s->ionic_evals;
   out->kernel_launches = s->launches;
   out->solver_block_bound = s->cluster > 0 ? kSolverTierBlock[0] : kSolverTierBlock[s->tier];
+  out->solver_tier = s->cluster > 0 ? 0 : s->tier;
   out->amg_levels = s->use_amg ? s->amg.nlev : 0;
   out->amg_coarse_rows = s->use_amg ? s->amg.nc : 0;
   return BD_OK;

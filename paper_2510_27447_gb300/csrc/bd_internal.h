@@ -12,11 +12,15 @@ namespace bd {
 constexpr int kMaxStim = 32;
 constexpr int kMaxNodes = 3;          // Gauss-Lobatto nodes per step
 constexpr int kMaxNS = 19;
-// The persistent solver kernels are built twice, for two __launch_bounds__:
-// tier 0 allows 1024-thread blocks (64 registers a thread; two 512-thread
-// blocks share an SM), tier 1 allows 512-thread blocks (128 registers; one
-// block an SM).  Tier 1 serves problems whose rows fit one block per SM.
-constexpr int kSolverTierBlock[2] = {1024, 512};
+// The persistent solver kernels are built for several __launch_bounds__
+// ("tiers"): tier 0 allows 1024-thread blocks (64 registers a thread; two
+// 512-thread blocks share an SM), tier 1 allows 512-thread blocks (128
+// registers; one block an SM) and serves problems whose rows fit one block
+// per SM; tier 2 is tier 0 except that the mixed AMG kernels are built for
+// two 1024-thread blocks an SM (32 registers, full occupancy), for meshes of
+// at least kTier2Rows rows, where the operator streams need the threads.
+constexpr int kSolverTierBlock[3] = {1024, 512, 1024};
+constexpr int64_t kTier2Rows = 1000000;
 
 // device status word bits (one per bd_status_t failure kind)
 enum : int {
@@ -275,6 +279,7 @@ struct MixedLaunch {
 cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const AmgDevF* M, int wmax, cudaStream_t st,
                              float* partf);
 int pcg_mixed_max_blocks(int block, int tier);
+int pcg_mixed_amg_max_blocks(int block, int tier);   // the mixed AMG kernels of a tier
 // two elliptic solves (right-hand sides c1 A_i va and c1 A_i va1) in one launch;
 // the MixedLaunch workspaces hold 2 n entries, H1 the second system's AMG
 // level vectors, partf8 / partd8 8 values per block

@@ -25,8 +25,8 @@ namespace bd {
 
 namespace {
 
-template <int WMAX, bool AMG, int TPB>
-__global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_mixed_kernel(const __grid_constant__ PcgLaunch a,
+template <int WMAX, bool AMG, int TPB, int MINB = BD_SOLVER_MIN_BLOCKS>
+__global__ void __launch_bounds__(TPB, MINB) pcg_mixed_kernel(const __grid_constant__ PcgLaunch a,
                                                              const __grid_constant__ MixedLaunch m,
                                                              const AmgDevF* __restrict__ Mp, float* partf) {
   __shared__ AmgDevF sM;    // descriptor staged in shared memory (see pcg_amg_kernel)
@@ -262,8 +262,8 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_mixed_kernel(co
 // refinement passes and convergence test; a converged one stops changing.
 // Workspace vectors of the second system sit n entries after the first's;
 // partd / partf hold 8 values per block.
-template <int WMAX, int TPB>
-__global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_mixed2_kernel(const __grid_constant__ PcgLaunch a,
+template <int WMAX, int TPB, int MINB = BD_SOLVER_MIN_BLOCKS>
+__global__ void __launch_bounds__(TPB, MINB) pcg_mixed2_kernel(const __grid_constant__ PcgLaunch a,
                                                               const double* va1, double* x1,
                                                               const __grid_constant__ MixedLaunch m,
                                                               const AmgDevF* __restrict__ H0p,
@@ -522,53 +522,67 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_mixed2_kernel(c
   }
 }
 
-template <int W, int TPB>
+template <int W, int TPB, int MINB = BD_SOLVER_MIN_BLOCKS>
 int max_blocks2_t(int block) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_mixed2_kernel<W, TPB>, block, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_mixed2_kernel<W, TPB, MINB>, block, 0) != cudaSuccess)
     return 0;
   return sms * per;
 }
 
-template <int W, bool AMG, int TPB>
+template <int W, bool AMG, int TPB, int MINB = BD_SOLVER_MIN_BLOCKS>
 int max_blocks_t(int block) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_mixed_kernel<W, AMG, TPB>, block, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pcg_mixed_kernel<W, AMG, TPB, MINB>, block, 0) !=
+      cudaSuccess)
     return 0;
   return sms * per;
 }
 
-template <int TPB>
+// the smallest co-resident count over a build's instantiations keeps every
+// launch legal; AMG_MINB is the occupancy bound of its AMG kernels
+template <int TPB, int AMG_MINB>
 int tier_max_blocks(int block) {
   int m = max_blocks_t<8, false, TPB>(block);
   m = std::min(m, max_blocks_t<0, false, TPB>(block));
-  m = std::min(m, max_blocks_t<8, true, TPB>(block));
-  m = std::min(m, max_blocks_t<0, true, TPB>(block));
-  m = std::min(m, max_blocks2_t<8, TPB>(block));
-  m = std::min(m, max_blocks2_t<0, TPB>(block));
+  m = std::min(m, max_blocks_t<8, true, TPB, AMG_MINB>(block));
+  m = std::min(m, max_blocks_t<0, true, TPB, AMG_MINB>(block));
+  m = std::min(m, max_blocks2_t<8, TPB, AMG_MINB>(block));
+  m = std::min(m, max_blocks2_t<0, TPB, AMG_MINB>(block));
   return m;
 }
 
-template <int TPB>
+// the AMG kernels alone (tier 2 sizes their grid separately)
+template <int TPB, int AMG_MINB>
+int tier_amg_max_blocks(int block) {
+  int m = max_blocks_t<8, true, TPB, AMG_MINB>(block);
+  m = std::min(m, max_blocks_t<0, true, TPB, AMG_MINB>(block));
+  m = std::min(m, max_blocks2_t<8, TPB, AMG_MINB>(block));
+  m = std::min(m, max_blocks2_t<0, TPB, AMG_MINB>(block));
+  return m;
+}
+
+template <int TPB, int AMG_MINB>
 cudaError_t launch_mixed_tier(const cudaLaunchConfig_t& cfg, const PcgLaunch& K, const MixedLaunch& X,
                               const AmgDevF* M, int wmax, float* partf) {
   if (X.use_amg)
-    return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<8, true, TPB>, K, X, M, partf)
-                    : cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<0, true, TPB>, K, X, M, partf);
+    return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<8, true, TPB, AMG_MINB>, K, X, M, partf)
+                    : cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<0, true, TPB, AMG_MINB>, K, X, M, partf);
   return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<8, false, TPB>, K, X, M, partf)
                   : cudaLaunchKernelEx(&cfg, pcg_mixed_kernel<0, false, TPB>, K, X, M, partf);
 }
 
-template <int TPB>
+template <int TPB, int AMG_MINB>
 cudaError_t launch_mixed2_tier(const cudaLaunchConfig_t& cfg, const PcgLaunch& K, const double* va1, double* x1,
                                const MixedLaunch& X, const AmgDevF* H0, const AmgDevF* H1, int wmax,
                                float* partf8, double* partd8) {
-  return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<8, TPB>, K, va1, x1, X, H0, H1, partf8, partd8)
-                  : cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<0, TPB>, K, va1, x1, X, H0, H1, partf8, partd8);
+  return wmax > 0
+             ? cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<8, TPB, AMG_MINB>, K, va1, x1, X, H0, H1, partf8, partd8)
+             : cudaLaunchKernelEx(&cfg, pcg_mixed2_kernel<0, TPB, AMG_MINB>, K, va1, x1, X, H0, H1, partf8, partd8);
 }
 
 __global__ void to_float_kernel(int64_t n, const double* src, float* dst) {
@@ -581,7 +595,14 @@ __global__ void to_float_kernel(int64_t n, const double* src, float* dst) {
 // sell_row's chunked loop serves every width bound (8, 16, 32) with the same
 // code, so one instantiation covers them; 0 (rows wider than 32) loops
 int pcg_mixed_max_blocks(int block, int tier) {
-  return tier ? tier_max_blocks<512>(block) : tier_max_blocks<1024>(block);
+  if (tier == 1) return tier_max_blocks<512, 1>(block);
+  return tier_max_blocks<1024, 1>(block);
+}
+
+int pcg_mixed_amg_max_blocks(int block, int tier) {
+  if (tier == 1) return tier_amg_max_blocks<512, 1>(block);
+  if (tier == 2) return tier_amg_max_blocks<1024, 2>(block);
+  return tier_amg_max_blocks<1024, 1>(block);
 }
 
 cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const AmgDevF* M, int wmax, cudaStream_t st,
@@ -590,8 +611,9 @@ cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const Amg
   cudaLaunchAttribute attr[1];
   PcgLaunch K;
   solver_launch_config(P, st, &cfg, attr, &K);
-  return K.tier ? launch_mixed_tier<512>(cfg, K, X, M, wmax, partf)
-                : launch_mixed_tier<1024>(cfg, K, X, M, wmax, partf);
+  if (K.tier == 1) return launch_mixed_tier<512, 1>(cfg, K, X, M, wmax, partf);
+  if (K.tier == 2) return launch_mixed_tier<1024, 2>(cfg, K, X, M, wmax, partf);
+  return launch_mixed_tier<1024, 1>(cfg, K, X, M, wmax, partf);
 }
 
 cudaError_t launch_pcg_mixed2(const PcgLaunch& P, const double* va1, double* x1, const MixedLaunch& X,
@@ -601,8 +623,9 @@ cudaError_t launch_pcg_mixed2(const PcgLaunch& P, const double* va1, double* x1,
   cudaLaunchAttribute attr[1];
   PcgLaunch K;
   solver_launch_config(P, st, &cfg, attr, &K);
-  return K.tier ? launch_mixed2_tier<512>(cfg, K, va1, x1, X, H0, H1, wmax, partf8, partd8)
-                : launch_mixed2_tier<1024>(cfg, K, va1, x1, X, H0, H1, wmax, partf8, partd8);
+  if (K.tier == 1) return launch_mixed2_tier<512, 1>(cfg, K, va1, x1, X, H0, H1, wmax, partf8, partd8);
+  if (K.tier == 2) return launch_mixed2_tier<1024, 2>(cfg, K, va1, x1, X, H0, H1, wmax, partf8, partd8);
+  return launch_mixed2_tier<1024, 1>(cfg, K, va1, x1, X, H0, H1, wmax, partf8, partd8);
 }
 
 // cluster launches use tier 0 (full-size blocks)

@@ -236,7 +236,7 @@ bool pcg_cluster_ok(int block, int size) {
 // sell_row's chunked loop serves every width bound (8, 16, 32) with the same
 // code, so one instantiation covers them; 0 (rows wider than 32) loops
 int pcg_max_blocks(int block, int wmax, int tier) {
-  if (tier) return wmax > 0 ? max_blocks_t<8, 512>(block) : max_blocks_t<0, 512>(block);
+  if (tier == 1) return wmax > 0 ? max_blocks_t<8, 512>(block) : max_blocks_t<0, 512>(block);
   return wmax > 0 ? max_blocks_t<8, 1024>(block) : max_blocks_t<0, 1024>(block);
 }
 
@@ -270,7 +270,7 @@ cudaError_t launch_pcg(const PcgLaunch& P, int wmax, cudaStream_t st) {
   cudaLaunchAttribute attr[1];
   PcgLaunch K;
   solver_launch_config(P, st, &cfg, attr, &K);
-  if (K.tier)
+  if (K.tier == 1)
     return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_kernel<8, 512>, K) : cudaLaunchKernelEx(&cfg, pcg_kernel<0, 512>, K);
   return wmax > 0 ? cudaLaunchKernelEx(&cfg, pcg_kernel<8, 1024>, K)
                   : cudaLaunchKernelEx(&cfg, pcg_kernel<0, 1024>, K);

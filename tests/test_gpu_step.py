@@ -200,22 +200,28 @@ def test_device_barrier_wait_is_bounded():
     assert np.all(np.isfinite(v)) and np.all(np.isfinite(u))
 
 
-@pytest.mark.parametrize("cg_block,coarse_max,bound", [(512, 0, 512), (1024, 0, 1024), (512, 3000, 512)])
-def test_amg_solver_builds_match_oracle(cg_block, coarse_max, bound):
-    """The AMG-preconditioned elliptic CG in both register builds of the
-    solver kernels (512-thread launch bound, chosen when the rows fit one
-    block per SM; 1024-thread bound) and with a dense coarse level too wide
-    for the shared-memory staging of its right-hand side (2,827 rows):
-    FP64 and mixed solutions within the solver tolerance of the oracle's
-    direct solve.  The handle's counters show which build and hierarchy ran;
-    the coarse levels use several lanes per row here."""
+@pytest.mark.parametrize("cg_block,coarse_max,force,tier", [(512, 0, 0, 1), (1024, 0, 0, 0), (512, 3000, 0, 1),
+                                                             (512, 0, 1, 0), (512, 0, 3, 2)])
+def test_amg_solver_builds_match_oracle(cg_block, coarse_max, force, tier):
+    """The AMG-preconditioned elliptic CG in every register build of the
+    solver kernels (tier 0: 1024-thread launch bound; tier 1: 512-thread
+    bound, chosen when the rows fit one block per SM; tier 2: the mixed AMG
+    kernels at two 1024-thread blocks per SM, chosen for meshes of a million
+    rows and forced here) and with a dense coarse level too wide for the
+    shared-memory staging of its right-hand side (2,827 rows): FP64 and mixed
+    solutions within the solver tolerance of the oracle's direct solve.  The
+    handle's counters show which build and hierarchy ran; the coarse levels
+    use several lanes per row here."""
     w = W.sheet(129, 1.25, W.LR91, 0.02, 1)
     v = -80 + 100 * np.exp(-30 * ((w.xyz[:, 0] - 0.4) ** 2 + (w.xyz[:, 1] - 0.7) ** 2))
     ref = oracle_problem(w).elliptic(v)
     for prec in (binding.FP64, binding.MIXED):
-        sim = gpu_sim(w, precision=prec, cg_block=cg_block, amg_coarse_max=coarse_max, cg_tol_e=1e-11)
+        sim = gpu_sim(w, precision=prec, cg_block=cg_block, amg_coarse_max=coarse_max, cg_tol_e=1e-11,
+                      solver_tier=force)
         st = sim.stats()
-        assert st["solver_block_bound"] == bound and st["amg_levels"] >= 1, st
+        want = 0 if (tier == 2 and prec == binding.FP64) else tier    # tier 2 differs only in mixed AMG kernels
+        assert st["solver_tier"] == want and st["amg_levels"] >= 1, st
+        assert st["solver_block_bound"] == (512 if want == 1 else 1024), st
         if coarse_max:
             assert st["amg_coarse_rows"] > 1536, st
         u, it = sim.solve_elliptic(v)
