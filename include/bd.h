@@ -150,7 +150,8 @@ typedef struct {
                                  thread, chosen when the rows fit one block per SM) or 1024 */
   int64_t solver_tier;     /* 0: 1024-thread build (64 registers); 1: 512-thread build (128
                               registers); 2: as 0, with the mixed AMG kernels built for two
-                              1024-thread blocks per SM (32 registers; meshes >= 1M rows) */
+                              1024-thread blocks per SM (32 registers; operators of >= 12M
+                              entries) */
   int64_t amg_levels;      /* smoothed AMG levels of the elliptic preconditioner (0: Jacobi) */
   int64_t amg_coarse_rows; /* rows of the dense coarsest AMG level (0: Jacobi) */
 } bd_stats_t;

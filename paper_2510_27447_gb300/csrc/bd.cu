@@ -1083,7 +1083,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   const int64_t want = s->opts.cg_grid > 0 ? s->opts.cg_grid : (N + s->pcg_block - 1) / s->pcg_block;
   // register tier (no cluster launches): the 128-register build when every
   // solver kernel of it holds the whole grid co-resident, else the 64-register
-  // build, with the mixed AMG kernels at full occupancy on large meshes;
+  // build, with the mixed AMG kernels at full occupancy on large operators;
   // solver_tier = 1..3 forces tier 0..2
   const int force = s->opts.solver_tier;
   if (force < 0 || force > 3 || (force == 2 && s->pcg_block > kSolverTierBlock[1])) {
@@ -1098,7 +1098,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
       if (s->precision == BD_MIXED) m1 = std::min(m1, pcg_mixed_max_blocks(s->pcg_block, 1));
       if (force == 2 || m1 >= want) s->tier = 1;
     }
-    if (s->tier == 0 && s->precision == BD_MIXED && (force == 3 || (force == 0 && N >= kTier2Rows))) s->tier = 2;
+    if (s->tier == 0 && s->precision == BD_MIXED && (force == 3 || (force == 0 && nnz >= kTier2Nnz))) s->tier = 2;
   }
   s->pcg_max = pcg_max_blocks(s->pcg_block, s->wmax, s->tier);
   if (ok && s->pcg_max <= 0) {

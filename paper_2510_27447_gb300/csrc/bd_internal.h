@@ -17,10 +17,12 @@ constexpr int kMaxNS = 19;
 // 512-thread blocks share an SM), tier 1 allows 512-thread blocks (128
 // registers; one block an SM) and serves problems whose rows fit one block
 // per SM; tier 2 is tier 0 except that the mixed AMG kernels are built for
-// two 1024-thread blocks an SM (32 registers, full occupancy), for meshes of
-// at least kTier2Rows rows, where the operator streams need the threads.
+// two 1024-thread blocks an SM (32 registers, full occupancy), for operators
+// of at least kTier2Nnz entries, where the operator streams need the threads
+// (measured on GB300: faster on 3-D meshes of 18M and 30M entries, slower or
+// even on 2-D meshes of 4.5M and 7.3M and a 3-D mesh of 4M).
 constexpr int kSolverTierBlock[3] = {1024, 512, 1024};
-constexpr int64_t kTier2Rows = 1000000;
+constexpr int64_t kTier2Nnz = 12000000;
 
 // device status word bits (one per bd_status_t failure kind)
 enum : int {
