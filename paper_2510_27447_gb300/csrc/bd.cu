@@ -430,6 +430,7 @@ int parabolic(bd_state* s, double alpha, double c1, const double* va, double c2,
     X.max_outer = 1;
     X.inner_cap = s->opts.cg_cap_p;
     X.use_amg = 0;
+    X.pipelined = s->tier == 1 ? 1 : 0;   // measured: pays where the barriers dominate
     P.grid = s->mixed_grid;
     CK(launch_pcg_mixed(P, X, s->d_amgf, s->wmax, s->stream, s->partf));
   } else {
@@ -1137,7 +1138,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
          alloc_n(s, &s->partf8, int64_t(part_blocks) * 8) && alloc_n(s, &s->partd8, int64_t(part_blocks) * 8) &&
          (NT == N || alloc_n(s, &s->vfull2, N)) &&
          alloc_n(s, reinterpret_cast<char**>(&s->d_amgf2), int64_t(sizeof(AmgDevF))) &&
-         alloc_n(s, &s->partf, int64_t(part_blocks) * 4);
+         alloc_n(s, &s->partf, int64_t(part_blocks) * 8);
   }
   if (!ok) {
     release(s);

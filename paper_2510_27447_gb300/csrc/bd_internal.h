@@ -277,6 +277,7 @@ struct MixedLaunch {
   int max_outer;            // 1: single FP32 solve (x = d); > 1: iterative refinement
   int inner_cap;
   int use_amg;
+  int pipelined;            // Jacobi inner CG in its pipelined form (one barrier an iteration)
 };
 cudaError_t launch_pcg_mixed(const PcgLaunch& P, const MixedLaunch& X, const AmgDevF* M, int wmax, cudaStream_t st,
                              float* partf);

@@ -45,10 +45,17 @@ __global__ void __launch_bounds__(TPB, MINB) pcg_mixed_kernel(const __grid_const
   // formed in the same pass (one device barrier fewer).
   const bool fused = !a.project;
   double acc0[3] = {0.0, 0.0, 0.0};
+  // the right-hand side products and the warm residual's A x share the
+  // operator pattern: one pass over each row
+  const double* const pv[3] = {a.val1, a.val2, a.valA};
+  const double* const px[3] = {a.va, a.vb, a.x};
+  const bool pon[3] = {a.val1 != nullptr, a.val2 != nullptr, fused && a.warm != 0};
   for (int i = i0; i < n; i += stride) {
+    double sp[3];
+    sell_row_multi<3>(a.sptr, a.swidth, a.col, pv, px, pon, i, sp);
     double b = a.rl ? a.rl[i] : 0.0;
-    if (a.val1) b += a.c1 * sell_row<WMAX, false>(a, a.val1, a.va, i);
-    if (a.val2) b += a.c2 * sell_row<WMAX, false>(a, a.val2, a.vb, i);
+    if (a.val1) b += a.c1 * sp[0];
+    if (a.val2) b += a.c2 * sp[1];
     m.b64[i] = b;
     double d = a.valA[a.diagpos[i]];
     if (a.dextra) d += a.dextra[i];
@@ -57,7 +64,7 @@ __global__ void __launch_bounds__(TPB, MINB) pcg_mixed_kernel(const __grid_const
     acc0[1] += b * b;
     if (fused) {
       double r = b;
-      if (a.warm) r = b - ((a.dextra ? a.dextra[i] * a.x[i] : 0.0) + sell_row<WMAX, true>(a, a.valA, a.x, i));
+      if (a.warm) r = b - ((a.dextra ? a.dextra[i] * a.x[i] : 0.0) + sp[2]);
       m.r64[i] = r;
       acc0[2] += r * r;
     }
@@ -144,85 +151,185 @@ __global__ void __launch_bounds__(TPB, MINB) pcg_mixed_kernel(const __grid_const
       m.r32[i] = float(m.r64[i] * inv_scale);
       m.d32[i] = 0.0f;
     }
-    if constexpr (AMG) {
-      if (!vcycle<float, TPB == 512>(M, m.r32, m.z32, a.bar, nb, a.status)) return;
-    } else {
-      for (int i = i0; i < n; i += stride) m.z32[i] = m.invd32[i] * m.r32[i];
-    }
-    float accf[2] = {0.0f, 0.0f};
-    for (int i = i0; i < n; i += stride) {
-      accf[0] += m.r32[i] * m.z32[i];
-      accf[1] += m.r32[i] * m.r32[i];
-    }
-    block_sum<2, float>(accf, shf);
-    if (threadIdx.x == 0) {
-      partf[blockIdx.x * 4 + 2] = accf[0];
-      partf[blockIdx.x * 4 + 3] = accf[1];
-    }
-    if (!grid_barrier(a.bar, nb, a.status)) return;
-    float tf[2];
-    grid_total<2, float>(partf, {2, 3}, nb, tf, shf);
-    float rho = tf[0];
-    float rr = tf[1];
     int it = 0;
-    float beta = 0.0f;
-    bool done = !(rr > target2);
-    while (!done) {
-      float pq[1] = {0.0f};
-      for (int i = i0; i < n; i += stride) {
-        const float z = m.z32[i];
-        float az = a.dextra ? float(a.dextra[i]) * z : 0.0f;
-        az += sell_row<WMAX, true, float>(a.sptr, a.swidth, a.col, m.valA32, m.z32, i);
-        const float p = it == 0 ? z : z + beta * m.p32[i];
-        const float q = it == 0 ? az : az + beta * m.q32[i];
-        m.p32[i] = p;
-        m.q32[i] = q;
-        pq[0] += p * q;
-      }
-      block_sum<1, float>(pq, shf);
-      if (threadIdx.x == 0) partf[blockIdx.x * 4 + 0] = pq[0];
+    if (!AMG && m.pipelined) {
+      // Pipelined Jacobi-PCG (Ghysels & Vanroose, Parallel Computing 40, 2014):
+      // the recurrences w = A u, s = A p, q = M s and z = A q let ONE device
+      // barrier per iteration carry both the dot products (r, u), (w, u),
+      // (r, r) and the input m = M w of the next product A m.  m is double
+      // buffered (neighbours read it while its successor is written); the
+      // per-block partial sums alternate between two slot groups.  Its
+      // recursively updated residual drifts from b - A d faster than the
+      // classic one's, so the host asks for it only for the well-conditioned
+      // parabolic systems in the latency-bound 128-register build.
+      float* const r = m.r32;
+      float* const u = m.r32 + n;
+      float* const w = m.z32;
+      float* const z = m.z32 + n;
+      float* const p = m.p32;
+      float* const s = m.p32 + n;
+      float* const q = m.q32;
+      float* const d = m.d32;
+      float* const mb[2] = {m.q32 + n, m.d32 + n};
+      for (int i = i0; i < n; i += stride) u[i] = m.invd32[i] * r[i];
       if (!grid_barrier(a.bar, nb, a.status)) return;
-      float tq[1];
-      grid_total<1, float>(partf, {0}, nb, tq, shf);
-      if (!(tq[0] > 0.0f)) {
-        if (!isfinite(tq[0])) fail = ST_NONFINITE;
-        break;     // FP32 breakdown: keep d, the outer step decides
+      {
+        float acc[3] = {0.0f, 0.0f, 0.0f};
+        for (int i = i0; i < n; i += stride) {
+          const float ui = u[i], ri = r[i];
+          float au = a.dextra ? float(a.dextra[i]) * ui : 0.0f;
+          au += sell_row<WMAX, true, float>(a.sptr, a.swidth, a.col, m.valA32, u, i);
+          w[i] = au;
+          mb[0][i] = m.invd32[i] * au;
+          acc[0] += ri * ui;
+          acc[1] += au * ui;
+          acc[2] += ri * ri;
+        }
+        block_sum<3, float>(acc, shf);
+        if (threadIdx.x == 0)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) partf[blockIdx.x * 8 + k] = acc[k];
+        if (!grid_barrier(a.bar, nb, a.status)) return;
       }
-      const float alpha = rho / tq[0];
-      float rrl = 0.0f;
-      for (int i = i0; i < n; i += stride) {
-        m.d32[i] += alpha * m.p32[i];
-        const float r = m.r32[i] - alpha * m.q32[i];
-        m.r32[i] = r;
-        rrl += r * r;
+      float gam_prev = 1.0f, alpha_prev = 1.0f;
+      for (;;) {
+        const int par = it & 1;
+        const int sl[3] = {4 * par, 4 * par + 1, 4 * par + 2};
+        float t[3];
+        grid_total<3, float, 8>(partf, sl, nb, t, shf);
+        const float gam = t[0], del = t[1], rr = t[2];
+        if (!isfinite(rr) || !isfinite(gam) || !isfinite(del)) {
+          fail = ST_NONFINITE;
+          break;
+        }
+        if (!(rr > target2)) break;
+        if (it >= m.inner_cap) {
+          if (m.max_outer == 1) fail = ST_NOT_CONVERGED;
+          break;
+        }
+        const float beta = it == 0 ? 0.0f : gam / gam_prev;
+        const float den = it == 0 ? del : del - beta * gam / alpha_prev;
+        if (!(den > 0.0f)) {
+          if (!isfinite(den)) fail = ST_NONFINITE;
+          break;     // FP32 breakdown: keep d, the outer step decides
+        }
+        const float alpha = gam / den;
+        const float* const mc = mb[par];
+        float* const mn = mb[par ^ 1];
+        float acc[3] = {0.0f, 0.0f, 0.0f};
+        for (int i = i0; i < n; i += stride) {
+          const float mi = mc[i];
+          float ni = a.dextra ? float(a.dextra[i]) * mi : 0.0f;
+          ni += sell_row<WMAX, true, float>(a.sptr, a.swidth, a.col, m.valA32, mc, i);
+          const float zi = it == 0 ? ni : ni + beta * z[i];
+          const float qi = it == 0 ? mi : mi + beta * q[i];
+          const float si = it == 0 ? w[i] : w[i] + beta * s[i];
+          const float pi = it == 0 ? u[i] : u[i] + beta * p[i];
+          z[i] = zi;
+          q[i] = qi;
+          s[i] = si;
+          p[i] = pi;
+          d[i] += alpha * pi;
+          const float ri = r[i] - alpha * si;
+          const float ui = u[i] - alpha * qi;
+          const float wi = w[i] - alpha * zi;
+          r[i] = ri;
+          u[i] = ui;
+          w[i] = wi;
+          mn[i] = m.invd32[i] * wi;
+          acc[0] += ri * ui;
+          acc[1] += wi * ui;
+          acc[2] += ri * ri;
+        }
+        block_sum<3, float>(acc, shf);
+        if (threadIdx.x == 0)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) partf[blockIdx.x * 8 + 4 * (par ^ 1) + k] = acc[k];
+        if (!grid_barrier(a.bar, nb, a.status)) return;
+        gam_prev = gam;
+        alpha_prev = alpha;
+        ++it;
       }
+    } else {
       if constexpr (AMG) {
         if (!vcycle<float, TPB == 512>(M, m.r32, m.z32, a.bar, nb, a.status)) return;
       } else {
         for (int i = i0; i < n; i += stride) m.z32[i] = m.invd32[i] * m.r32[i];
       }
-      float acc[2] = {0.0f, rrl};
-      for (int i = i0; i < n; i += stride) acc[0] += m.r32[i] * m.z32[i];
-      block_sum<2, float>(acc, shf);
+      float accf[2] = {0.0f, 0.0f};
+      for (int i = i0; i < n; i += stride) {
+        accf[0] += m.r32[i] * m.z32[i];
+        accf[1] += m.r32[i] * m.r32[i];
+      }
+      block_sum<2, float>(accf, shf);
       if (threadIdx.x == 0) {
-        partf[blockIdx.x * 4 + 2] = acc[0];
-        partf[blockIdx.x * 4 + 3] = acc[1];
+        partf[blockIdx.x * 4 + 2] = accf[0];
+        partf[blockIdx.x * 4 + 3] = accf[1];
       }
       if (!grid_barrier(a.bar, nb, a.status)) return;
+      float tf[2];
       grid_total<2, float>(partf, {2, 3}, nb, tf, shf);
-      ++it;
-      rr = tf[1];
-      if (!isfinite(rr) || !isfinite(tf[0])) {
-        fail = ST_NONFINITE;
-        break;
+      float rho = tf[0];
+      float rr = tf[1];
+      float beta = 0.0f;
+      bool done = !(rr > target2);
+      while (!done) {
+        float pq[1] = {0.0f};
+        for (int i = i0; i < n; i += stride) {
+          const float z = m.z32[i];
+          float az = a.dextra ? float(a.dextra[i]) * z : 0.0f;
+          az += sell_row<WMAX, true, float>(a.sptr, a.swidth, a.col, m.valA32, m.z32, i);
+          const float p = it == 0 ? z : z + beta * m.p32[i];
+          const float q = it == 0 ? az : az + beta * m.q32[i];
+          m.p32[i] = p;
+          m.q32[i] = q;
+          pq[0] += p * q;
+        }
+        block_sum<1, float>(pq, shf);
+        if (threadIdx.x == 0) partf[blockIdx.x * 4 + 0] = pq[0];
+        if (!grid_barrier(a.bar, nb, a.status)) return;
+        float tq[1];
+        grid_total<1, float>(partf, {0}, nb, tq, shf);
+        if (!(tq[0] > 0.0f)) {
+          if (!isfinite(tq[0])) fail = ST_NONFINITE;
+          break;     // FP32 breakdown: keep d, the outer step decides
+        }
+        const float alpha = rho / tq[0];
+        float rrl = 0.0f;
+        for (int i = i0; i < n; i += stride) {
+          m.d32[i] += alpha * m.p32[i];
+          const float r = m.r32[i] - alpha * m.q32[i];
+          m.r32[i] = r;
+          rrl += r * r;
+        }
+        if constexpr (AMG) {
+          if (!vcycle<float, TPB == 512>(M, m.r32, m.z32, a.bar, nb, a.status)) return;
+        } else {
+          for (int i = i0; i < n; i += stride) m.z32[i] = m.invd32[i] * m.r32[i];
+        }
+        float acc[2] = {0.0f, rrl};
+        for (int i = i0; i < n; i += stride) acc[0] += m.r32[i] * m.z32[i];
+        block_sum<2, float>(acc, shf);
+        if (threadIdx.x == 0) {
+          partf[blockIdx.x * 4 + 2] = acc[0];
+          partf[blockIdx.x * 4 + 3] = acc[1];
+        }
+        if (!grid_barrier(a.bar, nb, a.status)) return;
+        grid_total<2, float>(partf, {2, 3}, nb, tf, shf);
+        ++it;
+        rr = tf[1];
+        if (!isfinite(rr) || !isfinite(tf[0])) {
+          fail = ST_NONFINITE;
+          break;
+        }
+        if (rr <= target2) break;
+        if (it >= m.inner_cap) {
+          if (m.max_outer == 1) fail = ST_NOT_CONVERGED;
+          break;
+        }
+        beta = tf[0] / rho;
+        rho = tf[0];
       }
-      if (rr <= target2) break;
-      if (it >= m.inner_cap) {
-        if (m.max_outer == 1) fail = ST_NOT_CONVERGED;
-        break;
-      }
-      beta = tf[0] / rho;
-      rho = tf[0];
     }
     inner_total += it;
     if (fail) break;
@@ -293,10 +400,14 @@ __global__ void __launch_bounds__(TPB, MINB) pcg_mixed2_kernel(const __grid_cons
 
   // ---- FP64 right-hand sides ----------------------------------------------
   double acc0[4] = {0.0, 0.0, 0.0, 0.0};
+  const double* const v1v[2] = {a.val1, a.val1};
+  const bool both[2] = {true, true};
   for (int i = i0; i < n; i += stride) {
+    double sp[2];
+    sell_row_multi<2>(a.sptr, a.swidth, a.col, v1v, V, both, i, sp);   // both products in one pass
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const double b = a.c1 * sell_row<WMAX, false>(a, a.val1, V[k], i);
+      const double b = a.c1 * sp[k];
       b64[k][i] = b;
       acc0[2 * k] += b;
       acc0[2 * k + 1] += b * b;
@@ -333,11 +444,16 @@ __global__ void __launch_bounds__(TPB, MINB) pcg_mixed2_kernel(const __grid_cons
     ++outer_total;
     // ---- FP64 outer residuals -----------------------------------------------
     double accr[2] = {0.0, 0.0};
+    const double* const vAv[2] = {a.valA, a.valA};
+    const double* const Xc[2] = {X[0], X[1]};
+    const bool prod = !(outer == 0 && !a.warm);
+    const bool on2[2] = {prod, prod};
     for (int i = i0; i < n; i += stride) {
+      double ax[2];
+      sell_row_multi<2>(a.sptr, a.swidth, a.col, vAv, Xc, on2, i, ax);
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
-        const double r = (outer == 0 && !a.warm) ? b64[k][i]
-                                                 : b64[k][i] - sell_row<WMAX, true>(a, a.valA, X[k], i);
+        const double r = prod ? b64[k][i] - ax[k] : b64[k][i];
         r64[k][i] = r;
         accr[k] += r * r;
       }

@@ -43,16 +43,23 @@ __global__ void __launch_bounds__(TPB, BD_SOLVER_MIN_BLOCKS) pcg_kernel(const __
   // and its dot products) runs in the same pass: one device barrier fewer.
   const bool fused = !a.project;
   double acc0[4] = {0.0, 0.0, 0.0, 0.0};
+  // the right-hand side products and the warm residual's A x share the
+  // operator pattern: one pass over each row
+  const double* const pv[3] = {a.val1, a.val2, a.valA};
+  const double* const px[3] = {a.va, a.vb, a.x};
+  const bool pon[3] = {a.val1 != nullptr, a.val2 != nullptr, a.warm != 0};
   for (int i = i0; i < n; i += stride) {
+    double sp[3];
+    sell_row_multi<3>(a.sptr, a.swidth, a.col, pv, px, pon, i, sp);
     double b = a.rl ? a.rl[i] : 0.0;
-    if (a.val1) b += a.c1 * sell_row<WMAX, false>(a, a.val1, a.va, i);
-    if (a.val2) b += a.c2 * sell_row<WMAX, false>(a, a.val2, a.vb, i);
+    if (a.val1) b += a.c1 * sp[0];
+    if (a.val2) b += a.c2 * sp[1];
     double d = a.valA[a.diagpos[i]];
     if (a.dextra) d += a.dextra[i];
     a.invd[i] = 1.0 / d;
     double r = b;
     if (a.warm) {
-      const double ax = (a.dextra ? a.dextra[i] * a.x[i] : 0.0) + sell_row<WMAX, false>(a, a.valA, a.x, i);
+      const double ax = (a.dextra ? a.dextra[i] * a.x[i] : 0.0) + sp[2];
       r -= ax;
     }
     a.r[i] = r;

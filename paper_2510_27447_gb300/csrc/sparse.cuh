@@ -209,6 +209,43 @@ __device__ __forceinline__ T sell_row(const int64_t* __restrict__ sptr, const in
 }
 
 
+// Up to NV products of operators sharing one SELL pattern, out[q] = sum_k
+// val[q][k] x[q][col[k]] for every q with on[q], in one pass over the row:
+// the slice header and the column indices are loaded once, and every sum is
+// formed in the order sell_row forms it (bit-identical).  Vectors are read
+// through L2.
+template <int NV, class T = double>
+__device__ __forceinline__ void sell_row_multi(const int64_t* __restrict__ sptr, const int* __restrict__ swidth,
+                                               const int* __restrict__ colv, const T* const (&val)[NV],
+                                               const T* const (&x)[NV], const bool (&on)[NV], int i, T (&out)[NV]) {
+  const int s = i >> 5;
+  const int64_t base = sptr[s] + (i & 31);
+  const int w = swidth[s];
+  constexpr int CH = BD_SELL_CHUNK;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) out[q] = T(0);
+  for (int k0 = 0; k0 < w; k0 += CH) {
+    int c[CH];
+#pragma unroll
+    for (int k = 0; k < CH; ++k)
+      if (k0 + k < w) c[k] = colv[base + 32 * (k0 + k)];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      if (!on[q]) continue;
+      T v[CH], g[CH];
+#pragma unroll
+      for (int k = 0; k < CH; ++k)
+        if (k0 + k < w) {
+          v[k] = val[q][base + 32 * (k0 + k)];
+          g[k] = __ldcg(x[q] + c[k]);
+        }
+#pragma unroll
+      for (int k = 0; k < CH; ++k)
+        if (k0 + k < w) out[q] += v[k] * g[k];
+    }
+  }
+}
+
 template <int WMAX, bool CROSS>
 __device__ __forceinline__ double sell_row(const PcgLaunch& a, const double* __restrict__ val, const double* x, int i) {
   return sell_row<WMAX, CROSS>(a.sptr, a.swidth, a.col, val, x, i);
