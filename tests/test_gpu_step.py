@@ -227,3 +227,13 @@ def test_amg_solver_builds_match_oracle(cg_block, coarse_max, force, tier):
         u, it = sim.solve_elliptic(v)
         sim.close()
         assert 0 < it < 200 and rel(u, ref) < 1e-9, (prec, it, rel(u, ref))
+
+
+def test_solver_tier_option_is_checked():
+    """solver_tier outside 0..3, or the 512-thread tier with 1024-thread
+    blocks, is refused with BD_ERR_ARG before any solve."""
+    w = W.sheet(9, 0.2, W.LR91, 0.02, 3, strip=0.05)
+    for opt in (dict(solver_tier=4), dict(solver_tier=-1), dict(solver_tier=2, cg_block=1024)):
+        with pytest.raises(binding.BdError) as e:
+            gpu_sim(w, **opt)
+        assert binding.ERRORS[e.value.code] == "BD_ERR_ARG", e.value
