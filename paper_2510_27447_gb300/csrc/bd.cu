@@ -242,8 +242,8 @@ int status_code(int st) {
 
 int read_status(bd_state* s) {
   int st = 0;
+  CK(cudaMemcpyAsync(&st, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  CK(cudaMemcpy(&st, s->d_status, sizeof(int), cudaMemcpyDeviceToHost));
   const int c = status_code(st);
   if (c != BD_OK) {
     const char* what = c == BD_ERR_TIMEOUT ? "a device barrier wait timed out"
@@ -1331,10 +1331,11 @@ int bd_activation_times(const bd_state_t* cs, double* out, int64_t n) {
 int bd_get_fields(const bd_state_t* cs, double* vm, double* phie, double* X) {
   bd_state* s = const_cast<bd_state*>(cs);
   if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
-  CK(cudaStreamSynchronize(s->stream));
-  if (vm) CK(cudaMemcpy(vm, s->Xn, s->NT * 8, cudaMemcpyDeviceToHost));
-  if (phie) CK(cudaMemcpy(phie, s->u[0], s->N * 8, cudaMemcpyDeviceToHost));
-  if (X) CK(cudaMemcpy(X, s->Xn, int64_t(s->ns) * s->NT * 8, cudaMemcpyDeviceToHost));
+  // copies ordered on the handle's stream after the queued steps; one
+  // synchronisation (in read_status) for all of them
+  if (vm) CK(cudaMemcpyAsync(vm, s->Xn, s->NT * 8, cudaMemcpyDeviceToHost, s->stream));
+  if (phie) CK(cudaMemcpyAsync(phie, s->u[0], s->N * 8, cudaMemcpyDeviceToHost, s->stream));
+  if (X) CK(cudaMemcpyAsync(X, s->Xn, int64_t(s->ns) * s->NT * 8, cudaMemcpyDeviceToHost, s->stream));
   return read_status(s);
 }
 
@@ -1362,31 +1363,34 @@ int bd_get_state(const bd_state_t* cs, void* buf, size_t* bytes) {
     return BD_OK;
   }
   if (*bytes < need) return fail(s, BD_ERR_ARG, "buffer too small (%zu < %zu)", *bytes, need);
-  CK(cudaStreamSynchronize(s->stream));
-  char* p = static_cast<char*>(buf);
+  // copies ordered on the handle's stream after the queued steps, one
+  // synchronisation before the header is filled in
+  const cudaStream_t st = s->stream;
+  char* const p0 = static_cast<char*>(buf);
+  char* p = p0 + 64;
   int64_t hdr[8] = {0x62647376, s->model, s->N, 0, 0, 0, 0, 0};
   double clk[3];
-  CK(cudaMemcpy(&hdr[3], s->step_n, 8, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(clk, s->t_now, 24, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpyAsync(&hdr[3], s->step_n, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(clk, s->t_now, 24, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(p, s->Xn, int64_t(s->ns) * s->NT * 8, cudaMemcpyDeviceToHost, st));
+  p += int64_t(s->ns) * s->NT * 8;
+  CK(cudaMemcpyAsync(p, s->u[0], s->N * 8, cudaMemcpyDeviceToHost, st));
+  p += s->N * 8;
+  CK(cudaMemcpyAsync(p, s->t_act, s->NT * 8, cudaMemcpyDeviceToHost, st));
+  p += s->NT * 8;
+  CK(cudaMemcpyAsync(p, s->uprev, s->N * 8, cudaMemcpyDeviceToHost, st));
+  p += s->N * 8;
+  for (int m = 0; m < kMaxNodes - 1; ++m)
+    for (int g = 0; g < 3; ++g) {
+      CK(cudaMemcpyAsync(p, s->kinc[m][g], s->NT * 8, cudaMemcpyDeviceToHost, st));
+      p += s->NT * 8;
+    }
+  CK(cudaStreamSynchronize(st));
   std::memcpy(&hdr[4], &clk[0], 8);
   std::memcpy(&hdr[5], &s->dt_adapt, 8);
   std::memcpy(&hdr[6], &clk[1], 8);
   std::memcpy(&hdr[7], &clk[2], 8);
-  std::memcpy(p, hdr, 64);
-  p += 64;
-  CK(cudaMemcpy(p, s->Xn, int64_t(s->ns) * s->NT * 8, cudaMemcpyDeviceToHost));
-  p += int64_t(s->ns) * s->NT * 8;
-  CK(cudaMemcpy(p, s->u[0], s->N * 8, cudaMemcpyDeviceToHost));
-  p += s->N * 8;
-  CK(cudaMemcpy(p, s->t_act, s->NT * 8, cudaMemcpyDeviceToHost));
-  p += s->NT * 8;
-  CK(cudaMemcpy(p, s->uprev, s->N * 8, cudaMemcpyDeviceToHost));
-  p += s->N * 8;
-  for (int m = 0; m < kMaxNodes - 1; ++m)
-    for (int g = 0; g < 3; ++g) {
-      CK(cudaMemcpy(p, s->kinc[m][g], s->NT * 8, cudaMemcpyDeviceToHost));
-      p += s->NT * 8;
-    }
+  std::memcpy(p0, hdr, 64);
   *bytes = need;
   return BD_OK;
 }
@@ -1401,26 +1405,31 @@ int bd_set_state(bd_state_t* s, const void* buf, size_t bytes) {
   if (hdr[0] != 0x62647376 || hdr[1] != s->model || hdr[2] != s->N)
     return fail(s, BD_ERR_ARG, "state blob belongs to another model or mesh");
   p += 64;
-  CK(cudaStreamSynchronize(s->stream));
-  CK(cudaMemcpy(s->Xn, p, int64_t(s->ns) * s->NT * 8, cudaMemcpyHostToDevice));
+  // every copy is ordered on the handle's stream after the work already
+  // queued; one synchronisation at the end (the caller's buffer and the
+  // header copies on this stack frame are read by then)
+  const cudaStream_t st = s->stream;
+  CK(cudaMemcpyAsync(s->Xn, p, int64_t(s->ns) * s->NT * 8, cudaMemcpyHostToDevice, st));
   p += int64_t(s->ns) * s->NT * 8;
-  for (int m = 0; m < kMaxNodes; ++m) CK(cudaMemcpy(s->u[m], p, s->N * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpyAsync(s->u[0], p, s->N * 8, cudaMemcpyHostToDevice, st));
+  for (int m = 1; m < kMaxNodes; ++m) CK(cudaMemcpyAsync(s->u[m], s->u[0], s->N * 8, cudaMemcpyDeviceToDevice, st));
   p += s->N * 8;
-  CK(cudaMemcpy(s->t_act, p, s->NT * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpyAsync(s->t_act, p, s->NT * 8, cudaMemcpyHostToDevice, st));
   p += s->NT * 8;
-  CK(cudaMemcpy(s->uprev, p, s->N * 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpyAsync(s->uprev, p, s->N * 8, cudaMemcpyHostToDevice, st));
   p += s->N * 8;
   for (int m = 0; m < kMaxNodes - 1; ++m)
     for (int g = 0; g < 3; ++g) {
-      CK(cudaMemcpy(s->kinc[m][g], p, s->NT * 8, cudaMemcpyHostToDevice));
+      CK(cudaMemcpyAsync(s->kinc[m][g], p, s->NT * 8, cudaMemcpyHostToDevice, st));
       p += s->NT * 8;
     }
   double clk[3];
   std::memcpy(&clk[0], &hdr[4], 8);
   std::memcpy(&clk[1], &hdr[6], 8);
   std::memcpy(&clk[2], &hdr[7], 8);
-  CK(cudaMemcpy(s->step_n, &hdr[3], 8, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(s->t_now, clk, 24, cudaMemcpyHostToDevice));
+  CK(cudaMemcpyAsync(s->step_n, &hdr[3], 8, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(s->t_now, clk, 24, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
   std::memcpy(&s->dt_adapt, &hdr[5], 8);
   return BD_OK;
 }
