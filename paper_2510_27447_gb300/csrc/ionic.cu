@@ -91,91 +91,90 @@ __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, cons
     for (int k = 0; k < NS - 1; ++k) L.z[k * n + i] = double(z[k]);
     L.avec[i] = xs[0] + L.u[i];
     if (L.bvec) L.bvec[i] = k1v;
-    return;
-  }
-
-  T xt[NS];
-#pragma unroll
-  for (int k = 0; k < NS; ++k) xt[k] = T(xj[k]);
-
-  JacSink<T, Mod> e;
-  P.eval(xt, T(istim), T(L.inv_cm), e);
-
-  T rho[NS - 1];
-  double fv;                        // node field f_v at the F point
-  double avec = 0.0, bvec = 0.0;
-  if constexpr (MODE == MODE_S1) {
-#pragma unroll
-    for (int k = 1; k < NS; ++k) rho[k - 1] = e.f[k];
-    fv = double(e.f[0]);
-    avec = xj[0] + L.u[i];
-    if (L.pack) cond_store<T, Mod>(e, T(L.alpha), static_cast<T*>(L.pack) + i, n);
-    if (L.fq_out) {
-#pragma unroll
-      for (int k = 0; k < NS; ++k) L.fq_out[k * n + i] = double(e.f[k]);
-    }
-  } else if constexpr (MODE == MODE_S2) {
-    // F point X* = X + k1/gamma, k1_y = z1 + w1 k1_v
-    const double k1v = L.k1v[i];
-    double xs[NS];
-    double k1y[NS - 1];
-    xs[0] = xj[0] + k1v * L.inv_gamma;
-#pragma unroll
-    for (int k = 1; k < NS; ++k) {
-      k1y[k - 1] = L.z1[(k - 1) * n + i] + L.w1[(k - 1) * n + i] * k1v;
-      xs[k] = xj[k] + k1y[k - 1] * L.inv_gamma;
-    }
-    T xst[NS];
-#pragma unroll
-    for (int k = 0; k < NS; ++k) xst[k] = T(xs[k]);
-    ValSink<T, Mod> fs;
-    P.eval(xst, T(istim), T(L.inv_cm), fs);
-#pragma unroll
-    for (int k = 1; k < NS; ++k) rho[k - 1] = T(double(fs.f[k]) - L.ck1 * k1y[k - 1]);
-    fv = double(fs.f[0]);
-    avec = xs[0] + L.u[i];
-    bvec = k1v;
   } else {
-    // correction: rho = [(X_m^new - X~_{m+1}) + sum_j S_j f_j] / dt_m on the y rows
-    double q[NS];
+    T xt[NS];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) q[k] = 0.0;
-    double av = 0.0;
-    // NQ quadrature nodes, known at compile time: the node loop unrolls and
-    // every pointer of L is read at a constant offset
-#pragma unroll
-    for (int jn = 0; jn < NQ; ++jn) {
-      const double S = L.S[jn];
-      const double* fj = L.fq[jn];
-#pragma unroll
-      for (int k = 0; k < NS; ++k) q[k] += S * fj[k * n + i];
-      av += S * (L.Xq[jn][i] + L.uq[jn][i]);
-    }
-#pragma unroll
-    for (int k = 1; k < NS; ++k) rho[k - 1] = T(((L.Xprev[k * n + i] - xj[k]) + q[k]) * L.inv_dt);
-    fv = q[0] * L.inv_dt;
-    avec = av;
-    bvec = L.Xprev[i] - xj[0];
-  }
+    for (int k = 0; k < NS; ++k) xt[k] = T(xj[k]);
 
-  T s, corr;
-  T z[NS - 1], w[NS - 1];
-  condense<T, Mod>(e, T(L.alpha), rho, s, corr, z, w);
-  double sd = double(s);
-  if (sd < L.smin) {
-    sd = L.smin;
-    atomicAdd(L.clamp_count, 1ull);
-  }
-  const double ml = L.ML[i];
-  L.dgs[i] = ml * sd;
-  L.rl[i] = ml * (fv + double(corr));
+    JacSink<T, Mod> e;
+    P.eval(xt, T(istim), T(L.inv_cm), e);
+
+    T rho[NS - 1];
+    double fv;                        // node field f_v at the F point
+    double avec = 0.0, bvec = 0.0;
+    if constexpr (MODE == MODE_S1) {
 #pragma unroll
-  for (int k = 0; k < NS - 1; ++k) {
-    L.z[k * n + i] = double(z[k]);
-    L.w[k * n + i] = double(w[k]);
+      for (int k = 1; k < NS; ++k) rho[k - 1] = e.f[k];
+      fv = double(e.f[0]);
+      avec = xj[0] + L.u[i];
+      if (L.pack) cond_store<T, Mod>(e, T(L.alpha), static_cast<T*>(L.pack) + i, n);
+      if (L.fq_out) {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) L.fq_out[k * n + i] = double(e.f[k]);
+      }
+    } else if constexpr (MODE == MODE_S2) {
+      // F point X* = X + k1/gamma, k1_y = z1 + w1 k1_v
+      const double k1v = L.k1v[i];
+      double xs[NS];
+      double k1y[NS - 1];
+      xs[0] = xj[0] + k1v * L.inv_gamma;
+#pragma unroll
+      for (int k = 1; k < NS; ++k) {
+        k1y[k - 1] = L.z1[(k - 1) * n + i] + L.w1[(k - 1) * n + i] * k1v;
+        xs[k] = xj[k] + k1y[k - 1] * L.inv_gamma;
+      }
+      T xst[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) xst[k] = T(xs[k]);
+      ValSink<T, Mod> fs;
+      P.eval(xst, T(istim), T(L.inv_cm), fs);
+#pragma unroll
+      for (int k = 1; k < NS; ++k) rho[k - 1] = T(double(fs.f[k]) - L.ck1 * k1y[k - 1]);
+      fv = double(fs.f[0]);
+      avec = xs[0] + L.u[i];
+      bvec = k1v;
+    } else {
+      // correction: rho = [(X_m^new - X~_{m+1}) + sum_j S_j f_j] / dt_m on the y rows
+      double q[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) q[k] = 0.0;
+      double av = 0.0;
+      // NQ quadrature nodes, known at compile time: the node loop unrolls and
+      // every pointer of L is read at a constant offset
+#pragma unroll
+      for (int jn = 0; jn < NQ; ++jn) {
+        const double S = L.S[jn];
+        const double* fj = L.fq[jn];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) q[k] += S * fj[k * n + i];
+        av += S * (L.Xq[jn][i] + L.uq[jn][i]);
+      }
+#pragma unroll
+      for (int k = 1; k < NS; ++k) rho[k - 1] = T(((L.Xprev[k * n + i] - xj[k]) + q[k]) * L.inv_dt);
+      fv = q[0] * L.inv_dt;
+      avec = av;
+      bvec = L.Xprev[i] - xj[0];
+    }
+
+    T s, corr;
+    T z[NS - 1], w[NS - 1];
+    condense<T, Mod>(e, T(L.alpha), rho, s, corr, z, w);
+    double sd = double(s);
+    if (sd < L.smin) {
+      sd = L.smin;
+      atomicAdd(L.clamp_count, 1ull);
+    }
+    const double ml = L.ML[i];
+    L.dgs[i] = ml * sd;
+    L.rl[i] = ml * (fv + double(corr));
+#pragma unroll
+    for (int k = 0; k < NS - 1; ++k) {
+      L.z[k * n + i] = double(z[k]);
+      L.w[k * n + i] = double(w[k]);
+    }
+    L.avec[i] = avec;
+    if (L.bvec) L.bvec[i] = bvec;
   }
-  L.avec[i] = avec;
-  if (L.bvec) L.bvec[i] = bvec;
 }
 
 template <template <class> class Model, class T>
