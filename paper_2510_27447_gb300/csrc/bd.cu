@@ -125,6 +125,7 @@ struct bd_state {
   double* t_now = nullptr;                 // clock: t^n, t^{n-1}, previous-step data valid (0/1)
   double* uprev = nullptr;                 // sweep-1 elliptic solution of the previous step
   void* pack = nullptr;                    // stage-1 condensation of the current ROS2 step (stage 2 reuses it)
+  void* jpack = nullptr;                   // node Jacobian at X~_1 (the correction at that state reuses it)
   // adaptive stepping (bd_step_adaptive)
   bool adapt_on = false;                   // the step being enqueued estimates its error
   double adapt_tol = 1.0;
@@ -739,6 +740,8 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       L.w = s->w1;
       L.fq_out = (m >= 1 && s->opts.sdc_correction) ? s->fq[m] : nullptr;
       L.pack = s->pack;
+      // the correction of interval m - 1 takes its Jacobian at this same state
+      L.jac_out = (m >= 1 && s->opts.sdc_correction) ? s->jpack : nullptr;
       {
         Timed t(s, BD_K_IONIC);
         CK(launch_ionic(L, s->stream));
@@ -790,6 +793,8 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
         L.XJ = s->Xt[m + 1];
         L.Xprev = m == 0 ? s->Xn : s->Xc[m];
         L.n_nodes = M;
+        // the predictor of interval m + 1 stored the Jacobian at X~_{m+1}
+        L.jac_in = m + 2 < M ? s->jpack : nullptr;
         for (int j = 0; j < M; ++j) {
           L.S[j] = dt * S[m][j];
           L.Xq[j] = j == 0 ? s->Xn : s->Xt[j];
@@ -1062,7 +1067,9 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
             alloc_n(s, &s->avec, N) && alloc_n(s, &s->bvec, N) && alloc_n(s, &s->cg_r, N) &&
             alloc_n(s, &s->cg_z, N) && alloc_n(s, &s->cg_p, N) && alloc_n(s, &s->cg_q, N) &&
             alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->uprev, N) &&
-            alloc_n(s, reinterpret_cast<double**>(&s->pack), int64_t(cond_pack_values(s->model)) * NT) && alloc_n(s, &s->kinc[0][0], N) &&
+            alloc_n(s, reinterpret_cast<double**>(&s->pack), int64_t(cond_pack_values(s->model)) * NT) &&
+            alloc_n(s, reinterpret_cast<double**>(&s->jpack), int64_t(jac_pack_values(s->model)) * NT) &&
+            alloc_n(s, &s->kinc[0][0], N) &&
             alloc_n(s, &s->kinc[0][1], N) && alloc_n(s, &s->kinc[0][2], N) && alloc_n(s, &s->kinc[1][0], N) &&
             alloc_n(s, &s->kinc[1][1], N) && alloc_n(s, &s->kinc[1][2], N) && alloc_n(s, &s->t_act, NT) &&
             alloc_n(s, &s->stim_bits, NT) &&
@@ -1522,7 +1529,8 @@ size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts
   const double nnz = N * (mesh->dim == 2 ? 7.0 : 15.0);   // P1 node graph, upper estimate for structured meshes
   const double mat = nnz * (4 + 8 * 4 + 8 * 4) + N * (4 * 3 + 8);
   const double st = NT * 8 * (ns * (1 + 3 * kMaxNodes) + 4 * (ns - 1) + 4) + N * 8 * (3 * kMaxNodes + 12);
-  return size_t(mat + st) + (size_t(1) << 20);
+  const double packs = NT * 8.0 * (cond_pack_values(model) + jac_pack_values(model));
+  return size_t(mat + st + packs) + (size_t(1) << 20);
 }
 
 int bd_get_stats(const bd_state_t* cs, bd_stats_t* out) {

@@ -80,9 +80,13 @@ struct IonicLaunch {
   unsigned long long* clamp_count;
   const int* gate;           // optional: kernel does nothing when *gate == 0 (sweep test)
   void* pack;                // S1: store the condensation here (optional); S2P: read it
+  void* jac_out;             // S1 (optional): store the node Jacobian here
+  const void* jac_in;        // correction (optional): node Jacobian at XJ stored by an S1 launch
 };
 // values per node of the stage-1 condensation pack (model, compute type)
 int cond_pack_values(int model);
+// values per node of a stored node Jacobian (model)
+int jac_pack_values(int model);
 
 // launchers (ionic.cu)
 cudaError_t launch_ionic(const IonicLaunch& L, cudaStream_t st);

@@ -97,7 +97,13 @@ __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, cons
     for (int k = 0; k < NS; ++k) xt[k] = T(xj[k]);
 
     JacSink<T, Mod> e;
-    P.eval(xt, T(istim), T(L.inv_cm), e);
+    if (MODE == MODE_CORR && L.jac_in) {
+      // the Jacobian at this state was stored by a predictor launch of this
+      // sweep (same state, time and stimulus): load it, no evaluation
+      jac_load<T, Mod>(e, static_cast<const T*>(L.jac_in) + i, n);
+    } else {
+      P.eval(xt, T(istim), T(L.inv_cm), e);
+    }
 
     T rho[NS - 1];
     double fv;                        // node field f_v at the F point
@@ -108,6 +114,7 @@ __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, cons
       fv = double(e.f[0]);
       avec = xj[0] + L.u[i];
       if (L.pack) cond_store<T, Mod>(e, T(L.alpha), static_cast<T*>(L.pack) + i, n);
+      if (L.jac_out) jac_store<T, Mod>(e, static_cast<T*>(L.jac_out) + i, n);
       if (L.fq_out) {
 #pragma unroll
         for (int k = 0; k < NS; ++k) L.fq_out[k * n + i] = double(e.f[k]);
@@ -383,6 +390,10 @@ cudaError_t launch_ionic_t(const IonicLaunch& L, cudaStream_t st) {
 
 int cond_pack_values(int model) {
   return model == BD_TP06_EPI ? cond_pack_size<TP06<double>>() : cond_pack_size<LR91<double>>();
+}
+
+int jac_pack_values(int model) {
+  return model == BD_TP06_EPI ? jac_pack_size<TP06<double>>() : jac_pack_size<LR91<double>>();
 }
 
 int model_ns(int model) {

@@ -555,6 +555,65 @@ BD_HD void condense(const JacSink<T, Model>& e, T alpha, const T* rho, T& s, T& 
   });
 }
 
+// The node Jacobian itself (every entry of the declared pattern), stored by
+// one membrane kernel and loaded by another that needs the Jacobian at the
+// same state with a different shift.  Slots per node (strided by the node
+// count; entries outside the pattern are neither written nor read):
+//   [0, NS)                 d f_0 / d X_c
+//   [NS, NS + NG)           gate diagonals d g_k / d x_k, k = 1..NG
+//   [NS + NG, NS + 2 NG)    gate d g_k / dV
+//   then NB rows of NS      d f_{NG+1+r} / d X_c
+template <class Model>
+constexpr int jac_pack_size() {
+  return Model::NS + 2 * Model::NG + Model::NB * Model::NS;
+}
+
+template <class T, class Model>
+BD_HD void jac_store(const JacSink<T, Model>& e, T* pk, int64_t stride) {
+  constexpr int NS = Model::NS, NG = Model::NG, NB = Model::NB;
+  for_bits<Model::ROWMASK[0]>([&](auto b) {
+    constexpr int c = decltype(b)::value;
+    pk[c * stride] = e.jv[c];
+  });
+#pragma unroll
+  for (int g = 1; g <= NG; ++g) {
+    pk[(NS + g - 1) * stride] = e.jgd[g];
+    pk[(NS + NG + g - 1) * stride] = e.jgv[g];
+  }
+  auto row = [&](auto rr) {
+    constexpr int r = decltype(rr)::value;
+    for_bits<Model::ROWMASK[NG + 1 + r]>([&](auto b) {
+      constexpr int c = decltype(b)::value;
+      pk[(NS + 2 * NG + r * NS + c) * stride] = e.jb[r][c];
+    });
+  };
+  [&]<int... R>(std::integer_sequence<int, R...>) { (row(std::integral_constant<int, R>{}), ...); }
+  (std::make_integer_sequence<int, NB>{});
+}
+
+template <class T, class Model>
+BD_HD void jac_load(JacSink<T, Model>& e, const T* pk, int64_t stride) {
+  constexpr int NS = Model::NS, NG = Model::NG, NB = Model::NB;
+  for_bits<Model::ROWMASK[0]>([&](auto b) {
+    constexpr int c = decltype(b)::value;
+    e.jv[c] = pk[c * stride];
+  });
+#pragma unroll
+  for (int g = 1; g <= NG; ++g) {
+    e.jgd[g] = pk[(NS + g - 1) * stride];
+    e.jgv[g] = pk[(NS + NG + g - 1) * stride];
+  }
+  auto row = [&](auto rr) {
+    constexpr int r = decltype(rr)::value;
+    for_bits<Model::ROWMASK[NG + 1 + r]>([&](auto b) {
+      constexpr int c = decltype(b)::value;
+      e.jb[r][c] = pk[(NS + 2 * NG + r * NS + c) * stride];
+    });
+  };
+  [&]<int... R>(std::integer_sequence<int, R...>) { (row(std::integral_constant<int, R>{}), ...); }
+  (std::make_integer_sequence<int, NB>{});
+}
+
 // What stage 2 of a ROS2 step needs of stage 1's condensation (same node
 // Jacobian, same shift alpha): stage 1 stores it, stage 2 then solves
 // A z = rho for its new rho without evaluating the Jacobian again.  Layout per
