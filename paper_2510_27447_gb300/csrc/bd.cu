@@ -126,6 +126,7 @@ struct bd_state {
   double* uprev = nullptr;                 // sweep-1 elliptic solution of the previous step
   void* pack = nullptr;                    // stage-1 condensation of the current ROS2 step (stage 2 reuses it)
   void* jpack = nullptr;                   // node Jacobian at X~_1 (the correction at that state reuses it)
+  void* jpack0 = nullptr;                  // node field and Jacobian at X^n (later sweeps' first predictor)
   // adaptive stepping (bd_step_adaptive)
   bool adapt_on = false;                   // the step being enqueued estimates its error
   double adapt_tol = 1.0;
@@ -740,8 +741,14 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       L.w = s->w1;
       L.fq_out = (m >= 1 && s->opts.sdc_correction) ? s->fq[m] : nullptr;
       L.pack = s->pack;
-      // the correction of interval m - 1 takes its Jacobian at this same state
-      L.jac_out = (m >= 1 && s->opts.sdc_correction) ? s->jpack : nullptr;
+      // the correction of interval m - 1 takes its Jacobian at this same
+      // state; at m = 0 (state X^n, the same in every sweep) the first FP64
+      // sweep stores the field and Jacobian and the later sweeps load them
+      // (in FP32 the store costs more than the evaluation it saves)
+      const bool reuse0 = s->precision == BD_FP64 && K > 1;
+      if (m >= 1) L.jac_out = s->opts.sdc_correction ? s->jpack : nullptr;
+      else if (reuse0 && k == 1) L.jac_out = s->jpack0;
+      else if (reuse0) L.jac_in = s->jpack0;
       {
         Timed t(s, BD_K_IONIC);
         CK(launch_ionic(L, s->stream));
@@ -1069,6 +1076,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
             alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->uprev, N) &&
             alloc_n(s, reinterpret_cast<double**>(&s->pack), int64_t(cond_pack_values(s->model)) * NT) &&
             alloc_n(s, reinterpret_cast<double**>(&s->jpack), int64_t(jac_pack_values(s->model)) * NT) &&
+            alloc_n(s, reinterpret_cast<double**>(&s->jpack0), int64_t(jac_pack_values(s->model)) * NT) &&
             alloc_n(s, &s->kinc[0][0], N) &&
             alloc_n(s, &s->kinc[0][1], N) && alloc_n(s, &s->kinc[0][2], N) && alloc_n(s, &s->kinc[1][0], N) &&
             alloc_n(s, &s->kinc[1][1], N) && alloc_n(s, &s->kinc[1][2], N) && alloc_n(s, &s->t_act, NT) &&
@@ -1529,7 +1537,7 @@ size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts
   const double nnz = N * (mesh->dim == 2 ? 7.0 : 15.0);   // P1 node graph, upper estimate for structured meshes
   const double mat = nnz * (4 + 8 * 4 + 8 * 4) + N * (4 * 3 + 8);
   const double st = NT * 8 * (ns * (1 + 3 * kMaxNodes) + 4 * (ns - 1) + 4) + N * 8 * (3 * kMaxNodes + 12);
-  const double packs = NT * 8.0 * (cond_pack_values(model) + jac_pack_values(model));
+  const double packs = NT * 8.0 * (cond_pack_values(model) + 2 * jac_pack_values(model));
   return size_t(mat + st + packs) + (size_t(1) << 20);
 }
 

@@ -80,8 +80,8 @@ struct IonicLaunch {
   unsigned long long* clamp_count;
   const int* gate;           // optional: kernel does nothing when *gate == 0 (sweep test)
   void* pack;                // S1: store the condensation here (optional); S2P: read it
-  void* jac_out;             // S1 (optional): store the node Jacobian here
-  const void* jac_in;        // correction (optional): node Jacobian at XJ stored by an S1 launch
+  void* jac_out;             // S1 (optional): store the node field and Jacobian here
+  const void* jac_in;        // S1, correction (optional): field and Jacobian at XJ stored by an S1 launch
 };
 // values per node of the stage-1 condensation pack (model, compute type)
 int cond_pack_values(int model);

@@ -97,9 +97,12 @@ __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, cons
     for (int k = 0; k < NS; ++k) xt[k] = T(xj[k]);
 
     JacSink<T, Mod> e;
-    if (MODE == MODE_CORR && L.jac_in) {
-      // the Jacobian at this state was stored by a predictor launch of this
-      // sweep (same state, time and stimulus): load it, no evaluation
+    // field and Jacobian at this state may have been stored by an earlier
+    // launch (same state, time and stimulus): load them, no evaluation.  The
+    // FP32 predictor has no load path: it would cost it registers and, at
+    // 66k nodes, its single wave of blocks.
+    constexpr bool kLoad = MODE == MODE_CORR || (MODE == MODE_S1 && sizeof(T) == 8);
+    if (kLoad && L.jac_in) {
       jac_load<T, Mod>(e, static_cast<const T*>(L.jac_in) + i, n);
     } else {
       P.eval(xt, T(istim), T(L.inv_cm), e);
@@ -114,7 +117,9 @@ __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, cons
       fv = double(e.f[0]);
       avec = xj[0] + L.u[i];
       if (L.pack) cond_store<T, Mod>(e, T(L.alpha), static_cast<T*>(L.pack) + i, n);
-      if (L.jac_out) jac_store<T, Mod>(e, static_cast<T*>(L.jac_out) + i, n);
+      // the field goes with the Jacobian only where a later predictor loads
+      // both (FP64); the FP32 predictor keeps fewer values live without it
+      if (L.jac_out) jac_store<T, Mod, sizeof(T) == 8>(e, static_cast<T*>(L.jac_out) + i, n);
       if (L.fq_out) {
 #pragma unroll
         for (int k = 0; k < NS; ++k) L.fq_out[k * n + i] = double(e.f[k]);

@@ -555,20 +555,22 @@ BD_HD void condense(const JacSink<T, Model>& e, T alpha, const T* rho, T& s, T& 
   });
 }
 
-// The node Jacobian itself (every entry of the declared pattern), stored by
-// one membrane kernel and loaded by another that needs the Jacobian at the
-// same state with a different shift.  Slots per node (strided by the node
-// count; entries outside the pattern are neither written nor read):
+// The node field and Jacobian (every entry of the declared pattern), stored
+// by one membrane kernel and loaded by another that needs them at the same
+// state (with the same or another shift).  Slots per node (strided by the
+// node count; Jacobian entries outside the pattern are neither written nor
+// read):
 //   [0, NS)                 d f_0 / d X_c
 //   [NS, NS + NG)           gate diagonals d g_k / d x_k, k = 1..NG
 //   [NS + NG, NS + 2 NG)    gate d g_k / dV
 //   then NB rows of NS      d f_{NG+1+r} / d X_c
+//   then NS                 the field f
 template <class Model>
 constexpr int jac_pack_size() {
-  return Model::NS + 2 * Model::NG + Model::NB * Model::NS;
+  return Model::NS + 2 * Model::NG + Model::NB * Model::NS + Model::NS;
 }
 
-template <class T, class Model>
+template <class T, class Model, bool WITH_F = true>
 BD_HD void jac_store(const JacSink<T, Model>& e, T* pk, int64_t stride) {
   constexpr int NS = Model::NS, NG = Model::NG, NB = Model::NB;
   for_bits<Model::ROWMASK[0]>([&](auto b) {
@@ -589,6 +591,10 @@ BD_HD void jac_store(const JacSink<T, Model>& e, T* pk, int64_t stride) {
   };
   [&]<int... R>(std::integer_sequence<int, R...>) { (row(std::integral_constant<int, R>{}), ...); }
   (std::make_integer_sequence<int, NB>{});
+  if constexpr (WITH_F) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) pk[(NS + 2 * NG + NB * NS + k) * stride] = e.f[k];
+  }
 }
 
 template <class T, class Model>
@@ -612,6 +618,8 @@ BD_HD void jac_load(JacSink<T, Model>& e, const T* pk, int64_t stride) {
   };
   [&]<int... R>(std::integer_sequence<int, R...>) { (row(std::integral_constant<int, R>{}), ...); }
   (std::make_integer_sequence<int, NB>{});
+#pragma unroll
+  for (int k = 0; k < NS; ++k) e.f[k] = pk[(NS + 2 * NG + NB * NS + k) * stride];
 }
 
 // What stage 2 of a ROS2 step needs of stage 1's condensation (same node
