@@ -280,6 +280,11 @@ size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts
 
 int bd_get_stats(const bd_state_t* s, bd_stats_t* out);
 
+/* Sizes in bytes of the public structs as this library was compiled (a
+ * binding compares them with its own layouts); NULL arguments are skipped.
+ * Host only; returns BD_OK. */
+int bd_struct_sizes(size_t* mesh, size_t* cond, size_t* opts, size_t* stats);
+
 /* Allocation-free variant of bd_solve_elliptic for callers that must not
  * allocate GPU memory during the call -- for example code running under an
  * external memory budget or allocator, or a latency-critical loop that cannot

@@ -27,7 +27,7 @@ EXPORTS = ["bd_default_options", "bd_create", "bd_add_stimulus", "bd_set_initial
            "bd_ionic_eval", "bd_ionic_pattern", "bd_rest_state", "bd_operator_csr",
            "bd_solve_elliptic", "bd_profile_steps", "bd_solve_elliptic_noalloc", "bd_query",
            "bd_step_adaptive", "bd_get_time", "bd_num_tissue_nodes", "bd_step_decoupled",
-           "bd_selftest_wait_timeout"]
+           "bd_selftest_wait_timeout", "bd_struct_sizes"]
 
 
 class LibraryMissing(RuntimeError):
@@ -117,6 +117,7 @@ def lib():
         "bd_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
         "bd_footprint_bytes": (C.c_size_t, [P(Mesh), C.c_int, P(Opts)]),
         "bd_get_stats": (C.c_int, [C.c_void_p, P(Stats)]),
+        "bd_struct_sizes": (C.c_int, [P(C.c_size_t)] * 4),
         "bd_reset_stats": (C.c_int, [C.c_void_p]),
         "bd_num_nodes": (C.c_int64, [C.c_void_p]),
         "bd_num_tissue_nodes": (C.c_int64, [C.c_void_p]),

@@ -1541,6 +1541,14 @@ size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts
   return size_t(mat + st + packs) + (size_t(1) << 20);
 }
 
+int bd_struct_sizes(size_t* mesh, size_t* cond, size_t* opts, size_t* stats) {
+  if (mesh) *mesh = sizeof(bd_mesh_t);
+  if (cond) *cond = sizeof(bd_cond_t);
+  if (opts) *opts = sizeof(bd_opts_t);
+  if (stats) *stats = sizeof(bd_stats_t);
+  return BD_OK;
+}
+
 int bd_get_stats(const bd_state_t* cs, bd_stats_t* out) {
   bd_state* s = const_cast<bd_state*>(cs);
   if (!s || !out) return fail(s, BD_ERR_ARG, "NULL argument");

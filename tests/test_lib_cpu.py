@@ -118,3 +118,14 @@ def test_bath_footprint_counts_tissue_state_only(lib):
     with_bath = binding.footprint_bytes(w.xyz, w.elems, binding.TP06_EPI, None, w.elem_bath)
     all_tissue = binding.footprint_bytes(w.xyz, w.elems, binding.TP06_EPI)
     assert with_bath < 0.7 * all_tissue
+
+
+def test_struct_layouts_match_the_library(lib):
+    """The binding's ctypes layouts of the public structs have the sizes the
+    library was compiled with (a field added on one side only would shift
+    every later field)."""
+    sz = [ctypes.c_size_t(0) for _ in range(4)]
+    assert lib.bd_struct_sizes(*[ctypes.byref(x) for x in sz]) == 0
+    ours = [ctypes.sizeof(binding.Mesh), ctypes.sizeof(binding.Cond), ctypes.sizeof(binding.Opts),
+            ctypes.sizeof(binding.Stats)]
+    assert [x.value for x in sz] == ours
