@@ -21,6 +21,7 @@
 // right-hand side orthogonal to 1.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <thread>
@@ -49,14 +50,26 @@ void par_rows(int64_t n, F&& fn) {
   for (auto& x : th) x.join();
 }
 
-// C = A * B (row-wise, dense marker accumulator per thread)
+// C = A * B (row-wise, dense marker accumulator per thread).  Each thread
+// writes its rows contiguously into its own arrays (no per-row heap
+// blocks); the row pieces are then stitched by row pointer.
 HCsr spgemm(const HCsr& A, const HCsr& B) {
   HCsr C;
   C.n = A.n;
   C.m = B.m;
-  std::vector<std::vector<int32_t>> rc(A.n);
-  std::vector<std::vector<double>> rv(A.n);
+  struct Piece {
+    int64_t lo = 0, hi = 0;
+    std::vector<int64_t> len;
+    std::vector<int32_t> ci;
+    std::vector<double> v;
+  };
+  std::vector<Piece> pieces;
+  std::mutex mu;
   par_rows(A.n, [&](int64_t lo, int64_t hi) {
+    Piece pc;
+    pc.lo = lo;
+    pc.hi = hi;
+    pc.len.resize(hi - lo);
     std::vector<int64_t> mark(B.m, -1);
     std::vector<double> acc(B.m, 0.0);
     std::vector<int32_t> cols;
@@ -76,18 +89,24 @@ HCsr spgemm(const HCsr& A, const HCsr& B) {
         }
       }
       std::sort(cols.begin(), cols.end());
-      rc[i] = cols;
-      rv[i].resize(cols.size());
-      for (size_t t = 0; t < cols.size(); ++t) rv[i][t] = acc[cols[t]];
+      pc.len[i - lo] = int64_t(cols.size());
+      for (int32_t j : cols) {
+        pc.ci.push_back(j);
+        pc.v.push_back(acc[j]);
+      }
     }
+    std::lock_guard<std::mutex> g(mu);
+    pieces.push_back(std::move(pc));
   });
   C.rp.assign(A.n + 1, 0);
-  for (int64_t i = 0; i < A.n; ++i) C.rp[i + 1] = C.rp[i] + int64_t(rc[i].size());
+  for (const Piece& pc : pieces)
+    for (int64_t i = pc.lo; i < pc.hi; ++i) C.rp[i + 1] = pc.len[i - pc.lo];
+  for (int64_t i = 0; i < A.n; ++i) C.rp[i + 1] += C.rp[i];
   C.ci.resize(C.rp[A.n]);
   C.v.resize(C.rp[A.n]);
-  for (int64_t i = 0; i < A.n; ++i) {
-    std::copy(rc[i].begin(), rc[i].end(), C.ci.begin() + C.rp[i]);
-    std::copy(rv[i].begin(), rv[i].end(), C.v.begin() + C.rp[i]);
+  for (const Piece& pc : pieces) {
+    std::copy(pc.ci.begin(), pc.ci.end(), C.ci.begin() + C.rp[pc.lo]);
+    std::copy(pc.v.begin(), pc.v.end(), C.v.begin() + C.rp[pc.lo]);
   }
   return C;
 }
@@ -130,11 +149,13 @@ double rho_dinv_a(const HCsr& A, const std::vector<double>& d, int iters) {
     nrm = std::sqrt(nrm);
     if (!(nrm > 0)) break;
     for (auto& v : x) v /= nrm;
-    for (int64_t i = 0; i < A.n; ++i) {
-      double s = 0.0;
-      for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) s += A.v[p] * x[A.ci[p]];
-      y[i] = s / d[i];
-    }
+    par_rows(A.n, [&](int64_t lo, int64_t hi) {   // rows are independent; the sums below stay serial
+      for (int64_t i = lo; i < hi; ++i) {
+        double s = 0.0;
+        for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) s += A.v[p] * x[A.ci[p]];
+        y[i] = s / d[i];
+      }
+    });
     double num = 0.0;
     for (int64_t i = 0; i < A.n; ++i) num += x[i] * y[i];
     lam = num;
@@ -272,11 +293,23 @@ int amg_build(const HCsr& A0, const AmgParams& prm, AmgHost* out, std::string* e
     P.m = nc;
     P.rp.assign(A.n + 1, 0);
     {
-      std::vector<std::vector<int32_t>> rc(A.n);
-      std::vector<std::vector<double>> rv(A.n);
+      // rows built per thread into contiguous pieces, then stitched
+      struct Piece {
+        int64_t lo = 0, hi = 0;
+        std::vector<int64_t> len;
+        std::vector<int32_t> ci;
+        std::vector<double> v;
+      };
+      std::vector<Piece> pieces;
+      std::mutex mu;
       par_rows(A.n, [&](int64_t lo, int64_t hi) {
+        Piece pc;
+        pc.lo = lo;
+        pc.hi = hi;
+        pc.len.resize(hi - lo);
         std::vector<int32_t> cols;
         std::vector<double> vals;
+        std::vector<size_t> ord;
         for (int64_t i = lo; i < hi; ++i) {
           cols.clear();
           vals.clear();
@@ -291,21 +324,26 @@ int amg_build(const HCsr& A0, const AmgParams& prm, AmgHost* out, std::string* e
           };
           add(agg[i], 1.0);
           for (int64_t p = A.rp[i]; p < A.rp[i + 1]; ++p) add(agg[A.ci[p]], -w * A.v[p] / d[i]);
-          std::vector<size_t> ord(cols.size());
+          ord.resize(cols.size());
           std::iota(ord.begin(), ord.end(), 0);
           std::sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return cols[x] < cols[y]; });
+          pc.len[i - lo] = int64_t(cols.size());
           for (size_t t : ord) {
-            rc[i].push_back(cols[t]);
-            rv[i].push_back(vals[t]);
+            pc.ci.push_back(cols[t]);
+            pc.v.push_back(vals[t]);
           }
         }
+        std::lock_guard<std::mutex> g(mu);
+        pieces.push_back(std::move(pc));
       });
-      for (int64_t i = 0; i < A.n; ++i) P.rp[i + 1] = P.rp[i] + int64_t(rc[i].size());
+      for (const Piece& pc : pieces)
+        for (int64_t i = pc.lo; i < pc.hi; ++i) P.rp[i + 1] = pc.len[i - pc.lo];
+      for (int64_t i = 0; i < A.n; ++i) P.rp[i + 1] += P.rp[i];
       P.ci.resize(P.rp[A.n]);
       P.v.resize(P.rp[A.n]);
-      for (int64_t i = 0; i < A.n; ++i) {
-        std::copy(rc[i].begin(), rc[i].end(), P.ci.begin() + P.rp[i]);
-        std::copy(rv[i].begin(), rv[i].end(), P.v.begin() + P.rp[i]);
+      for (const Piece& pc : pieces) {
+        std::copy(pc.ci.begin(), pc.ci.end(), P.ci.begin() + P.rp[pc.lo]);
+        std::copy(pc.v.begin(), pc.v.end(), P.v.begin() + P.rp[pc.lo]);
       }
     }
     HCsr R = transpose(P);
