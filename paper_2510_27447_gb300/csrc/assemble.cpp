@@ -187,21 +187,30 @@ int assemble_host(const bd_mesh_t* mesh, const bd_cond_t* cond, HostOps* out, st
   // CSR pattern: sorted union of the element neighbours of each node
   out->n = N;
   out->rowptr.assign(N + 1, 0);
-  std::vector<std::vector<int32_t>> rows(N);
-  par(N, [&](int64_t lo, int64_t hi, unsigned) {
+  // each thread writes its rows' columns contiguously into its own piece
+  // (no per-row heap blocks), the pieces are stitched by row pointer
+  std::vector<std::vector<int32_t>> piece(nthreads);
+  std::vector<int64_t> piece_lo(nthreads, 0);
+  par(N, [&](int64_t lo, int64_t hi, unsigned t) {
     std::vector<int32_t> tmp;
+    std::vector<int32_t>& pc = piece[t];
+    piece_lo[t] = lo;
     for (int64_t i = lo; i < hi; ++i) {
       tmp.clear();
       for (int64_t q = nep[i]; q < nep[i + 1]; ++q)
         for (int a = 0; a < k; ++a) tmp.push_back(mesh->elems[nel[q] * k + a]);
       std::sort(tmp.begin(), tmp.end());
       tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
-      rows[i] = tmp;
+      out->rowptr[i + 1] = int32_t(tmp.size());
+      pc.insert(pc.end(), tmp.begin(), tmp.end());
     }
   });
-  for (int64_t i = 0; i < N; ++i) out->rowptr[i + 1] = out->rowptr[i] + int32_t(rows[i].size());
+  for (int64_t i = 0; i < N; ++i) out->rowptr[i + 1] += out->rowptr[i];
   const int64_t nnz = out->rowptr[N];
   out->col.resize(nnz);
+  for (unsigned t = 0; t < nthreads; ++t)
+    if (!piece[t].empty()) std::copy(piece[t].begin(), piece[t].end(), out->col.begin() + out->rowptr[piece_lo[t]]);
+  piece.clear();
   out->Ai.assign(nnz, 0.0);
   out->Aie.assign(nnz, 0.0);
   out->M.assign(nnz, 0.0);
@@ -212,9 +221,9 @@ int assemble_host(const bd_mesh_t* mesh, const bd_cond_t* cond, HostOps* out, st
   par(N, [&](int64_t lo, int64_t hi, unsigned) {
     for (int64_t i = lo; i < hi; ++i) {
       const int64_t r0 = out->rowptr[i];
-      const auto& cols = rows[i];
-      std::memcpy(&out->col[r0], cols.data(), cols.size() * sizeof(int32_t));
-      out->diagpos[i] = int32_t(r0 + (std::lower_bound(cols.begin(), cols.end(), int32_t(i)) - cols.begin()));
+      const int32_t* const cb = out->col.data() + r0;
+      const int32_t* const ce = out->col.data() + out->rowptr[i + 1];
+      out->diagpos[i] = int32_t(r0 + (std::lower_bound(cb, ce, int32_t(i)) - cb));
       ElemGeom G;
       double Si[9], Sie[9];
       for (int64_t q = nep[i]; q < nep[i + 1]; ++q) {
@@ -224,7 +233,7 @@ int assemble_host(const bd_mesh_t* mesh, const bd_cond_t* cond, HostOps* out, st
         while (en[la] != i) ++la;
         element(e, &G, Si, Sie);
         for (int b = 0; b < k; ++b) {
-          const int64_t p = r0 + (std::lower_bound(cols.begin(), cols.end(), en[b]) - cols.begin());
+          const int64_t p = r0 + (std::lower_bound(cb, ce, en[b]) - cb);
           double si = 0.0, sie = 0.0;
           for (int r = 0; r < dim; ++r)
             for (int c = 0; c < dim; ++c) {
