@@ -62,3 +62,22 @@ def test_mixed_config0_meets_stated_tolerances():
     cv = OB.conduction_velocity(w.xyz, ta, 0.5, 0.3)
     cv_ref = OB.conduction_velocity(w.xyz, ref["t_act"], 0.5, 0.3)
     assert abs(cv - cv_ref) / cv_ref < 0.01
+
+
+@pytest.mark.parametrize("force,tier", [(0, 1), (1, 0), (3, 2)])
+def test_mixed_amg_steps_in_every_solver_tier(force, tier):
+    """Mixed steps on a mesh with an AMG hierarchy (the sweep-2 elliptic pair
+    runs in the two-RHS kernel) in each register tier, forced where the mesh
+    would not pick it: within the mixed tolerance of the FP64 oracle."""
+    w = W.sheet(41, 0.4, W.LR91, 0.02, 10, strip=0.06)
+    X0 = rest_X(w)
+    Xo, uo, _ = OB.run(oracle_problem(w), X0, w.n_steps, w.dt, 3, 2)
+    sim = gpu_sim(w, precision=binding.MIXED, solver_tier=force)
+    st = sim.stats()
+    assert st["solver_tier"] == tier and st["amg_levels"] >= 1, st
+    sim.set_initial(X0)
+    for _ in range(w.n_steps):
+        sim.step(w.dt)
+    v, u, X = sim.fields(full=True)
+    sim.close()
+    assert rel(v, Xo[0]) < 1e-3 and rel(u, uo) < 1e-3
