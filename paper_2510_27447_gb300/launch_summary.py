@@ -1,7 +1,7 @@
 """Summarise an `ncu --metrics gpu__time_duration.sum --csv` launch list:
 per kernel (demangled short name) its launches, total time and share.
 
-usage: python -m paper_2510_27447_gb300.launch_summary <launches.csv>
+usage: python -m paper_2510_27447_gb300.launch_summary <launches.csv> [--markdown]
 """
 import csv
 import re
@@ -28,7 +28,7 @@ def short(name: str) -> str:
     return name[:60]
 
 
-def main(path):
+def main(path, markdown=False):
     tot = defaultdict(float)
     cnt = defaultdict(int)
     with open(path) as fh:
@@ -43,11 +43,19 @@ def main(path):
         tot[k] += v * scale
         cnt[k] += 1
     all_us = sum(tot.values())
+    order = sorted(tot, key=lambda x: -tot[x])
+    if markdown:
+        print("| kernel | launches | total us | share |")
+        print("|---|---|---|---|")
+        for k in order:
+            print(f"| `{k}` | {cnt[k]} | {tot[k]:.1f} | {100 * tot[k] / all_us:.2f}% |")
+        print(f"| TOTAL | {sum(cnt.values())} | {all_us:.1f} | |")
+        return
     print(f"{'kernel':52s} {'launches':>8s} {'total us':>12s} {'share':>7s}")
-    for k in sorted(tot, key=lambda x: -tot[x]):
+    for k in order:
         print(f"{k:52s} {cnt[k]:8d} {tot[k]:12.1f} {100 * tot[k] / all_us:6.2f}%")
     print(f"{'TOTAL':52s} {sum(cnt.values()):8d} {all_us:12.1f}")
 
 
 if __name__ == "__main__":
-    main(sys.argv[1])
+    main(sys.argv[1], markdown="--markdown" in sys.argv[2:])
