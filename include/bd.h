@@ -173,10 +173,21 @@ typedef struct {
   int64_t cg_solves[2];
   int64_t outer_iters[2];       /* FP64 residual passes (mixed path: refinement steps) */
   int64_t nnz;                  /* nonzeros of the shared operator pattern */
-  double alg_bytes[2];          /* algorithmic DRAM bytes of all elliptic / parabolic solves:
-                                   every operator value, index and vector element the
-                                   algorithm must move once per use (SpMV: values + indices
-                                   + one gather of x; vectors: each stream read or written) */
+  double alg_bytes[2];          /* algorithmic DRAM bytes of all elliptic / parabolic solves,
+                                   Krylov level only: every SpMV moves (vb + 4) bytes per
+                                   nonzero and 2 vb + 4 per row (value and column index per
+                                   entry; one gather of x, the result and a row pointer per
+                                   row), every CG iteration 16 vb bytes per row of vector
+                                   streams (13 vb with the AMG preconditioner, whose work is
+                                   counted below), every solve its FP64 right-hand-side
+                                   products and set-up passes, every mixed refinement pass an
+                                   FP64 residual product; vb = 4 (mixed) or 8 (FP64) */
+  double vcycle_bytes;          /* elliptic AMG V-cycles of the profiled steps, counted the same
+                                   way: per smoothed level two products with A_l and one each
+                                   with R_l and P_l plus the level's vector streams (operators
+                                   read once for both systems of a two-RHS iteration) */
+  double coarse_bytes;          /* ... their dense coarsest-level solves (nc^2 + 2 nc values
+                                   per cycle): a dense equivalent, reported apart */
 } bd_profile_t;
 
 void bd_default_options(bd_opts_t* opts);
@@ -292,7 +303,13 @@ int bd_struct_sizes(size_t* mesh, size_t* cond, size_t* opts, size_t* stats);
  * paper has no counterpart; this is a service of the library.
  *
  * Solves A_ie u = -A_i v by Jacobi-preconditioned CG (whatever the handle's
- * elliptic_precond) with the handle's resident operators, tolerance and pin:
+ * elliptic_precond and precision: the solve is FP64) with the handle's
+ * resident operators, tolerance and pin.  It is not part of a time step: a
+ * device-side sweep test (sweep_tol > 0) that closed the sweeps of the last
+ * bd_step does not affect it.  Every call runs on the handle's device (the
+ * one current at bd_create), which it makes current for the call and then
+ * restores, so the caller may have another device current; the pointers
+ * below are memory of the handle's device:
  * v_dev (n_nodes doubles, device; with a bath the entries of bath nodes are
  * multiplied by zero and must be finite) is read, u_dev (n_nodes doubles,
  * device) is written, u_guess_dev (device, n_nodes) warm-starts the iteration
@@ -303,8 +320,8 @@ int bd_struct_sizes(size_t* mesh, size_t* cond, size_t* opts, size_t* stats);
  * meshes return BD_ERR_ARG.
  *
  * The first call on a device looks up that array's device address (with the
- * handle's device current) and caches it, so the first call should come
- * before any stream capture.  Every call shares the array: the words that must
+ * handle's device current) and caches it per device, so the first call on
+ * each device should come before any stream capture.  Every call shares the array: the words that must
  * start at zero are cleared at the start of each call, and calls that overlap
  * on the GPU (on different streams or handles) race with each other.  The call
  * runs on the handle's stream and waits for it; *iters (if not NULL) receives

@@ -58,6 +58,7 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocWords];
 
 struct bd_state {
   int model = 0, ns = 0, dim = 0, precision = 0;
+  int device = 0;                 // CUDA device current at bd_create (the handle's device)
   int64_t N = 0, nnz = 0;
   int64_t NT = 0;                 // tissue nodes (v, membrane state); N - NT bath nodes follow them
   int64_t nnz_t = 0;              // nonzeros of the tissue block (rows and columns < NT)
@@ -93,8 +94,9 @@ struct bd_state {
   int mixed_amg_grid = 1;                  // grid of the mixed AMG kernels (differs in tier 2)
   int amg_grid = 1;
   int amg_levels = 0;
-  double amg_cycle_bytes[2] = {0.0, 0.0};   // algorithmic bytes of one V-cycle (FP64, FP32 values)
+  double amg_cycle_bytes[2] = {0.0, 0.0};   // algorithmic bytes of one V-cycle's smoothed levels (FP64, FP32)
   double amg_cycle_opbytes[2] = {0.0, 0.0}; // ... of which operator values and indices
+  double amg_coarse_bytes[2] = {0.0, 0.0};  // dense coarsest-level solve of one cycle
   double *Ai = nullptr, *Aie = nullptr, *Mv = nullptr, *Mc = nullptr, *ML = nullptr;
   struct PC { double alpha; double* val; };
   std::vector<PC> pcache;
@@ -625,16 +627,18 @@ int setup_amg(bd_state* s, const HostOps& H) {
       const AmgHostLevel& Lh = AH.lev[l];
       const double n = double(Lh.A.n), nn = double(Lh.P.m);
       ob += double(2 * Lh.A.ci.size() + Lh.R.ci.size() + Lh.P.ci.size()) * (vb + 4);
-      const double spA = double(Lh.A.ci.size()) * (vb + 4) + n * vb;
-      const double spR = double(Lh.R.ci.size()) * (vb + 4) + n * vb;
-      const double spP = double(Lh.P.ci.size()) * (vb + 4) + nn * vb;
+      // one product y = B x: (vb + 4) per entry, gather of x + result + row pointer per row
+      const double spA = double(Lh.A.ci.size()) * (vb + 4) + n * (2 * vb + 4);
+      const double spR = double(Lh.R.ci.size()) * (vb + 4) + nn * (vb + 4) + n * vb;
+      const double spP = double(Lh.P.ci.size()) * (vb + 4) + n * (vb + 4) + nn * vb;
       // 2 A products (residual, post-smoothing), R, P; vector streams of the
-      // pre-smoothing, residual, restriction, prolongation and post-smoothing
-      b += 2 * spA + spR + spP + vb * (3 * n + 2 * n + 3 * nn + 2 * n + 4 * n);
+      // pre-smoothing (b, 1/D in, x out), residual (b in), prolongation (x in
+      // and out) and post-smoothing (b, 1/D in, y out)
+      b += 2 * spA + spR + spP + vb * (3 * n + n + 2 * n + 3 * n);
     }
     const double nc = double(AH.nc);
-    b += vb * (nc * nc + 2 * nc);
     s->amg_cycle_bytes[v] = b;
+    s->amg_coarse_bytes[v] = vb * (nc * nc + 2 * nc);
     s->amg_cycle_opbytes[v] = ob + vb * nc * nc;
   }
   s->amg_levels = M.nlev;
@@ -1052,6 +1056,11 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     return fail(nullptr, BD_ERR_ARG, "operator too large for 32-bit SELL offsets");
   }
 
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return fail(nullptr, BD_ERR_CUDA, "cudaGetDevice failed (no CUDA device?)");
+  }
   if (s->opts.stream) {
     s->stream = static_cast<cudaStream_t>(s->opts.stream);
   } else {
@@ -1582,9 +1591,20 @@ int bd_solve_elliptic_noalloc(bd_state_t* s, const double* v_dev, const double* 
     return fail(s, BD_ERR_ARG, "bd_solve_elliptic_noalloc supports at most %lld nodes (mesh has %lld)",
                 (long long)kNoAllocRows, (long long)s->N);
   if (s->pcg_grid > kNoAllocBlocks) return fail(s, BD_ERR_ARG, "CG grid larger than the fixed scratch allows");
-  int dev = 0;
-  CK(cudaGetDevice(&dev));
+  const int dev = s->device;
   if (dev < 0 || dev >= 64) return fail(s, BD_ERR_ARG, "device ordinal out of range");
+  // the scratch array and the launch belong to the handle's device: make it
+  // current for the call and restore the caller's device afterwards
+  int prev = 0;
+  CK(cudaGetDevice(&prev));
+  if (prev != dev) CK(cudaSetDevice(dev));
+  struct Restore {
+    int d;
+    bool on;
+    ~Restore() {
+      if (on) cudaSetDevice(d);
+    }
+  } restore{prev, prev != dev};
   double* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(mu);
@@ -1604,6 +1624,9 @@ int bd_solve_elliptic_noalloc(bd_state_t* s, const double* v_dev, const double* 
   if (u_guess_dev && u_guess_dev != u_dev)
     CK(cudaMemcpyAsync(u_dev, u_guess_dev, s->N * 8, cudaMemcpyDeviceToDevice, s->stream));
   PcgLaunch P = pcg_base(s);
+  // not part of an SDC step: the sweep test's gate (which a step may have
+  // closed) must not turn this solve into a no-op
+  P.gate = nullptr;
   P.r = base;
   P.z = base + kNoAllocRows;
   P.p = base + 2 * kNoAllocRows;
@@ -1673,28 +1696,38 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
   // algorithmic bytes (see bd_profile_t); vb = bytes per value of the Krylov iteration
   const bool mixed = s->precision == BD_MIXED;
   const double vb = mixed ? 4.0 : 8.0;
+  const double pairs = double(st1[7] - st0[7]);     // two-RHS iterations in which both systems advanced
   for (int k = 0; k < 2; ++k) {
     const bool ell = k == 0;
     // elliptic: all nodes and the whole pattern; parabolic: the tissue block
     const double n = double(ell ? s->N : s->NT), nnz = double(ell ? s->nnz : s->nnz_t);
-    auto spmv = [&](double v) { return nnz * (v + 4) + n * v; };
+    auto spmv = [&](double v) { return nnz * (v + 4) + n * (2 * v + 4); };
     const double iters = double(out->cg_iters[k]), solves = double(out->cg_solves[k]);
-    const double extra = ell ? 0.0 : 8.0 * n;                       // condensed diagonal
-    double per_iter = spmv(vb) + 13.0 * vb * n + extra;
-    if (ell && s->use_amg) per_iter += s->amg_cycle_bytes[mixed ? 1 : 0] - 2.0 * vb * n;  // cycle replaces 1/D r
-    const double per_solve = (ell ? 1.0 : 2.0) * spmv(8.0) + 5.0 * 8.0 * n + extra;
+    const double extra = ell ? 0.0 : 8.0 * n;                        // condensed diagonal
+    const double vec = (ell && s->use_amg ? 13.0 : 16.0) * vb * n;   // dots, axpys, (Jacobi)
+    const double per_iter = spmv(vb) + vec + extra;
+    // per solve: right-hand-side products (elliptic A_i v; parabolic A_i a, M b, rl),
+    // the set-up passes (rhs, 1/D, x, r) and, elliptic, projection and pin shift
+    const double per_solve = (ell ? 1.0 : 2.0) * spmv(8.0) + (ell ? 7.0 : 5.0) * 8.0 * n + extra;
     double b = solves * per_solve + iters * per_iter;
     if (mixed) {
       const double outer = double(out->outer_iters[k]);
-      b += outer * (ell ? spmv(8.0) + 3.0 * 8.0 * n : 2.0 * 8.0 * n) + outer * 12.0 * n;  // FP64 residual + conversion
+      // FP64 residual product and streams (b, x in, r out), FP32 scaling (r in,
+      // r32 and d32 out) and the update x += s d (x in and out, d in)
+      b += outer * ((ell ? spmv(8.0) + 3.0 * 8.0 * n : 2.0 * 8.0 * n) + 16.0 * n + 20.0 * n);
     }
-    if (ell && mixed && s->use_amg) {
-      // paired solves read the operators once for both systems in the
-      // iterations where both advance
-      const double pairs = double(st1[7] - st0[7]);
-      b -= pairs * (nnz * (vb + 4) + s->amg_cycle_opbytes[1]);
-    }
+    if (ell && mixed && s->use_amg) b -= pairs * nnz * (vb + 4);   // shared operator pass
     out->alg_bytes[k] = b;
+  }
+  if (s->use_amg) {
+    const int v = mixed ? 1 : 0;
+    // one cycle per iteration plus the first of each inner solve (mixed: every
+    // refinement pass but the last, converged one of each solve)
+    const double cycles = double(out->cg_iters[0]) +
+                          double(mixed ? out->outer_iters[0] - out->cg_solves[0] : out->cg_solves[0]);
+    out->vcycle_bytes = cycles * s->amg_cycle_bytes[v];
+    out->coarse_bytes = cycles * s->amg_coarse_bytes[v];
+    if (mixed) out->vcycle_bytes -= pairs * (s->amg_cycle_opbytes[v] - vb * double(s->amg.nc) * double(s->amg.nc));
   }
   return read_status(s);
 }
