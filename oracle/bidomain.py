@@ -45,10 +45,16 @@ With correction=False this is Algorithm 1 (partitioned strategy without SDC).
 W-matrix safeguard (a reading; the paper solves with BiCGSTAB and needs no
 symmetry): per node the Schur complement of the node block onto v,
     s_i = -j_vv - j_vy (alpha I - j_yy)^{-1} j_yv,
-is raised to at least -0.9 alpha lambda_M (lambda_M = 1 lumped, 1/4 for P1
-triangles, 1/5 for P1 tetrahedra) by adding the difference to -j_vv.  This
-keeps alpha M + A_i + M_L diag(s) positive definite; ROS2 stays second order
-for any W.  Both the oracle and the CUDA path apply the same rule.
+is raised to at least -margin alpha lambda_M (margin = ``spd_margin``, 0.9 by
+default; lambda_M = 1 lumped, 1/4 for P1 triangles, 1/5 for P1 tetrahedra:
+the smallest generalised eigenvalue of (M, M_L) on one element, so
+M >= lambda_M M_L) by adding the difference to -j_vv.  This keeps
+alpha M + A_i + M_L diag(s) positive definite.  The modified matrix is a W
+matrix in the sense of W-methods, for which ROS2 stays second order; the
+floor only acts at finite steps, since s_i is bounded while alpha grows as
+the step shrinks.  Both the oracle and the CUDA path apply the same rule.
+``w_shift`` (0 by default, a test hook) subtracts a constant from the (v, v)
+entry of every node block, an h-independent W perturbation.
 
 Elliptic constraint (Eq. (3.15), Sec. 2 Dirichlet part left unstated): u is
 the solution of A_ie u = -A_i v with u[pin] = 0 (pin >= 0), or with zero
@@ -172,6 +178,8 @@ class Bidomain:
         keep[self.pin_row] = False
         self.keep = keep
         self.ell_lu = spla.splu(self.ops.A_ie[keep][:, keep].tocsc())
+        self.spd_margin = 0.9      # floor factor of the condensed diagonal (0 disables)
+        self.w_shift = 0.0         # test hook: W_vv = J_vv - w_shift
         self.clamp_count = 0
         self.adaptive_tol = 0.0    # > 0: step() records the embedded error estimate
         self.last_err = 0.0
@@ -220,10 +228,12 @@ class Bidomain:
         A_b = np.transpose(A, (2, 0, 1))
         w = np.linalg.solve(A_b, np.transpose(j[1:, 0:1, :], (2, 0, 1)))[:, :, 0]  # [N, n1]
         s = -j[0, 0, :] - np.einsum("kn,nk->n", j[0, 1:, :], w)
-        s_min = -0.9 * alpha * self.lambda_M
-        clamp = s < s_min
-        self.clamp_count += int(clamp.sum())
-        j[0, 0, :] -= np.where(clamp, s_min - s, 0.0)
+        if self.spd_margin > 0.0:
+            s_min = -self.spd_margin * alpha * self.lambda_M
+            clamp = s < s_min
+            self.clamp_count += int(clamp.sum())
+            j[0, 0, :] -= np.where(clamp, s_min - s, 0.0)
+        j[0, 0, :] -= self.w_shift
         return j
 
     def shifted_solve(self, alpha: float, j: np.ndarray, rhs: np.ndarray) -> np.ndarray:
