@@ -4,13 +4,26 @@
 Metric: node-steps/s of one partitioned-SDC time step (Algorithm 2: elliptic
 solve, ROS2 predictor, SDC correction; 3 Gauss-Lobatto nodes, 2 sweeps) on
 the TP06 epicardial sheet of 257 x 257 P1 nodes (66,049 nodes, 2.5 cm square,
-fibres along x, dt = 0.02 ms, S1 strip x < 0.1 cm at t = 0), inputs resident
-in HBM.  `value` is the mixed-precision path, `fp64` the pure FP64 path.
+fibres along x, dt = 0.02 ms, S1 strip x < 0.1 cm at t = 0, S2 on the corner
+quadrant at 310 ms), timed from a developed state (t = 330 ms: the S2 front
+running into the S1 wave's refractory tail), inputs resident in HBM.
+`value` is the mixed-precision path, `fp64` the pure FP64 path.  Further
+legs: the TP06 3-D slab of 201 x 201 x 51 nodes (HBM-bound; its own
+roofline), the LR91 bidomain-bath sheet of the paper's Sec. 4, the serving
+stream, and the FP64 oracle on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 runs one independent replica per GPU (the method has no data-path
-exchange here) under torchrun; rank 0 prints one JSON line.
+N > 1 runs one independent replica per GPU under torchrun (the method has no
+data-path exchange: each GPU steps its own simulation); rank 0 prints one
+JSON line.
+
+Two helpers for profiling runs:
+  python bench.py --profile-workload {sheet,slab,lv,bath} [--side N] [--lv-h H] [--steps K]
+      steps one workload K times (no timing) so that a profiler can capture it;
+  python bench.py --summarize-launches launches.csv
+      prints the per-kernel launches, total time and share of an
+      `ncu --metrics gpu__time_duration.sum --csv` launch list as a table.
 """
 from __future__ import annotations
 
@@ -28,9 +41,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "node-steps/s, partitioned SDC step, mixed vs FP64 on 1 GB300"
 WORKLOAD = "tp06_sheet_257x257"
 SIDE, LENGTH, DT, M_NODES, K_SWEEPS = 257, 2.5, 0.02, 3, 2
+S2_MS, S2_SIDE = 310.0, 1.25
 SAMPLE_SIDE = 33          # oracle sample: 33 x 33 nodes at the same spacing
 
 
@@ -39,6 +52,7 @@ SAMPLE_SIDE = 33          # oracle sample: 33 x 33 nodes at the same spacing
 # ---------------------------------------------------------------------------
 
 def oracle_sample_problem():
+    import numpy as np
     from oracle import bidomain as OB
     from oracle import tp06 as OT
     from paper_2510_27447_gb300 import workloads as W
@@ -46,7 +60,6 @@ def oracle_sample_problem():
     w = W.sheet(SAMPLE_SIDE, h * (SAMPLE_SIDE - 1), W.TP06_EPI, DT, 1)
     cell = OT.model()
     P = OB.Bidomain(w.xyz, w.elems, w.fibers, w.sigma, w.chi, w.cm, cell, w.stimuli, pin_node=0)
-    import numpy as np
     X = np.repeat(cell.initial()[:, None], w.n_nodes, axis=1)
     return P, X, w.n_nodes
 
@@ -68,22 +81,36 @@ def oracle_rate(warmup: int, steps: int, seconds: float) -> dict:
     return {"value": n * done / el, "steps": done, "seconds": el, "nodes": n}
 
 
-def run_oracle_subprocess(warmup: int, steps: int, seconds: float) -> dict:
+def run_oracle_processes(procs: int, warmup: int, steps: int, seconds: float) -> dict:
+    """`procs` independent single-threaded oracle processes on the same
+    sample at once (the oracle's sparse direct solves run on one thread, so
+    the host's cores are used by running one problem per core); the rate is
+    the node-steps of all processes over the longest one's time."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--warmup", str(warmup),
            "--steps", str(steps), "--seconds", str(seconds)]
-    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    ps = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+          for _ in range(procs)]
+    res = []
+    for p in ps:
+        out, err = p.communicate(timeout=900)
+        if p.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        res.append(json.loads(out.strip().splitlines()[-1]))
+    secs = max(r["seconds"] for r in res)
+    units = sum(r["nodes"] * r["steps"] for r in res)
+    return {"value": units / secs, "steps": min(r["steps"] for r in res), "seconds": secs,
+            "nodes": res[0]["nodes"], "processes": procs}
 
 
 def sample_text(res: dict) -> str:
+    who = "1 process" if res.get("processes", 1) == 1 else f"{res['processes']} concurrent processes"
     return (f"FP64 oracle (numpy/scipy, sparse direct solves), TP06 sheet of {SAMPLE_SIDE}x{SAMPLE_SIDE} "
-            f"nodes at the 257x257 grid spacing, dt={DT} ms, M={M_NODES}, K={K_SWEEPS}, "
-            f"{res['steps']} steps from t=0 in {res['seconds']:.1f} s, 1 thread")
+            f"nodes at the 257x257 grid spacing, dt={DT} ms, M={M_NODES}, K={K_SWEEPS}, from the published "
+            f"initial state with the S1 strip; {who} of 1 thread each, >= {res['steps']} steps in "
+            f"{res['seconds']:.1f} s")
 
 
 # ---------------------------------------------------------------------------
@@ -151,20 +178,20 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("pcg.cu", "amg.cu", "mixed.cu", "sparse.cuh", "vcycle.cuh", "bd_internal.h"):
-        with open(os.path.join(ROOT, "paper_2510_27447_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for f in ("pcg.cu", "amg.cu", "mixed.cu", "stream.cu", "sparse.cuh", "vcycle.cuh", "bd_internal.h"):
+        path = os.path.join(ROOT, "paper_2510_27447_gb300", "csrc", f)
+        if os.path.exists(path):
+            with open(path, "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def load_traffic(kind: str):
-    """DRAM traffic per launch from the committed ncu summary, if the kernel
-    source is unchanged since it was captured."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+def load_traffic(key: str):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if
+    the solver sources are unchanged since it was captured (else None)."""
     try:
-        with open(path) as fh:
-            d = json.load(fh)
-        e = d.get(kind)
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            e = json.load(fh).get(key)
         if e and e.get("source_hash") == kernel_source_hash():
             return e.get("bytes_per_launch")
     except (OSError, ValueError):
@@ -180,38 +207,100 @@ def measured_peaks() -> dict:
         return {}
 
 
+def l2_copy_gbs(torch, stream) -> float:
+    """Bandwidth of a copy whose source and destination (2 x 24 MB) stay in
+    L2 (129 MB): read + write bytes per second, best of 5 runs of 50 copies."""
+    a = torch.empty(6 * 1024 * 1024, dtype=torch.float32, device="cuda").fill_(1.0)
+    b = torch.empty_like(a)
+    best = 0.0
+    with torch.cuda.stream(stream):
+        for _ in range(10):
+            b.copy_(a)
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(50):
+                b.copy_(a)
+            e1.record(stream)
+            e1.synchronize()
+            best = max(best, 50 * 2 * a.numel() * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
+
+
+def solver_roofline(prof: dict, kind: str = "pcg_elliptic") -> dict:
+    """Algorithmic bytes and achieved GB/s of one solver kind from a profile
+    of whole steps: Krylov-level bytes by the per-SpMV and per-iteration
+    model, the V-cycle levels by the same per-SpMV model (listed apart), the
+    dense coarse solve apart and not counted."""
+    idx = 0 if kind == "pcg_elliptic" else 1
+    launches = prof["launches"][kind]
+    avg_s = prof["ms"][kind] / launches / 1e3
+    krylov = prof["alg_bytes"][idx] / launches
+    vcyc = prof["vcycle_bytes"] / launches if idx == 0 else 0.0
+    coarse = prof["coarse_bytes"] / launches if idx == 0 else 0.0
+    its = prof["cg_iters"][idx] / launches
+    return {"kernel": kind, "avg_launch_ms": round(avg_s * 1e3, 4),
+            "krylov_bytes_per_launch": round(krylov), "vcycle_bytes_per_launch": round(vcyc),
+            "coarse_dense_bytes_per_launch": round(coarse),
+            "achieved_gbs": round((krylov + vcyc) / avg_s / 1e9, 1),
+            "krylov_only_gbs": round(krylov / avg_s / 1e9, 1),
+            "cg_iters_per_launch": round(its, 1),
+            "per_iteration_us": round(avg_s * 1e6 / its, 2) if its > 0 else None}
+
+
+def shares(prof: dict) -> dict:
+    tot = sum(prof["ms"].values())
+    return {k: round(v / tot, 4) for k, v in prof["ms"].items()}
+
+
 # ---------------------------------------------------------------------------
-# GPU leg
+# GPU legs
 # ---------------------------------------------------------------------------
 
-def make_sim(precision: int, stream_handle: int):
-    from paper_2510_27447_gb300 import binding, workloads as W
-    w = W.sheet(SIDE, LENGTH, W.TP06_EPI, DT, 1, name=WORKLOAD)
-    opts = binding.default_options(precision=precision, stream=stream_handle, cg_tol_e=1e-10, cg_tol_p=1e-10)
-    return binding.simulation_from_workload(w, opts), w
+def headline_workload():
+    from paper_2510_27447_gb300 import workloads as W
+    return W.sheet(SIDE, LENGTH, W.TP06_EPI, DT, 1, s2=(S2_MS, S2_SIDE), name=WORKLOAD)
 
 
-def time_steps(sim, torch, stream, flush, steps: int) -> list:
+def timed(sim, torch, stream, flush, steps: int, dt: float) -> list:
     ms = []
     for _ in range(steps):
         flush.add_(1.0)                       # evict L2 between timed steps
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        sim.step(DT, M_NODES, K_SWEEPS)
+        sim.step(dt, M_NODES, K_SWEEPS)
         b.record(stream)
         b.synchronize()
         ms.append(a.elapsed_time(b))
     return ms
 
 
-def e2e_rate(sim, torch, steps: int) -> dict:
+def developed_state(w, torch, stream, dev_ms: float):
+    """State blob of the headline sheet at t = dev_ms, stepped from the
+    published initial state on the mixed path (S1 at 0, S2 at 310 ms)."""
+    import numpy as np
+    from paper_2510_27447_gb300 import binding
+    with torch.cuda.stream(stream):
+        opts = binding.default_options(precision=binding.MIXED, stream=stream.cuda_stream)
+        sim = binding.simulation_from_workload(w, opts)
+        for _ in range(int(round(dev_ms / DT))):
+            sim.step(DT, M_NODES, K_SWEEPS)
+        sim.sync()
+        blob = sim.get_state()
+        v, _ = sim.fields()
+        sim.close()
+    return blob, {"t_ms": dev_ms, "depolarised_frac": round(float(np.mean(v > -60.0)), 3),
+                  "v_range_mV": [round(float(v.min()), 1), round(float(v.max()), 1)]}
+
+
+def e2e_rate(sim, torch, blob: bytes, steps: int) -> dict:
     """Same metric through the C ABI with host buffers: every step uploads the
     state blob from pinned host memory, steps, and reads v and u back."""
     import ctypes as C
     from paper_2510_27447_gb300 import binding
     L = binding.lib()
-    blob = sim.get_state()
     nb = len(blob)
     host = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
     host.numpy()[:] = memoryview(blob)
@@ -233,6 +322,65 @@ def e2e_rate(sim, torch, steps: int) -> dict:
             "d2h_bytes_per_step": 8 * (sim.NT + sim.N)}
 
 
+def per_solve(st0, st1, key):
+    return round((st1[f"cg_iters_{key}"] - st0[f"cg_iters_{key}"]) /
+                 max(1, st1[f"cg_solves_{key}"] - st0[f"cg_solves_{key}"]), 1)
+
+
+def slab_leg(args, torch, stream, flush, peaks) -> dict:
+    """Config 2: TP06 in the 2 x 2 x 0.5 cm slab (201 x 201 x 51 nodes,
+    Kuhn tetrahedra, -60..+60 deg transmural fibres, gates perturbed by
+    +-2 % with PCG64(2)), dt = 0.025 ms, 3 Lobatto nodes, 2 sweeps, mixed and
+    FP64, timed from t = 2 ms (S1 front formed).  Its operators (30.4M
+    entries) do not fit in L2: the solver rooflines are against HBM."""
+    from paper_2510_27447_gb300 import binding, workloads as W
+    t0 = time.perf_counter()
+    rest = binding.rest_state(W.TP06_EPI)
+    w = W.config2(rest=rest, gate_rows=list(range(1, 13)))
+    out = {"workload": w.name, "nodes": w.n_nodes, "dt_ms": w.dt, "mesh_s": round(time.perf_counter() - t0, 1),
+           "start": "t = 2 ms from the seeded perturbed initial state (S1 plane x < 0.1 cm at 0 ms)"}
+    blob = None
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    for name, prec in (("mixed", binding.MIXED), ("fp64", binding.FP64)):
+        with torch.cuda.stream(stream):
+            t0 = time.perf_counter()
+            opts = binding.default_options(precision=prec, stream=stream.cuda_stream)
+            sim = binding.simulation_from_workload(w, opts)
+            setup = time.perf_counter() - t0
+            if blob is None:
+                for _ in range(int(round(2.0 / w.dt))):
+                    sim.step(w.dt, M_NODES, K_SWEEPS)
+                sim.sync()
+                blob = sim.get_state()
+            else:
+                sim.set_state(blob)
+            for _ in range(args.warmup):
+                sim.step(w.dt, M_NODES, K_SWEEPS)
+            sim.sync()
+            st0 = sim.stats()
+            torch.cuda.synchronize()
+            ms = timed(sim, torch, stream, flush, args.slab_steps, w.dt)
+            sim.sync()
+            st1 = sim.stats()
+            prof = sim.profile_steps(w.dt, M_NODES, K_SWEEPS, 2)
+            sim.close()
+        t = sum(ms) / len(ms)
+        out[name] = {"ms_per_step": round(t, 3), "value": round(w.n_nodes / (t / 1e3), 1),
+                     "setup_s": round(setup, 1), "cg_iters_e": per_solve(st0, st1, "e"),
+                     "cg_iters_p": per_solve(st0, st1, "p"), "kernel_share": shares(prof),
+                     "elliptic": solver_roofline(prof, "pcg_elliptic"),
+                     "parabolic": solver_roofline(prof, "pcg_parabolic"),
+                     "solver_tier": st1["solver_tier"], "amg_levels": st1["amg_levels"]}
+    m = out["mixed"]["elliptic"]
+    out["roofline"] = {"kernel": "pcg_elliptic (mixed)", "bound": "hbm", "achieved": m["achieved_gbs"],
+                       "peak": hbm, "unit": "GB/s", "frac": round(m["achieved_gbs"] / hbm, 4),
+                       "traffic": load_traffic("slab_pcg_elliptic"),
+                       "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                       "parabolic_frac": round(out["mixed"]["parabolic"]["achieved_gbs"] / hbm, 4)}
+    out["steps"] = args.slab_steps
+    return out
+
+
 def bath_leg(args, torch, stream, flush) -> dict:
     """The bidomain-bath run of Sec. 4 (801^2 nodes over [-1, 7]^2, tissue
     [0, 6]^2 with 601^2 nodes, LR91, 3 Lobatto nodes, 2 sweeps) at its maximum
@@ -245,33 +393,20 @@ def bath_leg(args, torch, stream, flush) -> dict:
            "sigma_bath": w.sbath, "paper_rate_node_steps_per_s": 6.29e4}
     for name, prec in (("mixed", binding.MIXED), ("fp64", binding.FP64)):
         with torch.cuda.stream(stream):
-            opts = binding.default_options(precision=prec, stream=stream.cuda_stream, pin_node=w.pin_node,
-                                           cg_tol_e=1e-10, cg_tol_p=1e-10)
+            opts = binding.default_options(precision=prec, stream=stream.cuda_stream, pin_node=w.pin_node)
             sim = binding.simulation_from_workload(w, opts)
-            for _ in range(max(3, args.warmup)):
-                sim.step(w.dt, 3, 2)
+            for _ in range(args.warmup):
+                sim.step(w.dt, M_NODES, K_SWEEPS)
             sim.sync()
             st0 = sim.stats()
             torch.cuda.synchronize()
-            ms = []
-            for _ in range(args.bath_steps):
-                flush.add_(1.0)
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                sim.step(w.dt, 3, 2)
-                b.record(stream)
-                b.synchronize()
-                ms.append(a.elapsed_time(b))
+            ms = timed(sim, torch, stream, flush, args.bath_steps, w.dt)
             sim.sync()
             st1 = sim.stats()
             sim.close()
         t = sum(ms) / len(ms)
         out[name] = {"ms_per_step": round(t, 3), "value": round(w.n_nodes / (t / 1e3), 1),
-                     "cg_iters_e": round((st1["cg_iters_e"] - st0["cg_iters_e"]) /
-                                         max(1, st1["cg_solves_e"] - st0["cg_solves_e"]), 1),
-                     "cg_iters_p": round((st1["cg_iters_p"] - st0["cg_iters_p"]) /
-                                         max(1, st1["cg_solves_p"] - st0["cg_solves_p"]), 1)}
+                     "cg_iters_e": per_solve(st0, st1, "e"), "cg_iters_p": per_solve(st0, st1, "p")}
     out["steps"] = args.bath_steps
     return out
 
@@ -280,51 +415,34 @@ def lv_leg(args, torch, stream, flush) -> dict:
     """The 3-D bidomain-bath configuration: TP06 in a truncated prolate LV
     shell inside a box bath (jittered Kuhn lattice, h = args.lv_h cm in the
     shell's bounding box, coarser bath margins), dt = 0.025 ms, 3 Lobatto
-    nodes, 2 sweeps, mixed and FP64, from rest + apical pacing: node-steps/s
-    over all nodes."""
+    nodes, 2 sweeps, mixed and FP64, from rest + apical pacing."""
     from paper_2510_27447_gb300 import binding, workloads as W
     t0 = time.perf_counter()
     w = W.lv_shell_bath(h=args.lv_h)
-    gen_s = time.perf_counter() - t0
     out = {"workload": w.name, "nodes": w.n_nodes, "tissue_nodes": w.n_tissue, "elements": int(len(w.elems)),
-           "dt_ms": w.dt, "sigma_bath": w.sbath, "mesh_s": round(gen_s, 1)}
+           "dt_ms": w.dt, "sigma_bath": w.sbath, "mesh_s": round(time.perf_counter() - t0, 1)}
     for name, prec in (("mixed", binding.MIXED), ("fp64", binding.FP64)):
         with torch.cuda.stream(stream):
             t0 = time.perf_counter()
-            opts = binding.default_options(precision=prec, stream=stream.cuda_stream, pin_node=w.pin_node,
-                                           cg_tol_e=1e-10, cg_tol_p=1e-10)
+            opts = binding.default_options(precision=prec, stream=stream.cuda_stream, pin_node=w.pin_node)
             sim = binding.simulation_from_workload(w, opts)
             setup = time.perf_counter() - t0
-            for _ in range(max(3, args.warmup)):
-                sim.step(w.dt, 3, 2)
+            for _ in range(args.warmup):
+                sim.step(w.dt, M_NODES, K_SWEEPS)
             sim.sync()
             st0 = sim.stats()
             torch.cuda.synchronize()
-            ms = []
-            for _ in range(args.lv_steps):
-                flush.add_(1.0)
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                sim.step(w.dt, 3, 2)
-                b.record(stream)
-                b.synchronize()
-                ms.append(a.elapsed_time(b))
+            ms = timed(sim, torch, stream, flush, args.lv_steps, w.dt)
             sim.sync()
             st1 = sim.stats()
-            prof = sim.profile_steps(w.dt, 3, 2, 2)
+            prof = sim.profile_steps(w.dt, M_NODES, K_SWEEPS, 2)
             sim.close()
         t = sum(ms) / len(ms)
-        tot = sum(prof["ms"].values())
         out[name] = {"ms_per_step": round(t, 3), "value": round(w.n_nodes / (t / 1e3), 1),
-                     "setup_s": round(setup, 1),
-                     "cg_iters_e": round((st1["cg_iters_e"] - st0["cg_iters_e"]) /
-                                         max(1, st1["cg_solves_e"] - st0["cg_solves_e"]), 1),
-                     "cg_iters_p": round((st1["cg_iters_p"] - st0["cg_iters_p"]) /
-                                         max(1, st1["cg_solves_p"] - st0["cg_solves_p"]), 1),
-                     "share": {k: round(v / tot, 3) for k, v in prof["ms"].items()},
-                     "elliptic_alg_gbs": round(prof["alg_bytes"][0] / (prof["ms"]["pcg_elliptic"] / 1e3) / 1e9, 1),
-                     "parabolic_alg_gbs": round(prof["alg_bytes"][1] / (prof["ms"]["pcg_parabolic"] / 1e3) / 1e9, 1)}
+                     "setup_s": round(setup, 1), "cg_iters_e": per_solve(st0, st1, "e"),
+                     "cg_iters_p": per_solve(st0, st1, "p"), "kernel_share": shares(prof),
+                     "elliptic": solver_roofline(prof, "pcg_elliptic"),
+                     "parabolic": solver_roofline(prof, "pcg_parabolic")}
     out["steps"] = args.lv_steps
     return out
 
@@ -370,13 +488,19 @@ def run_ours(args) -> None:
     if dist:
         dist.barrier()
     from paper_2510_27447_gb300 import binding
+    from paper_2510_27447_gb300.replicas import whole_job_rate
+    peaks = measured_peaks()
     stream = torch.cuda.Stream()
     flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
-    results = {}
-    profiles = {}
+    l2_gbs = l2_copy_gbs(torch, stream)
+    w = headline_workload()
+    blob, dev = developed_state(w, torch, stream, args.dev_ms)
+    results, profiles = {}, {}
     for name, prec in (("mixed", binding.MIXED), ("fp64", binding.FP64)):
         with torch.cuda.stream(stream):
-            sim, w = make_sim(prec, stream.cuda_stream)
+            opts = binding.default_options(precision=prec, stream=stream.cuda_stream)
+            sim = binding.simulation_from_workload(w, opts)
+            sim.set_state(blob)
             for _ in range(args.warmup):
                 sim.step(DT, M_NODES, K_SWEEPS)
             sim.sync()
@@ -385,21 +509,19 @@ def run_ours(args) -> None:
                 dist.barrier()
             torch.cuda.synchronize()
             with ClockSampler(local) as clk:
-                ms = time_steps(sim, torch, stream, flush, args.steps)
+                ms = timed(sim, torch, stream, flush, args.steps, DT)
             torch.cuda.synchronize()
             sim.sync()
             st1 = sim.stats()
-            from paper_2510_27447_gb300.replicas import whole_job_rate
             rate, secs = whole_job_rate(sim.N * args.steps, sum(ms) / 1e3, device="cuda")
-            results[name] = {"ms_per_step": secs * 1e3 / args.steps,
-                             "value": rate,
-                             "clocks": clk.summary(),
+            results[name] = {"ms_per_step": secs * 1e3 / args.steps, "value": rate, "clocks": clk.summary(),
                              "launches": st1["kernel_launches"] - st0["kernel_launches"],
-                             "cg_iters_e": (st1["cg_iters_e"] - st0["cg_iters_e"]) / max(1, st1["cg_solves_e"] - st0["cg_solves_e"]),
-                             "cg_iters_p": (st1["cg_iters_p"] - st0["cg_iters_p"]) / max(1, st1["cg_solves_p"] - st0["cg_solves_p"])}
+                             "cg_iters_e": per_solve(st0, st1, "e"), "cg_iters_p": per_solve(st0, st1, "p"),
+                             "solver_tier": st1["solver_tier"], "amg_levels": st1["amg_levels"]}
+            sim.set_state(blob)
             profiles[name] = sim.profile_steps(DT, M_NODES, K_SWEEPS, args.steps)
             if name == "mixed":
-                results[name]["e2e"] = e2e_rate(sim, torch, max(3, args.steps // 2))
+                results[name]["e2e"] = e2e_rate(sim, torch, blob, max(3, args.steps // 2))
             sim.close()
     if rank != 0:
         if dist:
@@ -407,62 +529,58 @@ def run_ours(args) -> None:
         return
 
     prof = profiles["mixed"]
-    dom = max(prof["ms"], key=lambda k: prof["ms"][k])
-    peaks = measured_peaks()
-    n = SIDE * SIDE
-    roof = None
-    if dom in ("pcg_elliptic", "pcg_parabolic"):
-        idx = 0 if dom == "pcg_elliptic" else 1
-        launches = prof["launches"][dom]
-        byt = prof["alg_bytes"][idx] / launches
-        avg_s = prof["ms"][dom] / launches / 1e3
-        achieved = byt / avg_s / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
-        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": load_traffic(dom),
-                "algorithmic_bytes_per_launch": round(byt), "avg_launch_ms": round(avg_s * 1e3, 4),
-                "cg_iters_per_launch": round(prof["cg_iters"][idx] / launches, 1),
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
-        # this mesh's operators and vectors fit in L2: the HBM fraction is
-        # small by construction and the solve is latency-bound; report the
-        # cost of one CG iteration and DRAM traffic against algorithmic bytes
-        its = prof["cg_iters"][idx] / launches
-        if its > 0:
-            roof["per_iteration_us"] = round(avg_s * 1e6 / its, 2)
-        if roof["traffic"]:
-            roof["traffic_over_algorithmic"] = round(roof["traffic"] / byt, 3)
-        roof["regime"] = "latency-bound, L2-resident working set (see profiles/pcg_mixed_amg_tp06_257x257.md)"
-    share = {k: round(v / sum(prof["ms"].values()), 4) for k, v in prof["ms"].items()}
+    ell = solver_roofline(prof, "pcg_elliptic")
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    # the headline sheet's operators and vectors (about 7 MB a matrix) live in
+    # L2: its solver is bounded by L2 bandwidth and by the latency of its
+    # dependent phases, not by HBM
+    roof = {"kernel": "pcg_elliptic (mixed)", "bound": "l2", "achieved": ell["achieved_gbs"],
+            "peak": round(l2_gbs, 1), "unit": "GB/s", "frac": round(ell["achieved_gbs"] / l2_gbs, 4),
+            "traffic": load_traffic("sheet_pcg_elliptic"),
+            "peak_source": "L2-resident copy measured in this run (2 x 24 MB, read + write)",
+            "hbm_frac": round(ell["achieved_gbs"] / hbm, 4), "hbm_peak": hbm,
+            "per_iteration_us": ell["per_iteration_us"], "cg_iters_per_launch": ell["cg_iters_per_launch"],
+            "krylov_bytes_per_launch": ell["krylov_bytes_per_launch"],
+            "vcycle_bytes_per_launch": ell["vcycle_bytes_per_launch"],
+            "coarse_dense_bytes_per_launch": ell["coarse_dense_bytes_per_launch"],
+            "avg_launch_ms": ell["avg_launch_ms"]}
 
-    lv = None
-    if args.lv_steps > 0:
+    slab = None
+    if args.slab_steps > 0:
         try:
-            lv = lv_leg(args, torch, stream, flush)
+            slab = slab_leg(args, torch, stream, flush, peaks)
         except Exception as e:  # noqa: BLE001
-            lv = {"error": str(e)[:200]}
-
+            slab = {"error": str(e)[:300]}
     bath = None
     if args.bath_steps > 0:
         try:
             bath = bath_leg(args, torch, stream, flush)
         except Exception as e:  # noqa: BLE001
-            bath = {"error": str(e)[:200]}
-
+            bath = {"error": str(e)[:300]}
+    lv = None
+    if args.lv_steps > 0:
+        try:
+            lv = lv_leg(args, torch, stream, flush)
+        except Exception as e:  # noqa: BLE001
+            lv = {"error": str(e)[:300]}
     serve = None
     if args.serve_requests > 0:
         try:
             serve = serve_leg(args)
         except Exception as e:  # noqa: BLE001
-            serve = {"error": str(e)[:200]}
+            serve = {"error": str(e)[:300]}
 
     base = None
     if world == 1 and not args.no_baseline:
         try:
-            res = run_oracle_subprocess(0, 1, 15.0)
-            base = {"value": round(res["value"], 2), "unit": "node-steps/s", "cores": 1, "kind": "oracle",
-                    "sample": sample_text(res)}
+            one = run_oracle_processes(1, 0, 1, 15.0)
+            ncores = os.cpu_count() or 1
+            allc = run_oracle_processes(ncores, 0, 1, 15.0)
+            base = {"value": round(allc["value"], 2), "unit": "node-steps/s", "cores": ncores, "kind": "oracle",
+                    "sample": sample_text(allc),
+                    "single_thread": {"value": round(one["value"], 2), "cores": 1, "sample": sample_text(one)}}
         except Exception as e:  # noqa: BLE001
-            base = {"value": None, "unit": "node-steps/s", "cores": 1, "kind": "oracle",
+            base = {"value": None, "unit": "node-steps/s", "cores": None, "kind": "oracle",
                     "sample": f"failed: {e}"[:200]}
 
     mixed = results["mixed"]
@@ -479,40 +597,116 @@ def run_ours(args) -> None:
         "vs_baseline": None,
         "dtype": "mixed: f32 membrane model and Krylov iterations, f64 refinement and state",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": n, "model": "TP06 epicardial", "dt_ms": DT,
-                   "sdc_nodes": M_NODES, "sweeps": K_SWEEPS, "start": "rest + S1 at t=0",
+        "config": {"workload": WORKLOAD, "nodes": w.n_nodes, "model": "TP06 epicardial", "dt_ms": DT,
+                   "sdc_nodes": M_NODES, "sweeps": K_SWEEPS,
+                   "start": f"developed state at {args.dev_ms:g} ms (S1 strip at 0 ms, S2 corner quadrant at "
+                            f"{S2_MS:g} ms), restored with bd_set_state before each leg",
+                   "developed_state": dev,
                    "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "fp64": {"value": round(results["fp64"]["value"], 1),
-                 "ms_per_step": round(results["fp64"]["ms_per_step"], 4), "dtype": "f64"},
+                 "ms_per_step": round(results["fp64"]["ms_per_step"], 4), "dtype": "f64",
+                 "kernel_share": shares(profiles["fp64"]),
+                 "elliptic": solver_roofline(profiles["fp64"], "pcg_elliptic"),
+                 "cg_iters_per_solve": {"elliptic": results["fp64"]["cg_iters_e"],
+                                        "parabolic": results["fp64"]["cg_iters_p"]}},
         "e2e": {k: (round(v, 1) if isinstance(v, float) else v) for k, v in mixed["e2e"].items()},
         "gpu_launches": int(mixed["launches"]),
         "clocks": mixed["clocks"],
         "roofline": roof,
-        "kernel_share": share,
-        "cg_iters_per_solve": {"elliptic": round(mixed["cg_iters_e"], 1), "parabolic": round(mixed["cg_iters_p"], 1)},
+        "kernel_share": shares(prof),
+        "parabolic": solver_roofline(prof, "pcg_parabolic"),
+        "cg_iters_per_solve": {"elliptic": mixed["cg_iters_e"], "parabolic": mixed["cg_iters_p"]},
+        "solver": {"tier": mixed["solver_tier"], "amg_levels": mixed["amg_levels"]},
         "cpu_baseline": base,
-        "serve": serve,
+        "slab": slab,
         "bath": bath,
         "lv_shell_bath": lv,
+        "serve": serve,
     }
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
 
+def profile_workload(args) -> None:
+    """Step one workload args.steps times and print the handle's counters."""
+    from paper_2510_27447_gb300 import binding, workloads as W
+    name = args.profile_workload
+    if name == "sheet":
+        w = W.sheet(args.side, LENGTH * (args.side - 1) / (SIDE - 1), W.TP06_EPI, DT, 1)
+    elif name == "slab":
+        w = W.config2()
+    elif name == "lv":
+        w = W.lv_shell_bath(h=args.lv_h)
+    else:
+        w = W.bath_paper_2d()
+    prec = binding.FP64 if args.precision == "fp64" else binding.MIXED
+    sim = binding.simulation_from_workload(w, binding.default_options(precision=prec, pin_node=w.pin_node))
+    for _ in range(args.steps):
+        sim.step(w.dt, M_NODES, K_SWEEPS)
+    sim.sync()
+    print(json.dumps({"workload": w.name, "nodes": int(w.n_nodes), "steps": args.steps, "stats": sim.stats()}))
+    sim.close()
+
+
+def _short_kernel_name(name: str) -> str:
+    import re
+    m = re.search(r"bd::\(anonymous namespace\)::(\w+)", name)
+    if m:
+        base = m.group(1)
+        for tag in ("TP06", "LR91"):
+            if tag in name:
+                base += f"<{tag}" + (",float" if "float" in name else ",double")
+                mode = re.search(r", \(int\)(\d)>", name) or re.search(r", (\d)>", name)
+                if mode and base.startswith("ionic_kernel"):
+                    base += f",mode{mode.group(1)}"
+                base += ">"
+                break
+        return base
+    if "at::" in name or "at_cuda" in name:
+        return "torch:" + re.sub(r"<.*", "", name.split("at::")[-1])[:40]
+    return name[:60]
+
+
+def summarize_launches(path: str) -> None:
+    """Markdown table of an ncu launch list: per kernel its launches, total
+    device time and share of the listed time."""
+    import csv
+    from collections import defaultdict
+    tot, cnt = defaultdict(float), defaultdict(int)
+    with open(path) as fh:
+        lines = [ln for ln in fh if ln.startswith('"')]
+    scale = {"ns": 1e-3, "nsecond": 1e-3, "us": 1.0, "usecond": 1.0, "ms": 1e3, "msecond": 1e3}
+    for row in csv.DictReader(lines):
+        if row.get("Metric Name") != "gpu__time_duration.sum":
+            continue
+        k = _short_kernel_name(row["Kernel Name"])
+        tot[k] += float(row["Metric Value"].replace(",", "")) * scale.get(row.get("Metric Unit", "ns"), 1e-3)
+        cnt[k] += 1
+    all_us = sum(tot.values())
+    print("| kernel | launches | total us | share |")
+    print("|---|---|---|---|")
+    for k in sorted(tot, key=lambda x: -tot[x]):
+        print(f"| `{k}` | {cnt[k]} | {tot[k]:.1f} | {100 * tot[k] / all_us:.2f}% |")
+    print(f"| TOTAL | {sum(cnt.values())} | {all_us:.1f} | |")
+
+
 def run_reference(args) -> None:
+    """The oracle, as it stands, on the host cores: one single-threaded
+    process per core on the bounded sample of the headline workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    res = run_oracle_subprocess(args.warmup, args.steps, 0.0)
+    ncores = os.cpu_count() or 1
+    res = run_oracle_processes(ncores, args.warmup, args.steps, 0.0)
     val = round(res["value"], 3)
     line = {"impl": "reference", "metric": "node-steps/s", "value": val, "unit": "node-steps/s",
             "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": res["steps"], "warmup": args.warmup,
             "ms_per_step": round(1e3 * res["seconds"] / res["steps"], 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample_nodes": res["nodes"], "model": "TP06 epicardial",
-                       "dt_ms": DT, "sdc_nodes": M_NODES, "sweeps": K_SWEEPS},
-            "cpu_baseline": {"value": val, "unit": "node-steps/s", "cores": 1, "kind": "oracle",
+                       "dt_ms": DT, "sdc_nodes": M_NODES, "sweeps": K_SWEEPS, "processes": ncores},
+            "cpu_baseline": {"value": val, "unit": "node-steps/s", "cores": ncores, "kind": "oracle",
                              "sample": sample_text(res)},
             "e2e": {"value": val, "unit": "node-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -525,6 +719,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-baseline", action="store_true")
+    ap.add_argument("--dev-ms", type=float, default=330.0,
+                    help="simulated time of the developed state the headline legs start from (ms)")
+    ap.add_argument("--slab-steps", type=int, default=5,
+                    help="timed steps of the 201x201x51 slab leg (0: skip)")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-ms", type=float, default=10.0)
     ap.add_argument("--lv-steps", type=int, default=0,
@@ -532,9 +730,20 @@ def main():
     ap.add_argument("--lv-h", type=float, default=0.04, help="lattice spacing of the LV leg (cm)")
     ap.add_argument("--bath-steps", type=int, default=10,
                     help="timed steps of the 801^2 bidomain-bath leg (0: skip)")
+    ap.add_argument("--profile-workload", choices=["sheet", "slab", "lv", "bath"],
+                    help="step one workload --steps times for a profiler (no timing)")
+    ap.add_argument("--side", type=int, default=SIDE, help="sheet side for --profile-workload sheet")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--summarize-launches", metavar="CSV", help="summarise an ncu launch list")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--seconds", type=float, default=0.0, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.summarize_launches:
+        summarize_launches(args.summarize_launches)
+        return
+    if args.profile_workload:
+        profile_workload(args)
+        return
     if args.oracle_sample:
         import numpy as np
         np.seterr(all="ignore")

@@ -79,7 +79,7 @@ KERNEL_KINDS = ("pcg_elliptic", "pcg_parabolic", "ionic", "field", "combine", "f
 class Profile(C.Structure):
     _fields_ = [("ms", C.c_double * 6), ("launches", C.c_int64 * 6), ("cg_iters", C.c_int64 * 2),
                 ("cg_solves", C.c_int64 * 2), ("outer_iters", C.c_int64 * 2), ("nnz", C.c_int64),
-                ("alg_bytes", C.c_double * 2)]
+                ("alg_bytes", C.c_double * 2), ("vcycle_bytes", C.c_double), ("coarse_bytes", C.c_double)]
 
 
 _lib = None
@@ -331,7 +331,9 @@ class Simulation:
                 "cg_iters": [int(p.cg_iters[0]), int(p.cg_iters[1])],
                 "cg_solves": [int(p.cg_solves[0]), int(p.cg_solves[1])],
                 "outer_iters": [int(p.outer_iters[0]), int(p.outer_iters[1])], "nnz": int(p.nnz),
-                "alg_bytes": [float(p.alg_bytes[0]), float(p.alg_bytes[1])]}
+                "alg_bytes": [float(p.alg_bytes[0]), float(p.alg_bytes[1])],
+                "vcycle_bytes": float(p.vcycle_bytes), "coarse_bytes": float(p.coarse_bytes),
+                "nodes": self.N, "tissue_nodes": self.NT}
 
     def reset_stats(self):
         _check(lib().bd_reset_stats(self.h), self.h)
