@@ -131,6 +131,12 @@ typedef struct {
                             (bd_stats_t.solver_tier); 1, 2, 3: force tier 0, 1 or 2 (2 needs
                             cg_block <= 512; 3 affects only the mixed AMG kernels);
                             BD_ERR_ARG otherwise; ignored with cg_cluster */
+  int streaming;         /* solver form: 0 (default) streaming for operators of at least
+                            12M entries (they do not fit in L2), persistent otherwise;
+                            1: always streaming; -1: never.  Streaming solves chain
+                            full-occupancy kernels whose CG loops run on the device as CUDA
+                            graph conditional nodes; persistent solves are one cooperative
+                            kernel each (bd_stats_t.streaming reports the form in use) */
 } bd_opts_t;
 
 typedef struct bd_state bd_state_t;
@@ -154,6 +160,7 @@ typedef struct {
                               entries) */
   int64_t amg_levels;      /* smoothed AMG levels of the elliptic preconditioner (0: Jacobi) */
   int64_t amg_coarse_rows; /* rows of the dense coarsest AMG level (0: Jacobi) */
+  int64_t streaming;       /* 1: the solves run as streaming kernel chains (bd_opts_t.streaming) */
 } bd_stats_t;
 
 /* Per-kind device time of profiled steps (bd_profile_steps). */

@@ -63,14 +63,15 @@ class Opts(C.Structure):
                 ("elliptic_precond", C.c_int), ("amg_coarse_max", C.c_int), ("cg_block", C.c_int),
                 ("cg_grid", C.c_int),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
-                ("stream", C.c_void_p), ("cg_cluster", C.c_int), ("solver_tier", C.c_int)]
+                ("stream", C.c_void_p), ("cg_cluster", C.c_int), ("solver_tier", C.c_int),
+                ("streaming", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("steps", "sweeps", "cg_iters_e", "cg_solves_e",
                                           "cg_iters_p", "cg_solves_p", "spd_clamps", "ionic_evals",
                                           "kernel_launches", "solver_block_bound", "solver_tier",
-                                          "amg_levels", "amg_coarse_rows")]
+                                          "amg_levels", "amg_coarse_rows", "streaming")]
 
 
 KERNEL_KINDS = ("pcg_elliptic", "pcg_parabolic", "ionic", "field", "combine", "finish")

@@ -135,6 +135,14 @@ struct bd_state {
   double dt_adapt = 0.0;                   // next step size (0: start at dt_max)
   unsigned long long* d_err = nullptr;
   double *Xbak = nullptr, *ubak = nullptr, *tbak = nullptr, *upbak = nullptr;
+  // streaming solver (operators that do not fit in L2): device scalars, block
+  // partials, FP64-path workspaces and two streams that capture loop bodies
+  bool streaming = false;
+  StreamScal* d_sc = nullptr;
+  double* spart = nullptr;
+  double *sb64 = nullptr, *sr64 = nullptr;
+  double *sr = nullptr, *sz = nullptr, *sp = nullptr, *sq = nullptr, *sd = nullptr, *sinvd = nullptr;
+  cudaStream_t side[2] = {nullptr, nullptr};
   int pcg_grid = 1, pcg_block = 512, pcg_max = 1;
   int tier = 0;                            // solver register tier (kSolverTierBlock)
   int cluster = 0;                         // > 0: solvers run as one cluster of this many 1024-thread blocks
@@ -208,6 +216,10 @@ void release(bd_state* s) {
     else cudaFree(p);
   }
   s->allocs.clear();
+  for (cudaStream_t& x : s->side) {
+    if (x) cudaStreamDestroy(x);
+    x = nullptr;
+  }
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
   s->stream = nullptr;
 }
@@ -229,10 +241,11 @@ struct Timed {
     }
     slot = s->evused++;
     s->evpool[slot].kind = k;
-    cudaEventRecord(s->evpool[slot].a, s->stream);
+    // profiled steps are captured: the records become event nodes of the graph
+    cudaEventRecordWithFlags(s->evpool[slot].a, s->stream, cudaEventRecordExternal);
   }
   ~Timed() {
-    if (s->prof) cudaEventRecord(s->evpool[slot].b, s->stream);
+    if (s->prof) cudaEventRecordWithFlags(s->evpool[slot].b, s->stream, cudaEventRecordExternal);
   }
 };
 
@@ -319,7 +332,61 @@ PcgLaunch pcg_base(bd_state* s) {
   return P;
 }
 
+StreamLaunch stream_base(bd_state* s, int n) {
+  StreamLaunch A{};
+  A.n = n;
+  A.sptr = s->sptr;
+  A.swidth = s->swidth;
+  A.col = s->col;
+  A.diagpos = s->diagpos;
+  A.part = s->spart;
+  A.sc = s->d_sc;
+  A.status = s->d_status;
+  A.launch_acc = s->d_stats + 8;
+  A.gate = s->opts.sweep_tol > 0 ? s->gate : nullptr;
+  A.grid = int(std::max<int64_t>(1, std::min<int64_t>((int64_t(n) + 255) / 256, stream_grid_cap())));
+  const bool mixed = s->precision == BD_MIXED;
+  A.b64 = mixed ? s->b64 : s->sb64;
+  A.r64 = mixed ? s->r64 : s->sr64;
+  A.r = mixed ? static_cast<void*>(s->r32) : static_cast<void*>(s->sr);
+  A.z = mixed ? static_cast<void*>(s->z32) : static_cast<void*>(s->sz);
+  A.p = mixed ? static_cast<void*>(s->p32) : static_cast<void*>(s->sp);
+  A.q = mixed ? static_cast<void*>(s->q32) : static_cast<void*>(s->sq);
+  A.d = mixed ? static_cast<void*>(s->d32) : static_cast<void*>(s->sd);
+  A.invd = mixed ? static_cast<void*>(s->invd32) : static_cast<void*>(s->sinvd);
+  return A;
+}
+
 int elliptic(bd_state* s, const double* v, double* u) {
+  if (s->streaming) {
+    if (s->NT < s->N) {
+      Timed t(s, BD_K_COMBINE);
+      CK(launch_copy(s->NT, v, s->vfull, s->stream, s->opts.sweep_tol > 0 ? s->gate : nullptr));
+      v = s->vfull;
+    }
+    StreamLaunch A = stream_base(s, int(s->N));
+    const bool mixed = s->precision == BD_MIXED;
+    A.valA = s->Aie;
+    A.valT = mixed ? static_cast<const void*>(s->fAie) : static_cast<const void*>(s->Aie);
+    A.val1 = s->Ai;
+    A.va = v;
+    A.c1 = -1.0;
+    A.project = 1;
+    A.warm = 1;
+    A.x = u;
+    A.pin = s->opts.pin_node >= 0 ? s->opts.pin_node : -1;
+    A.max_outer = mixed ? 12 : 1;
+    A.inner_cap = s->opts.cg_cap_e;
+    A.use_amg = s->use_amg ? 1 : 0;
+    A.tol = s->opts.cg_tol_e;
+    A.tol_inner = mixed ? double(BD_MIXED_TOL_INNER) : s->opts.cg_tol_e;
+    A.iters_acc = s->d_stats + 0;
+    A.solves_acc = s->d_stats + 1;
+    A.outer_acc = s->d_stats + 4;
+    Timed t(s, BD_K_PCG_ELLIPTIC, 0);   // its kernels count themselves on the device
+    CK(stream_solve(A, mixed ? 1 : 0, &s->amgf, &s->amg, s->stream, s->side));
+    return BD_OK;
+  }
   PcgLaunch P = pcg_base(s);
   if (s->NT < s->N) {   // the right-hand side -A_i v gathers v over all columns
     Timed t(s, BD_K_COMBINE);
@@ -361,7 +428,7 @@ int elliptic(bd_state* s, const double* v, double* u) {
 // u1 = E(v1) and u2 = E(v2): one two-RHS launch on the mixed AMG path, else
 // two solves
 int elliptic2(bd_state* s, const double* v1, double* u1, const double* v2, double* u2) {
-  if (!s->two_rhs || s->precision != BD_MIXED || !s->use_amg) {
+  if (!s->two_rhs || s->precision != BD_MIXED || !s->use_amg || s->streaming) {
     const int r = elliptic(s, v1, u1);
     if (r != BD_OK) return r;
     return elliptic(s, v2, u2);
@@ -404,6 +471,37 @@ int elliptic2(bd_state* s, const double* v1, double* u1, const double* v2, doubl
 // false drops diag(dgs) and rl (the plain Crank-Nicolson operator)
 int parabolic(bd_state* s, double alpha, double c1, const double* va, double c2, const double* vb, double* x,
               bool node_terms = true, bool warm = false) {
+  if (s->streaming) {
+    StreamLaunch A = stream_base(s, int(s->NT));   // tissue rows; their bath columns hold zeros
+    const bool mixed = s->precision == BD_MIXED;
+    A.valA = p_values(s, alpha);
+    A.valT = mixed ? static_cast<const void*>(p_values_f(s, alpha)) : static_cast<const void*>(A.valA);
+    A.dextra = node_terms ? s->dgs : nullptr;
+    A.rl = node_terms ? s->rl : nullptr;
+    A.val1 = s->Ai;
+    A.va = va;
+    A.c1 = c1;
+    if (vb) {
+      A.val2 = s->Mv;
+      A.vb = vb;
+      A.c2 = c2;
+    }
+    A.project = 0;
+    A.warm = warm ? 1 : 0;
+    A.x = x;
+    A.pin = -2;
+    A.max_outer = 1;
+    A.inner_cap = s->opts.cg_cap_p;
+    A.use_amg = 0;
+    A.tol = s->opts.cg_tol_p;
+    A.tol_inner = mixed ? std::max(s->opts.cg_tol_p, 1e-6) : s->opts.cg_tol_p;
+    A.iters_acc = s->d_stats + 2;
+    A.solves_acc = s->d_stats + 3;
+    A.outer_acc = s->d_stats + 5;
+    Timed t(s, BD_K_PCG_PARABOLIC, 0);
+    CK(stream_solve(A, mixed ? 1 : 0, nullptr, nullptr, s->stream, s->side));
+    return BD_OK;
+  }
   PcgLaunch P = pcg_base(s);
   P.n = int(s->NT);   // tissue rows; their bath columns hold zeros
   P.valA = p_values(s, alpha);
@@ -890,7 +988,35 @@ int enqueue_any(bd_state* s, double dt, int M, int K) {
 
 int do_step(bd_state* s, double dt, int M, int K) {
   RUN(prepare_step(s, dt, M));
-  if (!s->opts.use_graph || s->prof) {
+  if (s->prof) {
+    // a profiled step is captured with its event records and replayed, so
+    // every event pair brackets device work only (launched eagerly, a fast
+    // kernel's pair would also hold the time the GPU waits for the host)
+    while (s->evpool.size() < 1024) {
+      bd_state::Ev e{0, nullptr, nullptr};
+      CK(cudaEventCreate(&e.a));
+      CK(cudaEventCreate(&e.b));
+      s->evpool.push_back(e);
+    }
+    cudaGraph_t g = nullptr;
+    s->enq_launches = 0;
+    CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    const int r = enqueue_any(s, dt, M, K);
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    if (r != BD_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (e != cudaSuccess) return fail(s, BD_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(s, BD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    e = cudaGraphLaunch(ex, s->stream);
+    cudaGraphExecDestroy(ex);
+    if (e != cudaSuccess) return fail(s, BD_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+    s->launches += s->enq_launches;
+  } else if (!s->opts.use_graph) {
     s->enq_launches = 0;
     RUN(enqueue_any(s, dt, M, K));
     s->launches += s->enq_launches;
@@ -1092,7 +1218,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
             alloc_n(s, &s->stim_bits, NT) &&
             (NT == N || alloc_n(s, &s->vfull, N)) &&
             alloc_n(s, &s->step_n, 1) && alloc_n(s, &s->t_now, 3) && alloc_n(s, &s->d_err, 1) &&
-            alloc_n(s, &s->d_status, 1) && alloc_n(s, &s->d_stats, 8) &&
+            alloc_n(s, &s->d_status, 1) && alloc_n(s, &s->d_stats, 16) &&
             alloc_n(s, &s->d_clamps, 1) && alloc_n(s, &s->bar, 2) &&
             alloc_n(s, reinterpret_cast<char**>(&s->d_amg), int64_t(sizeof(AmgDev))) &&
             alloc_n(s, reinterpret_cast<char**>(&s->d_amgf), int64_t(sizeof(AmgDevF)));
@@ -1164,6 +1290,27 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
          alloc_n(s, reinterpret_cast<char**>(&s->d_amgf2), int64_t(sizeof(AmgDevF))) &&
          alloc_n(s, &s->partf, int64_t(part_blocks) * 8);
   }
+  {
+    const int so = s->opts.streaming;
+    if (so < -1 || so > 1) {
+      release(s);
+      delete s;
+      return fail(nullptr, BD_ERR_ARG, "streaming must be -1, 0 or 1");
+    }
+    s->streaming = s->opts.cg_cluster == 0 && (so == 1 || (so == 0 && nnz >= kTier2Nnz));
+  }
+  if (ok && s->streaming) {
+    ok = alloc_n(s, reinterpret_cast<char**>(&s->d_sc), int64_t(sizeof(StreamScal))) &&
+         alloc_n(s, &s->spart, int64_t(stream_grid_cap()) * 4);
+    if (ok && s->precision == BD_FP64)
+      ok = alloc_n(s, &s->sb64, N) && alloc_n(s, &s->sr64, N) && alloc_n(s, &s->sr, N) && alloc_n(s, &s->sz, N) &&
+           alloc_n(s, &s->sp, N) && alloc_n(s, &s->sq, N) && alloc_n(s, &s->sd, N) && alloc_n(s, &s->sinvd, N);
+    for (cudaStream_t& x : s->side)
+      if (ok && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        ok = false;
+      }
+  }
   if (!ok) {
     release(s);
     delete s;
@@ -1200,8 +1347,11 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, 2 * N * 4, s->stream);
   if (e == cudaSuccess && s->invd32) e = cudaMemsetAsync(s->invd32, 0, N * 4, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->bar, 0, 8, s->stream);
+  for (double* v : {s->sb64, s->sr64, s->sr, s->sz, s->sp, s->sq, s->sd, s->sinvd})
+    if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, N * 8, s->stream);
+  if (e == cudaSuccess && s->d_sc) e = cudaMemsetAsync(s->d_sc, 0, sizeof(StreamScal), s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, 4, s->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_stats, 0, 64, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->d_stats, 0, 128, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_clamps, 0, 8, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_amg, 0, sizeof(AmgDev), s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_amgf, 0, sizeof(AmgDevF), s->stream);
@@ -1561,10 +1711,10 @@ int bd_struct_sizes(size_t* mesh, size_t* cond, size_t* opts, size_t* stats) {
 int bd_get_stats(const bd_state_t* cs, bd_stats_t* out) {
   bd_state* s = const_cast<bd_state*>(cs);
   if (!s || !out) return fail(s, BD_ERR_ARG, "NULL argument");
-  long long st[7];
+  long long st[9];
   unsigned long long cl = 0;
   CK(cudaStreamSynchronize(s->stream));
-  CK(cudaMemcpy(st, s->d_stats, 56, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(st, s->d_stats, 72, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(&cl, s->d_clamps, 8, cudaMemcpyDeviceToHost));
   out->steps = s->steps;
   out->sweeps = s->opts.sweep_tol > 0 ? s->steps + st[6] : s->sweeps;
@@ -1574,11 +1724,12 @@ int bd_get_stats(const bd_state_t* cs, bd_stats_t* out) {
   out->cg_solves_p = st[3];
   out->spd_clamps = int64_t(cl);
   out->ionic_evals = s->ionic_evals;
-  out->kernel_launches = s->launches;
+  out->kernel_launches = s->launches + st[8];   // host-enqueued + counted on the device (streaming solves)
   out->solver_block_bound = s->cluster > 0 ? kSolverTierBlock[0] : kSolverTierBlock[s->tier];
   out->solver_tier = s->cluster > 0 ? 0 : s->tier;
   out->amg_levels = s->use_amg ? s->amg.nlev : 0;
   out->amg_coarse_rows = s->use_amg ? s->amg.nc : 0;
+  out->streaming = s->streaming ? 1 : 0;
   return BD_OK;
 }
 
@@ -1735,7 +1886,7 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
 int bd_reset_stats(bd_state_t* s) {
   if (!s) return fail(s, BD_ERR_ARG, "NULL handle");
   CK(cudaStreamSynchronize(s->stream));
-  CK(cudaMemset(s->d_stats, 0, 64));
+  CK(cudaMemset(s->d_stats, 0, 128));
   CK(cudaMemset(s->d_clamps, 0, 8));
   s->steps = s->sweeps = s->ionic_evals = s->launches = 0;
   return BD_OK;

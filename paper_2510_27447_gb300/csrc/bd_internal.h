@@ -295,6 +295,60 @@ cudaError_t launch_pcg_mixed2(const PcgLaunch& P, const double* va1, double* x1,
                               double* partd8);
 cudaError_t launch_to_float(int64_t n, const double* src, float* dst, cudaStream_t st);
 
+// ---- streaming solver (stream.cu) -------------------------------------------
+// For operators that do not fit in L2 the solves run as chains of ordinary
+// full-occupancy kernels instead of one persistent kernel; the Krylov loops
+// run on the device as CUDA-graph conditional WHILE nodes whose condition the
+// kernels set, so a solve needs no host round trip.
+struct StreamScal {               // device scalars of one streaming solve
+  double mean_b, bb, tol2;        // right-hand side mean (projected systems), |b|^2, tol^2 |b|^2
+  double rr64, scale, tgt;        // outer residual, its norm, inner target (relative, squared)
+  double rr_new, rho, alpha, beta, shift;
+  int outer, it, fail, stop, inner_ran, skip, first, pad;
+  long long inner_total, outer_total;
+  unsigned ticket, pad2;
+};
+struct StreamLaunch {
+  int n;                          // rows
+  const int64_t* sptr;            // shared SELL-32 pattern (see PcgLaunch)
+  const int* swidth;
+  const int* col;
+  const int* diagpos;
+  const double* valA;             // FP64 operator values (outer residual, diagonal)
+  const void* valT;               // operator values in the inner precision
+  const double* dextra;           // optional extra diagonal
+  const double* rl;               // rhs = rl + c1 V1 va + c2 V2 vb
+  const double* val1;
+  const double* va;
+  double c1;
+  const double* val2;
+  const double* vb;
+  double c2;
+  int project, warm, pin, max_outer, inner_cap, use_amg;
+  double tol, tol_inner;
+  double* x;
+  double* b64;                    // FP64 right-hand side
+  double* r64;                    // FP64 outer residual
+  void *r, *z, *p, *q, *d, *invd; // inner-precision vectors
+  void* part;                     // block partial sums (grid x 4 doubles)
+  StreamScal* sc;
+  int* status;
+  long long* iters_acc;
+  long long* solves_acc;
+  long long* outer_acc;
+  long long* launch_acc;          // kernels launched (counted on the device)
+  const int* gate;                // optional: the solve is skipped when *gate == 0
+  int grid;                       // blocks of the row kernels (capped at a multiple of the SMs)
+  unsigned long long h_outer, h_inner;   // conditional handles of the two loops
+};
+// Enqueue one streaming solve on `st` (captured or not).  side[0..1] are two
+// idle streams of the same device used to capture the loop bodies; inner type
+// float or double (f32 = 1: FP32 inner iterations on valT/M32), AMG hierarchy
+// M32/M64 or Jacobi when use_amg = 0.
+cudaError_t stream_solve(const StreamLaunch& a, int f32, const AmgDevF* M32, const AmgDev* M64, cudaStream_t st,
+                         const cudaStream_t* side);
+int stream_grid_cap();
+
 // host assembly (assemble.cpp)
 struct HostOps {
   int64_t n = 0;
