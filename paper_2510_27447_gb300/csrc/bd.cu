@@ -23,6 +23,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -1012,7 +1014,8 @@ int do_step(bd_state* s, double dt, int M, int K) {
     e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(s, BD_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    e = cudaGraphLaunch(ex, s->stream);
+    e = cudaGraphUpload(ex, s->stream);   // the upload precedes the first event node
+    if (e == cudaSuccess) e = cudaGraphLaunch(ex, s->stream);
     cudaGraphExecDestroy(ex);
     if (e != cudaSuccess) return fail(s, BD_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
     s->launches += s->enq_launches;
@@ -1063,6 +1066,481 @@ int do_step(bd_state* s, double dt, int M, int K) {
 void invalidate_graph(bd_state* s) {
   for (auto& g : s->graphs) cudaGraphExecDestroy(g.exec);
   s->graphs.clear();
+}
+
+// ---------------------------------------------------------------------------
+// batched steps (bd_batch_step): one launch per phase over the concatenated
+// nodes of many handles, the whole step captured as one graph per (dt, M, K)
+// ---------------------------------------------------------------------------
+//
+// Every phase of enqueue_step becomes one batched launch (segment.cuh): the
+// node-wise kernels over the handles' tissue nodes, every elliptic or
+// parabolic solve one batched streaming solve (stream.cu) whose systems keep
+// their own reductions, scalars, stopping tests and iteration caps.  The
+// per-handle argument tables and block prefixes are written into a device
+// arena when the step is captured; the graph reads them at replay.
+
+struct BatchPlan {
+  std::vector<bd_state*> m;
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  BatchCtl* ctl = nullptr;
+  // arena chunks (one per captured step shape; graphs keep pointing into theirs)
+  std::vector<char*> chunks;
+  char* cur = nullptr;             // chunk of the capture in progress
+  size_t cap = 0, used = 0;
+  bool overflow = false;
+  std::vector<char> host;          // host image of the current chunk
+  struct G {
+    double dt;
+    int M, K;
+    cudaGraphExec_t exec;
+    int64_t launches;
+  };
+  std::vector<G> graphs;
+  int64_t enq = 0;                 // launches enqueued by the capture in progress
+  ~BatchPlan() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    for (char* c : chunks) cudaFree(c);
+    if (ctl) cudaFree(ctl);
+    for (cudaStream_t x : side)
+      if (x) cudaStreamDestroy(x);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+  }
+};
+
+std::mutex g_batch_mu;
+std::vector<std::unique_ptr<BatchPlan>> g_batches;
+
+// copy a table into the chunk of the capture in progress; returns its device address
+template <class T>
+T* put(BatchPlan& B, const T* v, size_t count) {
+  const size_t bytes = sizeof(T) * count, at = (B.used + 255) & ~size_t(255);
+  if (at + bytes > B.cap) {
+    B.overflow = true;
+    return reinterpret_cast<T*>(B.cur);
+  }
+  if (B.host.size() < at + bytes) B.host.resize(at + bytes);
+  std::memcpy(B.host.data() + at, v, bytes);
+  B.used = at + bytes;
+  return reinterpret_cast<T*>(B.cur + at);
+}
+template <class T>
+T* put(BatchPlan& B, const std::vector<T>& v) {
+  return put(B, v.data(), v.size());
+}
+
+// block prefix of per-handle block counts; *total receives the sum
+int* prefix(BatchPlan& B, const std::vector<int>& counts, int* total) {
+  std::vector<int> p(counts.size() + 1, 0);
+  for (size_t i = 0; i < counts.size(); ++i) p[i + 1] = p[i] + counts[i];
+  *total = p.back();
+  return put(B, p);
+}
+std::vector<int> blocks_of(const BatchPlan& B, const std::function<int64_t(const bd_state*)>& n, int block) {
+  std::vector<int> c;
+  for (const bd_state* s : B.m) c.push_back(int((n(s) + block - 1) / block));
+  return c;
+}
+
+#define BCK(call)                                                                           \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail(s0, BD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// the streaming workspaces a handle needs to take part in a batch (its own
+// steps may use the persistent solvers and never allocate them)
+int ensure_stream_ws(bd_state* s) {
+  const int64_t N = s->N;
+  bool ok = true;
+  if (!s->d_sc)
+    ok = alloc_n(s, reinterpret_cast<char**>(&s->d_sc), int64_t(sizeof(StreamScal))) &&
+         cudaMemsetAsync(s->d_sc, 0, sizeof(StreamScal), s->stream) == cudaSuccess;
+  if (ok && !s->spart) ok = alloc_n(s, &s->spart, int64_t(stream_grid_cap()) * 4);
+  if (ok && s->precision == BD_FP64 && !s->sb64) {
+    ok = alloc_n(s, &s->sb64, N) && alloc_n(s, &s->sr64, N) && alloc_n(s, &s->sr, N) && alloc_n(s, &s->sz, N) &&
+         alloc_n(s, &s->sp, N) && alloc_n(s, &s->sq, N) && alloc_n(s, &s->sd, N) && alloc_n(s, &s->sinvd, N);
+    for (double* v : {s->sb64, s->sr64, s->sr, s->sz, s->sp, s->sq, s->sd, s->sinvd})
+      if (ok && v) ok = cudaMemsetAsync(v, 0, N * 8, s->stream) == cudaSuccess;
+  }
+  if (!ok) return fail(s, BD_ERR_OOM, "device allocation failed (batch workspaces)");
+  return BD_OK;
+}
+
+// one batched solve: elliptic (v -> u, all nodes) or parabolic (the
+// condensed systems of the tissue rows)
+struct BatchSolveArgs {
+  bool elliptic;
+  double alpha, c1, c2;            // parabolic: shift and right-hand-side factors
+  bool node_terms;
+  std::vector<const double*> va, vb;
+  std::vector<double*> x;
+};
+
+int batch_solve(BatchPlan& B, const BatchSolveArgs& q, cudaStream_t st) {
+  bd_state* s0 = B.m[0];
+  const int nseg = int(B.m.size());
+  const bool mixed = s0->precision == BD_MIXED;
+  std::vector<StreamLaunch> tab(nseg);
+  std::vector<int> rows(nseg), post0(nseg), coarse(nseg);
+  int nlev_max = 0;
+  std::vector<AmgDevF> hf(q.elliptic && mixed ? nseg : 0);
+  std::vector<AmgDev> hd(q.elliptic && !mixed ? nseg : 0);
+  std::vector<std::vector<int>> lA(kMaxAmgLevels, std::vector<int>(nseg, 0)), lR = lA, lP = lA;
+  for (int r = 0; r < nseg; ++r) {
+    bd_state* s = B.m[r];
+    const int n = int(q.elliptic ? s->N : s->NT);
+    StreamLaunch A = stream_base(s, n);
+    A.launch_acc = nullptr;
+    A.gate = nullptr;
+    A.grid = stream_grid(n);
+    if (q.elliptic) {
+      A.valA = s->Aie;
+      A.valT = mixed ? static_cast<const void*>(s->fAie) : static_cast<const void*>(s->Aie);
+      A.val1 = s->Ai;
+      A.va = q.va[r];
+      A.c1 = -1.0;
+      A.project = 1;
+      A.warm = 1;
+      A.pin = s->opts.pin_node >= 0 ? s->opts.pin_node : -1;
+      A.max_outer = mixed ? 12 : 1;
+      A.inner_cap = s->opts.cg_cap_e;
+      A.use_amg = s->use_amg ? 1 : 0;
+      A.tol = s->opts.cg_tol_e;
+      A.tol_inner = mixed ? double(BD_MIXED_TOL_INNER) : s->opts.cg_tol_e;
+      A.iters_acc = s->d_stats + 0;
+      A.solves_acc = s->d_stats + 1;
+      A.outer_acc = s->d_stats + 4;
+      int nlev = 0;
+      if (s->use_amg) {
+        nlev = mixed ? s->amgf.nlev : s->amg.nlev;
+        const int nc = mixed ? s->amgf.nc : s->amg.nc;
+        A.h0_invd = mixed ? static_cast<const void*>(s->amgf.L[0].invd) : static_cast<const void*>(s->amg.L[0].invd);
+        A.h0_x = mixed ? static_cast<void*>(s->amgf.L[0].x) : static_cast<void*>(s->amg.L[0].x);
+        A.h0_omega = mixed ? double(s->amgf.L[0].omega) : s->amg.L[0].omega;
+        for (int l = 0; l < nlev; ++l) {
+          auto grid_of = [&](const auto& M) { return stream_grid(M.rp ? int64_t(M.n) * 32 : int64_t(M.n)); };
+          if (mixed) {
+            lA[l][r] = grid_of(s->amgf.L[l].A);
+            lR[l][r] = grid_of(s->amgf.L[l].R);
+            lP[l][r] = grid_of(s->amgf.L[l].P);
+          } else {
+            lA[l][r] = grid_of(s->amg.L[l].A);
+            lR[l][r] = grid_of(s->amg.L[l].R);
+            lP[l][r] = grid_of(s->amg.L[l].P);
+          }
+        }
+        coarse[r] = stream_grid(int64_t(std::max(1, nc)) * 32);
+        if (mixed) hf[r] = s->amgf;
+        else hd[r] = s->amg;
+      } else {
+        if (mixed) hf[r] = AmgDevF{};
+        else hd[r] = AmgDev{};
+      }
+      nlev_max = std::max(nlev_max, nlev);
+      post0[r] = s->use_amg ? lA[0][r] : 1;
+    } else {
+      A.valA = p_values(s, q.alpha);
+      A.valT = mixed ? static_cast<const void*>(p_values_f(s, q.alpha)) : static_cast<const void*>(A.valA);
+      if (!A.valA || !A.valT) return fail(s0, BD_ERR_OOM, "device allocation failed");
+      A.dextra = q.node_terms ? s->dgs : nullptr;
+      A.rl = q.node_terms ? s->rl : nullptr;
+      A.val1 = s->Ai;
+      A.va = q.va[r];
+      A.c1 = q.c1;
+      if (!q.vb.empty() && q.vb[r]) {
+        A.val2 = s->Mv;
+        A.vb = q.vb[r];
+        A.c2 = q.c2;
+      }
+      A.project = 0;
+      A.warm = 1;
+      A.pin = -2;
+      A.max_outer = 1;
+      A.inner_cap = s->opts.cg_cap_p;
+      A.use_amg = 0;
+      A.tol = s->opts.cg_tol_p;
+      A.tol_inner = mixed ? std::max(s->opts.cg_tol_p, 1e-6) : s->opts.cg_tol_p;
+      A.iters_acc = s->d_stats + 2;
+      A.solves_acc = s->d_stats + 3;
+      A.outer_acc = s->d_stats + 5;
+      post0[r] = 1;
+    }
+    A.x = q.x[r];
+    rows[r] = A.grid;
+    tab[r] = A;
+  }
+  BatchSolve bs{};
+  bs.tab = put(B, tab);
+  bs.nseg = nseg;
+  bs.f32 = mixed ? 1 : 0;
+  bs.ctl = B.ctl;
+  bs.launch_acc = s0->d_stats + 8;
+  bs.blk_rows = prefix(B, rows, &bs.total_rows_blocks);
+  bs.blk_post0 = prefix(B, post0, &bs.total_post0_blocks);
+  bs.nlev_max = nlev_max;
+  for (int l = 0; l < nlev_max; ++l) {
+    bs.blk_A[l] = prefix(B, lA[l], &bs.total_A[l]);
+    bs.blk_R[l] = prefix(B, lR[l], &bs.total_R[l]);
+    bs.blk_P[l] = prefix(B, lP[l], &bs.total_P[l]);
+  }
+  bs.blk_coarse = prefix(B, coarse, &bs.total_coarse);
+  for (const StreamLaunch& A : tab) {
+    bs.inner_cap = std::max(bs.inner_cap, unsigned(std::max(A.inner_cap, 1)));
+    bs.max_outer = std::max(bs.max_outer, unsigned(std::max(A.max_outer, 1)));
+  }
+  bs.hier = mixed ? static_cast<const void*>(put(B, hf)) : static_cast<const void*>(put(B, hd));
+  BCK(stream_solve_batch(bs, st, B.side));   // its kernels count themselves on the device
+  return BD_OK;
+}
+
+int enqueue_batch_step(BatchPlan& B, double dt, int M, int K) {
+  bd_state* s0 = B.m[0];
+  const cudaStream_t st = s0->stream;
+  const int nseg = int(B.m.size());
+  const int model = s0->model, prec = s0->precision, ns = s0->ns;
+  const double gam = 1.0 + 1.0 / std::sqrt(2.0);
+  double c[kMaxNodes], S[kMaxNodes - 1][kMaxNodes];
+  lobatto(M, c);
+  integration_matrix(M, S);
+  auto NT = [](const bd_state* s) { return s->NT; };
+  auto NU = [](const bd_state* s) { return s->N; };
+  int tot = 0;
+  int* blk_node = prefix(B, blocks_of(B, NT, kNodeBlock), &tot);
+  const int nb_node = tot;
+  int* blk_vec_u = prefix(B, blocks_of(B, NU, kVecBlock), &tot);
+  const int nb_vec_u = tot;
+  int* blk_fin = prefix(B, blocks_of(B, [](const bd_state* s) { return std::max(s->NT, s->N); }, kVecBlock), &tot);
+  const int nb_fin = tot;
+  auto field = [&](auto Xof, auto fof) {
+    std::vector<FieldArgs> t;
+    for (bd_state* s : B.m) t.push_back({s->NT, Xof(s), s->inv_cm, dt, s->stim_bits, s->t_now, s->stim, fof(s)});
+    B.enq += 1;
+    return launch_field_batch(model, prec, put(B, t), blk_node, nseg, nb_node, st);
+  };
+  auto copy_u = [&](auto src, auto dst) {
+    std::vector<CopyArgs> t;
+    for (bd_state* s : B.m) t.push_back({s->N, src(s), dst(s)});
+    B.enq += 1;
+    return launch_copy_batch(put(B, t), blk_vec_u, nseg, nb_vec_u, st);
+  };
+  // the elliptic constraint u_m = E(v) for every handle (bath meshes gather v
+  // into the zero-padded N-vector first)
+  auto elliptic_all = [&](auto vof, auto uof) -> int {
+    bool bath = false;
+    for (bd_state* s : B.m) bath = bath || s->NT < s->N;
+    if (bath) {                     // copies for the bath members only
+      std::vector<CopyArgs> t;
+      std::vector<int> cnt;
+      for (bd_state* s : B.m) {
+        const bool b = s->NT < s->N;
+        t.push_back({b ? s->NT : 0, vof(s), b ? s->vfull : nullptr});
+        cnt.push_back(b ? int((s->NT + kVecBlock - 1) / kVecBlock) : 0);
+      }
+      int nb = 0;
+      int* blk = prefix(B, cnt, &nb);
+      B.enq += 1;
+      BCK(launch_copy_batch(put(B, t), blk, nseg, nb, st));
+    }
+    BatchSolveArgs q{};
+    q.elliptic = true;
+    for (bd_state* s : B.m) {
+      q.va.push_back(s->NT < s->N ? s->vfull : vof(s));
+      q.x.push_back(uof(s));
+    }
+    return batch_solve(B, q, st);
+  };
+  auto parabolic_all = [&](double alpha, double c1, double c2, bool with_b, int m, int g) -> int {
+    BatchSolveArgs q{};
+    q.elliptic = false;
+    q.alpha = alpha;
+    q.c1 = c1;
+    q.c2 = c2;
+    q.node_terms = true;
+    for (bd_state* s : B.m) {
+      q.va.push_back(s->avec);
+      q.vb.push_back(with_b ? s->bvec : nullptr);
+      q.x.push_back(s->kinc[m][g]);
+    }
+    return batch_solve(B, q, st);
+  };
+  auto ionic_all = [&](auto build) {
+    std::vector<IonicLaunch> t;
+    for (bd_state* s : B.m) t.push_back(build(s));
+    B.enq += 1;
+    return launch_ionic_batch(t[0], put(B, t), blk_node, nseg, nb_node, st);
+  };
+
+  BCK(field([](bd_state* s) { return s->Xn; }, [](bd_state* s) { return s->fq[0]; }));
+  for (int k = 1; k <= K; ++k) {
+    if (k == 1) {
+      RUN(elliptic_all([](bd_state* s) { return s->Xn; }, [M](bd_state* s) { return s->u[M - 1]; }));
+      for (int m = 1; m + 1 < M; ++m)
+        BCK(copy_u([M](bd_state* s) { return s->u[M - 1]; }, [m](bd_state* s) { return s->u[m]; }));
+    } else {
+      if (k == 2) {
+        std::vector<ExtrapArgs> t;
+        for (bd_state* s : B.m) t.push_back({s->N, M == 3 ? s->u[1] : nullptr, s->u[M - 1], s->uprev, 0.5, dt, s->t_now});
+        B.enq += 2;
+        BCK(launch_extrap_batch(put(B, t), blk_vec_u, nseg, nb_vec_u, st));
+      }
+      for (int m = 1; m < M; ++m)
+        RUN(elliptic_all([m](bd_state* s) { return s->Xc[m]; }, [m](bd_state* s) { return s->u[m]; }));
+    }
+    // ROS2 predictor (the launch arguments of enqueue_step)
+    for (int m = 0; m + 1 < M; ++m) {
+      const double h = dt * (c[m + 1] - c[m]);
+      const double alpha = 1.0 / (gam * h);
+      const bool reuse0 = prec == BD_FP64 && K > 1;
+      auto s1 = [&](bd_state* s) {
+        IonicLaunch L = ionic_base(s, MODE_S1, dt);
+        L.gate = nullptr;
+        L.alpha = alpha;
+        L.smin = s->opts.spd_margin > 0 ? -s->opts.spd_margin * alpha * s->lambda_M : -INFINITY;
+        L.XJ = m == 0 ? s->Xn : s->Xt[m];
+        L.u = s->u[m + 1];
+        L.z = s->z1;
+        L.w = s->w1;
+        L.fq_out = (m >= 1 && s->opts.sdc_correction) ? s->fq[m] : nullptr;
+        L.pack = s->pack;
+        if (m >= 1) L.jac_out = s->opts.sdc_correction ? s->jpack : nullptr;
+        else if (reuse0 && k == 1) L.jac_out = s->jpack0;
+        else if (reuse0) L.jac_in = s->jpack0;
+        return L;
+      };
+      BCK(ionic_all(s1));
+      RUN(parabolic_all(alpha, -1.0, 0.0, false, m, 0));
+      auto s2 = [&](bd_state* s) {
+        IonicLaunch L2 = ionic_base(s, MODE_S2P, dt);
+        L2.gate = nullptr;
+        L2.pack = s->pack;
+        L2.alpha = alpha;
+        L2.smin = s->opts.spd_margin > 0 ? -s->opts.spd_margin * alpha * s->lambda_M : -INFINITY;
+        L2.XJ = m == 0 ? s->Xn : s->Xt[m];
+        L2.u = s->u[m + 1];
+        L2.k1v = s->kinc[m][0];
+        L2.z1 = s->z1;
+        L2.w1 = s->w1;
+        L2.ck1 = 2.0 / (gam * h);
+        L2.inv_gamma = 1.0 / gam;
+        L2.z = s->z2;
+        L2.bvec = s->bvec;
+        return L2;
+      };
+      BCK(ionic_all(s2));
+      RUN(parabolic_all(alpha, -1.0, -2.0 / (gam * h), true, m, 1));
+      {
+        std::vector<CombineArgs> t;
+        for (bd_state* s : B.m)
+          t.push_back({s->NT, m == 0 ? s->Xn : s->Xt[m], s->kinc[m][0], s->z1, s->w1, s->kinc[m][1], s->z2, s->w1,
+                       1.5 / gam, 0.5 / gam, s->Xt[m + 1]});
+        B.enq += 1;
+        BCK(launch_combine_batch(model, put(B, t), blk_node, nseg, nb_node, st));
+      }
+    }
+    // SDC correction
+    if (s0->opts.sdc_correction) {
+      BCK(field([M](bd_state* s) { return s->Xt[M - 1]; }, [M](bd_state* s) { return s->fq[M - 1]; }));
+      for (int m = 0; m + 1 < M; ++m) {
+        const double h = dt * (c[m + 1] - c[m]);
+        const double alpha = 1.0 / h;
+        auto cr = [&](bd_state* s) {
+          IonicLaunch L = ionic_base(s, MODE_CORR, dt);
+          L.gate = nullptr;
+          L.alpha = alpha;
+          L.smin = s->opts.spd_margin > 0 ? -s->opts.spd_margin * alpha * s->lambda_M : -INFINITY;
+          L.inv_dt = 1.0 / h;
+          L.XJ = s->Xt[m + 1];
+          L.Xprev = m == 0 ? s->Xn : s->Xc[m];
+          L.n_nodes = M;
+          L.jac_in = m + 2 < M ? s->jpack : nullptr;
+          for (int j = 0; j < M; ++j) {
+            L.S[j] = dt * S[m][j];
+            L.Xq[j] = j == 0 ? s->Xn : s->Xt[j];
+            L.uq[j] = s->u[j];
+            L.fq[j] = s->fq[j];
+          }
+          L.z = s->z1;
+          L.w = s->w1;
+          L.bvec = s->bvec;
+          return L;
+        };
+        BCK(ionic_all(cr));
+        RUN(parabolic_all(alpha, -1.0 / h, 1.0 / h, true, m, 2));
+        std::vector<UpdateArgs> t;
+        for (bd_state* s : B.m) t.push_back({s->NT, s->Xt[m + 1], s->kinc[m][2], s->z1, s->w1, s->Xc[m + 1]});
+        B.enq += 1;
+        BCK(launch_update_batch(model, put(B, t), blk_node, nseg, nb_node, st));
+      }
+    } else {
+      for (int m = 1; m < M; ++m) {
+        std::vector<CopyArgs> t;
+        for (bd_state* s : B.m) t.push_back({int64_t(ns) * s->NT, s->Xt[m], s->Xc[m]});
+        std::vector<int> cnt;
+        for (bd_state* s : B.m) cnt.push_back(int((int64_t(ns) * s->NT + kVecBlock - 1) / kVecBlock));
+        int nb = 0;
+        int* blk = prefix(B, cnt, &nb);
+        B.enq += 1;
+        BCK(launch_copy_batch(put(B, t), blk, nseg, nb, st));
+      }
+    }
+  }
+  {
+    std::vector<FinishArgs> t;
+    for (bd_state* s : B.m)
+      t.push_back({ns, s->NT, s->N, s->Xn, s->Xc[M - 1], s->u[0], s->u[M - 1], s->t_act, s->opts.v_act_mV, dt,
+                   s->t_now, s->step_n, s->d_status});
+    B.enq += 2;
+    BCK(launch_finish_batch(put(B, t), blk_fin, nseg, nb_fin, st));
+  }
+  return BD_OK;
+}
+
+// capture the batched step of shape (dt, M, K) into a graph of its own, with
+// its tables in a fresh arena chunk (grown and captured again if too small)
+int capture_batch_step(BatchPlan& B, double dt, int M, int K, BatchPlan::G* out) {
+  bd_state* s0 = B.m[0];
+  size_t want = size_t(1) << 22;
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    char* chunk = nullptr;
+    BCK(cudaMalloc(&chunk, want));
+    B.cur = chunk;
+    B.cap = want;
+    B.used = 0;
+    B.overflow = false;
+    B.host.clear();
+    B.enq = 0;
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(s0->stream, cudaStreamCaptureModeThreadLocal));
+    const int r = enqueue_batch_step(B, dt, M, K);
+    const cudaError_t e = cudaStreamEndCapture(s0->stream, &g);
+    if (r != BD_OK || e != cudaSuccess || B.overflow) {
+      if (g) cudaGraphDestroy(g);
+      cudaFree(chunk);
+      if (r != BD_OK) return r;
+      if (e != cudaSuccess) return fail(s0, BD_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e));
+      want *= 4;                      // the tables did not fit: larger chunk, capture again
+      continue;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      cudaFree(chunk);
+      return fail(s0, BD_ERR_CUDA, "batch graph instantiate: %s", cudaGetErrorString(ei));
+    }
+    if (cudaMemcpy(chunk, B.host.data(), B.used, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGraphExecDestroy(ex);
+      cudaFree(chunk);
+      return fail(s0, BD_ERR_CUDA, "batch table upload failed");
+    }
+    B.chunks.push_back(chunk);
+    *out = {dt, M, K, ex, B.enq};
+    return BD_OK;
+  }
+  return fail(s0, BD_ERR_OOM, "batch tables do not fit");
 }
 
 }  // namespace
@@ -1464,10 +1942,70 @@ int bd_step_decoupled(bd_state_t* s, double dt) {
 }
 
 int bd_batch_step(bd_state_t* const* states, int n, double dt, int M, int K) {
-  if (!states || n < 0) return fail(nullptr, BD_ERR_ARG, "bad batch");
+  if (!states || n < 1) return fail(nullptr, BD_ERR_ARG, "bad batch");
+  if (!(dt > 0) || !std::isfinite(dt)) return fail(nullptr, BD_ERR_ARG, "dt must be positive");
+  if (M != 2 && M != 3) return fail(nullptr, BD_ERR_ARG, "n_sdc_nodes must be 2 or 3");
+  if (K < 1) return fail(nullptr, BD_ERR_ARG, "n_sweeps must be >= 1");
+  bd_state* const s0 = states[0];
+  bd_state* s = s0;                 // error reports go to the first handle
   for (int i = 0; i < n; ++i) {
-    const int r = bd_step(states[i], dt, M, K);
-    if (r != BD_OK) return r;
+    bd_state* h = states[i];
+    if (!h) return fail(nullptr, BD_ERR_ARG, "NULL handle in batch");
+    for (int j = 0; j < i; ++j)
+      if (states[j] == h) return fail(s0, BD_ERR_ARG, "a handle appears twice in the batch");
+    if (h->model != s0->model || h->precision != s0->precision || h->device != s0->device ||
+        h->opts.sdc_correction != s0->opts.sdc_correction)
+      return fail(s0, BD_ERR_ARG, "batched handles must share model, precision, device and sdc_correction");
+    if (h->opts.sweep_tol > 0) return fail(s0, BD_ERR_ARG, "batched handles must have sweep_tol = 0");
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  BatchPlan* B = nullptr;
+  for (auto& p : g_batches)
+    if (int(p->m.size()) == n && std::equal(p->m.begin(), p->m.end(), states)) B = p.get();
+  if (!B) {
+    auto P = std::make_unique<BatchPlan>();
+    P->m.assign(states, states + n);
+    if (cudaSetDevice(s0->device) != cudaSuccess) return fail(s0, BD_ERR_CUDA, "cudaSetDevice failed");
+    for (cudaStream_t& x : P->side)
+      if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(s0, BD_ERR_CUDA, "batch stream creation failed");
+    if (cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&P->ctl, sizeof(BatchCtl)) != cudaSuccess || cudaMemset(P->ctl, 0, sizeof(BatchCtl)) != cudaSuccess)
+      return fail(s0, BD_ERR_CUDA, "batch set-up failed");
+    g_batches.push_back(std::move(P));
+    B = g_batches.back().get();
+  }
+  for (bd_state* h : B->m) {
+    RUN(ensure_stream_ws(h));
+    RUN(prepare_step(h, dt, M));
+  }
+  // the members' queued work precedes the batch on the first handle's stream
+  for (bd_state* h : B->m) {
+    if (h == s0) continue;
+    CK(cudaEventRecord(B->ev_in, h->stream));
+    CK(cudaStreamWaitEvent(s0->stream, B->ev_in, 0));
+  }
+  BatchPlan::G* ge = nullptr;
+  for (auto& g : B->graphs)
+    if (g.dt == dt && g.M == M && g.K == K) ge = &g;
+  if (!ge) {
+    BatchPlan::G g{};
+    RUN(capture_batch_step(*B, dt, M, K, &g));
+    B->graphs.push_back(g);
+    ge = &B->graphs.back();
+  }
+  CK(cudaGraphLaunch(ge->exec, s0->stream));
+  // the members' later work follows the batch
+  CK(cudaEventRecord(B->ev_out, s0->stream));
+  for (bd_state* m : B->m)
+    if (m != s0) CK(cudaStreamWaitEvent(m->stream, B->ev_out, 0));
+  s0->launches += ge->launches;
+  const int64_t evals = int64_t(K) * (3 * (M - 1) + (s0->opts.sdc_correction ? M : 0)) + 1;
+  for (bd_state* m : B->m) {
+    m->steps += 1;
+    m->sweeps += K;
+    m->ionic_evals += evals;
   }
   return BD_OK;
 }
@@ -1904,6 +2442,19 @@ const char* bd_last_error(const bd_state_t* s) {
 void bd_destroy(bd_state_t* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t i = 0; i < g_batches.size();) {
+      auto& mm = g_batches[i]->m;
+      if (std::find(mm.begin(), mm.end(), s) != mm.end()) {
+        for (bd_state* o : mm)
+          if (o->stream) cudaStreamSynchronize(o->stream);
+        g_batches.erase(g_batches.begin() + i);
+      } else {
+        ++i;
+      }
+    }
+  }
   release(s);
   delete s;
 }

@@ -125,6 +125,68 @@ cudaError_t launch_finish(int ns, int64_t n, int64_t nu, double* Xn, const doubl
 int model_ns(int model);
 void rest_state_host(int model, double* x);
 
+// ---- batched node-wise launches (ionic.cu; see segment.cuh) ------------------
+// One launch over the nodes of many handles: tab holds one argument block per
+// handle (device memory), blk the block prefix (nseg + 1 ints, device), the
+// launch has blk[nseg] blocks.  The model, precision and mode are the batch's.
+struct FieldArgs {
+  int64_t n;
+  const double* X;
+  double inv_cm, dt;
+  const uint32_t* stim_bits;
+  const double* t_now;
+  StimTable stim;
+  double* fout;
+};
+struct CombineArgs {
+  int64_t n;
+  const double *src, *k1v, *z1, *w1, *k2v, *z2, *w2;
+  double m1, m2;
+  double* dst;
+};
+struct UpdateArgs {
+  int64_t n;
+  const double *Xt, *ev, *z, *w;
+  double* dst;
+};
+struct CopyArgs {
+  int64_t n;
+  const double* src;
+  double* dst;
+};
+struct ExtrapArgs {
+  int64_t n;
+  double *u1, *u2, *ep;
+  double c1, dt;
+  double* clk;
+};
+struct FinishArgs {
+  int ns;
+  int64_t n, nu;
+  double* Xn;
+  const double* Xlast;
+  double* u0;
+  const double* ulast;
+  double* t_act;
+  double v_act, dt;
+  double* t_now;
+  long long* step_n;
+  int* status;
+};
+constexpr int kNodeBlock = 128;   // block of the node-wise kernels (ionic, field, combine, update)
+constexpr int kVecBlock = 256;    // block of the copy, extrapolation and finish kernels
+cudaError_t launch_ionic_batch(const IonicLaunch& proto, const IonicLaunch* tab, const int* blk, int nseg,
+                               int nblocks, cudaStream_t st);
+cudaError_t launch_field_batch(int model, int precision, const FieldArgs* tab, const int* blk, int nseg, int nblocks,
+                               cudaStream_t st);
+cudaError_t launch_combine_batch(int model, const CombineArgs* tab, const int* blk, int nseg, int nblocks,
+                                 cudaStream_t st);
+cudaError_t launch_update_batch(int model, const UpdateArgs* tab, const int* blk, int nseg, int nblocks,
+                                cudaStream_t st);
+cudaError_t launch_copy_batch(const CopyArgs* tab, const int* blk, int nseg, int nblocks, cudaStream_t st);
+cudaError_t launch_extrap_batch(const ExtrapArgs* tab, const int* blk, int nseg, int nblocks, cudaStream_t st);
+cudaError_t launch_finish_batch(const FinishArgs* tab, const int* blk, int nseg, int nblocks, cudaStream_t st);
+
 // sparse (pcg.cu)
 //
 // Operators are stored in sliced ELL ("SELL-32"): rows are grouped in slices
@@ -304,7 +366,7 @@ struct StreamScal {               // device scalars of one streaming solve
   double mean_b, bb, tol2;        // right-hand side mean (projected systems), |b|^2, tol^2 |b|^2
   double rr64, scale, tgt;        // outer residual, its norm, inner target (relative, squared)
   double rr_new, rho, alpha, beta, shift;
-  int outer, it, fail, stop, inner_ran, skip, first, pad;
+  int outer, it, fail, stop, inner_ran, skip, first, more;   // more: wants another outer pass
   long long inner_total, outer_total;
   unsigned ticket, pad2;
 };
@@ -330,6 +392,9 @@ struct StreamLaunch {
   double* b64;                    // FP64 right-hand side
   double* r64;                    // FP64 outer residual
   void *r, *z, *p, *q, *d, *invd; // inner-precision vectors
+  const void* h0_invd;            // AMG level 0 (inner precision): 1/D, pre-smoothed x, damping weight
+  void* h0_x;
+  double h0_omega;
   void* part;                     // block partial sums (grid x 4 doubles)
   StreamScal* sc;
   int* status;
@@ -348,6 +413,43 @@ struct StreamLaunch {
 cudaError_t stream_solve(const StreamLaunch& a, int f32, const AmgDevF* M32, const AmgDev* M64, cudaStream_t st,
                          const cudaStream_t* side);
 int stream_grid_cap();
+int stream_grid(int64_t rows);
+
+// ---- batched solves (one launch per phase for many independent systems) -----
+// A batch of nseg systems runs every phase of its solves as one launch over
+// the concatenation of their rows: block b of a launch belongs to the system r
+// with blk[r] <= b < blk[r+1] (a prefix of per-system block counts) and runs
+// that system's rows with that system's parameters, reductions, scalars,
+// stopping test and iteration cap.  The loops of the batch continue while any
+// system still iterates: each system votes once per deciding launch and the
+// last vote sets the loop conditions.
+struct BatchCtl {
+  unsigned inner_iters;           // passes of the batch's inner loop in this outer pass
+  unsigned outer_iters;           // passes of its outer loop in this solve
+};
+struct BatchSolve {
+  const StreamLaunch* tab;        // device: one StreamLaunch per system
+  int nseg;
+  int f32;
+  BatchCtl* ctl;                  // device
+  long long* launch_acc;          // device counter of the batch's launches
+  // device block prefixes (nseg + 1 entries each): row kernels, and per
+  // hierarchy level the kernels over A_l (post: at least one block a system),
+  // R_l and P_l, and the coarse solve
+  const int* blk_rows;
+  const int* blk_post0;
+  const int* blk_A[kMaxAmgLevels];
+  const int* blk_R[kMaxAmgLevels];
+  const int* blk_P[kMaxAmgLevels];
+  const int* blk_coarse;
+  int total_rows_blocks, total_post0_blocks;
+  int total_A[kMaxAmgLevels], total_R[kMaxAmgLevels], total_P[kMaxAmgLevels], total_coarse;
+  int nlev_max;                   // deepest hierarchy of the batch
+  unsigned inner_cap, max_outer;  // largest per-system caps (the batch loops' backstop)
+  const void* hier;               // device: one AmgDevT<float or double> per system (nlev = 0: Jacobi)
+};
+// Enqueue a batched solve (captured or not) on st; side as for stream_solve.
+cudaError_t stream_solve_batch(const BatchSolve& b, cudaStream_t st, const cudaStream_t* side);
 
 // host assembly (assemble.cpp)
 struct HostOps {

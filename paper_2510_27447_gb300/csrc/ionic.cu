@@ -12,12 +12,13 @@
 
 #include "bd_internal.h"
 #include "models.cuh"
+#include "segment.cuh"
 
 namespace bd {
 
 namespace {
 
-constexpr int kBlock = 128;
+constexpr int kBlock = kNodeBlock;
 
 __device__ __forceinline__ double stim_current(const uint32_t* bits, int64_t i, const StimTable& st,
                                                double t, double dt) {
@@ -49,10 +50,9 @@ struct Params<TP06> {
 // condensation kernel: S1, S2 and correction modes
 // ---------------------------------------------------------------------------
 template <template <class> class Model, class T, int MODE, int NQ = 0>
-__global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, const Model<T> P) {
+__device__ __forceinline__ void ionic_body(const IonicLaunch& L, const Model<T>& P, int64_t i) {
   using Mod = Model<T>;
   constexpr int NS = Mod::NS;
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= L.n) return;
   if (L.gate && *L.gate == 0) return;
   const int64_t n = L.n;
@@ -189,14 +189,26 @@ __global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, cons
   }
 }
 
+template <template <class> class Model, class T, int MODE, int NQ = 0>
+__global__ void __launch_bounds__(kBlock) ionic_kernel(const IonicLaunch L, const Model<T> P) {
+  ionic_body<Model, T, MODE, NQ>(L, P, int64_t(blockIdx.x) * blockDim.x + threadIdx.x);
+}
+
+// the same over the nodes of a batch of handles (parameters per handle)
+template <template <class> class Model, class T, int MODE, int NQ = 0>
+__global__ void __launch_bounds__(kBlock) ionic_batch_kernel(const IonicLaunch* tab, const int* blk, int nseg,
+                                                             const Model<T> P) {
+  const SegInfo sg = seg_locate(blk, nseg);
+  const IonicLaunch& L = stage(tab, sg.r);
+  ionic_body<Model, T, MODE, NQ>(L, P, int64_t(sg.lb) * blockDim.x + threadIdx.x);
+}
+
 template <template <class> class Model, class T>
-__global__ void __launch_bounds__(kBlock) field_kernel(int64_t n, const double* X, double inv_cm, double dt,
-                                                       const uint32_t* stim_bits, const double* t_now,
-                                                       const StimTable stim, double* fout, const Model<T> P,
-                                                       const int* gate) {
+__device__ __forceinline__ void field_body(int64_t n, const double* X, double inv_cm, double dt,
+                                           const uint32_t* stim_bits, const double* t_now, const StimTable& stim,
+                                           double* fout, const Model<T>& P, const int* gate, int64_t i) {
   using Mod = Model<T>;
   constexpr int NS = Mod::NS;
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (gate && *gate == 0) return;
   const double t = t_now ? *t_now : 0.0;
@@ -208,6 +220,24 @@ __global__ void __launch_bounds__(kBlock) field_kernel(int64_t n, const double* 
   P.eval(x, T(istim), T(inv_cm), fs);
 #pragma unroll
   for (int k = 0; k < NS; ++k) fout[k * n + i] = double(fs.f[k]);
+}
+
+template <template <class> class Model, class T>
+__global__ void __launch_bounds__(kBlock) field_kernel(int64_t n, const double* X, double inv_cm, double dt,
+                                                       const uint32_t* stim_bits, const double* t_now,
+                                                       const StimTable stim, double* fout, const Model<T> P,
+                                                       const int* gate) {
+  field_body<Model, T>(n, X, inv_cm, dt, stim_bits, t_now, stim, fout, P, gate,
+                       int64_t(blockIdx.x) * blockDim.x + threadIdx.x);
+}
+
+template <template <class> class Model, class T>
+__global__ void __launch_bounds__(kBlock) field_batch_kernel(const FieldArgs* tab, const int* blk, int nseg,
+                                                             const Model<T> P) {
+  const SegInfo sg = seg_locate(blk, nseg);
+  const FieldArgs& a = stage(tab, sg.r);
+  field_body<Model, T>(a.n, a.X, a.inv_cm, a.dt, a.stim_bits, a.t_now, a.stim, a.fout, P, nullptr,
+                       int64_t(sg.lb) * blockDim.x + threadIdx.x);
 }
 
 // X_{m+1} = X + m1 k1 + m2 k2, k_y = z + w k_v  (ROS2 combination, Eq. (3.14)).
@@ -375,6 +405,109 @@ __global__ void clear_gated_kernel(unsigned long long* p, const int* gate) {
   *p = 0ull;
 }
 
+// ---- batched forms of the node-wise kernels (one launch over many handles)
+// Each block works on one handle's nodes with that handle's arguments; the
+// arithmetic per node is the one of the single-handle kernels above.
+
+template <int NS>
+__global__ void __launch_bounds__(kBlock) combine_batch_kernel(const CombineArgs* tab, const int* blk, int nseg) {
+  const SegInfo sg = seg_locate(blk, nseg);
+  const CombineArgs& a = stage(tab, sg.r);
+  const int64_t i = int64_t(sg.lb) * blockDim.x + threadIdx.x;
+  const int64_t n = a.n;
+  if (i >= n) return;
+  const double k1 = a.k1v[i], k2 = a.k2v[i];
+  a.dst[i] = a.src[i] + a.m1 * k1 + a.m2 * k2;
+#pragma unroll
+  for (int k = 1; k < NS; ++k) {
+    const int64_t o = (k - 1) * n + i;
+    const double y1 = a.z1[o] + a.w1[o] * k1;
+    const double y2 = a.z2[o] + a.w2[o] * k2;
+    a.dst[k * n + i] = a.src[k * n + i] + a.m1 * y1 + a.m2 * y2;
+  }
+}
+
+template <int NS>
+__global__ void __launch_bounds__(kBlock) update_batch_kernel(const UpdateArgs* tab, const int* blk, int nseg) {
+  const SegInfo sg = seg_locate(blk, nseg);
+  const UpdateArgs& a = stage(tab, sg.r);
+  const int64_t i = int64_t(sg.lb) * blockDim.x + threadIdx.x;
+  const int64_t n = a.n;
+  if (i >= n) return;
+  const double e = a.ev[i];
+  a.dst[i] = a.Xt[i] + e;
+#pragma unroll
+  for (int k = 1; k < NS; ++k) {
+    const int64_t o = (k - 1) * n + i;
+    a.dst[k * n + i] = a.Xt[k * n + i] + a.z[o] + a.w[o] * e;
+  }
+}
+
+__global__ void __launch_bounds__(kVecBlock) copy_batch_kernel(const CopyArgs* tab, const int* blk, int nseg) {
+  const SegInfo sg = seg_locate(blk, nseg);
+  const CopyArgs& a = stage(tab, sg.r);
+  const int64_t i = int64_t(sg.lb) * blockDim.x + threadIdx.x;
+  if (i < a.n) a.dst[i] = a.src[i];
+}
+
+// extrap_kernel per handle; the clock's valid flag is set by the per-handle
+// kernel below, after every block of the handle has read the clock
+__global__ void __launch_bounds__(kVecBlock) extrap_batch_kernel(const ExtrapArgs* tab, const int* blk, int nseg) {
+  const SegInfo sg = seg_locate(blk, nseg);
+  const ExtrapArgs& a = stage(tab, sg.r);
+  const int64_t i = int64_t(sg.lb) * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const double h = a.clk[0] - a.clk[1];
+  const double r = (a.clk[2] != 0.0 && h > 0.0) ? fmin(a.dt / h, 4.0) : 0.0;
+  const double e = a.u2[i];
+  const double d = e - a.ep[i];
+  if (a.u1) a.u1[i] = e + a.c1 * r * d;
+  a.u2[i] = e + r * d;
+  a.ep[i] = e;
+}
+__global__ void set_valid_batch_kernel(const ExtrapArgs* tab, int nseg) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nseg) tab[r].clk[2] = 1.0;
+}
+
+__global__ void __launch_bounds__(kVecBlock) finish_batch_kernel(const FinishArgs* tab, const int* blk, int nseg) {
+  const SegInfo sg = seg_locate(blk, nseg);
+  const FinishArgs& a = stage(tab, sg.r);
+  const int64_t i = int64_t(sg.lb) * blockDim.x + threadIdx.x;
+  const double t = *a.t_now;
+  if (i < a.n) {
+    const double vo = a.Xn[i], vn = a.Xlast[i];
+    if (!isfinite(vn)) atomicOr(a.status, ST_NONFINITE);
+    if (isnan(a.t_act[i]) && vo < a.v_act && vn >= a.v_act) a.t_act[i] = t + (a.v_act - vo) / (vn - vo) * a.dt;
+    for (int k = 0; k < a.ns; ++k) a.Xn[k * a.n + i] = a.Xlast[k * a.n + i];
+  }
+  if (i < a.nu) a.u0[i] = a.ulast[i];
+}
+__global__ void bump_batch_kernel(const FinishArgs* tab, int nseg) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nseg) return;
+  const FinishArgs& a = tab[r];
+  *a.step_n += 1;
+  a.t_now[1] = a.t_now[0];
+  a.t_now[0] += a.dt;
+}
+
+template <template <class> class Model, class T>
+cudaError_t launch_ionic_batch_t(const IonicLaunch& L, const IonicLaunch* tab, const int* blk, int nseg, int nb,
+                                 cudaStream_t st) {
+  const auto P = Params<Model>::template get<T>(L.model);
+  switch (L.mode) {
+    case MODE_S1: ionic_batch_kernel<Model, T, MODE_S1><<<nb, kBlock, 0, st>>>(tab, blk, nseg, P); break;
+    case MODE_S2: ionic_batch_kernel<Model, T, MODE_S2><<<nb, kBlock, 0, st>>>(tab, blk, nseg, P); break;
+    case MODE_S2P: ionic_batch_kernel<Model, T, MODE_S2P><<<nb, kBlock, 0, st>>>(tab, blk, nseg, P); break;
+    default:
+      if (L.n_nodes == 3) ionic_batch_kernel<Model, T, MODE_CORR, 3><<<nb, kBlock, 0, st>>>(tab, blk, nseg, P);
+      else ionic_batch_kernel<Model, T, MODE_CORR, 2><<<nb, kBlock, 0, st>>>(tab, blk, nseg, P);
+      break;
+  }
+  return cudaGetLastError();
+}
+
 template <template <class> class Model, class T>
 cudaError_t launch_ionic_t(const IonicLaunch& L, cudaStream_t st) {
   const auto P = Params<Model>::template get<T>(L.model);
@@ -415,6 +548,65 @@ cudaError_t launch_ionic(const IonicLaunch& L, cudaStream_t st) {
   const bool f32 = L.precision == BD_MIXED;
   if (L.model == BD_TP06_EPI) return f32 ? launch_ionic_t<TP06, float>(L, st) : launch_ionic_t<TP06, double>(L, st);
   return f32 ? launch_ionic_t<LR91, float>(L, st) : launch_ionic_t<LR91, double>(L, st);
+}
+
+cudaError_t launch_ionic_batch(const IonicLaunch& L, const IonicLaunch* tab, const int* blk, int nseg, int nb,
+                               cudaStream_t st) {
+  if (nb == 0) return cudaSuccess;
+  const bool f32 = L.precision == BD_MIXED;
+  if (L.model == BD_TP06_EPI)
+    return f32 ? launch_ionic_batch_t<TP06, float>(L, tab, blk, nseg, nb, st)
+               : launch_ionic_batch_t<TP06, double>(L, tab, blk, nseg, nb, st);
+  return f32 ? launch_ionic_batch_t<LR91, float>(L, tab, blk, nseg, nb, st)
+             : launch_ionic_batch_t<LR91, double>(L, tab, blk, nseg, nb, st);
+}
+
+cudaError_t launch_field_batch(int model, int precision, const FieldArgs* tab, const int* blk, int nseg, int nb,
+                               cudaStream_t st) {
+  if (nb == 0) return cudaSuccess;
+  const bool f32 = precision == BD_MIXED;
+  if (model == BD_TP06_EPI) {
+    if (f32) field_batch_kernel<TP06, float><<<nb, kBlock, 0, st>>>(tab, blk, nseg, TP06<float>::make());
+    else field_batch_kernel<TP06, double><<<nb, kBlock, 0, st>>>(tab, blk, nseg, TP06<double>::make());
+  } else {
+    const bool pm = model == BD_LR91_PAPER_MOD;
+    if (f32) field_batch_kernel<LR91, float><<<nb, kBlock, 0, st>>>(tab, blk, nseg, LR91<float>::make(pm));
+    else field_batch_kernel<LR91, double><<<nb, kBlock, 0, st>>>(tab, blk, nseg, LR91<double>::make(pm));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine_batch(int model, const CombineArgs* tab, const int* blk, int nseg, int nb,
+                                 cudaStream_t st) {
+  if (nb == 0) return cudaSuccess;
+  if (model == BD_TP06_EPI) combine_batch_kernel<19><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+  else combine_batch_kernel<8><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_batch(int model, const UpdateArgs* tab, const int* blk, int nseg, int nb, cudaStream_t st) {
+  if (nb == 0) return cudaSuccess;
+  if (model == BD_TP06_EPI) update_batch_kernel<19><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+  else update_batch_kernel<8><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_batch(const CopyArgs* tab, const int* blk, int nseg, int nb, cudaStream_t st) {
+  if (nb == 0) return cudaSuccess;
+  copy_batch_kernel<<<nb, kVecBlock, 0, st>>>(tab, blk, nseg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extrap_batch(const ExtrapArgs* tab, const int* blk, int nseg, int nb, cudaStream_t st) {
+  if (nb > 0) extrap_batch_kernel<<<nb, kVecBlock, 0, st>>>(tab, blk, nseg);
+  set_valid_batch_kernel<<<(nseg + 127) / 128, 128, 0, st>>>(tab, nseg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_batch(const FinishArgs* tab, const int* blk, int nseg, int nb, cudaStream_t st) {
+  if (nb > 0) finish_batch_kernel<<<nb, kVecBlock, 0, st>>>(tab, blk, nseg);
+  bump_batch_kernel<<<(nseg + 127) / 128, 128, 0, st>>>(tab, nseg);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_field(int model, int precision, int64_t n, const double* X, double inv_cm, double dt,

@@ -1,5 +1,5 @@
-// stream.cu -- streaming preconditioned conjugate gradients for operators
-// that do not fit in L2.
+// stream.cu -- streaming preconditioned conjugate gradients, for one system
+// whose operators do not fit in L2 and for batches of many small systems.
 //
 // The persistent solvers (pcg.cu, amg.cu, mixed.cu) keep one grid resident
 // for a whole solve and separate its phases with device-wide barriers; that
@@ -20,21 +20,30 @@
 //         (or what the outer tolerance still needs)
 //   FP64  x += |r| d; repeat (iterative refinement) up to max_outer passes,
 //         or stop after one pass (max_outer = 1: the single inner solve is the
-//         answer, to tol relative to |b|)
+//         answer)
 // then the pin / zero-mean shift of the elliptic solution.
 //
-// Reductions: every block writes its partial sums, the last block to arrive
-// (an atomic ticket) adds them in block order -- deterministic for a fixed
-// grid -- and takes the solve's scalar decisions.  A kernel whose work is
-// skipped (a finished loop, a closed sweep gate) reads the flag that says so
-// at entry; the flag is written by an earlier kernel, so every block of a
-// launch takes the same branch.
+// Every kernel takes its parameters through a policy: One (a single system,
+// the parameters by value, the whole grid its own) or Many (a batch: a table
+// of per-system parameters and a block -> system map; see BatchSolve).  A
+// system's arithmetic does not depend on the policy or on the other systems
+// of a batch (its reductions run over its own blocks in the same order), so a
+// system gives the same bits alone in a batch of one and in any batch.
+//
+// Reductions: every block writes its partial sums, the last block of the
+// system to arrive (an atomic ticket) adds them in block order and takes the
+// system's scalar decisions.  A kernel whose work is skipped (a finished
+// loop, a closed sweep gate) reads the flag that says so at entry; the flag
+// is written by an earlier kernel, so every block of a system takes the same
+// branch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "bd_internal.h"
 #include "sparse.cuh"
+#include "segment.cuh"
 #include "vcycle.cuh"
 
 namespace bd {
@@ -43,6 +52,76 @@ namespace {
 
 constexpr int kSB = 256;       // threads per block of every streaming kernel
 constexpr int kBlocksPerSM = 8;
+
+// ---- policies -------------------------------------------------------------------
+
+struct One {
+  StreamLaunch a;
+};
+struct Many {
+  const StreamLaunch* tab;
+  const int* blk;              // block prefix of this launch
+  int nseg;
+  BatchCtl* ctl;
+  long long* launch_acc;
+  unsigned long long h_outer, h_inner;
+};
+template <class T>
+struct VcOne {
+  AmgDevT<T> H;
+};
+template <class T>
+struct VcMany {
+  const AmgDevT<T>* tab;
+  const int* blk;
+  int nseg;
+};
+
+template <class S>
+constexpr bool kMany = std::is_same_v<S, Many>;
+
+__device__ __forceinline__ SegInfo seg_of(const One&) { return {0, int(blockIdx.x), int(gridDim.x)}; }
+__device__ __forceinline__ SegInfo seg_of(const Many& m) { return seg_locate(m.blk, m.nseg); }
+template <class T>
+__device__ __forceinline__ SegInfo seg_of(const VcOne<T>&) { return {0, int(blockIdx.x), int(gridDim.x)}; }
+template <class T>
+__device__ __forceinline__ SegInfo seg_of(const VcMany<T>& m) { return seg_locate(m.blk, m.nseg); }
+
+__device__ __forceinline__ const StreamLaunch& params(const One& o, int) { return o.a; }
+__device__ __forceinline__ const StreamLaunch& params(const Many& m, int r) { return stage(m.tab, r); }
+template <class T>
+__device__ __forceinline__ const AmgDevT<T>& hier(const VcOne<T>& o, int) { return o.H; }
+template <class T>
+__device__ __forceinline__ const AmgDevT<T>& hier(const VcMany<T>& m, int r) { return stage(m.tab, r); }
+
+// every kernel counts its launch (the loops run on the device, so the host
+// cannot); a batched launch counts once
+__device__ __forceinline__ void count_launch(long long* acc) {
+  if (acc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(acc), 1ull);
+}
+__device__ __forceinline__ void count_launch(const One& o) { count_launch(o.a.launch_acc); }
+__device__ __forceinline__ void count_launch(const Many& m) { count_launch(m.launch_acc); }
+
+__device__ __forceinline__ void set_cond(unsigned long long h, unsigned v) {
+  cudaGraphSetConditional(static_cast<cudaGraphConditionalHandle>(h), v);
+}
+
+// Loop conditions.  A single system sets them directly when it decides.  A
+// batch's conditions are set by st_batch_cond_kernel at the end of each loop
+// body from every system's flags (the loop continues while any system still
+// iterates), with a hard cap on the passes.
+__device__ __forceinline__ void vote_inner(const One&, const StreamLaunch& a, bool active) {
+  if (!active) {
+    set_cond(a.h_inner, 0u);
+    if (a.sc->fail) set_cond(a.h_outer, 0u);
+  }
+}
+__device__ __forceinline__ void vote_inner(const Many&, const StreamLaunch&, bool) {}
+__device__ __forceinline__ void vote_outer(const One&, const StreamLaunch& a, bool inner_on, bool outer_on) {
+  set_cond(a.h_inner, inner_on ? 1u : 0u);
+  set_cond(a.h_outer, outer_on ? 1u : 0u);
+}
+__device__ __forceinline__ void vote_outer(const Many&, const StreamLaunch&, bool, bool) {}
 
 // ---- row products ------------------------------------------------------------
 
@@ -85,13 +164,13 @@ __device__ __forceinline__ X srow(const int64_t* __restrict__ sptr, const int* _
 }
 
 // every row i of an AMG-level operator (SELL: thread per row; CSR: warp per
-// row, butterfly sum): epi(i, (M x)_i), run by one lane per row
-// (level 0's operators are streamed with evict-first loads, the coarser
-// levels' stay cacheable: they are read twice a cycle and fit in L2)
+// row, butterfly sum): epi(i, (M x)_i), run by one lane per row.  Level 0's
+// operators are streamed with evict-first loads, the coarser levels' stay
+// cacheable (read twice a cycle, they fit in L2).
 template <class T, class F>
-__device__ __forceinline__ void level_rows(const SellDevT<T>& M, const T* x, bool streamop, F&& epi) {
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gs = gridDim.x * blockDim.x;
+__device__ __forceinline__ void level_rows(const SellDevT<T>& M, const T* x, bool streamop, SegInfo sg, F&& epi) {
+  const int gt = sg.lb * blockDim.x + threadIdx.x;
+  const int gs = sg.nb * blockDim.x;
   if (M.rp) {
     const int lane = threadIdx.x & 31;
     for (int i = gt >> 5; i < M.n; i += gs >> 5) {
@@ -109,19 +188,13 @@ __device__ __forceinline__ void level_rows(const SellDevT<T>& M, const T* x, boo
   }
 }
 
-// every kernel of a streaming solve counts its launch (the loops run on the
-// device, so the host cannot)
-__device__ __forceinline__ void count_launch(long long* acc) {
-  if (acc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(acc), 1ull);
-}
-
 // ---- reductions ----------------------------------------------------------------
 
-// Block sums of v[0..NV) into part, an atomic ticket, and in the last block to
-// arrive the grid totals (block order, fixed tree): returns true there, with
-// v holding the totals in every thread of that block; false elsewhere.
+// Block sums of v[0..NV) into part, the system's atomic ticket, and in its last
+// block to arrive the system's totals (block order, fixed tree): returns true
+// there, with v holding the totals in every thread of that block.
 template <int NV, class T>
-__device__ __forceinline__ bool last_block_total(T (&v)[NV], void* partv, unsigned* ticket) {
+__device__ __forceinline__ bool last_block_total(T (&v)[NV], void* partv, unsigned* ticket, SegInfo sg) {
   __shared__ T sh[NV][32];
   __shared__ T tot[NV];
   __shared__ int amlast;
@@ -129,9 +202,9 @@ __device__ __forceinline__ bool last_block_total(T (&v)[NV], void* partv, unsign
   block_sum<NV, T>(v, sh);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) part[blockIdx.x * NV + k] = v[k];
+    for (int k = 0; k < NV; ++k) part[sg.lb * NV + k] = v[k];
     __threadfence();
-    amlast = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    amlast = atomicAdd(ticket, 1u) == unsigned(sg.nb) - 1u;
   }
   __syncthreads();
   if (!amlast) return false;
@@ -139,7 +212,7 @@ __device__ __forceinline__ bool last_block_total(T (&v)[NV], void* partv, unsign
   T acc[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) acc[k] = T(0);
-  for (int b = threadIdx.x; b < int(gridDim.x); b += blockDim.x)
+  for (int b = threadIdx.x; b < sg.nb; b += blockDim.x)
 #pragma unroll
     for (int k = 0; k < NV; ++k) acc[k] += __ldcg(part + b * NV + k);
   block_sum<NV, T>(acc, sh);
@@ -154,15 +227,12 @@ __device__ __forceinline__ bool last_block_total(T (&v)[NV], void* partv, unsign
   return true;
 }
 
-__device__ __forceinline__ void set_cond(unsigned long long h, unsigned v) {
-  cudaGraphSetConditional(static_cast<cudaGraphConditionalHandle>(h), v);
-}
-
 // Decision after the inner residual r and the preconditioned z are complete
-// (thread 0 of the last block): the first one of an inner solve sets rho,
-// later ones close an iteration as the persistent kernel's loop does.
+// (thread 0 of the system's last block): the first one of an inner solve sets
+// rho, later ones close an iteration as the persistent kernel's loop does.
+// Returns whether the inner loop continues.
 template <class T>
-__device__ __forceinline__ void inner_decide(const StreamLaunch& a, T rz) {
+__device__ __forceinline__ bool inner_decide(const StreamLaunch& a, T rz) {
   StreamScal& c = *a.sc;
   bool done = false;
   const T rr = T(c.rr_new);
@@ -188,24 +258,28 @@ __device__ __forceinline__ void inner_decide(const StreamLaunch& a, T rz) {
   if (done) {
     c.stop = 1;
     c.inner_total += c.it;
-    set_cond(a.h_inner, 0u);
-    if (c.fail) set_cond(a.h_outer, 0u);
   }
+  return !done;
 }
+
+#define SEG_BEGIN(src)                             \
+  count_launch(src);                               \
+  const SegInfo sg = seg_of(src);                  \
+  const StreamLaunch& a = params(src, sg.r);       \
+  const int gt = sg.lb * blockDim.x + threadIdx.x; \
+  const int gs = sg.nb * blockDim.x;
 
 // ---- kernels -------------------------------------------------------------------
 
 // right-hand side in FP64 (two operator products sharing the pattern), the
 // Jacobi scaling, a cold start's x = 0; the last block sets the solve up
-template <class T>
-__global__ void __launch_bounds__(kSB) st_rhs_kernel(const __grid_constant__ StreamLaunch a) {
-  count_launch(a.launch_acc);
+template <class T, class S>
+__global__ void __launch_bounds__(kSB) st_rhs_kernel(const __grid_constant__ S src) {
+  SEG_BEGIN(src)
   if (a.gate && *a.gate == 0) {        // the sweep test closed this solve (uniform)
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.sc->skip = 1;
+    if (sg.lb == 0 && threadIdx.x == 0) a.sc->skip = 1;
     return;
   }
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gs = gridDim.x * blockDim.x;
   T* invd = static_cast<T*>(a.invd);
   double acc[2] = {0.0, 0.0};
   const double* const pv[2] = {a.val1, a.val2};
@@ -227,7 +301,7 @@ __global__ void __launch_bounds__(kSB) st_rhs_kernel(const __grid_constant__ Str
     acc[0] += b;
     acc[1] += b * b;
   }
-  if (last_block_total<2, double>(acc, a.part, &a.sc->ticket) && threadIdx.x == 0) {
+  if (last_block_total<2, double>(acc, a.part, &a.sc->ticket, sg) && threadIdx.x == 0) {
     StreamScal& c = *a.sc;
     const double mean = a.project ? acc[0] / double(a.n) : 0.0;
     double bb = a.project ? acc[1] - double(a.n) * mean * mean : acc[1];
@@ -246,21 +320,19 @@ __global__ void __launch_bounds__(kSB) st_rhs_kernel(const __grid_constant__ Str
 }
 
 // FP64 outer residual r = b - A x (b projected) and the outer decision
-template <class T>
-__global__ void __launch_bounds__(kSB) st_outer_kernel(const __grid_constant__ StreamLaunch a) {
-  count_launch(a.launch_acc);
+template <class T, class S>
+__global__ void __launch_bounds__(kSB) st_outer_kernel(const __grid_constant__ S src) {
+  SEG_BEGIN(src)
   StreamScal& c = *a.sc;
   if (c.skip || c.fail) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (sg.lb == 0 && threadIdx.x == 0) {
       c.inner_ran = 0;
       c.stop = 1;
-      set_cond(a.h_inner, 0u);
-      set_cond(a.h_outer, 0u);
+      c.more = 0;
+      vote_outer(src, a, false, false);
     }
     return;
   }
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gs = gridDim.x * blockDim.x;
   const double mean = c.mean_b;
   const bool product = c.outer > 0 || a.warm;
   double acc[1] = {0.0};
@@ -274,7 +346,7 @@ __global__ void __launch_bounds__(kSB) st_outer_kernel(const __grid_constant__ S
     a.r64[i] = r;
     acc[0] += r * r;
   }
-  if (last_block_total<1, double>(acc, a.part, &c.ticket) && threadIdx.x == 0) {
+  if (last_block_total<1, double>(acc, a.part, &c.ticket, sg) && threadIdx.x == 0) {
     const double rr = acc[0];
     c.rr64 = rr;
     c.outer_total += 1;
@@ -293,8 +365,8 @@ __global__ void __launch_bounds__(kSB) st_outer_kernel(const __grid_constant__ S
     if (done) {
       c.inner_ran = 0;
       c.stop = 1;
-      set_cond(a.h_inner, 0u);
-      set_cond(a.h_outer, 0u);
+      c.more = 0;
+      vote_outer(src, a, false, false);
     } else {
       c.scale = sqrt(rr);
       // inner target relative to |r|^2: the FP32 solves follow the persistent
@@ -311,26 +383,30 @@ __global__ void __launch_bounds__(kSB) st_outer_kernel(const __grid_constant__ S
       c.inner_ran = 1;
       c.beta = 0.0;
       c.outer += 1;
-      set_cond(a.h_inner, 1u);
-      set_cond(a.h_outer, a.max_outer > 1 ? 1u : 0u);
+      c.more = a.max_outer > 1 ? 1 : 0;
+      vote_outer(src, a, true, a.max_outer > 1);
     }
   }
 }
 
 // inner start: r = r64 / |r|, d = 0, the first preconditioning step
 // (Jacobi z = D^-1 r and the first decision; AMG: the level-0 pre-smoothing)
-template <class T>
-__global__ void __launch_bounds__(kSB) st_inner_init_kernel(const __grid_constant__ StreamLaunch a, const T* invd0,
-                                                            T omega0, T* x0) {
-  count_launch(a.launch_acc);
+template <class T, class S>
+__global__ void __launch_bounds__(kSB) st_inner_init_kernel(const __grid_constant__ S src) {
+  SEG_BEGIN(src)
   StreamScal& c = *a.sc;
-  if (c.stop) return;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gs = gridDim.x * blockDim.x;
+  if (c.stop) {
+    if constexpr (kMany<S>)
+      if (sg.lb == 0 && threadIdx.x == 0) vote_inner(src, a, false);
+    return;
+  }
   T* r = static_cast<T*>(a.r);
   T* z = static_cast<T*>(a.z);
   T* d = static_cast<T*>(a.d);
   const T* invd = static_cast<const T*>(a.invd);
+  const T* invd0 = static_cast<const T*>(a.h0_invd);
+  T* x0 = static_cast<T*>(a.h0_x);
+  const T omega0 = T(a.h0_omega);
   const double inv_scale = 1.0 / c.scale;
   T acc[2] = {T(0), T(0)};
   for (int i = gt; i < a.n; i += gs) {
@@ -346,20 +422,23 @@ __global__ void __launch_bounds__(kSB) st_inner_init_kernel(const __grid_constan
       acc[1] += ri * zi;
     }
   }
-  if (last_block_total<2, T>(acc, a.part, &c.ticket) && threadIdx.x == 0) {
+  if (last_block_total<2, T>(acc, a.part, &c.ticket, sg) && threadIdx.x == 0) {
     c.rr_new = double(acc[0]);
-    if (!a.use_amg) inner_decide<T>(a, acc[1]);
+    if (!a.use_amg) vote_inner(src, a, inner_decide<T>(a, acc[1]));
+    else if constexpr (kMany<S>) vote_inner(src, a, true);
   }
 }
 
 // p = z + beta p, q = A z + beta q (q = A p by recurrence), p.q and alpha
-template <class T>
-__global__ void __launch_bounds__(kSB) st_pq_kernel(const __grid_constant__ StreamLaunch a) {
-  count_launch(a.launch_acc);
+template <class T, class S>
+__global__ void __launch_bounds__(kSB) st_pq_kernel(const __grid_constant__ S src) {
+  SEG_BEGIN(src)
   StreamScal& c = *a.sc;
-  if (c.stop) return;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gs = gridDim.x * blockDim.x;
+  if (c.stop) {
+    if constexpr (kMany<S>)
+      if (sg.lb == 0 && threadIdx.x == 0) vote_inner(src, a, false);
+    return;
+  }
   const T* z = static_cast<const T*>(a.z);
   T* p = static_cast<T*>(a.p);
   T* q = static_cast<T*>(a.q);
@@ -377,36 +456,41 @@ __global__ void __launch_bounds__(kSB) st_pq_kernel(const __grid_constant__ Stre
     q[i] = qi;
     acc[0] += pi * qi;
   }
-  if (last_block_total<1, T>(acc, a.part, &c.ticket) && threadIdx.x == 0) {
+  if (last_block_total<1, T>(acc, a.part, &c.ticket, sg) && threadIdx.x == 0) {
     const T pq = acc[0];
+    bool active = true;
     if (!(pq > T(0))) {       // breakdown: keep d, the outer pass decides
       if (!isfinite(pq)) c.fail |= ST_NONFINITE;
       c.stop = 1;
       c.inner_total += c.it;
-      set_cond(a.h_inner, 0u);
-      if (c.fail) set_cond(a.h_outer, 0u);
+      active = false;
     } else {
       c.alpha = double(T(c.rho) / pq);
     }
+    if (!active || kMany<S>) vote_inner(src, a, active);
   }
 }
 
 // d += alpha p, r -= alpha q, |r|^2; Jacobi: z = D^-1 r, r.z and the decision;
 // AMG: the level-0 pre-smoothing of the next cycle
-template <class T>
-__global__ void __launch_bounds__(kSB) st_update_kernel(const __grid_constant__ StreamLaunch a, const T* invd0,
-                                                        T omega0, T* x0) {
-  count_launch(a.launch_acc);
+template <class T, class S>
+__global__ void __launch_bounds__(kSB) st_update_kernel(const __grid_constant__ S src) {
+  SEG_BEGIN(src)
   StreamScal& c = *a.sc;
-  if (c.stop) return;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gs = gridDim.x * blockDim.x;
+  if (c.stop) {
+    if constexpr (kMany<S>)
+      if (sg.lb == 0 && threadIdx.x == 0) vote_inner(src, a, false);
+    return;
+  }
   T* r = static_cast<T*>(a.r);
   T* z = static_cast<T*>(a.z);
   T* d = static_cast<T*>(a.d);
   const T* p = static_cast<const T*>(a.p);
   const T* q = static_cast<const T*>(a.q);
   const T* invd = static_cast<const T*>(a.invd);
+  const T* invd0 = static_cast<const T*>(a.h0_invd);
+  T* x0 = static_cast<T*>(a.h0_x);
+  const T omega0 = T(a.h0_omega);
   const T alpha = T(c.alpha);
   T acc[2] = {T(0), T(0)};
   for (int i = gt; i < a.n; i += gs) {
@@ -422,122 +506,220 @@ __global__ void __launch_bounds__(kSB) st_update_kernel(const __grid_constant__ 
       acc[1] += ri * zi;
     }
   }
-  if (last_block_total<2, T>(acc, a.part, &c.ticket) && threadIdx.x == 0) {
+  if (last_block_total<2, T>(acc, a.part, &c.ticket, sg) && threadIdx.x == 0) {
     c.rr_new = double(acc[0]);
-    if (!a.use_amg) inner_decide<T>(a, acc[1]);
+    if (!a.use_amg) vote_inner(src, a, inner_decide<T>(a, acc[1]));
+    else if constexpr (kMany<S>) vote_inner(src, a, true);
   }
 }
 
-// ---- V(1,1) cycle, one kernel per phase (the cycle of amg.cu) ----------------
+// The batch's loop conditions (one block): phase 0 starts a solve (outer pass
+// counter), 1 starts an inner loop (inner = any system iterating), 2 closes an
+// inner pass, 3 closes an outer pass (outer = any system wanting another).
+// The pass caps are a backstop: every system stops itself at its own caps.
+__global__ void __launch_bounds__(kSB) st_batch_cond_kernel(const __grid_constant__ Many m, int phase,
+                                                            unsigned cap) {
+  count_launch(m);
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  if (phase != 0) {
+    int mine = 0;
+    for (int r = threadIdx.x; r < m.nseg; r += blockDim.x) {
+      const StreamScal& c = *m.tab[r].sc;
+      mine |= phase == 3 ? (c.more && !c.fail) : !c.stop;
+    }
+    if (mine) atomicOr(&any, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  BatchCtl& b = *m.ctl;
+  if (phase == 0) {
+    b.outer_iters = 0u;
+  } else if (phase == 1) {
+    b.inner_iters = 0u;
+    set_cond(m.h_inner, any ? 1u : 0u);
+  } else if (phase == 2) {
+    b.inner_iters += 1u;
+    set_cond(m.h_inner, (any && b.inner_iters < cap) ? 1u : 0u);
+  } else {
+    b.outer_iters += 1u;
+    set_cond(m.h_outer, (any && b.outer_iters < cap) ? 1u : 0u);
+  }
+}
+
+// ---- V(1,1) cycle, one kernel per phase and level (the cycle of amg.cu) -----
+//
+// V (VcOne / VcMany) gives a block its system's hierarchy, S its solve (stop
+// flag, level-0 vectors); both resolve the same system for a block.
 
 // r_l = b_l - A_l x_l
-template <class T>
-__global__ void __launch_bounds__(kSB) st_vc_res_kernel(const StreamScal* sc, long long* lc,
-                                                        const __grid_constant__ AmgLevelDevT<T> L, const T* b,
-                                                        int level0) {
-  count_launch(lc);
-  if (sc->stop) return;
-  level_rows<T>(L.A, L.x, level0 != 0, [&](int i, T ax) { L.r[i] = b[i] - ax; });
+template <class T, class V, class S>
+__global__ void __launch_bounds__(kSB) st_vc_res_kernel(const __grid_constant__ V hv, const __grid_constant__ S src,
+                                                        int l) {
+  count_launch(src);
+  const SegInfo sg = seg_of(hv);
+  const AmgDevT<T>& H = hier(hv, sg.r);
+  const StreamLaunch& a = params(src, sg.r);
+  if (a.sc->stop || l >= H.nlev) return;
+  const AmgLevelDevT<T>& L = H.L[l];
+  const T* b = l == 0 ? static_cast<const T*>(a.r) : L.b;
+  level_rows<T>(L.A, L.x, l == 0, sg, [&](int i, T ax) { L.r[i] = b[i] - ax; });
 }
 
 // b_{l+1} = R_l r_l and the next level's pre-smoothing x_{l+1} = w D^-1 b_{l+1}
-template <class T>
-__global__ void __launch_bounds__(kSB) st_vc_restrict_kernel(const StreamScal* sc, long long* lc,
-                                                             const __grid_constant__ AmgLevelDevT<T> L, T* bn,
-                                                             const T* invdn, T omegan, T* xn, int level0) {
-  count_launch(lc);
-  if (sc->stop) return;
-  level_rows<T>(L.R, L.r, level0 != 0, [&](int i, T v) {
+template <class T, class V, class S>
+__global__ void __launch_bounds__(kSB) st_vc_restrict_kernel(const __grid_constant__ V hv,
+                                                             const __grid_constant__ S src, int l) {
+  count_launch(src);
+  const SegInfo sg = seg_of(hv);
+  const AmgDevT<T>& H = hier(hv, sg.r);
+  const StreamLaunch& a = params(src, sg.r);
+  if (a.sc->stop || l >= H.nlev) return;
+  const AmgLevelDevT<T>& L = H.L[l];
+  const bool last = l + 1 == H.nlev;
+  T* bn = last ? H.bc : H.L[l + 1].b;
+  T* xn = last ? nullptr : H.L[l + 1].x;
+  const T* invdn = last ? nullptr : H.L[l + 1].invd;
+  const T omegan = last ? T(0) : H.L[l + 1].omega;
+  level_rows<T>(L.R, L.r, l == 0, sg, [&](int i, T v) {
     bn[i] = v;
     if (xn) xn[i] = omegan * invdn[i] * v;
   });
 }
 
-template <class T>
-__global__ void __launch_bounds__(kSB) st_vc_coarse_kernel(const StreamScal* sc, long long* lc, const T* cinv, int nc,
-                                                           int ldc, const T* bc, T* xc) {
-  count_launch(lc);
-  if (sc->stop) return;
-  const T* bcs[1] = {bc};
-  T* xcs[1] = {xc};
-  coarse_solve<T, 1>(cinv, nc, ldc, bcs, xcs);
+// dense coarsest solve xc = Cinv bc: one warp per row of the system's coarse
+// inverse (rows padded to 16-byte multiples), 16-byte loads, butterfly sum
+template <class T, class V, class S>
+__global__ void __launch_bounds__(kSB) st_vc_coarse_kernel(const __grid_constant__ V hv,
+                                                           const __grid_constant__ S src) {
+  count_launch(src);
+  const SegInfo sg = seg_of(hv);
+  const AmgDevT<T>& H = hier(hv, sg.r);
+  const StreamLaunch& a = params(src, sg.r);
+  if (a.sc->stop || H.nlev == 0) return;
+  using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int E = 16 / int(sizeof(T));
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int nvec = H.ldc / E;
+  if (sg.lb * wpb >= H.nc) return;                 // no rows in this block (uniform)
+  __shared__ __align__(16) T sbc[kCoarseStage];
+  const bool staged = H.ldc <= kCoarseStage;       // the right-hand side in shared memory
+  if (staged) {
+    for (int j = threadIdx.x; j < H.ldc; j += blockDim.x) sbc[j] = j < H.nc ? __ldcg(H.bc + j) : T(0);
+    __syncthreads();
+  }
+  for (int i = sg.lb * wpb + (threadIdx.x >> 5); i < H.nc; i += sg.nb * wpb) {
+    const VT* row = reinterpret_cast<const VT*>(H.cinv + int64_t(i) * H.ldc);
+    T s = T(0);
+    for (int q = lane; q < nvec; q += 32) {
+      const VT cv = __ldg(row + q);
+      if (staged) {
+        s += dot_vec(cv, &sbc[q * E]);
+      } else {
+        T bq[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+          const int j = q * E + k;
+          bq[k] = j < H.nc ? __ldcg(H.bc + j) : T(0);
+        }
+        s += dot_vec(cv, bq);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) H.xc[i] = s;
+  }
 }
 
 // x_l += P_l y_{l+1}
-template <class T>
-__global__ void __launch_bounds__(kSB) st_vc_prolong_kernel(const StreamScal* sc, long long* lc,
-                                                            const __grid_constant__ AmgLevelDevT<T> L, const T* yc,
-                                                            int level0) {
-  count_launch(lc);
-  if (sc->stop) return;
-  level_rows<T>(L.P, yc, level0 != 0, [&](int i, T v) { L.x[i] += v; });
+template <class T, class V, class S>
+__global__ void __launch_bounds__(kSB) st_vc_prolong_kernel(const __grid_constant__ V hv,
+                                                            const __grid_constant__ S src, int l) {
+  count_launch(src);
+  const SegInfo sg = seg_of(hv);
+  const AmgDevT<T>& H = hier(hv, sg.r);
+  const StreamLaunch& a = params(src, sg.r);
+  if (a.sc->stop || l >= H.nlev) return;
+  const AmgLevelDevT<T>& L = H.L[l];
+  const T* yc = l + 1 == H.nlev ? H.xc : H.L[l + 1].y;
+  level_rows<T>(L.P, yc, l == 0, sg, [&](int i, T v) { L.x[i] += v; });
 }
 
 // y_l = x_l + w D^-1 (b_l - A_l x_l); on level 0 y is z, r.z and the decision
-template <class T>
-__global__ void __launch_bounds__(kSB) st_vc_post_kernel(const __grid_constant__ StreamLaunch a,
-                                                         const __grid_constant__ AmgLevelDevT<T> L, const T* b, T* y,
-                                                         int level0) {
-  count_launch(a.launch_acc);
+// (every system of a batch has at least one block here and votes)
+template <class T, class V, class S>
+__global__ void __launch_bounds__(kSB) st_vc_post_kernel(const __grid_constant__ V hv, const __grid_constant__ S src,
+                                                         int l) {
+  count_launch(src);
+  const SegInfo sg = seg_of(hv);
+  const AmgDevT<T>& H = hier(hv, sg.r);
+  const StreamLaunch& a = params(src, sg.r);
   StreamScal& c = *a.sc;
-  if (c.stop) return;
+  if (c.stop) {
+    if constexpr (kMany<S>)
+      if (l == 0 && sg.lb == 0 && threadIdx.x == 0) vote_inner(src, a, false);
+    return;
+  }
+  if (l >= H.nlev) {            // a Jacobi system of a batch: nothing to do at level 0
+    if constexpr (kMany<S>)
+      if (l == 0 && sg.lb == 0 && threadIdx.x == 0) vote_inner(src, a, true);
+    return;
+  }
+  const AmgLevelDevT<T>& L = H.L[l];
+  const T* b = l == 0 ? static_cast<const T*>(a.r) : L.b;
+  T* y = l == 0 ? static_cast<T*>(a.z) : L.y;
   T acc[1] = {T(0)};
-  level_rows<T>(L.A, L.x, level0 != 0, [&](int i, T ax) {
+  level_rows<T>(L.A, L.x, l == 0, sg, [&](int i, T ax) {
     const T bi = b[i];
     const T yi = L.x[i] + L.omega * L.invd[i] * (bi - ax);
     y[i] = yi;
     acc[0] += bi * yi;
   });
-  if (!level0) return;
-  if (last_block_total<1, T>(acc, a.part, &c.ticket) && threadIdx.x == 0) inner_decide<T>(a, acc[0]);
+  if (l != 0) return;
+  if (last_block_total<1, T>(acc, a.part, &c.ticket, sg) && threadIdx.x == 0)
+    vote_inner(src, a, inner_decide<T>(a, acc[0]));
 }
 
 // x += |r| d after an inner solve that ran without failure
-__global__ void __launch_bounds__(kSB) st_xupdate_kernel(const __grid_constant__ StreamLaunch a, int f32) {
-  count_launch(a.launch_acc);
+template <class T, class S>
+__global__ void __launch_bounds__(kSB) st_xupdate_kernel(const __grid_constant__ S src) {
+  SEG_BEGIN(src)
   const StreamScal& c = *a.sc;
   if (!c.inner_ran || c.fail) return;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gs = gridDim.x * blockDim.x;
   const double s = c.scale;
-  if (f32) {
-    const float* d = static_cast<const float*>(a.d);
-    for (int i = gt; i < a.n; i += gs) a.x[i] += s * double(d[i]);
-  } else {
-    const double* d = static_cast<const double*>(a.d);
-    for (int i = gt; i < a.n; i += gs) a.x[i] += s * d[i];
-  }
+  const T* d = static_cast<const T*>(a.d);
+  for (int i = gt; i < a.n; i += gs) a.x[i] += s * double(d[i]);
 }
 
 // normalisation of the singular elliptic solution: the shift (u[pin], or the
 // nodal mean)
-__global__ void __launch_bounds__(kSB) st_shift_kernel(const __grid_constant__ StreamLaunch a) {
-  count_launch(a.launch_acc);
+template <class S>
+__global__ void __launch_bounds__(kSB) st_shift_kernel(const __grid_constant__ S src) {
+  SEG_BEGIN(src)
   StreamScal& c = *a.sc;
-  if (c.skip) return;
+  if (c.skip || a.pin < -1) return;
   if (a.pin >= 0) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) c.shift = a.x[a.pin];
+    if (sg.lb == 0 && threadIdx.x == 0) c.shift = a.x[a.pin];
     return;
   }
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-  const int gs = gridDim.x * blockDim.x;
   double acc[1] = {0.0};
   for (int i = gt; i < a.n; i += gs) acc[0] += a.x[i];
-  if (last_block_total<1, double>(acc, a.part, &c.ticket) && threadIdx.x == 0) c.shift = acc[0] / double(a.n);
+  if (last_block_total<1, double>(acc, a.part, &c.ticket, sg) && threadIdx.x == 0) c.shift = acc[0] / double(a.n);
 }
 
 // x -= shift (pin >= -1); the solve's status and counters
-__global__ void __launch_bounds__(kSB) st_finish_kernel(const __grid_constant__ StreamLaunch a) {
-  count_launch(a.launch_acc);
+template <class S>
+__global__ void __launch_bounds__(kSB) st_finish_kernel(const __grid_constant__ S src) {
+  SEG_BEGIN(src)
   const StreamScal& c = *a.sc;
   if (c.skip) return;
   if (a.pin >= -1) {
     const double sh = c.shift;
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int gs = gridDim.x * blockDim.x;
     for (int i = gt; i < a.n; i += gs) a.x[i] -= sh;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (sg.lb == 0 && threadIdx.x == 0) {
     if (c.fail) atomicOr(a.status, c.fail);
     if (a.iters_acc) atomicAdd(reinterpret_cast<unsigned long long*>(a.iters_acc), (unsigned long long)c.inner_total);
     if (a.outer_acc) atomicAdd(reinterpret_cast<unsigned long long*>(a.outer_acc), (unsigned long long)c.outer_total);
@@ -553,40 +735,6 @@ int grid_for(int64_t threads) {
 }
 
 int level_grid(const void* rp, int n) { return grid_for(rp ? int64_t(n) * 32 : int64_t(n)); }
-
-// the V-cycle z = V(r) of one hierarchy on stream s
-template <class T>
-cudaError_t enqueue_vcycle(const StreamLaunch& a, const AmgDevT<T>& M, const T* r, T* z, cudaStream_t s) {
-  const int L = M.nlev;
-  for (int l = 0; l < L; ++l) {
-    const AmgLevelDevT<T>& Lv = M.L[l];
-    const T* b = l == 0 ? r : Lv.b;
-    const int l0 = l == 0 ? 1 : 0;
-    st_vc_res_kernel<T><<<l0 ? a.grid : level_grid(Lv.A.rp, Lv.A.n), kSB, 0, s>>>(a.sc, a.launch_acc, Lv, b, l0);
-    const bool last = l + 1 == L;
-    T* bn = last ? M.bc : M.L[l + 1].b;
-    const T* invdn = last ? nullptr : M.L[l + 1].invd;
-    const T omegan = last ? T(0) : M.L[l + 1].omega;
-    T* xn = last ? nullptr : M.L[l + 1].x;
-    st_vc_restrict_kernel<T><<<level_grid(Lv.R.rp, Lv.R.n), kSB, 0, s>>>(a.sc, a.launch_acc, Lv, bn, invdn, omegan,
-                                                                          xn, l0);
-  }
-  {
-    const int warps = std::max(1, M.nc);
-    st_vc_coarse_kernel<T><<<grid_for(int64_t(warps) * 32), kSB, 0, s>>>(a.sc, a.launch_acc, M.cinv, M.nc, M.ldc,
-                                                                          M.bc, M.xc);
-  }
-  for (int l = L - 1; l >= 0; --l) {
-    const AmgLevelDevT<T>& Lv = M.L[l];
-    const T* yc = l + 1 == L ? M.xc : M.L[l + 1].y;
-    const int l0 = l == 0 ? 1 : 0;
-    st_vc_prolong_kernel<T><<<level_grid(Lv.P.rp, Lv.P.n), kSB, 0, s>>>(a.sc, a.launch_acc, Lv, yc, l0);
-    const T* b = l == 0 ? r : Lv.b;
-    T* y = l == 0 ? z : Lv.y;
-    st_vc_post_kernel<T><<<l0 ? a.grid : level_grid(Lv.A.rp, Lv.A.n), kSB, 0, s>>>(a, Lv, b, y, l0);
-  }
-  return cudaGetLastError();
-}
 
 // add a WHILE node after the current capture frontier of `cap` and return its
 // body graph; the capture continues after the node
@@ -617,56 +765,176 @@ cudaGraph_t capture_graph(cudaStream_t s) {
   return cs == cudaStreamCaptureStatusActive ? g : nullptr;
 }
 
+// The launches of one solve (One) or of one batch of solves (Many): the
+// policies and grids of every kernel family.
+template <class T>
+struct Plan {
+  bool many = false;
+  One one{};
+  Many many_base{};
+  VcOne<T> vone{};
+  VcMany<T> vmany{};
+  const BatchSolve* bs = nullptr;
+  int rows_grid = 1, nlev = 0, coarse_grid = 1;
+  int gA[kMaxAmgLevels] = {}, gR[kMaxAmgLevels] = {}, gP[kMaxAmgLevels] = {};
+  bool amg = false;
+  Many mk(const int* blk) const {
+    Many m = many_base;
+    m.blk = blk;
+    return m;
+  }
+  VcMany<T> vmk(const int* blk) const {
+    VcMany<T> v = vmany;
+    v.blk = blk;
+    return v;
+  }
+};
+
+// a kernel of the row family under either policy (KNAME<T, policy> or,
+// without the value type, KNAME<policy>)
+#define ROWS_LAUNCH_T(KNAME, stream)                                                                   \
+  do {                                                                                                 \
+    if (P.many) KNAME<T, Many><<<P.bs->total_rows_blocks, kSB, 0, stream>>>(P.mk(P.bs->blk_rows));      \
+    else KNAME<T, One><<<P.rows_grid, kSB, 0, stream>>>(P.one);                                        \
+  } while (0)
+#define ROWS_LAUNCH_S(KNAME, stream)                                                                   \
+  do {                                                                                                 \
+    if (P.many) KNAME<Many><<<P.bs->total_rows_blocks, kSB, 0, stream>>>(P.mk(P.bs->blk_rows));         \
+    else KNAME<One><<<P.rows_grid, kSB, 0, stream>>>(P.one);                                           \
+  } while (0)
+
+template <class T>
+void enqueue_vcycle(const Plan<T>& P, cudaStream_t s) {
+  for (int l = 0; l < P.nlev; ++l) {
+    if (P.many) {
+      const Many m = P.mk(P.bs->blk_rows);
+      st_vc_res_kernel<T, VcMany<T>, Many><<<P.bs->total_A[l], kSB, 0, s>>>(P.vmk(P.bs->blk_A[l]), m, l);
+      st_vc_restrict_kernel<T, VcMany<T>, Many><<<P.bs->total_R[l], kSB, 0, s>>>(P.vmk(P.bs->blk_R[l]), m, l);
+    } else {
+      st_vc_res_kernel<T, VcOne<T>, One><<<P.gA[l], kSB, 0, s>>>(P.vone, P.one, l);
+      st_vc_restrict_kernel<T, VcOne<T>, One><<<P.gR[l], kSB, 0, s>>>(P.vone, P.one, l);
+    }
+  }
+  if (P.many)
+    st_vc_coarse_kernel<T, VcMany<T>, Many><<<P.bs->total_coarse, kSB, 0, s>>>(P.vmk(P.bs->blk_coarse),
+                                                                                P.mk(P.bs->blk_rows));
+  else
+    st_vc_coarse_kernel<T, VcOne<T>, One><<<P.coarse_grid, kSB, 0, s>>>(P.vone, P.one);
+  for (int l = P.nlev - 1; l >= 0; --l) {
+    if (P.many) {
+      const Many m = P.mk(P.bs->blk_rows);
+      st_vc_prolong_kernel<T, VcMany<T>, Many><<<P.bs->total_P[l], kSB, 0, s>>>(P.vmk(P.bs->blk_P[l]), m, l);
+      if (l == 0)
+        st_vc_post_kernel<T, VcMany<T>, Many><<<P.bs->total_post0_blocks, kSB, 0, s>>>(
+            P.vmk(P.bs->blk_post0), P.mk(P.bs->blk_post0), 0);
+      else
+        st_vc_post_kernel<T, VcMany<T>, Many><<<P.bs->total_A[l], kSB, 0, s>>>(P.vmk(P.bs->blk_A[l]), m, l);
+    } else {
+      st_vc_prolong_kernel<T, VcOne<T>, One><<<P.gP[l], kSB, 0, s>>>(P.vone, P.one, l);
+      st_vc_post_kernel<T, VcOne<T>, One><<<l == 0 ? P.rows_grid : P.gA[l], kSB, 0, s>>>(P.vone, P.one, l);
+    }
+  }
+}
+
 // the solve's kernels and loops, appended to the capture of `st`
 template <class T>
-cudaError_t enqueue_solve(StreamLaunch a, const AmgDevT<T>* M, cudaStream_t st, const cudaStream_t* side) {
+cudaError_t enqueue_solve(Plan<T>& P, cudaStream_t st, const cudaStream_t* side) {
   cudaGraph_t g = capture_graph(st);
   if (!g) return cudaErrorStreamCaptureUnsupported;
   cudaGraphConditionalHandle ho, hi;
   cudaError_t e = cudaGraphConditionalHandleCreate(&ho, g, 1, cudaGraphCondAssignDefault);
   if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hi, g, 0, 0);
   if (e != cudaSuccess) return e;
-  a.h_outer = static_cast<unsigned long long>(ho);
-  a.h_inner = static_cast<unsigned long long>(hi);
-  const bool amg = a.use_amg && M;
-  const T* invd0 = amg ? M->L[0].invd : nullptr;
-  const T omega0 = amg ? M->L[0].omega : T(0);
-  T* x0 = amg ? M->L[0].x : nullptr;
-  T* r = static_cast<T*>(a.r);
-  T* z = static_cast<T*>(a.z);
-
-  st_rhs_kernel<T><<<a.grid, kSB, 0, st>>>(a);
+  P.one.a.h_outer = P.many_base.h_outer = static_cast<unsigned long long>(ho);
+  P.one.a.h_inner = P.many_base.h_inner = static_cast<unsigned long long>(hi);
+  ROWS_LAUNCH_T(st_rhs_kernel, st);
+  if (P.many) st_batch_cond_kernel<<<1, kSB, 0, st>>>(P.mk(P.bs->blk_rows), 0, 0u);
   cudaGraph_t ob = nullptr;
   if ((e = add_while(st, ho, &ob)) != cudaSuccess) return e;
   // outer body: residual and decision, inner start, inner loop, x update
   if ((e = cudaStreamBeginCaptureToGraph(side[0], ob, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
       cudaSuccess)
     return e;
-  st_outer_kernel<T><<<a.grid, kSB, 0, side[0]>>>(a);
-  st_inner_init_kernel<T><<<a.grid, kSB, 0, side[0]>>>(a, invd0, omega0, x0);
-  if (amg) enqueue_vcycle<T>(a, *M, r, z, side[0]);
+  ROWS_LAUNCH_T(st_outer_kernel, side[0]);
+  ROWS_LAUNCH_T(st_inner_init_kernel, side[0]);
+  if (P.amg) enqueue_vcycle<T>(P, side[0]);
+  if (P.many) st_batch_cond_kernel<<<1, kSB, 0, side[0]>>>(P.mk(P.bs->blk_rows), 1, 0u);
   cudaGraph_t ib = nullptr;
   e = add_while(side[0], hi, &ib);
   if (e == cudaSuccess)
     e = cudaStreamBeginCaptureToGraph(side[1], ib, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    st_pq_kernel<T><<<a.grid, kSB, 0, side[1]>>>(a);
-    st_update_kernel<T><<<a.grid, kSB, 0, side[1]>>>(a, invd0, omega0, x0);
-    if (amg) enqueue_vcycle<T>(a, *M, r, z, side[1]);
+    ROWS_LAUNCH_T(st_pq_kernel, side[1]);
+    ROWS_LAUNCH_T(st_update_kernel, side[1]);
+    if (P.amg) enqueue_vcycle<T>(P, side[1]);
+    if (P.many) st_batch_cond_kernel<<<1, kSB, 0, side[1]>>>(P.mk(P.bs->blk_rows), 2, P.bs->inner_cap + 1u);
     cudaGraph_t tmp = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(side[1], &tmp);
     if (e == cudaSuccess) e = e2;
   }
-  if (e == cudaSuccess) st_xupdate_kernel<<<a.grid, kSB, 0, side[0]>>>(a, sizeof(T) == 4 ? 1 : 0);
+  if (e == cudaSuccess) ROWS_LAUNCH_T(st_xupdate_kernel, side[0]);
+  if (e == cudaSuccess && P.many)
+    st_batch_cond_kernel<<<1, kSB, 0, side[0]>>>(P.mk(P.bs->blk_rows), 3, P.bs->max_outer + 1u);
   {
     cudaGraph_t tmp = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(side[0], &tmp);
     if (e == cudaSuccess) e = e2;
   }
   if (e != cudaSuccess) return e;
-  if (a.pin >= -1) st_shift_kernel<<<a.grid, kSB, 0, st>>>(a);
-  st_finish_kernel<<<a.grid, kSB, 0, st>>>(a);
+  ROWS_LAUNCH_S(st_shift_kernel, st);
+  ROWS_LAUNCH_S(st_finish_kernel, st);
   return cudaGetLastError();
+}
+
+// Outside a capture the solve is captured into a graph of its own, launched
+// and destroyed; inside one it is appended.
+template <class F>
+cudaError_t run_captured(cudaStream_t st, F&& body) {
+  cudaStreamCaptureStatus cs;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  if (cs == cudaStreamCaptureStatusActive) return body();
+  if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+  const cudaError_t r = body();
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(st, &g);
+  if (r != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) return e;
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return e;
+  e = cudaGraphUpload(ex, st);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ex, st);
+  cudaGraphExecDestroy(ex);   // released once the launch completes
+  return e;
+}
+
+template <class T>
+Plan<T> one_plan(const StreamLaunch& a, const AmgDevT<T>* M) {
+  Plan<T> P;
+  P.one.a = a;
+  P.amg = a.use_amg && M && M->nlev > 0;
+  if (P.amg) {
+    P.vone.H = *M;
+    P.nlev = M->nlev;
+    for (int l = 0; l < P.nlev; ++l) {
+      P.gA[l] = level_grid(M->L[l].A.rp, M->L[l].A.n);
+      P.gR[l] = level_grid(M->L[l].R.rp, M->L[l].R.n);
+      P.gP[l] = level_grid(M->L[l].P.rp, M->L[l].P.n);
+    }
+    P.coarse_grid = grid_for(int64_t(std::max(1, M->nc)) * 32);
+    P.one.a.h0_invd = M->L[0].invd;
+    P.one.a.h0_x = M->L[0].x;
+    P.one.a.h0_omega = double(M->L[0].omega);
+  } else {
+    P.one.a.use_amg = 0;
+  }
+  P.rows_grid = a.grid;
+  return P;
 }
 
 }  // namespace
@@ -685,31 +953,35 @@ int stream_grid_cap() {
   return cap;
 }
 
-// Outside a capture the solve is captured into a graph of its own, launched
-// and destroyed (the eager and profiling paths); inside one it is appended.
+int stream_grid(int64_t rows) { return grid_for(rows); }
+
 cudaError_t stream_solve(const StreamLaunch& a, int f32, const AmgDevF* M32, const AmgDev* M64, cudaStream_t st,
                          const cudaStream_t* side) {
-  cudaStreamCaptureStatus cs;
-  cudaError_t e = cudaStreamIsCapturing(st, &cs);
-  if (e != cudaSuccess) return e;
-  auto body = [&]() { return f32 ? enqueue_solve<float>(a, M32, st, side) : enqueue_solve<double>(a, M64, st, side); };
-  if (cs == cudaStreamCaptureStatusActive) return body();
-  if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
-  const cudaError_t r = body();
-  cudaGraph_t g = nullptr;
-  e = cudaStreamEndCapture(st, &g);
-  if (r != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
-    return r;
+  if (f32) {
+    Plan<float> P = one_plan<float>(a, M32);
+    return run_captured(st, [&]() { return enqueue_solve<float>(P, st, side); });
   }
-  if (e != cudaSuccess) return e;
-  cudaGraphExec_t ex = nullptr;
-  e = cudaGraphInstantiate(&ex, g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) return e;
-  e = cudaGraphLaunch(ex, st);
-  cudaGraphExecDestroy(ex);   // released once the launch completes
-  return e;
+  Plan<double> P = one_plan<double>(a, M64);
+  return run_captured(st, [&]() { return enqueue_solve<double>(P, st, side); });
+}
+
+cudaError_t stream_solve_batch(const BatchSolve& b, cudaStream_t st, const cudaStream_t* side) {
+  auto run = [&](auto tag) {
+    using T = decltype(tag);
+    Plan<T> P;
+    P.many = true;
+    P.bs = &b;
+    P.many_base.tab = b.tab;
+    P.many_base.nseg = b.nseg;
+    P.many_base.ctl = b.ctl;
+    P.many_base.launch_acc = b.launch_acc;
+    P.vmany.tab = static_cast<const AmgDevT<T>*>(b.hier);
+    P.vmany.nseg = b.nseg;
+    P.nlev = b.nlev_max;
+    P.amg = b.nlev_max > 0;
+    return run_captured(st, [&]() { return enqueue_solve<T>(P, st, side); });
+  };
+  return b.f32 ? run(float{}) : run(double{});
 }
 
 }  // namespace bd
