@@ -447,28 +447,133 @@ def lv_leg(args, torch, stream, flush) -> dict:
     return out
 
 
+def batch_leg(args) -> dict:
+    """Batched execution (bd_batch_step) of args.batch_requests independent
+    requests of the serving stream's shape (sides 33/65/129, LR91/TP06 50/50,
+    jittered conductivities), each timed for args.batch_steps steps of
+    dt = 0.02 ms: one launch per phase over the concatenated nodes of a batch,
+    packed by the autotuner, against the same requests stepped one at a time
+    (each its own graph) in the same precision."""
+    from paper_2510_27447_gb300 import binding, workloads as W
+    from paper_2510_27447_gb300.batching import BatchRunner
+    reqs = W.request_stream(args.batch_requests, 40.0, seed=5, sides=(33, 65, 129), t_end=10.0)
+    ws = [W.request_workload(r) for r in reqs]
+    dt, steps, warm = 0.02, args.batch_steps, 3
+    nodes = sum(w.n_nodes for w in ws)
+    out = {"requests": len(ws), "nodes": nodes, "sides": [33, 65, 129], "steps": steps,
+           "models": {"lr91": sum(w.model == W.LR91 for w in ws), "tp06": sum(w.model == W.TP06_EPI for w in ws)}}
+    for name, prec in (("mixed", binding.MIXED), ("fp64", binding.FP64)):
+        opts = lambda: binding.default_options(precision=prec)
+        el = 0.0
+        for w in ws:
+            sim = binding.simulation_from_workload(w, opts())
+            for _ in range(warm):
+                sim.step(dt, M_NODES, K_SWEEPS)
+            sim.sync()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                sim.step(dt, M_NODES, K_SWEEPS)
+            sim.sync()
+            el += time.perf_counter() - t0
+            sim.close()
+        alone = nodes * steps / el
+        sims = [binding.simulation_from_workload(w, opts()) for w in ws]
+        runner = BatchRunner()
+        t0 = time.perf_counter()
+        best = runner.tune(sims, dt, M_NODES, K_SWEEPS)
+        tune_s = time.perf_counter() - t0
+        runner.step(sims, dt, M_NODES, K_SWEEPS, warm)
+        for s in sims:
+            s.sync()
+        t0 = time.perf_counter()
+        runner.step(sims, dt, M_NODES, K_SWEEPS, steps)
+        for s in sims:
+            s.sync()
+        bt = time.perf_counter() - t0
+        packing = runner.packing(sims, dt, M_NODES, K_SWEEPS)
+        key = list(runner.timings)[0]
+        for s in sims:
+            s.close()
+        out[name] = {"batched_node_steps_per_s": round(nodes * steps / bt, 1),
+                     "one_at_a_time_node_steps_per_s": round(alone, 1),
+                     "speedup": round(alone and (nodes * steps / bt) / alone, 2),
+                     "batched_ms_per_step": round(1e3 * bt / steps, 3),
+                     "packing": best, "batches": len(packing), "tune_s": round(tune_s, 2),
+                     "candidate_ms_per_step": {k: round(1e3 * v, 3) for k, v in runner.timings[key].items()}}
+    return out
+
+
 def serve_leg(args) -> dict:
-    """Scaled serving workload (the 512-request, 400 ms stream is hours of GPU
-    time): args.serve_requests Poisson(40/s) arrivals, sides 33/65/129,
-    LR91/TP06 50/50, jittered conductivities, each simulated for
-    args.serve_ms ms.  Continuous batching on the mixed path vs the same
-    requests one at a time through the plain FP64 path."""
+    """The serving stream: args.serve_requests Poisson(40/s) arrivals (the
+    request recipe of the 512-request workload: sides 33/65/129/257,
+    LR91/TP06 50/50, jittered conductivities, strip and S2 positions), each
+    simulated for args.serve_ms ms at dt = 0.02 ms, mixed precision:
+      batched     resident requests advance together through bd_batch_step,
+                  joining at chunk boundaries (16 slots);
+      streams     each resident request on its own stream (8 slots);
+      closed      the batched form with 16 clients keeping one request each
+                  outstanding;
+      one at a time, mixed and FP64: every request's service time (handle
+                  set-up + its steps) measured on the GPU alone, the FIFO
+                  queue of the same arrivals computed from them exactly.
+    Handles are built by worker threads in every served form."""
     from paper_2510_27447_gb300 import binding, serving as S, workloads as W
-    reqs = W.request_stream(args.serve_requests, 40.0, seed=4, sides=(33, 65, 129), t_end=args.serve_ms)
+    sides = (33, 65, 129, 257)
+    reqs = W.request_stream(args.serve_requests, 40.0, seed=4, sides=sides, t_end=args.serve_ms)
 
     def jobs():
         return [S.Job(r.rid, r.arrival_s, r.side ** 2, int(round(args.serve_ms / r.dt)), W.request_workload(r))
                 for r in reqs]
-    out = {"requests": len(reqs), "rate_per_s": 40.0, "sides": [33, 65, 129], "t_end_ms": args.serve_ms,
-           "slots": 8, "chunk_steps": 25}
-    for name, prec, slots in (("batched_mixed", binding.MIXED, 8), ("one_at_a_time_fp64", binding.FP64, 1)):
-        ex = S.GpuExecutor(lambda p=prec: binding.default_options(precision=p), dt=0.02)
+    js = jobs()
+    out = {"requests": len(reqs), "rate_per_s": 40.0, "sides": list(sides), "t_end_ms": args.serve_ms,
+           "chunk_steps": 25, "work_node_steps": int(sum(j.n_nodes * j.n_steps for j in js))}
+
+    def record(sm, wall):
+        return {"p50_ms": round(sm["p50_ms"], 2), "p99_ms": round(sm["p99_ms"], 2),
+                "node_steps_per_s": round(sm["node_steps_per_s"], 1),
+                "offered_node_steps_per_s": round(sm["offered_node_steps_per_s"], 1),
+                "served_over_offered": round(sm["served_over_offered"], 4), "wall_s": round(wall, 2)}
+    mixed = lambda: binding.default_options(precision=binding.MIXED)          # noqa: E731
+    for name, batched, slots in (("batched_mixed", True, 16), ("streams_mixed", False, 8)):
+        ex = S.GpuExecutor(mixed, dt=0.02)
         t0 = time.perf_counter()
-        done = S.Server(ex, max_slots=slots, hbm_budget=32 << 30, chunk_steps=25).run(jobs())
+        done = S.Server(ex, max_slots=slots, hbm_budget=64 << 30, chunk_steps=25, batched=batched).run(jobs())
         wall = time.perf_counter() - t0
-        sm = S.summarize(done)
+        ex.close()
+        out[name] = record(S.summarize(done), wall)
+        out[name]["slots"] = slots
+    ex = S.GpuExecutor(mixed, dt=0.02)
+    t0 = time.perf_counter()
+    done = S.Server(ex, max_slots=16, hbm_budget=64 << 30, chunk_steps=25, batched=True).run_closed(jobs(), 16)
+    wall = time.perf_counter() - t0
+    ex.close()
+    sm = S.summarize(done)
+    out["closed_batched_mixed"] = {"clients": 16, "p50_ms": round(sm["p50_ms"], 2), "p99_ms": round(sm["p99_ms"], 2),
+                                   "node_steps_per_s": round(sm["node_steps_per_s"], 1), "wall_s": round(wall, 2)}
+    for name, prec in (("one_at_a_time_mixed", binding.MIXED), ("one_at_a_time_fp64", binding.FP64)):
+        service = []
+        for j in js:
+            t0 = time.perf_counter()
+            sim = binding.simulation_from_workload(j.payload, binding.default_options(precision=prec))
+            setup = time.perf_counter() - t0
+            k = min(j.n_steps, 20)
+            sim.step(0.02, M_NODES, K_SWEEPS)          # capture (part of the set-up)
+            sim.sync()
+            setup = time.perf_counter() - t0
+            t1 = time.perf_counter()
+            for _ in range(k):
+                sim.step(0.02, M_NODES, K_SWEEPS)
+            sim.sync()
+            per_step = (time.perf_counter() - t1) / k
+            sim.close()
+            service.append(setup + per_step * j.n_steps)
+        sm = S.summarize(S.fifo_schedule(js, service))
         out[name] = {"p50_ms": round(sm["p50_ms"], 2), "p99_ms": round(sm["p99_ms"], 2),
-                     "node_steps_per_s": round(sm["node_steps_per_s"], 1), "wall_s": round(wall, 2)}
+                     "node_steps_per_s": round(sm["node_steps_per_s"], 1),
+                     "served_over_offered": round(sm["served_over_offered"], 4),
+                     "service_s_total": round(sum(service), 2),
+                     "method": "service time per request measured alone on the GPU (set-up + 20 timed steps "
+                               "scaled to its step count); FIFO queue of the same arrivals computed exactly"}
     return out
 
 
@@ -563,6 +668,12 @@ def run_ours(args) -> None:
             lv = lv_leg(args, torch, stream, flush)
         except Exception as e:  # noqa: BLE001
             lv = {"error": str(e)[:300]}
+    batch = None
+    if args.batch_requests > 0:
+        try:
+            batch = batch_leg(args)
+        except Exception as e:  # noqa: BLE001
+            batch = {"error": str(e)[:300]}
     serve = None
     if args.serve_requests > 0:
         try:
@@ -621,6 +732,7 @@ def run_ours(args) -> None:
         "slab": slab,
         "bath": bath,
         "lv_shell_bath": lv,
+        "batch": batch,
         "serve": serve,
     }
     print(json.dumps(line), flush=True)
@@ -723,7 +835,10 @@ def main():
                     help="simulated time of the developed state the headline legs start from (ms)")
     ap.add_argument("--slab-steps", type=int, default=5,
                     help="timed steps of the 201x201x51 slab leg (0: skip)")
-    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--batch-requests", type=int, default=32,
+                    help="requests of the batched-execution leg (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batched-execution leg")
+    ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-ms", type=float, default=10.0)
     ap.add_argument("--lv-steps", type=int, default=0,
                     help="timed steps of the 3-D LV-shell-in-bath leg (0: skip; setup takes minutes)")

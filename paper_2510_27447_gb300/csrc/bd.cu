@@ -1099,6 +1099,7 @@ struct BatchPlan {
   };
   std::vector<G> graphs;
   int64_t enq = 0;                 // launches enqueued by the capture in progress
+  uint64_t last_use = 0;
   ~BatchPlan() {
     for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
     for (char* c : chunks) cudaFree(c);
@@ -1112,6 +1113,8 @@ struct BatchPlan {
 
 std::mutex g_batch_mu;
 std::vector<std::unique_ptr<BatchPlan>> g_batches;
+uint64_t g_batch_clock = 0;
+constexpr size_t kMaxBatchPlans = 16;   // plans kept (least recently used dropped first)
 
 // copy a table into the chunk of the capture in progress; returns its device address
 template <class T>
@@ -1975,7 +1978,21 @@ int bd_batch_step(bd_state_t* const* states, int n, double dt, int M, int K) {
       return fail(s0, BD_ERR_CUDA, "batch set-up failed");
     g_batches.push_back(std::move(P));
     B = g_batches.back().get();
+    if (g_batches.size() > kMaxBatchPlans) {   // drop the least recently used other plan
+      size_t lru = 0;
+      for (size_t i = 1; i < g_batches.size(); ++i)
+        if (g_batches[i]->last_use < g_batches[lru]->last_use) lru = i;
+      if (g_batches[lru].get() != B) {
+        for (bd_state* o : g_batches[lru]->m)
+          if (o->stream) cudaStreamSynchronize(o->stream);
+        g_batches.erase(g_batches.begin() + lru);
+        B = nullptr;
+        for (auto& p : g_batches)
+          if (int(p->m.size()) == n && std::equal(p->m.begin(), p->m.end(), states)) B = p.get();
+      }
+    }
   }
+  B->last_use = ++g_batch_clock;
   for (bd_state* h : B->m) {
     RUN(ensure_stream_ws(h));
     RUN(prepare_step(h, dt, M));

@@ -3,25 +3,36 @@
 Requests (independent tissue simulations of different mesh size, membrane
 model and stimulus protocol) arrive over time.  The server
   * admits a queued request as soon as a slot is free and its device
-    footprint (``bd_footprint_bytes``) fits in the remaining HBM budget,
-  * keeps every admitted simulation resident on the GPU, each on its own CUDA
-    stream, and keeps all of them advancing at once: whenever a simulation's
-    enqueued steps have completed (non-blocking ``bd_query``), the next chunk of
-    steps is enqueued (graph replays), so the work of different requests
-    overlaps on the device,
+    footprint (``bd_footprint_bytes``) fits in the remaining HBM budget; the
+    handle is built (host assembly, AMG set-up, upload) by a worker thread,
+    so admission never stalls the requests already on the GPU,
+  * keeps every admitted simulation resident on the GPU and keeps all of them
+    advancing at once, in one of two forms:
+      - per-request streams: whenever a simulation's enqueued steps have
+        completed (non-blocking ``bd_query``), its next chunk of steps is
+        enqueued (graph replays), so the work of different requests overlaps
+        on the device;
+      - batched (``batched=True``): resident simulations of the same group
+        (the executor's group_key: membrane model and mesh size, the packing
+        the batch autotuner prefers) advance together, a chunk at a time,
+        through ``bd_batch_step`` -- one launch per phase over their
+        concatenated nodes -- each group on its own stream and at its own
+        pace; a request admitted meanwhile joins its group at that group's
+        next chunk boundary,
   * completes a request when it has simulated its end time, reading its
     activation map, and frees its slot and memory for the queue.
 
 Latency = completion time - arrival time ("time to activation map").  The
-scheduler is written against a small executor interface so its admission and
-ordering logic can be tested on the CPU with a virtual-clock executor.
+scheduler is written against a small executor interface so its admission,
+ordering and batching logic can be tested on the CPU with a virtual-clock
+executor.
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
 import dataclasses
-import heapq
 import time
-from typing import Any, Callable, Dict, List, Optional
+from typing import Any, Callable, Dict, List, Optional, Sequence
 
 import numpy as np
 
@@ -50,42 +61,79 @@ class Completion:
         return self.finished - self.arrival
 
 
+class _Ready:
+    """An already completed preparation (executors without a worker pool)."""
+
+    def __init__(self, value):
+        self.value = value
+
+    def done(self) -> bool:
+        return True
+
+    def result(self):
+        return self.value
+
+
 class Executor:
-    """Interface the scheduler drives (all methods except advance/ready may block)."""
+    """Interface the scheduler drives.  prepare() must not block (it may hand
+    the handle's construction to a worker); advance*/ready* must not block."""
 
     def now(self) -> float: ...
     def footprint(self, job: Job) -> int: ...
-    def start(self, job: Job) -> Any: ...
-    def advance(self, h: Any, n_steps: int) -> None: ...      # enqueue, must not block
-    def ready(self, h: Any) -> bool: ...                      # must not block
+    def prepare(self, job: Job) -> Any: ...                   # future-like: done(), result() -> handle
+    def advance(self, h: Any, n_steps: int) -> None: ...      # per-request form
+    def ready(self, h: Any) -> bool: ...
+    def group_key(self, job: Job) -> Any: ...                 # batched form: jobs batched together
+    def advance_group(self, hs: Sequence[Any], n_steps: int) -> None: ...
+    def group_ready(self, hs: Sequence[Any]) -> bool: ...
     def finish(self, h: Any) -> Any: ...
     def release(self, h: Any) -> None: ...
     def idle(self) -> None: ...                               # nothing ready: yield / sleep
+    def wait_until(self, t: float) -> None: ...
 
 
 class Server:
     def __init__(self, executor: Executor, max_slots: int = 8, hbm_budget: int = 64 << 30,
-                 chunk_steps: int = 50):
+                 chunk_steps: int = 50, batched: bool = False):
         self.ex = executor
         self.max_slots = max_slots
         self.budget = hbm_budget
         self.chunk = chunk_steps
+        self.batched = batched
 
     def run(self, jobs: List[Job]) -> List[Completion]:
-        queue = sorted(jobs, key=lambda j: (j.arrival, j.rid))
+        """Open loop: each job arrives at its own time."""
+        return self._serve(sorted(jobs, key=lambda j: (j.arrival, j.rid)), None)
+
+    def run_closed(self, jobs: List[Job], clients: int) -> List[Completion]:
+        """Closed loop: `clients` clients each keep one request outstanding;
+        a client submits its next job (in list order) when its previous one
+        completes.  The jobs' own arrival times are ignored."""
+        return self._serve(list(jobs), clients)
+
+    def _serve(self, queue: List[Job], clients: Optional[int]) -> List[Completion]:
         qi = 0
-        waiting: List[Job] = []            # arrived, not admitted (FIFO)
+        total = len(queue)
+        waiting: List[Job] = []
+        starting: Dict[int, dict] = {}    # admitted, handle being built
         active: Dict[int, dict] = {}
         used = 0
         done: List[Completion] = []
-        total = len(queue)
-        while len(done) < total:
-            now = self.ex.now()
-            while qi < total and queue[qi].arrival <= now:
+        groups: Dict[Any, dict] = {}      # batched form: the chunk in flight, per group
+        if clients is not None:           # closed loop: the first `clients` jobs arrive now
+            t0 = self.ex.now()
+            for _ in range(min(clients, total)):
+                queue[qi] = dataclasses.replace(queue[qi], arrival=t0)
                 waiting.append(queue[qi])
                 qi += 1
-            # admission: FIFO, by free slot and footprint
-            while waiting and len(active) < self.max_slots:
+        while len(done) < total:
+            now = self.ex.now()
+            if clients is None:
+                while qi < total and queue[qi].arrival <= now:
+                    waiting.append(queue[qi])
+                    qi += 1
+            # admission: FIFO, by free slot and footprint; the handle is built by a worker
+            while waiting and len(active) + len(starting) < self.max_slots:
                 j = waiting[0]
                 fp = self.ex.footprint(j)
                 if fp > self.budget:
@@ -93,32 +141,73 @@ class Server:
                 if used + fp > self.budget:
                     break
                 waiting.pop(0)
-                h = self.ex.start(j)
                 used += fp
-                active[j.rid] = {"job": j, "h": h, "fp": fp, "steps": 0, "admitted": self.ex.now()}
-                n = min(self.chunk, j.n_steps)
-                self.ex.advance(h, n)
-                active[j.rid]["steps"] = n
+                starting[j.rid] = {"job": j, "fut": self.ex.prepare(j), "fp": fp, "admitted": self.ex.now()}
             progressed = False
-            for rid in list(active):
-                a = active[rid]
-                if not self.ex.ready(a["h"]):
-                    continue
-                progressed = True
+            for rid in list(starting):
+                st = starting[rid]
+                if st["fut"].done():
+                    progressed = True
+                    a = {"job": st["job"], "h": st["fut"].result(), "fp": st["fp"], "steps": 0,
+                         "admitted": st["admitted"]}
+                    del starting[rid]
+                    active[rid] = a
+                    if not self.batched:
+                        n = min(self.chunk, a["job"].n_steps)
+                        self.ex.advance(a["h"], n)
+                        a["steps"] = n
+
+            def complete(rid):
+                nonlocal used, qi
+                a = active.pop(rid)
                 j = a["job"]
-                if a["steps"] >= j.n_steps:
-                    res = self.ex.finish(a["h"])
-                    done.append(Completion(j.rid, j.arrival, a["admitted"], self.ex.now(), j.n_nodes,
-                                           j.n_steps, res))
-                    self.ex.release(a["h"])
-                    used -= a["fp"]
-                    del active[rid]
-                else:
-                    n = min(self.chunk, j.n_steps - a["steps"])
-                    self.ex.advance(a["h"], n)
-                    a["steps"] += n
+                res = self.ex.finish(a["h"])
+                done.append(Completion(j.rid, j.arrival, a["admitted"], self.ex.now(), j.n_nodes, j.n_steps, res))
+                self.ex.release(a["h"])
+                used -= a["fp"]
+                if clients is not None and qi < total:      # the client's next request
+                    queue[qi] = dataclasses.replace(queue[qi], arrival=self.ex.now())
+                    waiting.append(queue[qi])
+                    qi += 1
+
+            if self.batched:
+                for key in list(groups):
+                    g = groups[key]
+                    if self.ex.group_ready(g["hs"]):
+                        progressed = True
+                        for rid in g["rids"]:
+                            active[rid]["steps"] += g["n"]
+                            if active[rid]["steps"] >= active[rid]["job"].n_steps:
+                                complete(rid)
+                        del groups[key]
+                idle_members: Dict[Any, List[int]] = {}
+                busy = {rid for g in groups.values() for rid in g["rids"]}
+                for rid in sorted(active):
+                    if rid not in busy:
+                        idle_members.setdefault(self.ex.group_key(active[rid]["job"]), []).append(rid)
+                for key, rids in idle_members.items():
+                    if key in groups:
+                        continue                  # joins at this group's next chunk
+                    n = min([self.chunk] + [active[r]["job"].n_steps - active[r]["steps"] for r in rids])
+                    hs = [active[r]["h"] for r in rids]
+                    self.ex.advance_group(hs, n)
+                    groups[key] = {"rids": rids, "hs": hs, "n": n}
+                    progressed = True
+            else:
+                for rid in list(active):
+                    a = active[rid]
+                    if a["steps"] == 0 or not self.ex.ready(a["h"]):
+                        continue
+                    progressed = True
+                    j = a["job"]
+                    if a["steps"] >= j.n_steps:
+                        complete(rid)
+                    else:
+                        n = min(self.chunk, j.n_steps - a["steps"])
+                        self.ex.advance(a["h"], n)
+                        a["steps"] += n
             if not progressed:
-                if not active and not waiting and qi < total:
+                if not active and not starting and not waiting and qi < total and clients is None:
                     self.ex.wait_until(queue[qi].arrival)
                 else:
                     self.ex.idle()
@@ -126,14 +215,36 @@ class Server:
 
 
 def summarize(done: List[Completion], wall: Optional[float] = None) -> dict:
+    """Latency percentiles and throughput; `offered` is the work of all
+    requests over the span of their arrivals, `served` the completed work over
+    the span from the first arrival to the last completion."""
     lat = np.array([c.latency for c in done]) * 1e3
     t0 = min(c.arrival for c in done)
     t1 = max(c.finished for c in done)
     span = wall if wall is not None else (t1 - t0)
     work = float(sum(c.n_nodes * c.n_steps for c in done))
+    arr = sorted(c.arrival for c in done)
+    arr_span = arr[-1] - arr[0]
+    offered = work / arr_span if arr_span > 0 else float("inf")
+    served = work / span if span > 0 else float("nan")
     return {"requests": len(done), "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
-            "node_steps_per_s": work / span if span > 0 else float("nan"), "span_s": span}
+            "node_steps_per_s": served, "offered_node_steps_per_s": offered,
+            "served_over_offered": served / offered if np.isfinite(offered) else float("nan"), "span_s": span}
+
+
+def fifo_schedule(jobs: Sequence[Job], service_s: Sequence[float]) -> List[Completion]:
+    """Exact single-server FIFO queue: job i (in arrival order) starts when it
+    has arrived and the previous one has finished, and takes service_s[i]."""
+    order = sorted(range(len(jobs)), key=lambda i: (jobs[i].arrival, jobs[i].rid))
+    t = -np.inf
+    out = []
+    for i in order:
+        j = jobs[i]
+        start = max(t, j.arrival)
+        t = start + float(service_s[i])
+        out.append(Completion(j.rid, j.arrival, start, t, j.n_nodes, j.n_steps))
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -141,11 +252,15 @@ def summarize(done: List[Completion], wall: Optional[float] = None) -> dict:
 # ---------------------------------------------------------------------------
 
 class GpuExecutor(Executor):
-    """Real executor over the C ABI: one handle (and stream) per request.
+    """Real executor over the C ABI: one handle (and stream) per request,
+    built by `workers` threads (the C calls release the interpreter lock).
 
-    payload of a Job is a workloads.Workload; ``options`` builds bd_opts_t."""
+    payload of a Job is a workloads.Workload; ``options`` builds bd_opts_t.
+    In the batched form a group (same membrane model and mesh size) advances
+    a chunk at a time with bd_batch_step on its first handle's stream."""
 
-    def __init__(self, options: Callable[[], Any], dt: float, n_sdc_nodes: int = 3, n_sweeps: int = 2):
+    def __init__(self, options: Callable[[], Any], dt: float, n_sdc_nodes: int = 3, n_sweeps: int = 2,
+                 workers: int = 2):
         from . import binding
         self.b = binding
         self.options = options
@@ -153,6 +268,7 @@ class GpuExecutor(Executor):
         self.M = n_sdc_nodes
         self.K = n_sweeps
         self.t0 = time.perf_counter()
+        self.pool = cf.ThreadPoolExecutor(max_workers=workers)
 
     def now(self) -> float:
         return time.perf_counter() - self.t0
@@ -161,8 +277,8 @@ class GpuExecutor(Executor):
         w = job.payload
         return self.b.footprint_bytes(w.xyz, w.elems, w.model, self.options(), w.elem_bath)
 
-    def start(self, job: Job):
-        return self.b.simulation_from_workload(job.payload, self.options())
+    def prepare(self, job: Job):
+        return self.pool.submit(self.b.simulation_from_workload, job.payload, self.options())
 
     def advance(self, h, n_steps: int) -> None:
         for _ in range(n_steps):
@@ -170,6 +286,16 @@ class GpuExecutor(Executor):
 
     def ready(self, h) -> bool:
         return h.ready()
+
+    def group_key(self, job: Job):
+        return (job.payload.model, job.n_nodes)
+
+    def advance_group(self, hs, n_steps: int) -> None:
+        for _ in range(n_steps):
+            self.b.batch_step(hs, self.dt, self.M, self.K)
+
+    def group_ready(self, hs) -> bool:
+        return all(h.ready() for h in hs)
 
     def finish(self, h):
         return h.activation_times()
@@ -185,21 +311,43 @@ class GpuExecutor(Executor):
         if d > 0:
             time.sleep(d)
 
+    def close(self) -> None:
+        self.pool.shutdown(wait=True)
+
 
 class VirtualExecutor(Executor):
     """Deterministic stand-in with a virtual clock: a request advances at
     ``rate`` node-steps/s shared equally among the active requests
-    (processor sharing), its footprint is ``bytes_per_node`` per node."""
+    (processor sharing), its footprint is ``bytes_per_node`` per node, and
+    its handle takes ``setup`` seconds of a worker to build."""
 
-    def __init__(self, rate: float = 1e9, bytes_per_node: int = 2000, quantum: float = 1e-3):
+    def __init__(self, rate: float = 1e9, bytes_per_node: int = 2000, quantum: float = 1e-3, setup: float = 0.0):
         self.t = 0.0
         self.rate = rate
         self.bpn = bytes_per_node
         self.quantum = quantum
+        self.setup = setup
         self.live: Dict[int, dict] = {}
         self.started: List[int] = []
         self.max_live = 0
         self._next = 0
+
+    class _Build:
+        def __init__(self, ex, job):
+            self.ex, self.job, self.at = ex, job, ex.t + ex.setup
+            self.h = None
+
+        def done(self) -> bool:
+            return self.ex.t >= self.at - 1e-12
+
+        def result(self):
+            if self.h is None:
+                ex = self.ex
+                self.h = ex._next
+                ex._next += 1
+                ex.live[self.h] = {"job": self.job, "work": 0.0}
+                ex.max_live = max(ex.max_live, len(ex.live))
+            return self.h
 
     def now(self) -> float:
         return self.t
@@ -207,13 +355,9 @@ class VirtualExecutor(Executor):
     def footprint(self, job: Job) -> int:
         return job.n_nodes * self.bpn
 
-    def start(self, job: Job):
-        h = self._next
-        self._next += 1
-        self.live[h] = {"job": job, "work": 0.0}
+    def prepare(self, job: Job):
         self.started.append(job.rid)
-        self.max_live = max(self.max_live, len(self.live))
-        return h
+        return self._Build(self, job)
 
     def advance(self, h, n_steps: int) -> None:
         st = self.live[h]
@@ -221,6 +365,16 @@ class VirtualExecutor(Executor):
 
     def ready(self, h) -> bool:
         return self.live[h]["work"] <= 1e-9
+
+    def group_key(self, job: Job):
+        return job.n_nodes
+
+    def advance_group(self, hs, n_steps: int) -> None:
+        for h in hs:
+            self.advance(h, n_steps)
+
+    def group_ready(self, hs) -> bool:
+        return all(self.ready(h) for h in hs)
 
     def _tick(self, dt: float) -> None:
         busy = [st for st in self.live.values() if st["work"] > 1e-9]

@@ -38,3 +38,29 @@ def test_results_are_identical_alone_and_in_the_mix(precision):
         np.testing.assert_array_equal(c.result[~np.isnan(a)], a[~np.isnan(a)])
     s = S.summarize(mixed)
     assert s["p99_ms"] >= s["p50_ms"] > 0
+
+
+@pytest.mark.parametrize("precision", [binding.FP64, binding.MIXED])
+def test_batched_serving_gives_each_request_the_same_map_alone_and_in_the_mix(precision):
+    """The batched form: resident requests advance together through
+    bd_batch_step (one batch per membrane model), requests join at chunk
+    boundaries; a request's activation map is the same as when it is served
+    alone through the same batched kernels."""
+    opts = lambda: binding.default_options(precision=precision)       # noqa: E731
+    jobs = _jobs()
+    alone = {}
+    for j in jobs:
+        ex = S.GpuExecutor(opts, dt=0.02)
+        d = S.Server(ex, max_slots=1, chunk_steps=20, batched=True).run(
+            [S.Job(j.rid, 0.0, j.n_nodes, j.n_steps, j.payload)])
+        alone[j.rid] = d[0].result
+        ex.close()
+    ex = S.GpuExecutor(opts, dt=0.02)
+    mixed = S.Server(ex, max_slots=6, chunk_steps=7, batched=True).run(jobs)
+    ex.close()
+    assert len(mixed) == len(jobs)
+    for c in mixed:
+        a = alone[c.rid]
+        assert np.sum(~np.isnan(a)) > 0
+        np.testing.assert_array_equal(np.isnan(c.result), np.isnan(a))
+        np.testing.assert_array_equal(c.result[~np.isnan(a)], a[~np.isnan(a)])

@@ -71,3 +71,44 @@ def test_request_stream_workloads_are_well_formed():
     w = W.request_workload(reqs[0])
     assert w.n_nodes == reqs[0].side ** 2 and w.n_steps == 100
     assert w.stimuli[0].mask.sum() > 0
+
+
+def test_batched_form_completes_every_request_and_joins_at_chunk_boundaries():
+    ex = S.VirtualExecutor(rate=1e8)
+    jobs = [S.Job(r, 0.002 * r, 1089 * (1 + r % 3), 60 + 20 * (r % 2)) for r in range(12)]
+    done = S.Server(ex, max_slots=6, hbm_budget=10**12, chunk_steps=20, batched=True).run(jobs)
+    assert sorted(c.rid for c in done) == list(range(12))
+    assert 2 < ex.max_live <= 6                 # several requests share each chunk, within the slots
+    for c in done:
+        assert c.finished >= c.admitted >= c.arrival
+
+
+def test_handle_construction_does_not_stall_resident_requests():
+    """A slow build (a worker's time) delays only its own request: the
+    resident one keeps advancing and finishes as if alone."""
+    ex = S.VirtualExecutor(rate=1e8, setup=1.0)
+    jobs = [S.Job(0, 0.0, 1000, 100), S.Job(1, 1.5, 1000, 100)]
+    done = {c.rid: c for c in S.Server(ex, max_slots=2, hbm_budget=10**9, chunk_steps=10).run(jobs)}
+    # job 0: built in 1 s, then 1e5 node-steps at 1e8/s alone; job 1 arrives at 1.5 s
+    assert done[0].finished == pytest.approx(1.001, abs=0.01)
+    assert done[1].admitted == pytest.approx(1.5, abs=0.01)
+    assert done[1].finished >= 2.5
+
+
+def test_closed_loop_keeps_the_client_count_outstanding():
+    ex = S.VirtualExecutor(rate=1e8)
+    jobs = [S.Job(r, 99.0, 4225, 50) for r in range(10)]
+    done = S.Server(ex, max_slots=8, hbm_budget=10**12, chunk_steps=10).run_closed(jobs, clients=3)
+    assert len(done) == 10 and ex.max_live == 3
+    assert min(c.arrival for c in done) == 0.0            # arrival times are the submission times
+
+
+def test_fifo_schedule_and_offered_load():
+    jobs = [S.Job(0, 0.0, 100, 10), S.Job(1, 0.5, 100, 10), S.Job(2, 5.0, 100, 10)]
+    done = S.fifo_schedule(jobs, [1.0, 1.0, 1.0])
+    fin = {c.rid: c.finished for c in done}
+    assert fin == {0: 1.0, 1: 2.0, 2: 6.0}
+    sm = S.summarize(done)
+    assert sm["offered_node_steps_per_s"] == pytest.approx(3000 / 5.0)
+    assert sm["node_steps_per_s"] == pytest.approx(3000 / 6.0)
+    assert sm["served_over_offered"] == pytest.approx(5.0 / 6.0)
