@@ -747,17 +747,26 @@ def profile_workload(args) -> None:
     if name == "sheet":
         w = W.sheet(args.side, LENGTH * (args.side - 1) / (SIDE - 1), W.TP06_EPI, DT, 1)
     elif name == "slab":
-        w = W.config2()
+        w = W.config2() if args.side == SIDE else W.config2(args.side, args.side, (args.side - 1) // 4 + 1)
     elif name == "lv":
         w = W.lv_shell_bath(h=args.lv_h)
     else:
         w = W.bath_paper_2d()
     prec = binding.FP64 if args.precision == "fp64" else binding.MIXED
-    sim = binding.simulation_from_workload(w, binding.default_options(precision=prec, pin_node=w.pin_node))
+    sim = binding.simulation_from_workload(w, binding.default_options(precision=prec, pin_node=w.pin_node,
+                                                                      streaming=args.streaming, vec4=args.vec4))
     for _ in range(args.steps):
         sim.step(w.dt, M_NODES, K_SWEEPS)
     sim.sync()
-    print(json.dumps({"workload": w.name, "nodes": int(w.n_nodes), "steps": args.steps, "stats": sim.stats()}))
+    out = {"workload": w.name, "nodes": int(w.n_nodes), "steps": args.steps, "vec4": args.vec4,
+           "stats": sim.stats()}
+    if args.profile_steps > 0:
+        prof = sim.profile_steps(w.dt, M_NODES, K_SWEEPS, args.profile_steps)
+        out["ms_per_step"] = round(sum(prof["ms"].values()) / args.profile_steps, 3)
+        out["kernel_share"] = shares(prof)
+        out["elliptic"] = solver_roofline(prof, "pcg_elliptic")
+        out["parabolic"] = solver_roofline(prof, "pcg_parabolic")
+    print(json.dumps(out))
     sim.close()
 
 
@@ -847,8 +856,15 @@ def main():
                     help="timed steps of the 801^2 bidomain-bath leg (0: skip)")
     ap.add_argument("--profile-workload", choices=["sheet", "slab", "lv", "bath"],
                     help="step one workload --steps times for a profiler (no timing)")
-    ap.add_argument("--side", type=int, default=SIDE, help="sheet side for --profile-workload sheet")
+    ap.add_argument("--side", type=int, default=SIDE,
+                    help="--profile-workload: sheet side, or the slab's x/y nodes (z: (side-1)/4+1)")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--vec4", type=int, default=0, choices=[-1, 0],
+                    help="--profile-workload: SELL-32/4 copy of the FP32 elliptic operator (bd_opts_t.vec4)")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="--profile-workload: also time this many steps per kind (bd_profile_steps)")
+    ap.add_argument("--streaming", type=int, default=0, choices=[-1, 0, 1, 2],
+                    help="--profile-workload: solver form (bd_opts_t.streaming)")
     ap.add_argument("--summarize-launches", metavar="CSV", help="summarise an ncu launch list")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--seconds", type=float, default=0.0, help=argparse.SUPPRESS)

@@ -133,10 +133,19 @@ typedef struct {
                             BD_ERR_ARG otherwise; ignored with cg_cluster */
   int streaming;         /* solver form: 0 (default) streaming for operators of at least
                             12M entries (they do not fit in L2), persistent otherwise;
-                            1: always streaming; -1: never.  Streaming solves chain
-                            full-occupancy kernels whose CG loops run on the device as CUDA
-                            graph conditional nodes; persistent solves are one cooperative
-                            kernel each (bd_stats_t.streaming reports the form in use) */
+                            1: always streaming; -1: never; 2: streaming with the loops on
+                            the host (a profiling form: eager launches that tools can capture,
+                            one synchronisation per iteration; no graphs; sweep_tol must be 0).
+                            Streaming solves chain full-occupancy kernels whose CG loops run on
+                            the device as CUDA graph conditional nodes; persistent solves are
+                            one cooperative kernel each (bd_stats_t.streaming reports the form
+                            in use) */
+  int vec4;              /* 0 (default): mixed-precision streaming solves also keep the FP32
+                            elliptic operator in the SELL-32/4 layout (four consecutive entries
+                            of a row per 16-byte load; 8 more bytes per stored entry) and use it
+                            in the Krylov and AMG level-0 products; -1: they do not (the plain
+                            SELL-32 layout only); BD_ERR_ARG otherwise.  Both give the same sums
+                            in the same order */
 } bd_opts_t;
 
 typedef struct bd_state bd_state_t;

@@ -87,7 +87,13 @@ struct bd_state {
   AmgDevF* d_amgf = nullptr;
   // mixed path: FP32 operator values and CG workspaces
   float* fAie = nullptr;
-  struct PCF { double alpha; float* val; };
+  bool vec4 = false;            // FP32 operators also in SELL-32/4 (streaming, mixed)
+  int64_t n_slices = 0;         // SELL-32 slices of the shared pattern
+  int64_t ell_n4 = 0;           // stored entries of the SELL-32/4 layout
+  int64_t* sptr4 = nullptr;
+  int* col4 = nullptr;
+  float* fAie4 = nullptr;
+  struct PCF { double alpha; float* val; float* val4; };   // val4: SELL-32/4 copy (vec4)
   std::vector<PCF> fpcache;
   float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr, *invd32 = nullptr, *d32 = nullptr;
   float* partf = nullptr;
@@ -293,8 +299,20 @@ float* p_values_f(bd_state* s, double alpha) {
   float* v = nullptr;
   if (!dv || !alloc_n(s, &v, s->ell_n)) return nullptr;
   if (launch_to_float(s->ell_n, dv, v, s->stream) != cudaSuccess) return nullptr;
-  s->fpcache.push_back({alpha, v});
+  float* v4 = nullptr;
+  if (s->vec4 && (!alloc_n(s, &v4, s->ell_n4) ||
+                  launch_sell_v4(s->n_slices, s->sptr, s->swidth, s->sptr4, v, v4, s->stream) != cudaSuccess))
+    return nullptr;
+  s->fpcache.push_back({alpha, v, v4});
   return v;
+}
+
+// the SELL-32/4 copy of p_values_f(s, alpha) (NULL without vec4)
+float* p_values_f4(bd_state* s, double alpha) {
+  if (!p_values_f(s, alpha)) return nullptr;
+  for (auto& pc : s->fpcache)
+    if (pc.alpha == alpha) return pc.val4;
+  return nullptr;
 }
 
 MixedLaunch mixed_base(bd_state* s) {
@@ -334,6 +352,16 @@ PcgLaunch pcg_base(bd_state* s) {
   return P;
 }
 
+// the SELL-32/4 copy (values val4) of a launch's FP32 operator, when the
+// handle keeps one
+void set_vec4(const bd_state* s, StreamLaunch& A, const float* val4) {
+  if (!s->vec4 || !val4) return;
+  A.sptr4 = s->sptr4;
+  A.sw4 = s->swidth;
+  A.col4 = s->col4;
+  A.valT4 = val4;
+}
+
 StreamLaunch stream_base(bd_state* s, int n) {
   StreamLaunch A{};
   A.n = n;
@@ -347,6 +375,7 @@ StreamLaunch stream_base(bd_state* s, int n) {
   A.launch_acc = s->d_stats + 8;
   A.gate = s->opts.sweep_tol > 0 ? s->gate : nullptr;
   A.grid = int(std::max<int64_t>(1, std::min<int64_t>((int64_t(n) + 255) / 256, stream_grid_cap())));
+  A.host_loop = s->opts.streaming == 2 ? 1 : 0;
   const bool mixed = s->precision == BD_MIXED;
   A.b64 = mixed ? s->b64 : s->sb64;
   A.r64 = mixed ? s->r64 : s->sr64;
@@ -370,6 +399,7 @@ int elliptic(bd_state* s, const double* v, double* u) {
     const bool mixed = s->precision == BD_MIXED;
     A.valA = s->Aie;
     A.valT = mixed ? static_cast<const void*>(s->fAie) : static_cast<const void*>(s->Aie);
+    set_vec4(s, A, s->fAie4);
     A.val1 = s->Ai;
     A.va = v;
     A.c1 = -1.0;
@@ -478,6 +508,7 @@ int parabolic(bd_state* s, double alpha, double c1, const double* va, double c2,
     const bool mixed = s->precision == BD_MIXED;
     A.valA = p_values(s, alpha);
     A.valT = mixed ? static_cast<const void*>(p_values_f(s, alpha)) : static_cast<const void*>(A.valA);
+    if (mixed) set_vec4(s, A, p_values_f4(s, alpha));
     A.dextra = node_terms ? s->dgs : nullptr;
     A.rl = node_terms ? s->rl : nullptr;
     A.val1 = s->Ai;
@@ -990,7 +1021,7 @@ int enqueue_any(bd_state* s, double dt, int M, int K) {
 
 int do_step(bd_state* s, double dt, int M, int K) {
   RUN(prepare_step(s, dt, M));
-  if (s->prof) {
+  if (s->prof && s->opts.streaming != 2) {
     // a profiled step is captured with its event records and replayed, so
     // every event pair brackets device work only (launched eagerly, a fast
     // kernel's pair would also hold the time the GPU waits for the host)
@@ -1019,7 +1050,7 @@ int do_step(bd_state* s, double dt, int M, int K) {
     cudaGraphExecDestroy(ex);
     if (e != cudaSuccess) return fail(s, BD_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
     s->launches += s->enq_launches;
-  } else if (!s->opts.use_graph) {
+  } else if (!s->opts.use_graph || s->prof) {
     s->enq_launches = 0;
     RUN(enqueue_any(s, dt, M, K));
     s->launches += s->enq_launches;
@@ -1202,6 +1233,7 @@ int batch_solve(BatchPlan& B, const BatchSolveArgs& q, cudaStream_t st) {
     if (q.elliptic) {
       A.valA = s->Aie;
       A.valT = mixed ? static_cast<const void*>(s->fAie) : static_cast<const void*>(s->Aie);
+      set_vec4(s, A, s->fAie4);
       A.val1 = s->Ai;
       A.va = q.va[r];
       A.c1 = -1.0;
@@ -1248,6 +1280,7 @@ int batch_solve(BatchPlan& B, const BatchSolveArgs& q, cudaStream_t st) {
       A.valA = p_values(s, q.alpha);
       A.valT = mixed ? static_cast<const void*>(p_values_f(s, q.alpha)) : static_cast<const void*>(A.valA);
       if (!A.valA || !A.valT) return fail(s0, BD_ERR_OOM, "device allocation failed");
+      if (mixed) set_vec4(s, A, p_values_f4(s, q.alpha));
       A.dextra = q.node_terms ? s->dgs : nullptr;
       A.rl = q.node_terms ? s->rl : nullptr;
       A.val1 = s->Ai;
@@ -1773,12 +1806,18 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   }
   {
     const int so = s->opts.streaming;
-    if (so < -1 || so > 1) {
+    if (so < -1 || so > 2) {
       release(s);
       delete s;
-      return fail(nullptr, BD_ERR_ARG, "streaming must be -1, 0 or 1");
+      return fail(nullptr, BD_ERR_ARG, "streaming must be -1, 0, 1 or 2");
     }
-    s->streaming = s->opts.cg_cluster == 0 && (so == 1 || (so == 0 && nnz >= kTier2Nnz));
+    if (so == 2 && s->opts.sweep_tol > 0) {
+      release(s);
+      delete s;
+      return fail(nullptr, BD_ERR_ARG, "streaming = 2 (host-driven loops) needs sweep_tol = 0");
+    }
+    s->streaming = s->opts.cg_cluster == 0 && (so >= 1 || (so == 0 && nnz >= kTier2Nnz));
+    if (so == 2) s->opts.use_graph = 0;   // host-driven loops cannot be captured
   }
   if (ok && s->streaming) {
     ok = alloc_n(s, reinterpret_cast<char**>(&s->d_sc), int64_t(sizeof(StreamScal))) &&
@@ -1791,6 +1830,37 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
         cudaGetLastError();
         ok = false;
       }
+  }
+  // SELL-32/4 copy of the FP32 elliptic operator: four consecutive entries of
+  // a row per 16-byte load in the streaming products
+  if (s->opts.vec4 != 0 && s->opts.vec4 != -1) {
+    release(s);
+    delete s;
+    return fail(nullptr, BD_ERR_ARG, "vec4 must be 0 or -1");
+  }
+  s->vec4 = s->streaming && s->precision == BD_MIXED && s->opts.vec4 == 0;
+  std::vector<int64_t> h_sptr4;
+  std::vector<int> e_col4;
+  int64_t en4 = 0;
+  if (ok && s->vec4) {
+    h_sptr4.resize(nsl);
+    for (int64_t sl = 0; sl < nsl; ++sl) {
+      h_sptr4[sl] = en4;
+      en4 += 32 * int64_t((h_sw[sl] + 3) & ~3);
+    }
+    e_col4.assign(en4, 0);
+    for (int64_t sl = 0; sl < nsl; ++sl) {
+      const int w = h_sw[sl], w4 = (w + 3) & ~3;
+      for (int l = 0; l < 32; ++l) {
+        const int64_t i = sl * 32 + l;
+        for (int k = 0; k < w4; ++k)
+          e_col4[h_sptr4[sl] + 128 * (k / 4) + 4 * l + k % 4] =
+              k < w ? e_col[h_sptr[sl] + 32 * k + l] : (i < N ? int(i) : 0);
+      }
+    }
+    s->n_slices = nsl;
+    s->ell_n4 = en4;
+    ok = alloc_n(s, &s->sptr4, nsl) && alloc_n(s, &s->col4, en4) && alloc_n(s, &s->fAie4, en4);
   }
   if (!ok) {
     release(s);
@@ -1806,6 +1876,8 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   if (e == cudaSuccess) e = up(s->sptr, h_sptr.data(), nsl * 8);
   if (e == cudaSuccess) e = up(s->swidth, h_sw.data(), nsl * 4);
   if (e == cudaSuccess) e = up(s->col, e_col.data(), en * 4);
+  if (e == cudaSuccess && s->vec4) e = up(s->sptr4, h_sptr4.data(), nsl * 8);
+  if (e == cudaSuccess && s->vec4) e = up(s->col4, e_col4.data(), en4 * 4);
   if (e == cudaSuccess) e = up(s->diagpos, e_diag.data(), N * 4);
   if (e == cudaSuccess) e = up(s->Ai, eAi.data(), en * 8);
   if (e == cudaSuccess) e = up(s->Aie, eAie.data(), en * 8);
@@ -1845,6 +1917,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   }
   if (s->precision == BD_MIXED &&
       (launch_to_float(s->ell_n, s->Aie, s->fAie, s->stream) != cudaSuccess ||
+       (s->vec4 && launch_sell_v4(nsl, s->sptr, s->swidth, s->sptr4, s->fAie, s->fAie4, s->stream) != cudaSuccess) ||
        cudaStreamSynchronize(s->stream) != cudaSuccess)) {
     release(s);
     delete s;

@@ -357,6 +357,15 @@ cudaError_t launch_pcg_mixed2(const PcgLaunch& P, const double* va1, double* x1,
                               double* partd8);
 cudaError_t launch_to_float(int64_t n, const double* src, float* dst, cudaStream_t st);
 
+// SELL-32/4: the SELL-32 layout with four consecutive entries of a row side by
+// side, so a thread reads four column indices and four values with one 16-byte
+// load each.  Slice s keeps its rows 32 s .. 32 s + 31, its width is rounded
+// up to a multiple of 4 (w4), and entry k of row 32 s + l sits at
+// sptr4[s] + 128 (k / 4) + 4 l + k % 4; padding entries hold value 0 and the
+// row's own column.  Sums over a row keep the SELL-32 order (k ascending).
+cudaError_t launch_sell_v4(int64_t n_slices, const int64_t* sptr, const int* sw, const int64_t* sptr4,
+                           const float* src, float* dst, cudaStream_t st);
+
 // ---- streaming solver (stream.cu) -------------------------------------------
 // For operators that do not fit in L2 the solves run as chains of ordinary
 // full-occupancy kernels instead of one persistent kernel; the Krylov loops
@@ -404,6 +413,14 @@ struct StreamLaunch {
   long long* launch_acc;          // kernels launched (counted on the device)
   const int* gate;                // optional: the solve is skipped when *gate == 0
   int grid;                       // blocks of the row kernels (capped at a multiple of the SMs)
+  int host_loop;                  // 1: the loops run on the host (eager launches, no graph conditions)
+  // optional SELL-32/4 copy of the inner operator (FP32 only; see launch_sell_v4):
+  // used by the Krylov product and by the AMG level-0 products, whose operator
+  // is the same (elliptic) -- NULL: the SELL-32 arrays above
+  const int64_t* sptr4;
+  const int* sw4;
+  const int* col4;
+  const void* valT4;
   unsigned long long h_outer, h_inner;   // conditional handles of the two loops
 };
 // Enqueue one streaming solve on `st` (captured or not).  side[0..1] are two

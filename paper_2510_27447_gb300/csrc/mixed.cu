@@ -754,6 +754,27 @@ bool mixed_cluster_ok(int block, int size) {
          solver_cluster_ok(pcg_mixed2_kernel<0, 1024>, block, size);
 }
 
+// values of a SELL-32 operator into the SELL-32/4 layout (one thread per row
+// of a slice; the slice's SELL-32 width w, its SELL-32/4 width w4 = the next
+// multiple of 4)
+__global__ void sell_v4_kernel(int64_t n_slices, const int64_t* sptr, const int* sw, const int64_t* sptr4,
+                               const float* src, float* dst) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t s = t >> 5;
+  const int l = int(t & 31);
+  if (s >= n_slices) return;
+  const int w = sw[s], w4 = (w + 3) & ~3;
+  for (int k = 0; k < w4; ++k)
+    dst[sptr4[s] + 128 * (k >> 2) + 4 * l + (k & 3)] = k < w ? src[sptr[s] + 32 * k + l] : 0.0f;
+}
+
+cudaError_t launch_sell_v4(int64_t n_slices, const int64_t* sptr, const int* sw, const int64_t* sptr4,
+                           const float* src, float* dst, cudaStream_t st) {
+  if (n_slices == 0) return cudaSuccess;
+  sell_v4_kernel<<<unsigned((n_slices * 32 + 255) / 256), 256, 0, st>>>(n_slices, sptr, sw, sptr4, src, dst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_to_float(int64_t n, const double* src, float* dst, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   to_float_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(n, src, dst);

@@ -111,6 +111,7 @@ __device__ __forceinline__ void set_cond(unsigned long long h, unsigned v) {
 // body from every system's flags (the loop continues while any system still
 // iterates), with a hard cap on the passes.
 __device__ __forceinline__ void vote_inner(const One&, const StreamLaunch& a, bool active) {
+  if (a.host_loop) return;
   if (!active) {
     set_cond(a.h_inner, 0u);
     if (a.sc->fail) set_cond(a.h_outer, 0u);
@@ -118,6 +119,7 @@ __device__ __forceinline__ void vote_inner(const One&, const StreamLaunch& a, bo
 }
 __device__ __forceinline__ void vote_inner(const Many&, const StreamLaunch&, bool) {}
 __device__ __forceinline__ void vote_outer(const One&, const StreamLaunch& a, bool inner_on, bool outer_on) {
+  if (a.host_loop) return;
   set_cond(a.h_inner, inner_on ? 1u : 0u);
   set_cond(a.h_outer, outer_on ? 1u : 0u);
 }
@@ -163,6 +165,49 @@ __device__ __forceinline__ X srow(const int64_t* __restrict__ sptr, const int* _
   return acc;
 }
 
+// the same over the SELL-32/4 copy of an FP32 operator: four column indices
+// and four values per 16-byte load, evict-first, the entries added in the
+// SELL-32 order
+template <class X>
+__device__ __forceinline__ X srow4(const int64_t* __restrict__ sptr4, const int* __restrict__ sw,
+                                   const int* __restrict__ col4, const float* __restrict__ val4,
+                                   const X* __restrict__ x, int i) {
+  const int s = i >> 5;
+  const int64_t base = sptr4[s] + 4 * (i & 31);
+  const int w = sw[s];
+  X acc = X(0);
+  for (int k0 = 0; k0 < w; k0 += 8) {      // two 4-entry groups in flight
+    const int4 c0 = __ldcs(reinterpret_cast<const int4*>(col4 + base + 32 * k0));
+    const float4 v0 = __ldcs(reinterpret_cast<const float4*>(val4 + base + 32 * k0));
+    const bool two = k0 + 4 < w;
+    int4 c1 = c0;
+    float4 v1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (two) {
+      c1 = __ldcs(reinterpret_cast<const int4*>(col4 + base + 32 * (k0 + 4)));
+      v1 = __ldcs(reinterpret_cast<const float4*>(val4 + base + 32 * (k0 + 4)));
+    }
+    const X g0 = __ldg(x + c0.x), g1 = __ldg(x + c0.y), g2 = __ldg(x + c0.z), g3 = __ldg(x + c0.w);
+    X h0 = X(0), h1 = X(0), h2 = X(0), h3 = X(0);
+    if (two) {
+      h0 = __ldg(x + c1.x);
+      h1 = __ldg(x + c1.y);
+      h2 = __ldg(x + c1.z);
+      h3 = __ldg(x + c1.w);
+    }
+    acc += X(v0.x) * g0;
+    acc += X(v0.y) * g1;
+    acc += X(v0.z) * g2;
+    acc += X(v0.w) * g3;
+    if (two) {
+      acc += X(v1.x) * h0;
+      acc += X(v1.y) * h1;
+      acc += X(v1.z) * h2;
+      acc += X(v1.w) * h3;
+    }
+  }
+  return acc;
+}
+
 // every row i of an AMG-level operator (SELL: thread per row; CSR: warp per
 // row, butterfly sum): epi(i, (M x)_i), run by one lane per row.  Level 0's
 // operators are streamed with evict-first loads, the coarser levels' stay
@@ -174,9 +219,26 @@ __device__ __forceinline__ void level_rows(const SellDevT<T>& M, const T* x, boo
   if (M.rp) {
     const int lane = threadIdx.x & 31;
     for (int i = gt >> 5; i < M.n; i += gs >> 5) {
-      T s = T(0);
+      // four strided entries a lane in flight, four partial sums added in a
+      // fixed order (deterministic)
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
       const int64_t e = M.rp[i + 1];
-      for (int64_t p = M.rp[i] + lane; p < e; p += 32) s += __ldg(M.val + p) * __ldg(x + __ldg(M.col + p));
+      for (int64_t p = M.rp[i] + lane; p < e; p += 128) {
+        const bool b1 = p + 32 < e, b2 = p + 64 < e, b3 = p + 96 < e;
+        const int c0 = __ldg(M.col + p);
+        const int c1 = b1 ? __ldg(M.col + p + 32) : c0;
+        const int c2 = b2 ? __ldg(M.col + p + 64) : c0;
+        const int c3 = b3 ? __ldg(M.col + p + 96) : c0;
+        const T v0 = __ldg(M.val + p);
+        const T v1 = b1 ? __ldg(M.val + p + 32) : T(0);
+        const T v2 = b2 ? __ldg(M.val + p + 64) : T(0);
+        const T v3 = b3 ? __ldg(M.val + p + 96) : T(0);
+        s0 += v0 * __ldg(x + c0);
+        s1 += v1 * __ldg(x + c1);
+        s2 += v2 * __ldg(x + c2);
+        s3 += v3 * __ldg(x + c3);
+      }
+      T s = (s0 + s1) + (s2 + s3);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) epi(i, s);
@@ -446,9 +508,11 @@ __global__ void __launch_bounds__(kSB) st_pq_kernel(const __grid_constant__ S sr
   const bool first = c.it == 0;
   const T beta = T(c.beta);
   T acc[1] = {T(0)};
+  const bool v4 = sizeof(T) == 4 && a.col4 != nullptr;
   for (int i = gt; i < a.n; i += gs) {
     const T zi = z[i];
-    T az = srow<true, T, T>(a.sptr, a.swidth, a.col, val, z, i);
+    T az = v4 ? T(srow4<T>(a.sptr4, a.sw4, a.col4, static_cast<const float*>(a.valT4), z, i))
+              : srow<true, T, T>(a.sptr, a.swidth, a.col, val, z, i);
     if (a.dextra) az += T(a.dextra[i]) * zi;
     const T pi = first ? zi : zi + beta * p[i];
     const T qi = first ? az : az + beta * q[i];
@@ -564,6 +628,11 @@ __global__ void __launch_bounds__(kSB) st_vc_res_kernel(const __grid_constant__ 
   if (a.sc->stop || l >= H.nlev) return;
   const AmgLevelDevT<T>& L = H.L[l];
   const T* b = l == 0 ? static_cast<const T*>(a.r) : L.b;
+  if (l == 0 && sizeof(T) == 4 && a.col4) {
+    for (int i = sg.lb * blockDim.x + threadIdx.x; i < L.A.n; i += sg.nb * blockDim.x)
+      L.r[i] = b[i] - T(srow4<T>(a.sptr4, a.sw4, a.col4, static_cast<const float*>(a.valT4), L.x, i));
+    return;
+  }
   level_rows<T>(L.A, L.x, l == 0, sg, [&](int i, T ax) { L.r[i] = b[i] - ax; });
 }
 
@@ -671,12 +740,18 @@ __global__ void __launch_bounds__(kSB) st_vc_post_kernel(const __grid_constant__
   const T* b = l == 0 ? static_cast<const T*>(a.r) : L.b;
   T* y = l == 0 ? static_cast<T*>(a.z) : L.y;
   T acc[1] = {T(0)};
-  level_rows<T>(L.A, L.x, l == 0, sg, [&](int i, T ax) {
+  auto post = [&](int i, T ax) {
     const T bi = b[i];
     const T yi = L.x[i] + L.omega * L.invd[i] * (bi - ax);
     y[i] = yi;
     acc[0] += bi * yi;
-  });
+  };
+  if (l == 0 && sizeof(T) == 4 && a.col4) {
+    for (int i = sg.lb * blockDim.x + threadIdx.x; i < L.A.n; i += sg.nb * blockDim.x)
+      post(i, T(srow4<T>(a.sptr4, a.sw4, a.col4, static_cast<const float*>(a.valT4), L.x, i)));
+  } else {
+    level_rows<T>(L.A, L.x, l == 0, sg, post);
+  }
   if (l != 0) return;
   if (last_block_total<1, T>(acc, a.part, &c.ticket, sg) && threadIdx.x == 0)
     vote_inner(src, a, inner_decide<T>(a, acc[0]));
@@ -913,6 +988,41 @@ cudaError_t run_captured(cudaStream_t st, F&& body) {
   return e;
 }
 
+// The same solve with its loops on the host (a profiling form: every kernel
+// is an eager launch that tools can capture; the host reads the decisions
+// back after each deciding launch)
+template <class T>
+cudaError_t host_loop_solve(Plan<T>& P, cudaStream_t st) {
+  P.one.a.host_loop = 1;
+  StreamScal c{};
+  auto flags = [&]() {
+    const cudaError_t e = cudaMemcpyAsync(&c, P.one.a.sc, sizeof(StreamScal), cudaMemcpyDeviceToHost, st);
+    return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
+  };
+  cudaError_t e;
+  ROWS_LAUNCH_T(st_rhs_kernel, st);
+  for (int pass = 0; pass <= P.one.a.max_outer; ++pass) {
+    ROWS_LAUNCH_T(st_outer_kernel, st);
+    if ((e = flags()) != cudaSuccess) return e;
+    if (!c.inner_ran) break;
+    ROWS_LAUNCH_T(st_inner_init_kernel, st);
+    if (P.amg) enqueue_vcycle<T>(P, st);
+    if ((e = flags()) != cudaSuccess) return e;
+    for (int it = 0; !c.stop && it <= P.one.a.inner_cap; ++it) {
+      ROWS_LAUNCH_T(st_pq_kernel, st);
+      ROWS_LAUNCH_T(st_update_kernel, st);
+      if (P.amg) enqueue_vcycle<T>(P, st);
+      if ((e = flags()) != cudaSuccess) return e;
+    }
+    ROWS_LAUNCH_T(st_xupdate_kernel, st);
+    if ((e = flags()) != cudaSuccess) return e;
+    if (!c.more || c.fail) break;
+  }
+  ROWS_LAUNCH_S(st_shift_kernel, st);
+  ROWS_LAUNCH_S(st_finish_kernel, st);
+  return cudaGetLastError();
+}
+
 template <class T>
 Plan<T> one_plan(const StreamLaunch& a, const AmgDevT<T>* M) {
   Plan<T> P;
@@ -959,9 +1069,11 @@ cudaError_t stream_solve(const StreamLaunch& a, int f32, const AmgDevF* M32, con
                          const cudaStream_t* side) {
   if (f32) {
     Plan<float> P = one_plan<float>(a, M32);
+    if (a.host_loop) return host_loop_solve<float>(P, st);
     return run_captured(st, [&]() { return enqueue_solve<float>(P, st, side); });
   }
   Plan<double> P = one_plan<double>(a, M64);
+  if (a.host_loop) return host_loop_solve<double>(P, st);
   return run_captured(st, [&]() { return enqueue_solve<double>(P, st, side); });
 }
 

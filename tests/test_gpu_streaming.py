@@ -165,3 +165,41 @@ def test_profiled_steps_time_every_kind_and_advance_like_steps(form):
     assert np.array_equal(a, b)          # same kernels, same order: bit for bit
     for s in sims:
         s.close()
+
+
+def test_host_driven_loops_give_the_same_bits_as_graph_loops():
+    """streaming = 2 runs the same kernels with the loop decisions read back
+    by the host (a form profilers can capture launch by launch): the same
+    bits as the device-side loops."""
+    w = W.sheet(41, 0.4, W.TP06_EPI, 0.02, 5, strip=0.06)
+    X0 = rest_X(w)
+    out = []
+    for form in (1, 2):
+        sim = gpu_sim(w, precision=binding.MIXED, streaming=form)
+        sim.set_initial(X0)
+        for _ in range(w.n_steps):
+            sim.step(w.dt, 3, 2)
+        out.append(sim.fields(full=True))
+        sim.close()
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
+def test_vector_load_layout_gives_the_same_solves():
+    """The SELL-32/4 copy of the FP32 elliptic operator (16-byte loads of
+    four entries of a row) adds each row's entries in the SELL-32 order: the
+    mixed steps on a slab agree with the plain layout and with the oracle."""
+    w = _slab()
+    X0 = rest_X(w)
+    out = {}
+    for v4 in (0, -1):
+        sim = gpu_sim(w, precision=binding.MIXED, streaming=1, vec4=v4)
+        sim.set_initial(X0)
+        for _ in range(w.n_steps):
+            sim.step(w.dt, 3, 2)
+        out[v4] = sim.fields(full=True)
+        sim.close()
+    Xo, uo, _ = OB.run(oracle_problem(w), X0, w.n_steps, w.dt, 3, 2)
+    (v0, u0, _), (v1, u1, _) = out[0], out[-1]
+    assert rel(v0, v1) < 1e-6 and rel(u0, u1) < 1e-6
+    assert rel(v0, Xo[0]) < 1e-3 and rel(u0, uo) < 1e-3
