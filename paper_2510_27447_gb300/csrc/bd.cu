@@ -108,8 +108,13 @@ struct bd_state {
   double *Ai = nullptr, *Aie = nullptr, *Mv = nullptr, *Mc = nullptr, *ML = nullptr;
   struct PC { double alpha; double* val; };
   std::vector<PC> pcache;
-  double *Xn = nullptr, *Xt[kMaxNodes] = {}, *Xc[kMaxNodes] = {}, *fq[kMaxNodes] = {}, *u[kMaxNodes] = {};
-  double *dgs = nullptr, *rl = nullptr, *z1 = nullptr, *w1 = nullptr, *z2 = nullptr, *w2 = nullptr;
+  double *Xn = nullptr, *Xt[kMaxNodes] = {}, *Xc[kMaxNodes] = {}, *u[kMaxNodes] = {};
+  void* fq[kMaxNodes] = {};     // node fields f(X~_m), ns x NT values of the model's type
+  double *dgs = nullptr, *rl = nullptr;
+  // condensation vectors z, w of ROS2 stage 1 / the correction (z1, w1) and
+  // z of stage 2, (ns-1) x NT values of the membrane model's type (float on
+  // the mixed path: the condensation computes them in FP32)
+  void *z1 = nullptr, *w1 = nullptr, *z2 = nullptr;
   double *k1v = nullptr, *k2v = nullptr, *avec = nullptr, *bvec = nullptr;
   // increments of each (sub-interval, ROS2 stage 1 / 2, correction): every
   // solve warm-starts from the previous sweep's (sweep 1: the previous step's)
@@ -208,6 +213,12 @@ void* dalloc(bd_state* s, size_t bytes) {
 template <class T>
 bool alloc_n(bd_state* s, T** out, int64_t count) {
   *out = static_cast<T*>(dalloc(s, size_t(count) * sizeof(T)));
+  return *out != nullptr;
+}
+
+// count values of the membrane model's type (float on the mixed path)
+bool alloc_zw(bd_state* s, void** out, int64_t count) {
+  *out = dalloc(s, size_t(count) * (s->precision == BD_MIXED ? sizeof(float) : sizeof(double)));
   return *out != nullptr;
 }
 
@@ -657,6 +668,7 @@ int setup_amg(bd_state* s, const HostOps& H) {
     out->wmax = S.wmax;
     const bool csr = !S.rp.empty();
     out->rp = csr ? static_cast<const int64_t*>(upload(S.rp.data(), S.rp.size() * 8)) : nullptr;
+    out->lpr = csr ? csr_lanes(S.rp.back(), S.n) : 0;
     out->sptr = csr ? nullptr : static_cast<const int64_t*>(upload(S.sptr.data(), S.sptr.size() * 8));
     out->sw = csr ? nullptr : static_cast<const int*>(upload(S.sw.data(), S.sw.size() * 4));
     out->col = static_cast<const int*>(upload(S.col.data(), S.col.size() * 4));
@@ -704,6 +716,7 @@ int setup_amg(bd_state* s, const HostOps& H) {
       out->wmax = S.wmax;
       const bool csr = !S.rp.empty();
       out->rp = csr ? static_cast<const int64_t*>(upload(S.rp.data(), S.rp.size() * 8)) : nullptr;
+      out->lpr = csr ? csr_lanes(S.rp.back(), S.n) : 0;
       out->sptr = csr ? nullptr : static_cast<const int64_t*>(upload(S.sptr.data(), S.sptr.size() * 8));
       out->sw = csr ? nullptr : static_cast<const int*>(upload(S.sw.data(), S.sw.size() * 4));
       out->col = static_cast<const int*>(upload(S.col.data(), S.col.size() * 4));
@@ -911,7 +924,8 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
       RUN(parabolic(s, alpha, -1.0, s->avec, -L2.ck1, s->bvec, k2, true, true));
       {
         Timed t(s, BD_K_COMBINE);
-        CK(launch_combine(s->model, N, src, k1, s->z1, s->w1, k2, s->z2, s->w1, 1.5 / gam, 0.5 / gam,
+        CK(launch_combine(s->model, s->precision == BD_MIXED, N, src, k1, s->z1, s->w1, k2, s->z2, s->w1, 1.5 / gam,
+                          0.5 / gam,
                           s->Xt[m + 1], s->stream, gate, 1.0 / gam, s->adapt_tol,
                           s->adapt_on ? s->d_err : nullptr));
       }
@@ -954,7 +968,8 @@ int enqueue_step(bd_state* s, double dt, int M, int K) {
         RUN(parabolic(s, alpha, -1.0 / h, s->avec, 1.0 / h, s->bvec, ek, true, true));
         {
           Timed t(s, BD_K_COMBINE);
-          CK(launch_update(s->model, N, s->Xt[m + 1], ek, s->z1, s->w1, s->Xc[m + 1], s->stream, gate));
+          CK(launch_update(s->model, s->precision == BD_MIXED, N, s->Xt[m + 1], ek, s->z1, s->w1, s->Xc[m + 1],
+                           s->stream, gate));
         }
         s->ionic_evals += 1;
       }
@@ -1256,7 +1271,7 @@ int batch_solve(BatchPlan& B, const BatchSolveArgs& q, cudaStream_t st) {
         A.h0_x = mixed ? static_cast<void*>(s->amgf.L[0].x) : static_cast<void*>(s->amg.L[0].x);
         A.h0_omega = mixed ? double(s->amgf.L[0].omega) : s->amg.L[0].omega;
         for (int l = 0; l < nlev; ++l) {
-          auto grid_of = [&](const auto& M) { return stream_grid(M.rp ? int64_t(M.n) * 32 : int64_t(M.n)); };
+          auto grid_of = [&](const auto& M) { return stream_grid(level_threads(M)); };
           if (mixed) {
             lA[l][r] = grid_of(s->amgf.L[l].A);
             lR[l][r] = grid_of(s->amgf.L[l].R);
@@ -1473,7 +1488,7 @@ int enqueue_batch_step(BatchPlan& B, double dt, int M, int K) {
           t.push_back({s->NT, m == 0 ? s->Xn : s->Xt[m], s->kinc[m][0], s->z1, s->w1, s->kinc[m][1], s->z2, s->w1,
                        1.5 / gam, 0.5 / gam, s->Xt[m + 1]});
         B.enq += 1;
-        BCK(launch_combine_batch(model, put(B, t), blk_node, nseg, nb_node, st));
+        BCK(launch_combine_batch(model, s0->precision == BD_MIXED, put(B, t), blk_node, nseg, nb_node, st));
       }
     }
     // SDC correction
@@ -1508,7 +1523,7 @@ int enqueue_batch_step(BatchPlan& B, double dt, int M, int K) {
         std::vector<UpdateArgs> t;
         for (bd_state* s : B.m) t.push_back({s->NT, s->Xt[m + 1], s->kinc[m][2], s->z1, s->w1, s->Xc[m + 1]});
         B.enq += 1;
-        BCK(launch_update_batch(model, put(B, t), blk_node, nseg, nb_node, st));
+        BCK(launch_update_batch(model, s0->precision == BD_MIXED, put(B, t), blk_node, nseg, nb_node, st));
       }
     } else {
       for (int m = 1; m < M; ++m) {
@@ -1717,9 +1732,8 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   bool ok = alloc_n(s, &s->sptr, nsl) && alloc_n(s, &s->swidth, nsl) && alloc_n(s, &s->col, en) &&
             alloc_n(s, &s->diagpos, N) && alloc_n(s, &s->Ai, en) && alloc_n(s, &s->Aie, en) &&
             alloc_n(s, &s->Mc, en) && alloc_n(s, &s->Mv, en) && alloc_n(s, &s->ML, NT) && alloc_n(s, &s->Xn, ns * NT) &&
-            alloc_n(s, &s->dgs, NT) && alloc_n(s, &s->rl, NT) && alloc_n(s, &s->z1, (ns - 1) * NT) &&
-            alloc_n(s, &s->w1, (ns - 1) * NT) && alloc_n(s, &s->z2, (ns - 1) * NT) &&
-            alloc_n(s, &s->w2, (ns - 1) * NT) && alloc_n(s, &s->k1v, N) && alloc_n(s, &s->k2v, N) &&
+            alloc_n(s, &s->dgs, NT) && alloc_n(s, &s->rl, NT) && alloc_zw(s, &s->z1, (ns - 1) * NT) &&
+            alloc_zw(s, &s->w1, (ns - 1) * NT) && alloc_zw(s, &s->z2, (ns - 1) * NT) && alloc_n(s, &s->k1v, N) && alloc_n(s, &s->k2v, N) &&
             alloc_n(s, &s->avec, N) && alloc_n(s, &s->bvec, N) && alloc_n(s, &s->cg_r, N) &&
             alloc_n(s, &s->cg_z, N) && alloc_n(s, &s->cg_p, N) && alloc_n(s, &s->cg_q, N) &&
             alloc_n(s, &s->cg_invd, N) && alloc_n(s, &s->uprev, N) &&
@@ -1737,7 +1751,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
             alloc_n(s, reinterpret_cast<char**>(&s->d_amg), int64_t(sizeof(AmgDev))) &&
             alloc_n(s, reinterpret_cast<char**>(&s->d_amgf), int64_t(sizeof(AmgDevF)));
   for (int m = 0; ok && m < kMaxNodes; ++m)
-    ok = alloc_n(s, &s->Xt[m], ns * NT) && alloc_n(s, &s->Xc[m], ns * NT) && alloc_n(s, &s->fq[m], ns * NT) &&
+    ok = alloc_n(s, &s->Xt[m], ns * NT) && alloc_n(s, &s->Xc[m], ns * NT) && alloc_zw(s, &s->fq[m], ns * NT) &&
          alloc_n(s, &s->u[m], N);
   s->pcg_block = s->opts.cg_block > 0 ? s->opts.cg_block : 512;
   if (s->pcg_block % 32 != 0 || s->pcg_block > kSolverTierBlock[0]) {
@@ -1820,6 +1834,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     if (so == 2) s->opts.use_graph = 0;   // host-driven loops cannot be captured
   }
   if (ok && s->streaming) {
+    stream_prepare();   // kernel occupancies, queried outside any capture
     ok = alloc_n(s, reinterpret_cast<char**>(&s->d_sc), int64_t(sizeof(StreamScal))) &&
          alloc_n(s, &s->spart, int64_t(stream_grid_cap()) * 4);
     if (ok && s->precision == BD_FP64)

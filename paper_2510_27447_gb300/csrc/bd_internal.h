@@ -60,23 +60,23 @@ struct IonicLaunch {
   const double* XJ;          // state at which W is taken (ns x n)
   const double* u;           // S1/S2: u_{m+1}
   const double* k1v;         // S2
-  const double* z1;
-  const double* w1;
+  const void* z1;            // S2: stage 1's z, w ((ns-1) x n, the model's type T)
+  const void* w1;
   const double* Xprev;       // correction: X_m^new
   const double* Xq[kMaxNodes];   // correction: predictor nodes X~_j
   const double* uq[kMaxNodes];   // correction: u_j
-  const double* fq[kMaxNodes];   // correction: stored node fields f(X~_j)
+  const void* fq[kMaxNodes];     // correction: stored node fields f(X~_j) (ns x n, the model's type T)
   const double* ML;
   const uint32_t* stim_bits;
   const double* t_now;       // simulated time t^n of the step
   StimTable stim;
   double* dgs;               // out: M_L * s
   double* rl;                // out: node-local part of the condensed rhs
-  double* z;                 // out: (ns-1) x n
-  double* w;                 // out: (ns-1) x n
+  void* z;                   // out: (ns-1) x n values of the model's type T (exact: the
+  void* w;                   //      condensation computes them in T)
   double* avec;              // out: vector multiplied by A_i in the rhs
   double* bvec;              // out: vector multiplied by M in the rhs
-  double* fq_out;            // out (optional): node field at the F point
+  void* fq_out;              // out (optional): node field at the F point (type T)
   unsigned long long* clamp_count;
   const int* gate;           // optional: kernel does nothing when *gate == 0 (sweep test)
   void* pack;                // S1: store the condensation here (optional); S2P: read it
@@ -92,9 +92,10 @@ int jac_pack_values(int model);
 cudaError_t launch_ionic(const IonicLaunch& L, cudaStream_t st);
 cudaError_t launch_field(int model, int precision, int64_t n, const double* X, double inv_cm, double dt,
                          const uint32_t* stim_bits, const double* t_now, const StimTable& stim,
-                         double* fout, cudaStream_t st, const int* gate = nullptr);
-cudaError_t launch_combine(int model, int64_t n, const double* src, const double* k1v, const double* z1,
-                           const double* w1, const double* k2v, const double* z2, const double* w2, double m1,
+                         void* fout, cudaStream_t st, const int* gate = nullptr);   // fout: ns x n of the model's type
+// z/w arrays hold float when zw32 != 0 (the mixed path), double otherwise
+cudaError_t launch_combine(int model, int zw32, int64_t n, const double* src, const double* k1v, const void* z1,
+                           const void* w1, const double* k2v, const void* z2, const void* w2, double m1,
                            double m2, double* dst, cudaStream_t st, const int* gate = nullptr, double mhat1 = 0.0,
                            double etol = 1.0, unsigned long long* err = nullptr);
 // CN-RK2 reaction half step: Xout = X' + h f(X' + (h/2) f(X')), X' = X with
@@ -102,8 +103,8 @@ cudaError_t launch_combine(int model, int64_t n, const double* src, const double
 cudaError_t launch_rk2(int model, int precision, int64_t n, const double* X, const double* dv, double* Xout,
                        double h, double inv_cm, double dt, const uint32_t* stim_bits, const double* t_now,
                        const StimTable& stim, const double* u, double* avec, cudaStream_t st);
-cudaError_t launch_update(int model, int64_t n, const double* Xt, const double* ev, const double* z,
-                          const double* w, double* dst, cudaStream_t st, const int* gate = nullptr);
+cudaError_t launch_update(int model, int zw32, int64_t n, const double* Xt, const double* ev, const void* z,
+                          const void* w, double* dst, cudaStream_t st, const int* gate = nullptr);
 // sweep test of Algorithm 2: dmax = max |a - b| (dmax reset by the caller),
 // then gate = (dmax >= tol) and, while open, sweeps += 1
 cudaError_t launch_sweep_delta(int64_t n, const double* a, const double* b, unsigned long long* dmax,
@@ -136,17 +137,21 @@ struct FieldArgs {
   const uint32_t* stim_bits;
   const double* t_now;
   StimTable stim;
-  double* fout;
+  void* fout;                     // ns x n values of the model's type
 };
 struct CombineArgs {
   int64_t n;
-  const double *src, *k1v, *z1, *w1, *k2v, *z2, *w2;
+  const double *src, *k1v;
+  const void *z1, *w1;            // float or double (launch_combine_batch's zw32)
+  const double* k2v;
+  const void *z2, *w2;
   double m1, m2;
   double* dst;
 };
 struct UpdateArgs {
   int64_t n;
-  const double *Xt, *ev, *z, *w;
+  const double *Xt, *ev;
+  const void *z, *w;              // float or double (launch_update_batch's zw32)
   double* dst;
 };
 struct CopyArgs {
@@ -179,9 +184,9 @@ cudaError_t launch_ionic_batch(const IonicLaunch& proto, const IonicLaunch* tab,
                                int nblocks, cudaStream_t st);
 cudaError_t launch_field_batch(int model, int precision, const FieldArgs* tab, const int* blk, int nseg, int nblocks,
                                cudaStream_t st);
-cudaError_t launch_combine_batch(int model, const CombineArgs* tab, const int* blk, int nseg, int nblocks,
-                                 cudaStream_t st);
-cudaError_t launch_update_batch(int model, const UpdateArgs* tab, const int* blk, int nseg, int nblocks,
+cudaError_t launch_combine_batch(int model, int zw32, const CombineArgs* tab, const int* blk, int nseg,
+                                 int nblocks, cudaStream_t st);
+cudaError_t launch_update_batch(int model, int zw32, const UpdateArgs* tab, const int* blk, int nseg, int nblocks,
                                 cudaStream_t st);
 cudaError_t launch_copy_batch(const CopyArgs* tab, const int* blk, int nseg, int nblocks, cudaStream_t st);
 cudaError_t launch_extrap_batch(const ExtrapArgs* tab, const int* blk, int nseg, int nblocks, cudaStream_t st);
@@ -298,7 +303,28 @@ struct SellDevT {
   const int* col;
   const T* val;
   const int64_t* rp;               // non-null: CSR (col/val row-major), one warp per row
+  int lpr;                         // CSR in the streaming kernels: lanes per row (power of 2; 0: 32)
 };
+
+// lanes per CSR row in the streaming level kernels: the smallest power of two
+// at least a quarter of the mean row length, within [4, 32] (a lane keeps
+// four entries in flight, so most rows take one pass); rows of 256 entries
+// and more on average (restrictions onto the coarsest level: few rows, long)
+// get a whole block of kCsrBlockLanes threads each
+constexpr int kCsrBlockLanes = 256;
+inline int csr_lanes(int64_t nnz, int64_t n) {
+  if (n > 0 && nnz >= 256 * n) return kCsrBlockLanes;
+  const int64_t q = n > 0 ? (nnz + 4 * n - 1) / (4 * n) : 1;
+  int l = 4;
+  while (l < 32 && l < q) l *= 2;
+  return l;
+}
+
+// threads a streaming level kernel runs over M: one per row (SELL), lpr per row (CSR)
+template <class T>
+inline int64_t level_threads(const SellDevT<T>& M) {
+  return M.rp ? int64_t(M.n) * (M.lpr > 0 ? M.lpr : 32) : int64_t(M.n);
+}
 template <class T>
 struct AmgLevelDevT {
   SellDevT<T> A, P, R;
@@ -430,6 +456,9 @@ struct StreamLaunch {
 cudaError_t stream_solve(const StreamLaunch& a, int f32, const AmgDevF* M32, const AmgDev* M64, cudaStream_t st,
                          const cudaStream_t* side);
 int stream_grid_cap();
+// query (once, outside any capture) the resident blocks per SM of every
+// single-system streaming kernel; later plans read the cached values
+void stream_prepare();
 int stream_grid(int64_t rows);
 
 // ---- batched solves (one launch per phase for many independent systems) -----

@@ -46,6 +46,24 @@ struct Params<TP06> {
   static TP06<T> get(int) { return TP06<T>::make(); }
 };
 
+// ROS2 stage-2 evaluation point X* = X + k1/gamma with k1_y = z1 + w1 k1_v
+// (Eq. (3.13)); z1, w1 point at the node's entry of stage 1's vectors
+// (stride n).  On the FP64 path everything is FP64.  On the FP32 path z1 and
+// w1 are FP32 values, so k1_y is formed in FP32 and added to the rounded
+// state; the voltage xs0 stays FP64 (it also feeds the elliptic and
+// parabolic right-hand sides).
+template <class T, int NS>
+__device__ __forceinline__ void stage_point(const double* xj, double xs0, double k1v, const T* z1, const T* w1,
+                                            int64_t n, double inv_gamma, T* xst, T* k1y) {
+  xst[0] = T(xs0);
+  const T kv = T(k1v), ig = T(inv_gamma);
+#pragma unroll
+  for (int k = 1; k < NS; ++k) {
+    k1y[k - 1] = z1[(k - 1) * n] + w1[(k - 1) * n] * kv;
+    xst[k] = T(xj[k]) + k1y[k - 1] * ig;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // condensation kernel: S1, S2 and correction modes
 // ---------------------------------------------------------------------------
@@ -68,28 +86,24 @@ __device__ __forceinline__ void ionic_body(const IonicLaunch& L, const Model<T>&
     // z = A^-1 rho with stage 1's stored condensation; the condensed diagonal
     // and w are stage 1's (unchanged)
     const double k1v = L.k1v[i];
-    double xs[NS];
-    double k1y[NS - 1];
-    xs[0] = xj[0] + k1v * L.inv_gamma;
-#pragma unroll
-    for (int k = 1; k < NS; ++k) {
-      k1y[k - 1] = L.z1[(k - 1) * n + i] + L.w1[(k - 1) * n + i] * k1v;
-      xs[k] = xj[k] + k1y[k - 1] * L.inv_gamma;
-    }
+    const double xs0 = xj[0] + k1v * L.inv_gamma;
     T xst[NS];
-#pragma unroll
-    for (int k = 0; k < NS; ++k) xst[k] = T(xs[k]);
+    T k1y[NS - 1];
+    stage_point<T, NS>(xj, xs0, k1v, static_cast<const T*>(L.z1) + i, static_cast<const T*>(L.w1) + i, n,
+                       L.inv_gamma, xst, k1y);
     ValSink<T, Mod> fs;
     P.eval(xst, T(istim), T(L.inv_cm), fs);
     T rho[NS - 1];
+    const T ck1 = T(L.ck1);
 #pragma unroll
-    for (int k = 1; k < NS; ++k) rho[k - 1] = T(double(fs.f[k]) - L.ck1 * k1y[k - 1]);
+    for (int k = 1; k < NS; ++k) rho[k - 1] = fs.f[k] - ck1 * k1y[k - 1];
     T corr, z[NS - 1];
     cond_solve<T, Mod>(static_cast<const T*>(L.pack) + i, n, rho, corr, z);
     L.rl[i] = L.ML[i] * (double(fs.f[0]) + double(corr));
+    T* zo = static_cast<T*>(L.z);
 #pragma unroll
-    for (int k = 0; k < NS - 1; ++k) L.z[k * n + i] = double(z[k]);
-    L.avec[i] = xs[0] + L.u[i];
+    for (int k = 0; k < NS - 1; ++k) zo[k * n + i] = z[k];
+    L.avec[i] = xs0 + L.u[i];
     if (L.bvec) L.bvec[i] = k1v;
   } else {
     T xt[NS];
@@ -121,49 +135,48 @@ __device__ __forceinline__ void ionic_body(const IonicLaunch& L, const Model<T>&
       // both (FP64); the FP32 predictor keeps fewer values live without it
       if (L.jac_out) jac_store<T, Mod, sizeof(T) == 8>(e, static_cast<T*>(L.jac_out) + i, n);
       if (L.fq_out) {
+        T* fo = static_cast<T*>(L.fq_out);
 #pragma unroll
-        for (int k = 0; k < NS; ++k) L.fq_out[k * n + i] = double(e.f[k]);
+        for (int k = 0; k < NS; ++k) fo[k * n + i] = e.f[k];
       }
     } else if constexpr (MODE == MODE_S2) {
       // F point X* = X + k1/gamma, k1_y = z1 + w1 k1_v
       const double k1v = L.k1v[i];
-      double xs[NS];
-      double k1y[NS - 1];
-      xs[0] = xj[0] + k1v * L.inv_gamma;
-#pragma unroll
-      for (int k = 1; k < NS; ++k) {
-        k1y[k - 1] = L.z1[(k - 1) * n + i] + L.w1[(k - 1) * n + i] * k1v;
-        xs[k] = xj[k] + k1y[k - 1] * L.inv_gamma;
-      }
+      const double xs0 = xj[0] + k1v * L.inv_gamma;
       T xst[NS];
-#pragma unroll
-      for (int k = 0; k < NS; ++k) xst[k] = T(xs[k]);
+      T k1y[NS - 1];
+      stage_point<T, NS>(xj, xs0, k1v, static_cast<const T*>(L.z1) + i, static_cast<const T*>(L.w1) + i, n,
+                         L.inv_gamma, xst, k1y);
       ValSink<T, Mod> fs;
       P.eval(xst, T(istim), T(L.inv_cm), fs);
+      const T ck1 = T(L.ck1);
 #pragma unroll
-      for (int k = 1; k < NS; ++k) rho[k - 1] = T(double(fs.f[k]) - L.ck1 * k1y[k - 1]);
+      for (int k = 1; k < NS; ++k) rho[k - 1] = fs.f[k] - ck1 * k1y[k - 1];
       fv = double(fs.f[0]);
-      avec = xs[0] + L.u[i];
+      avec = xs0 + L.u[i];
       bvec = k1v;
     } else {
       // correction: rho = [(X_m^new - X~_{m+1}) + sum_j S_j f_j] / dt_m on the y rows
-      double q[NS];
+      // (the stored fields are values of T: the quadrature sum runs in T, the
+      // state difference in FP64 before it is rounded)
+      T q[NS];
 #pragma unroll
-      for (int k = 0; k < NS; ++k) q[k] = 0.0;
+      for (int k = 0; k < NS; ++k) q[k] = T(0);
       double av = 0.0;
       // NQ quadrature nodes, known at compile time: the node loop unrolls and
       // every pointer of L is read at a constant offset
 #pragma unroll
       for (int jn = 0; jn < NQ; ++jn) {
-        const double S = L.S[jn];
-        const double* fj = L.fq[jn];
+        const T S = T(L.S[jn]);
+        const T* fj = static_cast<const T*>(L.fq[jn]);
 #pragma unroll
         for (int k = 0; k < NS; ++k) q[k] += S * fj[k * n + i];
-        av += S * (L.Xq[jn][i] + L.uq[jn][i]);
+        av += L.S[jn] * (L.Xq[jn][i] + L.uq[jn][i]);
       }
+      const T idt = T(L.inv_dt);
 #pragma unroll
-      for (int k = 1; k < NS; ++k) rho[k - 1] = T(((L.Xprev[k * n + i] - xj[k]) + q[k]) * L.inv_dt);
-      fv = q[0] * L.inv_dt;
+      for (int k = 1; k < NS; ++k) rho[k - 1] = (T(L.Xprev[k * n + i] - xj[k]) + q[k]) * idt;
+      fv = double(q[0]) * L.inv_dt;
       avec = av;
       bvec = L.Xprev[i] - xj[0];
     }
@@ -179,10 +192,12 @@ __device__ __forceinline__ void ionic_body(const IonicLaunch& L, const Model<T>&
     const double ml = L.ML[i];
     L.dgs[i] = ml * sd;
     L.rl[i] = ml * (fv + double(corr));
+    T* zo = static_cast<T*>(L.z);
+    T* wo = static_cast<T*>(L.w);
 #pragma unroll
     for (int k = 0; k < NS - 1; ++k) {
-      L.z[k * n + i] = double(z[k]);
-      L.w[k * n + i] = double(w[k]);
+      zo[k * n + i] = z[k];
+      wo[k * n + i] = w[k];
     }
     L.avec[i] = avec;
     if (L.bvec) L.bvec[i] = bvec;
@@ -206,7 +221,7 @@ __global__ void __launch_bounds__(kBlock) ionic_batch_kernel(const IonicLaunch* 
 template <template <class> class Model, class T>
 __device__ __forceinline__ void field_body(int64_t n, const double* X, double inv_cm, double dt,
                                            const uint32_t* stim_bits, const double* t_now, const StimTable& stim,
-                                           double* fout, const Model<T>& P, const int* gate, int64_t i) {
+                                           void* foutv, const Model<T>& P, const int* gate, int64_t i) {
   using Mod = Model<T>;
   constexpr int NS = Mod::NS;
   if (i >= n) return;
@@ -218,14 +233,15 @@ __device__ __forceinline__ void field_body(int64_t n, const double* X, double in
   for (int k = 0; k < NS; ++k) x[k] = T(X[k * n + i]);
   ValSink<T, Mod> fs;
   P.eval(x, T(istim), T(inv_cm), fs);
+  T* fout = static_cast<T*>(foutv);
 #pragma unroll
-  for (int k = 0; k < NS; ++k) fout[k * n + i] = double(fs.f[k]);
+  for (int k = 0; k < NS; ++k) fout[k * n + i] = fs.f[k];
 }
 
 template <template <class> class Model, class T>
 __global__ void __launch_bounds__(kBlock) field_kernel(int64_t n, const double* X, double inv_cm, double dt,
                                                        const uint32_t* stim_bits, const double* t_now,
-                                                       const StimTable stim, double* fout, const Model<T> P,
+                                                       const StimTable stim, void* fout, const Model<T> P,
                                                        const int* gate) {
   field_body<Model, T>(n, X, inv_cm, dt, stim_bits, t_now, stim, fout, P, gate,
                        int64_t(blockIdx.x) * blockDim.x + threadIdx.x);
@@ -244,10 +260,10 @@ __global__ void __launch_bounds__(kBlock) field_batch_kernel(const FieldArgs* ta
 // With err != nullptr also the embedded error estimate: X_hat = X + k1/gamma,
 // |X_{m+1} - X_hat| / (etol (1 + |X_{m+1}|)), maximum over the launch
 // accumulated with an order-independent atomicMax on the bit pattern.
-template <int NS>
+template <int NS, class ZT>
 __global__ void __launch_bounds__(kBlock) combine_kernel(int64_t n, const double* src, const double* k1v,
-                                                         const double* z1, const double* w1, const double* k2v,
-                                                         const double* z2, const double* w2, double m1, double m2,
+                                                         const ZT* z1, const ZT* w1, const double* k2v,
+                                                         const ZT* z2, const ZT* w2, double m1, double m2,
                                                          double* dst, const int* gate, double mhat1, double etol,
                                                          unsigned long long* err) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -257,15 +273,32 @@ __global__ void __launch_bounds__(kBlock) combine_kernel(int64_t n, const double
     const double x0 = src[i] + m1 * a + m2 * b;
     dst[i] = x0;
     if (err) e = fabs(x0 - (src[i] + mhat1 * a)) / (etol * (1.0 + fabs(x0)));
+    if constexpr (sizeof(ZT) == 4) {
+      // FP32 stage vectors: the increment m1 k1 + m2 k2 is formed in FP32
+      // and added to the FP64 state (one conversion and one FP64 add per
+      // variable: GB300's FP64 pipe, not memory, bounds the FP64 form)
+      const float af = float(a), bf = float(b), m1f = float(m1), m2f = float(m2), mhf = float(mhat1);
 #pragma unroll
-    for (int k = 1; k < NS; ++k) {
-      const int64_t o = (k - 1) * n + i;
-      const double k1 = z1[o] + w1[o] * a;
-      const double k2 = z2[o] + w2[o] * b;
-      const double xs = src[k * n + i];
-      const double xk = xs + m1 * k1 + m2 * k2;
-      dst[k * n + i] = xk;
-      if (err) e = fmax(e, fabs(xk - (xs + mhat1 * k1)) / (etol * (1.0 + fabs(xk))));
+      for (int k = 1; k < NS; ++k) {
+        const int64_t o = (k - 1) * n + i;
+        const float k1 = z1[o] + w1[o] * af;
+        const float k2 = z2[o] + w2[o] * bf;
+        const float inc = m1f * k1 + m2f * k2;
+        const double xk = src[k * n + i] + double(inc);
+        dst[k * n + i] = xk;
+        if (err) e = fmax(e, double(fabsf(inc - mhf * k1)) / (etol * (1.0 + fabs(xk))));
+      }
+    } else {
+#pragma unroll
+      for (int k = 1; k < NS; ++k) {
+        const int64_t o = (k - 1) * n + i;
+        const double k1 = z1[o] + w1[o] * a;
+        const double k2 = z2[o] + w2[o] * b;
+        const double xs = src[k * n + i];
+        const double xk = xs + m1 * k1 + m2 * k2;
+        dst[k * n + i] = xk;
+        if (err) e = fmax(e, fabs(xk - (xs + mhat1 * k1)) / (etol * (1.0 + fabs(xk))));
+      }
     }
   }
   if (err) {
@@ -310,19 +343,28 @@ __global__ void __launch_bounds__(kBlock) rk2_kernel(int64_t n, const double* X,
 }
 
 // X^new_{m+1} = X~_{m+1} + eps, eps_y = z + w eps_v
-template <int NS>
+template <int NS, class ZT>
 __global__ void __launch_bounds__(kBlock) update_kernel(int64_t n, const double* Xt, const double* ev,
-                                                        const double* z, const double* w, double* dst,
+                                                        const ZT* z, const ZT* w, double* dst,
                                                         const int* gate) {
   const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (gate && *gate == 0) return;
   const double e = ev[i];
   dst[i] = Xt[i] + e;
+  if constexpr (sizeof(ZT) == 4) {   // FP32 increment added to the FP64 state
+    const float ef = float(e);
 #pragma unroll
-  for (int k = 1; k < NS; ++k) {
-    const int64_t o = (k - 1) * n + i;
-    dst[k * n + i] = Xt[k * n + i] + z[o] + w[o] * e;
+    for (int k = 1; k < NS; ++k) {
+      const int64_t o = (k - 1) * n + i;
+      dst[k * n + i] = Xt[k * n + i] + double(z[o] + w[o] * ef);
+    }
+  } else {
+#pragma unroll
+    for (int k = 1; k < NS; ++k) {
+      const int64_t o = (k - 1) * n + i;
+      dst[k * n + i] = Xt[k * n + i] + z[o] + w[o] * e;
+    }
   }
 }
 
@@ -409,7 +451,7 @@ __global__ void clear_gated_kernel(unsigned long long* p, const int* gate) {
 // Each block works on one handle's nodes with that handle's arguments; the
 // arithmetic per node is the one of the single-handle kernels above.
 
-template <int NS>
+template <int NS, class ZT>
 __global__ void __launch_bounds__(kBlock) combine_batch_kernel(const CombineArgs* tab, const int* blk, int nseg) {
   const SegInfo sg = seg_locate(blk, nseg);
   const CombineArgs& a = stage(tab, sg.r);
@@ -418,16 +460,29 @@ __global__ void __launch_bounds__(kBlock) combine_batch_kernel(const CombineArgs
   if (i >= n) return;
   const double k1 = a.k1v[i], k2 = a.k2v[i];
   a.dst[i] = a.src[i] + a.m1 * k1 + a.m2 * k2;
+  const ZT *z1 = static_cast<const ZT*>(a.z1), *w1 = static_cast<const ZT*>(a.w1);
+  const ZT *z2 = static_cast<const ZT*>(a.z2), *w2 = static_cast<const ZT*>(a.w2);
+  if constexpr (sizeof(ZT) == 4) {   // as combine_kernel: FP32 increment, FP64 state
+    const float af = float(k1), bf = float(k2), m1f = float(a.m1), m2f = float(a.m2);
 #pragma unroll
-  for (int k = 1; k < NS; ++k) {
-    const int64_t o = (k - 1) * n + i;
-    const double y1 = a.z1[o] + a.w1[o] * k1;
-    const double y2 = a.z2[o] + a.w2[o] * k2;
-    a.dst[k * n + i] = a.src[k * n + i] + a.m1 * y1 + a.m2 * y2;
+    for (int k = 1; k < NS; ++k) {
+      const int64_t o = (k - 1) * n + i;
+      const float y1 = z1[o] + w1[o] * af;
+      const float y2 = z2[o] + w2[o] * bf;
+      a.dst[k * n + i] = a.src[k * n + i] + double(m1f * y1 + m2f * y2);
+    }
+  } else {
+#pragma unroll
+    for (int k = 1; k < NS; ++k) {
+      const int64_t o = (k - 1) * n + i;
+      const double y1 = z1[o] + w1[o] * k1;
+      const double y2 = z2[o] + w2[o] * k2;
+      a.dst[k * n + i] = a.src[k * n + i] + a.m1 * y1 + a.m2 * y2;
+    }
   }
 }
 
-template <int NS>
+template <int NS, class ZT>
 __global__ void __launch_bounds__(kBlock) update_batch_kernel(const UpdateArgs* tab, const int* blk, int nseg) {
   const SegInfo sg = seg_locate(blk, nseg);
   const UpdateArgs& a = stage(tab, sg.r);
@@ -436,10 +491,20 @@ __global__ void __launch_bounds__(kBlock) update_batch_kernel(const UpdateArgs* 
   if (i >= n) return;
   const double e = a.ev[i];
   a.dst[i] = a.Xt[i] + e;
+  const ZT *z = static_cast<const ZT*>(a.z), *w = static_cast<const ZT*>(a.w);
+  if constexpr (sizeof(ZT) == 4) {   // as update_kernel: FP32 increment, FP64 state
+    const float ef = float(e);
 #pragma unroll
-  for (int k = 1; k < NS; ++k) {
-    const int64_t o = (k - 1) * n + i;
-    a.dst[k * n + i] = a.Xt[k * n + i] + a.z[o] + a.w[o] * e;
+    for (int k = 1; k < NS; ++k) {
+      const int64_t o = (k - 1) * n + i;
+      a.dst[k * n + i] = a.Xt[k * n + i] + double(z[o] + w[o] * ef);
+    }
+  } else {
+#pragma unroll
+    for (int k = 1; k < NS; ++k) {
+      const int64_t o = (k - 1) * n + i;
+      a.dst[k * n + i] = a.Xt[k * n + i] + z[o] + w[o] * e;
+    }
   }
 }
 
@@ -576,18 +641,31 @@ cudaError_t launch_field_batch(int model, int precision, const FieldArgs* tab, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_combine_batch(int model, const CombineArgs* tab, const int* blk, int nseg, int nb,
+cudaError_t launch_combine_batch(int model, int zw32, const CombineArgs* tab, const int* blk, int nseg, int nb,
                                  cudaStream_t st) {
   if (nb == 0) return cudaSuccess;
-  if (model == BD_TP06_EPI) combine_batch_kernel<19><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
-  else combine_batch_kernel<8><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+  const bool tp = model == BD_TP06_EPI;
+  if (zw32) {
+    if (tp) combine_batch_kernel<19, float><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+    else combine_batch_kernel<8, float><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+  } else {
+    if (tp) combine_batch_kernel<19, double><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+    else combine_batch_kernel<8, double><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_batch(int model, const UpdateArgs* tab, const int* blk, int nseg, int nb, cudaStream_t st) {
+cudaError_t launch_update_batch(int model, int zw32, const UpdateArgs* tab, const int* blk, int nseg, int nb,
+                                cudaStream_t st) {
   if (nb == 0) return cudaSuccess;
-  if (model == BD_TP06_EPI) update_batch_kernel<19><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
-  else update_batch_kernel<8><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+  const bool tp = model == BD_TP06_EPI;
+  if (zw32) {
+    if (tp) update_batch_kernel<19, float><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+    else update_batch_kernel<8, float><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+  } else {
+    if (tp) update_batch_kernel<19, double><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+    else update_batch_kernel<8, double><<<nb, kBlock, 0, st>>>(tab, blk, nseg);
+  }
   return cudaGetLastError();
 }
 
@@ -610,7 +688,7 @@ cudaError_t launch_finish_batch(const FinishArgs* tab, const int* blk, int nseg,
 }
 
 cudaError_t launch_field(int model, int precision, int64_t n, const double* X, double inv_cm, double dt,
-                         const uint32_t* stim_bits, const double* step_n, const StimTable& stim, double* fout,
+                         const uint32_t* stim_bits, const double* step_n, const StimTable& stim, void* fout,
                          cudaStream_t st, const int* gate) {
   if (n == 0) return cudaSuccess;
   const unsigned grid = unsigned((n + kBlock - 1) / kBlock);
@@ -643,25 +721,45 @@ cudaError_t launch_rk2(int model, int precision, int64_t n, const double* X, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_combine(int model, int64_t n, const double* src, const double* k1v, const double* z1,
-                           const double* w1, const double* k2v, const double* z2, const double* w2, double m1,
+namespace {
+template <class ZT>
+void combine_typed(int model, unsigned grid, cudaStream_t st, int64_t n, const double* src, const double* k1v,
+                   const void* z1, const void* w1, const double* k2v, const void* z2, const void* w2, double m1,
+                   double m2, double* dst, const int* gate, double mhat1, double etol, unsigned long long* err) {
+  const ZT *a = static_cast<const ZT*>(z1), *b = static_cast<const ZT*>(w1);
+  const ZT *c = static_cast<const ZT*>(z2), *d = static_cast<const ZT*>(w2);
+  if (model == BD_TP06_EPI)
+    combine_kernel<19, ZT><<<grid, kBlock, 0, st>>>(n, src, k1v, a, b, k2v, c, d, m1, m2, dst, gate, mhat1, etol, err);
+  else
+    combine_kernel<8, ZT><<<grid, kBlock, 0, st>>>(n, src, k1v, a, b, k2v, c, d, m1, m2, dst, gate, mhat1, etol, err);
+}
+}  // namespace
+
+cudaError_t launch_combine(int model, int zw32, int64_t n, const double* src, const double* k1v, const void* z1,
+                           const void* w1, const double* k2v, const void* z2, const void* w2, double m1,
                            double m2, double* dst, cudaStream_t st, const int* gate, double mhat1, double etol,
                            unsigned long long* err) {
   if (n == 0) return cudaSuccess;
   const unsigned grid = unsigned((n + kBlock - 1) / kBlock);
-  if (model == BD_TP06_EPI)
-    combine_kernel<19><<<grid, kBlock, 0, st>>>(n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst, gate, mhat1, etol, err);
-  else
-    combine_kernel<8><<<grid, kBlock, 0, st>>>(n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst, gate, mhat1, etol, err);
+  if (zw32) combine_typed<float>(model, grid, st, n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst, gate, mhat1, etol, err);
+  else combine_typed<double>(model, grid, st, n, src, k1v, z1, w1, k2v, z2, w2, m1, m2, dst, gate, mhat1, etol, err);
   return cudaGetLastError();
 }
 
-cudaError_t launch_update(int model, int64_t n, const double* Xt, const double* ev, const double* z,
-                          const double* w, double* dst, cudaStream_t st, const int* gate) {
+cudaError_t launch_update(int model, int zw32, int64_t n, const double* Xt, const double* ev, const void* z,
+                          const void* w, double* dst, cudaStream_t st, const int* gate) {
   if (n == 0) return cudaSuccess;
   const unsigned grid = unsigned((n + kBlock - 1) / kBlock);
-  if (model == BD_TP06_EPI) update_kernel<19><<<grid, kBlock, 0, st>>>(n, Xt, ev, z, w, dst, gate);
-  else update_kernel<8><<<grid, kBlock, 0, st>>>(n, Xt, ev, z, w, dst, gate);
+  const bool tp = model == BD_TP06_EPI;
+  if (zw32) {
+    const float *a = static_cast<const float*>(z), *b = static_cast<const float*>(w);
+    if (tp) update_kernel<19, float><<<grid, kBlock, 0, st>>>(n, Xt, ev, a, b, dst, gate);
+    else update_kernel<8, float><<<grid, kBlock, 0, st>>>(n, Xt, ev, a, b, dst, gate);
+  } else {
+    const double *a = static_cast<const double*>(z), *b = static_cast<const double*>(w);
+    if (tp) update_kernel<19, double><<<grid, kBlock, 0, st>>>(n, Xt, ev, a, b, dst, gate);
+    else update_kernel<8, double><<<grid, kBlock, 0, st>>>(n, Xt, ev, a, b, dst, gate);
+  }
   return cudaGetLastError();
 }
 

@@ -39,7 +39,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 
 #include "bd_internal.h"
 #include "sparse.cuh"
@@ -51,6 +53,7 @@ namespace bd {
 namespace {
 
 constexpr int kSB = 256;       // threads per block of every streaming kernel
+static_assert(kSB == kCsrBlockLanes, "a block-per-row CSR level needs blocks of kCsrBlockLanes threads");
 constexpr int kBlocksPerSM = 8;
 
 // ---- policies -------------------------------------------------------------------
@@ -211,39 +214,89 @@ __device__ __forceinline__ X srow4(const int64_t* __restrict__ sptr4, const int*
 // every row i of an AMG-level operator (SELL: thread per row; CSR: warp per
 // row, butterfly sum): epi(i, (M x)_i), run by one lane per row.  Level 0's
 // operators are streamed with evict-first loads, the coarser levels' stay
-// cacheable (read twice a cycle, they fit in L2).
-template <class T, class F>
+// cacheable (read twice a cycle, they fit in L2).  K is the set of forms a
+// kernel compiles (kRows* flags): a kernel that never meets a form leaves
+// it out, which keeps registers low and resident warps high for the
+// latency-bound coarse products.
+constexpr int kRowsSellStream = 1, kRowsSellCache = 2, kRowsCsrLanes = 4, kRowsCsrBlock = 8;
+constexpr int kRowsAll = 15;
+constexpr int kRowsCoarse = kRowsSellCache | kRowsCsrLanes | kRowsCsrBlock;   // levels >= 1
+
+template <class T, int K, class F>
 __device__ __forceinline__ void level_rows(const SellDevT<T>& M, const T* x, bool streamop, SegInfo sg, F&& epi) {
   const int gt = sg.lb * blockDim.x + threadIdx.x;
   const int gs = sg.nb * blockDim.x;
-  if (M.rp) {
+  if constexpr (K == kRowsSellStream) {
+    for (int i = gt; i < M.n; i += gs) epi(i, srow<true, T, T>(M.sptr, M.sw, M.col, M.val, x, i));
+    return;
+  }
+  if ((K & kRowsCsrBlock) && M.rp && M.lpr > 32) {
+    // a block per row (blockDim.x == kCsrBlockLanes): the row's entries
+    // strided over the block's threads (a few each: the rows are long, not
+    // huge), then the block's fixed-order sum; the row loop is block-uniform
+    // so every thread reaches the block sum's barriers
+    __shared__ T shb[1][32];
+    for (int i = sg.lb; i < M.n; i += sg.nb) {
+      const int64_t e = __ldg(M.rp + i + 1);
+      T v[1] = {T(0)};
+      for (int64_t p = __ldg(M.rp + i) + threadIdx.x; p < e; p += blockDim.x)
+        v[0] += __ldg(M.val + p) * __ldg(x + __ldg(M.col + p));
+      block_sum<1, T>(v, shb);
+      if (threadIdx.x == 0) epi(i, v[0]);
+    }
+  } else if ((K & kRowsCsrLanes) && M.rp) {
+    // L lanes per row (a power of two), 32 / L rows per warp pass; a lane
+    // keeps four entries L apart in flight, four partial sums added in a
+    // fixed order, then a butterfly over the row's lanes (deterministic).
+    // The pass loop is warp-uniform so every shuffle has all 32 lanes.
+    const int L = M.lpr > 0 ? M.lpr : 32;
     const int lane = threadIdx.x & 31;
-    for (int i = gt >> 5; i < M.n; i += gs >> 5) {
-      // four strided entries a lane in flight, four partial sums added in a
-      // fixed order (deterministic)
+    const int sub = lane & (L - 1);
+    const int rows_per_warp = 32 / L;
+    const int grp = lane / L;
+    const int step = (gs >> 5) * rows_per_warp;
+    int base = (gt >> 5) * rows_per_warp;
+    int i = base + grp;
+    int64_t pb = 0, pe = 0;
+    if (i < M.n) {
+      pb = __ldg(M.rp + i);
+      pe = __ldg(M.rp + i + 1);
+    }
+    for (; base < M.n; base += step) {
+      // the next pass's row pointers are requested before this pass's entries
+      const int inext = i + step;
+      int64_t nb = 0, ne = 0;
+      if (inext < M.n) {
+        nb = __ldg(M.rp + inext);
+        ne = __ldg(M.rp + inext + 1);
+      }
       T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-      const int64_t e = M.rp[i + 1];
-      for (int64_t p = M.rp[i] + lane; p < e; p += 128) {
-        const bool b1 = p + 32 < e, b2 = p + 64 < e, b3 = p + 96 < e;
-        const int c0 = __ldg(M.col + p);
-        const int c1 = b1 ? __ldg(M.col + p + 32) : c0;
-        const int c2 = b2 ? __ldg(M.col + p + 64) : c0;
-        const int c3 = b3 ? __ldg(M.col + p + 96) : c0;
-        const T v0 = __ldg(M.val + p);
-        const T v1 = b1 ? __ldg(M.val + p + 32) : T(0);
-        const T v2 = b2 ? __ldg(M.val + p + 64) : T(0);
-        const T v3 = b3 ? __ldg(M.val + p + 96) : T(0);
-        s0 += v0 * __ldg(x + c0);
-        s1 += v1 * __ldg(x + c1);
-        s2 += v2 * __ldg(x + c2);
-        s3 += v3 * __ldg(x + c3);
+      {
+        const int64_t e = pe;
+        for (int64_t p = pb + sub; p < e; p += 4 * L) {
+          const bool b1 = p + L < e, b2 = p + 2 * L < e, b3 = p + 3 * L < e;
+          const int c0 = __ldg(M.col + p);
+          const int c1 = b1 ? __ldg(M.col + p + L) : c0;
+          const int c2 = b2 ? __ldg(M.col + p + 2 * L) : c0;
+          const int c3 = b3 ? __ldg(M.col + p + 3 * L) : c0;
+          const T v0 = __ldg(M.val + p);
+          const T v1 = b1 ? __ldg(M.val + p + L) : T(0);
+          const T v2 = b2 ? __ldg(M.val + p + 2 * L) : T(0);
+          const T v3 = b3 ? __ldg(M.val + p + 3 * L) : T(0);
+          s0 += v0 * __ldg(x + c0);
+          s1 += v1 * __ldg(x + c1);
+          s2 += v2 * __ldg(x + c2);
+          s3 += v3 * __ldg(x + c3);
+        }
       }
       T s = (s0 + s1) + (s2 + s3);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) epi(i, s);
+      for (int o = L >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (sub == 0 && i < M.n) epi(i, s);
+      i = inext;
+      pb = nb;
+      pe = ne;
     }
-  } else if (streamop) {
+  } else if ((K & kRowsSellStream) && streamop) {
     for (int i = gt; i < M.n; i += gs) epi(i, srow<true, T, T>(M.sptr, M.sw, M.col, M.val, x, i));
   } else {
     for (int i = gt; i < M.n; i += gs) epi(i, srow<false, T, T>(M.sptr, M.sw, M.col, M.val, x, i));
@@ -618,7 +671,8 @@ __global__ void __launch_bounds__(kSB) st_batch_cond_kernel(const __grid_constan
 // flag, level-0 vectors); both resolve the same system for a block.
 
 // r_l = b_l - A_l x_l
-template <class T, class V, class S>
+// (L0: compiled for level 0 only, else for the coarser levels only)
+template <class T, class V, class S, bool L0>
 __global__ void __launch_bounds__(kSB) st_vc_res_kernel(const __grid_constant__ V hv, const __grid_constant__ S src,
                                                         int l) {
   count_launch(src);
@@ -627,17 +681,23 @@ __global__ void __launch_bounds__(kSB) st_vc_res_kernel(const __grid_constant__ 
   const StreamLaunch& a = params(src, sg.r);
   if (a.sc->stop || l >= H.nlev) return;
   const AmgLevelDevT<T>& L = H.L[l];
-  const T* b = l == 0 ? static_cast<const T*>(a.r) : L.b;
-  if (l == 0 && sizeof(T) == 4 && a.col4) {
-    for (int i = sg.lb * blockDim.x + threadIdx.x; i < L.A.n; i += sg.nb * blockDim.x)
-      L.r[i] = b[i] - T(srow4<T>(a.sptr4, a.sw4, a.col4, static_cast<const float*>(a.valT4), L.x, i));
-    return;
+  if constexpr (L0) {
+    const T* b = static_cast<const T*>(a.r);
+    if (sizeof(T) == 4 && a.col4) {
+      for (int i = sg.lb * blockDim.x + threadIdx.x; i < L.A.n; i += sg.nb * blockDim.x)
+        L.r[i] = b[i] - T(srow4<T>(a.sptr4, a.sw4, a.col4, static_cast<const float*>(a.valT4), L.x, i));
+      return;
+    }
+    level_rows<T, kRowsSellStream>(L.A, L.x, true, sg, [&](int i, T ax) { L.r[i] = b[i] - ax; });
+  } else {
+    const T* b = L.b;
+    level_rows<T, kRowsCoarse>(L.A, L.x, false, sg, [&](int i, T ax) { L.r[i] = b[i] - ax; });
   }
-  level_rows<T>(L.A, L.x, l == 0, sg, [&](int i, T ax) { L.r[i] = b[i] - ax; });
 }
 
 // b_{l+1} = R_l r_l and the next level's pre-smoothing x_{l+1} = w D^-1 b_{l+1}
-template <class T, class V, class S>
+// (K: the row forms compiled; the block-per-row form only where R_l has it)
+template <class T, class V, class S, int K>
 __global__ void __launch_bounds__(kSB) st_vc_restrict_kernel(const __grid_constant__ V hv,
                                                              const __grid_constant__ S src, int l) {
   count_launch(src);
@@ -651,7 +711,7 @@ __global__ void __launch_bounds__(kSB) st_vc_restrict_kernel(const __grid_consta
   T* xn = last ? nullptr : H.L[l + 1].x;
   const T* invdn = last ? nullptr : H.L[l + 1].invd;
   const T omegan = last ? T(0) : H.L[l + 1].omega;
-  level_rows<T>(L.R, L.r, l == 0, sg, [&](int i, T v) {
+  level_rows<T, K>(L.R, L.r, l == 0, sg, [&](int i, T v) {
     bn[i] = v;
     if (xn) xn[i] = omegan * invdn[i] * v;
   });
@@ -713,12 +773,13 @@ __global__ void __launch_bounds__(kSB) st_vc_prolong_kernel(const __grid_constan
   if (a.sc->stop || l >= H.nlev) return;
   const AmgLevelDevT<T>& L = H.L[l];
   const T* yc = l + 1 == H.nlev ? H.xc : H.L[l + 1].y;
-  level_rows<T>(L.P, yc, l == 0, sg, [&](int i, T v) { L.x[i] += v; });
+  // rows of P are short: never a block per row
+  level_rows<T, kRowsAll & ~kRowsCsrBlock>(L.P, yc, l == 0, sg, [&](int i, T v) { L.x[i] += v; });
 }
 
 // y_l = x_l + w D^-1 (b_l - A_l x_l); on level 0 y is z, r.z and the decision
 // (every system of a batch has at least one block here and votes)
-template <class T, class V, class S>
+template <class T, class V, class S, bool L0>
 __global__ void __launch_bounds__(kSB) st_vc_post_kernel(const __grid_constant__ V hv, const __grid_constant__ S src,
                                                          int l) {
   count_launch(src);
@@ -746,15 +807,18 @@ __global__ void __launch_bounds__(kSB) st_vc_post_kernel(const __grid_constant__
     y[i] = yi;
     acc[0] += bi * yi;
   };
-  if (l == 0 && sizeof(T) == 4 && a.col4) {
-    for (int i = sg.lb * blockDim.x + threadIdx.x; i < L.A.n; i += sg.nb * blockDim.x)
-      post(i, T(srow4<T>(a.sptr4, a.sw4, a.col4, static_cast<const float*>(a.valT4), L.x, i)));
+  if constexpr (L0) {
+    if (sizeof(T) == 4 && a.col4) {
+      for (int i = sg.lb * blockDim.x + threadIdx.x; i < L.A.n; i += sg.nb * blockDim.x)
+        post(i, T(srow4<T>(a.sptr4, a.sw4, a.col4, static_cast<const float*>(a.valT4), L.x, i)));
+    } else {
+      level_rows<T, kRowsSellStream>(L.A, L.x, true, sg, post);
+    }
+    if (last_block_total<1, T>(acc, a.part, &c.ticket, sg) && threadIdx.x == 0)
+      vote_inner(src, a, inner_decide<T>(a, acc[0]));
   } else {
-    level_rows<T>(L.A, L.x, l == 0, sg, post);
+    level_rows<T, kRowsCoarse>(L.A, L.x, false, sg, post);
   }
-  if (l != 0) return;
-  if (last_block_total<1, T>(acc, a.part, &c.ticket, sg) && threadIdx.x == 0)
-    vote_inner(src, a, inner_decide<T>(a, acc[0]));
 }
 
 // x += |r| d after an inner solve that ran without failure
@@ -809,7 +873,33 @@ int grid_for(int64_t threads) {
   return int(std::max<int64_t>(1, std::min<int64_t>(b, stream_grid_cap())));
 }
 
-int level_grid(const void* rp, int n) { return grid_for(rp ? int64_t(n) * 32 : int64_t(n)); }
+// resident blocks per SM of kernel k at kSB threads, queried once and cached
+// (stream_prepare fills the cache before any capture)
+std::mutex g_occ_mu;
+std::unordered_map<const void*, int> g_occ;
+
+int resident_blocks(const void* k) {
+  std::lock_guard<std::mutex> g(g_occ_mu);
+  auto it = g_occ.find(k);
+  if (it != g_occ.end()) return it->second;
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kSB, 0) != cudaSuccess || nb <= 0) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  nb = std::min(nb, kBlocksPerSM);
+  g_occ.emplace(k, nb);
+  return nb;
+}
+
+// grid of kernel k over `threads` grid-stride threads: at most one full wave
+// of resident blocks (a second partial wave would run its blocks' equal
+// shares of rows at a fraction of the occupancy)
+int fit(const void* k, int64_t threads) {
+  const int64_t b = (threads + kSB - 1) / kSB;
+  const int64_t wave = int64_t(stream_grid_cap() / kBlocksPerSM) * resident_blocks(k);
+  return int(std::max<int64_t>(1, std::min(b, wave)));
+}
 
 // add a WHILE node after the current capture frontier of `cap` and return its
 // body graph; the capture continues after the node
@@ -850,8 +940,10 @@ struct Plan {
   VcOne<T> vone{};
   VcMany<T> vmany{};
   const BatchSolve* bs = nullptr;
-  int rows_grid = 1, nlev = 0, coarse_grid = 1;
-  int gA[kMaxAmgLevels] = {}, gR[kMaxAmgLevels] = {}, gP[kMaxAmgLevels] = {};
+  int nlev = 0;
+  // grid-stride threads of each kernel family (single system)
+  int64_t rows = 1, tcoarse = 1;
+  int64_t tA[kMaxAmgLevels] = {}, tR[kMaxAmgLevels] = {}, tP[kMaxAmgLevels] = {};
   bool amg = false;
   Many mk(const int* blk) const {
     Many m = many_base;
@@ -870,12 +962,12 @@ struct Plan {
 #define ROWS_LAUNCH_T(KNAME, stream)                                                                   \
   do {                                                                                                 \
     if (P.many) KNAME<T, Many><<<P.bs->total_rows_blocks, kSB, 0, stream>>>(P.mk(P.bs->blk_rows));      \
-    else KNAME<T, One><<<P.rows_grid, kSB, 0, stream>>>(P.one);                                        \
+    else KNAME<T, One><<<fit((const void*)KNAME<T, One>, P.rows), kSB, 0, stream>>>(P.one);            \
   } while (0)
 #define ROWS_LAUNCH_S(KNAME, stream)                                                                   \
   do {                                                                                                 \
     if (P.many) KNAME<Many><<<P.bs->total_rows_blocks, kSB, 0, stream>>>(P.mk(P.bs->blk_rows));         \
-    else KNAME<One><<<P.rows_grid, kSB, 0, stream>>>(P.one);                                           \
+    else KNAME<One><<<fit((const void*)KNAME<One>, P.rows), kSB, 0, stream>>>(P.one);                  \
   } while (0)
 
 template <class T>
@@ -883,30 +975,53 @@ void enqueue_vcycle(const Plan<T>& P, cudaStream_t s) {
   for (int l = 0; l < P.nlev; ++l) {
     if (P.many) {
       const Many m = P.mk(P.bs->blk_rows);
-      st_vc_res_kernel<T, VcMany<T>, Many><<<P.bs->total_A[l], kSB, 0, s>>>(P.vmk(P.bs->blk_A[l]), m, l);
-      st_vc_restrict_kernel<T, VcMany<T>, Many><<<P.bs->total_R[l], kSB, 0, s>>>(P.vmk(P.bs->blk_R[l]), m, l);
+      if (l == 0)
+        st_vc_res_kernel<T, VcMany<T>, Many, true><<<P.bs->total_A[l], kSB, 0, s>>>(P.vmk(P.bs->blk_A[l]), m, l);
+      else
+        st_vc_res_kernel<T, VcMany<T>, Many, false><<<P.bs->total_A[l], kSB, 0, s>>>(P.vmk(P.bs->blk_A[l]), m, l);
+      st_vc_restrict_kernel<T, VcMany<T>, Many, kRowsAll><<<P.bs->total_R[l], kSB, 0, s>>>(P.vmk(P.bs->blk_R[l]), m,
+                                                                                         l);
     } else {
-      st_vc_res_kernel<T, VcOne<T>, One><<<P.gA[l], kSB, 0, s>>>(P.vone, P.one, l);
-      st_vc_restrict_kernel<T, VcOne<T>, One><<<P.gR[l], kSB, 0, s>>>(P.vone, P.one, l);
+      if (l == 0)
+        st_vc_res_kernel<T, VcOne<T>, One, true>
+            <<<fit((const void*)st_vc_res_kernel<T, VcOne<T>, One, true>, P.tA[l]), kSB, 0, s>>>(P.vone, P.one, l);
+      else
+        st_vc_res_kernel<T, VcOne<T>, One, false>
+            <<<fit((const void*)st_vc_res_kernel<T, VcOne<T>, One, false>, P.tA[l]), kSB, 0, s>>>(P.vone, P.one, l);
+      if (P.vone.H.L[l].R.lpr > 32)
+        st_vc_restrict_kernel<T, VcOne<T>, One, kRowsAll>
+            <<<fit((const void*)st_vc_restrict_kernel<T, VcOne<T>, One, kRowsAll>, P.tR[l]), kSB, 0, s>>>(P.vone,
+                                                                                                   P.one, l);
+      else
+        st_vc_restrict_kernel<T, VcOne<T>, One, kRowsAll & ~kRowsCsrBlock>
+            <<<fit((const void*)st_vc_restrict_kernel<T, VcOne<T>, One, kRowsAll & ~kRowsCsrBlock>, P.tR[l]), kSB, 0,
+               s>>>(P.vone, P.one, l);
     }
   }
   if (P.many)
     st_vc_coarse_kernel<T, VcMany<T>, Many><<<P.bs->total_coarse, kSB, 0, s>>>(P.vmk(P.bs->blk_coarse),
                                                                                 P.mk(P.bs->blk_rows));
   else
-    st_vc_coarse_kernel<T, VcOne<T>, One><<<P.coarse_grid, kSB, 0, s>>>(P.vone, P.one);
+    st_vc_coarse_kernel<T, VcOne<T>, One><<<fit((const void*)st_vc_coarse_kernel<T, VcOne<T>, One>, P.tcoarse), kSB,
+                                            0, s>>>(P.vone, P.one);
   for (int l = P.nlev - 1; l >= 0; --l) {
     if (P.many) {
       const Many m = P.mk(P.bs->blk_rows);
       st_vc_prolong_kernel<T, VcMany<T>, Many><<<P.bs->total_P[l], kSB, 0, s>>>(P.vmk(P.bs->blk_P[l]), m, l);
       if (l == 0)
-        st_vc_post_kernel<T, VcMany<T>, Many><<<P.bs->total_post0_blocks, kSB, 0, s>>>(
+        st_vc_post_kernel<T, VcMany<T>, Many, true><<<P.bs->total_post0_blocks, kSB, 0, s>>>(
             P.vmk(P.bs->blk_post0), P.mk(P.bs->blk_post0), 0);
       else
-        st_vc_post_kernel<T, VcMany<T>, Many><<<P.bs->total_A[l], kSB, 0, s>>>(P.vmk(P.bs->blk_A[l]), m, l);
+        st_vc_post_kernel<T, VcMany<T>, Many, false><<<P.bs->total_A[l], kSB, 0, s>>>(P.vmk(P.bs->blk_A[l]), m, l);
     } else {
-      st_vc_prolong_kernel<T, VcOne<T>, One><<<P.gP[l], kSB, 0, s>>>(P.vone, P.one, l);
-      st_vc_post_kernel<T, VcOne<T>, One><<<l == 0 ? P.rows_grid : P.gA[l], kSB, 0, s>>>(P.vone, P.one, l);
+      st_vc_prolong_kernel<T, VcOne<T>, One><<<fit((const void*)st_vc_prolong_kernel<T, VcOne<T>, One>, P.tP[l]),
+                                               kSB, 0, s>>>(P.vone, P.one, l);
+      if (l == 0)
+        st_vc_post_kernel<T, VcOne<T>, One, true>
+            <<<fit((const void*)st_vc_post_kernel<T, VcOne<T>, One, true>, P.rows), kSB, 0, s>>>(P.vone, P.one, l);
+      else
+        st_vc_post_kernel<T, VcOne<T>, One, false>
+            <<<fit((const void*)st_vc_post_kernel<T, VcOne<T>, One, false>, P.tA[l]), kSB, 0, s>>>(P.vone, P.one, l);
     }
   }
 }
@@ -1032,18 +1147,18 @@ Plan<T> one_plan(const StreamLaunch& a, const AmgDevT<T>* M) {
     P.vone.H = *M;
     P.nlev = M->nlev;
     for (int l = 0; l < P.nlev; ++l) {
-      P.gA[l] = level_grid(M->L[l].A.rp, M->L[l].A.n);
-      P.gR[l] = level_grid(M->L[l].R.rp, M->L[l].R.n);
-      P.gP[l] = level_grid(M->L[l].P.rp, M->L[l].P.n);
+      P.tA[l] = level_threads(M->L[l].A);
+      P.tR[l] = level_threads(M->L[l].R);
+      P.tP[l] = level_threads(M->L[l].P);
     }
-    P.coarse_grid = grid_for(int64_t(std::max(1, M->nc)) * 32);
+    P.tcoarse = int64_t(std::max(1, M->nc)) * 32;
     P.one.a.h0_invd = M->L[0].invd;
     P.one.a.h0_x = M->L[0].x;
     P.one.a.h0_omega = double(M->L[0].omega);
   } else {
     P.one.a.use_amg = 0;
   }
-  P.rows_grid = a.grid;
+  P.rows = a.n;
   return P;
 }
 
@@ -1064,6 +1179,32 @@ int stream_grid_cap() {
 }
 
 int stream_grid(int64_t rows) { return grid_for(rows); }
+
+namespace {
+template <class T>
+void prepare_family() {
+  for (const void* k : {(const void*)st_rhs_kernel<T, One>, (const void*)st_outer_kernel<T, One>,
+                        (const void*)st_inner_init_kernel<T, One>, (const void*)st_pq_kernel<T, One>,
+                        (const void*)st_update_kernel<T, One>, (const void*)st_xupdate_kernel<T, One>,
+                        (const void*)st_vc_res_kernel<T, VcOne<T>, One, true>,
+                        (const void*)st_vc_res_kernel<T, VcOne<T>, One, false>,
+                        (const void*)st_vc_restrict_kernel<T, VcOne<T>, One, kRowsAll>,
+                        (const void*)st_vc_restrict_kernel<T, VcOne<T>, One, kRowsAll & ~kRowsCsrBlock>,
+                        (const void*)st_vc_coarse_kernel<T, VcOne<T>, One>,
+                        (const void*)st_vc_prolong_kernel<T, VcOne<T>, One>,
+                        (const void*)st_vc_post_kernel<T, VcOne<T>, One, true>,
+                        (const void*)st_vc_post_kernel<T, VcOne<T>, One, false>})
+    resident_blocks(k);
+}
+}  // namespace
+
+void stream_prepare() {
+  stream_grid_cap();
+  prepare_family<float>();
+  prepare_family<double>();
+  resident_blocks((const void*)st_shift_kernel<One>);
+  resident_blocks((const void*)st_finish_kernel<One>);
+}
 
 cudaError_t stream_solve(const StreamLaunch& a, int f32, const AmgDevF* M32, const AmgDev* M64, cudaStream_t st,
                          const cudaStream_t* side) {
