@@ -146,6 +146,16 @@ typedef struct {
                             in the Krylov and AMG level-0 products; -1: they do not (the plain
                             SELL-32 layout only); BD_ERR_ARG otherwise.  Both give the same sums
                             in the same order */
+  int csr_lanes;         /* streaming solves, AMG levels stored as CSR: threads per row.  0
+                            (default): a quarter of the level's mean row length rounded up to a
+                            power of two in [4, 32], or 256 (a block per row) for rows of 256
+                            entries and more on average; 4, 8, 16, 32 or 256 force that width on
+                            every CSR level (tuning and testing); BD_ERR_ARG otherwise */
+  int wide_sell;         /* streaming handles, AMG levels with rows longer than 32 entries: 0
+                            (default) SELL-32 (thread per row) when padding stores at most 1.5x
+                            the entries and the level has at least 2^17 rows averaging at most 96
+                            entries, else CSR; 1: SELL-32 whenever the padding allows; -1:
+                            always CSR; BD_ERR_ARG otherwise */
 } bd_opts_t;
 
 typedef struct bd_state bd_state_t;
@@ -392,6 +402,15 @@ int bd_operator_csr(const bd_state_t* s, int which, int64_t* nnz, int32_t* rowpt
  * Returns the iteration count in *iters when not NULL. */
 int bd_solve_elliptic(bd_state_t* s, const double* v, const double* u_guess, double* u,
                       int* iters);
+
+/* Shape of level `level` of the elliptic AMG hierarchy (smoothed
+ * aggregation, the preconditioner class of Sec. 3.3.2; level 0's A is A_ie
+ * itself).  out[9] (host) receives rows, stored entries and storage form of
+ * A_l, R_l and P_l in that order; form 0: SELL-32 with rows of at most 32
+ * entries, -1: SELL-32 with longer rows (streaming handles), k > 0: CSR read
+ * by k threads per row in the streaming kernels.  BD_ERR_ARG when the
+ * handle has no such level (Jacobi handles have none).  No device work. */
+int bd_amg_level(const bd_state_t* s, int level, int64_t* out);
 
 #ifdef __cplusplus
 }

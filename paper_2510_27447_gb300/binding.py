@@ -27,7 +27,7 @@ EXPORTS = ["bd_default_options", "bd_create", "bd_add_stimulus", "bd_set_initial
            "bd_ionic_eval", "bd_ionic_pattern", "bd_rest_state", "bd_operator_csr",
            "bd_solve_elliptic", "bd_profile_steps", "bd_solve_elliptic_noalloc", "bd_query",
            "bd_step_adaptive", "bd_get_time", "bd_num_tissue_nodes", "bd_step_decoupled",
-           "bd_selftest_wait_timeout", "bd_struct_sizes"]
+           "bd_selftest_wait_timeout", "bd_struct_sizes", "bd_amg_level"]
 
 
 class LibraryMissing(RuntimeError):
@@ -64,7 +64,7 @@ class Opts(C.Structure):
                 ("cg_grid", C.c_int),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("stream", C.c_void_p), ("cg_cluster", C.c_int), ("solver_tier", C.c_int),
-                ("streaming", C.c_int), ("vec4", C.c_int)]
+                ("streaming", C.c_int), ("vec4", C.c_int), ("csr_lanes", C.c_int), ("wide_sell", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -132,6 +132,7 @@ def lib():
         "bd_solve_elliptic": (C.c_int, [C.c_void_p, dp, dp, dp, P(C.c_int)]),
         "bd_profile_steps": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_int, P(Profile)]),
         "bd_solve_elliptic_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, P(C.c_int)]),
+        "bd_amg_level": (C.c_int, [C.c_void_p, C.c_int, P(C.c_int64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -317,6 +318,17 @@ class Simulation:
     def set_state(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))
         _check(lib().bd_set_state(self.h, buf, len(blob)), self.h)
+
+    def amg_levels(self) -> list:
+        """Per AMG level: {A, R, P: (rows, stored entries, form)}; form 0 SELL-32,
+        -1 wide SELL-32, k > 0 CSR with k threads per row (bd_amg_level)."""
+        out, buf = [], (C.c_int64 * 9)()
+        L = lib()
+        for level in range(self.stats()["amg_levels"]):
+            _check(L.bd_amg_level(self.h, level, buf), self.h)
+            v = list(buf)
+            out.append({"A": tuple(v[0:3]), "R": tuple(v[3:6]), "P": tuple(v[6:9])})
+        return out
 
     def stats(self) -> dict:
         s = Stats()

@@ -385,12 +385,30 @@ int amg_build(const HCsr& A0, const AmgParams& prm, AmgHost* out, std::string* e
 
 namespace bd {
 
-SellHost sell_from_csr(const HCsr& A) {
+SellHost sell_from_csr(const HCsr& A, int wide) {
   SellHost S;
   S.n = A.n;
   int64_t maxw = 0;
   for (int64_t i = 0; i < A.n; ++i) maxw = std::max(maxw, A.rp[i + 1] - A.rp[i]);
-  if (maxw > 32) {
+  bool sell_wide = false;
+  if (maxw > 32 && wide > 0) {
+    // rows longer than 32 stay SELL-32 (thread per row, loads coalesced
+    // across the slice) when padding every slice to its longest row stores
+    // at most half again the entries and (wide == 1) the operator has many
+    // moderate rows -- measured on the 3-D slab: R_0 (210k rows of 49
+    // entries) and A_1 (210k rows of 74) run 1.4-1.8x faster than as CSR,
+    // while operators of 14k rows of 230 entries run 5-25x slower (too few
+    // threads, long chains)
+    int64_t padded = 0;
+    for (int64_t sl = 0; sl * 32 < A.n; ++sl) {
+      int64_t w = 0;
+      for (int64_t i = sl * 32; i < std::min<int64_t>(A.n, sl * 32 + 32); ++i) w = std::max(w, A.rp[i + 1] - A.rp[i]);
+      padded += 32 * w;
+    }
+    const int64_t nnz = A.rp[A.n];
+    sell_wide = 2 * padded <= 3 * nnz && (wide == 2 || (nnz <= 96 * A.n && A.n >= (int64_t(1) << 17)));
+  }
+  if (maxw > 32 && !sell_wide) {
     // long rows (coarse operators, restrictions in 3-D): CSR, one warp per row
     S.rp = A.rp;
     S.col.assign(A.ci.begin(), A.ci.end());
@@ -419,7 +437,7 @@ SellHost sell_from_csr(const HCsr& A) {
       S.val[base + 32 * k] = A.v[A.rp[i] + k];
     }
   }
-  S.wmax = maxw <= 8 ? 8 : maxw <= 16 ? 16 : 32;
+  S.wmax = maxw <= 8 ? 8 : maxw <= 16 ? 16 : maxw <= 32 ? 32 : 0;   // 0: wide (streaming kernels only)
   return S;
 }
 

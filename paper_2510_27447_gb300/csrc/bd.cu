@@ -102,6 +102,7 @@ struct bd_state {
   int mixed_amg_grid = 1;                  // grid of the mixed AMG kernels (differs in tier 2)
   int amg_grid = 1;
   int amg_levels = 0;
+  std::vector<int64_t> amg_shape;   // per level: rows, entries, form of A, R, P (bd_amg_level)
   double amg_cycle_bytes[2] = {0.0, 0.0};   // algorithmic bytes of one V-cycle's smoothed levels (FP64, FP32)
   double amg_cycle_opbytes[2] = {0.0, 0.0}; // ... of which operator values and indices
   double amg_coarse_bytes[2] = {0.0, 0.0};  // dense coarsest-level solve of one cycle
@@ -662,13 +663,22 @@ int setup_amg(bd_state* s, const HostOps& H) {
     if (d && cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) return nullptr;
     return d;
   };
+  s->amg_shape.assign(AH.lev.size() * 9, 0);
+  // rows, entries and storage form (0 SELL-32, -1 wide SELL-32, k > 0 CSR
+  // with k lanes per row) of one operator of the hierarchy
+  auto shape = [&](size_t l, int which, const HCsr& M, const SellDev& d) {
+    int64_t* o = s->amg_shape.data() + l * 9 + 3 * which;
+    o[0] = M.n;
+    o[1] = int64_t(M.ci.size());
+    o[2] = d.rp ? d.lpr : (d.wmax == 0 ? -1 : 0);
+  };
   auto sell_dev = [&](const HCsr& M, SellDev* out) {
-    const SellHost S = sell_from_csr(M);
+    const SellHost S = sell_from_csr(M, s->streaming ? s->opts.wide_sell + 1 : 0);
     out->n = int(S.n);
     out->wmax = S.wmax;
     const bool csr = !S.rp.empty();
     out->rp = csr ? static_cast<const int64_t*>(upload(S.rp.data(), S.rp.size() * 8)) : nullptr;
-    out->lpr = csr ? csr_lanes(S.rp.back(), S.n) : 0;
+    out->lpr = csr ? (s->opts.csr_lanes > 0 ? s->opts.csr_lanes : csr_lanes(S.rp.back(), S.n)) : 0;
     out->sptr = csr ? nullptr : static_cast<const int64_t*>(upload(S.sptr.data(), S.sptr.size() * 8));
     out->sw = csr ? nullptr : static_cast<const int*>(upload(S.sw.data(), S.sw.size() * 4));
     out->col = static_cast<const int*>(upload(S.col.data(), S.col.size() * 4));
@@ -689,6 +699,11 @@ int setup_amg(bd_state* s, const HostOps& H) {
       ok = sell_dev(Lh.A, &Ld.A);
     }
     ok = ok && sell_dev(Lh.P, &Ld.P) && sell_dev(Lh.R, &Ld.R);
+    if (ok) {
+      shape(size_t(l), 0, Lh.A, Ld.A);
+      shape(size_t(l), 1, Lh.R, Ld.R);
+      shape(size_t(l), 2, Lh.P, Ld.P);
+    }
     Ld.invd = static_cast<const double*>(upload(Lh.invdiag.data(), Lh.invdiag.size() * 8));
     Ld.omega = Lh.omega;
     const int64_t n = Lh.A.n;
@@ -710,13 +725,13 @@ int setup_amg(bd_state* s, const HostOps& H) {
     return fail(s, BD_ERR_OOM, "AMG upload failed");
   if (s->precision == BD_MIXED) {
     auto sell_devf = [&](const HCsr& Mh, SellDevT<float>* out) {
-      const SellHost S = sell_from_csr(Mh);
+      const SellHost S = sell_from_csr(Mh, s->streaming ? s->opts.wide_sell + 1 : 0);
       std::vector<float> fv(S.val.begin(), S.val.end());
       out->n = int(S.n);
       out->wmax = S.wmax;
       const bool csr = !S.rp.empty();
       out->rp = csr ? static_cast<const int64_t*>(upload(S.rp.data(), S.rp.size() * 8)) : nullptr;
-      out->lpr = csr ? csr_lanes(S.rp.back(), S.n) : 0;
+      out->lpr = csr ? (s->opts.csr_lanes > 0 ? s->opts.csr_lanes : csr_lanes(S.rp.back(), S.n)) : 0;
       out->sptr = csr ? nullptr : static_cast<const int64_t*>(upload(S.sptr.data(), S.sptr.size() * 8));
       out->sw = csr ? nullptr : static_cast<const int*>(upload(S.sw.data(), S.sw.size() * 4));
       out->col = static_cast<const int*>(upload(S.col.data(), S.col.size() * 4));
@@ -1853,6 +1868,15 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     delete s;
     return fail(nullptr, BD_ERR_ARG, "vec4 must be 0 or -1");
   }
+  {
+    const int cl = s->opts.csr_lanes;
+    if (!(cl == 0 || cl == 4 || cl == 8 || cl == 16 || cl == 32 || cl == kCsrBlockLanes) ||
+        s->opts.wide_sell < -1 || s->opts.wide_sell > 1) {
+      release(s);
+      delete s;
+      return fail(nullptr, BD_ERR_ARG, "csr_lanes must be 0, 4, 8, 16, 32 or 256 and wide_sell -1, 0 or 1");
+    }
+  }
   s->vec4 = s->streaming && s->precision == BD_MIXED && s->opts.vec4 == 0;
   std::vector<int64_t> h_sptr4;
   std::vector<int> e_col4;
@@ -2348,6 +2372,14 @@ int bd_struct_sizes(size_t* mesh, size_t* cond, size_t* opts, size_t* stats) {
   if (cond) *cond = sizeof(bd_cond_t);
   if (opts) *opts = sizeof(bd_opts_t);
   if (stats) *stats = sizeof(bd_stats_t);
+  return BD_OK;
+}
+
+int bd_amg_level(const bd_state_t* s, int level, int64_t* out) {
+  if (!s || !out) return fail(nullptr, BD_ERR_ARG, "NULL argument");
+  if (level < 0 || size_t(level) * 9 >= s->amg_shape.size())
+    return fail(const_cast<bd_state_t*>(s), BD_ERR_ARG, "no AMG level %d", level);
+  std::copy(s->amg_shape.begin() + size_t(level) * 9, s->amg_shape.begin() + size_t(level) * 9 + 9, out);
   return BD_OK;
 }
 

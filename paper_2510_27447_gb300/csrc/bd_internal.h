@@ -288,10 +288,15 @@ struct SellHost {
   std::vector<int> sw;
   std::vector<int> col;
   std::vector<double> val;
-  int wmax = 0;                    // 8, 16 or 32 (SELL, thread per row)
+  int wmax = 0;                    // 8, 16 or 32 (SELL, thread per row); 0 with rp empty: wide SELL
   std::vector<int64_t> rp;         // non-empty: CSR layout, one warp per row (rows longer than 32)
 };
-SellHost sell_from_csr(const HCsr& A);
+// SELL-32 for rows of at most 32 entries, else CSR.  For operators only the
+// streaming kernels read, wide > 0 also allows SELL-32 for longer rows when
+// padding stores at most 1.5x the entries (SellHost.wmax = 0 then): wide = 1
+// only for operators of at least 2^17 rows averaging at most 96 entries,
+// wide = 2 whenever the padding allows
+SellHost sell_from_csr(const HCsr& A, int wide = 0);
 
 constexpr int kMaxAmgLevels = 10;
 template <class T>

@@ -203,3 +203,38 @@ def test_vector_load_layout_gives_the_same_solves():
     (v0, u0, _), (v1, u1, _) = out[0], out[-1]
     assert rel(v0, v1) < 1e-6 and rel(u0, u1) < 1e-6
     assert rel(v0, Xo[0]) < 1e-3 and rel(u0, uo) < 1e-3
+
+
+@pytest.mark.parametrize("prec", [binding.FP64, binding.MIXED])
+@pytest.mark.parametrize("form", [(0, 0), (1, 0), (-1, 4), (-1, 16), (-1, 32), (-1, 256)])
+def test_every_coarse_level_row_form_solves_the_elliptic_system(prec, form):
+    """The AMG levels of a 3-D slab have rows longer than 32 entries: stored
+    as SELL-32 (wide_sell = 1, thread per row), by the size rule (0), or as
+    CSR read by 4 to 32 lanes per row or a whole block per row (csr_lanes
+    forced on every CSR level).  Every form gives the oracle's solution of
+    Eq. (3.15)."""
+    wide, lanes = form
+    w = _slab()
+    v = _bump(w.xyz, w.n_tissue)
+    u_ref = oracle_problem(w).elliptic(v)
+    sim = gpu_sim(w, precision=prec, cg_tol_e=1e-11, elliptic_precond=1, streaming=1, wide_sell=wide,
+                  csr_lanes=lanes)
+    st = sim.stats()
+    assert st["amg_levels"] >= 1
+    levels = sim.amg_levels()
+    forms = [L[k][2] for L in levels for k in "ARP"]
+    for lv, L in enumerate(levels):
+        assert L["P"][0] == L["A"][0]                                   # P_l: fine rows
+        nxt = levels[lv + 1]["A"][0] if lv + 1 < len(levels) else st["amg_coarse_rows"]
+        assert L["R"][0] == nxt                                         # R_l: coarse rows
+        assert min(L[k][1] for k in "ARP") > 0
+    if wide == -1:
+        assert -1 not in forms and any(f > 0 for f in forms)            # long rows are CSR here
+    if wide == 1:
+        assert -1 in forms
+    if lanes:
+        assert all(f == lanes for f in forms if f > 0)
+    u, it = sim.solve_elliptic(v)
+    sim.close()
+    assert u[w.pin_node] == 0.0 and it > 0
+    assert rel(u, u_ref) < 1e-8, (rel(u, u_ref), it)
