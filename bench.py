@@ -411,7 +411,7 @@ def bath_leg(args, torch, stream, flush) -> dict:
     return out
 
 
-def lv_leg(args, torch, stream, flush) -> dict:
+def lv_leg(args, torch, stream, flush, peaks) -> dict:
     """The 3-D bidomain-bath configuration: TP06 in a truncated prolate LV
     shell inside a box bath (jittered Kuhn lattice, h = args.lv_h cm in the
     shell's bounding box, coarser bath margins), dt = 0.025 ms, 3 Lobatto
@@ -443,6 +443,12 @@ def lv_leg(args, torch, stream, flush) -> dict:
                      "cg_iters_p": per_solve(st0, st1, "p"), "kernel_share": shares(prof),
                      "elliptic": solver_roofline(prof, "pcg_elliptic"),
                      "parabolic": solver_roofline(prof, "pcg_parabolic")}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    m = out["mixed"]["elliptic"]
+    out["roofline"] = {"kernel": "pcg_elliptic (mixed)", "bound": "hbm", "achieved": m["achieved_gbs"],
+                       "peak": hbm, "unit": "GB/s", "frac": round(m["achieved_gbs"] / hbm, 4), "traffic": None,
+                       "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                       "parabolic_frac": round(out["mixed"]["parabolic"]["achieved_gbs"] / hbm, 4)}
     out["steps"] = args.lv_steps
     return out
 
@@ -508,8 +514,10 @@ def serve_leg(args) -> dict:
     request recipe of the 512-request workload: sides 33/65/129/257,
     LR91/TP06 50/50, jittered conductivities, strip and S2 positions), each
     simulated for args.serve_ms ms at dt = 0.02 ms, mixed precision:
-      batched     resident requests advance together through bd_batch_step,
-                  joining at chunk boundaries (16 slots);
+      batched     resident requests below args.serve_solo_nodes nodes advance
+                  together through bd_batch_step, one batch per (model, mesh
+                  size), joining at chunk boundaries; larger ones run alone on
+                  their own streams (16 slots in all);
       streams     each resident request on its own stream (8 slots);
       closed      the batched form with 16 clients keeping one request each
                   outstanding;
@@ -534,15 +542,17 @@ def serve_leg(args) -> dict:
                 "offered_node_steps_per_s": round(sm["offered_node_steps_per_s"], 1),
                 "served_over_offered": round(sm["served_over_offered"], 4), "wall_s": round(wall, 2)}
     mixed = lambda: binding.default_options(precision=binding.MIXED)          # noqa: E731
+    out["solo_nodes"] = args.serve_solo_nodes
+    solo = args.serve_solo_nodes if args.serve_solo_nodes > 0 else None
     for name, batched, slots in (("batched_mixed", True, 16), ("streams_mixed", False, 8)):
-        ex = S.GpuExecutor(mixed, dt=0.02)
+        ex = S.GpuExecutor(mixed, dt=0.02, solo_nodes=solo)
         t0 = time.perf_counter()
         done = S.Server(ex, max_slots=slots, hbm_budget=64 << 30, chunk_steps=25, batched=batched).run(jobs())
         wall = time.perf_counter() - t0
         ex.close()
         out[name] = record(S.summarize(done), wall)
         out[name]["slots"] = slots
-    ex = S.GpuExecutor(mixed, dt=0.02)
+    ex = S.GpuExecutor(mixed, dt=0.02, solo_nodes=solo)
     t0 = time.perf_counter()
     done = S.Server(ex, max_slots=16, hbm_budget=64 << 30, chunk_steps=25, batched=True).run_closed(jobs(), 16)
     wall = time.perf_counter() - t0
@@ -665,7 +675,7 @@ def run_ours(args) -> None:
     lv = None
     if args.lv_steps > 0:
         try:
-            lv = lv_leg(args, torch, stream, flush)
+            lv = lv_leg(args, torch, stream, flush, peaks)
         except Exception as e:  # noqa: BLE001
             lv = {"error": str(e)[:300]}
     batch = None
@@ -850,8 +860,10 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batched-execution leg")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-ms", type=float, default=10.0)
-    ap.add_argument("--lv-steps", type=int, default=0,
-                    help="timed steps of the 3-D LV-shell-in-bath leg (0: skip; setup takes minutes)")
+    ap.add_argument("--serve-solo-nodes", type=int, default=50000,
+                    help="serve leg, batched form: requests of at least this many nodes run alone (0: batch all)")
+    ap.add_argument("--lv-steps", type=int, default=3,
+                    help="timed steps of the 3-D LV-shell-in-bath leg (0: skip; mesh and set-up take ~1 min)")
     ap.add_argument("--lv-h", type=float, default=0.04, help="lattice spacing of the LV leg (cm)")
     ap.add_argument("--bath-steps", type=int, default=10,
                     help="timed steps of the 801^2 bidomain-bath leg (0: skip)")

@@ -83,7 +83,7 @@ class Executor:
     def prepare(self, job: Job) -> Any: ...                   # future-like: done(), result() -> handle
     def advance(self, h: Any, n_steps: int) -> None: ...      # per-request form
     def ready(self, h: Any) -> bool: ...
-    def group_key(self, job: Job) -> Any: ...                 # batched form: jobs batched together
+    def group_key(self, job: Job) -> Any: ...                 # batched form: jobs batched together (None: alone)
     def advance_group(self, hs: Sequence[Any], n_steps: int) -> None: ...
     def group_ready(self, hs: Sequence[Any]) -> bool: ...
     def finish(self, h: Any) -> Any: ...
@@ -152,7 +152,8 @@ class Server:
                          "admitted": st["admitted"]}
                     del starting[rid]
                     active[rid] = a
-                    if not self.batched:
+                    a["solo"] = not self.batched or self.ex.group_key(a["job"]) is None
+                    if a["solo"]:
                         n = min(self.chunk, a["job"].n_steps)
                         self.ex.advance(a["h"], n)
                         a["steps"] = n
@@ -183,7 +184,7 @@ class Server:
                 idle_members: Dict[Any, List[int]] = {}
                 busy = {rid for g in groups.values() for rid in g["rids"]}
                 for rid in sorted(active):
-                    if rid not in busy:
+                    if rid not in busy and not active[rid]["solo"]:
                         idle_members.setdefault(self.ex.group_key(active[rid]["job"]), []).append(rid)
                 for key, rids in idle_members.items():
                     if key in groups:
@@ -193,19 +194,20 @@ class Server:
                     self.ex.advance_group(hs, n)
                     groups[key] = {"rids": rids, "hs": hs, "n": n}
                     progressed = True
-            else:
-                for rid in list(active):
-                    a = active[rid]
-                    if a["steps"] == 0 or not self.ex.ready(a["h"]):
-                        continue
-                    progressed = True
-                    j = a["job"]
-                    if a["steps"] >= j.n_steps:
-                        complete(rid)
-                    else:
-                        n = min(self.chunk, j.n_steps - a["steps"])
-                        self.ex.advance(a["h"], n)
-                        a["steps"] += n
+            # requests served alone (every one in the per-request form; in the
+            # batched form those whose group key is None)
+            for rid in list(active):
+                a = active[rid]
+                if not a["solo"] or not self.ex.ready(a["h"]):
+                    continue
+                progressed = True
+                j = a["job"]
+                if a["steps"] >= j.n_steps:
+                    complete(rid)
+                else:
+                    n = min(self.chunk, j.n_steps - a["steps"])
+                    self.ex.advance(a["h"], n)
+                    a["steps"] += n
             if not progressed:
                 if not active and not starting and not waiting and qi < total and clients is None:
                     self.ex.wait_until(queue[qi].arrival)
@@ -257,16 +259,20 @@ class GpuExecutor(Executor):
 
     payload of a Job is a workloads.Workload; ``options`` builds bd_opts_t.
     In the batched form a group (same membrane model and mesh size) advances
-    a chunk at a time with bd_batch_step on its first handle's stream."""
+    a chunk at a time with bd_batch_step on its first handle's stream;
+    meshes of at least ``solo_nodes`` nodes (None: no limit) are served
+    alone on their own streams (one request fills the GPU's persistent
+    solver kernels; batching it would only add graph captures)."""
 
     def __init__(self, options: Callable[[], Any], dt: float, n_sdc_nodes: int = 3, n_sweeps: int = 2,
-                 workers: int = 2):
+                 workers: int = 2, solo_nodes: Optional[int] = None):
         from . import binding
         self.b = binding
         self.options = options
         self.dt = dt
         self.M = n_sdc_nodes
         self.K = n_sweeps
+        self.solo_nodes = solo_nodes
         self.t0 = time.perf_counter()
         self.pool = cf.ThreadPoolExecutor(max_workers=workers)
 
@@ -288,6 +294,8 @@ class GpuExecutor(Executor):
         return h.ready()
 
     def group_key(self, job: Job):
+        if self.solo_nodes is not None and job.n_nodes >= self.solo_nodes:
+            return None
         return (job.payload.model, job.n_nodes)
 
     def advance_group(self, hs, n_steps: int) -> None:
@@ -319,10 +327,14 @@ class VirtualExecutor(Executor):
     """Deterministic stand-in with a virtual clock: a request advances at
     ``rate`` node-steps/s shared equally among the active requests
     (processor sharing), its footprint is ``bytes_per_node`` per node, and
-    its handle takes ``setup`` seconds of a worker to build."""
+    its handle takes ``setup`` seconds of a worker to build; requests of at
+    least ``solo_nodes`` nodes are not batched (None: every one is)."""
 
-    def __init__(self, rate: float = 1e9, bytes_per_node: int = 2000, quantum: float = 1e-3, setup: float = 0.0):
+    def __init__(self, rate: float = 1e9, bytes_per_node: int = 2000, quantum: float = 1e-3, setup: float = 0.0,
+                 solo_nodes: Optional[int] = None):
         self.t = 0.0
+        self.solo_nodes = solo_nodes
+        self.grouped: List[List[int]] = []      # rids of every group chunk launched
         self.rate = rate
         self.bpn = bytes_per_node
         self.quantum = quantum
@@ -367,9 +379,12 @@ class VirtualExecutor(Executor):
         return self.live[h]["work"] <= 1e-9
 
     def group_key(self, job: Job):
+        if self.solo_nodes is not None and job.n_nodes >= self.solo_nodes:
+            return None
         return job.n_nodes
 
     def advance_group(self, hs, n_steps: int) -> None:
+        self.grouped.append([self.live[h]["job"].rid for h in hs])
         for h in hs:
             self.advance(h, n_steps)
 

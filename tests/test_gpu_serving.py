@@ -64,3 +64,29 @@ def test_batched_serving_gives_each_request_the_same_map_alone_and_in_the_mix(pr
         assert np.sum(~np.isnan(a)) > 0
         np.testing.assert_array_equal(np.isnan(c.result), np.isnan(a))
         np.testing.assert_array_equal(c.result[~np.isnan(a)], a[~np.isnan(a)])
+
+
+@pytest.mark.parametrize("precision", [binding.FP64, binding.MIXED])
+def test_hybrid_serving_gives_each_request_the_same_map_alone_and_in_the_mix(precision):
+    """Batched form with a size threshold: 33 x 33 requests advance in
+    batches, 65 x 65 ones alone on their own streams, in one server; every
+    request's map is the same as when it is served alone in the same form."""
+    opts = lambda: binding.default_options(precision=precision)       # noqa: E731
+    jobs = _jobs()
+    assert {j.n_nodes for j in jobs} == {33 ** 2, 65 ** 2}
+    alone = {}
+    for j in jobs:
+        ex = S.GpuExecutor(opts, dt=0.02, solo_nodes=2000)
+        d = S.Server(ex, max_slots=1, chunk_steps=20, batched=True).run(
+            [S.Job(j.rid, 0.0, j.n_nodes, j.n_steps, j.payload)])
+        alone[j.rid] = d[0].result
+        ex.close()
+    ex = S.GpuExecutor(opts, dt=0.02, solo_nodes=2000)
+    mixed = S.Server(ex, max_slots=6, chunk_steps=7, batched=True).run(jobs)
+    ex.close()
+    assert len(mixed) == len(jobs)
+    for c in mixed:
+        a = alone[c.rid]
+        assert np.sum(~np.isnan(a)) > 0
+        np.testing.assert_array_equal(np.isnan(c.result), np.isnan(a))
+        np.testing.assert_array_equal(c.result[~np.isnan(a)], a[~np.isnan(a)])

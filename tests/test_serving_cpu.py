@@ -112,3 +112,19 @@ def test_fifo_schedule_and_offered_load():
     assert sm["offered_node_steps_per_s"] == pytest.approx(3000 / 5.0)
     assert sm["node_steps_per_s"] == pytest.approx(3000 / 6.0)
     assert sm["served_over_offered"] == pytest.approx(5.0 / 6.0)
+
+
+def test_batched_form_serves_large_requests_alone():
+    """With a size threshold the batched server groups only the small
+    requests (by mesh size); requests at or above it advance alone, and every
+    request completes, including ones of zero steps."""
+    ex = S.VirtualExecutor(rate=1e8, solo_nodes=10000)
+    jobs = [S.Job(r, 0.001 * r, (1089, 4225, 16641)[r % 3], 0 if r == 7 else 40 + 10 * (r % 2)) for r in range(15)]
+    done = S.Server(ex, max_slots=8, hbm_budget=10**12, chunk_steps=20, batched=True).run(jobs)
+    assert sorted(c.rid for c in done) == list(range(15))
+    size = {j.rid: j.n_nodes for j in jobs}
+    grouped = {r for g in ex.grouped for r in g}
+    assert grouped == {j.rid for j in jobs if j.n_nodes < 10000}
+    for g in ex.grouped:
+        assert len({size[r] for r in g}) == 1                 # one mesh size per group
+    assert any(len(g) > 1 for g in ex.grouped)                # small requests share chunks
