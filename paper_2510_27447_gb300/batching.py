@@ -9,6 +9,11 @@ system iterates).  ``BatchRunner`` picks the packing by timing each candidate
 on the live handles for a few steps, once per shape class (model, precision
 and the multiset of mesh sizes), restoring every handle's state afterwards so
 the tuning leaves the simulations where they were.
+
+``OptionTuner`` chooses a single handle's layout and thread mapping the same
+way: the storage form of long-row AMG levels (SELL-32 or CSR), the threads
+per CSR row, the SELL-32/4 vector-load copy (streaming handles) or the
+solver block size (persistent handles), timed once per shape class.
 """
 from __future__ import annotations
 
@@ -88,3 +93,59 @@ class BatchRunner:
 
     def step(self, sims: Sequence[binding.Simulation], dt: float, M: int = 3, K: int = 2, steps: int = 1) -> None:
         self._run(sims, self.packing(sims, dt, M, K), dt, M, K, steps)
+
+
+# ---------------------------------------------------------------------------
+# Layout and thread-mapping options of one handle, chosen by timing
+# ---------------------------------------------------------------------------
+
+def option_candidates(streaming: bool, precision: int) -> Dict[str, Dict[str, int]]:
+    """Candidate option sets for one shape class.  Streaming handles (large
+    operators) choose how the AMG levels with long rows are stored and read
+    (SELL-32 by the size rule or CSR; lanes per CSR row from the mean row
+    length or forced to 16 / 32) and, in mixed precision, the SELL-32/4
+    vector-load copy; persistent handles choose the solver block size."""
+    if streaming:
+        c = {"auto": {}, "csr": {"wide_sell": -1}, "csr16": {"wide_sell": -1, "csr_lanes": 16},
+             "csr32": {"wide_sell": -1, "csr_lanes": 32}}
+        if precision == binding.MIXED:
+            c["sell32"] = {"vec4": -1}
+        return c
+    return {"auto": {}, "block256": {"cg_block": 256}, "block1024": {"cg_block": 1024}}
+
+
+class OptionTuner:
+    """Times option candidates on a workload (a handle per candidate, one
+    untimed step for the graph capture, then ``trial_steps`` timed steps from
+    the same initial state) once per shape class (model, precision, nodes,
+    stored entries, solver form) and caches the fastest."""
+
+    def __init__(self, trial_steps: int = 2):
+        self.trial_steps = trial_steps
+        self.cache: Dict[Tuple, str] = {}
+        self.timings: Dict[Tuple, Dict[str, float]] = {}
+
+    def tune(self, w, base: Dict[str, int], dt: float, M: int = 3, K: int = 2) -> Dict[str, int]:
+        """Options (base updated with the chosen candidate) for workload w."""
+        probe = binding.simulation_from_workload(w, binding.default_options(**base))
+        st = probe.stats()
+        nnz = probe.nnz()
+        probe.close()
+        prec = base.get("precision", binding.FP64)
+        key = (w.model, prec, int(w.n_nodes), int(nnz), int(st["streaming"]))
+        cands = option_candidates(bool(st["streaming"]), prec)
+        if key not in self.cache:
+            times = {}
+            for name, extra in cands.items():
+                sim = binding.simulation_from_workload(w, binding.default_options(**{**base, **extra}))
+                sim.step(dt, M, K)
+                sim.sync()
+                t0 = time.perf_counter()
+                for _ in range(self.trial_steps):
+                    sim.step(dt, M, K)
+                sim.sync()
+                times[name] = (time.perf_counter() - t0) / self.trial_steps
+                sim.close()
+            self.cache[key] = min(times, key=times.get)
+            self.timings[key] = times
+        return {**base, **cands[self.cache[key]]}

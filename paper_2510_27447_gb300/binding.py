@@ -351,6 +351,12 @@ class Simulation:
     def reset_stats(self):
         _check(lib().bd_reset_stats(self.h), self.h)
 
+    def nnz(self) -> int:
+        """Stored entries of the shared operator pattern (of A_ie)."""
+        n = C.c_int64(0)
+        _check(lib().bd_operator_csr(self.h, 1, C.byref(n), None, None, None), self.h)
+        return int(n.value)
+
     def operator(self, which: int):
         """(rowptr, col, val) of A_i (0), A_ie (1), M (2); M_L (3) as a vector."""
         nnz = C.c_int64(0)

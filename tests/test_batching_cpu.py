@@ -56,3 +56,18 @@ def test_shape_class_ignores_order():
     sims = _mix()
     assert B.shape_class(sims) == B.shape_class(list(reversed(sims)))
     assert B.shape_class(sims) != B.shape_class(sims[:-1])
+
+
+def test_option_candidates_cover_the_layout_and_thread_choices():
+    from paper_2510_27447_gb300 import binding
+    s_mixed = B.option_candidates(True, binding.MIXED)
+    s_fp64 = B.option_candidates(False, binding.FP64)
+    assert s_mixed["auto"] == {} and s_fp64["auto"] == {}
+    assert {"wide_sell": -1, "csr_lanes": 16} in s_mixed.values()
+    assert {"vec4": -1} in s_mixed.values()
+    assert "sell32" not in B.option_candidates(True, binding.FP64)     # no vector-load copy in FP64
+    assert {c.get("cg_block") for c in s_fp64.values()} == {None, 256, 1024}
+    for c in list(s_mixed.values()) + list(s_fp64.values()):
+        o = binding.default_options(**c)                                   # every key is an option
+        for k, v in c.items():
+            assert getattr(o, k) == v

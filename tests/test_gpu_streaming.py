@@ -238,3 +238,30 @@ def test_every_coarse_level_row_form_solves_the_elliptic_system(prec, form):
     sim.close()
     assert u[w.pin_node] == 0.0 and it > 0
     assert rel(u, u_ref) < 1e-8, (rel(u, u_ref), it)
+
+
+def test_option_tuner_times_every_candidate_and_keeps_the_results():
+    """The option tuner times each layout / thread-mapping candidate once per
+    shape class and returns options whose steps agree with the default ones
+    (the candidates change only summation order)."""
+    from paper_2510_27447_gb300.batching import OptionTuner, option_candidates
+    w = _slab()
+    X0 = rest_X(w)
+    w.initial = X0
+    base = {"precision": binding.FP64, "streaming": 1, "pin_node": w.pin_node, "cg_tol_e": 1e-12,
+            "cg_tol_p": 1e-12}
+    tuner = OptionTuner(trial_steps=1)
+    opts = tuner.tune(w, base, w.dt)
+    assert len(tuner.timings) == 1
+    (key, times), = tuner.timings.items()
+    assert set(times) == set(option_candidates(True, binding.FP64))
+    assert tuner.tune(w, base, w.dt) == opts and len(tuner.timings) == 1      # cached
+    out = []
+    for o in (base, opts):
+        sim = gpu_sim(w, **o)
+        sim.set_initial(X0)
+        for _ in range(3):
+            sim.step(w.dt, 3, 2)
+        out.append(sim.fields(full=True))
+        sim.close()
+    assert rel(out[1][0], out[0][0]) < 1e-9 and rel(out[1][1], out[0][1]) < 1e-8
