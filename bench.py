@@ -186,13 +186,19 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def load_traffic(key: str):
+def load_traffic(key: str, alg_bytes_per_launch: float = 0.0):
     """DRAM bytes per launch of a kernel from the committed ncu summary, if
-    the solver sources are unchanged since it was captured (else None)."""
+    the solver sources are unchanged since it was captured (else None).  An
+    entry holds either the bytes of one launch or, for a solve made of a
+    chain of kernels captured on a smaller case, the ratio of DRAM bytes to
+    algorithmic bytes over whole iterations, applied here to the launch's
+    algorithmic bytes (traffic grows with the bytes the iterations move)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             e = json.load(fh).get(key)
         if e and e.get("source_hash") == kernel_source_hash():
+            if "dram_over_algorithmic" in e:
+                return round(e["dram_over_algorithmic"] * alg_bytes_per_launch) if alg_bytes_per_launch else None
             return e.get("bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -374,7 +380,8 @@ def slab_leg(args, torch, stream, flush, peaks) -> dict:
     m = out["mixed"]["elliptic"]
     out["roofline"] = {"kernel": "pcg_elliptic (mixed)", "bound": "hbm", "achieved": m["achieved_gbs"],
                        "peak": hbm, "unit": "GB/s", "frac": round(m["achieved_gbs"] / hbm, 4),
-                       "traffic": load_traffic("slab_pcg_elliptic"),
+                       "traffic": load_traffic("slab_pcg_elliptic", m["krylov_bytes_per_launch"] +
+                                               m["vcycle_bytes_per_launch"]),
                        "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                        "parabolic_frac": round(out["mixed"]["parabolic"]["achieved_gbs"] / hbm, 4)}
     out["steps"] = args.slab_steps
@@ -446,7 +453,9 @@ def lv_leg(args, torch, stream, flush, peaks) -> dict:
     hbm = peaks.get("hbm_gbs", 6800.0)
     m = out["mixed"]["elliptic"]
     out["roofline"] = {"kernel": "pcg_elliptic (mixed)", "bound": "hbm", "achieved": m["achieved_gbs"],
-                       "peak": hbm, "unit": "GB/s", "frac": round(m["achieved_gbs"] / hbm, 4), "traffic": None,
+                       "peak": hbm, "unit": "GB/s", "frac": round(m["achieved_gbs"] / hbm, 4),
+                       "traffic": load_traffic("lv_pcg_elliptic", m["krylov_bytes_per_launch"] +
+                                               m["vcycle_bytes_per_launch"]),
                        "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                        "parabolic_frac": round(out["mixed"]["parabolic"]["achieved_gbs"] / hbm, 4)}
     out["steps"] = args.lv_steps

@@ -94,8 +94,12 @@ class Executor:
 
 class Server:
     def __init__(self, executor: Executor, max_slots: int = 8, hbm_budget: int = 64 << 30,
-                 chunk_steps: int = 50, batched: bool = False):
+                 chunk_steps: int = 50, batched: bool = False, max_solo: Optional[int] = None):
+        """max_solo (batched form): at most this many requests served alone
+        advance at a time (in admission order); the others wait, built,
+        until one completes.  None: no limit."""
         self.ex = executor
+        self.max_solo = max_solo
         self.max_slots = max_slots
         self.budget = hbm_budget
         self.chunk = chunk_steps
@@ -153,10 +157,22 @@ class Server:
                     del starting[rid]
                     active[rid] = a
                     a["solo"] = not self.batched or self.ex.group_key(a["job"]) is None
-                    if a["solo"]:
-                        n = min(self.chunk, a["job"].n_steps)
-                        self.ex.advance(a["h"], n)
-                        a["steps"] = n
+                    a["running"] = False
+            # requests served alone start (in admission order) while the
+            # solo limit allows
+            running = sum(1 for a in active.values() if a["solo"] and a["running"])
+            for rid in sorted(active, key=lambda r: (active[r]["admitted"], r)):
+                a = active[rid]
+                if not a["solo"] or a["running"]:
+                    continue
+                if self.batched and self.max_solo is not None and running >= self.max_solo:
+                    break
+                a["running"] = True
+                running += 1
+                progressed = True
+                n = min(self.chunk, a["job"].n_steps)
+                self.ex.advance(a["h"], n)
+                a["steps"] = n
 
             def complete(rid):
                 nonlocal used, qi
@@ -198,7 +214,7 @@ class Server:
             # batched form those whose group key is None)
             for rid in list(active):
                 a = active[rid]
-                if not a["solo"] or not self.ex.ready(a["h"]):
+                if not a["solo"] or not a["running"] or not self.ex.ready(a["h"]):
                     continue
                 progressed = True
                 j = a["job"]
@@ -335,6 +351,7 @@ class VirtualExecutor(Executor):
         self.t = 0.0
         self.solo_nodes = solo_nodes
         self.grouped: List[List[int]] = []      # rids of every group chunk launched
+        self.max_busy_solo = 0                  # most requests of solo size with work at once
         self.rate = rate
         self.bpn = bytes_per_node
         self.quantum = quantum
@@ -393,6 +410,9 @@ class VirtualExecutor(Executor):
 
     def _tick(self, dt: float) -> None:
         busy = [st for st in self.live.values() if st["work"] > 1e-9]
+        if self.solo_nodes is not None:
+            nsolo = sum(1 for st in busy if st["job"].n_nodes >= self.solo_nodes)
+            self.max_busy_solo = max(self.max_busy_solo, nsolo)
         if busy:
             share = self.rate * dt / len(busy)
             for st in busy:

@@ -128,3 +128,17 @@ def test_batched_form_serves_large_requests_alone():
     for g in ex.grouped:
         assert len({size[r] for r in g}) == 1                 # one mesh size per group
     assert any(len(g) > 1 for g in ex.grouped)                # small requests share chunks
+
+
+@pytest.mark.parametrize("max_solo", [1, 2])
+def test_solo_limit_bounds_the_large_requests_advancing_at_once(max_solo):
+    """Batched form with max_solo: requests served alone advance at most
+    max_solo at a time (the others wait, admitted and built), the small
+    ones keep batching meanwhile, and every request completes."""
+    ex = S.VirtualExecutor(rate=1e8, solo_nodes=10000)
+    jobs = [S.Job(r, 0.0005 * r, (1089, 16641, 4225, 16641)[r % 4], 40) for r in range(16)]
+    done = S.Server(ex, max_slots=10, hbm_budget=10**12, chunk_steps=10, batched=True,
+                    max_solo=max_solo).run(jobs)
+    assert sorted(c.rid for c in done) == list(range(16))
+    assert ex.max_busy_solo == max_solo
+    assert any(len(g) > 1 for g in ex.grouped)
