@@ -525,8 +525,8 @@ def serve_leg(args) -> dict:
     simulated for args.serve_ms ms at dt = 0.02 ms, mixed precision:
       batched     resident requests below args.serve_solo_nodes nodes advance
                   together through bd_batch_step, one batch per (model, mesh
-                  size), joining at chunk boundaries; larger ones run alone on
-                  their own streams (16 slots in all);
+                  size), joining at 10-step chunk boundaries; larger ones run
+                  alone on their own streams, one at a time (16 slots in all);
       streams     each resident request on its own stream (8 slots);
       closed      the batched form with 16 clients keeping one request each
                   outstanding;
@@ -543,7 +543,7 @@ def serve_leg(args) -> dict:
                 for r in reqs]
     js = jobs()
     out = {"requests": len(reqs), "rate_per_s": 40.0, "sides": list(sides), "t_end_ms": args.serve_ms,
-           "chunk_steps": 25, "work_node_steps": int(sum(j.n_nodes * j.n_steps for j in js))}
+           "work_node_steps": int(sum(j.n_nodes * j.n_steps for j in js))}
 
     def record(sm, wall):
         return {"p50_ms": round(sm["p50_ms"], 2), "p99_ms": round(sm["p99_ms"], 2),
@@ -553,17 +553,20 @@ def serve_leg(args) -> dict:
     mixed = lambda: binding.default_options(precision=binding.MIXED)          # noqa: E731
     out["solo_nodes"] = args.serve_solo_nodes
     solo = args.serve_solo_nodes if args.serve_solo_nodes > 0 else None
-    for name, batched, slots in (("batched_mixed", True, 16), ("streams_mixed", False, 8)):
+    for name, batched, slots, chunk in (("batched_mixed", True, 16, 10), ("streams_mixed", False, 8, 25)):
         ex = S.GpuExecutor(mixed, dt=0.02, solo_nodes=solo)
         t0 = time.perf_counter()
-        done = S.Server(ex, max_slots=slots, hbm_budget=64 << 30, chunk_steps=25, batched=batched).run(jobs())
+        done = S.Server(ex, max_slots=slots, hbm_budget=64 << 30, chunk_steps=chunk, batched=batched,
+                        max_solo=1).run(jobs())
         wall = time.perf_counter() - t0
         ex.close()
         out[name] = record(S.summarize(done), wall)
         out[name]["slots"] = slots
+        out[name]["chunk_steps"] = chunk
     ex = S.GpuExecutor(mixed, dt=0.02, solo_nodes=solo)
     t0 = time.perf_counter()
-    done = S.Server(ex, max_slots=16, hbm_budget=64 << 30, chunk_steps=25, batched=True).run_closed(jobs(), 16)
+    done = S.Server(ex, max_slots=16, hbm_budget=64 << 30, chunk_steps=10, batched=True,
+                    max_solo=1).run_closed(jobs(), 16)
     wall = time.perf_counter() - t0
     ex.close()
     sm = S.summarize(done)
