@@ -132,7 +132,7 @@ typedef struct {
                             cg_block <= 512; 3 affects only the mixed AMG kernels);
                             BD_ERR_ARG otherwise; ignored with cg_cluster */
   int streaming;         /* solver form: 0 (default) streaming for operators of at least
-                            12M entries (they do not fit in L2), persistent otherwise;
+                            5M entries (measured crossover on GB300), persistent otherwise;
                             1: always streaming; -1: never; 2: streaming with the loops on
                             the host (a profiling form: eager launches that tools can capture,
                             one synchronisation per iteration; no graphs; sweep_tol must be 0).

@@ -1845,7 +1845,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
       delete s;
       return fail(nullptr, BD_ERR_ARG, "streaming = 2 (host-driven loops) needs sweep_tol = 0");
     }
-    s->streaming = s->opts.cg_cluster == 0 && (so >= 1 || (so == 0 && nnz >= kTier2Nnz));
+    s->streaming = s->opts.cg_cluster == 0 && (so >= 1 || (so == 0 && nnz >= kStreamNnz));
     if (so == 2) s->opts.use_graph = 0;   // host-driven loops cannot be captured
   }
   if (ok && s->streaming) {

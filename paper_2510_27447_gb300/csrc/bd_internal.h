@@ -23,6 +23,11 @@ constexpr int kMaxNS = 19;
 // even on 2-D meshes of 4.5M and 7.3M and a 3-D mesh of 4M).
 constexpr int kSolverTierBlock[3] = {1024, 512, 1024};
 constexpr int64_t kTier2Nnz = 12000000;
+// operators of at least kStreamNnz entries take the streaming solver form by
+// default (measured on GB300, mixed, ms per step persistent / streaming:
+// 513^2 sheet, 1.8M entries, 6.75 / 8.28; 3-D slab of 3.9M entries 11.7 /
+// 12.0; 1025^2 sheet, 7.3M, 19.3 / 17.9; 3-D slab of 10.6M 27.3 / 22.5)
+constexpr int64_t kStreamNnz = 5000000;
 
 // device status word bits (one per bd_status_t failure kind)
 enum : int {
