@@ -884,7 +884,7 @@ def main():
     ap.add_argument("--side", type=int, default=SIDE,
                     help="--profile-workload: sheet side, or the slab's x/y nodes (z: (side-1)/4+1)")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
-    ap.add_argument("--vec4", type=int, default=0, choices=[-1, 0],
+    ap.add_argument("--vec4", type=int, default=0, choices=[-1, 0, 1],
                     help="--profile-workload: SELL-32/4 copy of the FP32 elliptic operator (bd_opts_t.vec4)")
     ap.add_argument("--wide-sell", type=int, default=0, choices=[-1, 0, 1],
                     help="--profile-workload: SELL-32 for AMG levels with long rows (bd_opts_t.wide_sell)")

@@ -141,11 +141,13 @@ typedef struct {
                             one cooperative kernel each (bd_stats_t.streaming reports the form
                             in use) */
   int vec4;              /* 0 (default): mixed-precision streaming solves also keep the FP32
-                            elliptic operator in the SELL-32/4 layout (four consecutive entries
-                            of a row per 16-byte load; 8 more bytes per stored entry) and use it
-                            in the Krylov and AMG level-0 products; -1: they do not (the plain
-                            SELL-32 layout only); BD_ERR_ARG otherwise.  Both give the same sums
-                            in the same order */
+                            elliptic and parabolic operators, and every FP32 AMG level operator
+                            stored as SELL-32 with at least 2^17 rows, in the SELL-32/4 layout
+                            (four consecutive entries of a row per 16-byte load; 8 more bytes
+                            per stored entry) and use it in their products; 1: the same for
+                            every SELL-32 level operator whatever its size (testing); -1: none
+                            (the plain SELL-32 layout only); BD_ERR_ARG otherwise.  Both layouts
+                            give the same sums in the same order */
   int csr_lanes;         /* streaming solves, AMG levels stored as CSR: threads per row.  0
                             (default): a quarter of the level's mean row length rounded up to a
                             power of two in [4, 32], or 256 (a block per row) for rows of 256

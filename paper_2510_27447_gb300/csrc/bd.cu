@@ -736,8 +736,36 @@ int setup_amg(bd_state* s, const HostOps& H) {
       out->sw = csr ? nullptr : static_cast<const int*>(upload(S.sw.data(), S.sw.size() * 4));
       out->col = static_cast<const int*>(upload(S.col.data(), S.col.size() * 4));
       out->val = static_cast<const float*>(upload(fv.data(), fv.size() * 4));
+      // SELL-32/4 copy for the streaming kernels: operators of at least 2^17
+      // rows (vec4 = 0) or every SELL operator (vec4 = 1)
+      const bool v4 = !csr && s->vec4 && (s->opts.vec4 == 1 || S.n >= (int64_t(1) << 17));
+      std::vector<int64_t> p4;
+      std::vector<int> c4;
+      std::vector<float> f4;
+      if (v4) {
+        const int64_t nsl = int64_t(S.sw.size());
+        p4.resize(nsl);
+        int64_t off = 0;
+        for (int64_t sl = 0; sl < nsl; ++sl) {
+          p4[sl] = off;
+          off += 32 * int64_t((S.sw[sl] + 3) & ~3);
+        }
+        c4.assign(off, 0);
+        f4.assign(off, 0.0f);
+        for (int64_t sl = 0; sl < nsl; ++sl)
+          for (int l = 0; l < 32; ++l)
+            for (int k = 0; k < S.sw[sl]; ++k) {
+              const int64_t src = S.sptr[sl] + 32 * int64_t(k) + l;
+              const int64_t dst = p4[sl] + 128 * int64_t(k / 4) + 4 * l + k % 4;
+              c4[dst] = S.col[src];
+              f4[dst] = fv[src];
+            }
+        out->sptr4 = static_cast<const int64_t*>(upload(p4.data(), p4.size() * 8));
+        out->col4 = static_cast<const int*>(upload(c4.data(), c4.size() * 4));
+        out->val4 = static_cast<const float*>(upload(f4.data(), f4.size() * 4));
+      }
       return (csr ? out->rp != nullptr : (out->sptr && out->sw)) && out->col && out->val &&
-             cudaStreamSynchronize(s->stream) == cudaSuccess;
+             (!v4 || (out->sptr4 && out->col4 && out->val4)) && cudaStreamSynchronize(s->stream) == cudaSuccess;
     };
     AmgDevF& F = s->amgf;
     F.nlev = M.nlev;
@@ -1863,10 +1891,10 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   }
   // SELL-32/4 copy of the FP32 elliptic operator: four consecutive entries of
   // a row per 16-byte load in the streaming products
-  if (s->opts.vec4 != 0 && s->opts.vec4 != -1) {
+  if (s->opts.vec4 < -1 || s->opts.vec4 > 1) {
     release(s);
     delete s;
-    return fail(nullptr, BD_ERR_ARG, "vec4 must be 0 or -1");
+    return fail(nullptr, BD_ERR_ARG, "vec4 must be -1, 0 or 1");
   }
   {
     const int cl = s->opts.csr_lanes;
@@ -1877,7 +1905,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
       return fail(nullptr, BD_ERR_ARG, "csr_lanes must be 0, 4, 8, 16, 32 or 256 and wide_sell -1, 0 or 1");
     }
   }
-  s->vec4 = s->streaming && s->precision == BD_MIXED && s->opts.vec4 == 0;
+  s->vec4 = s->streaming && s->precision == BD_MIXED && s->opts.vec4 >= 0;
   std::vector<int64_t> h_sptr4;
   std::vector<int> e_col4;
   int64_t en4 = 0;

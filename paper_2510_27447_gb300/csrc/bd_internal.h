@@ -314,6 +314,11 @@ struct SellDevT {
   const T* val;
   const int64_t* rp;               // non-null: CSR (col/val row-major), one warp per row
   int lpr;                         // CSR in the streaming kernels: lanes per row (power of 2; 0: 32)
+  // optional SELL-32/4 copy (FP32 operators of streaming handles, see
+  // launch_sell_v4 for the layout; the slice widths are sw): NULL = none
+  const int64_t* sptr4;
+  const int* col4;
+  const T* val4;
 };
 
 // lanes per CSR row in the streaming level kernels: the smallest power of two

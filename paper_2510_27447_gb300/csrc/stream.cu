@@ -169,9 +169,19 @@ __device__ __forceinline__ X srow(const int64_t* __restrict__ sptr, const int* _
 }
 
 // the same over the SELL-32/4 copy of an FP32 operator: four column indices
-// and four values per 16-byte load, evict-first, the entries added in the
-// SELL-32 order
-template <class X>
+// and four values per 16-byte load (evict-first when STREAMOP, else through
+// the read-only cache), the entries added in the SELL-32 order
+template <bool STREAMOP>
+__device__ __forceinline__ int4 ld4i(const int* p) {
+  if constexpr (STREAMOP) return __ldcs(reinterpret_cast<const int4*>(p));
+  else return __ldg(reinterpret_cast<const int4*>(p));
+}
+template <bool STREAMOP>
+__device__ __forceinline__ float4 ld4f(const float* p) {
+  if constexpr (STREAMOP) return __ldcs(reinterpret_cast<const float4*>(p));
+  else return __ldg(reinterpret_cast<const float4*>(p));
+}
+template <class X, bool STREAMOP = true>
 __device__ __forceinline__ X srow4(const int64_t* __restrict__ sptr4, const int* __restrict__ sw,
                                    const int* __restrict__ col4, const float* __restrict__ val4,
                                    const X* __restrict__ x, int i) {
@@ -180,14 +190,14 @@ __device__ __forceinline__ X srow4(const int64_t* __restrict__ sptr4, const int*
   const int w = sw[s];
   X acc = X(0);
   for (int k0 = 0; k0 < w; k0 += 8) {      // two 4-entry groups in flight
-    const int4 c0 = __ldcs(reinterpret_cast<const int4*>(col4 + base + 32 * k0));
-    const float4 v0 = __ldcs(reinterpret_cast<const float4*>(val4 + base + 32 * k0));
+    const int4 c0 = ld4i<STREAMOP>(col4 + base + 32 * k0);
+    const float4 v0 = ld4f<STREAMOP>(val4 + base + 32 * k0);
     const bool two = k0 + 4 < w;
     int4 c1 = c0;
     float4 v1 = make_float4(0.f, 0.f, 0.f, 0.f);
     if (two) {
-      c1 = __ldcs(reinterpret_cast<const int4*>(col4 + base + 32 * (k0 + 4)));
-      v1 = __ldcs(reinterpret_cast<const float4*>(val4 + base + 32 * (k0 + 4)));
+      c1 = ld4i<STREAMOP>(col4 + base + 32 * (k0 + 4));
+      v1 = ld4f<STREAMOP>(val4 + base + 32 * (k0 + 4));
     }
     const X g0 = __ldg(x + c0.x), g1 = __ldg(x + c0.y), g2 = __ldg(x + c0.z), g3 = __ldg(x + c0.w);
     X h0 = X(0), h1 = X(0), h2 = X(0), h3 = X(0);
@@ -297,8 +307,20 @@ __device__ __forceinline__ void level_rows(const SellDevT<T>& M, const T* x, boo
       pe = ne;
     }
   } else if ((K & kRowsSellStream) && streamop) {
+    if constexpr (sizeof(T) == 4) {
+      if (M.col4) {   // SELL-32/4 copy of a large FP32 level operator
+        for (int i = gt; i < M.n; i += gs) epi(i, srow4<T, true>(M.sptr4, M.sw, M.col4, M.val4, x, i));
+        return;
+      }
+    }
     for (int i = gt; i < M.n; i += gs) epi(i, srow<true, T, T>(M.sptr, M.sw, M.col, M.val, x, i));
   } else {
+    if constexpr (sizeof(T) == 4) {
+      if (M.col4) {
+        for (int i = gt; i < M.n; i += gs) epi(i, srow4<T, false>(M.sptr4, M.sw, M.col4, M.val4, x, i));
+        return;
+      }
+    }
     for (int i = gt; i < M.n; i += gs) epi(i, srow<false, T, T>(M.sptr, M.sw, M.col, M.val, x, i));
   }
 }
