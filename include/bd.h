@@ -314,7 +314,12 @@ int bd_device_fields(const bd_state_t* s, const double** X_dev, const double** u
 int bd_get_state(const bd_state_t* s, void* buf, size_t* bytes);
 int bd_set_state(bd_state_t* s, const void* buf, size_t bytes);
 
-/* Device bytes bd_create would allocate for this mesh and model. */
+/* Estimate of the device bytes bd_create allocates for this mesh, model and
+ * options (opts NULL: defaults): operators, state and workspaces, the FP32
+ * copies of the mixed path, the AMG hierarchy (from the entry ratios of
+ * structured 2-D and 3-D meshes) and the streaming form's SELL-32/4 copies.
+ * Host only.  Meant for admission control; not a bound for arbitrary
+ * meshes. */
 size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts_t* opts);
 
 int bd_get_stats(const bd_state_t* s, bd_stats_t* out);

@@ -2370,7 +2370,6 @@ int bd_step_adaptive(bd_state_t* s, double dt_max, double tol, int M, int K, dou
 }
 
 size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts_t* opts) {
-  (void)opts;
   if (!mesh) return 0;
   const int ns = model_ns(int(model));
   if (ns == 0) return 0;
@@ -2388,11 +2387,34 @@ size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts
     NT = 0.0;
     for (uint8_t t : tis) NT += t;
   }
+  bd_opts_t o;
+  if (opts) o = *opts;
+  else bd_default_options(&o);
+  const bool mixed = o.precision == BD_MIXED;
   const double nnz = N * (mesh->dim == 2 ? 7.0 : 15.0);   // P1 node graph, upper estimate for structured meshes
+  // pattern + A_i, A_ie, M_c, M_v and up to four cached parabolic shifts (FP64)
   const double mat = nnz * (4 + 8 * 4 + 8 * 4) + N * (4 * 3 + 8);
   const double st = NT * 8 * (ns * (1 + 3 * kMaxNodes) + 4 * (ns - 1) + 4) + N * 8 * (3 * kMaxNodes + 12);
   const double packs = NT * 8.0 * (cond_pack_values(model) + 2 * jac_pack_values(model));
-  return size_t(mat + st + packs) + (size_t(1) << 20);
+  double extra = 0.0;
+  // FP32 copies of A_ie and of the parabolic shifts, FP32 workspaces
+  if (mixed) extra += nnz * 4 * 5 + N * 4 * 16;
+  // AMG hierarchy below level 0: measured about 2.1 x (3-D) and 1.2 x (2-D)
+  // the entries of A_0 over all A, R, P; SELL padding, FP64 values and
+  // indices, an FP32 copy on the mixed path, the dense coarse inverse
+  const bool amg = o.elliptic_precond == 1 && N > 1500;
+  const double lev = amg ? nnz * (mesh->dim == 2 ? 1.2 : 2.1) * 1.3 : 0.0;
+  const double nc = std::min(1500.0, N / 50.0 + 1.0);    // dense coarsest level (measured 1247 at 66k nodes)
+  if (amg) extra += lev * (12 + (mixed ? 8 : 0)) + nc * nc * 12 + N * 8 * 10;
+  // streaming form: its workspaces and, mixed, the SELL-32/4 copies of the
+  // FP32 operators (8 bytes an entry, widths padded to 4)
+  const bool streaming =
+      o.cg_cluster == 0 && (o.streaming >= 1 || (o.streaming == 0 && nnz >= double(kStreamNnz)));
+  if (streaming) {
+    extra += N * 8 * 8;
+    if (mixed && o.vec4 >= 0) extra += (nnz * 5 + lev) * 8 * 1.15;
+  }
+  return size_t(mat + st + packs + extra) + (size_t(1) << 20);
 }
 
 int bd_struct_sizes(size_t* mesh, size_t* cond, size_t* opts, size_t* stats) {

@@ -82,11 +82,26 @@ def test_bad_arguments_are_rejected_without_a_device(lib):
 
 def test_footprint_scales_with_nodes(lib):
     from paper_2510_27447_gb300 import workloads as W
-    a = binding.footprint_bytes(*W.square_grid(33), binding.LR91)
-    b = binding.footprint_bytes(*W.square_grid(65), binding.LR91)
-    c = binding.footprint_bytes(*W.square_grid(65), binding.TP06_EPI)
+    jac = binding.default_options(elliptic_precond=0)
+    a = binding.footprint_bytes(*W.square_grid(33), binding.LR91, jac)
+    b = binding.footprint_bytes(*W.square_grid(65), binding.LR91, jac)
+    c = binding.footprint_bytes(*W.square_grid(65), binding.TP06_EPI, jac)
     assert 3.5 < (b - 2**20) / (a - 2**20) < 4.2
     assert c > 1.5 * b
+
+
+def test_footprint_follows_the_options(lib):
+    """The estimate adds the AMG hierarchy, the FP32 copies of the mixed
+    path and, for streaming handles, the SELL-32/4 copies."""
+    from paper_2510_27447_gb300 import workloads as W
+    g = W.square_grid(129)
+    fp = lambda **o: binding.footprint_bytes(*g, binding.TP06_EPI, binding.default_options(**o))   # noqa: E731
+    jac, amg = fp(elliptic_precond=0), fp(elliptic_precond=1)
+    mixed = fp(elliptic_precond=1, precision=binding.MIXED)
+    stream = fp(elliptic_precond=1, precision=binding.MIXED, streaming=1)
+    plain = fp(elliptic_precond=1, precision=binding.MIXED, streaming=1, vec4=-1)
+    assert jac < amg < mixed < plain < stream
+    assert fp() == binding.footprint_bytes(*g, binding.TP06_EPI)       # NULL options = defaults
 
 
 def test_bath_mesh_errors_are_host_side(lib):
