@@ -267,3 +267,55 @@ def test_option_tuner_times_every_candidate_and_keeps_the_results():
         out.append(sim.fields(full=True))
         sim.close()
     assert rel(out[1][0], out[0][0]) < 1e-9 and rel(out[1][1], out[0][1]) < 1e-8
+
+
+def _bath_small():
+    # 625 nodes (289 tissue): the tissue rows' columns reach into the bath
+    return W.bath_sheet(24, -0.25, 1.25, 0.0, 1.0, W.LR91_PAPER_MOD, 0.05, 12, strip=0.1, s1_amp=80.0,
+                        s1_dur=1.0)
+
+
+@pytest.mark.parametrize("prec", [binding.FP64, binding.MIXED])
+def test_streaming_steps_on_a_bath_mesh_match_oracle(prec):
+    """Whole steps of the streaming form on a bidomain-bath mesh (the path of
+    the LV-shell leg): the parabolic solves over the tissue rows of the
+    shared pattern, the elliptic solve over tissue and bath."""
+    w = _bath_small()
+    X0 = rest_X(w)
+    Xo, uo, to = OB.run(oracle_problem(w), X0, w.n_steps, w.dt, 3, 2)
+    tight = dict(cg_tol_e=1e-13, cg_tol_p=1e-13) if prec == binding.FP64 else {}
+    sim = gpu_sim(w, precision=prec, streaming=1, **tight)
+    sim.set_initial(X0)
+    for _ in range(w.n_steps):
+        sim.step(w.dt, 3, 2)
+    v, u, X = sim.fields(full=True)
+    ta = sim.activation_times()
+    st = sim.stats()
+    sim.close()
+    assert st["streaming"] == 1 and X.shape == (8, w.n_tissue) and u.shape == (w.n_nodes,)
+    assert X[0].max() > -20.0
+    if prec == binding.FP64:
+        assert rel(X, Xo) < 1e-9 and rel(u, uo) < 1e-8
+        np.testing.assert_array_equal(np.isnan(ta), np.isnan(to))
+        np.testing.assert_allclose(ta[~np.isnan(ta)], to[~np.isnan(to)], atol=1e-6)
+    else:
+        assert rel(v, Xo[0]) < 1e-3 and rel(u, uo) < 1e-3
+
+
+def test_streaming_steps_on_the_lv_shell_in_a_bath_match_oracle():
+    """The 3-D bidomain-bath geometry on a coarse lattice with the AMG
+    hierarchy, TP06, streaming form, FP64 and mixed."""
+    w = W.lv_shell_bath(h=0.35, n_steps=3)
+    X0 = rest_X(w)
+    Xo, uo, _ = OB.run(oracle_problem(w), X0, 3, w.dt, 3, 2)
+    for prec, tx, tu in ((binding.FP64, 1e-9, 1e-8), (binding.MIXED, 1e-4, 1e-3)):
+        tight = dict(cg_tol_e=1e-13, cg_tol_p=1e-13) if prec == binding.FP64 else {}
+        sim = gpu_sim(w, precision=prec, streaming=1, **tight)
+        sim.set_initial(X0)
+        for _ in range(3):
+            sim.step(w.dt)
+        v, u, X = sim.fields(full=True)
+        st = sim.stats()
+        sim.close()
+        assert st["streaming"] == 1 and st["amg_levels"] >= 1
+        assert rel(X, Xo) < tx and rel(u, uo) < tu, prec
