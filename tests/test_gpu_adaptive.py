@@ -79,3 +79,24 @@ def test_adaptive_mixed_precision_tracks_fp64():
     # same step sequence up to decisions taken within FP32 rounding of err = 1
     assert sum(out[0][0]) == pytest.approx(sum(out[1][0]), rel=0.1)
     assert np.all(np.isfinite(out[1][1]))
+
+
+def test_adaptive_steps_in_the_streaming_form_match_oracle():
+    """The adaptive controller on a handle whose solves take the streaming
+    form: the same accepted steps and rejections as the oracle."""
+    w = _sheet()
+    X0 = rest_X(w)
+    X, u, t, ta, dts, rej = OB.run_adaptive(oracle_problem(w), X0, 30, 0.05, 1e-2)
+    sim = gpu_sim(w, streaming=1, **TIGHT)
+    sim.set_initial(X0)
+    gdts, grej = [], 0
+    for _ in range(30):
+        dt, err, r = sim.step_adaptive(0.05, 1e-2)
+        gdts.append(dt)
+        grej += r
+    _, ug, Xg = sim.fields(full=True)
+    st = sim.stats()
+    sim.close()
+    assert st["streaming"] == 1
+    assert gdts == dts and grej == rej
+    assert rel(Xg, X) < 1e-8 and rel(ug, u) < 1e-7

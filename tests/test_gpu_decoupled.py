@@ -64,3 +64,15 @@ def test_cnrk2_graph_replay_equals_eager():
         s.close()
     for a, b in zip(*out):
         np.testing.assert_array_equal(a, b)
+
+
+def test_cnrk2_streaming_form_matches_oracle():
+    """The decoupled scheme's diffusion and elliptic solves in the streaming
+    form (the form large meshes take)."""
+    w = W.sheet(17, 0.4, W.LR91, 0.01, 80, strip=0.06)
+    (X, u, ta, st), (Xo, uo, to) = _run_both(w, 80, 0.01, streaming=1, **TIGHT)
+    assert st["streaming"] == 1
+    assert X[0].max() > -40.0
+    assert rel(X, Xo) < 1e-9 and rel(u, uo) < 1e-8
+    np.testing.assert_array_equal(np.isnan(ta), np.isnan(to))
+    np.testing.assert_allclose(ta[~np.isnan(ta)], to[~np.isnan(to)], atol=1e-6)
