@@ -777,12 +777,14 @@ def profile_workload(args) -> None:
     prec = binding.FP64 if args.precision == "fp64" else binding.MIXED
     sim = binding.simulation_from_workload(w, binding.default_options(precision=prec, pin_node=w.pin_node,
                                                                       streaming=args.streaming, vec4=args.vec4,
-                                                                      wide_sell=args.wide_sell))
+                                                                      wide_sell=args.wide_sell,
+                                                                      pair_solve=args.pair_solve))
     for _ in range(args.steps):
         sim.step(w.dt, M_NODES, K_SWEEPS)
     sim.sync()
     out = {"workload": w.name, "nodes": int(w.n_nodes), "steps": args.steps, "vec4": args.vec4,
-           "wide_sell": args.wide_sell, "stats": sim.stats(), "amg": sim.amg_levels()}
+           "wide_sell": args.wide_sell, "pair_solve": args.pair_solve, "stats": sim.stats(),
+           "amg": sim.amg_levels()}
     if args.profile_steps > 0:
         prof = sim.profile_steps(w.dt, M_NODES, K_SWEEPS, args.profile_steps)
         out["ms_per_step"] = round(sum(prof["ms"].values()) / args.profile_steps, 3)
@@ -888,6 +890,8 @@ def main():
                     help="--profile-workload: SELL-32/4 copy of the FP32 elliptic operator (bd_opts_t.vec4)")
     ap.add_argument("--wide-sell", type=int, default=0, choices=[-1, 0, 1],
                     help="--profile-workload: SELL-32 for AMG levels with long rows (bd_opts_t.wide_sell)")
+    ap.add_argument("--pair-solve", type=int, default=0, choices=[-1, 0],
+                    help="--profile-workload: a sweep's two elliptic solves as one (bd_opts_t.pair_solve)")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="--profile-workload: also time this many steps per kind (bd_profile_steps)")
     ap.add_argument("--streaming", type=int, default=0, choices=[-1, 0, 1, 2],

@@ -158,6 +158,14 @@ typedef struct {
                             the entries and the level has at least 2^17 rows averaging at most 96
                             entries, else CSR; 1: SELL-32 whenever the padding allows; -1:
                             always CSR; BD_ERR_ARG otherwise */
+  int pair_solve;        /* mixed precision with the AMG preconditioner: the two elliptic
+                            solves of every sweep after the first (the constraint at two
+                            Gauss-Lobatto nodes, Sec. 3.3.2) run as one two-system solve whose
+                            operator passes serve both right-hand sides -- one cooperative
+                            kernel in the persistent form, one kernel chain in the streaming
+                            form.  0 (default): on; -1: one solve after the other (each
+                            system's arithmetic is the same either way; the reductions are
+                            formed over different block partitions); BD_ERR_ARG otherwise */
 } bd_opts_t;
 
 typedef struct bd_state bd_state_t;
@@ -209,13 +217,19 @@ typedef struct {
                                    streams (13 vb with the AMG preconditioner, whose work is
                                    counted below), every solve its FP64 right-hand-side
                                    products and set-up passes, every mixed refinement pass an
-                                   FP64 residual product; vb = 4 (mixed) or 8 (FP64) */
+                                   FP64 residual product; vb = 4 (mixed) or 8 (FP64).  A
+                                   two-system elliptic solve (bd_opts_t.pair_solve) counts an
+                                   operator once where both systems use the same pass of it:
+                                   the Krylov product of an iteration in which both advance
+                                   and, streaming, the FP64 right-hand-side and residual
+                                   products of a pass both run */
   double vcycle_bytes;          /* elliptic AMG V-cycles of the profiled steps, counted the same
                                    way: per smoothed level two products with A_l and one each
                                    with R_l and P_l plus the level's vector streams (operators
-                                   read once for both systems of a two-RHS iteration) */
+                                   read once for both systems of a cycle that serves both) */
   double coarse_bytes;          /* ... their dense coarsest-level solves (nc^2 + 2 nc values
-                                   per cycle): a dense equivalent, reported apart */
+                                   per cycle; the streaming two-system solve reads the inverse
+                                   once for both): a dense equivalent, reported apart */
 } bd_profile_t;
 
 void bd_default_options(bd_opts_t* opts);

@@ -64,7 +64,8 @@ class Opts(C.Structure):
                 ("cg_grid", C.c_int),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_ctx", C.c_void_p),
                 ("stream", C.c_void_p), ("cg_cluster", C.c_int), ("solver_tier", C.c_int),
-                ("streaming", C.c_int), ("vec4", C.c_int), ("csr_lanes", C.c_int), ("wide_sell", C.c_int)]
+                ("streaming", C.c_int), ("vec4", C.c_int), ("csr_lanes", C.c_int), ("wide_sell", C.c_int),
+                ("pair_solve", C.c_int)]
 
 
 class Stats(C.Structure):

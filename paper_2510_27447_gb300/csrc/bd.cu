@@ -128,7 +128,8 @@ struct bd_state {
   long long* step_n = nullptr;
   int* d_status = nullptr;
   long long* d_stats = nullptr;            // [iters_e, solves_e, iters_p, solves_p, outer_e, outer_p, extra sweeps,
-                                           //  paired elliptic iterations]
+                                           //  paired elliptic iterations, launches, paired FP64 operator
+                                           //  passes, paired first V-cycles]
   int* gate = nullptr;                     // sweep test of Algorithm 2 (sweep_tol > 0)
   unsigned long long* dmax = nullptr;
   double* Xsave = nullptr;
@@ -152,7 +153,7 @@ struct bd_state {
   // streaming solver (operators that do not fit in L2): device scalars, block
   // partials, FP64-path workspaces and two streams that capture loop bodies
   bool streaming = false;
-  StreamScal* d_sc = nullptr;
+  StreamScal* d_sc = nullptr;     // two: a solve's (or a pair's first system's) and a pair's second system's
   double* spart = nullptr;
   double *sb64 = nullptr, *sr64 = nullptr;
   double *sr = nullptr, *sz = nullptr, *sp = nullptr, *sq = nullptr, *sd = nullptr, *sinvd = nullptr;
@@ -400,6 +401,44 @@ StreamLaunch stream_base(bd_state* s, int n) {
   return A;
 }
 
+// the streaming elliptic solve u = E(v) over all N rows (v holds every node);
+// k = 1: the second system of a pair, whose vectors are the second halves of
+// the mixed two-system workspaces and whose scalars are d_sc[1]
+StreamLaunch elliptic_launch(bd_state* s, const double* v, double* u, int k = 0) {
+  StreamLaunch A = stream_base(s, int(s->N));
+  const bool mixed = s->precision == BD_MIXED;
+  A.valA = s->Aie;
+  A.valT = mixed ? static_cast<const void*>(s->fAie) : static_cast<const void*>(s->Aie);
+  set_vec4(s, A, s->fAie4);
+  A.val1 = s->Ai;
+  A.va = v;
+  A.c1 = -1.0;
+  A.project = 1;
+  A.warm = 1;
+  A.x = u;
+  A.pin = s->opts.pin_node >= 0 ? s->opts.pin_node : -1;
+  A.max_outer = mixed ? 12 : 1;
+  A.inner_cap = s->opts.cg_cap_e;
+  A.use_amg = s->use_amg ? 1 : 0;
+  A.tol = s->opts.cg_tol_e;
+  A.tol_inner = mixed ? double(BD_MIXED_TOL_INNER) : s->opts.cg_tol_e;
+  A.iters_acc = s->d_stats + 0;
+  A.solves_acc = s->d_stats + 1;
+  A.outer_acc = s->d_stats + 4;
+  if (k == 1) {
+    const int64_t N = s->N;
+    A.sc = s->d_sc + 1;
+    A.b64 += N;
+    A.r64 += N;
+    A.r = static_cast<float*>(A.r) + N;
+    A.z = static_cast<float*>(A.z) + N;
+    A.p = static_cast<float*>(A.p) + N;
+    A.q = static_cast<float*>(A.q) + N;
+    A.d = static_cast<float*>(A.d) + N;
+  }
+  return A;
+}
+
 int elliptic(bd_state* s, const double* v, double* u) {
   if (s->streaming) {
     if (s->NT < s->N) {
@@ -407,26 +446,8 @@ int elliptic(bd_state* s, const double* v, double* u) {
       CK(launch_copy(s->NT, v, s->vfull, s->stream, s->opts.sweep_tol > 0 ? s->gate : nullptr));
       v = s->vfull;
     }
-    StreamLaunch A = stream_base(s, int(s->N));
+    const StreamLaunch A = elliptic_launch(s, v, u);
     const bool mixed = s->precision == BD_MIXED;
-    A.valA = s->Aie;
-    A.valT = mixed ? static_cast<const void*>(s->fAie) : static_cast<const void*>(s->Aie);
-    set_vec4(s, A, s->fAie4);
-    A.val1 = s->Ai;
-    A.va = v;
-    A.c1 = -1.0;
-    A.project = 1;
-    A.warm = 1;
-    A.x = u;
-    A.pin = s->opts.pin_node >= 0 ? s->opts.pin_node : -1;
-    A.max_outer = mixed ? 12 : 1;
-    A.inner_cap = s->opts.cg_cap_e;
-    A.use_amg = s->use_amg ? 1 : 0;
-    A.tol = s->opts.cg_tol_e;
-    A.tol_inner = mixed ? double(BD_MIXED_TOL_INNER) : s->opts.cg_tol_e;
-    A.iters_acc = s->d_stats + 0;
-    A.solves_acc = s->d_stats + 1;
-    A.outer_acc = s->d_stats + 4;
     Timed t(s, BD_K_PCG_ELLIPTIC, 0);   // its kernels count themselves on the device
     CK(stream_solve(A, mixed ? 1 : 0, &s->amgf, &s->amg, s->stream, s->side));
     return BD_OK;
@@ -472,10 +493,25 @@ int elliptic(bd_state* s, const double* v, double* u) {
 // u1 = E(v1) and u2 = E(v2): one two-RHS launch on the mixed AMG path, else
 // two solves
 int elliptic2(bd_state* s, const double* v1, double* u1, const double* v2, double* u2) {
-  if (!s->two_rhs || s->precision != BD_MIXED || !s->use_amg || s->streaming) {
+  if (!s->two_rhs || s->precision != BD_MIXED || !s->use_amg || s->opts.pair_solve < 0) {
     const int r = elliptic(s, v1, u1);
     if (r != BD_OK) return r;
     return elliptic(s, v2, u2);
+  }
+  if (s->streaming) {   // one chain for both systems (stream2.cu)
+    if (s->NT < s->N) {
+      Timed t(s, BD_K_COMBINE, 2);
+      const int* gate = s->opts.sweep_tol > 0 ? s->gate : nullptr;
+      CK(launch_copy(s->NT, v1, s->vfull, s->stream, gate));
+      CK(launch_copy(s->NT, v2, s->vfull2, s->stream, gate));
+      v1 = s->vfull;
+      v2 = s->vfull2;
+    }
+    const StreamLaunch A[2] = {elliptic_launch(s, v1, u1, 0), elliptic_launch(s, v2, u2, 1)};
+    Timed t(s, BD_K_PCG_ELLIPTIC, 0);   // its kernels count themselves on the device
+    CK(stream_solve_pair(A, s->amgf, s->amgf2, s->d_stats + 7, s->d_stats + 9, s->d_stats + 10, s->stream,
+                         s->side));
+    return BD_OK;
   }
   PcgLaunch P = pcg_base(s);
   if (s->NT < s->N) {
@@ -1248,8 +1284,8 @@ int ensure_stream_ws(bd_state* s) {
   const int64_t N = s->N;
   bool ok = true;
   if (!s->d_sc)
-    ok = alloc_n(s, reinterpret_cast<char**>(&s->d_sc), int64_t(sizeof(StreamScal))) &&
-         cudaMemsetAsync(s->d_sc, 0, sizeof(StreamScal), s->stream) == cudaSuccess;
+    ok = alloc_n(s, reinterpret_cast<char**>(&s->d_sc), int64_t(2 * sizeof(StreamScal))) &&
+         cudaMemsetAsync(s->d_sc, 0, 2 * sizeof(StreamScal), s->stream) == cudaSuccess;
   if (ok && !s->spart) ok = alloc_n(s, &s->spart, int64_t(stream_grid_cap()) * 4);
   if (ok && s->precision == BD_FP64 && !s->sb64) {
     ok = alloc_n(s, &s->sb64, N) && alloc_n(s, &s->sr64, N) && alloc_n(s, &s->sr, N) && alloc_n(s, &s->sz, N) &&
@@ -1878,7 +1914,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   }
   if (ok && s->streaming) {
     stream_prepare();   // kernel occupancies, queried outside any capture
-    ok = alloc_n(s, reinterpret_cast<char**>(&s->d_sc), int64_t(sizeof(StreamScal))) &&
+    ok = alloc_n(s, reinterpret_cast<char**>(&s->d_sc), int64_t(2 * sizeof(StreamScal))) &&
          alloc_n(s, &s->spart, int64_t(stream_grid_cap()) * 4);
     if (ok && s->precision == BD_FP64)
       ok = alloc_n(s, &s->sb64, N) && alloc_n(s, &s->sr64, N) && alloc_n(s, &s->sr, N) && alloc_n(s, &s->sz, N) &&
@@ -1903,6 +1939,11 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
       release(s);
       delete s;
       return fail(nullptr, BD_ERR_ARG, "csr_lanes must be 0, 4, 8, 16, 32 or 256 and wide_sell -1, 0 or 1");
+    }
+    if (s->opts.pair_solve < -1 || s->opts.pair_solve > 0) {
+      release(s);
+      delete s;
+      return fail(nullptr, BD_ERR_ARG, "pair_solve must be -1 or 0");
     }
   }
   s->vec4 = s->streaming && s->precision == BD_MIXED && s->opts.vec4 >= 0;
@@ -1969,7 +2010,7 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
   if (e == cudaSuccess) e = cudaMemsetAsync(s->bar, 0, 8, s->stream);
   for (double* v : {s->sb64, s->sr64, s->sr, s->sz, s->sp, s->sq, s->sd, s->sinvd})
     if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, N * 8, s->stream);
-  if (e == cudaSuccess && s->d_sc) e = cudaMemsetAsync(s->d_sc, 0, sizeof(StreamScal), s->stream);
+  if (e == cudaSuccess && s->d_sc) e = cudaMemsetAsync(s->d_sc, 0, 2 * sizeof(StreamScal), s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, 4, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_stats, 0, 128, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_clamps, 0, 8, s->stream);
@@ -2539,9 +2580,9 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
   if (!(dt > 0) || (M != 2 && M != 3) || K < 1) return fail(s, BD_ERR_ARG, "bad step shape");
   std::memset(out, 0, sizeof(*out));
   out->nnz = s->nnz;
-  long long st0[8], st1[8];
+  long long st0[11], st1[11];
   CK(cudaStreamSynchronize(s->stream));
-  CK(cudaMemcpy(st0, s->d_stats, 64, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(st0, s->d_stats, sizeof(st0), cudaMemcpyDeviceToHost));
   s->prof = true;
   int rc = BD_OK;
   for (int n = 0; n < n_steps && rc == BD_OK; ++n) {
@@ -2562,7 +2603,7 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
   }
   s->prof = false;
   if (rc != BD_OK) return rc;
-  CK(cudaMemcpy(st1, s->d_stats, 64, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(st1, s->d_stats, sizeof(st1), cudaMemcpyDeviceToHost));
   out->cg_iters[0] = st1[0] - st0[0];
   out->cg_solves[0] = st1[1] - st0[1];
   out->cg_iters[1] = st1[2] - st0[2];
@@ -2573,6 +2614,8 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
   const bool mixed = s->precision == BD_MIXED;
   const double vb = mixed ? 4.0 : 8.0;
   const double pairs = double(st1[7] - st0[7]);     // two-RHS iterations in which both systems advanced
+  const double pairs64 = double(st1[9] - st0[9]);   // FP64 operator passes shared by a streaming pair
+  const double pairsc = double(st1[10] - st0[10]);  // first V-cycles shared by a streaming pair
   for (int k = 0; k < 2; ++k) {
     const bool ell = k == 0;
     // elliptic: all nodes and the whole pattern; parabolic: the tissue block
@@ -2593,6 +2636,7 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
       b += outer * ((ell ? spmv(8.0) + 3.0 * 8.0 * n : 2.0 * 8.0 * n) + 16.0 * n + 20.0 * n);
     }
     if (ell && mixed && s->use_amg) b -= pairs * nnz * (vb + 4);   // shared operator pass
+    if (ell) b -= pairs64 * nnz * (8.0 + 4.0);                     // shared FP64 products (A_i, A_ie)
     out->alg_bytes[k] = b;
   }
   if (s->use_amg) {
@@ -2603,7 +2647,9 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
                           double(mixed ? out->outer_iters[0] - out->cg_solves[0] : out->cg_solves[0]);
     out->vcycle_bytes = cycles * s->amg_cycle_bytes[v];
     out->coarse_bytes = cycles * s->amg_coarse_bytes[v];
-    if (mixed) out->vcycle_bytes -= pairs * (s->amg_cycle_opbytes[v] - vb * double(s->amg.nc) * double(s->amg.nc));
+    const double ncc = vb * double(s->amg.nc) * double(s->amg.nc);   // the dense coarse inverse
+    if (mixed) out->vcycle_bytes -= (pairs + pairsc) * (s->amg_cycle_opbytes[v] - ncc);
+    if (mixed && s->streaming) out->coarse_bytes -= (pairs + pairsc) * ncc;   // read once for both systems
   }
   return read_status(s);
 }

@@ -475,6 +475,20 @@ int stream_grid_cap();
 // single-system streaming kernel; later plans read the cached values
 void stream_prepare();
 int stream_grid(int64_t rows);
+// Two elliptic systems on one operator (stream2.cu): the AMG-preconditioned,
+// warm-started form of the elliptic solve for the two right-hand sides of a
+// later sweep, in one chain whose kernels load each operator entry once for
+// both.  a[k]: system k's parameters (its own vectors, scalars sc, counters;
+// the operator fields and the pin of a[0] serve both); H0 / H1: the FP32
+// hierarchy with system 0's / system 1's level vectors (the same operators).
+// pair_acc counts the inner iterations in which both systems advanced,
+// pair64_acc the FP64 operator passes (right-hand side, refinement residual)
+// and pairc_acc the first V-cycles of an inner solve shared by both.  FP32
+// inner iterations; cudaErrorInvalidValue for any other form.
+cudaError_t stream_solve_pair(const StreamLaunch (&a)[2], const AmgDevF& H0, const AmgDevF& H1, long long* pair_acc,
+                              long long* pair64_acc, long long* pairc_acc, cudaStream_t st, const cudaStream_t* side);
+// query (outside any capture) the resident blocks of the pair kernels
+void stream_prepare_pair();
 
 // ---- batched solves (one launch per phase for many independent systems) -----
 // A batch of nseg systems runs every phase of its solves as one launch over

@@ -46,15 +46,13 @@
 #include "bd_internal.h"
 #include "sparse.cuh"
 #include "segment.cuh"
+#include "stream_rows.cuh"
 #include "vcycle.cuh"
 
 namespace bd {
 
 namespace {
 
-constexpr int kSB = 256;       // threads per block of every streaming kernel
-static_assert(kSB == kCsrBlockLanes, "a block-per-row CSR level needs blocks of kCsrBlockLanes threads");
-constexpr int kBlocksPerSM = 8;
 
 // ---- policies -------------------------------------------------------------------
 
@@ -97,17 +95,10 @@ __device__ __forceinline__ const AmgDevT<T>& hier(const VcOne<T>& o, int) { retu
 template <class T>
 __device__ __forceinline__ const AmgDevT<T>& hier(const VcMany<T>& m, int r) { return stage(m.tab, r); }
 
-// every kernel counts its launch (the loops run on the device, so the host
-// cannot); a batched launch counts once
-__device__ __forceinline__ void count_launch(long long* acc) {
-  if (acc && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(acc), 1ull);
-}
+// every kernel counts its launch (see stream_rows.cuh); a batched launch counts once
 __device__ __forceinline__ void count_launch(const One& o) { count_launch(o.a.launch_acc); }
 __device__ __forceinline__ void count_launch(const Many& m) { count_launch(m.launch_acc); }
 
-__device__ __forceinline__ void set_cond(unsigned long long h, unsigned v) {
-  cudaGraphSetConditional(static_cast<cudaGraphConditionalHandle>(h), v);
-}
 
 // Loop conditions.  A single system sets them directly when it decides.  A
 // batch's conditions are set by st_batch_cond_kernel at the end of each loop
@@ -128,276 +119,7 @@ __device__ __forceinline__ void vote_outer(const One&, const StreamLaunch& a, bo
 }
 __device__ __forceinline__ void vote_outer(const Many&, const StreamLaunch&, bool, bool) {}
 
-// ---- row products ------------------------------------------------------------
 
-// evict-first load (operator streams: read once per use, larger than L2)
-template <class V>
-__device__ __forceinline__ V ld_stream(const V* p) {
-  return __ldcs(p);
-}
-
-// sum_k val[k] x[col[k]] over row i of a SELL-32 operator, entries in order,
-// four loads of each stream in flight per thread
-template <bool STREAMOP, class V, class X>
-__device__ __forceinline__ X srow(const int64_t* __restrict__ sptr, const int* __restrict__ sw,
-                                  const int* __restrict__ col, const V* __restrict__ val, const X* __restrict__ x,
-                                  int i) {
-  const int s = i >> 5;
-  const int64_t base = sptr[s] + (i & 31);
-  const int w = sw[s];
-  X acc = X(0);
-  constexpr int CH = 4;
-  for (int k0 = 0; k0 < w; k0 += CH) {
-    int c[CH];
-    V v[CH];
-    X g[CH];
-#pragma unroll
-    for (int k = 0; k < CH; ++k)
-      if (k0 + k < w) {
-        const int64_t e = base + 32 * (k0 + k);
-        c[k] = STREAMOP ? ld_stream(col + e) : __ldg(col + e);
-        v[k] = STREAMOP ? ld_stream(val + e) : __ldg(val + e);
-      }
-#pragma unroll
-    for (int k = 0; k < CH; ++k)
-      if (k0 + k < w) g[k] = __ldg(x + c[k]);
-#pragma unroll
-    for (int k = 0; k < CH; ++k)
-      if (k0 + k < w) acc += X(v[k]) * g[k];
-  }
-  return acc;
-}
-
-// the same over the SELL-32/4 copy of an FP32 operator: four column indices
-// and four values per 16-byte load (evict-first when STREAMOP, else through
-// the read-only cache), the entries added in the SELL-32 order
-template <bool STREAMOP>
-__device__ __forceinline__ int4 ld4i(const int* p) {
-  if constexpr (STREAMOP) return __ldcs(reinterpret_cast<const int4*>(p));
-  else return __ldg(reinterpret_cast<const int4*>(p));
-}
-template <bool STREAMOP>
-__device__ __forceinline__ float4 ld4f(const float* p) {
-  if constexpr (STREAMOP) return __ldcs(reinterpret_cast<const float4*>(p));
-  else return __ldg(reinterpret_cast<const float4*>(p));
-}
-template <class X, bool STREAMOP = true>
-__device__ __forceinline__ X srow4(const int64_t* __restrict__ sptr4, const int* __restrict__ sw,
-                                   const int* __restrict__ col4, const float* __restrict__ val4,
-                                   const X* __restrict__ x, int i) {
-  const int s = i >> 5;
-  const int64_t base = sptr4[s] + 4 * (i & 31);
-  const int w = sw[s];
-  X acc = X(0);
-  for (int k0 = 0; k0 < w; k0 += 8) {      // two 4-entry groups in flight
-    const int4 c0 = ld4i<STREAMOP>(col4 + base + 32 * k0);
-    const float4 v0 = ld4f<STREAMOP>(val4 + base + 32 * k0);
-    const bool two = k0 + 4 < w;
-    int4 c1 = c0;
-    float4 v1 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (two) {
-      c1 = ld4i<STREAMOP>(col4 + base + 32 * (k0 + 4));
-      v1 = ld4f<STREAMOP>(val4 + base + 32 * (k0 + 4));
-    }
-    const X g0 = __ldg(x + c0.x), g1 = __ldg(x + c0.y), g2 = __ldg(x + c0.z), g3 = __ldg(x + c0.w);
-    X h0 = X(0), h1 = X(0), h2 = X(0), h3 = X(0);
-    if (two) {
-      h0 = __ldg(x + c1.x);
-      h1 = __ldg(x + c1.y);
-      h2 = __ldg(x + c1.z);
-      h3 = __ldg(x + c1.w);
-    }
-    acc += X(v0.x) * g0;
-    acc += X(v0.y) * g1;
-    acc += X(v0.z) * g2;
-    acc += X(v0.w) * g3;
-    if (two) {
-      acc += X(v1.x) * h0;
-      acc += X(v1.y) * h1;
-      acc += X(v1.z) * h2;
-      acc += X(v1.w) * h3;
-    }
-  }
-  return acc;
-}
-
-// every row i of an AMG-level operator (SELL: thread per row; CSR: warp per
-// row, butterfly sum): epi(i, (M x)_i), run by one lane per row.  Level 0's
-// operators are streamed with evict-first loads, the coarser levels' stay
-// cacheable (read twice a cycle, they fit in L2).  K is the set of forms a
-// kernel compiles (kRows* flags): a kernel that never meets a form leaves
-// it out, which keeps registers low and resident warps high for the
-// latency-bound coarse products.
-constexpr int kRowsSellStream = 1, kRowsSellCache = 2, kRowsCsrLanes = 4, kRowsCsrBlock = 8;
-constexpr int kRowsAll = 15;
-constexpr int kRowsCoarse = kRowsSellCache | kRowsCsrLanes | kRowsCsrBlock;   // levels >= 1
-
-template <class T, int K, class F>
-__device__ __forceinline__ void level_rows(const SellDevT<T>& M, const T* x, bool streamop, SegInfo sg, F&& epi) {
-  const int gt = sg.lb * blockDim.x + threadIdx.x;
-  const int gs = sg.nb * blockDim.x;
-  if constexpr (K == kRowsSellStream) {
-    for (int i = gt; i < M.n; i += gs) epi(i, srow<true, T, T>(M.sptr, M.sw, M.col, M.val, x, i));
-    return;
-  }
-  if ((K & kRowsCsrBlock) && M.rp && M.lpr > 32) {
-    // a block per row (blockDim.x == kCsrBlockLanes): the row's entries
-    // strided over the block's threads (a few each: the rows are long, not
-    // huge), then the block's fixed-order sum; the row loop is block-uniform
-    // so every thread reaches the block sum's barriers
-    __shared__ T shb[1][32];
-    for (int i = sg.lb; i < M.n; i += sg.nb) {
-      const int64_t e = __ldg(M.rp + i + 1);
-      T v[1] = {T(0)};
-      for (int64_t p = __ldg(M.rp + i) + threadIdx.x; p < e; p += blockDim.x)
-        v[0] += __ldg(M.val + p) * __ldg(x + __ldg(M.col + p));
-      block_sum<1, T>(v, shb);
-      if (threadIdx.x == 0) epi(i, v[0]);
-    }
-  } else if ((K & kRowsCsrLanes) && M.rp) {
-    // L lanes per row (a power of two), 32 / L rows per warp pass; a lane
-    // keeps four entries L apart in flight, four partial sums added in a
-    // fixed order, then a butterfly over the row's lanes (deterministic).
-    // The pass loop is warp-uniform so every shuffle has all 32 lanes.
-    const int L = M.lpr > 0 ? M.lpr : 32;
-    const int lane = threadIdx.x & 31;
-    const int sub = lane & (L - 1);
-    const int rows_per_warp = 32 / L;
-    const int grp = lane / L;
-    const int step = (gs >> 5) * rows_per_warp;
-    int base = (gt >> 5) * rows_per_warp;
-    int i = base + grp;
-    int64_t pb = 0, pe = 0;
-    if (i < M.n) {
-      pb = __ldg(M.rp + i);
-      pe = __ldg(M.rp + i + 1);
-    }
-    for (; base < M.n; base += step) {
-      // the next pass's row pointers are requested before this pass's entries
-      const int inext = i + step;
-      int64_t nb = 0, ne = 0;
-      if (inext < M.n) {
-        nb = __ldg(M.rp + inext);
-        ne = __ldg(M.rp + inext + 1);
-      }
-      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
-      {
-        const int64_t e = pe;
-        for (int64_t p = pb + sub; p < e; p += 4 * L) {
-          const bool b1 = p + L < e, b2 = p + 2 * L < e, b3 = p + 3 * L < e;
-          const int c0 = __ldg(M.col + p);
-          const int c1 = b1 ? __ldg(M.col + p + L) : c0;
-          const int c2 = b2 ? __ldg(M.col + p + 2 * L) : c0;
-          const int c3 = b3 ? __ldg(M.col + p + 3 * L) : c0;
-          const T v0 = __ldg(M.val + p);
-          const T v1 = b1 ? __ldg(M.val + p + L) : T(0);
-          const T v2 = b2 ? __ldg(M.val + p + 2 * L) : T(0);
-          const T v3 = b3 ? __ldg(M.val + p + 3 * L) : T(0);
-          s0 += v0 * __ldg(x + c0);
-          s1 += v1 * __ldg(x + c1);
-          s2 += v2 * __ldg(x + c2);
-          s3 += v3 * __ldg(x + c3);
-        }
-      }
-      T s = (s0 + s1) + (s2 + s3);
-      for (int o = L >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (sub == 0 && i < M.n) epi(i, s);
-      i = inext;
-      pb = nb;
-      pe = ne;
-    }
-  } else if ((K & kRowsSellStream) && streamop) {
-    if constexpr (sizeof(T) == 4) {
-      if (M.col4) {   // SELL-32/4 copy of a large FP32 level operator
-        for (int i = gt; i < M.n; i += gs) epi(i, srow4<T, true>(M.sptr4, M.sw, M.col4, M.val4, x, i));
-        return;
-      }
-    }
-    for (int i = gt; i < M.n; i += gs) epi(i, srow<true, T, T>(M.sptr, M.sw, M.col, M.val, x, i));
-  } else {
-    if constexpr (sizeof(T) == 4) {
-      if (M.col4) {
-        for (int i = gt; i < M.n; i += gs) epi(i, srow4<T, false>(M.sptr4, M.sw, M.col4, M.val4, x, i));
-        return;
-      }
-    }
-    for (int i = gt; i < M.n; i += gs) epi(i, srow<false, T, T>(M.sptr, M.sw, M.col, M.val, x, i));
-  }
-}
-
-// ---- reductions ----------------------------------------------------------------
-
-// Block sums of v[0..NV) into part, the system's atomic ticket, and in its last
-// block to arrive the system's totals (block order, fixed tree): returns true
-// there, with v holding the totals in every thread of that block.
-template <int NV, class T>
-__device__ __forceinline__ bool last_block_total(T (&v)[NV], void* partv, unsigned* ticket, SegInfo sg) {
-  __shared__ T sh[NV][32];
-  __shared__ T tot[NV];
-  __shared__ int amlast;
-  T* part = static_cast<T*>(partv);
-  block_sum<NV, T>(v, sh);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) part[sg.lb * NV + k] = v[k];
-    __threadfence();
-    amlast = atomicAdd(ticket, 1u) == unsigned(sg.nb) - 1u;
-  }
-  __syncthreads();
-  if (!amlast) return false;
-  __threadfence();
-  T acc[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) acc[k] = T(0);
-  for (int b = threadIdx.x; b < sg.nb; b += blockDim.x)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) acc[k] += __ldcg(part + b * NV + k);
-  block_sum<NV, T>(acc, sh);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) tot[k] = acc[k];
-    *ticket = 0u;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = tot[k];
-  return true;
-}
-
-// Decision after the inner residual r and the preconditioned z are complete
-// (thread 0 of the system's last block): the first one of an inner solve sets
-// rho, later ones close an iteration as the persistent kernel's loop does.
-// Returns whether the inner loop continues.
-template <class T>
-__device__ __forceinline__ bool inner_decide(const StreamLaunch& a, T rz) {
-  StreamScal& c = *a.sc;
-  bool done = false;
-  const T rr = T(c.rr_new);
-  if (c.first) {
-    c.first = 0;
-    c.rho = double(rz);
-    done = !(rr > T(c.tgt));
-  } else {
-    c.it += 1;
-    if (!isfinite(rr) || !isfinite(rz)) {
-      c.fail |= ST_NONFINITE;
-      done = true;
-    } else if (rr <= T(c.tgt)) {
-      done = true;
-    } else if (c.it >= a.inner_cap) {
-      if (a.max_outer == 1) c.fail |= ST_NOT_CONVERGED;
-      done = true;
-    } else {
-      c.beta = double(rz / T(c.rho));
-      c.rho = double(rz);
-    }
-  }
-  if (done) {
-    c.stop = 1;
-    c.inner_total += c.it;
-  }
-  return !done;
-}
 
 #define SEG_BEGIN(src)                             \
   count_launch(src);                               \
@@ -438,22 +160,7 @@ __global__ void __launch_bounds__(kSB) st_rhs_kernel(const __grid_constant__ S s
     acc[0] += b;
     acc[1] += b * b;
   }
-  if (last_block_total<2, double>(acc, a.part, &a.sc->ticket, sg) && threadIdx.x == 0) {
-    StreamScal& c = *a.sc;
-    const double mean = a.project ? acc[0] / double(a.n) : 0.0;
-    double bb = a.project ? acc[1] - double(a.n) * mean * mean : acc[1];
-    if (bb < 0.0) bb = 0.0;
-    c.mean_b = mean;
-    c.bb = bb;
-    c.tol2 = a.tol * a.tol * bb;
-    c.outer = 0;
-    c.fail = 0;
-    c.skip = 0;
-    c.stop = 1;
-    c.inner_ran = 0;
-    c.inner_total = 0;
-    c.outer_total = 0;
-  }
+  if (last_block_total<2, double>(acc, a.part, &a.sc->ticket, sg) && threadIdx.x == 0) rhs_setup(a, acc[0], acc[1]);
 }
 
 // FP64 outer residual r = b - A x (b projected) and the outer decision
@@ -484,45 +191,8 @@ __global__ void __launch_bounds__(kSB) st_outer_kernel(const __grid_constant__ S
     acc[0] += r * r;
   }
   if (last_block_total<1, double>(acc, a.part, &c.ticket, sg) && threadIdx.x == 0) {
-    const double rr = acc[0];
-    c.rr64 = rr;
-    c.outer_total += 1;
-    bool done = false;
-    if (!isfinite(rr)) {
-      c.fail |= ST_NONFINITE;
-      done = true;
-    } else if (a.max_outer > 1 && rr <= c.tol2) {
-      done = true;
-    } else if (c.outer >= a.max_outer) {
-      if (a.max_outer > 1) c.fail |= ST_NOT_CONVERGED;
-      done = true;
-    } else if (!(rr > 0.0)) {
-      done = true;
-    }
-    if (done) {
-      c.inner_ran = 0;
-      c.stop = 1;
-      c.more = 0;
-      vote_outer(src, a, false, false);
-    } else {
-      c.scale = sqrt(rr);
-      // inner target relative to |r|^2: the FP32 solves follow the persistent
-      // mixed kernel; a single FP64 solve stops at |r| <= tol |b|, as the
-      // persistent FP64 kernel does
-      double tgt = a.tol_inner * a.tol_inner;
-      if (a.max_outer > 1) tgt = fmax(tgt, 0.25 * c.tol2 / rr);
-      else if (sizeof(T) == 8) tgt = c.tol2 / rr;
-      else if (a.warm) tgt = fmax(tgt, tgt * c.bb / rr);
-      c.tgt = tgt;
-      c.it = 0;
-      c.first = 1;
-      c.stop = 0;
-      c.inner_ran = 1;
-      c.beta = 0.0;
-      c.outer += 1;
-      c.more = a.max_outer > 1 ? 1 : 0;
-      vote_outer(src, a, true, a.max_outer > 1);
-    }
+    const bool on = outer_decide<T>(a, acc[0]);
+    vote_outer(src, a, on, on && a.max_outer > 1);
   }
 }
 
@@ -596,16 +266,7 @@ __global__ void __launch_bounds__(kSB) st_pq_kernel(const __grid_constant__ S sr
     acc[0] += pi * qi;
   }
   if (last_block_total<1, T>(acc, a.part, &c.ticket, sg) && threadIdx.x == 0) {
-    const T pq = acc[0];
-    bool active = true;
-    if (!(pq > T(0))) {       // breakdown: keep d, the outer pass decides
-      if (!isfinite(pq)) c.fail |= ST_NONFINITE;
-      c.stop = 1;
-      c.inner_total += c.it;
-      active = false;
-    } else {
-      c.alpha = double(T(c.rho) / pq);
-    }
+    const bool active = pq_decide<T>(a, acc[0]);   // a breakdown keeps d; the outer pass decides
     if (!active || kMany<S>) vote_inner(src, a, active);
   }
 }
@@ -895,12 +556,18 @@ int grid_for(int64_t threads) {
   return int(std::max<int64_t>(1, std::min<int64_t>(b, stream_grid_cap())));
 }
 
-// resident blocks per SM of kernel k at kSB threads, queried once and cached
-// (stream_prepare fills the cache before any capture)
+}  // namespace
+
+// ---- host helpers (declared in stream_rows.cuh; stream2.cu uses them too) -----
+
+namespace {
 std::mutex g_occ_mu;
 std::unordered_map<const void*, int> g_occ;
+}  // namespace
 
-int resident_blocks(const void* k) {
+// resident blocks per SM of kernel k at kSB threads, queried once and cached
+// (stream_prepare fills the cache before any capture)
+int stream_resident_blocks(const void* k) {
   std::lock_guard<std::mutex> g(g_occ_mu);
   auto it = g_occ.find(k);
   if (it != g_occ.end()) return it->second;
@@ -917,15 +584,15 @@ int resident_blocks(const void* k) {
 // grid of kernel k over `threads` grid-stride threads: at most one full wave
 // of resident blocks (a second partial wave would run its blocks' equal
 // shares of rows at a fraction of the occupancy)
-int fit(const void* k, int64_t threads) {
+int stream_fit(const void* k, int64_t threads) {
   const int64_t b = (threads + kSB - 1) / kSB;
-  const int64_t wave = int64_t(stream_grid_cap() / kBlocksPerSM) * resident_blocks(k);
+  const int64_t wave = int64_t(stream_grid_cap() / kBlocksPerSM) * stream_resident_blocks(k);
   return int(std::max<int64_t>(1, std::min(b, wave)));
 }
 
 // add a WHILE node after the current capture frontier of `cap` and return its
 // body graph; the capture continues after the node
-cudaError_t add_while(cudaStream_t cap, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+cudaError_t stream_add_while(cudaStream_t cap, cudaGraphConditionalHandle h, cudaGraph_t* body) {
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -945,12 +612,14 @@ cudaError_t add_while(cudaStream_t cap, cudaGraphConditionalHandle h, cudaGraph_
   return cudaStreamUpdateCaptureDependencies(cap, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
 }
 
-cudaGraph_t capture_graph(cudaStream_t s) {
+cudaGraph_t stream_capture_graph(cudaStream_t s) {
   cudaStreamCaptureStatus cs;
   cudaGraph_t g = nullptr;
   if (cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess) return nullptr;
   return cs == cudaStreamCaptureStatusActive ? g : nullptr;
 }
+
+namespace {
 
 // The launches of one solve (One) or of one batch of solves (Many): the
 // policies and grids of every kernel family.
@@ -984,12 +653,12 @@ struct Plan {
 #define ROWS_LAUNCH_T(KNAME, stream)                                                                   \
   do {                                                                                                 \
     if (P.many) KNAME<T, Many><<<P.bs->total_rows_blocks, kSB, 0, stream>>>(P.mk(P.bs->blk_rows));      \
-    else KNAME<T, One><<<fit((const void*)KNAME<T, One>, P.rows), kSB, 0, stream>>>(P.one);            \
+    else KNAME<T, One><<<stream_fit((const void*)KNAME<T, One>, P.rows), kSB, 0, stream>>>(P.one);            \
   } while (0)
 #define ROWS_LAUNCH_S(KNAME, stream)                                                                   \
   do {                                                                                                 \
     if (P.many) KNAME<Many><<<P.bs->total_rows_blocks, kSB, 0, stream>>>(P.mk(P.bs->blk_rows));         \
-    else KNAME<One><<<fit((const void*)KNAME<One>, P.rows), kSB, 0, stream>>>(P.one);                  \
+    else KNAME<One><<<stream_fit((const void*)KNAME<One>, P.rows), kSB, 0, stream>>>(P.one);                  \
   } while (0)
 
 template <class T>
@@ -1006,17 +675,17 @@ void enqueue_vcycle(const Plan<T>& P, cudaStream_t s) {
     } else {
       if (l == 0)
         st_vc_res_kernel<T, VcOne<T>, One, true>
-            <<<fit((const void*)st_vc_res_kernel<T, VcOne<T>, One, true>, P.tA[l]), kSB, 0, s>>>(P.vone, P.one, l);
+            <<<stream_fit((const void*)st_vc_res_kernel<T, VcOne<T>, One, true>, P.tA[l]), kSB, 0, s>>>(P.vone, P.one, l);
       else
         st_vc_res_kernel<T, VcOne<T>, One, false>
-            <<<fit((const void*)st_vc_res_kernel<T, VcOne<T>, One, false>, P.tA[l]), kSB, 0, s>>>(P.vone, P.one, l);
+            <<<stream_fit((const void*)st_vc_res_kernel<T, VcOne<T>, One, false>, P.tA[l]), kSB, 0, s>>>(P.vone, P.one, l);
       if (P.vone.H.L[l].R.lpr > 32)
         st_vc_restrict_kernel<T, VcOne<T>, One, kRowsAll>
-            <<<fit((const void*)st_vc_restrict_kernel<T, VcOne<T>, One, kRowsAll>, P.tR[l]), kSB, 0, s>>>(P.vone,
+            <<<stream_fit((const void*)st_vc_restrict_kernel<T, VcOne<T>, One, kRowsAll>, P.tR[l]), kSB, 0, s>>>(P.vone,
                                                                                                    P.one, l);
       else
         st_vc_restrict_kernel<T, VcOne<T>, One, kRowsAll & ~kRowsCsrBlock>
-            <<<fit((const void*)st_vc_restrict_kernel<T, VcOne<T>, One, kRowsAll & ~kRowsCsrBlock>, P.tR[l]), kSB, 0,
+            <<<stream_fit((const void*)st_vc_restrict_kernel<T, VcOne<T>, One, kRowsAll & ~kRowsCsrBlock>, P.tR[l]), kSB, 0,
                s>>>(P.vone, P.one, l);
     }
   }
@@ -1024,7 +693,7 @@ void enqueue_vcycle(const Plan<T>& P, cudaStream_t s) {
     st_vc_coarse_kernel<T, VcMany<T>, Many><<<P.bs->total_coarse, kSB, 0, s>>>(P.vmk(P.bs->blk_coarse),
                                                                                 P.mk(P.bs->blk_rows));
   else
-    st_vc_coarse_kernel<T, VcOne<T>, One><<<fit((const void*)st_vc_coarse_kernel<T, VcOne<T>, One>, P.tcoarse), kSB,
+    st_vc_coarse_kernel<T, VcOne<T>, One><<<stream_fit((const void*)st_vc_coarse_kernel<T, VcOne<T>, One>, P.tcoarse), kSB,
                                             0, s>>>(P.vone, P.one);
   for (int l = P.nlev - 1; l >= 0; --l) {
     if (P.many) {
@@ -1036,14 +705,14 @@ void enqueue_vcycle(const Plan<T>& P, cudaStream_t s) {
       else
         st_vc_post_kernel<T, VcMany<T>, Many, false><<<P.bs->total_A[l], kSB, 0, s>>>(P.vmk(P.bs->blk_A[l]), m, l);
     } else {
-      st_vc_prolong_kernel<T, VcOne<T>, One><<<fit((const void*)st_vc_prolong_kernel<T, VcOne<T>, One>, P.tP[l]),
+      st_vc_prolong_kernel<T, VcOne<T>, One><<<stream_fit((const void*)st_vc_prolong_kernel<T, VcOne<T>, One>, P.tP[l]),
                                                kSB, 0, s>>>(P.vone, P.one, l);
       if (l == 0)
         st_vc_post_kernel<T, VcOne<T>, One, true>
-            <<<fit((const void*)st_vc_post_kernel<T, VcOne<T>, One, true>, P.rows), kSB, 0, s>>>(P.vone, P.one, l);
+            <<<stream_fit((const void*)st_vc_post_kernel<T, VcOne<T>, One, true>, P.rows), kSB, 0, s>>>(P.vone, P.one, l);
       else
         st_vc_post_kernel<T, VcOne<T>, One, false>
-            <<<fit((const void*)st_vc_post_kernel<T, VcOne<T>, One, false>, P.tA[l]), kSB, 0, s>>>(P.vone, P.one, l);
+            <<<stream_fit((const void*)st_vc_post_kernel<T, VcOne<T>, One, false>, P.tA[l]), kSB, 0, s>>>(P.vone, P.one, l);
     }
   }
 }
@@ -1051,7 +720,7 @@ void enqueue_vcycle(const Plan<T>& P, cudaStream_t s) {
 // the solve's kernels and loops, appended to the capture of `st`
 template <class T>
 cudaError_t enqueue_solve(Plan<T>& P, cudaStream_t st, const cudaStream_t* side) {
-  cudaGraph_t g = capture_graph(st);
+  cudaGraph_t g = stream_capture_graph(st);
   if (!g) return cudaErrorStreamCaptureUnsupported;
   cudaGraphConditionalHandle ho, hi;
   cudaError_t e = cudaGraphConditionalHandleCreate(&ho, g, 1, cudaGraphCondAssignDefault);
@@ -1062,7 +731,7 @@ cudaError_t enqueue_solve(Plan<T>& P, cudaStream_t st, const cudaStream_t* side)
   ROWS_LAUNCH_T(st_rhs_kernel, st);
   if (P.many) st_batch_cond_kernel<<<1, kSB, 0, st>>>(P.mk(P.bs->blk_rows), 0, 0u);
   cudaGraph_t ob = nullptr;
-  if ((e = add_while(st, ho, &ob)) != cudaSuccess) return e;
+  if ((e = stream_add_while(st, ho, &ob)) != cudaSuccess) return e;
   // outer body: residual and decision, inner start, inner loop, x update
   if ((e = cudaStreamBeginCaptureToGraph(side[0], ob, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
       cudaSuccess)
@@ -1072,7 +741,7 @@ cudaError_t enqueue_solve(Plan<T>& P, cudaStream_t st, const cudaStream_t* side)
   if (P.amg) enqueue_vcycle<T>(P, side[0]);
   if (P.many) st_batch_cond_kernel<<<1, kSB, 0, side[0]>>>(P.mk(P.bs->blk_rows), 1, 0u);
   cudaGraph_t ib = nullptr;
-  e = add_while(side[0], hi, &ib);
+  e = stream_add_while(side[0], hi, &ib);
   if (e == cudaSuccess)
     e = cudaStreamBeginCaptureToGraph(side[1], ib, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
@@ -1096,33 +765,6 @@ cudaError_t enqueue_solve(Plan<T>& P, cudaStream_t st, const cudaStream_t* side)
   ROWS_LAUNCH_S(st_shift_kernel, st);
   ROWS_LAUNCH_S(st_finish_kernel, st);
   return cudaGetLastError();
-}
-
-// Outside a capture the solve is captured into a graph of its own, launched
-// and destroyed; inside one it is appended.
-template <class F>
-cudaError_t run_captured(cudaStream_t st, F&& body) {
-  cudaStreamCaptureStatus cs;
-  cudaError_t e = cudaStreamIsCapturing(st, &cs);
-  if (e != cudaSuccess) return e;
-  if (cs == cudaStreamCaptureStatusActive) return body();
-  if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
-  const cudaError_t r = body();
-  cudaGraph_t g = nullptr;
-  e = cudaStreamEndCapture(st, &g);
-  if (r != cudaSuccess) {
-    if (g) cudaGraphDestroy(g);
-    return r;
-  }
-  if (e != cudaSuccess) return e;
-  cudaGraphExec_t ex = nullptr;
-  e = cudaGraphInstantiate(&ex, g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) return e;
-  e = cudaGraphUpload(ex, st);
-  if (e == cudaSuccess) e = cudaGraphLaunch(ex, st);
-  cudaGraphExecDestroy(ex);   // released once the launch completes
-  return e;
 }
 
 // The same solve with its loops on the host (a profiling form: every kernel
@@ -1216,7 +858,7 @@ void prepare_family() {
                         (const void*)st_vc_prolong_kernel<T, VcOne<T>, One>,
                         (const void*)st_vc_post_kernel<T, VcOne<T>, One, true>,
                         (const void*)st_vc_post_kernel<T, VcOne<T>, One, false>})
-    resident_blocks(k);
+    stream_resident_blocks(k);
 }
 }  // namespace
 
@@ -1224,8 +866,9 @@ void stream_prepare() {
   stream_grid_cap();
   prepare_family<float>();
   prepare_family<double>();
-  resident_blocks((const void*)st_shift_kernel<One>);
-  resident_blocks((const void*)st_finish_kernel<One>);
+  stream_resident_blocks((const void*)st_shift_kernel<One>);
+  stream_resident_blocks((const void*)st_finish_kernel<One>);
+  stream_prepare_pair();
 }
 
 cudaError_t stream_solve(const StreamLaunch& a, int f32, const AmgDevF* M32, const AmgDev* M64, cudaStream_t st,
@@ -1233,11 +876,11 @@ cudaError_t stream_solve(const StreamLaunch& a, int f32, const AmgDevF* M32, con
   if (f32) {
     Plan<float> P = one_plan<float>(a, M32);
     if (a.host_loop) return host_loop_solve<float>(P, st);
-    return run_captured(st, [&]() { return enqueue_solve<float>(P, st, side); });
+    return stream_run_captured(st, [&]() { return enqueue_solve<float>(P, st, side); });
   }
   Plan<double> P = one_plan<double>(a, M64);
   if (a.host_loop) return host_loop_solve<double>(P, st);
-  return run_captured(st, [&]() { return enqueue_solve<double>(P, st, side); });
+  return stream_run_captured(st, [&]() { return enqueue_solve<double>(P, st, side); });
 }
 
 cudaError_t stream_solve_batch(const BatchSolve& b, cudaStream_t st, const cudaStream_t* side) {
@@ -1254,7 +897,7 @@ cudaError_t stream_solve_batch(const BatchSolve& b, cudaStream_t st, const cudaS
     P.vmany.nseg = b.nseg;
     P.nlev = b.nlev_max;
     P.amg = b.nlev_max > 0;
-    return run_captured(st, [&]() { return enqueue_solve<T>(P, st, side); });
+    return stream_run_captured(st, [&]() { return enqueue_solve<T>(P, st, side); });
   };
   return b.f32 ? run(float{}) : run(double{});
 }
