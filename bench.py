@@ -178,7 +178,8 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("pcg.cu", "amg.cu", "mixed.cu", "stream.cu", "sparse.cuh", "vcycle.cuh", "bd_internal.h"):
+    for f in ("pcg.cu", "amg.cu", "mixed.cu", "stream.cu", "stream2.cu", "stream_rows.cuh", "sparse.cuh",
+              "vcycle.cuh", "bd_internal.h"):
         path = os.path.join(ROOT, "paper_2510_27447_gb300", "csrc", f)
         if os.path.exists(path):
             with open(path, "rb") as fh:
