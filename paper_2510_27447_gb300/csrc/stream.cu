@@ -255,12 +255,15 @@ __global__ void __launch_bounds__(kSB) st_pq_kernel(const __grid_constant__ S sr
   T acc[1] = {T(0)};
   const bool v4 = sizeof(T) == 4 && a.col4 != nullptr;
   for (int i = gt; i < a.n; i += gs) {
+    // the row's vector entries are requested before its product
     const T zi = z[i];
+    const T pv = first ? T(0) : p[i];
+    const T qv = first ? T(0) : q[i];
     T az = v4 ? T(srow4<T>(a.sptr4, a.sw4, a.col4, static_cast<const float*>(a.valT4), z, i))
               : srow<true, T, T>(a.sptr, a.swidth, a.col, val, z, i);
     if (a.dextra) az += T(a.dextra[i]) * zi;
-    const T pi = first ? zi : zi + beta * p[i];
-    const T qi = first ? az : az + beta * q[i];
+    const T pi = first ? zi : zi + beta * pv;
+    const T qi = first ? az : az + beta * qv;
     p[i] = pi;
     q[i] = qi;
     acc[0] += pi * qi;

@@ -94,7 +94,11 @@ __device__ __forceinline__ void pair_vote_outer(const StreamLaunch& a, bool inne
 // loaded once, and each system's sum is formed in the order the single-system
 // product (srow / srow4 / level_rows) forms it.
 
-template <int M, bool STREAMOP, class V, class X>
+// PIPE: the next chunk's indices and values are requested before this
+// chunk's gathers (two chunks of the operator stream in flight) -- faster for
+// the FP64 products of the right-hand side and the refinement residual,
+// slower for the FP32 level products, whose extra registers cost occupancy
+template <int M, bool STREAMOP, class V, class X, bool PIPE = false>
 __device__ __forceinline__ void srow_m(const int64_t* __restrict__ sptr, const int* __restrict__ sw,
                                        const int* __restrict__ col, const V* __restrict__ val,
                                        const X* __restrict__ x0, const X* __restrict__ x1, int i, X (&acc)[2]) {
@@ -104,17 +108,24 @@ __device__ __forceinline__ void srow_m(const int64_t* __restrict__ sptr, const i
   acc[0] = X(0);
   acc[1] = X(0);
   constexpr int CH = 4;
-  for (int k0 = 0; k0 < w; k0 += CH) {
-    int c[CH];
-    V v[CH];
-    X g0[CH], g1[CH];
+  int c[CH];
+  V v[CH];
+  auto load = [&](int k0, int (&cc)[CH], V (&vv)[CH]) {
 #pragma unroll
     for (int k = 0; k < CH; ++k)
       if (k0 + k < w) {
         const int64_t e = base + 32 * (k0 + k);
-        c[k] = STREAMOP ? ld_stream(col + e) : __ldg(col + e);
-        v[k] = STREAMOP ? ld_stream(val + e) : __ldg(val + e);
+        cc[k] = STREAMOP ? ld_stream(col + e) : __ldg(col + e);
+        vv[k] = STREAMOP ? ld_stream(val + e) : __ldg(val + e);
       }
+  };
+  if (PIPE) load(0, c, v);
+  for (int k0 = 0; k0 < w; k0 += CH) {
+    int cn[CH];
+    V vn[CH];
+    if (!PIPE) load(k0, c, v);
+    else if (k0 + CH < w) load(k0 + CH, cn, vn);
+    X g0[CH], g1[CH];
 #pragma unroll
     for (int k = 0; k < CH; ++k)
       if (k0 + k < w) {
@@ -126,6 +137,12 @@ __device__ __forceinline__ void srow_m(const int64_t* __restrict__ sptr, const i
       if (k0 + k < w) {
         if (ON(0)) acc[0] += X(v[k]) * g0[k];
         if (ON(1)) acc[1] += X(v[k]) * g1[k];
+      }
+    if (PIPE)
+#pragma unroll
+      for (int k = 0; k < CH; ++k) {
+        c[k] = cn[k];
+        v[k] = vn[k];
       }
   }
 }
@@ -306,7 +323,7 @@ __global__ void __launch_bounds__(kSB) st2_rhs_kernel(const __grid_constant__ Pa
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int i = gt; i < a.n; i += gs) {
     double sp[2];
-    srow_m<3, true, double, double>(a.sptr, a.swidth, a.col, a.val1, P.a[0].va, P.a[1].va, i, sp);
+    srow_m<3, true, double, double, true>(a.sptr, a.swidth, a.col, a.val1, P.a[0].va, P.a[1].va, i, sp);
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const StreamLaunch& ak = P.a[k];
@@ -354,7 +371,7 @@ __global__ void __launch_bounds__(kSB) st2_outer_kernel(const __grid_constant__ 
     const double mean[2] = {P.a[0].sc->mean_b, P.a[1].sc->mean_b};
     for (int i = gt; i < a.n; i += gs) {
       double ax[2];
-      srow_m<M, true, double, double>(a.sptr, a.swidth, a.col, a.valA, P.a[0].x, P.a[1].x, i, ax);
+      srow_m<M, true, double, double, true>(a.sptr, a.swidth, a.col, a.valA, P.a[0].x, P.a[1].x, i, ax);
 #pragma unroll
       for (int k = 0; k < 2; ++k)
         if (ON(k)) {
@@ -424,10 +441,14 @@ __global__ void __launch_bounds__(kSB) st2_pq_kernel(const __grid_constant__ Pai
     const T beta[2] = {T(P.a[0].sc->beta), T(P.a[1].sc->beta)};
     const bool v4 = sizeof(T) == 4 && a.col4 != nullptr;
     for (int i = gt; i < a.n; i += gs) {
-      T zi[2], az[2];
+      T zi[2], az[2], pv[2], qv[2];   // the row's vector entries, requested before its products
 #pragma unroll
       for (int k = 0; k < 2; ++k)
-        if (ON(k)) zi[k] = z[k][i];
+        if (ON(k)) {
+          zi[k] = z[k][i];
+          pv[k] = first[k] ? T(0) : static_cast<const T*>(P.a[k].p)[i];
+          qv[k] = first[k] ? T(0) : static_cast<const T*>(P.a[k].q)[i];
+        }
       if (v4) {
         float azf[2];
         srow4_m<M, true, float>(a.sptr4, a.sw4, a.col4, static_cast<const float*>(a.valT4),
@@ -442,8 +463,8 @@ __global__ void __launch_bounds__(kSB) st2_pq_kernel(const __grid_constant__ Pai
         if (ON(k)) {
           T* p = static_cast<T*>(P.a[k].p);
           T* q = static_cast<T*>(P.a[k].q);
-          const T pi = first[k] ? zi[k] : zi[k] + beta[k] * p[i];
-          const T qi = first[k] ? az[k] : az[k] + beta[k] * q[i];
+          const T pi = first[k] ? zi[k] : zi[k] + beta[k] * pv[k];
+          const T qi = first[k] ? az[k] : az[k] + beta[k] * qv[k];
           p[i] = pi;
           q[i] = qi;
           acc[k] += pi * qi;
