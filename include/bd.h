@@ -158,12 +158,14 @@ typedef struct {
                             the entries and the level has at least 2^17 rows averaging at most 96
                             entries, else CSR; 1: SELL-32 whenever the padding allows; -1:
                             always CSR; BD_ERR_ARG otherwise */
-  int pair_solve;        /* mixed precision with the AMG preconditioner: the two elliptic
-                            solves of every sweep after the first (the constraint at two
-                            Gauss-Lobatto nodes, Sec. 3.3.2) run as one two-system solve whose
-                            operator passes serve both right-hand sides -- one cooperative
-                            kernel in the persistent form, one kernel chain in the streaming
-                            form.  0 (default): on; -1: one solve after the other (each
+  int pair_solve;        /* AMG-preconditioned elliptic solves: the two elliptic solves of
+                            every sweep after the first (the constraint at two Gauss-Lobatto
+                            nodes, Sec. 3.3.2) run as one two-system solve whose operator
+                            passes serve both right-hand sides -- in mixed precision one
+                            cooperative kernel (persistent form) or one kernel chain
+                            (streaming form), in FP64 one kernel chain (streaming form; the
+                            persistent FP64 form solves one after the other).  0 (default):
+                            on; -1: one solve after the other (each
                             system's arithmetic is the same either way; the reductions are
                             formed over different block partitions); BD_ERR_ARG otherwise */
 } bd_opts_t;

@@ -78,6 +78,8 @@ struct bd_state {
   AmgDev amg{};
   AmgDevF amgf{};                 // FP32 copy of the hierarchy (mixed path)
   AmgDevF amgf2{};                // its operators with a second set of level vectors (two-RHS solves)
+  AmgDev amg2{};                  // FP64 streaming: the hierarchy with a second set of level vectors (two-system solves)
+  bool pair64 = false;            // amg2 and two-system FP64 streaming workspaces are set up
   AmgDevF* d_amgf2 = nullptr;
   bool two_rhs = false;           // sweeps >= 2 solve their elliptic pair in one launch (mixed AMG path)
   float* partf8 = nullptr;
@@ -157,6 +159,7 @@ struct bd_state {
   double* spart = nullptr;
   double *sb64 = nullptr, *sr64 = nullptr;
   double *sr = nullptr, *sz = nullptr, *sp = nullptr, *sq = nullptr, *sd = nullptr, *sinvd = nullptr;
+  int s64_sys = 1;                // systems the FP64 workspaces above (but sinvd) hold
   cudaStream_t side[2] = {nullptr, nullptr};
   int pcg_grid = 1, pcg_block = 512, pcg_max = 1;
   int tier = 0;                            // solver register tier (kSolverTierBlock)
@@ -403,7 +406,7 @@ StreamLaunch stream_base(bd_state* s, int n) {
 
 // the streaming elliptic solve u = E(v) over all N rows (v holds every node);
 // k = 1: the second system of a pair, whose vectors are the second halves of
-// the mixed two-system workspaces and whose scalars are d_sc[1]
+// the two-system workspaces and whose scalars are d_sc[1]
 StreamLaunch elliptic_launch(bd_state* s, const double* v, double* u, int k = 0) {
   StreamLaunch A = stream_base(s, int(s->N));
   const bool mixed = s->precision == BD_MIXED;
@@ -430,11 +433,10 @@ StreamLaunch elliptic_launch(bd_state* s, const double* v, double* u, int k = 0)
     A.sc = s->d_sc + 1;
     A.b64 += N;
     A.r64 += N;
-    A.r = static_cast<float*>(A.r) + N;
-    A.z = static_cast<float*>(A.z) + N;
-    A.p = static_cast<float*>(A.p) + N;
-    A.q = static_cast<float*>(A.q) + N;
-    A.d = static_cast<float*>(A.d) + N;
+    auto second = [&](void*& v) {
+      v = mixed ? static_cast<void*>(static_cast<float*>(v) + N) : static_cast<void*>(static_cast<double*>(v) + N);
+    };
+    for (void** v : {&A.r, &A.z, &A.p, &A.q, &A.d}) second(*v);
   }
   return A;
 }
@@ -493,13 +495,17 @@ int elliptic(bd_state* s, const double* v, double* u) {
 // u1 = E(v1) and u2 = E(v2): one two-RHS launch on the mixed AMG path, else
 // two solves
 int elliptic2(bd_state* s, const double* v1, double* u1, const double* v2, double* u2) {
-  if (!s->two_rhs || s->precision != BD_MIXED || !s->use_amg || s->opts.pair_solve < 0) {
+  const bool mixed = s->precision == BD_MIXED;
+  // pairs: mixed AMG solves in both forms, FP64 AMG solves in the streaming form
+  const bool pair = s->use_amg && s->opts.pair_solve >= 0 && (mixed ? s->two_rhs : s->streaming && s->pair64);
+  if (!pair) {
     const int r = elliptic(s, v1, u1);
     if (r != BD_OK) return r;
     return elliptic(s, v2, u2);
   }
   if (s->streaming) {   // one chain for both systems (stream2.cu)
     if (s->NT < s->N) {
+      if (!s->vfull || !s->vfull2) return fail(s, BD_ERR_ARG, "two-system solve without its full-length potentials");
       Timed t(s, BD_K_COMBINE, 2);
       const int* gate = s->opts.sweep_tol > 0 ? s->gate : nullptr;
       CK(launch_copy(s->NT, v1, s->vfull, s->stream, gate));
@@ -509,8 +515,12 @@ int elliptic2(bd_state* s, const double* v1, double* u1, const double* v2, doubl
     }
     const StreamLaunch A[2] = {elliptic_launch(s, v1, u1, 0), elliptic_launch(s, v2, u2, 1)};
     Timed t(s, BD_K_PCG_ELLIPTIC, 0);   // its kernels count themselves on the device
-    CK(stream_solve_pair(A, s->amgf, s->amgf2, s->d_stats + 7, s->d_stats + 9, s->d_stats + 10, s->stream,
-                         s->side));
+    if (mixed)
+      CK(stream_solve_pair(A, s->amgf, s->amgf2, s->d_stats + 7, s->d_stats + 9, s->d_stats + 10, s->stream,
+                           s->side));
+    else
+      CK(stream_solve_pair(A, s->amg, s->amg2, s->d_stats + 7, s->d_stats + 9, s->d_stats + 10, s->stream,
+                           s->side));
     return BD_OK;
   }
   PcgLaunch P = pcg_base(s);
@@ -759,6 +769,20 @@ int setup_amg(bd_state* s, const HostOps& H) {
   if (!M.cinv || !alloc_n(s, &M.bc, AH.nc) || !alloc_n(s, &M.xc, AH.nc) ||
       cudaStreamSynchronize(s->stream) != cudaSuccess)
     return fail(s, BD_ERR_OOM, "AMG upload failed");
+  if (s->precision == BD_FP64 && s->streaming && s->opts.pair_solve >= 0) {
+    // the same hierarchy with its own level vectors: the second system of the
+    // streaming two-system solves (sweeps >= 2)
+    AmgDev& G = s->amg2;
+    G = M;
+    bool ok2 = alloc_n(s, &G.bc, AH.nc) && alloc_n(s, &G.xc, AH.nc);
+    for (int l = 0; ok2 && l < G.nlev; ++l) {
+      const int64_t n = AH.lev[l].A.n;
+      ok2 = alloc_n(s, &G.L[l].x, n) && alloc_n(s, &G.L[l].r, n);
+      if (ok2 && l > 0) ok2 = alloc_n(s, &G.L[l].b, n) && alloc_n(s, &G.L[l].y, n);
+    }
+    if (!ok2) return fail(s, BD_ERR_OOM, "AMG upload failed");
+    s->pair64 = true;
+  }
   if (s->precision == BD_MIXED) {
     auto sell_devf = [&](const HCsr& Mh, SellDevT<float>* out) {
       const SellHost S = sell_from_csr(Mh, s->streaming ? s->opts.wide_sell + 1 : 0);
@@ -1916,9 +1940,16 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     stream_prepare();   // kernel occupancies, queried outside any capture
     ok = alloc_n(s, reinterpret_cast<char**>(&s->d_sc), int64_t(2 * sizeof(StreamScal))) &&
          alloc_n(s, &s->spart, int64_t(stream_grid_cap()) * 4);
-    if (ok && s->precision == BD_FP64)
-      ok = alloc_n(s, &s->sb64, N) && alloc_n(s, &s->sr64, N) && alloc_n(s, &s->sr, N) && alloc_n(s, &s->sz, N) &&
-           alloc_n(s, &s->sp, N) && alloc_n(s, &s->sq, N) && alloc_n(s, &s->sd, N) && alloc_n(s, &s->sinvd, N);
+    if (ok && s->precision == BD_FP64) {
+      // b, r64, r, z, p, q, d hold two systems (two-system elliptic solves)
+      const int64_t N2 = s->opts.pair_solve >= 0 ? 2 * N : N;
+      s->s64_sys = N2 == N ? 1 : 2;
+      ok = alloc_n(s, &s->sb64, N2) && alloc_n(s, &s->sr64, N2) && alloc_n(s, &s->sr, N2) &&
+           alloc_n(s, &s->sz, N2) && alloc_n(s, &s->sp, N2) && alloc_n(s, &s->sq, N2) && alloc_n(s, &s->sd, N2) &&
+           alloc_n(s, &s->sinvd, N);
+      // a bath mesh's second system gathers its potential over all nodes too
+      if (ok && N2 > N && NT < N && !s->vfull2) ok = alloc_n(s, &s->vfull2, N);
+    }
     for (cudaStream_t& x : s->side)
       if (ok && cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
@@ -2008,8 +2039,9 @@ int bd_create(const bd_mesh_t* mesh, const bd_cond_t* cond, bd_ionic_t model, co
     if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, 2 * N * 4, s->stream);
   if (e == cudaSuccess && s->invd32) e = cudaMemsetAsync(s->invd32, 0, N * 4, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->bar, 0, 8, s->stream);
-  for (double* v : {s->sb64, s->sr64, s->sr, s->sz, s->sp, s->sq, s->sd, s->sinvd})
-    if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, N * 8, s->stream);
+  for (double* v : {s->sb64, s->sr64, s->sr, s->sz, s->sp, s->sq, s->sd})
+    if (e == cudaSuccess && v) e = cudaMemsetAsync(v, 0, s->s64_sys * N * 8, s->stream);
+  if (e == cudaSuccess && s->sinvd) e = cudaMemsetAsync(s->sinvd, 0, N * 8, s->stream);
   if (e == cudaSuccess && s->d_sc) e = cudaMemsetAsync(s->d_sc, 0, 2 * sizeof(StreamScal), s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, 4, s->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s->d_stats, 0, 128, s->stream);
@@ -2453,6 +2485,9 @@ size_t bd_footprint_bytes(const bd_mesh_t* mesh, bd_ionic_t model, const bd_opts
       o.cg_cluster == 0 && (o.streaming >= 1 || (o.streaming == 0 && nnz >= double(kStreamNnz)));
   if (streaming) {
     extra += N * 8 * 8;
+    // FP64 two-system solves: second halves of seven workspaces and a second
+    // set of AMG level vectors
+    if (!mixed && amg && o.pair_solve >= 0) extra += N * 8 * 7 + N * 8 * 2.6;
     if (mixed && o.vec4 >= 0) extra += (nnz * 5 + lev) * 8 * 1.15;
   }
   return size_t(mat + st + packs + extra) + (size_t(1) << 20);
@@ -2635,7 +2670,7 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
       // r32 and d32 out) and the update x += s d (x in and out, d in)
       b += outer * ((ell ? spmv(8.0) + 3.0 * 8.0 * n : 2.0 * 8.0 * n) + 16.0 * n + 20.0 * n);
     }
-    if (ell && mixed && s->use_amg) b -= pairs * nnz * (vb + 4);   // shared operator pass
+    if (ell && s->use_amg) b -= pairs * nnz * (vb + 4);            // shared operator pass
     if (ell) b -= pairs64 * nnz * (8.0 + 4.0);                     // shared FP64 products (A_i, A_ie)
     out->alg_bytes[k] = b;
   }
@@ -2648,8 +2683,8 @@ int bd_profile_steps(bd_state_t* s, double dt, int M, int K, int n_steps, bd_pro
     out->vcycle_bytes = cycles * s->amg_cycle_bytes[v];
     out->coarse_bytes = cycles * s->amg_coarse_bytes[v];
     const double ncc = vb * double(s->amg.nc) * double(s->amg.nc);   // the dense coarse inverse
-    if (mixed) out->vcycle_bytes -= (pairs + pairsc) * (s->amg_cycle_opbytes[v] - ncc);
-    if (mixed && s->streaming) out->coarse_bytes -= (pairs + pairsc) * ncc;   // read once for both systems
+    out->vcycle_bytes -= (pairs + pairsc) * (s->amg_cycle_opbytes[v] - ncc);
+    if (s->streaming) out->coarse_bytes -= (pairs + pairsc) * ncc;   // read once for both systems
   }
   return read_status(s);
 }

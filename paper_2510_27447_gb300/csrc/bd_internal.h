@@ -483,9 +483,12 @@ int stream_grid(int64_t rows);
 // hierarchy with system 0's / system 1's level vectors (the same operators).
 // pair_acc counts the inner iterations in which both systems advanced,
 // pair64_acc the FP64 operator passes (right-hand side, refinement residual)
-// and pairc_acc the first V-cycles of an inner solve shared by both.  FP32
-// inner iterations; cudaErrorInvalidValue for any other form.
+// and pairc_acc the first V-cycles of an inner solve shared by both.  Inner
+// iterations in FP32 (AmgDevF: the mixed path) or FP64 (AmgDev);
+// cudaErrorInvalidValue for any other form.
 cudaError_t stream_solve_pair(const StreamLaunch (&a)[2], const AmgDevF& H0, const AmgDevF& H1, long long* pair_acc,
+                              long long* pair64_acc, long long* pairc_acc, cudaStream_t st, const cudaStream_t* side);
+cudaError_t stream_solve_pair(const StreamLaunch (&a)[2], const AmgDev& H0, const AmgDev& H1, long long* pair_acc,
                               long long* pair64_acc, long long* pairc_acc, cudaStream_t st, const cudaStream_t* side);
 // query (outside any capture) the resident blocks of the pair kernels
 void stream_prepare_pair();

@@ -939,24 +939,21 @@ void prepare_pair_family() {
     stream_resident_blocks(k);
 }
 
-}  // namespace
-
-void stream_prepare_pair() { prepare_pair_family<float>(); }
-
-cudaError_t stream_solve_pair(const StreamLaunch (&a)[2], const AmgDevF& H0, const AmgDevF& H1, long long* pair_acc,
-                              long long* pair64_acc, long long* pairc_acc, cudaStream_t st, const cudaStream_t* side) {
+template <class T>
+cudaError_t solve_pair(const StreamLaunch (&a)[2], const AmgDevT<T>& H0, const AmgDevT<T>& H1, long long* pair_acc,
+                       long long* pair64_acc, long long* pairc_acc, cudaStream_t st, const cudaStream_t* side) {
   // the form built here: the AMG-preconditioned, warm-started elliptic solve
   for (int k = 0; k < 2; ++k)
     if (!a[k].use_amg || !a[k].warm || a[k].rl || a[k].val2 || a[k].dextra || !a[k].val1 || a[k].n != a[0].n ||
         a[k].pin != a[0].pin || a[k].sc == a[1 - k].sc)
       return cudaErrorInvalidValue;
   if (H0.nlev <= 0 || H1.nlev != H0.nlev) return cudaErrorInvalidValue;
-  PairPlan<float> Q;
-  Pair<float>& P = Q.P;
+  PairPlan<T> Q;
+  Pair<T>& P = Q.P;
   P.a[0] = a[0];
   P.a[1] = a[1];
   P.H = H0;
-  for (int l = 0; l < H0.nlev; ++l) P.v1[l] = LevVec<float>{H1.L[l].x, H1.L[l].b, H1.L[l].r, H1.L[l].y};
+  for (int l = 0; l < H0.nlev; ++l) P.v1[l] = LevVec<T>{H1.L[l].x, H1.L[l].b, H1.L[l].r, H1.L[l].y};
   P.bc1 = H1.bc;
   P.xc1 = H1.xc;
   P.pair_acc = pair_acc;
@@ -976,8 +973,25 @@ cudaError_t stream_solve_pair(const StreamLaunch (&a)[2], const AmgDevF& H0, con
     Q.tP[l] = level_threads(H0.L[l].P);
   }
   Q.tcoarse = int64_t(std::max(1, H0.nc)) * 32;
-  if (a[0].host_loop) return host_loop_pair<float>(Q, st);
-  return stream_run_captured(st, [&]() { return enqueue_pair<float>(Q, st, side); });
+  if (a[0].host_loop) return host_loop_pair<T>(Q, st);
+  return stream_run_captured(st, [&]() { return enqueue_pair<T>(Q, st, side); });
+}
+
+}  // namespace
+
+void stream_prepare_pair() {
+  prepare_pair_family<float>();
+  prepare_pair_family<double>();
+}
+
+cudaError_t stream_solve_pair(const StreamLaunch (&a)[2], const AmgDevF& H0, const AmgDevF& H1, long long* pair_acc,
+                              long long* pair64_acc, long long* pairc_acc, cudaStream_t st, const cudaStream_t* side) {
+  return solve_pair<float>(a, H0, H1, pair_acc, pair64_acc, pairc_acc, st, side);
+}
+
+cudaError_t stream_solve_pair(const StreamLaunch (&a)[2], const AmgDev& H0, const AmgDev& H1, long long* pair_acc,
+                              long long* pair64_acc, long long* pairc_acc, cudaStream_t st, const cudaStream_t* side) {
+  return solve_pair<double>(a, H0, H1, pair_acc, pair64_acc, pairc_acc, st, side);
 }
 
 }  // namespace bd

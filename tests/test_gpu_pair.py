@@ -1,7 +1,8 @@
 """The two-system elliptic solve of the streaming form: from the second sweep
 on, Algorithm 2 (Sec. 3.3.2) solves the elliptic constraint at two
 Gauss-Lobatto nodes, and one chain of kernels serves both right-hand sides,
-loading each operator entry once (bd_opts_t.pair_solve).  Each system gets
+loading each operator entry once (bd_opts_t.pair_solve), in mixed precision
+and in FP64.  Each system gets
 what the single-system chain gives it, to the solver tolerance; whole steps
 match the oracle on a slab and on a bidomain-bath sheet; the host-driven
 loops give the same bits as the graph loops; the device-side sweep test
@@ -35,7 +36,8 @@ def _bath():
 
 
 def _run(w, X0, steps, K=2, **opt):
-    sim = gpu_sim(w, precision=binding.MIXED, streaming=opt.pop("streaming", 1), **opt)
+    opt.setdefault("precision", binding.MIXED)
+    sim = gpu_sim(w, streaming=opt.pop("streaming", 1), **opt)
     sim.set_initial(X0)
     for _ in range(steps):
         sim.step(w.dt, 3, K)
@@ -64,13 +66,30 @@ def test_pair_solve_matches_single_solves_and_the_oracle(mesh):
     assert rel(vp, Xo[0]) < 1e-3 and rel(up, uo) < 1e-3
 
 
-def test_pair_host_driven_loops_give_the_same_bits_as_graph_loops():
+@pytest.mark.parametrize("mesh", ["slab", "bath"])
+def test_fp64_pair_solve_matches_single_solves_and_the_oracle(mesh):
+    """The paper's precision: FP64 inner iterations on both systems."""
+    w = _slab() if mesh == "slab" else _bath()
+    X0 = rest_X(w)
+    tight = dict(precision=binding.FP64, cg_tol_e=1e-13, cg_tol_p=1e-13)
+    (vp, up, Xp), sp = _run(w, X0, w.n_steps, **tight)
+    (vs, us, Xs), ss = _run(w, X0, w.n_steps, pair_solve=-1, **tight)
+    assert sp["streaming"] == 1 and sp["amg_levels"] >= 1
+    assert sp["cg_solves_e"] == ss["cg_solves_e"] > 0
+    assert sp["kernel_launches"] < ss["kernel_launches"]
+    assert rel(up, us) < 1e-9 and rel(Xp, Xs) < 1e-10
+    Xo, uo, _ = OB.run(oracle_problem(w), X0, w.n_steps, w.dt, 3, 2)
+    assert rel(Xp, Xo) < 1e-9 and rel(up, uo) < 1e-8
+
+
+@pytest.mark.parametrize("prec", [binding.MIXED, binding.FP64])
+def test_pair_host_driven_loops_give_the_same_bits_as_graph_loops(prec):
     """streaming = 2 launches the pair's kernels eagerly and reads both
     systems' decisions back on the host: the same bits as the conditional
     graph loops."""
     w = _slab(3)
     X0 = rest_X(w)
-    out = [_run(w, X0, 3, streaming=form)[0] for form in (1, 2)]
+    out = [_run(w, X0, 3, streaming=form, precision=prec)[0] for form in (1, 2)]
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
 
@@ -87,12 +106,13 @@ def test_sweep_test_closes_pair_sweeps_on_the_device():
     assert rel(up, us) < 1e-5 and rel(Xp, Xs) < 1e-5
 
 
-def test_profile_counts_a_shared_operator_pass_once():
+@pytest.mark.parametrize("prec", [binding.MIXED, binding.FP64])
+def test_profile_counts_a_shared_operator_pass_once(prec):
     w = _slab(3)
     X0 = rest_X(w)
     prof = {}
     for pair in (0, -1):
-        sim = gpu_sim(w, precision=binding.MIXED, streaming=1, pair_solve=pair)
+        sim = gpu_sim(w, precision=prec, streaming=1, pair_solve=pair)
         sim.set_initial(X0)
         prof[pair] = sim.profile_steps(w.dt, 3, 2, 3)
         sim.close()
