@@ -144,3 +144,35 @@ def test_struct_layouts_match_the_library(lib):
     ours = [ctypes.sizeof(binding.Mesh), ctypes.sizeof(binding.Cond), ctypes.sizeof(binding.Opts),
             ctypes.sizeof(binding.Stats)]
     assert [x.value for x in sz] == ours
+
+
+def _header_struct_fields():
+    """Field names, in order, of every `typedef struct {...} NAME;` in bd.h."""
+    text = open(os.path.join(ROOT, "include", "bd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", text, flags=re.S):
+        names = []
+        for decl in body.split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            fp = re.search(r"\(\s*\*\s*(\w+)\s*\)", decl)            # function pointer
+            if fp:
+                names.append(fp.group(1))
+                continue
+            decl = re.sub(r"\[[^\]]*\]", "", decl)                    # array extents
+            for part in decl.split(","):                               # int a, b;
+                names.append(re.findall(r"(\w+)\s*$", part.strip())[0])
+        out[name] = names
+    return out
+
+
+def test_binding_fields_follow_the_header_in_order():
+    """The ctypes structs name the header's fields in the header's order (equal
+    sizes alone would not catch two fields of one type swapped)."""
+    fields = _header_struct_fields()
+    pairs = {"bd_mesh_t": binding.Mesh, "bd_cond_t": binding.Cond, "bd_opts_t": binding.Opts,
+             "bd_stats_t": binding.Stats, "bd_profile_t": binding.Profile}
+    for cname, cls in pairs.items():
+        assert [f[0] for f in cls._fields_] == fields[cname], cname
