@@ -1,5 +1,7 @@
 // stream.cu -- streaming preconditioned conjugate gradients, for one system
 // whose operators do not fit in L2 and for batches of many small systems.
+// (The row products, reductions and decisions these kernels share with the
+// two-system elliptic chain of stream2.cu live in stream_rows.cuh.)
 //
 // The persistent solvers (pcg.cu, amg.cu, mixed.cu) keep one grid resident
 // for a whole solve and separate its phases with device-wide barriers; that
