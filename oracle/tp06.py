@@ -26,8 +26,10 @@ State order (gates first, then the coupled calcium/concentration block):
   V, m, h, j, d, f, f2, s, r, Xr1, Xr2, Xs, fCass, Rbar, Ki, Nai, Cai, CaSR, CaSS
 
 Parity with the 2006 publication is only partly pinned (the paper prints no
-traces): finite-difference Jacobian, gate bounds and the biomarker ranges of
-Sec. 4 (APD90 of about 354 ms) are the pins.
+traces): finite-difference Jacobian, the fast gates' steady states at the
+published end-diastolic state, every gate's relaxation form, bounds and
+direction, the current balance and the biomarker ranges of Sec. 4 (APD90 of
+about 354 ms) are the pins.
 """
 from __future__ import annotations
 
