@@ -1,6 +1,8 @@
-"""Gate pins of the oracle's TP06 epicardial cell (Sec. 2, "Ten Tusscher
-model") for all twelve gates, the slow ones (j, f, f2, Xr1, Xs, fCass)
-included.
+"""Gate pins of the oracle's membrane models (Sec. 2): all twelve gates of
+the TP06 epicardial cell, the slow ones (j, f, f2, Xr1, Xs, fCass) included,
+and the six gates of LR91 (m, h, j, d, f, X; written as rates,
+dx/dt = alpha (1 - x) - beta x, so x_inf = alpha / (alpha + beta) and
+tau = 1 / (alpha + beta), with alpha, beta >= 0).
 
   * The gate rows of the vector field that the step integrates are the
     relaxations dx/dt = (x_inf - x) / tau.  Each row is affine in its own
@@ -22,7 +24,7 @@ None of them sees a single slow gate's direction or wiring.
 import numpy as np
 import pytest
 
-from oracle import tp06
+from oracle import lr91, tp06
 
 GATES = ("m", "h", "j", "d", "f", "f2", "s", "r", "Xr1", "Xr2", "Xs", "fCass")
 OPENS = ("m", "d", "r", "Xr1", "Xs")                 # activation: x_inf rises with V
@@ -89,3 +91,48 @@ def test_fcass_inactivates_as_subspace_calcium_rises():
     # voltage plays no part in it
     other = tp06.model().gate_inf_tau(np.full_like(cass, 30.0), cass)[GATES.index("fCass")]
     np.testing.assert_array_equal(other[0], xinf)
+
+
+LR91_GATES = ("m", "h", "j", "d", "f", "X")
+LR91_OPENS = ("m", "d", "X")
+LR91_CLOSES = ("h", "j", "f")
+
+
+@pytest.mark.parametrize("paper", [False, True])
+def test_lr91_gate_rows_of_the_field_are_the_rate_relaxations(paper):
+    cell = lr91.model(paper)
+    rng = np.random.default_rng(5)
+    n = 400
+    X = np.repeat(cell.initial()[:, None], n, axis=1)
+    X[0] = rng.uniform(-95.0, 45.0, n)
+    X[1:7] = rng.uniform(0.05, 0.95, (6, n))
+    f0 = cell.field(X, 0.0)
+    rates = cell.rates(X[0])
+    for k, name in enumerate(LR91_GATES):
+        row = 1 + k
+        a, b = rates[k]
+        Xd = X.copy()
+        Xd[row] += 0.25
+        slope = (cell.field(Xd, 0.0)[row] - f0[row]) / 0.25
+        np.testing.assert_allclose(-slope, a + b, rtol=1e-9, err_msg=name)
+        np.testing.assert_allclose(X[row] - f0[row] / slope, a / (a + b), rtol=1e-9, atol=1e-12, err_msg=name)
+        for other in range(1, 7):
+            if other != row:
+                Xo = X.copy()
+                Xo[other] += 0.25
+                np.testing.assert_array_equal(cell.field(Xo, 0.0)[row], f0[row], err_msg=f"{name} <- {other}")
+
+
+@pytest.mark.parametrize("name", LR91_GATES)
+def test_lr91_gates_are_bounded_and_open_or_close_with_depolarisation(name):
+    V = np.linspace(-100.0, 60.0, 1601)
+    a, b = lr91.model().rates(V)[LR91_GATES.index(name)]
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(b))
+    assert np.all(a >= 0.0) and np.all(b >= 0.0) and np.all(a + b > 0.0)
+    xinf = a / (a + b)
+    d = np.diff(xinf)
+    if name in LR91_OPENS:
+        assert np.all(d >= 0.0) and xinf[-1] - xinf[0] > 0.5
+    else:
+        assert name in LR91_CLOSES
+        assert np.all(d <= 0.0) and xinf[0] - xinf[-1] > 0.5
