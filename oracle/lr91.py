@@ -20,7 +20,8 @@ State order: V, m, h, j, d, f, X, Cai.
 Parity of these formulas with the 1991 publication is only partly pinned:
 the paper prints no cell traces.  Pins used: rest state near the published
 -84 mV, biomarker ranges of Sec. 4 (conduction velocity with the paper's
-parameter set), finite-difference Jacobian, gate bounds.
+parameter set), finite-difference Jacobian, every gate's rate relaxation
+form, non-negative rates, bounds and direction.
 """
 from __future__ import annotations
 
